@@ -1,0 +1,171 @@
+"""ctypes binding and build step for the plain-C oracle (``gnm_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring). Every function states the passage
+of the paper it follows in the C source; this file only marshals numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from typing import Dict, Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gnm_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NO_SITE = 0xFFFFFFFF
+NSTAT = 6  # flows, octets, pkts, e_flows, e_octets, e_dur_ms
+# unmatched classes
+NONLOCAL, LOCALLOCAL, IN_UNREG, OUT_UNREG = 0, 1, 2, 3
+IN, OUT = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (portable C11, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-pthread", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = C.CDLL(_LIB)
+            P = C.c_void_p
+            lib.orc_lpm_build.restype = P
+            lib.orc_lpm_build.argtypes = [P, P, P, C.c_size_t, C.POINTER(C.c_int)]
+            lib.orc_lpm_free.argtypes = [P]
+            lib.orc_lpm_lookup.argtypes = [P, P, C.c_size_t, P]
+            lib.orc_lpm_scan.argtypes = [P, P, P, C.c_size_t, P, C.c_size_t, P]
+            lib.orc_flatten.restype = C.c_longlong
+            lib.orc_flatten.argtypes = [P, P, P, C.c_size_t]
+            lib.orc_window.argtypes = [P, P, P, C.c_size_t, C.c_uint32, C.c_uint32, C.c_uint32,
+                                       C.c_uint32, C.c_int, C.c_int] + [P] * 6 + [C.c_size_t, P, P]
+            lib.orc_window_mt.argtypes = [P, P, P, C.c_size_t, C.c_uint32, C.c_uint32, C.c_uint32,
+                                          C.c_uint32, C.c_int] + [P] * 6 + [C.c_size_t, P, P, C.c_int]
+            lib.orc_rates.argtypes = [P, C.c_size_t, P]
+            lib.orc_flags.argtypes = [P, P, C.c_size_t, C.c_double, C.c_uint32, P]
+            lib.orc_rate_bucket.restype = C.c_uint32
+            lib.orc_rate_bucket.argtypes = [C.c_uint32, C.c_uint32]
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class LPM:
+    """Longest-prefix matcher over a registry: hash tables per length, plus the
+    sequential scan of every prefix."""
+
+    ERRORS = {1: "length > 32", 2: "host bits set", 3: "duplicate (prefix, length)", 4: "out of memory"}
+
+    def __init__(self, prefix, plen, site):
+        lib = _load()
+        self._pfx = _c(prefix, np.uint32)
+        self._len = _c(plen, np.uint8)
+        self._site = _c(site, np.uint32)
+        err = C.c_int(0)
+        self._h = lib.orc_lpm_build(_p(self._pfx), _p(self._len), _p(self._site), self._pfx.size,
+                                    C.byref(err))
+        if not self._h:
+            raise ValueError(f"invalid registry: {self.ERRORS.get(err.value, err.value)}")
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.orc_lpm_free(self._h)
+            self._h = None
+
+    def lookup(self, x) -> np.ndarray:
+        x = _c(x, np.uint32)
+        out = np.empty_like(x)
+        _load().orc_lpm_lookup(self._h, _p(x), x.size, _p(out))
+        return out
+
+    def scan(self, x) -> np.ndarray:
+        x = _c(x, np.uint32)
+        out = np.empty_like(x)
+        _load().orc_lpm_scan(_p(self._pfx), _p(self._len), _p(self._site), self._pfx.size, _p(x),
+                             x.size, _p(out))
+        return out
+
+    def flatten(self) -> Tuple[np.ndarray, np.ndarray]:
+        cap = 2 * self._pfx.size + 1
+        st = np.empty(cap, np.uint32)
+        si = np.empty(cap, np.uint32)
+        n = _load().orc_flatten(self._h, _p(st), _p(si), cap)
+        assert n > 0
+        return st[:n].copy(), si[:n].copy()
+
+
+DEFAULT_FILTER = dict(min_avg_pkt_bytes=100, min_pkts=10, min_dur_ms=1000, admin_rule=0)
+
+
+def window(lpm: LPM, local_prefix, local_len, n_sites: int, rec: Dict[str, np.ndarray],
+           min_avg_pkt_bytes: int = 100, min_pkts: int = 10, min_dur_ms: int = 1000,
+           admin_rule: int = 0, use_scan: bool = False, n_threads: int = 0):
+    """Per-window sums. Returns (stats[(2*n_sites), 6] u64, unmatched[4, 3] u64).
+
+    Row site*2+dir holds flows, octets, pkts, e_flows, e_octets, e_dur_ms (dir 0 inbound,
+    1 outbound). ``n_threads`` > 0 uses the threaded variant (hash matcher only)."""
+    lib = _load()
+    lp = _c(local_prefix, np.uint32)
+    ll = _c(local_len, np.uint8)
+    f = [_c(rec[k], np.uint32) for k in ("srcaddr", "dstaddr", "dPkts", "dOctets", "first", "last")]
+    n = f[0].size
+    stats = np.zeros((2 * n_sites, NSTAT), np.uint64)
+    un = np.zeros((4, 3), np.uint64)
+    if n_threads > 0:
+        assert not use_scan
+        rc = lib.orc_window_mt(lpm._h, _p(lp), _p(ll), lp.size, n_sites, min_avg_pkt_bytes, min_pkts,
+                               min_dur_ms, admin_rule, *[_p(a) for a in f], n, _p(stats), _p(un),
+                               n_threads)
+    else:
+        rc = lib.orc_window(lpm._h, _p(lp), _p(ll), lp.size, n_sites, min_avg_pkt_bytes, min_pkts,
+                            min_dur_ms, admin_rule, int(use_scan), *[_p(a) for a in f], n, _p(stats),
+                            _p(un))
+    assert rc == 0
+    return stats, un
+
+
+def rates(stats: np.ndarray) -> np.ndarray:
+    s = _c(stats, np.uint64)
+    out = np.empty(s.shape[0], np.float64)
+    _load().orc_rates(_p(s), s.shape[0], _p(out))
+    return out
+
+
+def flags(stats: np.ndarray, rate: np.ndarray, threshold: float, min_flows: int = 1) -> np.ndarray:
+    s = _c(stats, np.uint64)
+    r = _c(rate, np.float64)
+    out = np.empty(s.shape[0], np.uint8)
+    _load().orc_flags(_p(s), _p(r), s.shape[0], float(threshold), int(min_flows), _p(out))
+    return out
+
+
+def rate_bucket(octets: int, dur: int) -> int:
+    return int(_load().orc_rate_bucket(int(octets), int(dur)))
+
+
+def full_window(lpm: LPM, reg, rec, threshold: float = 1e8, min_flows: int = 1, **kw):
+    """stats, unmatched, rate and flag of one window (the whole per-window definition)."""
+    st, un = window(lpm, reg.local_prefix, reg.local_len, reg.n_sites, rec, **kw)
+    r = rates(st)
+    fl = flags(st, r, threshold, min_flows)
+    return st, un, r, fl

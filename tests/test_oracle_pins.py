@@ -1,0 +1,401 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself:
+hand-worked cases, brute force, closed forms, invariants and library routines.
+
+The paper prints no worked example (no record with its site, rate or bucket), so the
+hand-worked window in tests/golden/window_hand.json carries the definitions of
+Sec. III.B.1-III.B.2.1 and Sec. IV.B through values computed by hand.
+"""
+import ipaddress
+import json
+import os
+
+import numpy as np
+import pytest
+
+import flowgen as fg
+import oracle
+from oracle import rmi_ref
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def ip(s):
+    return int(ipaddress.IPv4Address(s))
+
+
+def load_hand():
+    with open(os.path.join(GOLD, "window_hand.json")) as f:
+        g = json.load(f)
+    reg = np.array([(ip(a), l, s) for a, l, s in g["registry"]], dtype=np.int64)
+    loc = np.array([(ip(a), l) for a, l in g["local"]], dtype=np.int64)
+    cols = {k: [] for k in fg.FIELDS}
+    for r in g["records"]:
+        cols["srcaddr"].append(ip(r[0]))
+        cols["dstaddr"].append(ip(r[1]))
+        cols["dPkts"].append(r[2])
+        cols["dOctets"].append(r[3])
+        cols["first"].append(r[4])
+        cols["last"].append(r[5])
+    rec = {k: np.array(v, dtype=np.uint32) for k, v in cols.items()}
+    return g, reg, loc, rec
+
+
+# ----------------------------------------------------------------- prefix match
+
+HAND_REG = [("10.0.0.0", 8, 0), ("10.1.0.0", 16, 1), ("10.1.2.0", 24, 2), ("10.1.2.4", 30, 3),
+            ("10.1.3.0", 24, 4), ("255.255.255.255", 32, 5), ("192.0.2.0", 25, 6),
+            ("192.0.2.128", 25, 7)]
+HAND_CASES = [("10.0.0.0", 0), ("9.255.255.255", oracle.NO_SITE), ("10.255.255.255", 0),
+              ("11.0.0.0", oracle.NO_SITE), ("10.1.0.0", 1), ("10.1.1.255", 1), ("10.1.2.0", 2),
+              ("10.1.2.3", 2), ("10.1.2.4", 3), ("10.1.2.7", 3), ("10.1.2.8", 2), ("10.1.2.255", 2),
+              ("10.1.3.0", 4), ("10.1.3.255", 4), ("10.1.4.0", 1), ("10.2.0.0", 0),
+              ("255.255.255.255", 5), ("255.255.255.254", oracle.NO_SITE), ("0.0.0.0", oracle.NO_SITE),
+              ("192.0.2.127", 6), ("192.0.2.128", 7), ("192.0.3.0", oracle.NO_SITE)]
+
+
+def _hand_lpm(extra=()):
+    rows = HAND_REG + list(extra)
+    p = np.array([ip(a) for a, _, _ in rows], np.uint32)
+    l = np.array([b for _, b, _ in rows], np.uint8)
+    s = np.array([c for _, _, c in rows], np.uint32)
+    return oracle.LPM(p, l, s)
+
+
+def test_lpm_hand_cases_hash_and_scan():
+    m = _hand_lpm()
+    x = np.array([ip(a) for a, _ in HAND_CASES], np.uint32)
+    want = np.array([s for _, s in HAND_CASES], np.uint32)
+    np.testing.assert_array_equal(m.lookup(x), want)
+    np.testing.assert_array_equal(m.scan(x), want)
+
+
+def test_lpm_default_route():
+    m = _hand_lpm(extra=[("0.0.0.0", 0, 9)])
+    x = np.array([ip(a) for a, _ in HAND_CASES], np.uint32)
+    want = np.array([9 if s == oracle.NO_SITE else s for _, s in HAND_CASES], np.uint32)
+    np.testing.assert_array_equal(m.lookup(x), want)
+    np.testing.assert_array_equal(m.scan(x), want)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_lpm_hash_equals_bruteforce_scan(seed):
+    """Random nested registries inside one /16 (plus a few covering prefixes); every one
+    of the 65,536 addresses of the /16 and its neighbours is matched both ways."""
+    rng = np.random.default_rng(seed)
+    base = ip("172.16.0.0")
+    rows = {}
+    for _ in range(60):
+        l = int(rng.integers(16, 33))
+        a = base + int(rng.integers(0, 1 << 16))
+        a &= (0xFFFFFFFF << (32 - l)) & 0xFFFFFFFF
+        rows[(a, l)] = int(rng.integers(0, 20))
+    rows[(ip("172.0.0.0"), 8)] = 21
+    rows[(ip("172.16.0.0"), 12)] = 22
+    p = np.array([k[0] for k in rows], np.uint32)
+    l = np.array([k[1] for k in rows], np.uint8)
+    s = np.array(list(rows.values()), np.uint32)
+    m = oracle.LPM(p, l, s)
+    x = (np.arange(-256, (1 << 16) + 256, dtype=np.int64) + base).astype(np.uint32)
+    np.testing.assert_array_equal(m.lookup(x), m.scan(x))
+
+
+def test_lpm_rejects_invalid():
+    with pytest.raises(ValueError, match="host bits"):
+        oracle.LPM(np.array([ip("10.0.0.1")], np.uint32), np.array([24], np.uint8), np.array([0], np.uint32))
+    with pytest.raises(ValueError, match="length"):
+        oracle.LPM(np.array([0], np.uint32), np.array([33], np.uint8), np.array([0], np.uint32))
+    with pytest.raises(ValueError, match="duplicate"):
+        oracle.LPM(np.array([ip("10.0.0.0")] * 2, np.uint32), np.array([8, 8], np.uint8),
+                   np.array([0, 1], np.uint32))
+
+
+def test_flatten_matches_lpm_at_every_boundary():
+    reg = fg.registry_c2()
+    m = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    st, si = m.flatten()
+    assert st[0] == 0 and np.all(np.diff(st.astype(np.int64)) > 0)
+    assert np.all(si[1:] != si[:-1])  # neighbours merged
+    probes = np.concatenate([st.astype(np.int64), st.astype(np.int64) - 1, st.astype(np.int64) + 1,
+                             np.random.default_rng(0).integers(0, 1 << 32, 100000)])
+    probes = np.unique(probes[(probes >= 0) & (probes < (1 << 32))]).astype(np.uint32)
+    idx = np.searchsorted(st, probes, side="right") - 1
+    np.testing.assert_array_equal(si[idx], m.lookup(probes))
+
+
+# ----------------------------------------------------------------------- window
+
+def _gold_window(g, reg, loc, rec, **kw):
+    m = oracle.LPM(reg[:, 0], reg[:, 1], reg[:, 2])
+    return oracle.window(m, loc[:, 0], loc[:, 1], g["n_sites"], rec, **kw)
+
+
+@pytest.mark.parametrize("use_scan", [False, True])
+def test_hand_window(use_scan):
+    g, reg, loc, rec = load_hand()
+    st, un = _gold_window(g, reg, loc, rec, use_scan=use_scan)
+    want = np.zeros_like(st)
+    for row in g["expected_rows"]:
+        want[row[0] * 2 + row[1]] = row[2:]
+    np.testing.assert_array_equal(st, want)
+    np.testing.assert_array_equal(un, np.array(g["expected_unmatched"], np.uint64))
+    r = oracle.rates(st)
+    for key, v in g["expected_rates_bps"].items():
+        s, d = map(int, key.split(","))
+        assert r[s * 2 + d] == pytest.approx(v, rel=1e-15)
+    nan_rows = [i for i in range(st.shape[0]) if st[i, 5] == 0]
+    assert np.all(np.isnan(r[nan_rows]))
+    for thr, rows in g["thresholds"].items():
+        fl = oracle.flags(st, r, float(thr))
+        want_fl = np.zeros(st.shape[0], np.uint8)
+        for s, d in rows:
+            want_fl[s * 2 + d] = 1
+        np.testing.assert_array_equal(fl, want_fl)
+
+
+def test_hand_window_and_rule():
+    g, reg, loc, rec = load_hand()
+    st, _ = _gold_window(g, reg, loc, rec, admin_rule=1)
+    want = np.zeros_like(st)
+    for row in g["expected_rows"]:
+        want[row[0] * 2 + row[1]] = row[2:]
+    for row in g["admin_rule_and"]["changed_rows"]:
+        want[row[0] * 2 + row[1]] = row[2:]
+    np.testing.assert_array_equal(st, want)
+    r = oracle.rates(st)
+    for key, v in g["admin_rule_and"]["rates_bps"].items():
+        s, d = map(int, key.split(","))
+        assert r[s * 2 + d] == pytest.approx(v, rel=1e-15)
+
+
+def _one_record_stats(pk, oc, first, last, **kw):
+    """A single outbound record to a one-prefix registry; returns its row."""
+    m = oracle.LPM(np.array([ip("10.0.0.0")], np.uint32), np.array([8], np.uint8),
+                   np.array([0], np.uint32))
+    rec = {k: np.array([v], np.uint32) for k, v in zip(
+        fg.FIELDS, [ip("131.225.0.1"), ip("10.0.0.1"), pk, oc, first, last])}
+    st, _ = oracle.window(m, np.array([ip("131.225.0.0")]), np.array([16]), 1, rec, **kw)
+    return st[1]
+
+
+@pytest.mark.parametrize("pk,oc,first,last,eligible", [
+    (10, 1000, 0, 1000, True),       # avg exactly 100 B, 10 pkts, 1000 ms
+    (10, 999, 0, 1000, False),       # avg 99.9 B
+    (9, 900, 0, 1000, False),        # 9 packets
+    (10, 1000, 0, 999, False),       # 999 ms
+    (10, 1000, 7, 7, False),         # zero duration
+    (10, 1000, 0xFFFFFF00, 0x2E8, True),  # Last < First: 1000 ms across the wrap
+    (10, 1000, 1000, 0, True),       # Last < First: modulo 2^32 a 4,294,966,296 ms flow
+    (0, 0, 0, 5000, False),          # no packets at all
+])
+def test_filter_boundaries(pk, oc, first, last, eligible):
+    row = _one_record_stats(pk, oc, first, last)
+    dur = (last - first) & 0xFFFFFFFF
+    assert row[0] == 1 and row[1] == oc and row[2] == pk
+    assert tuple(row[3:]) == ((1, oc, dur) if eligible else (0, 0, 0))
+
+
+def test_filter_thresholds_are_parameters():
+    row = _one_record_stats(5, 5000, 0, 500, min_pkts=5, min_dur_ms=500, min_avg_pkt_bytes=1000)
+    assert tuple(row[3:]) == (1, 5000, 500)
+    row = _one_record_stats(5, 4999, 0, 500, min_pkts=5, min_dur_ms=500, min_avg_pkt_bytes=1000)
+    assert tuple(row[3:]) == (0, 0, 0)
+
+
+def test_rate_closed_form_and_threshold():
+    # 125,000 bytes in 1,000 ms = 1,000,000 bits/s exactly
+    st = np.zeros((3, oracle.NSTAT), np.uint64)
+    st[0] = [1, 125000, 100, 1, 125000, 1000]
+    st[1] = [3, 10, 1, 2, 1, 3]          # 8000/3 b/s, inexact in binary
+    st[2] = [4, 10, 1, 0, 0, 0]          # no eligible flow
+    r = oracle.rates(st)
+    assert r[0] == 1e6
+    assert r[1] == np.float64(8000.0) / np.float64(3.0)
+    assert np.isnan(r[2])
+    np.testing.assert_array_equal(oracle.flags(st, r, 1e6), [0, 1, 0])
+    np.testing.assert_array_equal(oracle.flags(st, r, np.nextafter(1e6, 2e6)), [1, 1, 0])
+    np.testing.assert_array_equal(oracle.flags(st, r, 1e7, min_flows=2), [0, 1, 0])
+
+
+def test_rate_large_sums_round_once():
+    # sums above 2^53 convert to double with one rounding, then multiply, then divide
+    eo = (1 << 60) + 12345
+    ed = 3
+    st = np.array([[1, eo, 1, 1, eo, ed]], np.uint64)
+    r = oracle.rates(st)[0]
+    assert r == (np.float64(eo) * np.float64(8000.0)) / np.float64(ed)
+
+
+def _c1_window(n=20000, seed=5):
+    reg = fg.registry_c1()
+    rec = fg.window_records_c1(reg, n=n, seed=seed)
+    return reg, rec, oracle.LPM(reg.prefix, reg.plen, reg.site)
+
+
+def test_window_conservation_and_bounds():
+    reg, rec, m = _c1_window()
+    st, un = oracle.window(m, reg.local_prefix, reg.local_len, reg.n_sites, rec)
+    tot_flows = st[:, 0].sum() + un[:, 0].sum()
+    tot_oct = st[:, 1].sum() + un[:, 1].sum()
+    tot_pk = st[:, 2].sum() + un[:, 2].sum()
+    assert tot_flows == rec["srcaddr"].size
+    assert tot_oct == rec["dOctets"].astype(np.uint64).sum()
+    assert tot_pk == rec["dPkts"].astype(np.uint64).sum()
+    assert np.all(st[:, 3] <= st[:, 0]) and np.all(st[:, 4] <= st[:, 1])
+    # generated records always have exactly one local endpoint
+    assert un[0, 0] == 0 and un[1, 0] == 0
+    # eligible durations are bounded by the window's maximum flow duration
+    assert np.all(st[:, 5] <= st[:, 3] * 60000)
+    assert np.all(st[:, 5] >= st[:, 3] * 1000)
+
+
+def test_window_permutation_and_split_invariance():
+    reg, rec, m = _c1_window()
+    a, ua = oracle.window(m, reg.local_prefix, reg.local_len, reg.n_sites, rec)
+    perm = np.random.default_rng(1).permutation(rec["srcaddr"].size)
+    b, ub = oracle.window(m, reg.local_prefix, reg.local_len, reg.n_sites,
+                          {k: v[perm] for k, v in rec.items()})
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(ua, ub)
+    cut = 7777
+    p1, q1 = oracle.window(m, reg.local_prefix, reg.local_len, reg.n_sites, {k: v[:cut] for k, v in rec.items()})
+    p2, q2 = oracle.window(m, reg.local_prefix, reg.local_len, reg.n_sites, {k: v[cut:] for k, v in rec.items()})
+    np.testing.assert_array_equal(a, p1 + p2)
+    np.testing.assert_array_equal(ua, q1 + q2)
+
+
+def test_window_scan_equals_hash_and_threads():
+    reg, rec, m = _c1_window(n=4000)
+    a, ua = oracle.window(m, reg.local_prefix, reg.local_len, reg.n_sites, rec)
+    b, ub = oracle.window(m, reg.local_prefix, reg.local_len, reg.n_sites, rec, use_scan=True)
+    c, uc = oracle.window(m, reg.local_prefix, reg.local_len, reg.n_sites, rec, n_threads=3)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(a, c)
+    np.testing.assert_array_equal(ua, ub)
+    np.testing.assert_array_equal(ua, uc)
+
+
+def test_window_direction_from_numpy_definition():
+    """Independent numpy restatement of the direction and key assignment on C1 data:
+    per-key flow counts must agree with the oracle."""
+    reg, rec, m = _c1_window(n=20000)
+    st, un = oracle.window(m, reg.local_prefix, reg.local_len, reg.n_sites, rec)
+    src, dst = rec["srcaddr"].astype(np.int64), rec["dstaddr"].astype(np.int64)
+
+    def local(a):
+        out = np.zeros(a.shape, bool)
+        for p, l in zip(reg.local_prefix, reg.local_len):
+            out |= (a >> (32 - int(l))) == (int(p) >> (32 - int(l)))
+        return out
+
+    sl, dl = local(src), local(dst)
+    out_ = sl & ~dl
+    in_ = dl & ~sl
+    flat_s, flat_site = m.flatten()
+    remote = np.where(out_, dst, src).astype(np.uint32)
+    site = flat_site[np.searchsorted(flat_s, remote, side="right") - 1]
+    key = site.astype(np.int64) * 2 + out_.astype(np.int64)
+    ok = (out_ | in_) & (site != oracle.NO_SITE)
+    counts = np.bincount(key[ok], minlength=2 * reg.n_sites)
+    np.testing.assert_array_equal(st[:, 0], counts)
+    assert un[3, 0] == np.sum(out_ & (site == oracle.NO_SITE))
+    assert un[2, 0] == np.sum(in_ & (site == oracle.NO_SITE))
+
+
+def test_rate_bucket_closed_form():
+    # 1,250 bytes in 1 s = 10,000 b/s: first byte of bucket 1
+    assert oracle.rate_bucket(1250, 1000) == 1
+    assert oracle.rate_bucket(1249, 1000) == 0
+    assert oracle.rate_bucket(1_250_000, 1000) == 1000           # 10 Mb/s
+    assert oracle.rate_bucket(12_500_000, 1000) == 10000         # 100 Mb/s: last bucket
+    assert oracle.rate_bucket(0xFFFFFFFF, 1) == 10000            # capped
+
+
+# ---------------------------------------------------------- learned-index maths
+
+def test_lstsq_line_equals_polyfit():
+    rng = np.random.default_rng(0)
+    x = rng.random(5000) * 1e6
+    y = 3.5 * x - 17 + rng.normal(0, 50, x.size)
+    a, b = rmi_ref.lstsq_line(x, y)
+    pa, pb = np.polyfit(x, y, 1)
+    assert a == pytest.approx(pa, rel=1e-10)
+    assert b == pytest.approx(pb, rel=1e-8, abs=1e-6)
+
+
+def test_linear_grad_finite_difference():
+    rng = np.random.default_rng(1)
+    z = rng.normal(size=1000)
+    y = 2 * z + 1 + rng.normal(size=1000)
+    w, c, h = 0.3, -0.2, 1e-6
+    _, gw, gc = rmi_ref.linear_grad(w, c, z, y)
+    fw = (rmi_ref.linear_grad(w + h, c, z, y)[0] - rmi_ref.linear_grad(w - h, c, z, y)[0]) / (2 * h)
+    fc = (rmi_ref.linear_grad(w, c + h, z, y)[0] - rmi_ref.linear_grad(w, c - h, z, y)[0]) / (2 * h)
+    assert gw == pytest.approx(fw, rel=1e-6)
+    assert gc == pytest.approx(fc, rel=1e-6)
+
+
+def test_mlp_grad_finite_difference():
+    rng = np.random.default_rng(2)
+    H = 32
+    p = {"w1": rng.normal(size=H), "b1": rng.normal(size=H) * 0.1, "w2": rng.normal(size=H),
+         "b2": 0.05}
+    xn = rng.random(2000)
+    y = np.sqrt(xn) * 100
+    _, g = rmi_ref.mlp_loss_grad(p, xn, y)
+    h = 1e-6
+    for name in ("w1", "b1", "w2"):
+        for j in (0, 7, 31):
+            q = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in p.items()}
+            q[name][j] += h
+            lp = rmi_ref.mlp_loss_grad(q, xn, y)[0]
+            q[name][j] -= 2 * h
+            lm = rmi_ref.mlp_loss_grad(q, xn, y)[0]
+            assert g[name][j] == pytest.approx((lp - lm) / (2 * h), rel=1e-4, abs=1e-6)
+    lp = rmi_ref.mlp_loss_grad({**p, "b2": p["b2"] + h}, xn, y)[0]
+    lm = rmi_ref.mlp_loss_grad({**p, "b2": p["b2"] - h}, xn, y)[0]
+    assert g["b2"] == pytest.approx((lp - lm) / (2 * h), rel=1e-6)
+    # forward agrees with the explicit formula
+    out = rmi_ref.mlp_forward(p, xn[:3])
+    want = [sum(p["w2"][j] * max(p["w1"][j] * v + p["b1"][j], 0) for j in range(H)) + p["b2"] for v in xn[:3]]
+    np.testing.assert_allclose(out, want, rtol=1e-12)
+
+
+def test_eps_endpoints_bound_holds_and_is_tight():
+    """The per-leaf error bound from range endpoints against predictions at many
+    sampled addresses (all range boundaries +-1 and random ones)."""
+    reg = fg.registry_c1()
+    m = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    st, _ = m.flatten()
+    n, L = st.size, 64
+    # a crude monotone model: root and leaves from least squares on the starts
+    pos = np.arange(n, dtype=np.float64)
+    ra, rb = rmi_ref.lstsq_line(st.astype(np.float64) / 2 ** 32, pos * L / n)
+    ra = max(ra, 0.0)
+    leaf_of_start = rmi_ref.root_linear(ra, rb, st, L)
+    a = np.zeros(L)
+    b = np.zeros(L)
+    x0 = np.zeros(L, np.int64)
+    for l in range(L):
+        sel = leaf_of_start == l
+        if sel.sum() >= 2:
+            x0[l] = int(st[sel][0])
+            al, bl = rmi_ref.lstsq_line(st[sel].astype(np.float64) - x0[l], pos[sel])
+            a[l], b[l] = max(al, 0.0), bl
+    elo, ehi = rmi_ref.eps_endpoints_linear(st, ra, rb, a, b, x0, L)
+    s64 = st.astype(np.int64)
+    lf = rmi_ref.leaf_first_addresses(ra, rb, L)
+    probes = np.concatenate([s64, s64 - 1, s64 + 1, lf, lf - 1,
+                             np.random.default_rng(0).integers(0, 1 << 32, 200000)])
+    probes = np.unique(probes[(probes >= 0) & (probes < (1 << 32))])
+    t = np.searchsorted(st, probes.astype(np.uint32), side="right") - 1
+    leaf = rmi_ref.root_linear(ra, rb, probes.astype(np.uint32), L)
+    p = rmi_ref.leaf_predict(a, b, x0, leaf, probes, n)
+    assert np.all(p - t <= elo[leaf])
+    assert np.all(t - p <= ehi[leaf])
+    # tight: the bound is reached at some sampled endpoint of every non-empty leaf
+    got_lo = np.zeros(L, np.int64)
+    got_hi = np.zeros(L, np.int64)
+    np.maximum.at(got_lo, leaf, np.maximum(p - t, 0))
+    np.maximum.at(got_hi, leaf, np.maximum(t - p, 0))
+    np.testing.assert_array_equal(got_lo, elo)
+    np.testing.assert_array_equal(got_hi, ehi)
