@@ -1,0 +1,326 @@
+/*
+ * gnm.h -- C ABI of the GB300 flow-analysis library (G-NetMon hot path).
+ *
+ * Paper: W. Wu, P. DeMar, D. Holmgren, A. Singh, R. Pordes, "G-NetMon: A GPU-accelerated
+ * Network Performance Monitoring System for Large Scale Scientific Collaborations".
+ *
+ * The library computes, for every window of NetFlow-v5-shaped flow records:
+ *   - the remote endpoint's collaboration site, by longest-prefix match against the
+ *     registered subnets (Sec. III.B.1 "Site Registration Thread", Sec. III.B.2.1
+ *     "Catalog Kernel" / "TransRate Kernel");
+ *   - per (site, direction) unsigned 64-bit sums of flows, octets and packets of every
+ *     record between the local site and a registered site, and of flows, octets and
+ *     durations of the records that pass the ACK and administrative filters
+ *     (Sec. III.B.2.1);
+ *   - the site transfer rate in bits per second, 8000 * sum(octets) / sum(duration ms)
+ *     over eligible records, and a sub-optimal flag when the rate is strictly below a
+ *     supplied standard (Sec. III.B.1 "NetPerf Monitoring Thread", Sec. IV.B).
+ *
+ * Conventions (all calls):
+ *   - every call returns a gnm_status and never throws or aborts; on failure
+ *     gnm_last_error() holds a message for the calling thread;
+ *   - a context is used by one host thread at a time;
+ *   - record arrays are owned by the caller and never freed or retained by the library;
+ *     device pointers must stay valid until the work queued on the stream has finished;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream);
+ *     work is queued on it and no call synchronises the host unless it returns host
+ *     data (gnm_site_stats, gnm_flag_suboptimal, gnm_window_dense and the reports);
+ *   - site ids are dense in [0, n_sites); direction 0 = inbound (remote endpoint is the
+ *     source), 1 = outbound (remote endpoint is the destination);
+ *   - an output array that is too small gives GNM_E_CAPACITY with *n_out set to the
+ *     required count.
+ */
+#ifndef GNM_H
+#define GNM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GNM_NO_SITE 0xFFFFFFFFu
+#define GNM_NSTAT 6     /* flows, octets, pkts, e_flows, e_octets, e_dur_ms */
+#define GNM_MAX_LOCAL 8 /* local-site prefixes */
+
+typedef enum {
+    GNM_OK = 0,
+    GNM_E_INVAL = 1,    /* bad argument or registry */
+    GNM_E_NOMEM = 2,    /* host or device allocation failed */
+    GNM_E_CUDA = 3,     /* a CUDA runtime call failed */
+    GNM_E_STATE = 4,    /* wrong call order, unknown window id */
+    GNM_E_CAPACITY = 5, /* output array too small; *n_out holds the required count */
+    GNM_E_TIMEOUT = 6,  /* a bounded device or host wait gave up */
+    GNM_E_INTERNAL = 7  /* a device-side consistency check failed */
+} gnm_status;
+
+enum { GNM_LOOKUP_AUTO = 0, GNM_LOOKUP_BSEARCH = 1, GNM_LOOKUP_RMI = 2 };
+enum { GNM_PLACE_AUTO = 0, GNM_PLACE_SMEM = 1, GNM_PLACE_L2 = 2 };
+enum { GNM_AGG_AUTO = 0, GNM_AGG_DIRECT = 1, GNM_AGG_WARP = 2 };
+enum { GNM_ADMIN_OR = 0, GNM_ADMIN_AND = 1 };
+/* Per-CTA accumulation: a shared-memory row per key (DIRECT, when all keys fit), a
+ * shared-memory hash table of the keys a CTA meets with global atomics for the overflow
+ * (HASH), or warp-aggregated global atomics only (GLOBAL). */
+enum { GNM_TABLE_AUTO = 0, GNM_TABLE_DIRECT = 1, GNM_TABLE_HASH = 2, GNM_TABLE_GLOBAL = 3 };
+
+/* Filters and execution knobs. The paper fixes none of the filter constants
+ * (Sec. III.B.2.1 says only "average packet size ... usually small" and "small number
+ * of packets with short durations"); the defaults are this library's reading. */
+typedef struct {
+    uint32_t min_avg_pkt_bytes; /* eligible needs dOctets >= this * dPkts (default 100) */
+    uint32_t min_pkts;          /* administrative filter: packets (default 10) */
+    uint32_t min_dur_ms;        /* administrative filter: duration (default 1000) */
+    uint32_t min_flows_to_flag; /* a key needs this many eligible flows to be flagged (1) */
+    int32_t admin_rule;         /* GNM_ADMIN_OR: exclude if few packets OR short (default);
+                                   GNM_ADMIN_AND: exclude only if both */
+    int32_t lookup_mode;        /* GNM_LOOKUP_*: prefix-match method */
+    int32_t placement;          /* GNM_PLACE_*: registry in shared memory or L2 */
+    int32_t aggregation;        /* GNM_AGG_*: shared-memory atomics per record, or
+                                   warp-aggregated */
+    int32_t device;             /* CUDA device ordinal (default 0) */
+    uint32_t window_slots;      /* per-window result slots kept on the device (64) */
+    double threshold_bps;       /* flag standard used when a window is finalised (1e8) */
+    int32_t block_threads;      /* 0: tuned default; else 128..1024, multiple of 32 */
+    int32_t ctas_per_sm;        /* 0: tuned default; else 1..8 */
+    int32_t unroll;             /* 0: tuned default; else 1 or 2 (4-record groups per
+                                   thread per iteration) */
+    int32_t table_mode;         /* GNM_TABLE_*: where a CTA accumulates its sums */
+    uint32_t hash_slots;        /* GNM_TABLE_HASH size: 0 = largest that fits, else a
+                                   power of two in 256..32768 */
+    uint32_t reserved;
+} gnm_config;
+
+/* One struct-of-arrays batch of NetFlow v5 fields (Sec. IV.A.3: 48-byte v5 records; only
+ * the six fields below are read). Element i of every array is record i. Device arrays
+ * that share the same address modulo 16 bytes are read with 16-byte vector loads; any
+ * other 4-byte alignment is read element by element. */
+typedef struct {
+    uint64_t n;
+    const uint32_t *srcaddr, *dstaddr; /* IPv4 addresses, host byte order */
+    const uint32_t *dPkts, *dOctets;   /* packets and layer-3 bytes of the flow */
+    const uint32_t *first, *last;      /* router uptime (ms) at first / last packet */
+    const uint16_t *srcport, *dstport; /* not read; may be NULL */
+    const uint8_t *prot;               /* not read; may be NULL */
+    int32_t on_device;                 /* 1: device pointers; 0: host pointers (copied
+                                          through a library-owned staging buffer) */
+} gnm_records;
+
+typedef struct {
+    uint32_t site, dir;
+    uint64_t flows, octets, pkts, e_flows, e_octets, e_dur_ms;
+    double rate_bps; /* NaN when e_dur_ms == 0 */
+    uint32_t flag;   /* against the context's threshold_bps */
+    uint32_t reserved;
+} gnm_site_stat;
+
+typedef struct {
+    uint64_t n_ranges;      /* disjoint address ranges after flattening */
+    uint64_t n_registered;  /* ranges that carry a site */
+    uint32_t n_sites;
+    uint32_t n_prefixes;
+    int32_t placement;      /* resolved GNM_PLACE_* */
+    int32_t lookup_mode;    /* resolved GNM_LOOKUP_* */
+    int32_t privatized;     /* per-CTA shared-memory sums in use */
+    int32_t rmi_ready;
+} gnm_registry_info;
+
+typedef struct gnm_ctx gnm_ctx;
+
+/* Fills *cfg with the defaults listed above. */
+void gnm_config_default(gnm_config *cfg);
+
+/* Creates a context on cfg->device (NULL cfg = defaults). Owns all device state. */
+gnm_status gnm_create(const gnm_config *cfg, gnm_ctx **out);
+
+/* Releases the context and all device memory it owns (synchronises its work). */
+void gnm_destroy(gnm_ctx *ctx);
+
+/* Message of the last failure on this thread (empty string if none). */
+const char *gnm_last_error(const gnm_ctx *ctx);
+
+/* Registers the collaboration sites' subnets and the local site (Sec. III.B.1 "Site
+ * Registration Thread"; the "Site Catalog"). prefix[i]/len[i] is a CIDR block, host
+ * order, with site_id[i] < n_sites. Prefixes may nest: an address belongs to the site of
+ * the longest prefix that contains it. Rejected with GNM_E_INVAL: len > 32, host bits
+ * set, the same (prefix, len) twice, site_id >= n_sites, n_local == 0 or > GNM_MAX_LOCAL,
+ * a local prefix that overlaps a registered one. All arrays are host memory and are
+ * copied. Replaces any earlier registry (and drops the learned index and all window
+ * results). The flattened ranges are uploaded once and stay resident. */
+gnm_status gnm_registry_load(gnm_ctx *ctx, const uint32_t *prefix, const uint8_t *len,
+                             const uint32_t *site_id, size_t n, uint32_t n_sites,
+                             const uint32_t *local_prefix, const uint8_t *local_len,
+                             size_t n_local);
+
+gnm_status gnm_registry_info_get(gnm_ctx *ctx, gnm_registry_info *out);
+
+/* Host-only form of the registry step (no context, no GPU): validates the registry as
+ * gnm_registry_load does and writes the flattened ranges (see gnm_registry_ranges).
+ * *n_out receives the number of ranges (GNM_E_CAPACITY if cap is smaller). */
+gnm_status gnm_registry_flatten(const uint32_t *prefix, const uint8_t *len,
+                                const uint32_t *site_id, size_t n, uint32_t n_sites,
+                                uint32_t *starts, uint32_t *site, size_t cap, size_t *n_out);
+
+/* Copies the flattened registry to host arrays: starts[i] is the first address of
+ * range i (starts[0] = 0, strictly increasing), site[i] its site or GNM_NO_SITE.
+ * GNM_E_CAPACITY if cap < n_ranges. */
+gnm_status gnm_registry_ranges(gnm_ctx *ctx, uint32_t *starts, uint32_t *site, size_t cap,
+                               size_t *n_out);
+
+/* Processes one window (Sec. III.B.1: the NetPerf thread hands a batch of records to the
+ * kernels; Sec. III.B.2.1 TransRate Kernel). Results go to the window's device slot
+ * (reusing the oldest slot when all are taken) and are finalised (rates, flags) in the
+ * same launch. window_id is any caller-chosen key; processing an id again replaces its
+ * results. Host records (on_device = 0) are copied on `stream` first. n must be below
+ * 2^32 so that the 64-bit sums cannot overflow. */
+gnm_status gnm_window_process(gnm_ctx *ctx, const gnm_records *rec, uint64_t window_id,
+                              void *stream);
+
+/* Many windows in one launch: window k is records [offsets[k], offsets[k+1]) of the
+ * struct-of-arrays `rec` (rec->n >= offsets[n_win]); offsets is host memory,
+ * non-decreasing, offsets[0] may be > 0. Each window gets its own slot and is finalised
+ * when its last CTA finishes. Empty windows are allowed. */
+gnm_status gnm_windows_process(gnm_ctx *ctx, const gnm_records *rec, const uint64_t *offsets,
+                               const uint64_t *window_ids, size_t n_win, void *stream);
+
+/* Streaming form of a window: open (zero the sums), add any number of batches, close
+ * (finalise). Between open and close the window's sums are partial. */
+gnm_status gnm_window_open(gnm_ctx *ctx, uint64_t window_id, void *stream);
+gnm_status gnm_window_add(gnm_ctx *ctx, const gnm_records *rec, uint64_t window_id,
+                          void *stream);
+gnm_status gnm_window_close(gnm_ctx *ctx, uint64_t window_id, void *stream);
+
+/* Per-site statistics of a window (synchronises with the window's work). Writes the
+ * keys with at least one flow, ordered by (site, dir), into out[0..*n_out). unmatched,
+ * if not NULL, receives 4 classes x {flows, octets, pkts}: 0 neither endpoint local,
+ * 1 both endpoints local, 2 inbound from an unregistered address, 3 outbound to one.
+ * GNM_E_STATE for an unknown or evicted window id. */
+gnm_status gnm_site_stats(gnm_ctx *ctx, uint64_t window_id, gnm_site_stat *out, size_t cap,
+                          size_t *n_out, uint64_t unmatched[12]);
+
+/* Sub-optimal (site, dir) keys of a window: at least min_flows_to_flag eligible flows
+ * and rate strictly below threshold_bps (Sec. III.B.1, Sec. IV.B "less than"). Computed
+ * on the device against this threshold, compacted, then copied to site_out/dir_out. */
+gnm_status gnm_flag_suboptimal(gnm_ctx *ctx, uint64_t window_id, double threshold_bps,
+                               uint32_t *site_out, uint8_t *dir_out, size_t cap, size_t *n_out);
+
+/* Dense copies of a window's results to host arrays (each may be NULL):
+ * stats[(2*n_sites) x GNM_NSTAT] (row site*2+dir), unmatched[12], rate[2*n_sites],
+ * flag[2*n_sites] (against the context threshold). Synchronises with the window. */
+gnm_status gnm_window_dense(gnm_ctx *ctx, uint64_t window_id, uint64_t *stats,
+                            uint64_t *unmatched, double *rate, uint8_t *flag);
+
+/* Device addresses of a window's dense results (same layouts as gnm_window_dense; the
+ * stats block has 2*n_sites+4 rows, the last four being the unmatched classes with
+ * e_* columns zero). Valid until the slot is reused or the registry is replaced. No
+ * synchronisation: order reads after the window's stream. */
+gnm_status gnm_window_device(gnm_ctx *ctx, uint64_t window_id, const uint64_t **stats,
+                             const double **rate, const uint8_t **flag);
+
+/* Forgets a window id (its slot becomes free). */
+gnm_status gnm_window_release(gnm_ctx *ctx, uint64_t window_id);
+
+/* Longest-prefix match of n device addresses: site_out[i] (device, may be NULL) gets the
+ * site or GNM_NO_SITE, pos_out[i] (device, may be NULL) the index of the flattened range.
+ * Uses the context's lookup mode. */
+gnm_status gnm_lookup(gnm_ctx *ctx, const uint32_t *addr, uint64_t n, uint32_t *site_out,
+                      uint32_t *pos_out, void *stream);
+
+/* ----------------------------------------------------------------- learned index */
+
+/* Two-stage recursive model index over the flattened range starts (not in the paper;
+ * Kraska et al. 2018). It predicts the position of an address; an exact search within
+ * [pred - eps_lo, pred + eps_hi] of the leaf finishes the lookup and a full binary search
+ * is the fallback whenever that window does not hold the answer, so results never depend
+ * on the model. */
+enum { GNM_RMI_ROOT_LINEAR = 0, GNM_RMI_ROOT_MLP = 1 };
+
+typedef struct {
+    int32_t root_kind;   /* GNM_RMI_ROOT_* */
+    uint32_t n_leaves;   /* 1..65536 (4096) */
+    uint32_t hidden;     /* MLP root width, 1..32 (32) */
+    uint32_t leaf_iters; /* gradient steps for the linear stages (4) */
+    uint32_t mlp_steps;  /* Adam steps for the MLP root (600) */
+    uint32_t mlp_batch;  /* samples per Adam step (65536) */
+    float mlp_lr;        /* Adam learning rate (0.01) */
+    uint32_t seed;       /* initialisation and mini-batch sampling seed */
+    int32_t exhaustive_eps; /* 1: error bounds from all 2^32 addresses (default);
+                               0: from the training samples only (the verify-and-
+                               fall-back path keeps results exact either way) */
+} gnm_rmi_config;
+
+typedef struct {
+    uint64_t n_train;
+    double root_loss, leaf_loss;  /* final mean squared errors */
+    uint32_t eps_max;             /* max over leaves of eps_lo + eps_hi */
+    double eps_mean;              /* mean window width (eps_lo + eps_hi + 1) per leaf,
+                                     weighted by training samples */
+    uint32_t empty_leaves;
+    double train_ms, sweep_ms;
+} gnm_rmi_report;
+
+void gnm_rmi_config_default(gnm_rmi_config *cfg);
+
+/* Trains the learned index on the GPU from n device addresses `keys` (the lookups the
+ * plain binary search answers; their positions are computed by it), then computes the
+ * per-leaf error bounds. Sets the lookup mode to GNM_LOOKUP_RMI on success. */
+gnm_status gnm_rmi_train(gnm_ctx *ctx, const uint32_t *keys, uint64_t n,
+                         const gnm_rmi_config *cfg, gnm_rmi_report *report, void *stream);
+
+/* Number of lookups since the last reset whose model window missed the answer and fell
+ * back to the full binary search (0 when the error bounds hold). */
+gnm_status gnm_rmi_violations(gnm_ctx *ctx, uint64_t *count, int reset);
+
+/* Gradient of the mean squared error of one linear stage yhat = w*z + c over n device
+ * samples (z float, y float): grad[0] = dL/dw, grad[1] = dL/dc, grad[2] = L (host out).
+ * Exposed so the training arithmetic can be checked against an FP64 reference. */
+gnm_status gnm_rmi_linear_grad(gnm_ctx *ctx, const float *z, const float *y, uint64_t n,
+                               float w, float c, double grad[3], void *stream);
+
+/* Gradient of the mean squared error of the 1 -> H -> 1 ReLU root over n device samples
+ * (xn float in [0,1), y float). params (host) = w1[H], b1[H], w2[H], b2; grad (host) has
+ * the same layout, followed by the loss. */
+gnm_status gnm_rmi_mlp_grad(gnm_ctx *ctx, const float *xn, const float *y, uint64_t n,
+                            uint32_t hidden, const float *params, double *grad, void *stream);
+
+/* Copies the trained model to host arrays (any may be NULL): root[2 + 3*32 + 1]
+ * (ra, rb, w1[32], b1[32], w2[32], b2), a/b/x0/eps_lo/eps_hi[n_leaves]. */
+gnm_status gnm_rmi_export(gnm_ctx *ctx, int32_t *root_kind, uint32_t *n_leaves, float *root,
+                          float *a, float *b, uint32_t *x0, uint32_t *eps_lo, uint32_t *eps_hi);
+
+/* Installs a model (same layout as gnm_rmi_export) and computes its error bounds by the
+ * exhaustive sweep over all 2^32 addresses. */
+gnm_status gnm_rmi_import(gnm_ctx *ctx, int32_t root_kind, uint32_t n_leaves, const float *root,
+                          const float *a, const float *b, const uint32_t *x0, void *stream);
+
+/* ------------------------------------------------------- batched plans and tuning */
+
+typedef struct gnm_plan gnm_plan;
+
+/* A reusable launch of gnm_windows_process over fixed device buffers and window shapes,
+ * captured once into a CUDA graph (zeroing of the result slots + the persistent
+ * aggregation kernel, which finalises each window). */
+gnm_status gnm_plan_create(gnm_ctx *ctx, const gnm_records *rec, const uint64_t *offsets,
+                           const uint64_t *window_ids, size_t n_win, gnm_plan **out);
+gnm_status gnm_plan_launch(gnm_plan *plan, void *stream);
+void gnm_plan_destroy(gnm_plan *plan);
+
+typedef struct {
+    int32_t block_threads, ctas_per_sm, unroll, aggregation, placement;
+    double best_ms, default_ms;
+    uint32_t n_tried;
+} gnm_tune_report;
+
+/* Times candidate launch shapes (block size, CTAs per SM, records per thread,
+ * aggregation, registry placement) on these windows with CUDA events, keeps the fastest
+ * in the context and reports it. Results of the windows are those of the last run. */
+gnm_status gnm_autotune(gnm_ctx *ctx, const gnm_records *rec, const uint64_t *offsets,
+                        const uint64_t *window_ids, size_t n_win, gnm_tune_report *report);
+
+/* Number of kernels the last processing call enqueued (for launch accounting). */
+uint32_t gnm_last_launch_count(const gnm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GNM_H */

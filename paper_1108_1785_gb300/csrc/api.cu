@@ -1,0 +1,780 @@
+// api.cu -- the C ABI: contexts, registry upload, window processing and result readout.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctx.hpp"
+
+namespace gnm {
+
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+const char* get_error() { return g_err.c_str(); }
+gnm_status fail(gnm_status s, const std::string& m) {
+    set_error(m);
+    return s;
+}
+
+std::string flatten_registry(const uint32_t* prefix, const uint8_t* len, const uint32_t* site,
+                             size_t n, uint32_t n_sites, std::vector<uint32_t>* starts,
+                             std::vector<uint32_t>* sites);
+bool local_overlaps(uint32_t lp, uint8_t ll, const uint32_t* prefix, const uint8_t* len, size_t n);
+
+constexpr uint32_t kRingSize = 16;
+constexpr size_t kRegistrySmemMax = 96 * 1024;   // bytes of ranges kept in shared memory
+constexpr size_t kDirectTableMax = 120 * 1024;   // direct-indexed per-CTA sums
+constexpr size_t kHashTableMax = 176 * 1024;     // hashed per-CTA sums
+constexpr uint32_t kFinalizeInKernelMaxKeys = 65536;
+constexpr uint64_t kMaxWindowRecords = 0xFFFFFFFFull;
+
+static uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+static void free_dev(void* p) {
+    if (p) cudaFree(p);
+}
+
+// ------------------------------------------------------------------ slots
+
+static gnm_status wait_slot_on_stream(gnm_ctx* c, uint32_t s, cudaStream_t st) {
+    Slot& sl = c->slots[s];
+    if (sl.ev_recorded) GNM_CU(cudaStreamWaitEvent(st, sl.ev, 0));
+    return GNM_OK;
+}
+
+gnm_status acquire_slot(gnm_ctx* c, uint64_t wid, cudaStream_t st, uint32_t* out) {
+    auto it = c->slot_of.find(wid);
+    uint32_t s;
+    if (it != c->slot_of.end()) {
+        s = it->second;
+    } else {
+        s = UINT32_MAX;
+        for (uint32_t i = 0; i < c->n_slots; ++i)
+            if (!c->slots[i].used) { s = i; break; }
+        if (s == UINT32_MAX) {  // evict the oldest window
+            uint64_t best = UINT64_MAX;
+            for (uint32_t i = 0; i < c->n_slots; ++i)
+                if (c->slots[i].age < best) { best = c->slots[i].age; s = i; }
+            c->slot_of.erase(c->slots[s].window_id);
+        }
+        c->slot_of[wid] = s;
+    }
+    GNM_TRY(wait_slot_on_stream(c, s, st));
+    Slot& sl = c->slots[s];
+    if (sl.used && sl.open) {  // partial sums of an unfinished window: clear them
+        GNM_CU(cudaMemsetAsync(c->d_acc + (size_t)s * c->keys * kAccCols, 0,
+                               (size_t)c->keys * kAccCols * 8, st));
+    }
+    sl.used = true;
+    sl.open = false;
+    sl.finalized = false;
+    sl.window_id = wid;
+    sl.records = 0;
+    sl.age = ++c->age;
+    *out = s;
+    return GNM_OK;
+}
+
+static gnm_status mark_slot(gnm_ctx* c, uint32_t s, cudaStream_t st) {
+    Slot& sl = c->slots[s];
+    GNM_CU(cudaEventRecord(sl.ev, st));
+    sl.ev_recorded = true;
+    return GNM_OK;
+}
+
+void release_slots(gnm_ctx* c) {
+    for (auto& s : c->slots)
+        if (s.ev) cudaEventDestroy(s.ev);
+    c->slots.clear();
+    c->slot_of.clear();
+    free_dev(c->d_acc);
+    free_dev(c->d_stats);
+    free_dev(c->d_rate);
+    free_dev(c->d_flag);
+    free_dev(c->d_flag_keys);
+    c->d_acc = nullptr;
+    c->d_stats = nullptr;
+    c->d_rate = nullptr;
+    c->d_flag = nullptr;
+    c->d_flag_keys = nullptr;
+    c->n_slots = 0;
+}
+
+static gnm_status find_window(gnm_ctx* c, uint64_t wid, uint32_t* s) {
+    if (!c->have_registry) return fail(GNM_E_STATE, "no registry loaded");
+    auto it = c->slot_of.find(wid);
+    if (it == c->slot_of.end())
+        return fail(GNM_E_STATE, "unknown or evicted window id " + std::to_string(wid));
+    *s = it->second;
+    return GNM_OK;
+}
+
+// ------------------------------------------------------------- launch buffers
+
+static gnm_status acquire_ring(gnm_ctx* c, uint32_t n_win, LaunchBuf** out) {
+    LaunchBuf& b = c->ring[c->ring_next];
+    c->ring_next = (c->ring_next + 1) % kRingSize;
+    if (b.ev_recorded) GNM_CU(cudaEventSynchronize(b.ev));  // its previous launch is done
+    if (b.cap < n_win) {
+        const uint32_t cap = std::max<uint32_t>(n_win, 64);
+        if (b.h_wins) cudaFreeHost(b.h_wins);
+        free_dev(b.d_wins);
+        free_dev(b.d_done);
+        b.h_wins = nullptr;
+        b.d_wins = nullptr;
+        b.d_done = nullptr;
+        b.cap = 0;
+        GNM_CU(cudaMallocHost(&b.h_wins, sizeof(WinDesc) * cap));
+        GNM_CU(cudaMalloc(&b.d_wins, sizeof(WinDesc) * cap));
+        GNM_CU(cudaMalloc(&b.d_done, sizeof(uint32_t) * cap));
+        GNM_CU(cudaMemset(b.d_done, 0, sizeof(uint32_t) * cap));
+        b.cap = cap;
+    }
+    *out = &b;
+    return GNM_OK;
+}
+
+static gnm_status stage_records(gnm_ctx* c, const gnm_records* rec, uint64_t lo, uint64_t hi,
+                                cudaStream_t st, const uint32_t* out[6]) {
+    Staging& g = c->staging;
+    if (g.ev_recorded) GNM_CU(cudaEventSynchronize(g.ev));
+    const uint64_t n = hi - lo;
+    if (g.cap < n) {
+        for (auto& p : g.d) {
+            free_dev(p);
+            p = nullptr;
+        }
+        g.cap = 0;
+        const uint64_t cap = std::max<uint64_t>(n, 1 << 16);
+        for (auto& p : g.d) GNM_CU(cudaMalloc(&p, cap * 4));
+        g.cap = cap;
+    }
+    const uint32_t* src[6] = {rec->srcaddr, rec->dstaddr, rec->dPkts, rec->dOctets, rec->first, rec->last};
+    for (int k = 0; k < 6; ++k) {
+        if (n) GNM_CU(cudaMemcpyAsync(g.d[k], src[k] + lo, n * 4, cudaMemcpyHostToDevice, st));
+        out[k] = g.d[k];
+    }
+    GNM_CU(cudaEventRecord(g.ev, st));
+    g.ev_recorded = true;
+    return GNM_OK;
+}
+
+// ------------------------------------------------------------- shapes and params
+
+gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
+    const gnm_config& cfg = c->cfg;
+    const uint32_t nr = (uint32_t)c->h_starts.size();
+    int mode = cfg.lookup_mode;
+    if (mode == GNM_LOOKUP_AUTO) mode = c->rmi_ready ? GNM_LOOKUP_RMI : GNM_LOOKUP_BSEARCH;
+    if (mode == GNM_LOOKUP_RMI && !c->rmi_ready)
+        return fail(GNM_E_STATE, "lookup mode RMI requested but no learned index is trained");
+    size_t lookup_bytes = 0;
+    if (mode == GNM_LOOKUP_RMI) {
+        s->lookup = kLookupRmi;
+        lookup_bytes = (size_t)c->rmi.n_leaves * 16;
+    } else {
+        int place = cfg.placement != GNM_PLACE_AUTO ? cfg.placement : c->tuned.placement;
+        if (place == GNM_PLACE_AUTO) place = (size_t)nr * 8 <= kRegistrySmemMax ? GNM_PLACE_SMEM : GNM_PLACE_L2;
+        if (place == GNM_PLACE_SMEM && (size_t)nr * 8 + 1024 > (size_t)c->smem_optin)
+            return fail(GNM_E_INVAL, "registry too large for shared-memory placement");
+        s->lookup = place == GNM_PLACE_SMEM ? kLookupSmem : kLookupL2;
+        if (s->lookup == kLookupSmem) lookup_bytes = (size_t)nr * 8;
+    }
+    const size_t budget = (size_t)c->smem_optin > lookup_bytes + 1024 ? (size_t)c->smem_optin - lookup_bytes - 1024 : 0;
+    const size_t direct = (size_t)c->keys * kAccCols * 8;
+    const size_t row = kAccCols * 8 + 4;
+    uint32_t cap = 0;
+    int tm = cfg.table_mode;
+    if (tm == GNM_TABLE_AUTO) tm = direct <= std::min(kDirectTableMax, budget) ? GNM_TABLE_DIRECT : GNM_TABLE_HASH;
+    if (tm == GNM_TABLE_DIRECT) {
+        if (direct > budget) return fail(GNM_E_INVAL, "per-site sums do not fit in shared memory (table_mode DIRECT)");
+        s->table = kTableDirect;
+    } else if (tm == GNM_TABLE_HASH) {
+        if (cfg.hash_slots) {
+            cap = cfg.hash_slots;
+            if (cap < 256 || cap > 32768 || (cap & (cap - 1)))
+                return fail(GNM_E_INVAL, "hash_slots must be a power of two in 256..32768");
+            if ((size_t)cap * row > budget) return fail(GNM_E_INVAL, "hash_slots do not fit in shared memory");
+        } else {
+            cap = 1u << 15;
+            while (cap >= 256 && (size_t)cap * row > std::min(kHashTableMax, budget)) cap >>= 1;
+        }
+        s->table = cap >= 256 ? kTableHash : kTableGlobal;
+        if (s->table == kTableGlobal) cap = 0;
+    } else if (tm == GNM_TABLE_GLOBAL) {
+        s->table = kTableGlobal;
+    } else {
+        return fail(GNM_E_INVAL, "unknown table_mode");
+    }
+    int agg = cfg.aggregation != GNM_AGG_AUTO ? cfg.aggregation : c->tuned.agg;
+    s->agg = agg == GNM_AGG_WARP ? GNM_AGG_WARP : GNM_AGG_DIRECT;
+    int block = cfg.block_threads ? cfg.block_threads : (c->tuned.block ? c->tuned.block : 512);
+    int unroll = cfg.unroll ? cfg.unroll : (c->tuned.unroll ? c->tuned.unroll : 1);
+    if (block < 64 || block > 1024 || block % 32) return fail(GNM_E_INVAL, "block_threads must be 64..1024, multiple of 32");
+    if (unroll != 1 && unroll != 2) return fail(GNM_E_INVAL, "unroll must be 1 or 2");
+    if (unroll == 2 && block > 512) unroll = 1;
+    s->block = block;
+    s->unroll = unroll;
+    s->smem = aggregate_smem_bytes(s->lookup, s->table, nr, c->keys, cap, s->lookup == kLookupRmi ? c->rmi.n_leaves : 0);
+    if (s->smem > (size_t)c->smem_optin) return fail(GNM_E_INVAL, "shared-memory layout exceeds the device limit");
+    int cps = cfg.ctas_per_sm ? cfg.ctas_per_sm : c->tuned.ctas_per_sm;
+    const int by_threads = std::max(1, 2048 / block);
+    const int by_smem = s->smem ? std::max(1, (int)(c->smem_per_sm / (s->smem + 1024))) : 32;
+    const int fit = std::min(by_threads, by_smem);
+    if (cps <= 0 || cps > fit) cps = fit;
+    s->ctas_per_sm = cps;
+    const uint64_t resident = (uint64_t)c->sm_count * cps;
+    const uint64_t min_per_cta = (uint64_t)block * 8;  // at least two groups of 4 per thread
+    uint64_t grid = std::min<uint64_t>(resident, std::max<uint64_t>(1, ceil_div(n, min_per_cta)));
+    s->grid = (int)grid;
+    s->cap = cap;
+    return GNM_OK;
+}
+
+gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p) {
+    std::memset(p, 0, sizeof(*p));
+    p->src = rec->srcaddr;
+    p->dst = rec->dstaddr;
+    p->pkts = rec->dPkts;
+    p->oct = rec->dOctets;
+    p->first = rec->first;
+    p->last = rec->last;
+    p->starts = c->d_starts;
+    p->rsite = c->d_site;
+    p->n_ranges = (uint32_t)c->h_starts.size();
+    p->n_sites = c->n_sites;
+    p->rmi = c->rmi;
+    for (uint32_t i = 0; i < GNM_MAX_LOCAL; ++i) {
+        p->local_pfx[i] = c->local_pfx[i];
+        p->local_mask[i] = c->local_mask[i];
+    }
+    p->n_local = c->n_local;
+    p->min_avg = c->cfg.min_avg_pkt_bytes;
+    p->min_pkts = c->cfg.min_pkts;
+    p->min_dur = c->cfg.min_dur_ms;
+    p->admin_rule = c->cfg.admin_rule;
+    p->acc = c->d_acc;
+    p->stats = c->d_stats;
+    p->rate = c->d_rate;
+    p->flag = c->d_flag;
+    p->keys = c->keys;
+    p->min_flows = c->cfg.min_flows_to_flag;
+    p->threshold = c->cfg.threshold_bps;
+    p->violations = c->d_violations;
+    return GNM_OK;
+}
+
+static gnm_status check_records(const gnm_records* rec, uint64_t need) {
+    if (!rec) return fail(GNM_E_INVAL, "records is NULL");
+    if (rec->n < need) return fail(GNM_E_INVAL, "records->n is smaller than the windows need");
+    if (rec->n == 0) return GNM_OK;
+    const uint32_t* f[6] = {rec->srcaddr, rec->dstaddr, rec->dPkts, rec->dOctets, rec->first, rec->last};
+    for (auto* q : f) {
+        if (!q) return fail(GNM_E_INVAL, "a record field pointer is NULL");
+        if (((uintptr_t)q & 3u) != 0) return fail(GNM_E_INVAL, "record arrays must be 4-byte aligned");
+    }
+    return GNM_OK;
+}
+
+// Core of every processing call: windows k = [offsets[k], offsets[k+1]) of rec.
+// finalize: rates and flags at the end; open_add: add to already open windows.
+static gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets,
+                              const uint64_t* wids, size_t n_win, cudaStream_t st, bool finalize,
+                              bool open_add) {
+    if (!c->have_registry) return fail(GNM_E_STATE, "no registry loaded");
+    if (n_win == 0) return GNM_OK;
+    if (!offsets || !wids) return fail(GNM_E_INVAL, "offsets or window ids are NULL");
+    for (size_t k = 0; k < n_win; ++k) {
+        if (offsets[k + 1] < offsets[k]) return fail(GNM_E_INVAL, "offsets must be non-decreasing");
+        if (offsets[k + 1] - offsets[k] > kMaxWindowRecords) return fail(GNM_E_INVAL, "a window holds 2^32 records or more");
+    }
+    if (n_win > c->n_slots) return fail(GNM_E_CAPACITY, "more windows in one call than result slots");
+    GNM_TRY(check_records(rec, offsets[n_win]));
+    const uint64_t base = offsets[0], N = offsets[n_win] - offsets[0];
+
+    gnm_records dr = *rec;
+    if (N && !rec->on_device) {
+        const uint32_t* d[6];
+        GNM_TRY(stage_records(c, rec, base, offsets[n_win], st, d));
+        dr.srcaddr = d[0]; dr.dstaddr = d[1]; dr.dPkts = d[2]; dr.dOctets = d[3]; dr.first = d[4]; dr.last = d[5];
+    } else if (N) {
+        dr.srcaddr += base; dr.dstaddr += base; dr.dPkts += base; dr.dOctets += base; dr.first += base; dr.last += base;
+    }
+    // slots
+    std::vector<uint32_t> slot(n_win);
+    for (size_t k = 0; k < n_win; ++k) {
+        if (open_add) {
+            uint32_t s;
+            GNM_TRY(find_window(c, wids[k], &s));
+            Slot& sl = c->slots[s];
+            if (!sl.open) return fail(GNM_E_STATE, "window is not open");
+            if (sl.records + (offsets[k + 1] - offsets[k]) > kMaxWindowRecords)
+                return fail(GNM_E_INVAL, "an open window would reach 2^32 records");
+            GNM_TRY(wait_slot_on_stream(c, s, st));
+            slot[k] = s;
+        } else {
+            for (size_t j = 0; j < k; ++j)
+                if (wids[j] == wids[k]) return fail(GNM_E_INVAL, "duplicate window id in one call");
+            GNM_TRY(acquire_slot(c, wids[k], st, &slot[k]));
+        }
+    }
+    c->last_launches = 0;
+    if (N) {
+        AggParams p;
+        GNM_TRY(build_params(c, &dr, &p));
+        LaunchShape sh;
+        GNM_TRY(choose_shape(c, N, &sh));
+        p.table_cap = sh.cap;
+        p.n_total = N;
+        uint64_t chunk = ceil_div(N, (uint64_t)sh.grid);
+        chunk = (chunk + 3) & ~3ull;
+        sh.grid = (int)ceil_div(N, chunk);
+        p.chunk = chunk;
+        const uintptr_t a0 = (uintptr_t)dr.srcaddr & 15u;
+        const uint32_t* f[6] = {dr.srcaddr, dr.dstaddr, dr.dPkts, dr.dOctets, dr.first, dr.last};
+        p.vec_ok = 1;
+        for (auto* q : f)
+            if (((uintptr_t)q & 15u) != a0) p.vec_ok = 0;
+        p.phase = (uint32_t)(a0 >> 2);
+        const bool fin_in_kernel = finalize && c->keys <= kFinalizeInKernelMaxKeys;
+        // descriptors of the non-empty windows
+        LaunchBuf* lb;
+        GNM_TRY(acquire_ring(c, (uint32_t)n_win, &lb));
+        uint32_t nw = 0;
+        for (size_t k = 0; k < n_win; ++k) {
+            const uint64_t b = offsets[k] - base, e = offsets[k + 1] - base;
+            if (b == e) continue;
+            WinDesc& w = lb->h_wins[nw++];
+            w.begin = b;
+            w.end = e;
+            w.slot = slot[k];
+            w.flags = fin_in_kernel ? kWinFinalize : 0u;
+            w.ctas = (uint32_t)((e - 1) / chunk - b / chunk + 1);
+            w.pad = 0;
+        }
+        GNM_CU(cudaMemcpyAsync(lb->d_wins, lb->h_wins, sizeof(WinDesc) * nw, cudaMemcpyHostToDevice, st));
+        p.wins = lb->d_wins;
+        p.n_wins = nw;
+        p.done = lb->d_done;
+        GNM_CU(launch_aggregate(p, sh, st));
+        c->last_launches++;
+        if (finalize && !fin_in_kernel) {
+            for (size_t k = 0; k < n_win; ++k) {
+                if (offsets[k + 1] == offsets[k]) continue;
+                GNM_CU(launch_finalize(p, slot[k], st));
+                c->last_launches++;
+            }
+        }
+        GNM_CU(cudaEventRecord(lb->ev, st));
+        lb->ev_recorded = true;
+    }
+    // empty windows: zero sums, no rate, no flag
+    for (size_t k = 0; k < n_win; ++k) {
+        if (offsets[k + 1] != offsets[k] || !finalize) continue;
+        const uint32_t s = slot[k];
+        GNM_CU(cudaMemsetAsync(c->d_stats + (size_t)s * c->keys * kNStat, 0, (size_t)c->keys * kNStat * 8, st));
+        GNM_CU(cudaMemsetAsync(c->d_rate + (size_t)s * 2 * c->n_sites, 0xFF, (size_t)2 * c->n_sites * 8, st));
+        GNM_CU(cudaMemsetAsync(c->d_flag + (size_t)s * 2 * c->n_sites, 0, (size_t)2 * c->n_sites, st));
+    }
+    for (size_t k = 0; k < n_win; ++k) {
+        Slot& sl = c->slots[slot[k]];
+        sl.records += offsets[k + 1] - offsets[k];
+        sl.open = !finalize;
+        sl.finalized = finalize;
+        GNM_TRY(mark_slot(c, slot[k], st));
+    }
+    return GNM_OK;
+}
+
+}  // namespace gnm
+
+using namespace gnm;
+
+extern "C" {
+
+void gnm_config_default(gnm_config* cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->min_avg_pkt_bytes = 100;
+    cfg->min_pkts = 10;
+    cfg->min_dur_ms = 1000;
+    cfg->min_flows_to_flag = 1;
+    cfg->admin_rule = GNM_ADMIN_OR;
+    cfg->lookup_mode = GNM_LOOKUP_AUTO;
+    cfg->placement = GNM_PLACE_AUTO;
+    cfg->aggregation = GNM_AGG_AUTO;
+    cfg->device = 0;
+    cfg->window_slots = 64;
+    cfg->threshold_bps = 1e8;
+}
+
+gnm_status gnm_create(const gnm_config* cfg, gnm_ctx** out) {
+    if (!out) return fail(GNM_E_INVAL, "out is NULL");
+    *out = nullptr;
+    gnm_ctx* c = new (std::nothrow) gnm_ctx();
+    if (!c) return fail(GNM_E_NOMEM, "host allocation failed");
+    if (cfg) c->cfg = *cfg;
+    else gnm_config_default(&c->cfg);
+    if (c->cfg.admin_rule != GNM_ADMIN_OR && c->cfg.admin_rule != GNM_ADMIN_AND) {
+        delete c;
+        return fail(GNM_E_INVAL, "admin_rule must be GNM_ADMIN_OR or GNM_ADMIN_AND");
+    }
+    if (c->cfg.window_slots == 0) c->cfg.window_slots = 64;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        delete c;
+        return fail(GNM_E_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+    if (c->cfg.device < 0 || c->cfg.device >= ndev) {
+        delete c;
+        return fail(GNM_E_INVAL, "device ordinal out of range");
+    }
+    c->device = c->cfg.device;
+    if ((e = cudaSetDevice(c->device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device)) != cudaSuccess) {
+        delete c;
+        return fail(GNM_E_CUDA, std::string("device query: ") + cudaGetErrorString(e));
+    }
+    c->ring.resize(kRingSize);
+    for (auto& b : c->ring) {
+        if (cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) != cudaSuccess) {
+            gnm_destroy(c);
+            return fail(GNM_E_CUDA, "event creation failed");
+        }
+    }
+    if (cudaEventCreateWithFlags(&c->staging.ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&c->d_violations, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_flag_count, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(c->d_violations, 0, sizeof(unsigned long long)) != cudaSuccess) {
+        gnm_destroy(c);
+        return fail(GNM_E_CUDA, "context allocation failed");
+    }
+    *out = c;
+    return GNM_OK;
+}
+
+void gnm_destroy(gnm_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    release_slots(c);
+    for (auto& b : c->ring) {
+        if (b.h_wins) cudaFreeHost(b.h_wins);
+        free_dev(b.d_wins);
+        free_dev(b.d_done);
+        if (b.ev) cudaEventDestroy(b.ev);
+    }
+    for (auto* p : c->staging.d) free_dev(p);
+    if (c->staging.ev) cudaEventDestroy(c->staging.ev);
+    if (c->aux) cudaStreamDestroy(c->aux);
+    free_dev(c->d_starts);
+    free_dev(c->d_site);
+    free_dev(c->d_violations);
+    free_dev(c->d_flag_count);
+    free_dev(c->d_rmi_a);
+    free_dev(c->d_rmi_b);
+    free_dev(c->d_rmi_x0);
+    free_dev(c->d_rmi_eps);
+    free_dev(c->d_rmi_elo);
+    free_dev(c->d_rmi_ehi);
+    delete c;
+}
+
+const char* gnm_last_error(const gnm_ctx*) { return get_error(); }
+
+gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* len,
+                             const uint32_t* site_id, size_t n, uint32_t n_sites,
+                             const uint32_t* local_prefix, const uint8_t* local_len, size_t n_local) {
+    if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
+    if (n && (!prefix || !len || !site_id)) return fail(GNM_E_INVAL, "registry arrays are NULL");
+    if (n_sites == 0 || n_sites > (1u << 26)) return fail(GNM_E_INVAL, "n_sites must be 1..2^26");
+    if (n_local == 0 || n_local > GNM_MAX_LOCAL || !local_prefix || !local_len)
+        return fail(GNM_E_INVAL, "need 1..8 local prefixes");
+    for (size_t i = 0; i < n_local; ++i) {
+        if (local_len[i] > 32) return fail(GNM_E_INVAL, "local prefix length > 32");
+        const uint32_t m = local_len[i] == 0 ? 0u : (0xFFFFFFFFu << (32 - local_len[i]));
+        if (local_prefix[i] & ~m) return fail(GNM_E_INVAL, "local prefix has host bits set");
+        if (local_overlaps(local_prefix[i], local_len[i], prefix, len, n))
+            return fail(GNM_E_INVAL, "a local prefix overlaps a registered prefix");
+    }
+    std::vector<uint32_t> starts, sites;
+    const std::string why = flatten_registry(prefix, len, site_id, n, n_sites, &starts, &sites);
+    if (!why.empty()) return fail(GNM_E_INVAL, why);
+    GNM_CU(cudaSetDevice(c->device));
+    GNM_CU(cudaDeviceSynchronize());
+    // drop everything that depended on the old registry
+    release_slots(c);
+    free_dev(c->d_starts);
+    free_dev(c->d_site);
+    c->d_starts = nullptr;
+    c->d_site = nullptr;
+    c->have_registry = false;
+    c->rmi_ready = false;
+    c->tuned = Tuned();
+    const size_t nr = starts.size();
+    GNM_CU(cudaMalloc(&c->d_starts, nr * 4));
+    GNM_CU(cudaMalloc(&c->d_site, nr * 4));
+    GNM_CU(cudaMemcpy(c->d_starts, starts.data(), nr * 4, cudaMemcpyHostToDevice));
+    GNM_CU(cudaMemcpy(c->d_site, sites.data(), nr * 4, cudaMemcpyHostToDevice));
+    c->h_starts.swap(starts);
+    c->h_site.swap(sites);
+    c->n_sites = n_sites;
+    c->n_prefixes = (uint32_t)n;
+    c->keys = 2 * n_sites + kUnmatched;
+    c->n_local = (uint32_t)n_local;
+    for (uint32_t i = 0; i < GNM_MAX_LOCAL; ++i) {
+        c->local_pfx[i] = i < n_local ? local_prefix[i] : 0u;
+        c->local_mask[i] = i < n_local ? (local_len[i] == 0 ? 0u : (0xFFFFFFFFu << (32 - local_len[i]))) : 0u;
+    }
+    // result slots; accumulators start (and stay, between windows) at zero
+    c->n_slots = c->cfg.window_slots;
+    const size_t keys = c->keys, slots = c->n_slots;
+    GNM_CU(cudaMalloc(&c->d_acc, slots * keys * kAccCols * 8));
+    GNM_CU(cudaMalloc(&c->d_stats, slots * keys * kNStat * 8));
+    GNM_CU(cudaMalloc(&c->d_rate, slots * 2 * n_sites * 8));
+    GNM_CU(cudaMalloc(&c->d_flag, slots * 2 * n_sites));
+    GNM_CU(cudaMalloc(&c->d_flag_keys, (size_t)2 * n_sites * 4));
+    GNM_CU(cudaMemset(c->d_acc, 0, slots * keys * kAccCols * 8));
+    c->slots.resize(slots);
+    for (auto& s : c->slots) GNM_CU(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
+    c->have_registry = true;
+    return GNM_OK;
+}
+
+gnm_status gnm_registry_info_get(gnm_ctx* c, gnm_registry_info* out) {
+    if (!c || !out) return fail(GNM_E_INVAL, "NULL argument");
+    if (!c->have_registry) return fail(GNM_E_STATE, "no registry loaded");
+    std::memset(out, 0, sizeof(*out));
+    out->n_ranges = c->h_starts.size();
+    for (uint32_t s : c->h_site) out->n_registered += s != GNM_NO_SITE;
+    out->n_sites = c->n_sites;
+    out->n_prefixes = c->n_prefixes;
+    LaunchShape sh;
+    if (choose_shape(c, 1u << 20, &sh) == GNM_OK) {
+        out->placement = sh.lookup == kLookupSmem ? GNM_PLACE_SMEM : GNM_PLACE_L2;
+        out->lookup_mode = sh.lookup == kLookupRmi ? GNM_LOOKUP_RMI : GNM_LOOKUP_BSEARCH;
+        out->privatized = sh.table != kTableGlobal;
+    }
+    out->rmi_ready = c->rmi_ready;
+    return GNM_OK;
+}
+
+gnm_status gnm_registry_ranges(gnm_ctx* c, uint32_t* starts, uint32_t* site, size_t cap, size_t* n_out) {
+    if (!c || !n_out) return fail(GNM_E_INVAL, "NULL argument");
+    if (!c->have_registry) return fail(GNM_E_STATE, "no registry loaded");
+    *n_out = c->h_starts.size();
+    if (cap < c->h_starts.size()) return fail(GNM_E_CAPACITY, "cap smaller than the number of ranges");
+    if (starts) std::memcpy(starts, c->h_starts.data(), c->h_starts.size() * 4);
+    if (site) std::memcpy(site, c->h_site.data(), c->h_site.size() * 4);
+    return GNM_OK;
+}
+
+gnm_status gnm_window_process(gnm_ctx* c, const gnm_records* rec, uint64_t wid, void* stream) {
+    if (!c || !rec) return fail(GNM_E_INVAL, "NULL argument");
+    GNM_CU(cudaSetDevice(c->device));
+    const uint64_t off[2] = {0, rec->n};
+    return run_windows(c, rec, off, &wid, 1, (cudaStream_t)stream, true, false);
+}
+
+gnm_status gnm_windows_process(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets,
+                               const uint64_t* wids, size_t n_win, void* stream) {
+    if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
+    GNM_CU(cudaSetDevice(c->device));
+    return run_windows(c, rec, offsets, wids, n_win, (cudaStream_t)stream, true, false);
+}
+
+gnm_status gnm_window_open(gnm_ctx* c, uint64_t wid, void* stream) {
+    if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
+    if (!c->have_registry) return fail(GNM_E_STATE, "no registry loaded");
+    GNM_CU(cudaSetDevice(c->device));
+    uint32_t s;
+    GNM_TRY(acquire_slot(c, wid, (cudaStream_t)stream, &s));
+    c->slots[s].open = true;
+    GNM_TRY(mark_slot(c, s, (cudaStream_t)stream));
+    return GNM_OK;
+}
+
+gnm_status gnm_window_add(gnm_ctx* c, const gnm_records* rec, uint64_t wid, void* stream) {
+    if (!c || !rec) return fail(GNM_E_INVAL, "NULL argument");
+    GNM_CU(cudaSetDevice(c->device));
+    const uint64_t off[2] = {0, rec->n};
+    return run_windows(c, rec, off, &wid, 1, (cudaStream_t)stream, false, true);
+}
+
+gnm_status gnm_window_close(gnm_ctx* c, uint64_t wid, void* stream) {
+    if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
+    GNM_CU(cudaSetDevice(c->device));
+    uint32_t s;
+    GNM_TRY(find_window(c, wid, &s));
+    Slot& sl = c->slots[s];
+    if (!sl.open) return fail(GNM_E_STATE, "window is not open");
+    cudaStream_t st = (cudaStream_t)stream;
+    GNM_TRY(wait_slot_on_stream(c, s, st));
+    AggParams p;
+    gnm_records none{};
+    GNM_TRY(build_params(c, &none, &p));
+    GNM_CU(launch_finalize(p, s, st));
+    c->last_launches = 1;
+    sl.open = false;
+    sl.finalized = true;
+    return mark_slot(c, s, st);
+}
+
+static gnm_status sync_slot(gnm_ctx* c, uint32_t s) {
+    Slot& sl = c->slots[s];
+    if (!sl.finalized) return fail(GNM_E_STATE, "window is open (not finalised)");
+    if (sl.ev_recorded) GNM_CU(cudaEventSynchronize(sl.ev));
+    return GNM_OK;
+}
+
+gnm_status gnm_window_dense(gnm_ctx* c, uint64_t wid, uint64_t* stats, uint64_t* unmatched,
+                            double* rate, uint8_t* flag) {
+    if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
+    GNM_CU(cudaSetDevice(c->device));
+    uint32_t s;
+    GNM_TRY(find_window(c, wid, &s));
+    GNM_TRY(sync_slot(c, s));
+    const size_t nk = 2 * (size_t)c->n_sites;
+    const uint64_t* st = c->d_stats + (size_t)s * c->keys * kNStat;
+    if (stats) GNM_CU(cudaMemcpyAsync(stats, st, nk * kNStat * 8, cudaMemcpyDeviceToHost, c->aux));
+    uint64_t un6[kUnmatched * kNStat];
+    if (unmatched) GNM_CU(cudaMemcpyAsync(un6, st + nk * kNStat, sizeof(un6), cudaMemcpyDeviceToHost, c->aux));
+    if (rate) GNM_CU(cudaMemcpyAsync(rate, c->d_rate + (size_t)s * nk, nk * 8, cudaMemcpyDeviceToHost, c->aux));
+    if (flag) GNM_CU(cudaMemcpyAsync(flag, c->d_flag + (size_t)s * nk, nk, cudaMemcpyDeviceToHost, c->aux));
+    GNM_CU(cudaStreamSynchronize(c->aux));
+    if (unmatched)
+        for (int k = 0; k < kUnmatched; ++k)
+            for (int j = 0; j < 3; ++j) unmatched[k * 3 + j] = un6[k * kNStat + j];
+    return GNM_OK;
+}
+
+gnm_status gnm_window_device(gnm_ctx* c, uint64_t wid, const uint64_t** stats, const double** rate,
+                             const uint8_t** flag) {
+    if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
+    uint32_t s;
+    GNM_TRY(find_window(c, wid, &s));
+    const size_t nk = 2 * (size_t)c->n_sites;
+    if (stats) *stats = c->d_stats + (size_t)s * c->keys * kNStat;
+    if (rate) *rate = c->d_rate + (size_t)s * nk;
+    if (flag) *flag = c->d_flag + (size_t)s * nk;
+    return GNM_OK;
+}
+
+gnm_status gnm_site_stats(gnm_ctx* c, uint64_t wid, gnm_site_stat* out, size_t cap, size_t* n_out,
+                          uint64_t unmatched[12]) {
+    if (!c || !n_out) return fail(GNM_E_INVAL, "NULL argument");
+    const size_t nk = 2 * (size_t)c->n_sites;
+    std::vector<uint64_t> st(nk * kNStat);
+    std::vector<double> rate(nk);
+    std::vector<uint8_t> flag(nk);
+    GNM_TRY(gnm_window_dense(c, wid, st.data(), unmatched, rate.data(), flag.data()));
+    size_t n = 0;
+    for (size_t k = 0; k < nk; ++k) n += st[k * kNStat] != 0;
+    *n_out = n;
+    if (cap < n) return fail(GNM_E_CAPACITY, "cap smaller than the number of active keys");
+    size_t j = 0;
+    for (size_t k = 0; k < nk; ++k) {
+        const uint64_t* r = &st[k * kNStat];
+        if (r[0] == 0) continue;
+        gnm_site_stat& o = out[j++];
+        o.site = (uint32_t)(k >> 1);
+        o.dir = (uint32_t)(k & 1);
+        o.flows = r[0];
+        o.octets = r[1];
+        o.pkts = r[2];
+        o.e_flows = r[3];
+        o.e_octets = r[4];
+        o.e_dur_ms = r[5];
+        o.rate_bps = rate[k];
+        o.flag = flag[k];
+        o.reserved = 0;
+    }
+    return GNM_OK;
+}
+
+gnm_status gnm_flag_suboptimal(gnm_ctx* c, uint64_t wid, double thr, uint32_t* site_out,
+                               uint8_t* dir_out, size_t cap, size_t* n_out) {
+    if (!c || !n_out) return fail(GNM_E_INVAL, "NULL argument");
+    GNM_CU(cudaSetDevice(c->device));
+    uint32_t s;
+    GNM_TRY(find_window(c, wid, &s));
+    if (!c->slots[s].finalized) return fail(GNM_E_STATE, "window is open (not finalised)");
+    GNM_TRY(wait_slot_on_stream(c, s, c->aux));
+    const size_t nk = 2 * (size_t)c->n_sites;
+    GNM_CU(launch_flag_compact(c->d_rate + (size_t)s * nk, c->d_stats + (size_t)s * c->keys * kNStat,
+                               (uint32_t)nk, thr, c->cfg.min_flows_to_flag, c->d_flag_keys,
+                               c->d_flag_count, c->aux));
+    uint32_t cnt = 0;
+    GNM_CU(cudaMemcpyAsync(&cnt, c->d_flag_count, 4, cudaMemcpyDeviceToHost, c->aux));
+    GNM_CU(cudaStreamSynchronize(c->aux));
+    std::vector<uint32_t> keys(cnt);
+    if (cnt) GNM_CU(cudaMemcpyAsync(keys.data(), c->d_flag_keys, cnt * 4, cudaMemcpyDeviceToHost, c->aux));
+    GNM_CU(cudaStreamSynchronize(c->aux));
+    *n_out = cnt;
+    if (cap < cnt) return fail(GNM_E_CAPACITY, "cap smaller than the number of flagged keys");
+    std::sort(keys.begin(), keys.end());
+    for (uint32_t i = 0; i < cnt; ++i) {
+        if (site_out) site_out[i] = keys[i] >> 1;
+        if (dir_out) dir_out[i] = (uint8_t)(keys[i] & 1);
+    }
+    return GNM_OK;
+}
+
+gnm_status gnm_window_release(gnm_ctx* c, uint64_t wid) {
+    if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
+    uint32_t s;
+    GNM_TRY(find_window(c, wid, &s));
+    Slot& sl = c->slots[s];
+    if (sl.open) {  // keep the zero-accumulator invariant
+        GNM_CU(cudaSetDevice(c->device));
+        if (sl.ev_recorded) GNM_CU(cudaEventSynchronize(sl.ev));
+        GNM_CU(cudaMemset(c->d_acc + (size_t)s * c->keys * kAccCols, 0, (size_t)c->keys * kAccCols * 8));
+    }
+    sl.used = false;
+    sl.open = false;
+    sl.finalized = false;
+    sl.age = 0;
+    c->slot_of.erase(wid);
+    return GNM_OK;
+}
+
+gnm_status gnm_lookup(gnm_ctx* c, const uint32_t* addr, uint64_t n, uint32_t* site_out,
+                      uint32_t* pos_out, void* stream) {
+    if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
+    if (!c->have_registry) return fail(GNM_E_STATE, "no registry loaded");
+    if (n && !addr) return fail(GNM_E_INVAL, "addr is NULL");
+    GNM_CU(cudaSetDevice(c->device));
+    LaunchShape sh;
+    GNM_TRY(choose_shape(c, n ? n : 1, &sh));
+    AggParams p;
+    gnm_records none{};
+    GNM_TRY(build_params(c, &none, &p));
+    GNM_CU(launch_lookup(p, sh.lookup, addr, n, site_out, pos_out, (cudaStream_t)stream));
+    c->last_launches = 1;
+    return GNM_OK;
+}
+
+uint32_t gnm_last_launch_count(const gnm_ctx* c) { return c ? c->last_launches : 0; }
+
+gnm_status gnm_registry_flatten(const uint32_t* prefix, const uint8_t* len, const uint32_t* site_id,
+                                size_t n, uint32_t n_sites, uint32_t* starts, uint32_t* site,
+                                size_t cap, size_t* n_out) {
+    if (!n_out) return fail(GNM_E_INVAL, "n_out is NULL");
+    if (n && (!prefix || !len || !site_id)) return fail(GNM_E_INVAL, "registry arrays are NULL");
+    if (n_sites == 0 || n_sites > (1u << 26)) return fail(GNM_E_INVAL, "n_sites must be 1..2^26");
+    std::vector<uint32_t> st, si;
+    const std::string why = flatten_registry(prefix, len, site_id, n, n_sites, &st, &si);
+    if (!why.empty()) return fail(GNM_E_INVAL, why);
+    *n_out = st.size();
+    if (cap < st.size()) return fail(GNM_E_CAPACITY, "cap smaller than the number of ranges");
+    if (starts) std::memcpy(starts, st.data(), st.size() * 4);
+    if (site) std::memcpy(site, si.data(), si.size() * 4);
+    return GNM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// ctx.hpp -- host-side state of a gnm context (library-internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "gnm.h"
+#include "gnm_internal.cuh"
+
+namespace gnm {
+
+// Thread-local message of the last failure.
+void set_error(const std::string& msg);
+const char* get_error();
+
+#define GNM_CU(call)                                                                     \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            ::gnm::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));        \
+            return GNM_E_CUDA;                                                           \
+        }                                                                                \
+    } while (0)
+
+#define GNM_TRY(expr)                     \
+    do {                                  \
+        gnm_status s_ = (expr);           \
+        if (s_ != GNM_OK) return s_;      \
+    } while (0)
+
+gnm_status fail(gnm_status s, const std::string& msg);
+
+// One result slot on the device.
+struct Slot {
+    bool used = false;
+    bool open = false;        // accumulating, not finalised
+    bool finalized = false;
+    uint64_t window_id = 0;
+    uint64_t records = 0;     // records added so far (must stay below 2^32)
+    uint64_t age = 0;         // assignment order, for eviction
+    cudaEvent_t ev = nullptr; // last work that wrote the slot
+    bool ev_recorded = false;
+};
+
+// Per-launch device scratch: window descriptors and finalise tickets.
+struct LaunchBuf {
+    WinDesc* h_wins = nullptr;   // pinned
+    WinDesc* d_wins = nullptr;
+    uint32_t* d_done = nullptr;  // zero between launches (each launch resets it)
+    uint32_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    bool ev_recorded = false;
+};
+
+struct Staging {
+    uint32_t* d[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint64_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    bool ev_recorded = false;
+};
+
+struct Tuned {
+    int block = 0, ctas_per_sm = 0, unroll = 0, agg = 0, placement = 0;
+};
+
+}  // namespace gnm
+
+struct gnm_ctx {
+    gnm_config cfg{};
+    int device = 0;
+    int sm_count = 0;
+    int smem_optin = 0;      // max dynamic shared memory per block
+    int smem_per_sm = 0;
+    // registry
+    bool have_registry = false;
+    uint32_t n_sites = 0;
+    uint32_t n_prefixes = 0;
+    uint32_t keys = 0;       // 2*n_sites + 4
+    std::vector<uint32_t> h_starts, h_site;
+    uint32_t* d_starts = nullptr;
+    uint32_t* d_site = nullptr;
+    uint32_t local_pfx[GNM_MAX_LOCAL] = {0};
+    uint32_t local_mask[GNM_MAX_LOCAL] = {0};
+    uint32_t n_local = 0;
+    // window results
+    uint32_t n_slots = 0;
+    uint64_t* d_acc = nullptr;
+    uint64_t* d_stats = nullptr;
+    double* d_rate = nullptr;
+    uint8_t* d_flag = nullptr;
+    std::vector<gnm::Slot> slots;
+    std::unordered_map<uint64_t, uint32_t> slot_of;
+    uint64_t age = 0;
+    // scratch
+    std::vector<gnm::LaunchBuf> ring;
+    uint32_t ring_next = 0;
+    gnm::Staging staging;
+    unsigned long long* d_violations = nullptr;
+    uint32_t* d_flag_keys = nullptr;
+    uint32_t* d_flag_count = nullptr;
+    // learned index
+    bool rmi_ready = false;
+    gnm::RmiDev rmi{};
+    float* d_rmi_a = nullptr;
+    float* d_rmi_b = nullptr;
+    uint32_t* d_rmi_x0 = nullptr;
+    uint32_t* d_rmi_eps = nullptr;  // packed
+    uint32_t* d_rmi_elo = nullptr;
+    uint32_t* d_rmi_ehi = nullptr;
+    uint32_t rmi_cap = 0;
+    // tuning
+    gnm::Tuned tuned;
+    uint32_t last_launches = 0;
+    cudaStream_t aux = nullptr;  // private non-blocking stream for readouts
+};
+
+namespace gnm {
+// shared by api.cu and plan.cu
+gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p);
+gnm_status choose_shape(gnm_ctx* c, uint64_t n_records, LaunchShape* s);
+gnm_status acquire_slot(gnm_ctx* c, uint64_t window_id, cudaStream_t st, uint32_t* slot_out);
+void release_slots(gnm_ctx* c);
+}  // namespace gnm

@@ -1,0 +1,134 @@
+// gnm_internal.cuh -- device-side layouts and launch parameters shared by the library's
+// translation units (never by the oracle).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gnm.h"
+
+namespace gnm {
+
+constexpr uint32_t kNoSite = GNM_NO_SITE;
+constexpr int kNStat = GNM_NSTAT;   // columns of a user-facing stats row
+constexpr int kAccCols = 5;         // accumulator row: flows<<32|e_flows, oct, pkts, e_oct, e_dur
+constexpr int kUnmatched = 4;       // classes appended after the 2*n_sites site rows
+constexpr int kMaxLeaves = 65536;
+constexpr int kMaxHidden = 32;
+constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
+
+// One window of a launch: records [begin, end) of the launch's struct-of-arrays.
+struct WinDesc {
+    uint64_t begin, end;
+    uint32_t slot;    // result slot
+    uint32_t flags;   // kWinFinalize
+    uint32_t ctas;    // CTAs whose record range overlaps the window (ticket target)
+    uint32_t pad;
+};
+constexpr uint32_t kWinFinalize = 1u;
+
+// Learned index: root parameters by value, per-leaf arrays in device memory.
+struct RmiDev {
+    int32_t root_kind;     // GNM_RMI_ROOT_*
+    uint32_t n_leaves;
+    uint32_t hidden;
+    float ra, rb;          // linear root, on xn = float(x) * 2^-32
+    float w1[kMaxHidden], b1[kMaxHidden], w2[kMaxHidden], b2;
+    const float* a;
+    const float* b;
+    const uint32_t* x0;
+    const uint32_t* eps;   // packed eps_lo | eps_hi << 16; 0xFFFFFFFF: always full search
+};
+
+struct AggParams {
+    // struct-of-arrays records of this launch
+    const uint32_t* src;
+    const uint32_t* dst;
+    const uint32_t* pkts;
+    const uint32_t* oct;
+    const uint32_t* first;
+    const uint32_t* last;
+    uint64_t n_total;
+    uint64_t chunk;              // records per CTA (multiple of 4)
+    const WinDesc* wins;
+    uint32_t n_wins;
+    uint32_t vec_ok;             // all six arrays share the same 16-byte phase
+    uint32_t phase;              // (address / 4) mod 4 of element 0
+    // registry
+    const uint32_t* starts;
+    const uint32_t* rsite;
+    uint32_t n_ranges;
+    uint32_t n_sites;
+    // learned index (lookup mode RMI)
+    RmiDev rmi;
+    // local site
+    uint32_t local_pfx[GNM_MAX_LOCAL];
+    uint32_t local_mask[GNM_MAX_LOCAL];
+    uint32_t n_local;
+    // filters
+    uint32_t min_avg, min_pkts, min_dur;
+    int32_t admin_rule;
+    // results
+    uint64_t* acc;               // [slots][keys][kAccCols] accumulators (zeroed per window)
+    uint64_t* stats;             // [slots][keys][kNStat] finalised sums
+    double* rate;                // [slots][2*n_sites]
+    uint8_t* flag;               // [slots][2*n_sites]
+    uint32_t keys;               // 2*n_sites + 4
+    uint32_t table_cap;          // shared-memory hash slots (table mode 1)
+    uint32_t min_flows;
+    uint32_t pad0;
+    double threshold;
+    // scratch
+    uint32_t* done;              // [n_wins] finalise tickets, zero between launches
+    unsigned long long* violations;  // learned-index fallbacks
+};
+
+enum { kLookupL2 = 0, kLookupSmem = 1, kLookupRmi = 2 };
+enum { kTableDirect = 0, kTableHash = 1, kTableGlobal = 2 };
+
+// Launch shape chosen by the host.
+struct LaunchShape {
+    int block;
+    int ctas_per_sm;
+    int unroll;      // 1 or 2 four-record groups per thread per iteration
+    int lookup;      // kLookup*
+    int table;       // kTable*
+    int agg;         // GNM_AGG_DIRECT / GNM_AGG_WARP (shared-memory tables only)
+    int grid;
+    uint32_t cap;    // hash-table slots (kTableHash)
+    size_t smem;
+};
+
+// aggregate*.cu
+cudaError_t launch_aggregate(const AggParams& p, const LaunchShape& s, cudaStream_t st);
+size_t aggregate_smem_bytes(int lookup, int table, uint32_t n_ranges, uint32_t keys,
+                            uint32_t table_cap, uint32_t n_leaves);
+cudaError_t launch_finalize(const AggParams& p, uint32_t slot, cudaStream_t st);
+cudaError_t launch_flag_compact(const double* rate, const uint64_t* stats, uint32_t n_site_keys,
+                                double thr, uint32_t min_flows, uint32_t* out_keys,
+                                uint32_t* out_count, cudaStream_t st);
+cudaError_t launch_lookup(const AggParams& p, int lookup, const uint32_t* addr, uint64_t n,
+                          uint32_t* site_out, uint32_t* pos_out, cudaStream_t st);
+
+// rmi.cu
+struct RmiTrainOut {
+    double root_loss, leaf_loss;
+    uint32_t empty_leaves;
+};
+size_t rmi_train_scratch_bytes(uint64_t n, uint32_t n_leaves);
+cudaError_t rmi_train_device(RmiDev* model, float* d_a, float* d_b, uint32_t* d_x0,
+                             const uint32_t* keys, const uint32_t* pos, uint64_t n,
+                             uint32_t n_ranges, const gnm_rmi_config& cfg, void* scratch,
+                             RmiTrainOut* out, cudaStream_t st);
+cudaError_t rmi_eps_sweep(const RmiDev& model, const uint32_t* starts, uint32_t n_ranges,
+                          uint32_t* d_eps_lo, uint32_t* d_eps_hi, int sm_count, cudaStream_t st);
+cudaError_t rmi_eps_from_samples(const RmiDev& model, const uint32_t* keys, const uint32_t* pos,
+                                 uint64_t n, uint32_t n_ranges, uint32_t* d_eps_lo,
+                                 uint32_t* d_eps_hi, cudaStream_t st);
+cudaError_t rmi_pack_eps(const uint32_t* lo, const uint32_t* hi, uint32_t* packed,
+                         uint32_t n_leaves, cudaStream_t st);
+cudaError_t rmi_linear_grad(const float* z, const float* y, uint64_t n, float w, float c,
+                            double* d_acc3, cudaStream_t st);
+cudaError_t rmi_mlp_grad(const float* xn, const float* y, uint64_t n, uint32_t hidden,
+                         const float* d_params, double* d_grad, cudaStream_t st);
+
+}  // namespace gnm

@@ -1,0 +1,136 @@
+// kernels_misc.cu -- dispatch of the aggregation variants, and the small kernels around
+// it: stand-alone finalisation (rates, flags), flag compaction and batch lookups.
+#include "agg_kernel.cuh"
+
+namespace gnm {
+
+cudaError_t launch_aggregate_l2(const AggParams& p, const LaunchShape& s, cudaStream_t st);
+cudaError_t launch_aggregate_smem(const AggParams& p, const LaunchShape& s, cudaStream_t st);
+cudaError_t launch_aggregate_rmi(const AggParams& p, const LaunchShape& s, cudaStream_t st);
+
+cudaError_t launch_aggregate(const AggParams& p, const LaunchShape& s, cudaStream_t st) {
+    switch (s.lookup) {
+        case kLookupSmem: return launch_aggregate_smem(p, s, st);
+        case kLookupRmi: return launch_aggregate_rmi(p, s, st);
+        default: return launch_aggregate_l2(p, s, st);
+    }
+}
+
+size_t aggregate_smem_bytes(int lookup, int table, uint32_t n_ranges, uint32_t keys,
+                            uint32_t table_cap, uint32_t n_leaves) {
+    size_t a, b;
+    return dev::smem_layout(lookup, table, n_ranges, keys, table_cap, n_leaves, &a, &b);
+}
+
+namespace {
+
+__global__ void k_finalize(const __grid_constant__ AggParams p, uint32_t slot) {
+    dev::finalize_rows(p, slot, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// Keys (site*2+dir) whose eligible flows reach min_flows and whose rate is strictly
+// below thr (Sec. III.B.1; Sec. IV.B "less than"); order is restored on the host.
+__global__ void k_flag_compact(const double* __restrict__ rate, const uint64_t* __restrict__ stats,
+                               uint32_t n_site_keys, double thr, uint32_t min_flows,
+                               uint32_t* __restrict__ out, uint32_t* __restrict__ count) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_site_keys; k += stride) {
+        const uint64_t ef = stats[(size_t)k * kNStat + 3];
+        if (ef >= (uint64_t)min_flows && rate[k] < thr) out[atomicAdd(count, 1u)] = k;
+    }
+}
+
+template <int LOOKUP>
+__global__ void k_lookup(const __grid_constant__ AggParams p, const uint32_t* __restrict__ addr,
+                         uint64_t n, uint32_t* __restrict__ site_out, uint32_t* __restrict__ pos_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t* s_starts = nullptr;
+    const float *ra = nullptr, *rb = nullptr;
+    const uint32_t *rx0 = nullptr, *reps = nullptr;
+    if (LOOKUP == kLookupSmem) {
+        uint32_t* st = reinterpret_cast<uint32_t*>(smem_raw);
+        for (uint32_t i = threadIdx.x; i < p.n_ranges; i += blockDim.x) st[i] = __ldg(p.starts + i);
+        s_starts = st;
+    }
+    if (LOOKUP == kLookupRmi) {
+        const uint32_t L = p.rmi.n_leaves;
+        float* a = reinterpret_cast<float*>(smem_raw);
+        float* b = a + L;
+        uint32_t* x0 = reinterpret_cast<uint32_t*>(b + L);
+        uint32_t* e = x0 + L;
+        for (uint32_t i = threadIdx.x; i < L; i += blockDim.x) {
+            a[i] = __ldg(p.rmi.a + i);
+            b[i] = __ldg(p.rmi.b + i);
+            x0[i] = __ldg(p.rmi.x0 + i);
+            e[i] = __ldg(p.rmi.eps + i);
+        }
+        ra = a; rb = b; rx0 = x0; reps = e;
+    }
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t x = __ldg(addr + i);
+        uint32_t idx;
+        if (LOOKUP == kLookupRmi) {
+            idx = dev::rmi_lookup(p.rmi, ra, rb, rx0, reps, p.starts, p.n_ranges, x, p.violations);
+        } else {
+            uint32_t xs[1] = {x}, b[1];
+            if (LOOKUP == kLookupSmem) dev::pred_search<1, true>(s_starts, p.n_ranges, xs, b);
+            else dev::pred_search<1, false>(p.starts, p.n_ranges, xs, b);
+            idx = b[0];
+        }
+        if (pos_out) pos_out[i] = idx;
+        if (site_out) site_out[i] = __ldg(p.rsite + idx);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_finalize(const AggParams& p, uint32_t slot, cudaStream_t st) {
+    const uint32_t blocks = (p.keys + 255) / 256;
+    k_finalize<<<blocks > 4096 ? 4096 : blocks, 256, 0, st>>>(p, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flag_compact(const double* rate, const uint64_t* stats, uint32_t n_site_keys,
+                                double thr, uint32_t min_flows, uint32_t* out_keys,
+                                uint32_t* out_count, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out_count, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    uint32_t blocks = (n_site_keys + 255) / 256;
+    if (blocks == 0) blocks = 1;
+    if (blocks > 4096) blocks = 4096;
+    k_flag_compact<<<blocks, 256, 0, st>>>(rate, stats, n_site_keys, thr, min_flows, out_keys, out_count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lookup(const AggParams& p, int lookup, const uint32_t* addr, uint64_t n,
+                          uint32_t* site_out, uint32_t* pos_out, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t want = (n + 255) / 256;
+    const int blocks = (int)(want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8);
+    size_t smem = 0;
+    if (lookup == kLookupSmem) smem = (size_t)p.n_ranges * 4;
+    if (lookup == kLookupRmi) smem = (size_t)p.rmi.n_leaves * 16;
+    cudaError_t e;
+    switch (lookup) {
+        case kLookupSmem:
+            e = cudaFuncSetAttribute(k_lookup<kLookupSmem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_lookup<kLookupSmem><<<blocks, 256, smem, st>>>(p, addr, n, site_out, pos_out);
+            break;
+        case kLookupRmi:
+            e = cudaFuncSetAttribute(k_lookup<kLookupRmi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_lookup<kLookupRmi><<<blocks, 256, smem, st>>>(p, addr, n, site_out, pos_out);
+            break;
+        default:
+            k_lookup<kLookupL2><<<blocks, 256, 0, st>>>(p, addr, n, site_out, pos_out);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gnm

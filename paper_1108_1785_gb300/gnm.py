@@ -1,0 +1,432 @@
+"""Python binding of libgnm.so (the C ABI declared in include/gnm.h).
+
+Argument marshalling only: every step of the flow analysis runs in the library's CUDA
+kernels. Device buffers are torch CUDA tensors (their data_ptr() is passed through),
+streams are torch streams. The library must have been built (``build.build()``); the
+binding raises if it is missing instead of computing anything itself.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgnm.so")
+
+NO_SITE = 0xFFFFFFFF
+NSTAT = 6
+LOOKUP_AUTO, LOOKUP_BSEARCH, LOOKUP_RMI = 0, 1, 2
+PLACE_AUTO, PLACE_SMEM, PLACE_L2 = 0, 1, 2
+AGG_AUTO, AGG_DIRECT, AGG_WARP = 0, 1, 2
+ADMIN_OR, ADMIN_AND = 0, 1
+TABLE_AUTO, TABLE_DIRECT, TABLE_HASH, TABLE_GLOBAL = 0, 1, 2, 3
+ROOT_LINEAR, ROOT_MLP = 0, 1
+FIELDS = ("srcaddr", "dstaddr", "dPkts", "dOctets", "first", "last")
+
+STATUS = {0: "GNM_OK", 1: "GNM_E_INVAL", 2: "GNM_E_NOMEM", 3: "GNM_E_CUDA", 4: "GNM_E_STATE",
+          5: "GNM_E_CAPACITY", 6: "GNM_E_TIMEOUT", 7: "GNM_E_INTERNAL"}
+
+
+class GnmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("min_avg_pkt_bytes", C.c_uint32), ("min_pkts", C.c_uint32), ("min_dur_ms", C.c_uint32),
+                ("min_flows_to_flag", C.c_uint32), ("admin_rule", C.c_int32), ("lookup_mode", C.c_int32),
+                ("placement", C.c_int32), ("aggregation", C.c_int32), ("device", C.c_int32),
+                ("window_slots", C.c_uint32), ("threshold_bps", C.c_double), ("block_threads", C.c_int32),
+                ("ctas_per_sm", C.c_int32), ("unroll", C.c_int32), ("table_mode", C.c_int32),
+                ("hash_slots", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class RecordsC(C.Structure):
+    _fields_ = [("n", C.c_uint64)] + [(f, C.c_void_p) for f in FIELDS] + \
+        [("srcport", C.c_void_p), ("dstport", C.c_void_p), ("prot", C.c_void_p), ("on_device", C.c_int32)]
+
+
+class SiteStat(C.Structure):
+    _fields_ = [("site", C.c_uint32), ("dir", C.c_uint32), ("flows", C.c_uint64), ("octets", C.c_uint64),
+                ("pkts", C.c_uint64), ("e_flows", C.c_uint64), ("e_octets", C.c_uint64),
+                ("e_dur_ms", C.c_uint64), ("rate_bps", C.c_double), ("flag", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
+class RegistryInfo(C.Structure):
+    _fields_ = [("n_ranges", C.c_uint64), ("n_registered", C.c_uint64), ("n_sites", C.c_uint32),
+                ("n_prefixes", C.c_uint32), ("placement", C.c_int32), ("lookup_mode", C.c_int32),
+                ("privatized", C.c_int32), ("rmi_ready", C.c_int32)]
+
+
+class RmiConfig(C.Structure):
+    _fields_ = [("root_kind", C.c_int32), ("n_leaves", C.c_uint32), ("hidden", C.c_uint32),
+                ("leaf_iters", C.c_uint32), ("mlp_steps", C.c_uint32), ("mlp_batch", C.c_uint32),
+                ("mlp_lr", C.c_float), ("seed", C.c_uint32), ("exhaustive_eps", C.c_int32)]
+
+
+class RmiReport(C.Structure):
+    _fields_ = [("n_train", C.c_uint64), ("root_loss", C.c_double), ("leaf_loss", C.c_double),
+                ("eps_max", C.c_uint32), ("eps_mean", C.c_double), ("empty_leaves", C.c_uint32),
+                ("train_ms", C.c_double), ("sweep_ms", C.c_double)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("block_threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("unroll", C.c_int32),
+                ("aggregation", C.c_int32), ("placement", C.c_int32), ("best_ms", C.c_double),
+                ("default_ms", C.c_double), ("n_tried", C.c_uint32)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded C library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1108_1785_gb300.build.build() first "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        P, S, U64, U32 = C.c_void_p, C.c_size_t, C.c_uint64, C.c_uint32
+        st = C.c_int
+        sig = {
+            "gnm_config_default": (None, [C.POINTER(Config)]),
+            "gnm_create": (st, [C.POINTER(Config), C.POINTER(P)]),
+            "gnm_destroy": (None, [P]),
+            "gnm_last_error": (C.c_char_p, [P]),
+            "gnm_registry_load": (st, [P, P, P, P, S, U32, P, P, S]),
+            "gnm_registry_info_get": (st, [P, C.POINTER(RegistryInfo)]),
+            "gnm_registry_ranges": (st, [P, P, P, S, C.POINTER(S)]),
+            "gnm_registry_flatten": (st, [P, P, P, S, U32, P, P, S, C.POINTER(S)]),
+            "gnm_window_process": (st, [P, C.POINTER(RecordsC), U64, P]),
+            "gnm_windows_process": (st, [P, C.POINTER(RecordsC), P, P, S, P]),
+            "gnm_window_open": (st, [P, U64, P]),
+            "gnm_window_add": (st, [P, C.POINTER(RecordsC), U64, P]),
+            "gnm_window_close": (st, [P, U64, P]),
+            "gnm_site_stats": (st, [P, U64, C.POINTER(SiteStat), S, C.POINTER(S), P]),
+            "gnm_flag_suboptimal": (st, [P, U64, C.c_double, P, P, S, C.POINTER(S)]),
+            "gnm_window_dense": (st, [P, U64, P, P, P, P]),
+            "gnm_window_device": (st, [P, U64, C.POINTER(P), C.POINTER(P), C.POINTER(P)]),
+            "gnm_window_release": (st, [P, U64]),
+            "gnm_lookup": (st, [P, P, U64, P, P, P]),
+            "gnm_rmi_config_default": (None, [C.POINTER(RmiConfig)]),
+            "gnm_rmi_train": (st, [P, P, U64, C.POINTER(RmiConfig), C.POINTER(RmiReport), P]),
+            "gnm_rmi_violations": (st, [P, C.POINTER(U64), C.c_int]),
+            "gnm_rmi_linear_grad": (st, [P, P, P, U64, C.c_float, C.c_float, P, P]),
+            "gnm_rmi_mlp_grad": (st, [P, P, P, U64, U32, P, P, P]),
+            "gnm_rmi_export": (st, [P, P, P, P, P, P, P, P, P]),
+            "gnm_rmi_import": (st, [P, C.c_int32, U32, P, P, P, P, P]),
+            "gnm_plan_create": (st, [P, C.POINTER(RecordsC), P, P, S, C.POINTER(P)]),
+            "gnm_plan_launch": (st, [P, P]),
+            "gnm_plan_destroy": (None, [P]),
+            "gnm_autotune": (st, [P, C.POINTER(RecordsC), P, P, S, C.POINTER(TuneReport)]),
+            "gnm_last_launch_count": (U32, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name, None)
+            if f is None:
+                continue
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(ctx_ptr, status: int):
+    if status != 0:
+        msg = lib().gnm_last_error(ctx_ptr)
+        raise GnmError(status, msg.decode() if msg else "")
+
+
+def _ptr(a) -> int:
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Records:
+    """A struct-of-arrays record batch: six uint32 arrays, all torch CUDA tensors
+    (device) or all numpy arrays (host). Keeps the arrays alive while in use."""
+
+    def __init__(self, fields: Dict[str, object]):
+        self.fields = {k: fields[k] for k in FIELDS}
+        first = self.fields["srcaddr"]
+        self.on_device = hasattr(first, "data_ptr") and getattr(first, "is_cuda", False)
+        n = {int(v.numel() if hasattr(v, "numel") else v.size) for v in self.fields.values()}
+        if len(n) != 1:
+            raise ValueError("record arrays differ in length")
+        self.n = n.pop()
+        for k, v in self.fields.items():
+            dt = str(v.dtype)
+            if "int32" not in dt:  # torch.int32 or numpy uint32 / int32
+                raise TypeError(f"{k} must hold 32-bit integers, got {dt}")
+            if hasattr(v, "is_contiguous") and not v.is_contiguous():
+                raise ValueError(f"{k} must be contiguous")
+        self.c = RecordsC()
+        self.c.n = self.n
+        for k in FIELDS:
+            setattr(self.c, k, _ptr(self.fields[k]))
+        self.c.on_device = 1 if self.on_device else 0
+
+    @staticmethod
+    def to_device(rec: Dict[str, np.ndarray], device: str = "cuda") -> "Records":
+        import torch
+        return Records({k: torch.from_numpy(np.ascontiguousarray(rec[k]).view(np.int32)).to(device)
+                        for k in FIELDS})
+
+    @staticmethod
+    def host(rec: Dict[str, np.ndarray]) -> "Records":
+        return Records({k: np.ascontiguousarray(rec[k], dtype=np.uint32) for k in FIELDS})
+
+
+def registry_flatten(prefix, plen, site, n_sites: int) -> Tuple[np.ndarray, np.ndarray]:
+    """Host-only registry flattening (no GPU): sorted range starts and their sites."""
+    p = np.ascontiguousarray(prefix, np.uint32)
+    l = np.ascontiguousarray(plen, np.uint8)
+    s = np.ascontiguousarray(site, np.uint32)
+    n = C.c_size_t()
+    st = lib().gnm_registry_flatten(_ptr(p), _ptr(l), _ptr(s), p.size, n_sites, None, None, 0, C.byref(n))
+    if st not in (0, 5):
+        _check(None, st)
+    a = np.empty(n.value, np.uint32)
+    b = np.empty(n.value, np.uint32)
+    _check(None, lib().gnm_registry_flatten(_ptr(p), _ptr(l), _ptr(s), p.size, n_sites, _ptr(a), _ptr(b),
+                                            n.value, C.byref(n)))
+    return a, b
+
+
+class Context:
+    """A gnm context (one GPU)."""
+
+    def __init__(self, **cfg):
+        L = lib()
+        c = Config()
+        L.gnm_config_default(C.byref(c))
+        for k, v in cfg.items():
+            if not hasattr(c, k):
+                raise TypeError(f"unknown config key {k}")
+            setattr(c, k, v)
+        self.config = c
+        h = C.c_void_p()
+        _check(None, L.gnm_create(C.byref(c), C.byref(h)))
+        self.h = h
+        self.n_sites = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gnm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _c(self, status):
+        _check(self.h, status)
+
+    # ---------------------------------------------------------------- registry
+    def load_registry(self, prefix, plen, site, n_sites: int, local_prefix, local_len):
+        p = np.ascontiguousarray(prefix, np.uint32)
+        l = np.ascontiguousarray(plen, np.uint8)
+        s = np.ascontiguousarray(site, np.uint32)
+        lp = np.ascontiguousarray(local_prefix, np.uint32)
+        ll = np.ascontiguousarray(local_len, np.uint8)
+        self._c(lib().gnm_registry_load(self.h, _ptr(p), _ptr(l), _ptr(s), p.size, n_sites, _ptr(lp),
+                                        _ptr(ll), lp.size))
+        self.n_sites = n_sites
+
+    def load(self, reg):
+        """Registry object with prefix/plen/site/n_sites/local_prefix/local_len."""
+        self.load_registry(reg.prefix, reg.plen, reg.site, reg.n_sites, reg.local_prefix, reg.local_len)
+
+    def registry_info(self) -> RegistryInfo:
+        info = RegistryInfo()
+        self._c(lib().gnm_registry_info_get(self.h, C.byref(info)))
+        return info
+
+    def ranges(self) -> Tuple[np.ndarray, np.ndarray]:
+        n = C.c_size_t()
+        lib().gnm_registry_ranges(self.h, None, None, 0, C.byref(n))
+        st = np.empty(n.value, np.uint32)
+        si = np.empty(n.value, np.uint32)
+        self._c(lib().gnm_registry_ranges(self.h, _ptr(st), _ptr(si), n.value, C.byref(n)))
+        return st, si
+
+    # ---------------------------------------------------------------- windows
+    def process(self, rec: Records, window_id: int, stream=None):
+        self._c(lib().gnm_window_process(self.h, C.byref(rec.c), window_id, _stream_ptr(stream)))
+
+    def process_windows(self, rec: Records, offsets: Sequence[int], window_ids: Sequence[int], stream=None):
+        off = np.ascontiguousarray(offsets, np.uint64)
+        ids = np.ascontiguousarray(window_ids, np.uint64)
+        self._c(lib().gnm_windows_process(self.h, C.byref(rec.c), _ptr(off), _ptr(ids), ids.size,
+                                          _stream_ptr(stream)))
+
+    def open(self, window_id: int, stream=None):
+        self._c(lib().gnm_window_open(self.h, window_id, _stream_ptr(stream)))
+
+    def add(self, rec: Records, window_id: int, stream=None):
+        self._c(lib().gnm_window_add(self.h, C.byref(rec.c), window_id, _stream_ptr(stream)))
+
+    def close_window(self, window_id: int, stream=None):
+        self._c(lib().gnm_window_close(self.h, window_id, _stream_ptr(stream)))
+
+    def release(self, window_id: int):
+        self._c(lib().gnm_window_release(self.h, window_id))
+
+    def dense(self, window_id: int):
+        """(stats[2S, 6] u64, unmatched[4, 3] u64, rate[2S] f64, flag[2S] u8) on the host."""
+        nk = 2 * self.n_sites
+        st = np.empty((nk, NSTAT), np.uint64)
+        un = np.empty((4, 3), np.uint64)
+        r = np.empty(nk, np.float64)
+        f = np.empty(nk, np.uint8)
+        self._c(lib().gnm_window_dense(self.h, window_id, _ptr(st), _ptr(un), _ptr(r), _ptr(f)))
+        return st, un, r, f
+
+    def device_results(self, window_id: int):
+        """Raw device addresses (stats, rate, flag) of a window's dense results."""
+        a, b, c = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        self._c(lib().gnm_window_device(self.h, window_id, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def site_stats(self, window_id: int):
+        n = C.c_size_t()
+        un = np.empty(12, np.uint64)
+        s = lib().gnm_site_stats(self.h, window_id, None, 0, C.byref(n), _ptr(un))
+        if s not in (0, 5):
+            self._c(s)
+        arr = (SiteStat * max(n.value, 1))()
+        self._c(lib().gnm_site_stats(self.h, window_id, arr, n.value, C.byref(n), _ptr(un)))
+        return [arr[i] for i in range(n.value)], un.reshape(4, 3)
+
+    def flag_suboptimal(self, window_id: int, threshold_bps: float):
+        n = C.c_size_t()
+        cap = 2 * self.n_sites
+        sites = np.empty(cap, np.uint32)
+        dirs = np.empty(cap, np.uint8)
+        self._c(lib().gnm_flag_suboptimal(self.h, window_id, threshold_bps, _ptr(sites), _ptr(dirs), cap,
+                                          C.byref(n)))
+        return sites[:n.value].copy(), dirs[:n.value].copy()
+
+    def lookup(self, addr, site_out=None, pos_out=None, stream=None):
+        """Longest-prefix match of a device uint32 tensor of addresses."""
+        self._c(lib().gnm_lookup(self.h, _ptr(addr), int(addr.numel()), _ptr(site_out), _ptr(pos_out),
+                                 _stream_ptr(stream)))
+
+    def last_launch_count(self) -> int:
+        return int(lib().gnm_last_launch_count(self.h))
+
+    # ------------------------------------------------------------ learned index
+    def rmi_train(self, keys, stream=None, **cfg) -> RmiReport:
+        c = RmiConfig()
+        lib().gnm_rmi_config_default(C.byref(c))
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        rep = RmiReport()
+        self._c(lib().gnm_rmi_train(self.h, _ptr(keys), int(keys.numel()), C.byref(c), C.byref(rep),
+                                    _stream_ptr(stream)))
+        return rep
+
+    def rmi_violations(self, reset: bool = False) -> int:
+        v = C.c_uint64()
+        self._c(lib().gnm_rmi_violations(self.h, C.byref(v), int(reset)))
+        return v.value
+
+    def rmi_linear_grad(self, z, y, w: float, c: float, stream=None) -> np.ndarray:
+        g = np.zeros(3, np.float64)
+        self._c(lib().gnm_rmi_linear_grad(self.h, _ptr(z), _ptr(y), int(z.numel()), w, c, _ptr(g),
+                                          _stream_ptr(stream)))
+        return g
+
+    def rmi_mlp_grad(self, xn, y, hidden: int, params: np.ndarray, stream=None) -> np.ndarray:
+        p = np.ascontiguousarray(params, np.float32)
+        g = np.zeros(3 * hidden + 2, np.float64)
+        self._c(lib().gnm_rmi_mlp_grad(self.h, _ptr(xn), _ptr(y), int(xn.numel()), hidden, _ptr(p), _ptr(g),
+                                       _stream_ptr(stream)))
+        return g
+
+    def rmi_export(self):
+        kind = C.c_int32()
+        L = C.c_uint32()
+        lib().gnm_rmi_export(self.h, C.byref(kind), C.byref(L), None, None, None, None, None, None)
+        n = L.value
+        root = np.zeros(2 + 3 * 32 + 1, np.float32)
+        a = np.zeros(n, np.float32)
+        b = np.zeros(n, np.float32)
+        x0 = np.zeros(n, np.uint32)
+        elo = np.zeros(n, np.uint32)
+        ehi = np.zeros(n, np.uint32)
+        self._c(lib().gnm_rmi_export(self.h, C.byref(kind), C.byref(L), _ptr(root), _ptr(a), _ptr(b), _ptr(x0),
+                                     _ptr(elo), _ptr(ehi)))
+        return dict(root_kind=kind.value, n_leaves=n, root=root, a=a, b=b, x0=x0, eps_lo=elo, eps_hi=ehi)
+
+    def rmi_import(self, root_kind: int, root, a, b, x0, stream=None):
+        r = np.ascontiguousarray(root, np.float32)
+        a = np.ascontiguousarray(a, np.float32)
+        b = np.ascontiguousarray(b, np.float32)
+        x0 = np.ascontiguousarray(x0, np.uint32)
+        self._c(lib().gnm_rmi_import(self.h, root_kind, a.size, _ptr(r), _ptr(a), _ptr(b), _ptr(x0),
+                                     _stream_ptr(stream)))
+
+    # ---------------------------------------------------------- plans / tuning
+    def plan(self, rec: Records, offsets, window_ids) -> "Plan":
+        return Plan(self, rec, offsets, window_ids)
+
+    def autotune(self, rec: Records, offsets, window_ids) -> TuneReport:
+        off = np.ascontiguousarray(offsets, np.uint64)
+        ids = np.ascontiguousarray(window_ids, np.uint64)
+        rep = TuneReport()
+        self._c(lib().gnm_autotune(self.h, C.byref(rec.c), _ptr(off), _ptr(ids), ids.size, C.byref(rep)))
+        return rep
+
+
+class Plan:
+    """A CUDA-graph launch of many windows over fixed device buffers."""
+
+    def __init__(self, ctx: Context, rec: Records, offsets, window_ids):
+        self.ctx = ctx
+        self.rec = rec
+        off = np.ascontiguousarray(offsets, np.uint64)
+        ids = np.ascontiguousarray(window_ids, np.uint64)
+        h = C.c_void_p()
+        ctx._c(lib().gnm_plan_create(ctx.h, C.byref(rec.c), _ptr(off), _ptr(ids), ids.size, C.byref(h)))
+        self.h = h
+
+    def launch(self, stream=None):
+        self.ctx._c(lib().gnm_plan_launch(self.h, _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gnm_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,245 @@
+"""Parity of the CUDA window path (through the C ABI) with the CPU oracle.
+
+Integers (per-key flows, octets, packets, eligible flows/octets/durations, unmatched
+classes, flags) must be bit-exact; rates within 1e-12 relative of the FP64 oracle.
+"""
+import ipaddress
+
+import numpy as np
+import pytest
+
+import flowgen as fg
+import oracle
+from helpers import assert_rates_close, assert_window_matches, oracle_full
+from test_oracle_pins import load_hand
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gnm():
+    from paper_1108_1785_gb300 import build, gnm as g
+    build.build()
+    return g
+
+
+@pytest.fixture(scope="module")
+def c1():
+    reg = fg.registry_c1()
+    rec = fg.window_records_c1(reg)
+    return reg, rec, oracle_full(reg, rec)
+
+
+def _ctx(gnm, reg, **cfg):
+    ctx = gnm.Context(**cfg)
+    ctx.load(reg)
+    return ctx
+
+
+def test_hand_window(gnm):
+    g, reg, loc, rec = load_hand()
+
+    class R:
+        pass
+    r = R()
+    r.prefix, r.plen, r.site = reg[:, 0], reg[:, 1], reg[:, 2]
+    r.n_sites = g["n_sites"]
+    r.local_prefix, r.local_len = loc[:, 0], loc[:, 1]
+    for table in (gnm.TABLE_DIRECT, gnm.TABLE_HASH, gnm.TABLE_GLOBAL):
+        ctx = _ctx(gnm, r, table_mode=table, threshold_bps=1e6)
+        ctx.process(gnm.Records.to_device(rec), 7)
+        st, un, rate, fl = ctx.dense(7)
+        want = np.zeros_like(st)
+        for row in g["expected_rows"]:
+            want[row[0] * 2 + row[1]] = row[2:]
+        np.testing.assert_array_equal(st, want)
+        np.testing.assert_array_equal(un, np.array(g["expected_unmatched"], np.uint64))
+        for key, v in g["expected_rates_bps"].items():
+            s, d = map(int, key.split(","))
+            assert rate[s * 2 + d] == pytest.approx(v, rel=1e-15)
+        want_fl = np.zeros(st.shape[0], np.uint8)
+        for s, d in g["thresholds"]["1e6"]:
+            want_fl[s * 2 + d] = 1
+        np.testing.assert_array_equal(fl, want_fl)
+        sites, dirs = ctx.flag_suboptimal(7, 1e8)
+        assert sorted(zip(sites.tolist(), dirs.tolist())) == sorted(map(tuple, g["thresholds"]["1e8"]))
+        ctx.close()
+
+
+@pytest.mark.parametrize("table", ["DIRECT", "HASH", "GLOBAL"])
+@pytest.mark.parametrize("agg", ["DIRECT", "WARP"])
+@pytest.mark.parametrize("place", ["SMEM", "L2"])
+@pytest.mark.parametrize("unroll,block", [(1, 256), (2, 512), (1, 1024)])
+def test_c1_window_all_variants(gnm, c1, table, agg, place, unroll, block):
+    reg, rec, expect = c1
+    ctx = _ctx(gnm, reg, table_mode=getattr(gnm, "TABLE_" + table), aggregation=getattr(gnm, "AGG_" + agg),
+               placement=getattr(gnm, "PLACE_" + place), unroll=unroll, block_threads=block,
+               hash_slots=512 if table == "HASH" else 0)
+    d = gnm.Records.to_device(rec)
+    ctx.process(d, 1)
+    assert_window_matches(ctx.dense(1), expect)
+    # same window again into the same slot: identical
+    ctx.process(d, 1)
+    assert_window_matches(ctx.dense(1), expect)
+    ctx.close()
+
+
+def test_c1_host_records_and_site_stats(gnm, c1):
+    reg, rec, expect = c1
+    ctx = _ctx(gnm, reg)
+    ctx.process(gnm.Records.host(rec), 3)  # host arrays: staged by the library
+    assert_window_matches(ctx.dense(3), expect)
+    rows, un = ctx.site_stats(3)
+    ost = expect[0]
+    active = np.nonzero(ost[:, 0])[0]
+    assert [r.site * 2 + r.dir for r in rows] == active.tolist()
+    for r in rows:
+        k = r.site * 2 + r.dir
+        assert [r.flows, r.octets, r.pkts, r.e_flows, r.e_octets, r.e_dur_ms] == ost[k].tolist()
+        assert r.flag == expect[3][k]
+    np.testing.assert_array_equal(un, expect[1])
+    for thr in (1e5, 1e6, 3e6, 1e7, 1e8):
+        sites, dirs = ctx.flag_suboptimal(3, thr)
+        want = np.nonzero(oracle.flags(ost, expect[2], thr))[0]
+        np.testing.assert_array_equal(sites.astype(np.int64) * 2 + dirs, want)
+    ctx.close()
+
+
+def test_c1_ragged_and_unaligned(gnm, c1):
+    """Windows of 0..9 records and arbitrary offsets (head/tail peeling), plus arrays
+    whose 16-byte phases differ (element-wise path)."""
+    reg, rec, _ = c1
+    ctx = _ctx(gnm, reg, window_slots=128)
+    d = gnm.Records.to_device(rec)
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    wid = 100
+    for start in (0, 1, 2, 3, 5, 4093):
+        for n in (0, 1, 2, 3, 4, 5, 7, 9, 33, 1001):
+            sub = {k: v[start:start + n] for k, v in d.fields.items()}
+            ctx.process(gnm.Records(sub), wid)
+            host = {k: v[start:start + n] for k, v in rec.items()}
+            assert_window_matches(ctx.dense(wid), oracle_full(reg, host, lpm=lpm, n_threads=0))
+            wid += 1
+    # mixed phases: shift some fields by one element
+    n = 5000
+    fields = {}
+    for j, k in enumerate(gnm.FIELDS):
+        buf = torch.zeros(n + 4, dtype=torch.int32, device="cuda")
+        off = j % 3
+        buf[off:off + n] = d.fields[k][:n]
+        fields[k] = buf[off:off + n]
+    ctx.process(gnm.Records(fields), 999)
+    host = {k: v[:n] for k, v in rec.items()}
+    assert_window_matches(ctx.dense(999), oracle_full(reg, host, lpm=lpm))
+    ctx.close()
+
+
+def test_c2_hour_batched_bitexact(gnm):
+    """Sixty one-minute windows (10M records, nested registry) in one launch; every
+    window equals the oracle. Window 30 straddles the 32-bit millisecond wrap."""
+    reg = fg.registry_c2()
+    rec, off = fg.hour_records_c2(reg)
+    ctx = _ctx(gnm, reg)
+    info = ctx.registry_info()
+    assert info.placement == gnm.PLACE_L2
+    d = gnm.Records.to_device(rec)
+    ids = np.arange(60) + 5000
+    ctx.process_windows(d, off, ids)
+    assert ctx.last_launch_count() == 1
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    for w in range(60):
+        host = {k: v[off[w]:off[w + 1]] for k, v in rec.items()}
+        assert_window_matches(ctx.dense(int(ids[w])), oracle_full(reg, host, lpm=lpm))
+    ctx.close()
+
+
+def test_windows_with_empty_and_many(gnm, c1):
+    reg, rec, _ = c1
+    ctx = _ctx(gnm, reg, window_slots=64)
+    d = gnm.Records.to_device(rec)
+    off = [0, 10, 10, 5000, 5001, 5001, 77777, 100000]
+    ids = list(range(1, len(off)))
+    ctx.process_windows(d, off, ids)
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    for w in range(len(ids)):
+        host = {k: v[off[w]:off[w + 1]] for k, v in rec.items()}
+        assert_window_matches(ctx.dense(ids[w]), oracle_full(reg, host, lpm=lpm, n_threads=0))
+    ctx.close()
+
+
+def test_open_add_close_equals_whole(gnm, c1):
+    reg, rec, expect = c1
+    ctx = _ctx(gnm, reg)
+    d = gnm.Records.to_device(rec)
+    ctx.open(11)
+    cuts = [0, 1, 4097, 50000, 99999, 100000]
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        ctx.add(gnm.Records({k: v[a:b] for k, v in d.fields.items()}), 11)
+    with pytest.raises(gnm.GnmError):
+        ctx.dense(11)  # still open
+    ctx.close_window(11)
+    assert_window_matches(ctx.dense(11), expect)
+    ctx.close()
+
+
+def test_slot_eviction_and_release(gnm, c1):
+    reg, rec, expect = c1
+    ctx = _ctx(gnm, reg, window_slots=2)
+    d = gnm.Records.to_device(rec)
+    ctx.process(d, 1)
+    ctx.process(d, 2)
+    ctx.process(d, 3)  # evicts window 1
+    with pytest.raises(gnm.GnmError, match="STATE"):
+        ctx.dense(1)
+    assert_window_matches(ctx.dense(3), expect)
+    ctx.release(2)
+    with pytest.raises(gnm.GnmError, match="STATE"):
+        ctx.dense(2)
+    ctx.close()
+
+
+@pytest.mark.parametrize("which", ["c1", "c2"])
+def test_lookup_matches_oracle(gnm, which):
+    reg = fg.registry_c1() if which == "c1" else fg.registry_c2()
+    ctx = _ctx(gnm, reg)
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    st, _ = lpm.flatten()
+    s64 = st.astype(np.int64)
+    x = np.concatenate([s64, s64 - 1, s64 + 1, [0, 0xFFFFFFFF],
+                        np.random.default_rng(3).integers(0, 1 << 32, 200000)])
+    x = x[(x >= 0) & (x < (1 << 32))].astype(np.uint32)
+    dx = torch.from_numpy(x.view(np.int32)).cuda()
+    site = torch.empty_like(dx)
+    pos = torch.empty_like(dx)
+    ctx.lookup(dx, site, pos)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(site.cpu().numpy().view(np.uint32), lpm.lookup(x))
+    gst, gsi = ctx.ranges()
+    np.testing.assert_array_equal(gst, st)  # the library's ranges equal the oracle's flattening
+    np.testing.assert_array_equal(pos.cpu().numpy().view(np.uint32), np.searchsorted(st, x, side="right") - 1)
+    ctx.close()
+
+
+def _ip(s):
+    return int(ipaddress.IPv4Address(s))
+
+
+def test_registry_validation(gnm):
+    ctx = gnm.Context()
+    loc_p, loc_l = np.array([_ip("131.225.0.0")]), np.array([16])
+    bad = [
+        ([_ip("10.0.0.1")], [24], [0], 1, "host bits"),
+        ([_ip("10.0.0.0")], [33], [0], 1, "length"),
+        ([_ip("10.0.0.0")] * 2, [8, 8], [0, 0], 1, "duplicate"),
+        ([_ip("10.0.0.0")], [8], [5], 1, "site id"),
+        ([_ip("131.0.0.0")], [8], [0], 1, "overlaps"),
+        ([_ip("131.225.7.0")], [24], [0], 1, "overlaps"),
+    ]
+    for p, l, s, ns, msg in bad:
+        with pytest.raises(gnm.GnmError, match=msg):
+            ctx.load_registry(np.array(p), np.array(l), np.array(s), ns, loc_p, loc_l)
+    with pytest.raises(gnm.GnmError, match="STATE"):
+        ctx.dense(0)
+    ctx.close()
