@@ -56,7 +56,10 @@ typedef enum {
 } gnm_status;
 
 enum { GNM_LOOKUP_AUTO = 0, GNM_LOOKUP_BSEARCH = 1, GNM_LOOKUP_RMI = 2 };
-enum { GNM_PLACE_AUTO = 0, GNM_PLACE_SMEM = 1, GNM_PLACE_L2 = 2 };
+/* Where the flattened registry is searched: wholly in shared memory (SMEM), wholly in L2
+ * (L2), or STAGED: the first start of every block of 8 ranges in shared memory and the
+ * 64-byte blocks (8 starts, 8 sites) in L2, one L2 access per lookup. */
+enum { GNM_PLACE_AUTO = 0, GNM_PLACE_SMEM = 1, GNM_PLACE_L2 = 2, GNM_PLACE_STAGED = 3 };
 enum { GNM_AGG_AUTO = 0, GNM_AGG_DIRECT = 1, GNM_AGG_WARP = 2 };
 enum { GNM_ADMIN_OR = 0, GNM_ADMIN_AND = 1 };
 /* Per-CTA accumulation: a shared-memory row per key (DIRECT, when all keys fit), a
@@ -210,6 +213,13 @@ gnm_status gnm_flag_suboptimal(gnm_ctx *ctx, uint64_t window_id, double threshol
 gnm_status gnm_window_dense(gnm_ctx *ctx, uint64_t window_id, uint64_t *stats,
                             uint64_t *unmatched, double *rate, uint8_t *flag);
 
+/* The dense results of n windows in one call: window k's arrays start at stats +
+ * k*(2*n_sites)*GNM_NSTAT, unmatched + k*12, rate + k*2*n_sites, flag + k*2*n_sites (each
+ * may be NULL). One synchronisation for all of them. */
+gnm_status gnm_windows_results(gnm_ctx *ctx, const uint64_t *window_ids, size_t n,
+                               uint64_t *stats, uint64_t *unmatched, double *rate,
+                               uint8_t *flag);
+
 /* Device addresses of a window's dense results (same layouts as gnm_window_dense; the
  * stats block has 2*n_sites+4 rows, the last four being the unmatched classes with
  * e_* columns zero). Valid until the slot is reused or the registry is replaced. No
@@ -238,7 +248,7 @@ enum { GNM_RMI_ROOT_LINEAR = 0, GNM_RMI_ROOT_MLP = 1 };
 typedef struct {
     int32_t root_kind;   /* GNM_RMI_ROOT_* */
     uint32_t n_leaves;   /* 1..65536 (4096) */
-    uint32_t hidden;     /* MLP root width, 1..32 (32) */
+    uint32_t hidden;     /* MLP root width: 8, 16 or 32 (32) */
     uint32_t leaf_iters; /* gradient steps for the linear stages (4) */
     uint32_t mlp_steps;  /* Adam steps for the MLP root (600) */
     uint32_t mlp_batch;  /* samples per Adam step (65536) */
@@ -263,7 +273,9 @@ void gnm_rmi_config_default(gnm_rmi_config *cfg);
 
 /* Trains the learned index on the GPU from n device addresses `keys` (the lookups the
  * plain binary search answers; their positions are computed by it), then computes the
- * per-leaf error bounds. Sets the lookup mode to GNM_LOOKUP_RMI on success. */
+ * per-leaf error bounds. Contexts whose lookup_mode is GNM_LOOKUP_AUTO use the learned
+ * index from then on. Needs fewer than 2^24 ranges. Allocates and frees its own training
+ * scratch and synchronises `stream`. */
 gnm_status gnm_rmi_train(gnm_ctx *ctx, const uint32_t *keys, uint64_t n,
                          const gnm_rmi_config *cfg, gnm_rmi_report *report, void *stream);
 

@@ -18,7 +18,6 @@ namespace gnm {
 namespace dev {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kMaxProbe = 8;
 
 __device__ __forceinline__ uint4 ld_stream4(const uint32_t* p) {
     return __ldcs(reinterpret_cast<const uint4*>(p));
@@ -119,6 +118,26 @@ __device__ __forceinline__ uint32_t rmi_lookup(const RmiDev& m, const float* a, 
     return pred_search1(starts, 0, n, x);
 }
 
+// Staged placement, last level: the 64-byte block of 8 ranges holding x (8 starts, then
+// their 8 sites; padding past the last range repeats 0xFFFFFFFF as start and the last site,
+// so it only ever matches x = 0xFFFFFFFF, which belongs to the last range anyway).
+__device__ __forceinline__ uint32_t staged_block_site(const uint4* b, uint32_t x) {
+    const uint4 s0 = __ldg(b), s1 = __ldg(b + 1), w0 = __ldg(b + 2), w1 = __ldg(b + 3);
+    const uint32_t c = (s0.y <= x) + (s0.z <= x) + (s0.w <= x) + (s1.x <= x) + (s1.y <= x) +
+                       (s1.z <= x) + (s1.w <= x);  // s0.x <= x holds: it is the block's sample
+    const uint4 w = c < 4 ? w0 : w1;
+    const uint32_t q = c & 3u;
+    return q == 0 ? w.x : (q == 1 ? w.y : (q == 2 ? w.z : w.w));
+}
+
+// Range index form of the same lookup (largest i with start_i <= x), clamped to n-1.
+__device__ __forceinline__ uint32_t staged_block_pos(const uint4* b, uint32_t jb, uint32_t x, uint32_t n) {
+    const uint4 s0 = __ldg(b), s1 = __ldg(b + 1);
+    const uint32_t c = (s0.y <= x) + (s0.z <= x) + (s0.w <= x) + (s1.x <= x) + (s1.y <= x) +
+                       (s1.z <= x) + (s1.w <= x);
+    return min(jb * kBlockRanges + c, n - 1);
+}
+
 // One classified record.
 struct Item {
     uint32_t key;   // site*2+dir, or 2*n_sites + unmatched class
@@ -187,19 +206,24 @@ __device__ __forceinline__ uint64_t peer_sum(unsigned peers, uint32_t v) {
     return ((uint64_t)hi << 16) + (uint64_t)lo;
 }
 
-// Shared-memory hash slot of `key` (insert if absent); -1 after kMaxProbe probes.
+// Shared-memory cache slot of `key`: one of the two slots of its bucket pair, taking a
+// free one if needed; -1 when both hold other keys (the record then goes to global
+// memory). Keys seen early in a CTA's range -- the frequent ones -- keep their slots.
 __device__ __forceinline__ int table_slot(uint32_t* tk, uint32_t cap, uint32_t key) {
     uint32_t h = (key * 2654435761u);
-    h = (h ^ (h >> 15)) & (cap - 1u);
-#pragma unroll 1
-    for (int probe = 0; probe < kMaxProbe; ++probe) {
-        const uint32_t k = *reinterpret_cast<volatile uint32_t*>(tk + h);
-        if (k == key) return (int)h;
-        if (k == kEmptyKey) {
-            const uint32_t old = atomicCAS(tk + h, kEmptyKey, key);
-            if (old == kEmptyKey || old == key) return (int)h;
-        }
-        h = (h + 1u) & (cap - 1u);
+    h = (h ^ (h >> 15)) & (cap - 2u);  // even slot of the pair
+    volatile uint32_t* vk = tk;
+    uint32_t k0 = vk[h];
+    if (k0 == key) return (int)h;
+    uint32_t k1 = vk[h + 1];
+    if (k1 == key) return (int)h + 1;
+    if (k0 == kEmptyKey) {
+        k0 = atomicCAS(tk + h, kEmptyKey, key);
+        if (k0 == kEmptyKey || k0 == key) return (int)h;
+    }
+    if (k1 == kEmptyKey) {
+        k1 = atomicCAS(tk + h + 1, kEmptyKey, key);
+        if (k1 == kEmptyKey || k1 == key) return (int)h + 1;
     }
     return -1;
 }
@@ -212,21 +236,10 @@ __device__ __forceinline__ uint64_t* smem_row(uint64_t* tv, uint32_t* tk, uint32
     return s >= 0 ? tv + (size_t)s * kAccCols : nullptr;
 }
 
-// Accumulate one item per lane. Warp-collective in the warp-aggregated and global
-// modes: every lane of the warp calls it (invalid lanes with valid = false).
-template <int TABLE, int AGG>
-__device__ __forceinline__ void accumulate(const Item& it, uint64_t* tv, uint32_t* tk,
-                                           uint32_t cap, uint64_t* gacc) {
-    if (TABLE != kTableGlobal && AGG == GNM_AGG_DIRECT) {
-        if (!it.valid) return;
-        uint64_t* row = smem_row<TABLE>(tv, tk, cap, it.key);
-        if (row == nullptr) row = gacc + (size_t)it.key * kAccCols;
-        row_add(row, it);
-        return;
-    }
-    const uint32_t k = it.valid ? it.key : kEmptyKey;
-    const unsigned peers = __match_any_sync(kFull, k);
-    if (!it.valid) return;
+// Sums of one item per lane over the lanes that share its key, added by the group
+// leader to `row` (or, when row is null, to the key's global accumulator row).
+// Warp-collective over the lanes with `part` set.
+__device__ __forceinline__ void group_add(const Item& it, unsigned peers, uint64_t* row, uint64_t* gacc) {
     const uint32_t e = it.elig ? 1u : 0u;
     const uint32_t n = __popc(peers);
     const uint32_t ne = __reduce_add_sync(peers, e);
@@ -238,10 +251,39 @@ __device__ __forceinline__ void accumulate(const Item& it, uint64_t* tv, uint32_
         edur = peer_sum(peers, it.elig ? it.dur : 0u);
     }
     if ((int)(threadIdx.x & 31u) != __ffs(peers) - 1) return;
-    uint64_t* row = nullptr;
-    if (TABLE != kTableGlobal) row = smem_row<TABLE>(tv, tk, cap, it.key);
     if (row == nullptr) row = gacc + (size_t)it.key * kAccCols;
     row_add_sums(row, ((uint64_t)n << 32) | ne, oc, pk, eoc, edur, ne != 0);
+}
+
+// Accumulate one item per lane. Warp-collective: every lane of the warp calls it
+// (invalid lanes with valid = false).
+//   DIRECT aggregation: each lane adds to its key's shared-memory row; lanes whose key
+//   has no row (cache full) are combined per key across the warp and added globally.
+//   WARP aggregation: lanes are first combined per key; the group leader adds.
+template <int TABLE, int AGG>
+__device__ __forceinline__ void accumulate(const Item& it, uint64_t* tv, uint32_t* tk,
+                                           uint32_t cap, uint64_t* gacc) {
+    if (TABLE != kTableGlobal && AGG == GNM_AGG_DIRECT) {
+        uint64_t* row = it.valid ? smem_row<TABLE>(tv, tk, cap, it.key) : nullptr;
+        const bool miss = it.valid && row == nullptr;
+        if (TABLE == kTableHash && __any_sync(kFull, miss)) {
+            const unsigned peers = __match_any_sync(kFull, miss ? it.key : kEmptyKey);
+            if (miss) group_add(it, peers, nullptr, gacc);
+        }
+        if (row) row_add(row, it);
+        return;
+    }
+    const unsigned peers = __match_any_sync(kFull, it.valid ? it.key : kEmptyKey);
+    if (!it.valid) return;
+    uint64_t* row = nullptr;
+    if (TABLE != kTableGlobal) {
+        // the leader probes for the whole group
+        const int leader = __ffs(peers) - 1;
+        uint64_t* r = nullptr;
+        if ((int)(threadIdx.x & 31u) == leader) r = smem_row<TABLE>(tv, tk, cap, it.key);
+        row = (uint64_t*)__shfl_sync(peers, (unsigned long long)r, leader);
+    }
+    group_add(it, peers, row, gacc);
 }
 
 // Adds the CTA's shared-memory sums to the window's global accumulators and clears them.
@@ -339,6 +381,7 @@ __host__ __device__ inline size_t smem_layout(int lookup, int table, uint32_t n_
     o = align_up(o, 16);
     *off_lookup = o;
     if (lookup == kLookupSmem) o += (size_t)n_ranges * 8;
+    if (lookup == kLookupStaged) o += (size_t)((n_ranges + kBlockRanges - 1) / kBlockRanges) * 4;
     if (lookup == kLookupRmi) o += (size_t)n_leaves * 16;
     return align_up(o, 16);
 }
@@ -362,6 +405,10 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
         pred_search<R, false>(p.starts, p.n_ranges, x, idx);
 #pragma unroll
         for (int j = 0; j < R; ++j) site[j] = __ldg(p.rsite + idx[j]);
+    } else if (LOOKUP == kLookupStaged) {
+        pred_search<R, true>(sm.s_starts, p.n_blocks, x, idx);  // block of x
+#pragma unroll
+        for (int j = 0; j < R; ++j) site[j] = staged_block_site(p.blocks + 4 * (size_t)idx[j], x[j]);
     } else {
 #pragma unroll
         for (int j = 0; j < R; ++j) {
@@ -465,6 +512,11 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512)
         sm.s_starts = st;
         sm.s_site = si;
     }
+    if (LOOKUP == kLookupStaged) {
+        uint32_t* st = reinterpret_cast<uint32_t*>(smem_raw + off_lookup);
+        for (uint32_t i = tid; i < p.n_blocks; i += B) st[i] = __ldg(p.sample + i);
+        sm.s_starts = st;
+    }
     if (LOOKUP == kLookupRmi) {
         const uint32_t L = p.rmi.n_leaves;
         float* a = reinterpret_cast<float*>(smem_raw + off_lookup);
@@ -530,6 +582,7 @@ cudaError_t launch_variant(const AggParams& p, const LaunchShape& s, cudaStream_
         if (e != cudaSuccess) return e;
         if (dev < 64) set_bytes[dev] = (int)s.smem;
     }
+    (void)cudaGetLastError();  // report this launch's error only
     k<<<s.grid, s.block, s.smem, st>>>(p);
     return cudaGetLastError();
 }

@@ -24,6 +24,7 @@ bool local_overlaps(uint32_t lp, uint8_t ll, const uint32_t* prefix, const uint8
 
 constexpr uint32_t kRingSize = 16;
 constexpr size_t kRegistrySmemMax = 96 * 1024;   // bytes of ranges kept in shared memory
+constexpr size_t kSampleSmemMax = 96 * 1024;     // bytes of block samples (staged placement)
 constexpr size_t kDirectTableMax = 120 * 1024;   // direct-indexed per-CTA sums
 constexpr size_t kHashTableMax = 176 * 1024;     // hashed per-CTA sums
 constexpr uint32_t kFinalizeInKernelMaxKeys = 65536;
@@ -39,23 +40,25 @@ static void free_dev(void* p) {
 
 static gnm_status wait_slot_on_stream(gnm_ctx* c, uint32_t s, cudaStream_t st) {
     Slot& sl = c->slots[s];
-    if (sl.ev_recorded) GNM_CU(cudaStreamWaitEvent(st, sl.ev, 0));
+    if (sl.ev) GNM_CU(cudaStreamWaitEvent(st, sl.ev, 0));
     return GNM_OK;
 }
 
-gnm_status acquire_slot(gnm_ctx* c, uint64_t wid, cudaStream_t st, uint32_t* out) {
+static gnm_status acquire_slot_impl(gnm_ctx* c, uint64_t wid, cudaStream_t st, bool pin, uint32_t* out) {
     auto it = c->slot_of.find(wid);
     uint32_t s;
     if (it != c->slot_of.end()) {
         s = it->second;
+        if (c->slots[s].pinned) return fail(GNM_E_STATE, "window id belongs to a plan");
     } else {
         s = UINT32_MAX;
         for (uint32_t i = 0; i < c->n_slots; ++i)
             if (!c->slots[i].used) { s = i; break; }
-        if (s == UINT32_MAX) {  // evict the oldest window
+        if (s == UINT32_MAX) {  // evict the oldest window not held by a plan
             uint64_t best = UINT64_MAX;
             for (uint32_t i = 0; i < c->n_slots; ++i)
-                if (c->slots[i].age < best) { best = c->slots[i].age; s = i; }
+                if (!c->slots[i].pinned && c->slots[i].age < best) { best = c->slots[i].age; s = i; }
+            if (s == UINT32_MAX) return fail(GNM_E_CAPACITY, "every result slot is held by a plan");
             c->slot_of.erase(c->slots[s].window_id);
         }
         c->slot_of[wid] = s;
@@ -69,6 +72,7 @@ gnm_status acquire_slot(gnm_ctx* c, uint64_t wid, cudaStream_t st, uint32_t* out
     sl.used = true;
     sl.open = false;
     sl.finalized = false;
+    sl.pinned = pin;
     sl.window_id = wid;
     sl.records = 0;
     sl.age = ++c->age;
@@ -76,16 +80,38 @@ gnm_status acquire_slot(gnm_ctx* c, uint64_t wid, cudaStream_t st, uint32_t* out
     return GNM_OK;
 }
 
-static gnm_status mark_slot(gnm_ctx* c, uint32_t s, cudaStream_t st) {
-    Slot& sl = c->slots[s];
-    GNM_CU(cudaEventRecord(sl.ev, st));
-    sl.ev_recorded = true;
+gnm_status acquire_slot(gnm_ctx* c, uint64_t wid, cudaStream_t st, uint32_t* out) {
+    return acquire_slot_impl(c, wid, st, false, out);
+}
+
+gnm_status acquire_slot_pinned(gnm_ctx* c, uint64_t wid, cudaStream_t st, uint32_t* out) {
+    return acquire_slot_impl(c, wid, st, true, out);
+}
+
+void unpin_slot(gnm_ctx* c, uint32_t s) {
+    if (s < c->slots.size()) c->slots[s].pinned = false;
+}
+
+void set_slots_done(gnm_ctx* c, const uint32_t* slots, size_t n, cudaEvent_t ev, bool finalized) {
+    for (size_t k = 0; k < n; ++k) {
+        Slot& sl = c->slots[slots[k]];
+        sl.ev = ev;
+        sl.open = !finalized;
+        sl.finalized = finalized;
+    }
+}
+
+// Records a completion event on st (a ring entry's) and returns it.
+static gnm_status record_event(gnm_ctx* c, cudaStream_t st, cudaEvent_t* ev) {
+    LaunchBuf* lb;
+    GNM_TRY(acquire_ring(c, 0, &lb));
+    GNM_CU(cudaEventRecord(lb->ev, st));
+    lb->ev_recorded = true;
+    *ev = lb->ev;
     return GNM_OK;
 }
 
 void release_slots(gnm_ctx* c) {
-    for (auto& s : c->slots)
-        if (s.ev) cudaEventDestroy(s.ev);
     c->slots.clear();
     c->slot_of.clear();
     free_dev(c->d_acc);
@@ -112,11 +138,11 @@ static gnm_status find_window(gnm_ctx* c, uint64_t wid, uint32_t* s) {
 
 // ------------------------------------------------------------- launch buffers
 
-static gnm_status acquire_ring(gnm_ctx* c, uint32_t n_win, LaunchBuf** out) {
+gnm_status acquire_ring(gnm_ctx* c, uint32_t n_win, LaunchBuf** out) {
     LaunchBuf& b = c->ring[c->ring_next];
     c->ring_next = (c->ring_next + 1) % kRingSize;
     if (b.ev_recorded) GNM_CU(cudaEventSynchronize(b.ev));  // its previous launch is done
-    if (b.cap < n_win) {
+    if (b.cap < n_win || b.cap == 0) {
         const uint32_t cap = std::max<uint32_t>(n_win, 64);
         if (b.h_wins) cudaFreeHost(b.h_wins);
         free_dev(b.d_wins);
@@ -175,11 +201,26 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
         lookup_bytes = (size_t)c->rmi.n_leaves * 16;
     } else {
         int place = cfg.placement != GNM_PLACE_AUTO ? cfg.placement : c->tuned.placement;
-        if (place == GNM_PLACE_AUTO) place = (size_t)nr * 8 <= kRegistrySmemMax ? GNM_PLACE_SMEM : GNM_PLACE_L2;
+        const size_t sample_bytes = (size_t)c->n_blocks * 4;
+        if (place == GNM_PLACE_AUTO)
+            place = (size_t)nr * 8 <= kRegistrySmemMax ? GNM_PLACE_SMEM
+                    : sample_bytes <= kSampleSmemMax   ? GNM_PLACE_STAGED
+                                                       : GNM_PLACE_L2;
         if (place == GNM_PLACE_SMEM && (size_t)nr * 8 + 1024 > (size_t)c->smem_optin)
             return fail(GNM_E_INVAL, "registry too large for shared-memory placement");
-        s->lookup = place == GNM_PLACE_SMEM ? kLookupSmem : kLookupL2;
-        if (s->lookup == kLookupSmem) lookup_bytes = (size_t)nr * 8;
+        if (place == GNM_PLACE_STAGED && sample_bytes + 1024 > (size_t)c->smem_optin)
+            return fail(GNM_E_INVAL, "registry too large for staged placement");
+        if (place == GNM_PLACE_SMEM) {
+            s->lookup = kLookupSmem;
+            lookup_bytes = (size_t)nr * 8;
+        } else if (place == GNM_PLACE_STAGED) {
+            s->lookup = kLookupStaged;
+            lookup_bytes = sample_bytes;
+        } else if (place == GNM_PLACE_L2) {
+            s->lookup = kLookupL2;
+        } else {
+            return fail(GNM_E_INVAL, "unknown placement");
+        }
     }
     const size_t budget = (size_t)c->smem_optin > lookup_bytes + 1024 ? (size_t)c->smem_optin - lookup_bytes - 1024 : 0;
     const size_t direct = (size_t)c->keys * kAccCols * 8;
@@ -242,6 +283,9 @@ gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p) {
     p->last = rec->last;
     p->starts = c->d_starts;
     p->rsite = c->d_site;
+    p->blocks = reinterpret_cast<const uint4*>(c->d_blocks);
+    p->sample = c->d_sample;
+    p->n_blocks = c->n_blocks;
     p->n_ranges = (uint32_t)c->h_starts.size();
     p->n_sites = c->n_sites;
     p->rmi = c->rmi;
@@ -277,22 +321,93 @@ static gnm_status check_records(const gnm_records* rec, uint64_t need) {
     return GNM_OK;
 }
 
-// Core of every processing call: windows k = [offsets[k], offsets[k+1]) of rec.
-// finalize: rates and flags at the end; open_add: add to already open windows.
-static gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets,
-                              const uint64_t* wids, size_t n_win, cudaStream_t st, bool finalize,
-                              bool open_add) {
+gnm_status check_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets, size_t n_win) {
     if (!c->have_registry) return fail(GNM_E_STATE, "no registry loaded");
-    if (n_win == 0) return GNM_OK;
-    if (!offsets || !wids) return fail(GNM_E_INVAL, "offsets or window ids are NULL");
+    if (!offsets) return fail(GNM_E_INVAL, "offsets are NULL");
     for (size_t k = 0; k < n_win; ++k) {
         if (offsets[k + 1] < offsets[k]) return fail(GNM_E_INVAL, "offsets must be non-decreasing");
         if (offsets[k + 1] - offsets[k] > kMaxWindowRecords) return fail(GNM_E_INVAL, "a window holds 2^32 records or more");
     }
     if (n_win > c->n_slots) return fail(GNM_E_CAPACITY, "more windows in one call than result slots");
-    GNM_TRY(check_records(rec, offsets[n_win]));
-    const uint64_t base = offsets[0], N = offsets[n_win] - offsets[0];
+    return check_records(rec, offsets[n_win]);
+}
 
+gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* offsets, size_t n_win,
+                          const uint32_t* slots, bool finalize, Prepared* out) {
+    const uint64_t base = offsets[0], N = offsets[n_win] - offsets[0];
+    out->n = N;
+    out->wins.clear();
+    if (N == 0) return GNM_OK;
+    AggParams& p = out->p;
+    GNM_TRY(build_params(c, dr, &p));
+    LaunchShape& sh = out->sh;
+    GNM_TRY(choose_shape(c, N, &sh));
+    p.table_cap = sh.cap;
+    p.n_total = N;
+    uint64_t chunk = ceil_div(N, (uint64_t)sh.grid);
+    chunk = (chunk + 3) & ~3ull;
+    sh.grid = (int)ceil_div(N, chunk);
+    p.chunk = chunk;
+    const uintptr_t a0 = (uintptr_t)dr->srcaddr & 15u;
+    const uint32_t* f[6] = {dr->srcaddr, dr->dstaddr, dr->dPkts, dr->dOctets, dr->first, dr->last};
+    p.vec_ok = 1;
+    for (auto* q : f)
+        if (((uintptr_t)q & 15u) != a0) p.vec_ok = 0;
+    p.phase = (uint32_t)(a0 >> 2);
+    out->fin_in_kernel = finalize && c->keys <= kFinalizeInKernelMaxKeys;
+    for (size_t k = 0; k < n_win; ++k) {
+        const uint64_t b = offsets[k] - base, e = offsets[k + 1] - base;
+        if (b == e) continue;
+        WinDesc w;
+        w.begin = b;
+        w.end = e;
+        w.slot = slots[k];
+        w.flags = out->fin_in_kernel ? kWinFinalize : 0u;
+        w.ctas = (uint32_t)((e - 1) / chunk - b / chunk + 1);
+        w.pad = 0;
+        out->wins.push_back(w);
+    }
+    return GNM_OK;
+}
+
+gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, size_t n_win,
+                            const uint32_t* slots, bool finalize, WinDesc* d_wins, uint32_t* d_done,
+                            cudaStream_t st, uint32_t* launches) {
+    *launches = 0;
+    if (pr.n) {
+        pr.p.wins = d_wins;
+        pr.p.n_wins = (uint32_t)pr.wins.size();
+        pr.p.done = d_done;
+        GNM_CU(launch_aggregate(pr.p, pr.sh, st));
+        ++*launches;
+        if (finalize && !pr.fin_in_kernel) {
+            for (size_t k = 0; k < n_win; ++k) {
+                if (offsets[k + 1] == offsets[k]) continue;
+                GNM_CU(launch_finalize(pr.p, slots[k], st));
+                ++*launches;
+            }
+        }
+    }
+    // empty windows: zero sums, no rate, no flag
+    for (size_t k = 0; k < n_win && finalize; ++k) {
+        if (offsets[k + 1] != offsets[k]) continue;
+        const uint32_t s = slots[k];
+        GNM_CU(cudaMemsetAsync(c->d_stats + (size_t)s * c->keys * kNStat, 0, (size_t)c->keys * kNStat * 8, st));
+        GNM_CU(cudaMemsetAsync(c->d_rate + (size_t)s * 2 * c->n_sites, 0xFF, (size_t)2 * c->n_sites * 8, st));
+        GNM_CU(cudaMemsetAsync(c->d_flag + (size_t)s * 2 * c->n_sites, 0, (size_t)2 * c->n_sites, st));
+    }
+    return GNM_OK;
+}
+
+// Core of every processing call: windows k = [offsets[k], offsets[k+1]) of rec.
+// finalize: rates and flags at the end; open_add: add to already open windows.
+static gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets,
+                              const uint64_t* wids, size_t n_win, cudaStream_t st, bool finalize,
+                              bool open_add) {
+    if (n_win == 0) return GNM_OK;
+    if (!wids) return fail(GNM_E_INVAL, "window ids are NULL");
+    GNM_TRY(check_windows(c, rec, offsets, n_win));
+    const uint64_t base = offsets[0], N = offsets[n_win] - offsets[0];
     gnm_records dr = *rec;
     if (N && !rec->on_device) {
         const uint32_t* d[6];
@@ -301,7 +416,6 @@ static gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t
     } else if (N) {
         dr.srcaddr += base; dr.dstaddr += base; dr.dPkts += base; dr.dOctets += base; dr.first += base; dr.last += base;
     }
-    // slots
     std::vector<uint32_t> slot(n_win);
     for (size_t k = 0; k < n_win; ++k) {
         if (open_add) {
@@ -319,71 +433,20 @@ static gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t
             GNM_TRY(acquire_slot(c, wids[k], st, &slot[k]));
         }
     }
-    c->last_launches = 0;
-    if (N) {
-        AggParams p;
-        GNM_TRY(build_params(c, &dr, &p));
-        LaunchShape sh;
-        GNM_TRY(choose_shape(c, N, &sh));
-        p.table_cap = sh.cap;
-        p.n_total = N;
-        uint64_t chunk = ceil_div(N, (uint64_t)sh.grid);
-        chunk = (chunk + 3) & ~3ull;
-        sh.grid = (int)ceil_div(N, chunk);
-        p.chunk = chunk;
-        const uintptr_t a0 = (uintptr_t)dr.srcaddr & 15u;
-        const uint32_t* f[6] = {dr.srcaddr, dr.dstaddr, dr.dPkts, dr.dOctets, dr.first, dr.last};
-        p.vec_ok = 1;
-        for (auto* q : f)
-            if (((uintptr_t)q & 15u) != a0) p.vec_ok = 0;
-        p.phase = (uint32_t)(a0 >> 2);
-        const bool fin_in_kernel = finalize && c->keys <= kFinalizeInKernelMaxKeys;
-        // descriptors of the non-empty windows
-        LaunchBuf* lb;
-        GNM_TRY(acquire_ring(c, (uint32_t)n_win, &lb));
-        uint32_t nw = 0;
-        for (size_t k = 0; k < n_win; ++k) {
-            const uint64_t b = offsets[k] - base, e = offsets[k + 1] - base;
-            if (b == e) continue;
-            WinDesc& w = lb->h_wins[nw++];
-            w.begin = b;
-            w.end = e;
-            w.slot = slot[k];
-            w.flags = fin_in_kernel ? kWinFinalize : 0u;
-            w.ctas = (uint32_t)((e - 1) / chunk - b / chunk + 1);
-            w.pad = 0;
-        }
-        GNM_CU(cudaMemcpyAsync(lb->d_wins, lb->h_wins, sizeof(WinDesc) * nw, cudaMemcpyHostToDevice, st));
-        p.wins = lb->d_wins;
-        p.n_wins = nw;
-        p.done = lb->d_done;
-        GNM_CU(launch_aggregate(p, sh, st));
-        c->last_launches++;
-        if (finalize && !fin_in_kernel) {
-            for (size_t k = 0; k < n_win; ++k) {
-                if (offsets[k + 1] == offsets[k]) continue;
-                GNM_CU(launch_finalize(p, slot[k], st));
-                c->last_launches++;
-            }
-        }
-        GNM_CU(cudaEventRecord(lb->ev, st));
-        lb->ev_recorded = true;
+    Prepared pr;
+    GNM_TRY(prepare_launch(c, &dr, offsets, n_win, slot.data(), finalize, &pr));
+    LaunchBuf* lb;
+    GNM_TRY(acquire_ring(c, (uint32_t)n_win, &lb));
+    if (!pr.wins.empty()) {
+        std::memcpy(lb->h_wins, pr.wins.data(), sizeof(WinDesc) * pr.wins.size());
+        GNM_CU(cudaMemcpyAsync(lb->d_wins, lb->h_wins, sizeof(WinDesc) * pr.wins.size(), cudaMemcpyHostToDevice, st));
     }
-    // empty windows: zero sums, no rate, no flag
-    for (size_t k = 0; k < n_win; ++k) {
-        if (offsets[k + 1] != offsets[k] || !finalize) continue;
-        const uint32_t s = slot[k];
-        GNM_CU(cudaMemsetAsync(c->d_stats + (size_t)s * c->keys * kNStat, 0, (size_t)c->keys * kNStat * 8, st));
-        GNM_CU(cudaMemsetAsync(c->d_rate + (size_t)s * 2 * c->n_sites, 0xFF, (size_t)2 * c->n_sites * 8, st));
-        GNM_CU(cudaMemsetAsync(c->d_flag + (size_t)s * 2 * c->n_sites, 0, (size_t)2 * c->n_sites, st));
-    }
-    for (size_t k = 0; k < n_win; ++k) {
-        Slot& sl = c->slots[slot[k]];
-        sl.records += offsets[k + 1] - offsets[k];
-        sl.open = !finalize;
-        sl.finalized = finalize;
-        GNM_TRY(mark_slot(c, slot[k], st));
-    }
+    GNM_TRY(enqueue_prepared(c, pr, offsets, n_win, slot.data(), finalize, lb->d_wins, lb->d_done, st,
+                             &c->last_launches));
+    GNM_CU(cudaEventRecord(lb->ev, st));
+    lb->ev_recorded = true;
+    for (size_t k = 0; k < n_win; ++k) c->slots[slot[k]].records += offsets[k + 1] - offsets[k];
+    set_slots_done(c, slot.data(), n_win, lb->ev, finalize);
     return GNM_OK;
 }
 
@@ -474,6 +537,8 @@ void gnm_destroy(gnm_ctx* c) {
     if (c->aux) cudaStreamDestroy(c->aux);
     free_dev(c->d_starts);
     free_dev(c->d_site);
+    free_dev(c->d_blocks);
+    free_dev(c->d_sample);
     free_dev(c->d_violations);
     free_dev(c->d_flag_count);
     free_dev(c->d_rmi_a);
@@ -511,8 +576,13 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     release_slots(c);
     free_dev(c->d_starts);
     free_dev(c->d_site);
+    free_dev(c->d_blocks);
+    free_dev(c->d_sample);
     c->d_starts = nullptr;
     c->d_site = nullptr;
+    c->d_blocks = nullptr;
+    c->d_sample = nullptr;
+    c->n_blocks = 0;
     c->have_registry = false;
     c->rmi_ready = false;
     c->tuned = Tuned();
@@ -521,6 +591,23 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     GNM_CU(cudaMalloc(&c->d_site, nr * 4));
     GNM_CU(cudaMemcpy(c->d_starts, starts.data(), nr * 4, cudaMemcpyHostToDevice));
     GNM_CU(cudaMemcpy(c->d_site, sites.data(), nr * 4, cudaMemcpyHostToDevice));
+    // staged layout: blocks of 8 ranges (8 starts, then 8 sites; the last block padded
+    // with start 0xFFFFFFFF and the last site) and the first start of every block
+    const size_t nb = (nr + kBlockRanges - 1) / kBlockRanges;
+    std::vector<uint32_t> blk(nb * 2 * kBlockRanges), smp(nb);
+    for (size_t j = 0; j < nb; ++j) {
+        for (size_t k = 0; k < kBlockRanges; ++k) {
+            const size_t i = j * kBlockRanges + k;
+            blk[j * 16 + k] = i < nr ? starts[i] : 0xFFFFFFFFu;
+            blk[j * 16 + 8 + k] = i < nr ? sites[i] : sites[nr - 1];
+        }
+        smp[j] = starts[j * kBlockRanges];
+    }
+    GNM_CU(cudaMalloc(&c->d_blocks, blk.size() * 4));
+    GNM_CU(cudaMalloc(&c->d_sample, nb * 4));
+    GNM_CU(cudaMemcpy(c->d_blocks, blk.data(), blk.size() * 4, cudaMemcpyHostToDevice));
+    GNM_CU(cudaMemcpy(c->d_sample, smp.data(), nb * 4, cudaMemcpyHostToDevice));
+    c->n_blocks = (uint32_t)nb;
     c->h_starts.swap(starts);
     c->h_site.swap(sites);
     c->n_sites = n_sites;
@@ -541,7 +628,6 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     GNM_CU(cudaMalloc(&c->d_flag_keys, (size_t)2 * n_sites * 4));
     GNM_CU(cudaMemset(c->d_acc, 0, slots * keys * kAccCols * 8));
     c->slots.resize(slots);
-    for (auto& s : c->slots) GNM_CU(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
     c->have_registry = true;
     return GNM_OK;
 }
@@ -556,7 +642,8 @@ gnm_status gnm_registry_info_get(gnm_ctx* c, gnm_registry_info* out) {
     out->n_prefixes = c->n_prefixes;
     LaunchShape sh;
     if (choose_shape(c, 1u << 20, &sh) == GNM_OK) {
-        out->placement = sh.lookup == kLookupSmem ? GNM_PLACE_SMEM : GNM_PLACE_L2;
+        out->placement = sh.lookup == kLookupSmem ? GNM_PLACE_SMEM
+                         : sh.lookup == kLookupStaged ? GNM_PLACE_STAGED : GNM_PLACE_L2;
         out->lookup_mode = sh.lookup == kLookupRmi ? GNM_LOOKUP_RMI : GNM_LOOKUP_BSEARCH;
         out->privatized = sh.table != kTableGlobal;
     }
@@ -594,8 +681,9 @@ gnm_status gnm_window_open(gnm_ctx* c, uint64_t wid, void* stream) {
     GNM_CU(cudaSetDevice(c->device));
     uint32_t s;
     GNM_TRY(acquire_slot(c, wid, (cudaStream_t)stream, &s));
-    c->slots[s].open = true;
-    GNM_TRY(mark_slot(c, s, (cudaStream_t)stream));
+    cudaEvent_t ev;
+    GNM_TRY(record_event(c, (cudaStream_t)stream, &ev));
+    set_slots_done(c, &s, 1, ev, false);
     return GNM_OK;
 }
 
@@ -620,15 +708,16 @@ gnm_status gnm_window_close(gnm_ctx* c, uint64_t wid, void* stream) {
     GNM_TRY(build_params(c, &none, &p));
     GNM_CU(launch_finalize(p, s, st));
     c->last_launches = 1;
-    sl.open = false;
-    sl.finalized = true;
-    return mark_slot(c, s, st);
+    cudaEvent_t ev;
+    GNM_TRY(record_event(c, st, &ev));
+    set_slots_done(c, &s, 1, ev, true);
+    return GNM_OK;
 }
 
 static gnm_status sync_slot(gnm_ctx* c, uint32_t s) {
     Slot& sl = c->slots[s];
     if (!sl.finalized) return fail(GNM_E_STATE, "window is open (not finalised)");
-    if (sl.ev_recorded) GNM_CU(cudaEventSynchronize(sl.ev));
+    if (sl.ev) GNM_CU(cudaEventSynchronize(sl.ev));
     return GNM_OK;
 }
 
@@ -650,6 +739,36 @@ gnm_status gnm_window_dense(gnm_ctx* c, uint64_t wid, uint64_t* stats, uint64_t*
     if (unmatched)
         for (int k = 0; k < kUnmatched; ++k)
             for (int j = 0; j < 3; ++j) unmatched[k * 3 + j] = un6[k * kNStat + j];
+    return GNM_OK;
+}
+
+gnm_status gnm_windows_results(gnm_ctx* c, const uint64_t* wids, size_t n, uint64_t* stats,
+                               uint64_t* unmatched, double* rate, uint8_t* flag) {
+    if (!c || (n && !wids)) return fail(GNM_E_INVAL, "NULL argument");
+    GNM_CU(cudaSetDevice(c->device));
+    const size_t nk = 2 * (size_t)c->n_sites;
+    std::vector<uint32_t> slot(n);
+    for (size_t k = 0; k < n; ++k) {
+        GNM_TRY(find_window(c, wids[k], &slot[k]));
+        if (!c->slots[slot[k]].finalized) return fail(GNM_E_STATE, "window is open (not finalised)");
+        GNM_TRY(wait_slot_on_stream(c, slot[k], c->aux));
+    }
+    std::vector<uint64_t> un6(unmatched ? n * kUnmatched * kNStat : 0);
+    for (size_t k = 0; k < n; ++k) {
+        const uint32_t s = slot[k];
+        const uint64_t* st = c->d_stats + (size_t)s * c->keys * kNStat;
+        if (stats) GNM_CU(cudaMemcpyAsync(stats + k * nk * kNStat, st, nk * kNStat * 8, cudaMemcpyDeviceToHost, c->aux));
+        if (unmatched)
+            GNM_CU(cudaMemcpyAsync(un6.data() + k * kUnmatched * kNStat, st + nk * kNStat, kUnmatched * kNStat * 8,
+                                   cudaMemcpyDeviceToHost, c->aux));
+        if (rate) GNM_CU(cudaMemcpyAsync(rate + k * nk, c->d_rate + (size_t)s * nk, nk * 8, cudaMemcpyDeviceToHost, c->aux));
+        if (flag) GNM_CU(cudaMemcpyAsync(flag + k * nk, c->d_flag + (size_t)s * nk, nk, cudaMemcpyDeviceToHost, c->aux));
+    }
+    GNM_CU(cudaStreamSynchronize(c->aux));
+    if (unmatched)
+        for (size_t k = 0; k < n; ++k)
+            for (int q = 0; q < kUnmatched; ++q)
+                for (int j = 0; j < 3; ++j) unmatched[(k * kUnmatched + q) * 3 + j] = un6[(k * kUnmatched + q) * kNStat + j];
     return GNM_OK;
 }
 
@@ -730,9 +849,10 @@ gnm_status gnm_window_release(gnm_ctx* c, uint64_t wid) {
     uint32_t s;
     GNM_TRY(find_window(c, wid, &s));
     Slot& sl = c->slots[s];
+    if (sl.pinned) return fail(GNM_E_STATE, "window id belongs to a plan");
     if (sl.open) {  // keep the zero-accumulator invariant
         GNM_CU(cudaSetDevice(c->device));
-        if (sl.ev_recorded) GNM_CU(cudaEventSynchronize(sl.ev));
+        if (sl.ev) GNM_CU(cudaEventSynchronize(sl.ev));
         GNM_CU(cudaMemset(c->d_acc + (size_t)s * c->keys * kAccCols, 0, (size_t)c->keys * kAccCols * 8));
     }
     sl.used = false;

@@ -20,6 +20,7 @@ const char* get_error();
     do {                                                                                 \
         cudaError_t e_ = (call);                                                         \
         if (e_ != cudaSuccess) {                                                         \
+            (void)cudaGetLastError(); /* do not leak a non-sticky error into later calls */ \
             ::gnm::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));        \
             return GNM_E_CUDA;                                                           \
         }                                                                                \
@@ -38,11 +39,12 @@ struct Slot {
     bool used = false;
     bool open = false;        // accumulating, not finalised
     bool finalized = false;
+    bool pinned = false;      // owned by a plan: never evicted or reassigned
     uint64_t window_id = 0;
     uint64_t records = 0;     // records added so far (must stay below 2^32)
     uint64_t age = 0;         // assignment order, for eviction
-    cudaEvent_t ev = nullptr; // last work that wrote the slot
-    bool ev_recorded = false;
+    cudaEvent_t ev = nullptr; // recorded after the last work that wrote the slot (not owned;
+                              // re-recording it later only makes waits more conservative)
 };
 
 // Per-launch device scratch: window descriptors and finalise tickets.
@@ -82,6 +84,9 @@ struct gnm_ctx {
     std::vector<uint32_t> h_starts, h_site;
     uint32_t* d_starts = nullptr;
     uint32_t* d_site = nullptr;
+    uint32_t* d_blocks = nullptr;   // staged placement: [n_blocks][8 starts, 8 sites]
+    uint32_t* d_sample = nullptr;   // staged placement: first start of every block
+    uint32_t n_blocks = 0;
     uint32_t local_pfx[GNM_MAX_LOCAL] = {0};
     uint32_t local_mask[GNM_MAX_LOCAL] = {0};
     uint32_t n_local = 0;
@@ -118,9 +123,29 @@ struct gnm_ctx {
 };
 
 namespace gnm {
-// shared by api.cu and plan.cu
+// shared by api.cu, plan.cu and rmi_api.cu
 gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p);
 gnm_status choose_shape(gnm_ctx* c, uint64_t n_records, LaunchShape* s);
 gnm_status acquire_slot(gnm_ctx* c, uint64_t window_id, cudaStream_t st, uint32_t* slot_out);
 void release_slots(gnm_ctx* c);
+gnm_status check_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets, size_t n_win);
+
+// A launch over windows [offsets[k], offsets[k+1]) of device records `dr` (already
+// rebased so that offsets[0] is element 0): parameters, shape and descriptors.
+struct Prepared {
+    AggParams p;
+    LaunchShape sh;
+    std::vector<WinDesc> wins;   // non-empty windows only
+    bool fin_in_kernel = false;
+    uint64_t n = 0;
+};
+gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* offsets, size_t n_win,
+                          const uint32_t* slots, bool finalize, Prepared* out);
+// Enqueues the kernels of a prepared launch (descriptors already on the device).
+gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, size_t n_win,
+                            const uint32_t* slots, bool finalize, WinDesc* d_wins, uint32_t* d_done,
+                            cudaStream_t st, uint32_t* launches);
+// Next launch-scratch entry of the ring (waits for its previous use).
+gnm_status acquire_ring(gnm_ctx* c, uint32_t n_win, LaunchBuf** out);
+void set_slots_done(gnm_ctx* c, const uint32_t* slots, size_t n, cudaEvent_t ev, bool finalized);
 }  // namespace gnm

@@ -56,8 +56,12 @@ struct AggParams {
     // registry
     const uint32_t* starts;
     const uint32_t* rsite;
+    const uint4* blocks;         // staged placement: per 8 ranges, 8 starts then 8 sites
+    const uint32_t* sample;      // staged placement: first start of every block
+    uint32_t n_blocks;
     uint32_t n_ranges;
     uint32_t n_sites;
+    uint32_t pad1;
     // learned index (lookup mode RMI)
     RmiDev rmi;
     // local site
@@ -82,7 +86,8 @@ struct AggParams {
     unsigned long long* violations;  // learned-index fallbacks
 };
 
-enum { kLookupL2 = 0, kLookupSmem = 1, kLookupRmi = 2 };
+enum { kLookupL2 = 0, kLookupSmem = 1, kLookupRmi = 2, kLookupStaged = 3 };
+constexpr uint32_t kBlockRanges = 8;  // ranges per staged block (64 bytes)
 enum { kTableDirect = 0, kTableHash = 1, kTableGlobal = 2 };
 
 // Launch shape chosen by the host.

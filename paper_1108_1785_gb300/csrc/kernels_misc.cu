@@ -7,11 +7,13 @@ namespace gnm {
 cudaError_t launch_aggregate_l2(const AggParams& p, const LaunchShape& s, cudaStream_t st);
 cudaError_t launch_aggregate_smem(const AggParams& p, const LaunchShape& s, cudaStream_t st);
 cudaError_t launch_aggregate_rmi(const AggParams& p, const LaunchShape& s, cudaStream_t st);
+cudaError_t launch_aggregate_staged(const AggParams& p, const LaunchShape& s, cudaStream_t st);
 
 cudaError_t launch_aggregate(const AggParams& p, const LaunchShape& s, cudaStream_t st) {
     switch (s.lookup) {
         case kLookupSmem: return launch_aggregate_smem(p, s, st);
         case kLookupRmi: return launch_aggregate_rmi(p, s, st);
+        case kLookupStaged: return launch_aggregate_staged(p, s, st);
         default: return launch_aggregate_l2(p, s, st);
     }
 }
@@ -52,6 +54,11 @@ __global__ void k_lookup(const __grid_constant__ AggParams p, const uint32_t* __
         for (uint32_t i = threadIdx.x; i < p.n_ranges; i += blockDim.x) st[i] = __ldg(p.starts + i);
         s_starts = st;
     }
+    if (LOOKUP == kLookupStaged) {
+        uint32_t* st = reinterpret_cast<uint32_t*>(smem_raw);
+        for (uint32_t i = threadIdx.x; i < p.n_blocks; i += blockDim.x) st[i] = __ldg(p.sample + i);
+        s_starts = st;
+    }
     if (LOOKUP == kLookupRmi) {
         const uint32_t L = p.rmi.n_leaves;
         float* a = reinterpret_cast<float*>(smem_raw);
@@ -73,6 +80,10 @@ __global__ void k_lookup(const __grid_constant__ AggParams p, const uint32_t* __
         uint32_t idx;
         if (LOOKUP == kLookupRmi) {
             idx = dev::rmi_lookup(p.rmi, ra, rb, rx0, reps, p.starts, p.n_ranges, x, p.violations);
+        } else if (LOOKUP == kLookupStaged) {
+            uint32_t xs[1] = {x}, b[1];
+            dev::pred_search<1, true>(s_starts, p.n_blocks, xs, b);
+            idx = dev::staged_block_pos(p.blocks + 4 * (size_t)b[0], b[0], x, p.n_ranges);
         } else {
             uint32_t xs[1] = {x}, b[1];
             if (LOOKUP == kLookupSmem) dev::pred_search<1, true>(s_starts, p.n_ranges, xs, b);
@@ -88,6 +99,7 @@ __global__ void k_lookup(const __grid_constant__ AggParams p, const uint32_t* __
 
 cudaError_t launch_finalize(const AggParams& p, uint32_t slot, cudaStream_t st) {
     const uint32_t blocks = (p.keys + 255) / 256;
+    (void)cudaGetLastError();
     k_finalize<<<blocks > 4096 ? 4096 : blocks, 256, 0, st>>>(p, slot);
     return cudaGetLastError();
 }
@@ -113,7 +125,9 @@ cudaError_t launch_lookup(const AggParams& p, int lookup, const uint32_t* addr, 
     const uint64_t want = (n + 255) / 256;
     const int blocks = (int)(want < (uint64_t)sms * 8 ? want : (uint64_t)sms * 8);
     size_t smem = 0;
+    (void)cudaGetLastError();  // report this launch's error only
     if (lookup == kLookupSmem) smem = (size_t)p.n_ranges * 4;
+    if (lookup == kLookupStaged) smem = (size_t)p.n_blocks * 4;
     if (lookup == kLookupRmi) smem = (size_t)p.rmi.n_leaves * 16;
     cudaError_t e;
     switch (lookup) {
@@ -126,6 +140,11 @@ cudaError_t launch_lookup(const AggParams& p, int lookup, const uint32_t* addr, 
             e = cudaFuncSetAttribute(k_lookup<kLookupRmi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             k_lookup<kLookupRmi><<<blocks, 256, smem, st>>>(p, addr, n, site_out, pos_out);
+            break;
+        case kLookupStaged:
+            e = cudaFuncSetAttribute(k_lookup<kLookupStaged>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_lookup<kLookupStaged><<<blocks, 256, smem, st>>>(p, addr, n, site_out, pos_out);
             break;
         default:
             k_lookup<kLookupL2><<<blocks, 256, 0, st>>>(p, addr, n, site_out, pos_out);

@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kThreads) k_eps_sweep(const RmiDev m, const ui
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const uint64_t per = ((1ull << 32) + T - 1) / T;
     const uint64_t xa = tid * per;
-    const uint64_t xb = min(xa + per, 1ull << 32);
+    const uint64_t xb = (xa + per < (1ull << 32)) ? xa + per : (1ull << 32);
     if (xa >= xb) return;
     uint32_t t = dev::pred_search1(starts, 0, n, (uint32_t)xa);
     uint64_t next = t + 1 < n ? (uint64_t)__ldg(starts + t + 1) : (1ull << 32);

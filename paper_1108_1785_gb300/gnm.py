@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libgnm.so")
 NO_SITE = 0xFFFFFFFF
 NSTAT = 6
 LOOKUP_AUTO, LOOKUP_BSEARCH, LOOKUP_RMI = 0, 1, 2
-PLACE_AUTO, PLACE_SMEM, PLACE_L2 = 0, 1, 2
+PLACE_AUTO, PLACE_SMEM, PLACE_L2, PLACE_STAGED = 0, 1, 2, 3
 AGG_AUTO, AGG_DIRECT, AGG_WARP = 0, 1, 2
 ADMIN_OR, ADMIN_AND = 0, 1
 TABLE_AUTO, TABLE_DIRECT, TABLE_HASH, TABLE_GLOBAL = 0, 1, 2, 3
@@ -112,6 +112,7 @@ def lib():
             "gnm_flag_suboptimal": (st, [P, U64, C.c_double, P, P, S, C.POINTER(S)]),
             "gnm_window_dense": (st, [P, U64, P, P, P, P]),
             "gnm_window_device": (st, [P, U64, C.POINTER(P), C.POINTER(P), C.POINTER(P)]),
+            "gnm_windows_results": (st, [P, P, S, P, P, P, P]),
             "gnm_window_release": (st, [P, U64]),
             "gnm_lookup": (st, [P, P, U64, P, P, P]),
             "gnm_rmi_config_default": (None, [C.POINTER(RmiConfig)]),
@@ -307,6 +308,12 @@ class Context:
         f = np.empty(nk, np.uint8)
         self._c(lib().gnm_window_dense(self.h, window_id, _ptr(st), _ptr(un), _ptr(r), _ptr(f)))
         return st, un, r, f
+
+    def windows_results(self, window_ids, stats=None, unmatched=None, rate=None, flag=None):
+        """Dense results of many windows into caller-provided host arrays (one sync)."""
+        ids = np.ascontiguousarray(window_ids, np.uint64)
+        self._c(lib().gnm_windows_results(self.h, _ptr(ids), ids.size, _ptr(stats), _ptr(unmatched), _ptr(rate),
+                                          _ptr(flag)))
 
     def device_results(self, window_id: int):
         """Raw device addresses (stats, rate, flag) of a window's dense results."""

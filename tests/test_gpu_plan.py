@@ -1,0 +1,106 @@
+"""Batched plans (CUDA graph over many uneven windows) and the autotuner: every window
+of the batch equals the oracle, on every replay and after tuning."""
+import numpy as np
+import pytest
+
+import flowgen as fg
+import oracle
+from helpers import assert_window_matches, oracle_full
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gnm():
+    from paper_1108_1785_gb300 import build, gnm as g
+    build.build()
+    return g
+
+
+@pytest.fixture(scope="module")
+def batch():
+    reg = fg.registry_c1()
+    counts = fg.uneven_windows_c4(n_windows=48, seed=9, lo=1000, hi=200_000, median=20_000)
+    counts[5] = 0  # an empty window in the middle
+    rec, off = fg.batched_records_c4(reg, counts, seed=9)
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    expect = [oracle_full(reg, {k: v[off[w]:off[w + 1]] for k, v in rec.items()}, lpm=lpm)
+              for w in range(len(counts))]
+    return reg, rec, off, expect
+
+
+def test_plan_replays_match_oracle(gnm, batch):
+    reg, rec, off, expect = batch
+    ctx = gnm.Context(window_slots=64)
+    ctx.load(reg)
+    d = gnm.Records.to_device(rec)
+    ids = np.arange(len(off) - 1) + 1000
+    plan = ctx.plan(d, off, ids)
+    for rep in range(3):
+        plan.launch()
+        assert ctx.last_launch_count() == 1
+        for w in range(len(ids)):
+            assert_window_matches(ctx.dense(int(ids[w])), expect[w])
+    with pytest.raises(gnm.GnmError, match="plan"):
+        ctx.process(d, int(ids[0]))  # a plan's window id cannot be reused elsewhere
+    plan.close()
+    ctx.process(gnm.Records({k: v[:10] for k, v in d.fields.items()}), int(ids[0]))  # released with the plan
+    ctx.close()
+
+
+def test_plan_sees_new_buffer_contents(gnm, batch):
+    """Plans bind buffers, not contents: refill the buffers and replay."""
+    reg, rec, off, expect = batch
+    ctx = gnm.Context(window_slots=64)
+    ctx.load(reg)
+    d = gnm.Records.to_device(rec)
+    ids = np.arange(len(off) - 1)
+    plan = ctx.plan(d, off, ids)
+    plan.launch()
+    rec2, _ = fg.batched_records_c4(reg, np.diff(off), seed=10)
+    for k in gnm.FIELDS:
+        d.fields[k].copy_(torch.from_numpy(rec2[k].view(np.int32)))
+    plan.launch()
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    for w in (0, 7, 20, 47):
+        host = {k: v[off[w]:off[w + 1]] for k, v in rec2.items()}
+        assert_window_matches(ctx.dense(int(ids[w])), oracle_full(reg, host, lpm=lpm))
+    plan.close()
+    ctx.close()
+
+
+def test_autotune_then_exact(gnm, batch):
+    reg, rec, off, expect = batch
+    ctx = gnm.Context(window_slots=64)
+    ctx.load(reg)
+    d = gnm.Records.to_device(rec)
+    ids = np.arange(len(off) - 1) + 5
+    rep = ctx.autotune(d, off, ids)
+    assert rep.n_tried >= 8
+    assert 0 < rep.best_ms <= rep.default_ms * 1.05
+    assert rep.block_threads in (256, 512, 1024) and rep.unroll in (1, 2)
+    for w in range(len(ids)):
+        assert_window_matches(ctx.dense(int(ids[w])), expect[w])
+    ctx.process_windows(d, off, ids)  # tuned shape from now on
+    for w in range(len(ids)):
+        assert_window_matches(ctx.dense(int(ids[w])), expect[w])
+    ctx.close()
+
+
+def test_windows_results_batch_readout(gnm, batch):
+    reg, rec, off, expect = batch
+    ctx = gnm.Context(window_slots=64)
+    ctx.load(reg)
+    ids = np.arange(len(off) - 1) + 77
+    ctx.process_windows(gnm.Records.to_device(rec), off, ids)
+    nk = 2 * reg.n_sites
+    W = len(ids)
+    st = np.empty((W, nk, 6), np.uint64)
+    un = np.empty((W, 4, 3), np.uint64)
+    r = np.empty((W, nk), np.float64)
+    f = np.empty((W, nk), np.uint8)
+    ctx.windows_results(ids, st, un, r, f)
+    for w in range(W):
+        assert_window_matches((st[w], un[w], r[w], f[w]), expect[w])
+    ctx.close()

@@ -1,0 +1,244 @@
+"""The learned index on the GPU: training gradients against the FP64 oracle, trained
+stages against closed-form least squares, error bounds against the oracle's endpoint
+analysis, lookups bit-exact against the oracle (with and without proven bounds), and
+what the model gains over the plain binary search."""
+import numpy as np
+import pytest
+
+import flowgen as fg
+import oracle
+from helpers import assert_window_matches, oracle_full
+from oracle import rmi_ref
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gnm():
+    from paper_1108_1785_gb300 import build, gnm as g
+    build.build()
+    return g
+
+
+def remote_of(reg, rec):
+    src = rec["srcaddr"].astype(np.int64)
+    loc = np.zeros(src.shape, bool)
+    for p, l in zip(reg.local_prefix, reg.local_len):
+        loc |= (src >> (32 - int(l))) == (int(p) >> (32 - int(l)))
+    return np.where(loc, rec["dstaddr"], rec["srcaddr"]).astype(np.uint32)
+
+
+@pytest.fixture(scope="module")
+def c3():
+    reg = fg.registry_c3()
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    starts, sites = lpm.flatten()
+    rec = fg.make_records(reg, 2_000_000, seed=21, p_reg=0.9, zipf_s=0.9)
+    keys = remote_of(reg, rec)
+    return reg, lpm, starts, sites, rec, keys
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+
+
+def probe_set(starts, n_random=500_000, seed=0):
+    s = starts.astype(np.int64)
+    x = np.concatenate([s, s - 1, s + 1, [0, 0xFFFFFFFF], np.random.default_rng(seed).integers(0, 1 << 32, n_random)])
+    return x[(x >= 0) & (x < (1 << 32))].astype(np.uint32)
+
+
+def test_linear_gradient_matches_fp64(gnm):
+    ctx = gnm.Context()
+    rng = np.random.default_rng(4)
+    z = rng.normal(size=300_000).astype(np.float32)
+    y = (3 * z + 0.5 + rng.normal(size=z.size)).astype(np.float32)
+    for w, c in [(0.0, 0.0), (2.5, -1.0), (3.0, 0.5)]:
+        g = ctx.rmi_linear_grad(torch.from_numpy(z).cuda(), torch.from_numpy(y).cuda(), w, c)
+        loss, gw, gc = rmi_ref.linear_grad(np.float32(w), np.float32(c), z, y)
+        scale = max(abs(gw), abs(gc), 1e-3)
+        assert abs(g[0] - gw) <= 1e-4 * scale and abs(g[1] - gc) <= 1e-4 * scale
+        assert g[2] == pytest.approx(loss, rel=1e-4)
+    ctx.close()
+
+
+@pytest.mark.parametrize("H", [8, 32])
+def test_mlp_gradient_matches_fp64(gnm, H):
+    ctx = gnm.Context()
+    rng = np.random.default_rng(5 + H)
+    p = {"w1": rng.normal(size=H), "b1": rng.normal(size=H) * 0.3, "w2": rng.normal(size=H), "b2": 0.1}
+    flat = np.concatenate([p["w1"], p["b1"], p["w2"], [p["b2"]]]).astype(np.float32)
+    p32 = {"w1": flat[:H].astype(np.float64), "b1": flat[H:2 * H].astype(np.float64),
+           "w2": flat[2 * H:3 * H].astype(np.float64), "b2": float(flat[3 * H])}
+    xn = rng.random(200_000).astype(np.float32)
+    y = np.sqrt(xn).astype(np.float32)
+    g = ctx.rmi_mlp_grad(torch.from_numpy(xn).cuda(), torch.from_numpy(y).cuda(), H, flat)
+    loss, ref = rmi_ref.mlp_loss_grad(p32, xn.astype(np.float64), y.astype(np.float64))
+    want = np.concatenate([ref["w1"], ref["b1"], ref["w2"], [ref["b2"]]])
+    scale = np.max(np.abs(want))
+    np.testing.assert_allclose(g[:3 * H + 1], want, rtol=1e-4, atol=1e-4 * scale)
+    assert g[3 * H + 1] == pytest.approx(loss, rel=1e-4)
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def trained_linear(gnm, c3):
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx = gnm.Context(window_slots=4)
+    ctx.load(reg)
+    rep = ctx.rmi_train(to_dev(keys), root_kind=gnm.ROOT_LINEAR, n_leaves=4096, leaf_iters=4)
+    return ctx, rep
+
+
+def test_linear_rmi_bounds_equal_endpoint_analysis(gnm, c3, trained_linear):
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx, rep = trained_linear
+    m = ctx.rmi_export()
+    assert m["root_kind"] == gnm.ROOT_LINEAR and m["n_leaves"] == 4096
+    elo, ehi = rmi_ref.eps_endpoints_linear(starts, float(m["root"][0]), float(m["root"][1]), m["a"], m["b"],
+                                            m["x0"], 4096)
+    np.testing.assert_array_equal(m["eps_lo"], elo)
+    np.testing.assert_array_equal(m["eps_hi"], ehi)
+    assert rep.eps_max == int(np.max(elo + ehi))
+    print(f"\nlinear RMI: ranges {starts.size}, eps_max {rep.eps_max}, mean window {rep.eps_mean:.1f}, "
+          f"train {rep.train_ms:.1f} ms, sweep {rep.sweep_ms:.1f} ms, empty leaves {rep.empty_leaves}")
+
+
+def test_linear_rmi_leaves_are_least_squares(gnm, c3, trained_linear):
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx, _ = trained_linear
+    m = ctx.rmi_export()
+    pos = np.searchsorted(starts, keys, side="right") - 1
+    leaf = rmi_ref.root_linear(float(m["root"][0]), float(m["root"][1]), keys, 4096)
+    checked = 0
+    for l in np.unique(leaf)[:: max(1, len(np.unique(leaf)) // 40)]:
+        sel = leaf == l
+        if sel.sum() < 50:
+            continue
+        d = (keys[sel].astype(np.int64) - int(m["x0"][l])).astype(np.float32).astype(np.float64)
+        y = pos[sel].astype(np.float64)
+        if np.ptp(d) == 0:
+            continue
+        a, b = rmi_ref.lstsq_line(d, y)
+        a = max(a, 0.0)
+        got = float(m["a"][l]) * d + float(m["b"][l])
+        ls = a * d + b
+        assert np.max(np.abs(got - ls)) <= 1e-3 * max(1.0, np.ptp(y)) + 0.05, f"leaf {l}"
+        checked += 1
+    assert checked >= 20
+
+
+def test_linear_rmi_lookups_exact_without_fallback(gnm, c3, trained_linear):
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx, _ = trained_linear
+    ctx.rmi_violations(reset=True)
+    x = probe_set(starts)
+    dx = to_dev(x)
+    site = torch.empty_like(dx)
+    pos = torch.empty_like(dx)
+    ctx.lookup(dx, site, pos)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(pos.cpu().numpy().view(np.uint32), np.searchsorted(starts, x, side="right") - 1)
+    np.testing.assert_array_equal(site.cpu().numpy().view(np.uint32), lpm.lookup(x))
+    assert ctx.rmi_violations() == 0  # exhaustive bounds hold for every address
+
+
+def test_rmi_window_equals_bsearch_and_oracle(gnm, c3, trained_linear):
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx, _ = trained_linear
+    d = gnm.Records.to_device(rec)
+    ctx.process(d, 1)  # AUTO lookup: learned index
+    expect = oracle_full(reg, rec, lpm=lpm)
+    assert_window_matches(ctx.dense(1), expect)
+    plain = gnm.Context(window_slots=2, lookup_mode=gnm.LOOKUP_BSEARCH)
+    plain.load(reg)
+    plain.process(d, 1)
+    assert_window_matches(plain.dense(1), expect)
+    plain.close()
+
+
+def test_rmi_gain_over_binary_search(gnm, c3, trained_linear):
+    """Same GPU, same addresses: the model's window needs fewer dependent probes than
+    the full search, and the lookup kernel is faster."""
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx, rep = trained_linear
+    plain = gnm.Context(lookup_mode=gnm.LOOKUP_BSEARCH)
+    plain.load(reg)
+    n = 20_000_000
+    x = np.resize(keys, n)
+    dx = to_dev(x)
+    s1 = torch.empty_like(dx)
+    s2 = torch.empty_like(dx)
+
+    def t(c, out):
+        for _ in range(2):
+            c.lookup(dx, out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(5):
+            c.lookup(dx, out)
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 5
+
+    tb, tr = t(plain, s1), t(ctx, s2)
+    assert torch.equal(s1, s2)
+    probes_plain = np.ceil(np.log2(starts.size))
+    probes_rmi = np.log2(rep.eps_mean + 1) + 1
+    print(f"\nlookups of {n:,} addresses: bsearch {tb:.3f} ms, learned index {tr:.3f} ms "
+          f"({tb / tr:.2f}x); probes {probes_plain:.0f} vs ~{probes_rmi:.1f}")
+    assert probes_rmi < probes_plain / 2
+    assert tr < tb
+    plain.close()
+
+
+def test_rmi_sample_bounds_fall_back_exactly(gnm, c3):
+    """Bounds from a small training sample only: lookups outside it may miss the model
+    window; the fallback keeps every result exact and counts the misses."""
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx = gnm.Context(window_slots=2)
+    ctx.load(reg)
+    ctx.rmi_train(to_dev(keys[:20000]), n_leaves=4096, exhaustive_eps=0)
+    ctx.rmi_violations(reset=True)
+    x = probe_set(starts, seed=1)
+    dx = to_dev(x)
+    site = torch.empty_like(dx)
+    ctx.lookup(dx, site)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(site.cpu().numpy().view(np.uint32), lpm.lookup(x))
+    assert ctx.rmi_violations() > 0
+    ctx.close()
+
+
+def test_mlp_root_rmi_exact(gnm, c3):
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx = gnm.Context(window_slots=2)
+    ctx.load(reg)
+    rep = ctx.rmi_train(to_dev(keys), root_kind=gnm.ROOT_MLP, hidden=32, mlp_steps=300, n_leaves=4096)
+    assert np.isfinite(rep.root_loss) and rep.root_loss < (4096 ** 2) / 12  # beats a constant root
+    ctx.rmi_violations(reset=True)
+    x = probe_set(starts, n_random=200_000, seed=2)
+    dx = to_dev(x)
+    site = torch.empty_like(dx)
+    ctx.lookup(dx, site)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(site.cpu().numpy().view(np.uint32), lpm.lookup(x))
+    assert ctx.rmi_violations() == 0
+    print(f"\nMLP-root RMI: root mse {rep.root_loss:.2f} (leaf units), eps_max {rep.eps_max}, "
+          f"mean window {rep.eps_mean:.1f}, train {rep.train_ms:.1f} ms, sweep {rep.sweep_ms:.1f} ms")
+    ctx.close()
+
+
+def test_rmi_export_import_roundtrip(gnm, c3, trained_linear):
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx, _ = trained_linear
+    m = ctx.rmi_export()
+    other = gnm.Context()
+    other.load(reg)
+    other.rmi_import(m["root_kind"], m["root"], m["a"], m["b"], m["x0"])
+    m2 = other.rmi_export()
+    for k in ("a", "b", "x0", "eps_lo", "eps_hi"):
+        np.testing.assert_array_equal(m[k], m2[k])
+    other.close()

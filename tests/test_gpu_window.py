@@ -70,7 +70,7 @@ def test_hand_window(gnm):
 
 @pytest.mark.parametrize("table", ["DIRECT", "HASH", "GLOBAL"])
 @pytest.mark.parametrize("agg", ["DIRECT", "WARP"])
-@pytest.mark.parametrize("place", ["SMEM", "L2"])
+@pytest.mark.parametrize("place", ["SMEM", "STAGED", "L2"])
 @pytest.mark.parametrize("unroll,block", [(1, 256), (2, 512), (1, 1024)])
 def test_c1_window_all_variants(gnm, c1, table, agg, place, unroll, block):
     reg, rec, expect = c1
@@ -136,22 +136,39 @@ def test_c1_ragged_and_unaligned(gnm, c1):
     ctx.close()
 
 
-def test_c2_hour_batched_bitexact(gnm):
-    """Sixty one-minute windows (10M records, nested registry) in one launch; every
-    window equals the oracle. Window 30 straddles the 32-bit millisecond wrap."""
+@pytest.fixture(scope="module")
+def c2hour():
     reg = fg.registry_c2()
-    rec, off = fg.hour_records_c2(reg)
-    ctx = _ctx(gnm, reg)
-    info = ctx.registry_info()
-    assert info.placement == gnm.PLACE_L2
+    rec, off = fg.hour_records_c2(reg, seed=1)
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    expect = [oracle_full(reg, {k: v[off[w]:off[w + 1]] for k, v in rec.items()}, lpm=lpm) for w in range(60)]
+    return reg, rec, off, expect
+
+
+@pytest.mark.parametrize("cfg", [{}, {"placement": "L2"}, {"aggregation": "WARP"}, {"hash_slots": 1024},
+                                 {"table_mode": "GLOBAL"}])
+def test_c2_hour_batched_bitexact(gnm, c2hour, cfg):
+    """Sixty one-minute windows (10M records, nested registry) in one launch -- the
+    benchmark's workload and, with cfg {}, its launch configuration; every window equals
+    the oracle. Window 30 straddles the 32-bit millisecond wrap."""
+    reg, rec, off, expect = c2hour
+    kw = {}
+    for k, v in cfg.items():
+        kw[k] = getattr(gnm, {"placement": "PLACE_", "aggregation": "AGG_", "table_mode": "TABLE_"}[k] + v) \
+            if isinstance(v, str) else v
+    if "hash_slots" in kw:
+        kw["table_mode"] = gnm.TABLE_HASH
+    ctx = _ctx(gnm, reg, window_slots=64, **kw)
+    if not cfg:
+        assert ctx.registry_info().placement == gnm.PLACE_STAGED
     d = gnm.Records.to_device(rec)
     ids = np.arange(60) + 5000
-    ctx.process_windows(d, off, ids)
+    plan = ctx.plan(d, off, ids)  # the benchmark's path: a CUDA graph of one launch
+    plan.launch()
     assert ctx.last_launch_count() == 1
-    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
     for w in range(60):
-        host = {k: v[off[w]:off[w + 1]] for k, v in rec.items()}
-        assert_window_matches(ctx.dense(int(ids[w])), oracle_full(reg, host, lpm=lpm))
+        assert_window_matches(ctx.dense(int(ids[w])), expect[w])
+    plan.close()
     ctx.close()
 
 
@@ -200,10 +217,10 @@ def test_slot_eviction_and_release(gnm, c1):
     ctx.close()
 
 
-@pytest.mark.parametrize("which", ["c1", "c2"])
-def test_lookup_matches_oracle(gnm, which):
+@pytest.mark.parametrize("which,place", [("c1", "SMEM"), ("c1", "STAGED"), ("c2", "STAGED"), ("c2", "L2")])
+def test_lookup_matches_oracle(gnm, which, place):
     reg = fg.registry_c1() if which == "c1" else fg.registry_c2()
-    ctx = _ctx(gnm, reg)
+    ctx = _ctx(gnm, reg, placement=getattr(gnm, "PLACE_" + place))
     lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
     st, _ = lpm.flatten()
     s64 = st.astype(np.int64)
