@@ -332,6 +332,35 @@ gnm_status gnm_autotune(gnm_ctx *ctx, const gnm_records *rec, const uint64_t *of
 /* Number of kernels the last processing call enqueued (for launch accounting). */
 uint32_t gnm_last_launch_count(const gnm_ctx *ctx);
 
+/* ------------------------------------------------------------ without allocation */
+
+/* Largest n_sites gnm_window_process_noalloc accepts (its fixed scratch is 1 MiB). */
+#define GNM_NOALLOC_MAX_SITES 13102u
+
+/* One window, as gnm_window_process computes it, for callers that cannot call cudaMalloc:
+ * a process whose device memory is held up front by another allocator (a framework's
+ * caching allocator, a fixed budget), or a latency-critical loop that cannot afford
+ * cudaMalloc's implicit device synchronisation. The paper has no counterpart to this call.
+ * It needs no context and allocates nothing: the caller owns every input and output, and
+ * the kernel's scratch (window descriptor, finalise ticket, per-key partial sums) is one
+ * fixed 1 MiB array in the library's device image, which every GPU that loads the library
+ * keeps until the process exits -- hence n_sites <= GNM_NOALLOC_MAX_SITES (GNM_E_INVAL with
+ * a message beyond it). The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make the first call on each device before any stream capture.
+ * All calls on a device share the one array and clear it before use: calls that overlap
+ * on the GPU (other streams, other host threads) race on it and must not be issued.
+ * Arguments: cfg (host; NULL = defaults; filters and threshold_bps apply), starts/site
+ * (device, n_ranges entries: the flattened registry, e.g. gnm_registry_flatten's output
+ * copied to the device), n_sites, the local prefixes (host), rec (device records,
+ * n < 2^32), and the device results stats[(2*n_sites+4) x GNM_NSTAT] (layout of
+ * gnm_window_device), rate[2*n_sites], flag[2*n_sites]. Work is queued on `stream`; the
+ * call does not synchronise the host. */
+gnm_status gnm_window_process_noalloc(const gnm_config *cfg, const uint32_t *starts,
+                                      const uint32_t *site, uint32_t n_ranges, uint32_t n_sites,
+                                      const uint32_t *local_prefix, const uint8_t *local_len,
+                                      size_t n_local, const gnm_records *rec, uint64_t *stats,
+                                      double *rate, uint8_t *flag, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

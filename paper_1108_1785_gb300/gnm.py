@@ -127,6 +127,8 @@ def lib():
             "gnm_plan_destroy": (None, [P]),
             "gnm_autotune": (st, [P, C.POINTER(RecordsC), P, P, S, C.POINTER(TuneReport)]),
             "gnm_last_launch_count": (U32, [P]),
+            "gnm_window_process_noalloc": (st, [C.POINTER(Config), P, P, U32, U32, P, P, S, C.POINTER(RecordsC),
+                                                P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name, None)
@@ -210,6 +212,24 @@ def registry_flatten(prefix, plen, site, n_sites: int) -> Tuple[np.ndarray, np.n
     _check(None, lib().gnm_registry_flatten(_ptr(p), _ptr(l), _ptr(s), p.size, n_sites, _ptr(a), _ptr(b),
                                             n.value, C.byref(n)))
     return a, b
+
+
+def window_process_noalloc(starts, site, n_sites: int, local_prefix, local_len, rec: "Records", stats, rate, flag,
+                           stream=None, **cfg):
+    """One window without any device allocation by the library (gnm_window_process_noalloc):
+    the caller provides the flattened registry (device starts/site), device records and
+    device result arrays stats[(2*n_sites+4)*6] (u64), rate[2*n_sites] (f64), flag[2*n_sites]."""
+    c = Config()
+    lib().gnm_config_default(C.byref(c))
+    for k, v in cfg.items():
+        if not hasattr(c, k):
+            raise TypeError(f"unknown config key {k}")
+        setattr(c, k, v)
+    lp = np.ascontiguousarray(local_prefix, np.uint32)
+    ll = np.ascontiguousarray(local_len, np.uint8)
+    _check(None, lib().gnm_window_process_noalloc(C.byref(c), _ptr(starts), _ptr(site), int(starts.numel()), n_sites,
+                                                  _ptr(lp), _ptr(ll), lp.size, C.byref(rec.c), _ptr(stats), _ptr(rate),
+                                                  _ptr(flag), _stream_ptr(stream)))
 
 
 class Context:
