@@ -207,9 +207,12 @@ def main():
     n_win = len(off) - 1
     ctx = gnm.Context(device=local, window_slots=2 * n_win + 8)
     ctx.load(reg)
-    info = ctx.registry_info()
     dev = gnm.Records.to_device(rec)
     ids = np.arange(n_win, dtype=np.uint64)
+    # the library's own autotuner picks block size, records per thread, aggregation and
+    # registry placement on this workload (outside the timed region)
+    tune = ctx.autotune(dev, off, ids)
+    info = ctx.registry_info()
     plan = ctx.plan(dev, off, ids)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -220,12 +223,14 @@ def main():
     with ClockSampler(local) as clk:
         barrier(world)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")  # profilers select the timed steps by this range
         for a, b in ev:
             a.record(stream)
             plan.launch(stream)
             b.record(stream)
             launches += ctx.last_launch_count()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         barrier(world)
     total_ms = ev[0][0].elapsed_time(ev[-1][1])
     kern_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
@@ -257,7 +262,11 @@ def main():
                    "parallelism": f"replicas x{world} (independent hours per GPU)",
                    "lookup": "bsearch, registry " + {gnm.PLACE_SMEM: "in smem", gnm.PLACE_STAGED: "staged (block samples in smem, 64-B blocks in L2)", gnm.PLACE_L2: "in L2"}[info.placement],
                    "l2": "inputs 240 MB per GPU > 129 MB L2; no flush between steps",
-                   "launch": "CUDA graph: one persistent aggregation kernel per step (finalise fused)"},
+                   "launch": "CUDA graph: one persistent aggregation kernel per step (finalise fused)",
+                   "tuned": {"block_threads": tune.block_threads, "ctas_per_sm": tune.ctas_per_sm,
+                             "unroll": tune.unroll, "aggregation": tune.aggregation, "placement": tune.placement,
+                             "default_ms": round(tune.default_ms, 4), "tuned_ms": round(tune.best_ms, 4),
+                             "candidates": tune.n_tried}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                      "kernel": "k_aggregate", "kernel_ms": kern_ms, "algorithmic_bytes": alg_bytes},

@@ -55,10 +55,16 @@ typedef enum {
     GNM_E_INTERNAL = 7  /* a device-side consistency check failed */
 } gnm_status;
 
-enum { GNM_LOOKUP_AUTO = 0, GNM_LOOKUP_BSEARCH = 1, GNM_LOOKUP_RMI = 2 };
+/* Prefix-match methods. BSEARCH: binary search over all range starts (placement below).
+ * RMI: the learned index (gnm_rmi_train). RADIX: a directory indexed by the top
+ * `radix_bits` address bits -- the paper's direct-indexed site catalog (Sec. III.B.2.1
+ * hashes /24 subnets) generalised to any prefix length -- gives each bucket's range
+ * interval, and a binary search inside the bucket finishes. AUTO: RMI when trained, else
+ * RADIX. */
+enum { GNM_LOOKUP_AUTO = 0, GNM_LOOKUP_BSEARCH = 1, GNM_LOOKUP_RMI = 2, GNM_LOOKUP_RADIX = 3 };
 /* Where the flattened registry is searched: wholly in shared memory (SMEM), wholly in L2
- * (L2), or STAGED: the first start of every block of 8 ranges in shared memory and the
- * 64-byte blocks (8 starts, 8 sites) in L2, one L2 access per lookup. */
+ * (L2), or STAGED: the first start of every block of 16 ranges in shared memory, the
+ * 64-byte blocks of 16 starts and the sites in L2 (two L2 accesses per lookup). */
 enum { GNM_PLACE_AUTO = 0, GNM_PLACE_SMEM = 1, GNM_PLACE_L2 = 2, GNM_PLACE_STAGED = 3 };
 enum { GNM_AGG_AUTO = 0, GNM_AGG_DIRECT = 1, GNM_AGG_WARP = 2 };
 enum { GNM_ADMIN_OR = 0, GNM_ADMIN_AND = 1 };
@@ -89,9 +95,10 @@ typedef struct {
     int32_t unroll;             /* 0: tuned default; else 1 or 2 (4-record groups per
                                    thread per iteration) */
     int32_t table_mode;         /* GNM_TABLE_*: where a CTA accumulates its sums */
-    uint32_t hash_slots;        /* GNM_TABLE_HASH size: 0 = largest that fits, else a
-                                   power of two in 256..32768 */
-    uint32_t reserved;
+    uint32_t hash_slots;        /* GNM_TABLE_HASH size: 0 = largest that fits, else an
+                                   even number in 256..65536 */
+    uint32_t radix_bits;        /* GNM_LOOKUP_RADIX directory bits: 0 = sized from the
+                                   registry, else 4..16 */
 } gnm_config;
 
 /* One struct-of-arrays batch of NetFlow v5 fields (Sec. IV.A.3: 48-byte v5 records; only
@@ -122,7 +129,7 @@ typedef struct {
     uint64_t n_registered;  /* ranges that carry a site */
     uint32_t n_sites;
     uint32_t n_prefixes;
-    int32_t placement;      /* resolved GNM_PLACE_* */
+    int32_t placement;      /* resolved GNM_PLACE_* (binary search) */
     int32_t lookup_mode;    /* resolved GNM_LOOKUP_* */
     int32_t privatized;     /* per-CTA shared-memory sums in use */
     int32_t rmi_ready;
@@ -321,6 +328,7 @@ typedef struct {
     int32_t block_threads, ctas_per_sm, unroll, aggregation, placement;
     double best_ms, default_ms;
     uint32_t n_tried;
+    uint32_t radix_bits;
 } gnm_tune_report;
 
 /* Times candidate launch shapes (block size, CTAs per SM, records per thread,

@@ -24,13 +24,18 @@ __device__ __forceinline__ uint4 ld_stream4(const uint32_t* p) {
 }
 __device__ __forceinline__ uint32_t ld_stream1(const uint32_t* p) { return __ldcs(p); }
 
-// Local-site membership: any of the (at most GNM_MAX_LOCAL) local prefixes contains a.
-__device__ __forceinline__ bool is_local(const AggParams& p, uint32_t a) {
-    bool r = false;
+// Local-site membership of both endpoints: any of the (at most GNM_MAX_LOCAL) local
+// prefixes contains the address. The loop stops at n_local (uniform across the grid).
+__device__ __forceinline__ void local_pair(const AggParams& p, uint32_t src, uint32_t dst, bool& sl, bool& dl) {
+    sl = false;
+    dl = false;
 #pragma unroll
-    for (int i = 0; i < GNM_MAX_LOCAL; ++i)
-        if (i < (int)p.n_local) r |= ((a & p.local_mask[i]) == p.local_pfx[i]);
-    return r;
+    for (int i = 0; i < GNM_MAX_LOCAL; ++i) {
+        if (i >= (int)p.n_local) break;
+        const uint32_t m = p.local_mask[i], q = p.local_pfx[i];
+        sl |= (src & m) == q;
+        dl |= (dst & m) == q;
+    }
 }
 
 // Predecessor search over sorted range starts (s[0] = 0): largest i with s[i] <= x.
@@ -61,6 +66,37 @@ __device__ __forceinline__ uint32_t pred_search1(const uint32_t* __restrict__ s,
         len -= half;
     }
     return base;
+}
+
+// Radix-directed search: dir[t] is the range holding the first address of bucket t (the
+// top `bits` bits of an address), so x's range lies in [dir[t], dir[t+1]]; a binary search
+// over the starts inside that interval finishes (R lookups in lock step, each stopping
+// when its interval has one entry).
+template <int R>
+__device__ __forceinline__ void radix_search(const uint32_t* __restrict__ dir, uint32_t bits,
+                                             const uint32_t* __restrict__ starts, const uint32_t (&x)[R],
+                                             uint32_t (&base)[R]) {
+    uint32_t len[R];
+    bool more = false;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const uint32_t t = bits ? x[j] >> (32u - bits) : 0u;
+        base[j] = dir[t];
+        len[j] = dir[t + 1] - base[j] + 1u;
+        more |= len[j] > 1u;
+    }
+    while (more) {
+        more = false;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (len[j] > 1u) {
+                const uint32_t half = len[j] >> 1;
+                base[j] = (__ldg(starts + base[j] + half) <= x[j]) ? base[j] + half : base[j];
+                len[j] -= half;
+                more |= len[j] > 1u;
+            }
+        }
+    }
 }
 
 // floor(v) clamped to [0, n-1] (n - 1 < 2^24, so the comparison is exact); NaN -> 0.
@@ -118,24 +154,18 @@ __device__ __forceinline__ uint32_t rmi_lookup(const RmiDev& m, const float* a, 
     return pred_search1(starts, 0, n, x);
 }
 
-// Staged placement, last level: the 64-byte block of 8 ranges holding x (8 starts, then
-// their 8 sites; padding past the last range repeats 0xFFFFFFFF as start and the last site,
-// so it only ever matches x = 0xFFFFFFFF, which belongs to the last range anyway).
-__device__ __forceinline__ uint32_t staged_block_site(const uint4* b, uint32_t x) {
-    const uint4 s0 = __ldg(b), s1 = __ldg(b + 1), w0 = __ldg(b + 2), w1 = __ldg(b + 3);
-    const uint32_t c = (s0.y <= x) + (s0.z <= x) + (s0.w <= x) + (s1.x <= x) + (s1.y <= x) +
-                       (s1.z <= x) + (s1.w <= x);  // s0.x <= x holds: it is the block's sample
-    const uint4 w = c < 4 ? w0 : w1;
-    const uint32_t q = c & 3u;
-    return q == 0 ? w.x : (q == 1 ? w.y : (q == 2 ? w.z : w.w));
+// Staged placement, last level: position of x inside the 64-byte block jb of 16 range
+// starts (the block's first start is its shared-memory sample, <= x). Padding past the
+// last range is 0xFFFFFFFF, which only x = 0xFFFFFFFF passes; the clamp to n-1 maps that
+// to the last range, which holds it anyway.
+__device__ __forceinline__ uint32_t block_count(uint4 v, uint32_t x) {
+    return (v.x <= x) + (v.y <= x) + (v.z <= x) + (v.w <= x);
 }
 
-// Range index form of the same lookup (largest i with start_i <= x), clamped to n-1.
 __device__ __forceinline__ uint32_t staged_block_pos(const uint4* b, uint32_t jb, uint32_t x, uint32_t n) {
-    const uint4 s0 = __ldg(b), s1 = __ldg(b + 1);
-    const uint32_t c = (s0.y <= x) + (s0.z <= x) + (s0.w <= x) + (s1.x <= x) + (s1.y <= x) +
-                       (s1.z <= x) + (s1.w <= x);
-    return min(jb * kBlockRanges + c, n - 1);
+    const uint4 s0 = __ldg(b), s1 = __ldg(b + 1), s2 = __ldg(b + 2), s3 = __ldg(b + 3);
+    const uint32_t c = block_count(s0, x) + block_count(s1, x) + block_count(s2, x) + block_count(s3, x);
+    return min(jb * kBlockRanges + c - 1u, n - 1u);
 }
 
 // One classified record.
@@ -145,30 +175,23 @@ struct Item {
     bool elig, valid;
 };
 
-__device__ __forceinline__ Item classify(const AggParams& p, bool valid, uint32_t src,
-                                         uint32_t dst, uint32_t pk, uint32_t oc, uint32_t fi,
-                                         uint32_t la, uint32_t site) {
+__device__ __forceinline__ Item classify(const AggParams& p, bool valid, bool sl, bool dl, uint32_t pk,
+                                         uint32_t oc, uint32_t fi, uint32_t la, uint32_t site) {
     Item it;
-    const bool sl = is_local(p, src), dl = is_local(p, dst);
     const uint32_t nk = 2u * p.n_sites;
     const uint32_t dir = sl ? 1u : 0u;  // outbound when the source is local
     const uint32_t dur = la - fi;       // modulo 2^32
-    bool elig = false;
-    if (sl == dl) {
-        it.key = nk + (sl ? 1u : 0u);   // 0 neither local, 1 both local
-    } else if (site == kNoSite) {
-        it.key = nk + 2u + dir;         // 2 inbound unregistered, 3 outbound unregistered
-    } else {
-        it.key = site * 2u + dir;
-        const bool ack_ok = (uint64_t)oc >= (uint64_t)p.min_avg * (uint64_t)pk;
-        const bool many = pk >= p.min_pkts, longd = dur >= p.min_dur;
-        const bool admin_ok = p.admin_rule == GNM_ADMIN_OR ? (many && longd) : (many || longd);
-        elig = dur != 0u && ack_ok && admin_ok;
-    }
+    const bool mixed = sl != dl;        // exactly one endpoint local
+    const bool reg = site != kNoSite;
+    // unmatched classes: 0 neither local, 1 both local, 2 inbound unregistered, 3 outbound
+    it.key = mixed ? (reg ? site * 2u + dir : nk + 2u + dir) : nk + dir;
+    const bool ack_ok = (uint64_t)oc >= (uint64_t)p.min_avg * (uint64_t)pk;
+    const bool many = pk >= p.min_pkts, longd = dur >= p.min_dur;
+    const bool admin_ok = p.admin_rule == GNM_ADMIN_OR ? (many && longd) : (many || longd);
+    it.elig = mixed && reg && dur != 0u && ack_ok && admin_ok;
     it.oc = oc;
     it.pk = pk;
     it.dur = dur;
-    it.elig = elig;
     it.valid = valid;
     return it;
 }
@@ -177,17 +200,8 @@ __device__ __forceinline__ void red_add(uint64_t* a, uint64_t v) {
     atomicAdd(reinterpret_cast<unsigned long long*>(a), (unsigned long long)v);
 }
 
-// Adds one record's contribution to a packed 5-column row (shared or global).
-__device__ __forceinline__ void row_add(uint64_t* row, const Item& it) {
-    red_add(row + 0, it.elig ? 0x100000001ull : 0x100000000ull);
-    red_add(row + 1, it.oc);
-    red_add(row + 2, it.pk);
-    if (it.elig) {
-        red_add(row + 3, it.oc);
-        red_add(row + 4, it.dur);
-    }
-}
-
+// Adds summed contributions to a key's global accumulator row (5 u64 columns; column 0
+// packs flows << 32 | e_flows, which cannot carry: a window holds < 2^32 records).
 __device__ __forceinline__ void row_add_sums(uint64_t* row, uint64_t packed, uint64_t oc,
                                              uint64_t pk, uint64_t eoc, uint64_t edur, bool any_e) {
     red_add(row + 0, packed);
@@ -196,6 +210,70 @@ __device__ __forceinline__ void row_add_sums(uint64_t* row, uint64_t packed, uin
     if (any_e) {
         red_add(row + 3, eoc);
         red_add(row + 4, edur);
+    }
+}
+
+// Per-CTA sums in shared memory use 32-bit atomics (64-bit shared atomics serialise the
+// lanes of a warp). A row is 5 words, stride 5 (odd, so random rows spread over the 32
+// banks):
+//   [0] flows (bits 0-15) | e_flows (bits 16-31)   [1] octets  [2] pkts  [3] e_octets
+//   [4] e_dur
+// The counts cannot wrap because a CTA flushes at least every kFlushRecords records. The
+// sums keep their low 32 bits; the lane whose add wraps a word adds 2^32 to the key's
+// global accumulator column directly (rare: a word wraps once per ~4 GB of octets), so
+// every total stays exact.
+constexpr int kRowWords = 5;
+constexpr uint32_t kFlushRecords = 65532;  // < 2^16, multiple of 4
+static_assert(kRowWords * 4 == kSmemRowBytes, "host and device disagree on the shared row size");
+
+__device__ __forceinline__ void red32(uint32_t* a, uint32_t v) { atomicAdd(a, v); }
+
+// lo += v (mod 2^32); a wrap adds 2^32 to the global column g.
+__device__ __forceinline__ void add_wrap(uint32_t* lo, uint64_t* g, uint32_t v) {
+    const uint32_t old = atomicAdd(lo, v);
+    if (old > ~v) red_add(g, 1ull << 32);  // old + v >= 2^32
+}
+
+__device__ __forceinline__ void add_wrap64(uint32_t* lo, uint64_t* g, uint64_t v) {
+    const uint32_t vl = (uint32_t)v;
+    const uint32_t old = atomicAdd(lo, vl);
+    const uint64_t h = (v >> 32) + (old > ~vl ? 1ull : 0ull);
+    if (h) red_add(g, h << 32);
+}
+
+struct Smem {
+    uint32_t* t;        // table rows (kRowWords words each)
+    uint32_t* tk;       // hash keys
+    uint32_t rows;      // table rows
+    const uint32_t* s_starts;
+    const uint32_t* s_site;
+    const float* ra;    // learned index leaf arrays
+    const float* rb;
+    const uint32_t* rx0;
+    const uint32_t* reps;
+};
+
+// One record's contribution to shared-memory row r (gk: the key's global row).
+__device__ __forceinline__ void srow_add(const Smem& sm, int r, const Item& it, uint64_t* gk) {
+    uint32_t* w = sm.t + r * kRowWords;
+    red32(w, it.elig ? 0x10001u : 1u);
+    add_wrap(w + 1, gk + 1, it.oc);
+    add_wrap(w + 2, gk + 2, it.pk);
+    if (it.elig) {
+        add_wrap(w + 3, gk + 3, it.oc);
+        add_wrap(w + 4, gk + 4, it.dur);
+    }
+}
+
+__device__ __forceinline__ void srow_add_sums(const Smem& sm, int r, uint32_t n, uint32_t ne, uint64_t oc,
+                                              uint64_t pk, uint64_t eoc, uint64_t edur, uint64_t* gk) {
+    uint32_t* w = sm.t + r * kRowWords;
+    red32(w, n | (ne << 16));
+    add_wrap64(w + 1, gk + 1, oc);
+    add_wrap64(w + 2, gk + 2, pk);
+    if (ne) {
+        add_wrap64(w + 3, gk + 3, eoc);
+        add_wrap64(w + 4, gk + 4, edur);
     }
 }
 
@@ -211,7 +289,8 @@ __device__ __forceinline__ uint64_t peer_sum(unsigned peers, uint32_t v) {
 // memory). Keys seen early in a CTA's range -- the frequent ones -- keep their slots.
 __device__ __forceinline__ int table_slot(uint32_t* tk, uint32_t cap, uint32_t key) {
     uint32_t h = (key * 2654435761u);
-    h = (h ^ (h >> 15)) & (cap - 2u);  // even slot of the pair
+    h ^= h >> 15;
+    h = __umulhi(h * 0x85EBCA6Bu, cap >> 1) << 1;  // even slot of a pair, any even cap
     volatile uint32_t* vk = tk;
     uint32_t k0 = vk[h];
     if (k0 == key) return (int)h;
@@ -228,18 +307,17 @@ __device__ __forceinline__ int table_slot(uint32_t* tk, uint32_t cap, uint32_t k
     return -1;
 }
 
+// Shared-memory row of `key` (-1: none).
 template <int TABLE>
-__device__ __forceinline__ uint64_t* smem_row(uint64_t* tv, uint32_t* tk, uint32_t cap,
-                                              uint32_t key) {
-    if (TABLE == kTableDirect) return tv + (size_t)key * kAccCols;
-    const int s = table_slot(tk, cap, key);
-    return s >= 0 ? tv + (size_t)s * kAccCols : nullptr;
+__device__ __forceinline__ int smem_row(const Smem& sm, uint32_t cap, uint32_t key) {
+    if (TABLE == kTableDirect) return (int)key;
+    return table_slot(sm.tk, cap, key);
 }
 
-// Sums of one item per lane over the lanes that share its key, added by the group
-// leader to `row` (or, when row is null, to the key's global accumulator row).
-// Warp-collective over the lanes with `part` set.
-__device__ __forceinline__ void group_add(const Item& it, unsigned peers, uint64_t* row, uint64_t* gacc) {
+// Sums of one item per lane over the lanes of `peers` (all share its key), added by the
+// group leader to shared-memory row r, or, when r < 0, to the key's global row.
+__device__ __forceinline__ void group_add(const Item& it, unsigned peers, int r, const Smem& sm,
+                                          uint64_t* gacc) {
     const uint32_t e = it.elig ? 1u : 0u;
     const uint32_t n = __popc(peers);
     const uint32_t ne = __reduce_add_sync(peers, e);
@@ -251,8 +329,9 @@ __device__ __forceinline__ void group_add(const Item& it, unsigned peers, uint64
         edur = peer_sum(peers, it.elig ? it.dur : 0u);
     }
     if ((int)(threadIdx.x & 31u) != __ffs(peers) - 1) return;
-    if (row == nullptr) row = gacc + (size_t)it.key * kAccCols;
-    row_add_sums(row, ((uint64_t)n << 32) | ne, oc, pk, eoc, edur, ne != 0);
+    uint64_t* gk = gacc + (size_t)it.key * kAccCols;
+    if (r >= 0) srow_add_sums(sm, r, n, ne, oc, pk, eoc, edur, gk);
+    else row_add_sums(gk, ((uint64_t)n << 32) | ne, oc, pk, eoc, edur, ne != 0);
 }
 
 // Accumulate one item per lane. Warp-collective: every lane of the warp calls it
@@ -261,48 +340,47 @@ __device__ __forceinline__ void group_add(const Item& it, unsigned peers, uint64
 //   has no row (cache full) are combined per key across the warp and added globally.
 //   WARP aggregation: lanes are first combined per key; the group leader adds.
 template <int TABLE, int AGG>
-__device__ __forceinline__ void accumulate(const Item& it, uint64_t* tv, uint32_t* tk,
-                                           uint32_t cap, uint64_t* gacc) {
+__device__ __forceinline__ void accumulate(const Item& it, const Smem& sm, uint32_t cap, uint64_t* gacc) {
     if (TABLE != kTableGlobal && AGG == GNM_AGG_DIRECT) {
-        uint64_t* row = it.valid ? smem_row<TABLE>(tv, tk, cap, it.key) : nullptr;
-        const bool miss = it.valid && row == nullptr;
+        const int r = it.valid ? smem_row<TABLE>(sm, cap, it.key) : -1;
+        const bool miss = it.valid && r < 0;
         if (TABLE == kTableHash && __any_sync(kFull, miss)) {
             const unsigned peers = __match_any_sync(kFull, miss ? it.key : kEmptyKey);
-            if (miss) group_add(it, peers, nullptr, gacc);
+            if (miss) group_add(it, peers, -1, sm, gacc);
         }
-        if (row) row_add(row, it);
+        if (r >= 0) srow_add(sm, r, it, gacc + (size_t)it.key * kAccCols);
         return;
     }
     const unsigned peers = __match_any_sync(kFull, it.valid ? it.key : kEmptyKey);
     if (!it.valid) return;
-    uint64_t* row = nullptr;
-    if (TABLE != kTableGlobal) {
-        // the leader probes for the whole group
+    int r = -1;
+    if (TABLE != kTableGlobal) {  // the leader probes for the whole group
         const int leader = __ffs(peers) - 1;
-        uint64_t* r = nullptr;
-        if ((int)(threadIdx.x & 31u) == leader) r = smem_row<TABLE>(tv, tk, cap, it.key);
-        row = (uint64_t*)__shfl_sync(peers, (unsigned long long)r, leader);
+        int q = -1;
+        if ((int)(threadIdx.x & 31u) == leader) q = smem_row<TABLE>(sm, cap, it.key);
+        r = __shfl_sync(peers, q, leader);
     }
-    group_add(it, peers, row, gacc);
+    group_add(it, peers, r, sm, gacc);
 }
 
 // Adds the CTA's shared-memory sums to the window's global accumulators and clears them.
 template <int TABLE>
-__device__ __forceinline__ void flush(uint64_t* tv, uint32_t* tk, uint32_t rows, uint64_t* gacc) {
-    for (uint32_t r = threadIdx.x; r < rows; r += blockDim.x) {
-        uint64_t* row = tv + (size_t)r * kAccCols;
-        const uint64_t packed = row[0];
+__device__ __forceinline__ void flush(const Smem& sm, uint64_t* gacc) {
+    for (uint32_t r = threadIdx.x; r < sm.rows; r += blockDim.x) {
+        uint32_t* w = sm.t + r * kRowWords;
         uint32_t key = r;
         if (TABLE == kTableHash) {
-            key = tk[r];
-            tk[r] = kEmptyKey;
+            key = sm.tk[r];
+            sm.tk[r] = kEmptyKey;
         }
-        if (packed == 0) continue;
-        uint64_t* g = gacc + (size_t)key * kAccCols;
-        const bool any_e = (packed & 0xFFFFFFFFull) != 0;
-        row_add_sums(g, packed, row[1], row[2], row[3], row[4], any_e);
+        const uint32_t cnt = w[0];
+        // a row can hold only wrap-carried sums (count 0 is impossible after an add)
+        if (cnt == 0 && (w[1] | w[2] | w[3] | w[4]) == 0) continue;
+        const uint32_t ef = cnt >> 16;
+        row_add_sums(gacc + (size_t)key * kAccCols, ((uint64_t)(cnt & 0xFFFFu) << 32) | ef, w[1], w[2], w[3], w[4],
+                     ef != 0 || (w[3] | w[4]) != 0);
 #pragma unroll
-        for (int c = 0; c < kAccCols; ++c) row[c] = 0;
+        for (int c = 0; c < kRowWords; ++c) w[c] = 0;
     }
 }
 
@@ -356,26 +434,15 @@ __device__ __forceinline__ uint32_t first_window(const WinDesc* w, uint32_t n, u
     return a;
 }
 
-struct Smem {
-    uint64_t* tv;       // table values
-    uint32_t* tk;       // hash keys
-    uint32_t rows;      // table rows
-    const uint32_t* s_starts;
-    const uint32_t* s_site;
-    const float* ra;    // learned index leaf arrays
-    const float* rb;
-    const uint32_t* rx0;
-    const uint32_t* reps;
-};
 
 __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Shared-memory layout: [table values][hash keys][registry or leaf arrays].
 __host__ __device__ inline size_t smem_layout(int lookup, int table, uint32_t n_ranges,
                                               uint32_t keys, uint32_t cap, uint32_t n_leaves,
-                                              size_t* off_keys, size_t* off_lookup) {
+                                              uint32_t radix_bits, size_t* off_keys, size_t* off_lookup) {
     const uint32_t rows = table == kTableDirect ? keys : (table == kTableHash ? cap : 0u);
-    size_t o = (size_t)rows * kAccCols * 8;
+    size_t o = (size_t)rows * kSmemRowBytes;
     *off_keys = o;
     if (table == kTableHash) o += (size_t)cap * 4;
     o = align_up(o, 16);
@@ -383,6 +450,7 @@ __host__ __device__ inline size_t smem_layout(int lookup, int table, uint32_t n_
     if (lookup == kLookupSmem) o += (size_t)n_ranges * 8;
     if (lookup == kLookupStaged) o += (size_t)((n_ranges + kBlockRanges - 1) / kBlockRanges) * 4;
     if (lookup == kLookupRmi) o += (size_t)n_leaves * 16;
+    if (lookup == kLookupRadix) o += ((size_t)1 << radix_bits) * 4 + 4;
     return align_up(o, 16);
 }
 
@@ -395,8 +463,12 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
                                         const uint32_t (&oc)[R], const uint32_t (&fi)[R],
                                         const uint32_t (&la)[R]) {
     uint32_t x[R], idx[R], site[R];
+    bool sl[R], dl[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) x[j] = is_local(p, src[j]) ? dst[j] : src[j];
+    for (int j = 0; j < R; ++j) {
+        local_pair(p, src[j], dst[j], sl[j], dl[j]);
+        x[j] = sl[j] ? dst[j] : src[j];  // the remote endpoint
+    }
     if (LOOKUP == kLookupSmem) {
         pred_search<R, true>(sm.s_starts, p.n_ranges, x, idx);
 #pragma unroll
@@ -405,10 +477,16 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
         pred_search<R, false>(p.starts, p.n_ranges, x, idx);
 #pragma unroll
         for (int j = 0; j < R; ++j) site[j] = __ldg(p.rsite + idx[j]);
+    } else if (LOOKUP == kLookupRadix) {
+        radix_search<R>(sm.s_starts, p.radix_bits, p.starts, x, idx);
+#pragma unroll
+        for (int j = 0; j < R; ++j) site[j] = __ldg(p.rsite + idx[j]);
     } else if (LOOKUP == kLookupStaged) {
         pred_search<R, true>(sm.s_starts, p.n_blocks, x, idx);  // block of x
 #pragma unroll
-        for (int j = 0; j < R; ++j) site[j] = staged_block_site(p.blocks + 4 * (size_t)idx[j], x[j]);
+        for (int j = 0; j < R; ++j) idx[j] = staged_block_pos(p.blocks + 4 * (size_t)idx[j], idx[j], x[j], p.n_ranges);
+#pragma unroll
+        for (int j = 0; j < R; ++j) site[j] = __ldg(p.rsite + idx[j]);
     } else {
 #pragma unroll
         for (int j = 0; j < R; ++j) {
@@ -421,8 +499,8 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
     }
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-        const Item it = classify(p, valid[j], src[j], dst[j], pk[j], oc[j], fi[j], la[j], site[j]);
-        accumulate<TABLE, AGG>(it, sm.tv, sm.tk, p.table_cap, gacc);
+        const Item it = classify(p, valid[j], sl[j], dl[j], pk[j], oc[j], fi[j], la[j], site[j]);
+        accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
     }
 }
 
@@ -493,13 +571,13 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512)
 
     size_t off_keys, off_lookup;
     smem_layout(LOOKUP, TABLE, p.n_ranges, p.keys, p.table_cap,
-                LOOKUP == kLookupRmi ? p.rmi.n_leaves : 0u, &off_keys, &off_lookup);
+                LOOKUP == kLookupRmi ? p.rmi.n_leaves : 0u, p.radix_bits, &off_keys, &off_lookup);
     Smem sm;
-    sm.tv = reinterpret_cast<uint64_t*>(smem_raw);
-    sm.tk = reinterpret_cast<uint32_t*>(smem_raw + off_keys);
     sm.rows = TABLE == kTableDirect ? p.keys : (TABLE == kTableHash ? p.table_cap : 0u);
+    sm.t = reinterpret_cast<uint32_t*>(smem_raw);
+    sm.tk = reinterpret_cast<uint32_t*>(smem_raw + off_keys);
     // stage the table (zero), the registry or the leaf parameters
-    for (uint32_t i = tid; i < sm.rows * kAccCols; i += B) sm.tv[i] = 0;
+    for (uint32_t i = tid; i < sm.rows * kRowWords; i += B) sm.t[i] = 0;
     if (TABLE == kTableHash)
         for (uint32_t i = tid; i < p.table_cap; i += B) sm.tk[i] = kEmptyKey;
     if (LOOKUP == kLookupSmem) {
@@ -516,6 +594,12 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512)
         uint32_t* st = reinterpret_cast<uint32_t*>(smem_raw + off_lookup);
         for (uint32_t i = tid; i < p.n_blocks; i += B) st[i] = __ldg(p.sample + i);
         sm.s_starts = st;
+    }
+    if (LOOKUP == kLookupRadix) {  // every 2^(16-bits)-th entry of the 16-bit directory
+        uint32_t* d = reinterpret_cast<uint32_t*>(smem_raw + off_lookup);
+        const uint32_t nd = 1u << p.radix_bits, sh = 16u - p.radix_bits;
+        for (uint32_t i = tid; i <= nd; i += B) d[i] = __ldg(p.dir16 + ((size_t)i << sh));
+        sm.s_starts = d;
     }
     if (LOOKUP == kLookupRmi) {
         const uint32_t L = p.rmi.n_leaves;
@@ -539,20 +623,25 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512)
     for (uint32_t w = first_window(p.wins, p.n_wins, lo); w < p.n_wins; ++w) {
         const WinDesc wd = p.wins[w];
         if (wd.begin >= hi) break;
-        const uint64_t s = max(wd.begin, lo), e = min(wd.end, hi);
+        const uint64_t s0 = max(wd.begin, lo), e0 = min(wd.end, hi);
         uint64_t* gacc = p.acc + (size_t)wd.slot * p.keys * kAccCols;
-        uint64_t a0 = e, a1 = e;
-        if (p.vec_ok) {
-            const uint32_t mis = (uint32_t)((s + p.phase) & 3u);
-            a0 = mis ? min(s + (4u - mis), e) : s;
-            a1 = a0 + ((e - a0) & ~3ull);
-        }
-        scalar_range<LOOKUP, TABLE, AGG>(p, sm, gacc, s, a0);
-        if (a1 > a0) vector_range<LOOKUP, TABLE, AGG, U>(p, sm, gacc, a0, (a1 - a0) >> 2);
-        scalar_range<LOOKUP, TABLE, AGG>(p, sm, gacc, a1, e);
-        if (TABLE != kTableGlobal) {
-            __syncthreads();
-            flush<TABLE>(sm.tv, sm.tk, sm.rows, gacc);
+        // pieces of at most kFlushRecords records, so the 16-bit counts cannot wrap
+        for (uint64_t s = s0; s < e0; s += kFlushRecords) {
+            const uint64_t e = min(e0, s + kFlushRecords);
+            uint64_t a0 = e, a1 = e;
+            if (p.vec_ok) {
+                const uint32_t mis = (uint32_t)((s + p.phase) & 3u);
+                a0 = mis ? min(s + (4u - mis), e) : s;
+                a1 = a0 + ((e - a0) & ~3ull);
+            }
+            scalar_range<LOOKUP, TABLE, AGG>(p, sm, gacc, s, a0);
+            if (a1 > a0) vector_range<LOOKUP, TABLE, AGG, U>(p, sm, gacc, a0, (a1 - a0) >> 2);
+            scalar_range<LOOKUP, TABLE, AGG>(p, sm, gacc, a1, e);
+            if (TABLE != kTableGlobal) {
+                __syncthreads();
+                flush<TABLE>(sm, gacc);
+                __syncthreads();
+            }
         }
         __threadfence();
         __syncthreads();
@@ -577,7 +666,7 @@ cudaError_t launch_variant(const AggParams& p, const LaunchShape& s, cudaStream_
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (s.smem > 48 * 1024 && (dev >= 64 || set_bytes[dev] < (int)s.smem)) {
+    if (s.smem >= 46 * 1024 && (dev >= 64 || set_bytes[dev] < (int)s.smem)) {
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
         if (e != cudaSuccess) return e;
         if (dev < 64) set_bytes[dev] = (int)s.smem;

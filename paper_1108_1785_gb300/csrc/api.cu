@@ -25,8 +25,8 @@ bool local_overlaps(uint32_t lp, uint8_t ll, const uint32_t* prefix, const uint8
 constexpr uint32_t kRingSize = 16;
 constexpr size_t kRegistrySmemMax = 96 * 1024;   // bytes of ranges kept in shared memory
 constexpr size_t kSampleSmemMax = 96 * 1024;     // bytes of block samples (staged placement)
-constexpr size_t kDirectTableMax = 120 * 1024;   // direct-indexed per-CTA sums
-constexpr size_t kHashTableMax = 176 * 1024;     // hashed per-CTA sums
+constexpr size_t kDirectTableMax = 208 * 1024;   // direct-indexed per-CTA sums
+constexpr size_t kHashTableMax = 200 * 1024;     // hashed per-CTA sums
 constexpr uint32_t kFinalizeInKernelMaxKeys = 65536;
 constexpr uint64_t kMaxWindowRecords = 0xFFFFFFFFull;
 
@@ -192,14 +192,33 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
     const gnm_config& cfg = c->cfg;
     const uint32_t nr = (uint32_t)c->h_starts.size();
     int mode = cfg.lookup_mode;
-    if (mode == GNM_LOOKUP_AUTO) mode = c->rmi_ready ? GNM_LOOKUP_RMI : GNM_LOOKUP_BSEARCH;
+    if (mode == GNM_LOOKUP_AUTO) mode = c->rmi_ready ? GNM_LOOKUP_RMI : GNM_LOOKUP_RADIX;
     if (mode == GNM_LOOKUP_RMI && !c->rmi_ready)
         return fail(GNM_E_STATE, "lookup mode RMI requested but no learned index is trained");
     size_t lookup_bytes = 0;
+    s->radix_bits = 0;
     if (mode == GNM_LOOKUP_RMI) {
         s->lookup = kLookupRmi;
         lookup_bytes = (size_t)c->rmi.n_leaves * 16;
-    } else {
+    } else if (mode == GNM_LOOKUP_RADIX) {
+        uint32_t bits = cfg.radix_bits ? cfg.radix_bits : c->tuned.radix_bits;
+        if (bits && (bits < 4 || bits > 16)) return fail(GNM_E_INVAL, "radix_bits must be 4..16");
+        if (!bits) {  // about two buckets per range, shrunk while it crowds out direct rows
+            uint32_t lg = 0;
+            while ((1ull << lg) < nr) ++lg;
+            bits = std::min<uint32_t>(14, std::max<uint32_t>(8, lg + 1));  // directory <= 64 KB
+            const size_t direct = (size_t)c->keys * kSmemRowBytes;
+            const uint32_t floor_bits = std::max<uint32_t>(8, lg > 3 ? lg - 3 : 0);
+            while (bits > floor_bits && direct <= kDirectTableMax &&
+                   direct + ((size_t)1 << bits) * 4 + 4 + 1024 > (size_t)c->smem_optin)
+                --bits;
+        }
+        s->lookup = kLookupRadix;
+        s->radix_bits = bits;
+        lookup_bytes = ((size_t)1 << bits) * 4 + 4;
+        if (lookup_bytes + 1024 > (size_t)c->smem_optin)
+            return fail(GNM_E_INVAL, "radix directory too large for shared memory");
+    } else if (mode == GNM_LOOKUP_BSEARCH) {
         int place = cfg.placement != GNM_PLACE_AUTO ? cfg.placement : c->tuned.placement;
         const size_t sample_bytes = (size_t)c->n_blocks * 4;
         if (place == GNM_PLACE_AUTO)
@@ -221,10 +240,12 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
         } else {
             return fail(GNM_E_INVAL, "unknown placement");
         }
+    } else {
+        return fail(GNM_E_INVAL, "unknown lookup mode");
     }
     const size_t budget = (size_t)c->smem_optin > lookup_bytes + 1024 ? (size_t)c->smem_optin - lookup_bytes - 1024 : 0;
-    const size_t direct = (size_t)c->keys * kAccCols * 8;
-    const size_t row = kAccCols * 8 + 4;
+    const size_t direct = (size_t)c->keys * kSmemRowBytes;
+    const size_t row = kSmemRowBytes + 4;
     uint32_t cap = 0;
     int tm = cfg.table_mode;
     if (tm == GNM_TABLE_AUTO) tm = direct <= std::min(kDirectTableMax, budget) ? GNM_TABLE_DIRECT : GNM_TABLE_HASH;
@@ -234,12 +255,12 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
     } else if (tm == GNM_TABLE_HASH) {
         if (cfg.hash_slots) {
             cap = cfg.hash_slots;
-            if (cap < 256 || cap > 32768 || (cap & (cap - 1)))
-                return fail(GNM_E_INVAL, "hash_slots must be a power of two in 256..32768");
+            if (cap < 256 || cap > 65536 || (cap & 1u))
+                return fail(GNM_E_INVAL, "hash_slots must be even, 256..65536");
             if ((size_t)cap * row > budget) return fail(GNM_E_INVAL, "hash_slots do not fit in shared memory");
-        } else {
-            cap = 1u << 15;
-            while (cap >= 256 && (size_t)cap * row > std::min(kHashTableMax, budget)) cap >>= 1;
+        } else {  // as many slot pairs as fit
+            cap = (uint32_t)(std::min(kHashTableMax, budget) / row) & ~1u;
+            if (cap > 65536) cap = 65536;
         }
         s->table = cap >= 256 ? kTableHash : kTableGlobal;
         if (s->table == kTableGlobal) cap = 0;
@@ -250,14 +271,15 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
     }
     int agg = cfg.aggregation != GNM_AGG_AUTO ? cfg.aggregation : c->tuned.agg;
     s->agg = agg == GNM_AGG_WARP ? GNM_AGG_WARP : GNM_AGG_DIRECT;
-    int block = cfg.block_threads ? cfg.block_threads : (c->tuned.block ? c->tuned.block : 512);
+    int block = cfg.block_threads ? cfg.block_threads : (c->tuned.block ? c->tuned.block : 1024);
     int unroll = cfg.unroll ? cfg.unroll : (c->tuned.unroll ? c->tuned.unroll : 1);
     if (block < 64 || block > 1024 || block % 32) return fail(GNM_E_INVAL, "block_threads must be 64..1024, multiple of 32");
     if (unroll != 1 && unroll != 2) return fail(GNM_E_INVAL, "unroll must be 1 or 2");
     if (unroll == 2 && block > 512) unroll = 1;
     s->block = block;
     s->unroll = unroll;
-    s->smem = aggregate_smem_bytes(s->lookup, s->table, nr, c->keys, cap, s->lookup == kLookupRmi ? c->rmi.n_leaves : 0);
+    s->smem = aggregate_smem_bytes(s->lookup, s->table, nr, c->keys, cap, s->lookup == kLookupRmi ? c->rmi.n_leaves : 0,
+                                   s->radix_bits);
     if (s->smem > (size_t)c->smem_optin) return fail(GNM_E_INVAL, "shared-memory layout exceeds the device limit");
     int cps = cfg.ctas_per_sm ? cfg.ctas_per_sm : c->tuned.ctas_per_sm;
     const int by_threads = std::max(1, 2048 / block);
@@ -285,6 +307,7 @@ gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p) {
     p->rsite = c->d_site;
     p->blocks = reinterpret_cast<const uint4*>(c->d_blocks);
     p->sample = c->d_sample;
+    p->dir16 = c->d_dir16;
     p->n_blocks = c->n_blocks;
     p->n_ranges = (uint32_t)c->h_starts.size();
     p->n_sites = c->n_sites;
@@ -343,6 +366,7 @@ gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* off
     LaunchShape& sh = out->sh;
     GNM_TRY(choose_shape(c, N, &sh));
     p.table_cap = sh.cap;
+    p.radix_bits = sh.radix_bits;
     p.n_total = N;
     uint64_t chunk = ceil_div(N, (uint64_t)sh.grid);
     chunk = (chunk + 3) & ~3ull;
@@ -539,6 +563,7 @@ void gnm_destroy(gnm_ctx* c) {
     free_dev(c->d_site);
     free_dev(c->d_blocks);
     free_dev(c->d_sample);
+    free_dev(c->d_dir16);
     free_dev(c->d_violations);
     free_dev(c->d_flag_count);
     free_dev(c->d_rmi_a);
@@ -578,6 +603,8 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     free_dev(c->d_site);
     free_dev(c->d_blocks);
     free_dev(c->d_sample);
+    free_dev(c->d_dir16);
+    c->d_dir16 = nullptr;
     c->d_starts = nullptr;
     c->d_site = nullptr;
     c->d_blocks = nullptr;
@@ -591,18 +618,31 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     GNM_CU(cudaMalloc(&c->d_site, nr * 4));
     GNM_CU(cudaMemcpy(c->d_starts, starts.data(), nr * 4, cudaMemcpyHostToDevice));
     GNM_CU(cudaMemcpy(c->d_site, sites.data(), nr * 4, cudaMemcpyHostToDevice));
-    // staged layout: blocks of 8 ranges (8 starts, then 8 sites; the last block padded
-    // with start 0xFFFFFFFF and the last site) and the first start of every block
+    // staged layout: blocks of 16 range starts (the last block padded with 0xFFFFFFFF)
+    // and the first start of every block
     const size_t nb = (nr + kBlockRanges - 1) / kBlockRanges;
-    std::vector<uint32_t> blk(nb * 2 * kBlockRanges), smp(nb);
+    std::vector<uint32_t> blk(nb * kBlockRanges), smp(nb);
     for (size_t j = 0; j < nb; ++j) {
         for (size_t k = 0; k < kBlockRanges; ++k) {
             const size_t i = j * kBlockRanges + k;
-            blk[j * 16 + k] = i < nr ? starts[i] : 0xFFFFFFFFu;
-            blk[j * 16 + 8 + k] = i < nr ? sites[i] : sites[nr - 1];
+            blk[j * kBlockRanges + k] = i < nr ? starts[i] : 0xFFFFFFFFu;
         }
         smp[j] = starts[j * kBlockRanges];
     }
+    // radix directory: for each /16 t (and t = 65536 for the end), the range holding its
+    // first address
+    std::vector<uint32_t> dir(65537);
+    {
+        size_t i = 0;
+        for (uint64_t t = 0; t <= 65536; ++t) {
+            const uint64_t a = t << 16;
+            while (i + 1 < nr && (uint64_t)starts[i + 1] <= a) ++i;
+            dir[t] = (uint32_t)i;
+        }
+        dir[65536] = (uint32_t)(nr - 1);
+    }
+    GNM_CU(cudaMalloc(&c->d_dir16, dir.size() * 4));
+    GNM_CU(cudaMemcpy(c->d_dir16, dir.data(), dir.size() * 4, cudaMemcpyHostToDevice));
     GNM_CU(cudaMalloc(&c->d_blocks, blk.size() * 4));
     GNM_CU(cudaMalloc(&c->d_sample, nb * 4));
     GNM_CU(cudaMemcpy(c->d_blocks, blk.data(), blk.size() * 4, cudaMemcpyHostToDevice));
@@ -644,7 +684,8 @@ gnm_status gnm_registry_info_get(gnm_ctx* c, gnm_registry_info* out) {
     if (choose_shape(c, 1u << 20, &sh) == GNM_OK) {
         out->placement = sh.lookup == kLookupSmem ? GNM_PLACE_SMEM
                          : sh.lookup == kLookupStaged ? GNM_PLACE_STAGED : GNM_PLACE_L2;
-        out->lookup_mode = sh.lookup == kLookupRmi ? GNM_LOOKUP_RMI : GNM_LOOKUP_BSEARCH;
+        out->lookup_mode = sh.lookup == kLookupRmi ? GNM_LOOKUP_RMI
+                           : sh.lookup == kLookupRadix ? GNM_LOOKUP_RADIX : GNM_LOOKUP_BSEARCH;
         out->privatized = sh.table != kTableGlobal;
     }
     out->rmi_ready = c->rmi_ready;
@@ -874,6 +915,7 @@ gnm_status gnm_lookup(gnm_ctx* c, const uint32_t* addr, uint64_t n, uint32_t* si
     AggParams p;
     gnm_records none{};
     GNM_TRY(build_params(c, &none, &p));
+    p.radix_bits = sh.radix_bits;
     GNM_CU(launch_lookup(p, sh.lookup, addr, n, site_out, pos_out, (cudaStream_t)stream));
     c->last_launches = 1;
     return GNM_OK;

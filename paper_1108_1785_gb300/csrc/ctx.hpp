@@ -66,6 +66,7 @@ struct Staging {
 
 struct Tuned {
     int block = 0, ctas_per_sm = 0, unroll = 0, agg = 0, placement = 0;
+    uint32_t radix_bits = 0;
 };
 
 }  // namespace gnm
@@ -87,6 +88,7 @@ struct gnm_ctx {
     uint32_t* d_blocks = nullptr;   // staged placement: [n_blocks][8 starts, 8 sites]
     uint32_t* d_sample = nullptr;   // staged placement: first start of every block
     uint32_t n_blocks = 0;
+    uint32_t* d_dir16 = nullptr;    // radix directory: range of each /16's first address
     uint32_t local_pfx[GNM_MAX_LOCAL] = {0};
     uint32_t local_mask[GNM_MAX_LOCAL] = {0};
     uint32_t n_local = 0;

@@ -11,6 +11,7 @@ namespace gnm {
 constexpr uint32_t kNoSite = GNM_NO_SITE;
 constexpr int kNStat = GNM_NSTAT;   // columns of a user-facing stats row
 constexpr int kAccCols = 5;         // accumulator row: flows<<32|e_flows, oct, pkts, e_oct, e_dur
+constexpr size_t kSmemRowBytes = 20;  // per-CTA shared-memory row: packed counts + 4 low words
 constexpr int kUnmatched = 4;       // classes appended after the 2*n_sites site rows
 constexpr int kMaxLeaves = 65536;
 constexpr int kMaxHidden = 32;
@@ -56,8 +57,10 @@ struct AggParams {
     // registry
     const uint32_t* starts;
     const uint32_t* rsite;
-    const uint4* blocks;         // staged placement: per 8 ranges, 8 starts then 8 sites
+    const uint4* blocks;         // staged placement: 16 starts per block (64 bytes)
     const uint32_t* sample;      // staged placement: first start of every block
+    const uint32_t* dir16;       // radix directory over the top 16 bits (65537 entries)
+    uint32_t radix_bits;         // directory bits used by this launch (<= 16)
     uint32_t n_blocks;
     uint32_t n_ranges;
     uint32_t n_sites;
@@ -86,8 +89,8 @@ struct AggParams {
     unsigned long long* violations;  // learned-index fallbacks
 };
 
-enum { kLookupL2 = 0, kLookupSmem = 1, kLookupRmi = 2, kLookupStaged = 3 };
-constexpr uint32_t kBlockRanges = 8;  // ranges per staged block (64 bytes)
+enum { kLookupL2 = 0, kLookupSmem = 1, kLookupRmi = 2, kLookupStaged = 3, kLookupRadix = 4 };
+constexpr uint32_t kBlockRanges = 16;  // ranges per staged block (16 starts, 64 bytes)
 enum { kTableDirect = 0, kTableHash = 1, kTableGlobal = 2 };
 
 // Launch shape chosen by the host.
@@ -100,13 +103,14 @@ struct LaunchShape {
     int agg;         // GNM_AGG_DIRECT / GNM_AGG_WARP (shared-memory tables only)
     int grid;
     uint32_t cap;    // hash-table slots (kTableHash)
+    uint32_t radix_bits;  // kLookupRadix directory bits
     size_t smem;
 };
 
 // aggregate*.cu
 cudaError_t launch_aggregate(const AggParams& p, const LaunchShape& s, cudaStream_t st);
 size_t aggregate_smem_bytes(int lookup, int table, uint32_t n_ranges, uint32_t keys,
-                            uint32_t table_cap, uint32_t n_leaves);
+                            uint32_t table_cap, uint32_t n_leaves, uint32_t radix_bits);
 cudaError_t launch_finalize(const AggParams& p, uint32_t slot, cudaStream_t st);
 cudaError_t launch_flag_compact(const double* rate, const uint64_t* stats, uint32_t n_site_keys,
                                 double thr, uint32_t min_flows, uint32_t* out_keys,

@@ -8,20 +8,22 @@ cudaError_t launch_aggregate_l2(const AggParams& p, const LaunchShape& s, cudaSt
 cudaError_t launch_aggregate_smem(const AggParams& p, const LaunchShape& s, cudaStream_t st);
 cudaError_t launch_aggregate_rmi(const AggParams& p, const LaunchShape& s, cudaStream_t st);
 cudaError_t launch_aggregate_staged(const AggParams& p, const LaunchShape& s, cudaStream_t st);
+cudaError_t launch_aggregate_radix(const AggParams& p, const LaunchShape& s, cudaStream_t st);
 
 cudaError_t launch_aggregate(const AggParams& p, const LaunchShape& s, cudaStream_t st) {
     switch (s.lookup) {
         case kLookupSmem: return launch_aggregate_smem(p, s, st);
         case kLookupRmi: return launch_aggregate_rmi(p, s, st);
         case kLookupStaged: return launch_aggregate_staged(p, s, st);
+        case kLookupRadix: return launch_aggregate_radix(p, s, st);
         default: return launch_aggregate_l2(p, s, st);
     }
 }
 
 size_t aggregate_smem_bytes(int lookup, int table, uint32_t n_ranges, uint32_t keys,
-                            uint32_t table_cap, uint32_t n_leaves) {
+                            uint32_t table_cap, uint32_t n_leaves, uint32_t radix_bits) {
     size_t a, b;
-    return dev::smem_layout(lookup, table, n_ranges, keys, table_cap, n_leaves, &a, &b);
+    return dev::smem_layout(lookup, table, n_ranges, keys, table_cap, n_leaves, radix_bits, &a, &b);
 }
 
 namespace {
@@ -59,6 +61,12 @@ __global__ void k_lookup(const __grid_constant__ AggParams p, const uint32_t* __
         for (uint32_t i = threadIdx.x; i < p.n_blocks; i += blockDim.x) st[i] = __ldg(p.sample + i);
         s_starts = st;
     }
+    if (LOOKUP == kLookupRadix) {
+        uint32_t* d = reinterpret_cast<uint32_t*>(smem_raw);
+        const uint32_t nd = 1u << p.radix_bits, sh = 16u - p.radix_bits;
+        for (uint32_t i = threadIdx.x; i <= nd; i += blockDim.x) d[i] = __ldg(p.dir16 + ((size_t)i << sh));
+        s_starts = d;
+    }
     if (LOOKUP == kLookupRmi) {
         const uint32_t L = p.rmi.n_leaves;
         float* a = reinterpret_cast<float*>(smem_raw);
@@ -80,6 +88,10 @@ __global__ void k_lookup(const __grid_constant__ AggParams p, const uint32_t* __
         uint32_t idx;
         if (LOOKUP == kLookupRmi) {
             idx = dev::rmi_lookup(p.rmi, ra, rb, rx0, reps, p.starts, p.n_ranges, x, p.violations);
+        } else if (LOOKUP == kLookupRadix) {
+            uint32_t xs[1] = {x}, b[1];
+            dev::radix_search<1>(s_starts, p.radix_bits, p.starts, xs, b);
+            idx = b[0];
         } else if (LOOKUP == kLookupStaged) {
             uint32_t xs[1] = {x}, b[1];
             dev::pred_search<1, true>(s_starts, p.n_blocks, xs, b);
@@ -128,6 +140,7 @@ cudaError_t launch_lookup(const AggParams& p, int lookup, const uint32_t* addr, 
     (void)cudaGetLastError();  // report this launch's error only
     if (lookup == kLookupSmem) smem = (size_t)p.n_ranges * 4;
     if (lookup == kLookupStaged) smem = (size_t)p.n_blocks * 4;
+    if (lookup == kLookupRadix) smem = ((size_t)1 << p.radix_bits) * 4 + 4;
     if (lookup == kLookupRmi) smem = (size_t)p.rmi.n_leaves * 16;
     cudaError_t e;
     switch (lookup) {
@@ -145,6 +158,11 @@ cudaError_t launch_lookup(const AggParams& p, int lookup, const uint32_t* addr, 
             e = cudaFuncSetAttribute(k_lookup<kLookupStaged>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             k_lookup<kLookupStaged><<<blocks, 256, smem, st>>>(p, addr, n, site_out, pos_out);
+            break;
+        case kLookupRadix:
+            e = cudaFuncSetAttribute(k_lookup<kLookupRadix>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_lookup<kLookupRadix><<<blocks, 256, smem, st>>>(p, addr, n, site_out, pos_out);
             break;
         default:
             k_lookup<kLookupL2><<<blocks, 256, 0, st>>>(p, addr, n, site_out, pos_out);

@@ -150,19 +150,18 @@ extern "C" gnm_status gnm_window_process_noalloc(const gnm_config* cfg_in, const
     const size_t lookup_bytes = sh.lookup == kLookupSmem ? (size_t)n_ranges * 8 : 0;
     const size_t budget = (size_t)optin > lookup_bytes + 1024 ? (size_t)optin - lookup_bytes - 1024 : 0;
     uint32_t cap = 0;
-    if ((size_t)keys * kAccCols * 8 <= std::min<size_t>(120 * 1024, budget)) {
+    if ((size_t)keys * kSmemRowBytes <= std::min<size_t>(120 * 1024, budget)) {
         sh.table = kTableDirect;
     } else {
-        cap = 1u << 15;
-        while (cap >= 256 && (size_t)cap * (kAccCols * 8 + 4) > std::min<size_t>(176 * 1024, budget)) cap >>= 1;
+        cap = (uint32_t)(std::min<size_t>(200 * 1024, budget) / (kSmemRowBytes + 4)) & ~1u;
         sh.table = cap >= 256 ? kTableHash : kTableGlobal;
         if (sh.table == kTableGlobal) cap = 0;
     }
     sh.cap = cap;
     sh.agg = GNM_AGG_DIRECT;
-    sh.block = 512;
+    sh.block = 1024;
     sh.unroll = 1;
-    sh.smem = aggregate_smem_bytes(sh.lookup, sh.table, n_ranges, keys, cap, 0);
+    sh.smem = aggregate_smem_bytes(sh.lookup, sh.table, n_ranges, keys, cap, 0, 0);
     const int fit = std::max(1, std::min(2048 / sh.block, (int)(per_sm / (sh.smem + 1024))));
     const uint64_t min_per_cta = (uint64_t)sh.block * 8;
     uint64_t grid = std::min<uint64_t>((uint64_t)sms * fit, std::max<uint64_t>(1, (rec->n + min_per_cta - 1) / min_per_cta));

@@ -6,6 +6,7 @@
 // buffers and window shapes stay, only their contents change between launches.
 #include <algorithm>
 #include <cstring>
+#include <iterator>
 #include <vector>
 
 #include "ctx.hpp"
@@ -157,34 +158,52 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
     const int unrolls[] = {1, 2};
     const int aggs[] = {GNM_AGG_DIRECT, GNM_AGG_WARP};
     const int places[] = {GNM_PLACE_SMEM, GNM_PLACE_STAGED, GNM_PLACE_L2};
+    // the lookup method decides which knob matters: placement (binary search) or
+    // directory size (radix)
+    LaunchShape base_shape;
+    GNM_TRY(choose_shape(c, offsets[n_win] - offsets[0], &base_shape));
+    std::vector<int> places_v, bits_v;
+    if (base_shape.lookup == kLookupRadix) {
+        places_v.push_back(GNM_PLACE_AUTO);
+        const int b0 = (int)base_shape.radix_bits;
+        for (int d : {0, -2, -1, 1, 2})
+            if (b0 + d >= 4 && b0 + d <= 16) bits_v.push_back(b0 + d);
+    } else {
+        bits_v.push_back(0);
+        if (base_shape.lookup == kLookupRmi) places_v.push_back(GNM_PLACE_AUTO);
+        else places_v.assign(std::begin(places), std::end(places));
+    }
     const int cpss[] = {0, 1};
     for (int b : blocks)
         for (int u : unrolls)
             for (int a : aggs)
-                for (int pl : places)
-                    for (int cps : cpss) {
-                        if (status != GNM_OK) break;
-                        if (u == 2 && b > 512) continue;
-                        c->cfg = saved;
-                        if (c->cfg.block_threads == 0) c->cfg.block_threads = b;
-                        if (c->cfg.unroll == 0) c->cfg.unroll = u;
-                        if (c->cfg.aggregation == GNM_AGG_AUTO) c->cfg.aggregation = a;
-                        if (c->cfg.placement == GNM_PLACE_AUTO) c->cfg.placement = pl;
-                        if (c->cfg.ctas_per_sm == 0) c->cfg.ctas_per_sm = cps;
-                        LaunchShape sh;
-                        if (choose_shape(c, offsets[n_win] - offsets[0], &sh) != GNM_OK) continue;  // does not fit
-                        double ms;
-                        status = time_cfg(&ms);
-                        rep->n_tried++;
-                        if (status == GNM_OK && ms < rep->best_ms) {
-                            rep->best_ms = ms;
-                            rep->block_threads = c->cfg.block_threads;
-                            rep->unroll = c->cfg.unroll;
-                            rep->aggregation = c->cfg.aggregation;
-                            rep->placement = c->cfg.placement;
-                            rep->ctas_per_sm = sh.ctas_per_sm;
+                for (int pl : places_v)
+                    for (int rb : bits_v)
+                        for (int cps : cpss) {
+                            if (status != GNM_OK) break;
+                            if (u == 2 && b > 512) continue;
+                            c->cfg = saved;
+                            if (c->cfg.block_threads == 0) c->cfg.block_threads = b;
+                            if (c->cfg.unroll == 0) c->cfg.unroll = u;
+                            if (c->cfg.aggregation == GNM_AGG_AUTO) c->cfg.aggregation = a;
+                            if (c->cfg.placement == GNM_PLACE_AUTO) c->cfg.placement = pl;
+                            if (c->cfg.radix_bits == 0) c->cfg.radix_bits = (uint32_t)rb;
+                            if (c->cfg.ctas_per_sm == 0) c->cfg.ctas_per_sm = cps;
+                            LaunchShape sh;
+                            if (choose_shape(c, offsets[n_win] - offsets[0], &sh) != GNM_OK) continue;  // does not fit
+                            double ms;
+                            status = time_cfg(&ms);
+                            rep->n_tried++;
+                            if (status == GNM_OK && ms < rep->best_ms) {
+                                rep->best_ms = ms;
+                                rep->block_threads = c->cfg.block_threads;
+                                rep->unroll = c->cfg.unroll;
+                                rep->aggregation = c->cfg.aggregation;
+                                rep->placement = c->cfg.placement;
+                                rep->ctas_per_sm = sh.ctas_per_sm;
+                                rep->radix_bits = sh.radix_bits;
+                            }
                         }
-                    }
     c->cfg = saved;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -197,6 +216,7 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
     c->tuned.agg = rep->aggregation;
     c->tuned.placement = rep->placement;
     c->tuned.ctas_per_sm = rep->ctas_per_sm;
+    c->tuned.radix_bits = rep->radix_bits;
     // leave the windows holding the results of the chosen shape
     return gnm_windows_process(c, rec, offsets, wids, n_win, st) == GNM_OK && cudaStreamSynchronize(st) == cudaSuccess
                ? GNM_OK

@@ -151,11 +151,12 @@ def test_rmi_window_equals_bsearch_and_oracle(gnm, c3, trained_linear):
     ctx.process(d, 1)  # AUTO lookup: learned index
     expect = oracle_full(reg, rec, lpm=lpm)
     assert_window_matches(ctx.dense(1), expect)
-    plain = gnm.Context(window_slots=2, lookup_mode=gnm.LOOKUP_BSEARCH)
-    plain.load(reg)
-    plain.process(d, 1)
-    assert_window_matches(plain.dense(1), expect)
-    plain.close()
+    for mode in (gnm.LOOKUP_BSEARCH, gnm.LOOKUP_RADIX):
+        plain = gnm.Context(window_slots=2, lookup_mode=mode)
+        plain.load(reg)
+        plain.process(d, 1)
+        assert_window_matches(plain.dense(1), expect)
+        plain.close()
 
 
 def test_rmi_gain_over_binary_search(gnm, c3, trained_linear):
@@ -185,6 +186,13 @@ def test_rmi_gain_over_binary_search(gnm, c3, trained_linear):
 
     tb, tr = t(plain, s1), t(ctx, s2)
     assert torch.equal(s1, s2)
+    radix = gnm.Context(lookup_mode=gnm.LOOKUP_RADIX)
+    radix.load(reg)
+    s3 = torch.empty_like(dx)
+    td = t(radix, s3)
+    assert torch.equal(s1, s3)
+    radix.close()
+    print(f"\nradix-directed lookups: {td:.3f} ms")
     probes_plain = np.ceil(np.log2(starts.size))
     probes_rmi = np.log2(rep.eps_mean + 1) + 1
     print(f"\nlookups of {n:,} addresses: bsearch {tb:.3f} ms, learned index {tr:.3f} ms "

@@ -68,15 +68,20 @@ def test_hand_window(gnm):
         ctx.close()
 
 
+LOOKUPS = [("BSEARCH", "SMEM", 0), ("BSEARCH", "STAGED", 0), ("BSEARCH", "L2", 0), ("RADIX", "AUTO", 0),
+           ("RADIX", "AUTO", 5)]
+
+
 @pytest.mark.parametrize("table", ["DIRECT", "HASH", "GLOBAL"])
 @pytest.mark.parametrize("agg", ["DIRECT", "WARP"])
-@pytest.mark.parametrize("place", ["SMEM", "STAGED", "L2"])
+@pytest.mark.parametrize("lookup", LOOKUPS, ids=lambda l: f"{l[0]}-{l[1]}-{l[2]}")
 @pytest.mark.parametrize("unroll,block", [(1, 256), (2, 512), (1, 1024)])
-def test_c1_window_all_variants(gnm, c1, table, agg, place, unroll, block):
+def test_c1_window_all_variants(gnm, c1, table, agg, lookup, unroll, block):
     reg, rec, expect = c1
+    mode, place, bits = lookup
     ctx = _ctx(gnm, reg, table_mode=getattr(gnm, "TABLE_" + table), aggregation=getattr(gnm, "AGG_" + agg),
-               placement=getattr(gnm, "PLACE_" + place), unroll=unroll, block_threads=block,
-               hash_slots=512 if table == "HASH" else 0)
+               lookup_mode=getattr(gnm, "LOOKUP_" + mode), placement=getattr(gnm, "PLACE_" + place),
+               radix_bits=bits, unroll=unroll, block_threads=block, hash_slots=512 if table == "HASH" else 0)
     d = gnm.Records.to_device(rec)
     ctx.process(d, 1)
     assert_window_matches(ctx.dense(1), expect)
@@ -145,8 +150,9 @@ def c2hour():
     return reg, rec, off, expect
 
 
-@pytest.mark.parametrize("cfg", [{}, {"placement": "L2"}, {"aggregation": "WARP"}, {"hash_slots": 1024},
-                                 {"table_mode": "GLOBAL"}])
+@pytest.mark.parametrize("cfg", [{}, {"lookup_mode": "BSEARCH"}, {"lookup_mode": "BSEARCH", "placement": "L2"},
+                                 {"aggregation": "WARP"}, {"hash_slots": 1024}, {"table_mode": "GLOBAL"},
+                                 {"radix_bits": 12}])
 def test_c2_hour_batched_bitexact(gnm, c2hour, cfg):
     """Sixty one-minute windows (10M records, nested registry) in one launch -- the
     benchmark's workload and, with cfg {}, its launch configuration; every window equals
@@ -154,13 +160,14 @@ def test_c2_hour_batched_bitexact(gnm, c2hour, cfg):
     reg, rec, off, expect = c2hour
     kw = {}
     for k, v in cfg.items():
-        kw[k] = getattr(gnm, {"placement": "PLACE_", "aggregation": "AGG_", "table_mode": "TABLE_"}[k] + v) \
-            if isinstance(v, str) else v
+        kw[k] = getattr(gnm, {"placement": "PLACE_", "aggregation": "AGG_", "table_mode": "TABLE_",
+                              "lookup_mode": "LOOKUP_"}[k] + v) if isinstance(v, str) else v
     if "hash_slots" in kw:
         kw["table_mode"] = gnm.TABLE_HASH
     ctx = _ctx(gnm, reg, window_slots=64, **kw)
-    if not cfg:
-        assert ctx.registry_info().placement == gnm.PLACE_STAGED
+    if not cfg:  # the benchmark's default: radix-directed lookup, per-CTA shared-memory sums
+        info = ctx.registry_info()
+        assert info.lookup_mode == gnm.LOOKUP_RADIX and info.privatized
     d = gnm.Records.to_device(rec)
     ids = np.arange(60) + 5000
     plan = ctx.plan(d, off, ids)  # the benchmark's path: a CUDA graph of one launch
@@ -217,10 +224,14 @@ def test_slot_eviction_and_release(gnm, c1):
     ctx.close()
 
 
-@pytest.mark.parametrize("which,place", [("c1", "SMEM"), ("c1", "STAGED"), ("c2", "STAGED"), ("c2", "L2")])
-def test_lookup_matches_oracle(gnm, which, place):
+@pytest.mark.parametrize("which,mode,place,bits", [("c1", "BSEARCH", "SMEM", 0), ("c1", "BSEARCH", "STAGED", 0),
+                                                   ("c2", "BSEARCH", "STAGED", 0), ("c2", "BSEARCH", "L2", 0),
+                                                   ("c1", "RADIX", "AUTO", 0), ("c2", "RADIX", "AUTO", 0),
+                                                   ("c2", "RADIX", "AUTO", 4), ("c2", "RADIX", "AUTO", 15)])
+def test_lookup_matches_oracle(gnm, which, mode, place, bits):
     reg = fg.registry_c1() if which == "c1" else fg.registry_c2()
-    ctx = _ctx(gnm, reg, placement=getattr(gnm, "PLACE_" + place))
+    ctx = _ctx(gnm, reg, lookup_mode=getattr(gnm, "LOOKUP_" + mode), placement=getattr(gnm, "PLACE_" + place),
+               radix_bits=bits)
     lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
     st, _ = lpm.flatten()
     s64 = st.astype(np.int64)
@@ -241,6 +252,15 @@ def test_lookup_matches_oracle(gnm, which, place):
 
 def _ip(s):
     return int(ipaddress.IPv4Address(s))
+
+
+def test_radix_directory_must_fit(gnm):
+    reg = fg.registry_c2()
+    ctx = _ctx(gnm, reg, lookup_mode=gnm.LOOKUP_RADIX, radix_bits=16)  # 256 KB > shared memory
+    d = gnm.Records.to_device(fg.make_records(reg, 1000, seed=3))
+    with pytest.raises(gnm.GnmError, match="radix directory too large"):
+        ctx.process(d, 1)
+    ctx.close()
 
 
 def test_registry_validation(gnm):
