@@ -60,7 +60,7 @@ typedef enum {
  * `radix_bits` address bits -- the paper's direct-indexed site catalog (Sec. III.B.2.1
  * hashes /24 subnets) generalised to any prefix length -- gives each bucket's range
  * interval, and a binary search inside the bucket finishes. AUTO: RMI when trained, else
- * RADIX. */
+ * BSEARCH when the registry fits shared memory, else RADIX. */
 enum { GNM_LOOKUP_AUTO = 0, GNM_LOOKUP_BSEARCH = 1, GNM_LOOKUP_RMI = 2, GNM_LOOKUP_RADIX = 3 };
 /* Where the flattened registry is searched: wholly in shared memory (SMEM), wholly in L2
  * (L2), or STAGED: the first start of every block of 16 ranges in shared memory, the
@@ -72,6 +72,7 @@ enum { GNM_ADMIN_OR = 0, GNM_ADMIN_AND = 1 };
  * shared-memory hash table of the keys a CTA meets with global atomics for the overflow
  * (HASH), or warp-aggregated global atomics only (GLOBAL). */
 enum { GNM_TABLE_AUTO = 0, GNM_TABLE_DIRECT = 1, GNM_TABLE_HASH = 2, GNM_TABLE_GLOBAL = 3 };
+enum { GNM_SPLIT_AUTO = 0, GNM_SPLIT_FUSED = 1, GNM_SPLIT_TWO_KERNELS = 2 };
 
 /* Filters and execution knobs. The paper fixes none of the filter constants
  * (Sec. III.B.2.1 says only "average packet size ... usually small" and "small number
@@ -99,6 +100,12 @@ typedef struct {
                                    even number in 256..65536 */
     uint32_t radix_bits;        /* GNM_LOOKUP_RADIX directory bits: 0 = sized from the
                                    registry, else 4..16 */
+    int32_t split;              /* GNM_SPLIT_*: one fused kernel, or a lookup kernel that
+                                   writes a 4-byte key per record followed by the
+                                   aggregation kernel (registries outside shared memory) */
+    int32_t key_directory;      /* split RADIX lookups: 0 = 32-bit range directory,
+                                   1 = 16-bit directory of 8-range blocks that carry their
+                                   sites (one 64-byte L2 load per lookup) */
 } gnm_config;
 
 /* One struct-of-arrays batch of NetFlow v5 fields (Sec. IV.A.3: 48-byte v5 records; only
@@ -329,6 +336,7 @@ typedef struct {
     double best_ms, default_ms;
     uint32_t n_tried;
     uint32_t radix_bits;
+    int32_t split;
 } gnm_tune_report;
 
 /* Times candidate launch shapes (block size, CTAs per SM, records per thread,

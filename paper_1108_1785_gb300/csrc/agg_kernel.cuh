@@ -99,6 +99,48 @@ __device__ __forceinline__ void radix_search(const uint32_t* __restrict__ dir, u
     }
 }
 
+// Block-directory search (key kernel): dirb[t] is the 8-range block holding the first
+// address of bucket t (the top `bits` bits), so x lies in blocks [dirb[t], dirb[t+1]];
+// usually one block, else a binary search over the blocks' first starts picks it. The
+// block's 8 starts and 8 sites come in one 64-byte load; padding past the last range is
+// start 0xFFFFFFFF with the last site.
+template <int R>
+__device__ __forceinline__ void radix_block_sites(const uint16_t* __restrict__ dirb, uint32_t bits,
+                                                  const uint32_t* __restrict__ sample8, const uint4* __restrict__ blk8,
+                                                  const uint32_t (&x)[R], uint32_t (&site)[R]) {
+    uint32_t b[R], len[R];
+    bool more = false;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const uint32_t t = x[j] >> (32u - bits);
+        b[j] = dirb[t];
+        len[j] = (uint32_t)dirb[t + 1] - b[j] + 1u;
+        more |= len[j] > 1u;
+    }
+    while (more) {
+        more = false;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (len[j] > 1u) {
+                const uint32_t half = len[j] >> 1;
+                b[j] = (__ldg(sample8 + b[j] + half) <= x[j]) ? b[j] + half : b[j];
+                len[j] -= half;
+                more |= len[j] > 1u;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const uint4* q = blk8 + 4 * (size_t)b[j];
+        const uint4 s0 = __ldg(q), s1 = __ldg(q + 1), w0 = __ldg(q + 2), w1 = __ldg(q + 3);
+        const uint32_t c = (s0.y <= x[j]) + (s0.z <= x[j]) + (s0.w <= x[j]) + (s1.x <= x[j]) + (s1.y <= x[j]) +
+                           (s1.z <= x[j]) + (s1.w <= x[j]);  // s0.x <= x: it is the block's first start
+        const uint4 w = c < 4 ? w0 : w1;
+        const uint32_t r = c & 3u;
+        site[j] = r == 0 ? w.x : (r == 1 ? w.y : (r == 2 ? w.z : w.w));
+    }
+}
+
 // floor(v) clamped to [0, n-1] (n - 1 < 2^24, so the comparison is exact); NaN -> 0.
 __device__ __forceinline__ uint32_t clamp_floor(float v, uint32_t n) {
     if (!(v >= 0.f)) return 0u;
@@ -223,7 +265,6 @@ __device__ __forceinline__ void row_add_sums(uint64_t* row, uint64_t packed, uin
 // global accumulator column directly (rare: a word wraps once per ~4 GB of octets), so
 // every total stays exact.
 constexpr int kRowWords = 5;
-constexpr uint32_t kFlushRecords = 65532;  // < 2^16, multiple of 4
 static_assert(kRowWords * 4 == kSmemRowBytes, "host and device disagree on the shared row size");
 
 __device__ __forceinline__ void red32(uint32_t* a, uint32_t v) { atomicAdd(a, v); }
@@ -363,6 +404,17 @@ __device__ __forceinline__ void accumulate(const Item& it, const Smem& sm, uint3
     group_add(it, peers, r, sm, gacc);
 }
 
+// Direct tables with a partial-sum area: the CTA stores its rows (as they are, 16-bit
+// counts and low 32-bit sums) to its own block of the area with plain coalesced stores
+// and clears them; the window's last CTA adds the blocks up when it finalises.
+__device__ __forceinline__ void dump_rows(const Smem& sm, uint32_t* dst) {
+    const uint32_t words = sm.rows * kRowWords;
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) {
+        __stcg(dst + i, sm.t[i]);
+        sm.t[i] = 0;
+    }
+}
+
 // Adds the CTA's shared-memory sums to the window's global accumulators and clears them.
 template <int TABLE>
 __device__ __forceinline__ void flush(const Smem& sm, uint64_t* gacc) {
@@ -387,20 +439,31 @@ __device__ __forceinline__ void flush(const Smem& sm, uint64_t* gacc) {
 // Rates and flags of one window from its accumulators (Sec. III.B.1: rates per site;
 // a site is sub-optimal when its rate is below the standard).
 __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot, uint32_t k0,
-                                              uint32_t step) {
+                                              uint32_t step, const uint32_t* parts = nullptr,
+                                              uint32_t n_parts = 0) {
     const size_t keys = p.keys;
     uint64_t* acc = p.acc + (size_t)slot * keys * kAccCols;
     uint64_t* st = p.stats + (size_t)slot * keys * kNStat;
     const uint32_t nk = 2u * p.n_sites;
     double* rate = p.rate + (size_t)slot * nk;
     uint8_t* flag = p.flag + (size_t)slot * nk;
+#pragma unroll 1
     for (uint32_t k = k0; k < keys; k += step) {
         uint64_t* a = acc + (size_t)k * kAccCols;
-        const uint64_t packed = __ldcg(reinterpret_cast<const unsigned long long*>(a));
-        const uint64_t oc = __ldcg(reinterpret_cast<const unsigned long long*>(a + 1));
-        const uint64_t pk = __ldcg(reinterpret_cast<const unsigned long long*>(a + 2));
-        const uint64_t eo = __ldcg(reinterpret_cast<const unsigned long long*>(a + 3));
-        const uint64_t ed = __ldcg(reinterpret_cast<const unsigned long long*>(a + 4));
+        uint64_t packed = __ldcg(reinterpret_cast<const unsigned long long*>(a));
+        uint64_t oc = __ldcg(reinterpret_cast<const unsigned long long*>(a + 1));
+        uint64_t pk = __ldcg(reinterpret_cast<const unsigned long long*>(a + 2));
+        uint64_t eo = __ldcg(reinterpret_cast<const unsigned long long*>(a + 3));
+        uint64_t ed = __ldcg(reinterpret_cast<const unsigned long long*>(a + 4));
+        for (uint32_t q = 0; q < n_parts; ++q) {  // partial blocks of the window's CTAs
+            const uint32_t* w = parts + ((size_t)q * keys + k) * kRowWords;
+            const uint32_t cnt = __ldcg(w);
+            packed += ((uint64_t)(cnt & 0xFFFFu) << 32) | (cnt >> 16);
+            oc += __ldcg(w + 1);
+            pk += __ldcg(w + 2);
+            eo += __ldcg(w + 3);
+            ed += __ldcg(w + 4);
+        }
         const uint64_t ef = packed & 0xFFFFFFFFull;
         // accumulators return to zero for the slot's next window
 #pragma unroll
@@ -454,21 +517,12 @@ __host__ __device__ inline size_t smem_layout(int lookup, int table, uint32_t n_
     return align_up(o, 16);
 }
 
-// Processes R records per thread: lookups for all of them first (independent loads in
-// flight together), then classification and accumulation.
-template <int LOOKUP, int TABLE, int AGG, int R>
-__device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint64_t* gacc,
-                                        const bool (&valid)[R], const uint32_t (&src)[R],
-                                        const uint32_t (&dst)[R], const uint32_t (&pk)[R],
-                                        const uint32_t (&oc)[R], const uint32_t (&fi)[R],
-                                        const uint32_t (&la)[R]) {
-    uint32_t x[R], idx[R], site[R];
-    bool sl[R], dl[R];
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-        local_pair(p, src[j], dst[j], sl[j], dl[j]);
-        x[j] = sl[j] ? dst[j] : src[j];  // the remote endpoint
-    }
+// Site of each remote address x[j] (kNoSite when unregistered) by the launch's lookup
+// method; the R lookups advance together so their loads overlap.
+template <int LOOKUP, int R>
+__device__ __forceinline__ void lookup_sites(const AggParams& p, const Smem& sm, const bool (&valid)[R],
+                                             const uint32_t (&x)[R], uint32_t (&site)[R]) {
+    uint32_t idx[R];
     if (LOOKUP == kLookupSmem) {
         pred_search<R, true>(sm.s_starts, p.n_ranges, x, idx);
 #pragma unroll
@@ -487,7 +541,9 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
         for (int j = 0; j < R; ++j) idx[j] = staged_block_pos(p.blocks + 4 * (size_t)idx[j], idx[j], x[j], p.n_ranges);
 #pragma unroll
         for (int j = 0; j < R; ++j) site[j] = __ldg(p.rsite + idx[j]);
-    } else {
+    } else if (LOOKUP == kLookupRadixBlk) {
+        radix_block_sites<R>(reinterpret_cast<const uint16_t*>(sm.s_starts), p.radix_bits, p.sample8, p.blk8, x, site);
+    } else if (LOOKUP == kLookupRmi) {
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             idx[j] = valid[j] ? rmi_lookup(p.rmi, sm.ra, sm.rb, sm.rx0, sm.reps, p.starts,
@@ -497,10 +553,64 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
 #pragma unroll
         for (int j = 0; j < R; ++j) site[j] = __ldg(p.rsite + idx[j]);
     }
+}
+
+// Key of a record: site*2+dir for a record between the local site and a registered
+// site, else 2*n_sites + unmatched class (0 neither local, 1 both local, 2 inbound from
+// an unregistered address, 3 outbound to one).
+__device__ __forceinline__ uint32_t record_key(const AggParams& p, bool sl, bool dl, uint32_t site) {
+    const uint32_t nk = 2u * p.n_sites;
+    const uint32_t dir = sl ? 1u : 0u;  // outbound when the source is local
+    const bool mixed = sl != dl;
+    return mixed ? (site != kNoSite ? site * 2u + dir : nk + 2u + dir) : nk + dir;
+}
+
+// A record whose key is already known (split launches: a lookup kernel wrote it).
+__device__ __forceinline__ Item classify_key(const AggParams& p, bool valid, uint32_t key, uint32_t pk,
+                                             uint32_t oc, uint32_t fi, uint32_t la) {
+    Item it;
+    const uint32_t dur = la - fi;  // modulo 2^32
+    const bool ack_ok = (uint64_t)oc >= (uint64_t)p.min_avg * (uint64_t)pk;
+    const bool many = pk >= p.min_pkts, longd = dur >= p.min_dur;
+    const bool admin_ok = p.admin_rule == GNM_ADMIN_OR ? (many && longd) : (many || longd);
+    it.key = key;
+    it.elig = key < 2u * p.n_sites && dur != 0u && ack_ok && admin_ok;
+    it.oc = oc;
+    it.pk = pk;
+    it.dur = dur;
+    it.valid = valid;
+    return it;
+}
+
+// Processes R records per thread: lookups for all of them first (independent loads in
+// flight together), then classification and accumulation. With LOOKUP == kLookupKeys the
+// `src` field carries each record's precomputed key instead of an address.
+template <int LOOKUP, int TABLE, int AGG, int R>
+__device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint64_t* gacc,
+                                        const bool (&valid)[R], const uint32_t (&src)[R],
+                                        const uint32_t (&dst)[R], const uint32_t (&pk)[R],
+                                        const uint32_t (&oc)[R], const uint32_t (&fi)[R],
+                                        const uint32_t (&la)[R]) {
+    if constexpr (LOOKUP == kLookupKeys) {
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-        const Item it = classify(p, valid[j], sl[j], dl[j], pk[j], oc[j], fi[j], la[j], site[j]);
-        accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
+        for (int j = 0; j < R; ++j) {
+            const Item it = classify_key(p, valid[j], src[j], pk[j], oc[j], fi[j], la[j]);
+            accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
+        }
+    } else {
+        uint32_t x[R], site[R];
+        bool sl[R], dl[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            local_pair(p, src[j], dst[j], sl[j], dl[j]);
+            x[j] = sl[j] ? dst[j] : src[j];  // the remote endpoint
+        }
+        lookup_sites<LOOKUP, R>(p, sm, valid, x, site);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const Item it = classify(p, valid[j], sl[j], dl[j], pk[j], oc[j], fi[j], la[j], site[j]);
+            accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
+        }
     }
 }
 
@@ -518,7 +628,7 @@ __device__ __forceinline__ void scalar_range(const AggParams& p, const Smem& sm,
             v[j] = i < hi;
             const uint64_t ii = v[j] ? i : lo;
             s[j] = ld_stream1(p.src + ii);
-            d[j] = ld_stream1(p.dst + ii);
+            d[j] = LOOKUP == kLookupKeys ? 0u : ld_stream1(p.dst + ii);
             pk[j] = ld_stream1(p.pkts + ii);
             oc[j] = ld_stream1(p.oct + ii);
             fi[j] = ld_stream1(p.first + ii);
@@ -542,7 +652,8 @@ __device__ __forceinline__ void vector_range(const AggParams& p, const Smem& sm,
             const uint64_t g = gb + (uint64_t)u * B + threadIdx.x;
             const bool ok = g < G;
             const uint64_t i = a0 + 4u * (ok ? g : 0u);
-            const uint4 vs = ld_stream4(p.src + i), vd = ld_stream4(p.dst + i);
+            const uint4 vs = ld_stream4(p.src + i);
+            const uint4 vd = LOOKUP == kLookupKeys ? make_uint4(0, 0, 0, 0) : ld_stream4(p.dst + i);
             const uint4 vp = ld_stream4(p.pkts + i), vo = ld_stream4(p.oct + i);
             const uint4 vf = ld_stream4(p.first + i), vl = ld_stream4(p.last + i);
             s[4 * u + 0] = vs.x; s[4 * u + 1] = vs.y; s[4 * u + 2] = vs.z; s[4 * u + 3] = vs.w;
@@ -555,6 +666,57 @@ __device__ __forceinline__ void vector_range(const AggParams& p, const Smem& sm,
             for (int j = 0; j < 4; ++j) v[4 * u + j] = ok;
         }
         process<LOOKUP, TABLE, AGG, R>(p, sm, gacc, v, s, d, pk, oc, fi, la);
+    }
+}
+
+// Copies the lookup method's shared-memory structure (registry, block samples, radix
+// directory or leaf parameters) to `base` and points `sm` at it.
+template <int LOOKUP>
+__device__ __forceinline__ void stage_lookup(const AggParams& p, unsigned char* base, Smem& sm) {
+    const uint32_t tid = threadIdx.x, B = blockDim.x;
+    if (LOOKUP == kLookupSmem) {
+        uint32_t* st = reinterpret_cast<uint32_t*>(base);
+        uint32_t* si = st + p.n_ranges;
+        for (uint32_t i = tid; i < p.n_ranges; i += B) {
+            st[i] = __ldg(p.starts + i);
+            si[i] = __ldg(p.rsite + i);
+        }
+        sm.s_starts = st;
+        sm.s_site = si;
+    }
+    if (LOOKUP == kLookupStaged) {
+        uint32_t* st = reinterpret_cast<uint32_t*>(base);
+        for (uint32_t i = tid; i < p.n_blocks; i += B) st[i] = __ldg(p.sample + i);
+        sm.s_starts = st;
+    }
+    if (LOOKUP == kLookupRadix) {  // every 2^(16-bits)-th entry of the 16-bit directory
+        uint32_t* d = reinterpret_cast<uint32_t*>(base);
+        const uint32_t nd = 1u << p.radix_bits, sh = 16u - p.radix_bits;
+        for (uint32_t i = tid; i <= nd; i += B) d[i] = __ldg(p.dir16 + ((size_t)i << sh));
+        sm.s_starts = d;
+    }
+    if (LOOKUP == kLookupRadixBlk) {  // every 2^(16-bits)-th entry of the 16-bit block directory
+        uint16_t* d = reinterpret_cast<uint16_t*>(base);
+        const uint32_t nd = 1u << p.radix_bits, sh = 16u - p.radix_bits;
+        for (uint32_t i = tid; i <= nd; i += B) d[i] = p.dirb16[(size_t)i << sh];
+        sm.s_starts = reinterpret_cast<const uint32_t*>(d);
+    }
+    if (LOOKUP == kLookupRmi) {
+        const uint32_t L = p.rmi.n_leaves;
+        float* a = reinterpret_cast<float*>(base);
+        float* b = a + L;
+        uint32_t* x0 = reinterpret_cast<uint32_t*>(b + L);
+        uint32_t* e = x0 + L;
+        for (uint32_t i = tid; i < L; i += B) {
+            a[i] = __ldg(p.rmi.a + i);
+            b[i] = __ldg(p.rmi.b + i);
+            x0[i] = __ldg(p.rmi.x0 + i);
+            e[i] = __ldg(p.rmi.eps + i);
+        }
+        sm.ra = a;
+        sm.rb = b;
+        sm.rx0 = x0;
+        sm.reps = e;
     }
 }
 
@@ -580,44 +742,7 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512)
     for (uint32_t i = tid; i < sm.rows * kRowWords; i += B) sm.t[i] = 0;
     if (TABLE == kTableHash)
         for (uint32_t i = tid; i < p.table_cap; i += B) sm.tk[i] = kEmptyKey;
-    if (LOOKUP == kLookupSmem) {
-        uint32_t* st = reinterpret_cast<uint32_t*>(smem_raw + off_lookup);
-        uint32_t* si = st + p.n_ranges;
-        for (uint32_t i = tid; i < p.n_ranges; i += B) {
-            st[i] = __ldg(p.starts + i);
-            si[i] = __ldg(p.rsite + i);
-        }
-        sm.s_starts = st;
-        sm.s_site = si;
-    }
-    if (LOOKUP == kLookupStaged) {
-        uint32_t* st = reinterpret_cast<uint32_t*>(smem_raw + off_lookup);
-        for (uint32_t i = tid; i < p.n_blocks; i += B) st[i] = __ldg(p.sample + i);
-        sm.s_starts = st;
-    }
-    if (LOOKUP == kLookupRadix) {  // every 2^(16-bits)-th entry of the 16-bit directory
-        uint32_t* d = reinterpret_cast<uint32_t*>(smem_raw + off_lookup);
-        const uint32_t nd = 1u << p.radix_bits, sh = 16u - p.radix_bits;
-        for (uint32_t i = tid; i <= nd; i += B) d[i] = __ldg(p.dir16 + ((size_t)i << sh));
-        sm.s_starts = d;
-    }
-    if (LOOKUP == kLookupRmi) {
-        const uint32_t L = p.rmi.n_leaves;
-        float* a = reinterpret_cast<float*>(smem_raw + off_lookup);
-        float* b = a + L;
-        uint32_t* x0 = reinterpret_cast<uint32_t*>(b + L);
-        uint32_t* e = x0 + L;
-        for (uint32_t i = tid; i < L; i += B) {
-            a[i] = __ldg(p.rmi.a + i);
-            b[i] = __ldg(p.rmi.b + i);
-            x0[i] = __ldg(p.rmi.x0 + i);
-            e[i] = __ldg(p.rmi.eps + i);
-        }
-        sm.ra = a;
-        sm.rb = b;
-        sm.rx0 = x0;
-        sm.reps = e;
-    }
+    stage_lookup<LOOKUP>(p, smem_raw + off_lookup, sm);
     __syncthreads();
 
     for (uint32_t w = first_window(p.wins, p.n_wins, lo); w < p.n_wins; ++w) {
@@ -625,8 +750,20 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512)
         if (wd.begin >= hi) break;
         const uint64_t s0 = max(wd.begin, lo), e0 = min(wd.end, hi);
         uint64_t* gacc = p.acc + (size_t)wd.slot * p.keys * kAccCols;
-        // pieces of at most kFlushRecords records, so the 16-bit counts cannot wrap
-        for (uint64_t s = s0; s < e0; s += kFlushRecords) {
+        // pieces of at most kFlushRecords records, so the 16-bit counts cannot wrap; with a
+        // partial-sum area every piece stores its own block: the blocks of earlier CTAs of
+        // the window come first (the first CTA's segment may be short, the others are full
+        // chunks)
+        uint32_t q = 0;
+        if (TABLE == kTableDirect && p.partials) {
+            const uint64_t f = wd.begin / p.chunk;
+            if (blockIdx.x > f) {
+                const uint64_t len_f = min(wd.end, (f + 1) * p.chunk) - wd.begin;
+                const uint64_t per_full = (p.chunk + kFlushRecords - 1) / kFlushRecords;
+                q = (uint32_t)((len_f + kFlushRecords - 1) / kFlushRecords + (blockIdx.x - f - 1) * per_full);
+            }
+        }
+        for (uint64_t s = s0; s < e0; s += kFlushRecords, ++q) {
             const uint64_t e = min(e0, s + kFlushRecords);
             uint64_t a0 = e, a1 = e;
             if (p.vec_ok) {
@@ -639,7 +776,11 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512)
             scalar_range<LOOKUP, TABLE, AGG>(p, sm, gacc, a1, e);
             if (TABLE != kTableGlobal) {
                 __syncthreads();
-                flush<TABLE>(sm, gacc);
+                if (TABLE == kTableDirect && p.partials) {
+                    dump_rows(sm, p.partials + ((size_t)wd.part_base + q) * p.keys * kRowWords);
+                } else {
+                    flush<TABLE>(sm, gacc);
+                }
                 __syncthreads();
             }
         }
@@ -654,9 +795,106 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512)
             }
         }
         __syncthreads();
-        if (s_last && (wd.flags & kWinFinalize)) finalize_rows(p, wd.slot, tid, B);
+        if (s_last && (wd.flags & kWinFinalize)) {
+            if (TABLE == kTableDirect && p.partials)
+                finalize_rows(p, wd.slot, tid, B, p.partials + (size_t)wd.part_base * p.keys * kRowWords, wd.n_parts);
+            else
+                finalize_rows(p, wd.slot, tid, B);
+        }
         __syncthreads();
     }
+}
+
+// Split launches, first kernel: the key of every record of [0, n_total) (lookups only;
+// the shared memory holds just the lookup structure, so many CTAs fit per SM). The key
+// array has the same 16-byte phase as the record arrays.
+template <int LOOKUP, int U>
+__global__ void __launch_bounds__(U == 1 ? 1024 : 512) k_keys(const __grid_constant__ AggParams p,
+                                                             uint32_t* __restrict__ keys) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem sm;
+    sm.t = nullptr;
+    sm.tk = nullptr;
+    sm.rows = 0;
+    stage_lookup<LOOKUP>(p, smem_raw, sm);
+    __syncthreads();
+    const uint64_t N = p.n_total;
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t a0 = N, a1 = N;
+    if (p.vec_ok) {
+        const uint32_t mis = p.phase & 3u;
+        a0 = mis ? min((uint64_t)(4u - mis), N) : 0;
+        a1 = a0 + ((N - a0) & ~3ull);
+    }
+    // unaligned head and tail (at most 3 + 3 records), or every record when the arrays'
+    // 16-byte phases differ
+    const uint64_t ns = a0 + (N - a1);
+    for (uint64_t t = tid; t < ns; t += T) {
+        const uint64_t i = t < a0 ? t : a1 + (t - a0);
+        const uint32_t src = __ldcs(p.src + i), dst = __ldcs(p.dst + i);
+        bool sl, dl;
+        local_pair(p, src, dst, sl, dl);
+        const bool v[1] = {true};
+        const uint32_t x[1] = {sl ? dst : src};
+        uint32_t site[1];
+        lookup_sites<LOOKUP, 1>(p, sm, v, x, site);
+        keys[i] = record_key(p, sl, dl, site[0]);
+    }
+    constexpr int R = 4 * U;
+    const uint64_t G = (a1 - a0) >> 2;
+    for (uint64_t gb = 0; gb < G; gb += T * U) {
+        bool v[R];
+        uint32_t s[R], d[R], x[R], site[R];
+        bool sl[R], dl[R];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t g = gb + (uint64_t)u * T + tid;
+            const bool ok = g < G;
+            const uint64_t i = a0 + 4u * (ok ? g : 0u);
+            const uint4 vs = ld_stream4(p.src + i), vd = ld_stream4(p.dst + i);
+            s[4 * u + 0] = vs.x; s[4 * u + 1] = vs.y; s[4 * u + 2] = vs.z; s[4 * u + 3] = vs.w;
+            d[4 * u + 0] = vd.x; d[4 * u + 1] = vd.y; d[4 * u + 2] = vd.z; d[4 * u + 3] = vd.w;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[4 * u + j] = ok;
+        }
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            local_pair(p, s[j], d[j], sl[j], dl[j]);
+            x[j] = sl[j] ? d[j] : s[j];
+        }
+        lookup_sites<LOOKUP, R>(p, sm, v, x, site);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t g = gb + (uint64_t)u * T + tid;
+            if (g < G) {
+                uint4 k;
+                k.x = record_key(p, sl[4 * u + 0], dl[4 * u + 0], site[4 * u + 0]);
+                k.y = record_key(p, sl[4 * u + 1], dl[4 * u + 1], site[4 * u + 1]);
+                k.z = record_key(p, sl[4 * u + 2], dl[4 * u + 2], site[4 * u + 2]);
+                k.w = record_key(p, sl[4 * u + 3], dl[4 * u + 3], site[4 * u + 3]);
+                __stcg(reinterpret_cast<uint4*>(keys + a0 + 4u * g), k);
+            }
+        }
+    }
+}
+
+template <int LOOKUP>
+cudaError_t launch_keys_impl(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st) {
+    auto k = s.unroll == 2 ? k_keys<LOOKUP, 2> : k_keys<LOOKUP, 1>;
+    static int set_bytes[64][2];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int ui = s.unroll == 2 ? 1 : 0;
+    if (s.keys_smem >= 46 * 1024 && (dev >= 64 || set_bytes[dev][ui] < (int)s.keys_smem)) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.keys_smem);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) set_bytes[dev][ui] = (int)s.keys_smem;
+    }
+    (void)cudaGetLastError();
+    k<<<s.keys_grid, s.keys_block, s.keys_smem, st>>>(p, keys);
+    return cudaGetLastError();
 }
 
 template <int LOOKUP, int TABLE, int AGG, int U>

@@ -1,8 +1,11 @@
-// agg_staged.cu -- aggregation kernel variants for one prefix-match mode (see agg_kernel.cuh).
+// agg_staged.cu -- aggregation and key kernels for one prefix-match mode (see agg_kernel.cuh).
 #include "agg_kernel.cuh"
 
 namespace gnm {
 cudaError_t launch_aggregate_staged(const AggParams& p, const LaunchShape& s, cudaStream_t st) {
     return dev::launch_lookup_mode<kLookupStaged>(p, s, st);
+}
+cudaError_t launch_keys_staged(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st) {
+    return dev::launch_keys_impl<kLookupStaged>(p, s, keys, st);
 }
 }  // namespace gnm

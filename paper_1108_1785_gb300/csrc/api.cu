@@ -27,7 +27,8 @@ constexpr size_t kRegistrySmemMax = 96 * 1024;   // bytes of ranges kept in shar
 constexpr size_t kSampleSmemMax = 96 * 1024;     // bytes of block samples (staged placement)
 constexpr size_t kDirectTableMax = 208 * 1024;   // direct-indexed per-CTA sums
 constexpr size_t kHashTableMax = 200 * 1024;     // hashed per-CTA sums
-constexpr uint32_t kFinalizeInKernelMaxKeys = 65536;
+constexpr uint32_t kFinalizeInCtaMaxKeys = 4096;
+constexpr uint64_t kPartialBytesMax = 1ull << 30;  // per launch; larger launches flush atomically
 constexpr uint64_t kMaxWindowRecords = 0xFFFFFFFFull;
 
 static uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
@@ -192,7 +193,9 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
     const gnm_config& cfg = c->cfg;
     const uint32_t nr = (uint32_t)c->h_starts.size();
     int mode = cfg.lookup_mode;
-    if (mode == GNM_LOOKUP_AUTO) mode = c->rmi_ready ? GNM_LOOKUP_RMI : GNM_LOOKUP_RADIX;
+    if (mode == GNM_LOOKUP_AUTO)  // a registry that fits shared memory is searched there directly
+        mode = c->rmi_ready ? GNM_LOOKUP_RMI
+               : (size_t)nr * 8 <= kRegistrySmemMax ? GNM_LOOKUP_BSEARCH : GNM_LOOKUP_RADIX;
     if (mode == GNM_LOOKUP_RMI && !c->rmi_ready)
         return fail(GNM_E_STATE, "lookup mode RMI requested but no learned index is trained");
     size_t lookup_bytes = 0;
@@ -216,8 +219,6 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
         s->lookup = kLookupRadix;
         s->radix_bits = bits;
         lookup_bytes = ((size_t)1 << bits) * 4 + 4;
-        if (lookup_bytes + 1024 > (size_t)c->smem_optin)
-            return fail(GNM_E_INVAL, "radix directory too large for shared memory");
     } else if (mode == GNM_LOOKUP_BSEARCH) {
         int place = cfg.placement != GNM_PLACE_AUTO ? cfg.placement : c->tuned.placement;
         const size_t sample_bytes = (size_t)c->n_blocks * 4;
@@ -243,6 +244,27 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
     } else {
         return fail(GNM_E_INVAL, "unknown lookup mode");
     }
+    // split launches: the lookup structure lives in the key kernel only
+    int split = cfg.split != GNM_SPLIT_AUTO ? cfg.split : c->tuned.split;
+    if (split == GNM_SPLIT_AUTO) split = s->lookup == kLookupSmem ? GNM_SPLIT_FUSED : GNM_SPLIT_TWO_KERNELS;
+    if (split != GNM_SPLIT_FUSED && split != GNM_SPLIT_TWO_KERNELS) return fail(GNM_E_INVAL, "unknown split mode");
+    s->split = split == GNM_SPLIT_TWO_KERNELS;
+    s->keys_smem = s->split ? (lookup_bytes + 15) / 16 * 16 : 0;
+    s->keys_blk = 0;
+    s->keys_bits = 0;
+    if (s->split && s->lookup == kLookupRadix && c->n_blk8 && cfg.key_directory == 1) {
+        // 16-bit block directory in the key kernel (it has shared memory to spare)
+        uint32_t kb = cfg.radix_bits ? cfg.radix_bits : (c->tuned.radix_bits ? c->tuned.radix_bits : 15);
+        if (kb < 4 || kb > 16) return fail(GNM_E_INVAL, "radix_bits must be 4..16");
+        s->keys_blk = 1;
+        s->keys_bits = kb;
+        s->keys_smem = ((((size_t)1 << kb) + 1) * 2 + 15) / 16 * 16;
+    }
+    if (s->split && s->keys_smem + 1024 > (size_t)c->smem_optin)
+        return fail(GNM_E_INVAL, "lookup structure too large for shared memory");
+    if (!s->split && s->lookup == kLookupRadix && lookup_bytes + 1024 > (size_t)c->smem_optin)
+        return fail(GNM_E_INVAL, "radix directory too large for shared memory");
+    if (s->split) lookup_bytes = 0;
     const size_t budget = (size_t)c->smem_optin > lookup_bytes + 1024 ? (size_t)c->smem_optin - lookup_bytes - 1024 : 0;
     const size_t direct = (size_t)c->keys * kSmemRowBytes;
     const size_t row = kSmemRowBytes + 4;
@@ -278,8 +300,8 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
     if (unroll == 2 && block > 512) unroll = 1;
     s->block = block;
     s->unroll = unroll;
-    s->smem = aggregate_smem_bytes(s->lookup, s->table, nr, c->keys, cap, s->lookup == kLookupRmi ? c->rmi.n_leaves : 0,
-                                   s->radix_bits);
+    s->smem = aggregate_smem_bytes(s->split ? kLookupKeys : s->lookup, s->table, nr, c->keys, cap,
+                                   s->lookup == kLookupRmi ? c->rmi.n_leaves : 0, s->radix_bits);
     if (s->smem > (size_t)c->smem_optin) return fail(GNM_E_INVAL, "shared-memory layout exceeds the device limit");
     int cps = cfg.ctas_per_sm ? cfg.ctas_per_sm : c->tuned.ctas_per_sm;
     const int by_threads = std::max(1, 2048 / block);
@@ -291,6 +313,15 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
     const uint64_t min_per_cta = (uint64_t)block * 8;  // at least two groups of 4 per thread
     uint64_t grid = std::min<uint64_t>(resident, std::max<uint64_t>(1, ceil_div(n, min_per_cta)));
     s->grid = (int)grid;
+    if (s->split) {  // key kernel: as many CTAs per SM as its shared memory allows
+        s->keys_block = s->unroll == 2 ? 512 : 1024;
+        const int kfit = std::max(1, std::min(2048 / s->keys_block, (int)(c->smem_per_sm / (s->keys_smem + 1024))));
+        const uint64_t kres = (uint64_t)c->sm_count * kfit;
+        s->keys_grid = (int)std::min<uint64_t>(kres, std::max<uint64_t>(1, ceil_div(n, (uint64_t)s->keys_block * 4 * s->unroll)));
+    } else {
+        s->keys_block = 0;
+        s->keys_grid = 0;
+    }
     s->cap = cap;
     return GNM_OK;
 }
@@ -308,6 +339,10 @@ gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p) {
     p->blocks = reinterpret_cast<const uint4*>(c->d_blocks);
     p->sample = c->d_sample;
     p->dir16 = c->d_dir16;
+    p->blk8 = reinterpret_cast<const uint4*>(c->d_blk8);
+    p->sample8 = c->d_sample8;
+    p->dirb16 = c->d_dirb16;
+    p->n_blk8 = c->n_blk8;
     p->n_blocks = c->n_blocks;
     p->n_ranges = (uint32_t)c->h_starts.size();
     p->n_sites = c->n_sites;
@@ -378,7 +413,11 @@ gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* off
     for (auto* q : f)
         if (((uintptr_t)q & 15u) != a0) p.vec_ok = 0;
     p.phase = (uint32_t)(a0 >> 2);
-    out->fin_in_kernel = finalize && c->keys <= kFinalizeInKernelMaxKeys;
+    // one CTA finalises a window in place when its key space is small; larger ones are
+    // finalised by a grid-wide kernel after the aggregation (partial sums or per window)
+    out->fin_in_kernel = finalize && c->keys <= kFinalizeInCtaMaxKeys;
+    out->fin_grid = finalize && !out->fin_in_kernel;
+    uint64_t parts = 0;
     for (size_t k = 0; k < n_win; ++k) {
         const uint64_t b = offsets[k] - base, e = offsets[k + 1] - base;
         if (b == e) continue;
@@ -388,28 +427,52 @@ gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* off
         w.slot = slots[k];
         w.flags = out->fin_in_kernel ? kWinFinalize : 0u;
         w.ctas = (uint32_t)((e - 1) / chunk - b / chunk + 1);
+        w.part_base = (uint32_t)parts;
+        uint64_t np = 0;  // one block per flush piece of every CTA segment of the window
+        for (uint64_t cta = b / chunk; cta <= (e - 1) / chunk; ++cta) {
+            const uint64_t len = std::min(e, (cta + 1) * chunk) - std::max(b, cta * chunk);
+            np += (len + kFlushRecords - 1) / kFlushRecords;
+        }
+        w.n_parts = (uint32_t)np;
         w.pad = 0;
+        parts += np;
         out->wins.push_back(w);
+    }
+    // direct tables of finalising launches hand their sums over through plain stores
+    out->partial_words = 0;
+    if (sh.table == kTableDirect && (out->fin_in_kernel || out->fin_grid)) {
+        const uint64_t words = parts * c->keys * (kSmemRowBytes / 4);
+        if (words * 4 <= kPartialBytesMax) out->partial_words = words;
     }
     return GNM_OK;
 }
 
 gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, size_t n_win,
                             const uint32_t* slots, bool finalize, WinDesc* d_wins, uint32_t* d_done,
-                            cudaStream_t st, uint32_t* launches) {
+                            uint32_t* d_partials, uint32_t* d_keys, cudaStream_t st, uint32_t* launches) {
     *launches = 0;
     if (pr.n) {
         pr.p.wins = d_wins;
         pr.p.n_wins = (uint32_t)pr.wins.size();
         pr.p.done = d_done;
-        GNM_CU(launch_aggregate(pr.p, pr.sh, st));
+        pr.p.partials = pr.partial_words ? d_partials : nullptr;
+        if (pr.sh.split) {  // keys first (same 16-byte phase as the records), then the sums
+            uint32_t* keys = d_keys + pr.p.phase;
+            AggParams pk = pr.p;
+            if (pr.sh.keys_blk) pk.radix_bits = pr.sh.keys_bits;
+            GNM_CU(launch_keys(pk, pr.sh, keys, st));
+            ++*launches;
+            AggParams pa = pr.p;
+            pa.src = keys;
+            pa.dst = keys;
+            GNM_CU(launch_aggregate(pa, pr.sh, st));
+        } else {
+            GNM_CU(launch_aggregate(pr.p, pr.sh, st));
+        }
         ++*launches;
-        if (finalize && !pr.fin_in_kernel) {
-            for (size_t k = 0; k < n_win; ++k) {
-                if (offsets[k + 1] == offsets[k]) continue;
-                GNM_CU(launch_finalize(pr.p, slots[k], st));
-                ++*launches;
-            }
+        if (finalize && pr.fin_grid) {
+            GNM_CU(launch_finalize_windows(pr.p, st));
+            ++*launches;
         }
     }
     // empty windows: zero sums, no rate, no flag
@@ -461,12 +524,27 @@ static gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t
     GNM_TRY(prepare_launch(c, &dr, offsets, n_win, slot.data(), finalize, &pr));
     LaunchBuf* lb;
     GNM_TRY(acquire_ring(c, (uint32_t)n_win, &lb));
+    const uint64_t key_words = pr.sh.split ? pr.n + 4 : 0;
+    if (key_words > lb->keys_cap) {  // grow this entry's key array
+        free_dev(lb->d_keys);
+        lb->d_keys = nullptr;
+        lb->keys_cap = 0;
+        GNM_CU(cudaMalloc(&lb->d_keys, key_words * 4));
+        lb->keys_cap = key_words;
+    }
+    if (pr.partial_words > lb->partial_cap) {  // grow this entry's partial-sum area
+        free_dev(lb->d_partials);
+        lb->d_partials = nullptr;
+        lb->partial_cap = 0;
+        GNM_CU(cudaMalloc(&lb->d_partials, pr.partial_words * 4));
+        lb->partial_cap = pr.partial_words;
+    }
     if (!pr.wins.empty()) {
         std::memcpy(lb->h_wins, pr.wins.data(), sizeof(WinDesc) * pr.wins.size());
         GNM_CU(cudaMemcpyAsync(lb->d_wins, lb->h_wins, sizeof(WinDesc) * pr.wins.size(), cudaMemcpyHostToDevice, st));
     }
-    GNM_TRY(enqueue_prepared(c, pr, offsets, n_win, slot.data(), finalize, lb->d_wins, lb->d_done, st,
-                             &c->last_launches));
+    GNM_TRY(enqueue_prepared(c, pr, offsets, n_win, slot.data(), finalize, lb->d_wins, lb->d_done,
+                             lb->d_partials, lb->d_keys, st, &c->last_launches));
     GNM_CU(cudaEventRecord(lb->ev, st));
     lb->ev_recorded = true;
     for (size_t k = 0; k < n_win; ++k) c->slots[slot[k]].records += offsets[k + 1] - offsets[k];
@@ -554,6 +632,8 @@ void gnm_destroy(gnm_ctx* c) {
         if (b.h_wins) cudaFreeHost(b.h_wins);
         free_dev(b.d_wins);
         free_dev(b.d_done);
+        free_dev(b.d_partials);
+        free_dev(b.d_keys);
         if (b.ev) cudaEventDestroy(b.ev);
     }
     for (auto* p : c->staging.d) free_dev(p);
@@ -564,6 +644,9 @@ void gnm_destroy(gnm_ctx* c) {
     free_dev(c->d_blocks);
     free_dev(c->d_sample);
     free_dev(c->d_dir16);
+    free_dev(c->d_blk8);
+    free_dev(c->d_sample8);
+    free_dev(c->d_dirb16);
     free_dev(c->d_violations);
     free_dev(c->d_flag_count);
     free_dev(c->d_rmi_a);
@@ -604,7 +687,14 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     free_dev(c->d_blocks);
     free_dev(c->d_sample);
     free_dev(c->d_dir16);
+    free_dev(c->d_blk8);
+    free_dev(c->d_sample8);
+    free_dev(c->d_dirb16);
     c->d_dir16 = nullptr;
+    c->d_blk8 = nullptr;
+    c->d_sample8 = nullptr;
+    c->d_dirb16 = nullptr;
+    c->n_blk8 = 0;
     c->d_starts = nullptr;
     c->d_site = nullptr;
     c->d_blocks = nullptr;
@@ -643,6 +733,29 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     }
     GNM_CU(cudaMalloc(&c->d_dir16, dir.size() * 4));
     GNM_CU(cudaMemcpy(c->d_dir16, dir.data(), dir.size() * 4, cudaMemcpyHostToDevice));
+    // key-kernel layout: 8-range blocks carrying their sites, and a 16-bit directory of
+    // block indices (when the block count fits 16 bits)
+    const size_t nb8 = (nr + 7) / 8;
+    if (nb8 < 65536) {
+        std::vector<uint32_t> b8(nb8 * 16), s8(nb8);
+        std::vector<uint16_t> db(65537);
+        for (size_t j = 0; j < nb8; ++j) {
+            for (size_t k = 0; k < 8; ++k) {
+                const size_t i = j * 8 + k;
+                b8[j * 16 + k] = i < nr ? starts[i] : 0xFFFFFFFFu;
+                b8[j * 16 + 8 + k] = i < nr ? sites[i] : sites[nr - 1];
+            }
+            s8[j] = starts[j * 8];
+        }
+        for (size_t t = 0; t <= 65536; ++t) db[t] = (uint16_t)(dir[t] / 8);
+        GNM_CU(cudaMalloc(&c->d_blk8, b8.size() * 4));
+        GNM_CU(cudaMalloc(&c->d_sample8, s8.size() * 4));
+        GNM_CU(cudaMalloc(&c->d_dirb16, db.size() * 2));
+        GNM_CU(cudaMemcpy(c->d_blk8, b8.data(), b8.size() * 4, cudaMemcpyHostToDevice));
+        GNM_CU(cudaMemcpy(c->d_sample8, s8.data(), s8.size() * 4, cudaMemcpyHostToDevice));
+        GNM_CU(cudaMemcpy(c->d_dirb16, db.data(), db.size() * 2, cudaMemcpyHostToDevice));
+        c->n_blk8 = (uint32_t)nb8;
+    }
     GNM_CU(cudaMalloc(&c->d_blocks, blk.size() * 4));
     GNM_CU(cudaMalloc(&c->d_sample, nb * 4));
     GNM_CU(cudaMemcpy(c->d_blocks, blk.data(), blk.size() * 4, cudaMemcpyHostToDevice));

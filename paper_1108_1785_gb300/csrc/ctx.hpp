@@ -53,6 +53,10 @@ struct LaunchBuf {
     WinDesc* d_wins = nullptr;
     uint32_t* d_done = nullptr;  // zero between launches (each launch resets it)
     uint32_t cap = 0;
+    uint32_t* d_partials = nullptr;  // per-(window, CTA) partial sums
+    uint64_t partial_cap = 0;        // in u32 words
+    uint32_t* d_keys = nullptr;      // per-record keys of split launches
+    uint64_t keys_cap = 0;           // in u32 words
     cudaEvent_t ev = nullptr;
     bool ev_recorded = false;
 };
@@ -65,7 +69,7 @@ struct Staging {
 };
 
 struct Tuned {
-    int block = 0, ctas_per_sm = 0, unroll = 0, agg = 0, placement = 0;
+    int block = 0, ctas_per_sm = 0, unroll = 0, agg = 0, placement = 0, split = 0;
     uint32_t radix_bits = 0;
 };
 
@@ -89,6 +93,10 @@ struct gnm_ctx {
     uint32_t* d_sample = nullptr;   // staged placement: first start of every block
     uint32_t n_blocks = 0;
     uint32_t* d_dir16 = nullptr;    // radix directory: range of each /16's first address
+    uint32_t* d_blk8 = nullptr;     // key kernel: blocks of 8 ranges (8 starts, 8 sites)
+    uint32_t* d_sample8 = nullptr;  // key kernel: first start of every 8-range block
+    uint16_t* d_dirb16 = nullptr;   // key kernel: 8-range block of each /16's first address
+    uint32_t n_blk8 = 0;
     uint32_t local_pfx[GNM_MAX_LOCAL] = {0};
     uint32_t local_mask[GNM_MAX_LOCAL] = {0};
     uint32_t n_local = 0;
@@ -139,14 +147,16 @@ struct Prepared {
     LaunchShape sh;
     std::vector<WinDesc> wins;   // non-empty windows only
     bool fin_in_kernel = false;
+    bool fin_grid = false;       // finalise in a grid-wide kernel after the aggregation
     uint64_t n = 0;
+    uint64_t partial_words = 0;  // u32 words of per-(window, CTA) partial sums (0: none)
 };
 gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* offsets, size_t n_win,
                           const uint32_t* slots, bool finalize, Prepared* out);
 // Enqueues the kernels of a prepared launch (descriptors already on the device).
 gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, size_t n_win,
                             const uint32_t* slots, bool finalize, WinDesc* d_wins, uint32_t* d_done,
-                            cudaStream_t st, uint32_t* launches);
+                            uint32_t* d_partials, uint32_t* d_keys, cudaStream_t st, uint32_t* launches);
 // Next launch-scratch entry of the ring (waits for its previous use).
 gnm_status acquire_ring(gnm_ctx* c, uint32_t n_win, LaunchBuf** out);
 void set_slots_done(gnm_ctx* c, const uint32_t* slots, size_t n, cudaEvent_t ev, bool finalized);

@@ -20,11 +20,15 @@ constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 // One window of a launch: records [begin, end) of the launch's struct-of-arrays.
 struct WinDesc {
     uint64_t begin, end;
-    uint32_t slot;    // result slot
-    uint32_t flags;   // kWinFinalize
-    uint32_t ctas;    // CTAs whose record range overlaps the window (ticket target)
+    uint32_t slot;       // result slot
+    uint32_t flags;      // kWinFinalize
+    uint32_t ctas;       // CTAs whose record range overlaps the window (ticket target)
+    uint32_t part_base;  // first partial-sum block of the window (when partials are used)
+    uint32_t n_parts;    // partial-sum blocks of the window (one per CTA piece)
     uint32_t pad;
 };
+// A CTA flushes its shared sums at least every kFlushRecords records (16-bit counts).
+constexpr uint64_t kFlushRecords = 65532;  // < 2^16, multiple of 4
 constexpr uint32_t kWinFinalize = 1u;
 
 // Learned index: root parameters by value, per-leaf arrays in device memory.
@@ -61,6 +65,10 @@ struct AggParams {
     const uint32_t* sample;      // staged placement: first start of every block
     const uint32_t* dir16;       // radix directory over the top 16 bits (65537 entries)
     uint32_t radix_bits;         // directory bits used by this launch (<= 16)
+    const uint4* blk8;           // key kernel: blocks of 8 ranges (8 starts, then 8 sites)
+    const uint32_t* sample8;     // key kernel: first start of every 8-range block
+    const uint16_t* dirb16;      // key kernel: 8-range block of each /16's first address
+    uint32_t n_blk8;
     uint32_t n_blocks;
     uint32_t n_ranges;
     uint32_t n_sites;
@@ -85,11 +93,17 @@ struct AggParams {
     uint32_t pad0;
     double threshold;
     // scratch
+    uint32_t* partials;          // per (window, CTA) dumps of the shared rows, or null
     uint32_t* done;              // [n_wins] finalise tickets, zero between launches
     unsigned long long* violations;  // learned-index fallbacks
 };
 
-enum { kLookupL2 = 0, kLookupSmem = 1, kLookupRmi = 2, kLookupStaged = 3, kLookupRadix = 4 };
+// kLookupKeys: the aggregation reads per-record keys that a lookup kernel wrote (split
+// launches), instead of addresses.
+// kLookupRadixBlk (key kernel only): 16-bit block directory in shared memory, one 64-byte
+// block of 8 starts and 8 sites from L2.
+enum { kLookupL2 = 0, kLookupSmem = 1, kLookupRmi = 2, kLookupStaged = 3, kLookupRadix = 4, kLookupKeys = 5,
+       kLookupRadixBlk = 6 };
 constexpr uint32_t kBlockRanges = 16;  // ranges per staged block (16 starts, 64 bytes)
 enum { kTableDirect = 0, kTableHash = 1, kTableGlobal = 2 };
 
@@ -105,13 +119,23 @@ struct LaunchShape {
     uint32_t cap;    // hash-table slots (kTableHash)
     uint32_t radix_bits;  // kLookupRadix directory bits
     size_t smem;
+    // split launches: a lookup kernel (this lookup method) writes keys, then the
+    // aggregation kernel reads them (kLookupKeys)
+    int split;
+    int keys_grid, keys_block;
+    size_t keys_smem;
+    int keys_blk;          // radix key kernel uses the 16-bit block directory
+    uint32_t keys_bits;    // its directory bits
 };
 
 // aggregate*.cu
 cudaError_t launch_aggregate(const AggParams& p, const LaunchShape& s, cudaStream_t st);
+cudaError_t launch_keys(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
 size_t aggregate_smem_bytes(int lookup, int table, uint32_t n_ranges, uint32_t keys,
                             uint32_t table_cap, uint32_t n_leaves, uint32_t radix_bits);
 cudaError_t launch_finalize(const AggParams& p, uint32_t slot, cudaStream_t st);
+// Finalises every window of a launch from its partial-sum blocks (grid over windows x keys).
+cudaError_t launch_finalize_windows(const AggParams& p, cudaStream_t st);
 cudaError_t launch_flag_compact(const double* rate, const uint64_t* stats, uint32_t n_site_keys,
                                 double thr, uint32_t min_flows, uint32_t* out_keys,
                                 uint32_t* out_count, cudaStream_t st);

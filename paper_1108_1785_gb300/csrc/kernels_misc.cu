@@ -9,8 +9,27 @@ cudaError_t launch_aggregate_smem(const AggParams& p, const LaunchShape& s, cuda
 cudaError_t launch_aggregate_rmi(const AggParams& p, const LaunchShape& s, cudaStream_t st);
 cudaError_t launch_aggregate_staged(const AggParams& p, const LaunchShape& s, cudaStream_t st);
 cudaError_t launch_aggregate_radix(const AggParams& p, const LaunchShape& s, cudaStream_t st);
+cudaError_t launch_aggregate_keys(const AggParams& p, const LaunchShape& s, cudaStream_t st);
+cudaError_t launch_keys_l2(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
+cudaError_t launch_keys_smem(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
+cudaError_t launch_keys_rmi(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
+cudaError_t launch_keys_staged(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
+cudaError_t launch_keys_radix(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
+cudaError_t launch_keys_radixblk(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
+
+cudaError_t launch_keys(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st) {
+    switch (s.lookup) {
+        case kLookupSmem: return launch_keys_smem(p, s, keys, st);
+        case kLookupRmi: return launch_keys_rmi(p, s, keys, st);
+        case kLookupStaged: return launch_keys_staged(p, s, keys, st);
+        case kLookupRadix:
+            return s.keys_blk ? launch_keys_radixblk(p, s, keys, st) : launch_keys_radix(p, s, keys, st);
+        default: return launch_keys_l2(p, s, keys, st);
+    }
+}
 
 cudaError_t launch_aggregate(const AggParams& p, const LaunchShape& s, cudaStream_t st) {
+    if (s.split) return launch_aggregate_keys(p, s, st);
     switch (s.lookup) {
         case kLookupSmem: return launch_aggregate_smem(p, s, st);
         case kLookupRmi: return launch_aggregate_rmi(p, s, st);
@@ -30,6 +49,14 @@ namespace {
 
 __global__ void k_finalize(const __grid_constant__ AggParams p, uint32_t slot) {
     dev::finalize_rows(p, slot, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// blockIdx.y: window of the launch; its keys are spread over blockIdx.x.
+__global__ void k_finalize_windows(const __grid_constant__ AggParams p) {
+    const WinDesc wd = p.wins[blockIdx.y];
+    const uint32_t* parts = p.partials ? p.partials + (size_t)wd.part_base * p.keys * 5 : nullptr;
+    dev::finalize_rows(p, wd.slot, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, parts,
+                       p.partials ? wd.n_parts : 0u);
 }
 
 // Keys (site*2+dir) whose eligible flows reach min_flows and whose rate is strictly
@@ -113,6 +140,14 @@ cudaError_t launch_finalize(const AggParams& p, uint32_t slot, cudaStream_t st) 
     const uint32_t blocks = (p.keys + 255) / 256;
     (void)cudaGetLastError();
     k_finalize<<<blocks > 4096 ? 4096 : blocks, 256, 0, st>>>(p, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_windows(const AggParams& p, cudaStream_t st) {
+    if (p.n_wins == 0) return cudaSuccess;
+    const uint32_t bx = (p.keys + 255) / 256;
+    (void)cudaGetLastError();
+    k_finalize_windows<<<dim3(bx > 64 ? 64 : bx, p.n_wins), 256, 0, st>>>(p);
     return cudaGetLastError();
 }
 

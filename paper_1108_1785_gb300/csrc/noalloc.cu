@@ -184,6 +184,8 @@ extern "C" gnm_status gnm_window_process_noalloc(const gnm_config* cfg_in, const
     d.slot = 0;
     d.flags = kWinFinalize;
     d.ctas = (uint32_t)grid;
+    d.part_base = 0;
+    d.n_parts = 0;
     d.pad = 0;
     (void)cudaGetLastError();
     k_noalloc_desc<<<1, 1, 0, st>>>(d);

@@ -21,6 +21,8 @@ struct gnm_plan {
     cudaGraphExec_t exec = nullptr;
     gnm::WinDesc* d_wins = nullptr;
     uint32_t* d_done = nullptr;
+    uint32_t* d_partials = nullptr;
+    uint32_t* d_keys = nullptr;
     std::vector<uint32_t> slots;
     cudaEvent_t ev = nullptr;
     uint32_t launches = 0;
@@ -42,6 +44,8 @@ static void plan_free(gnm_plan* p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->d_wins) cudaFree(p->d_wins);
     if (p->d_done) cudaFree(p->d_done);
+    if (p->d_partials) cudaFree(p->d_partials);
+    if (p->d_keys) cudaFree(p->d_keys);
     if (p->ev) cudaEventDestroy(p->ev);
     delete p;
 }
@@ -88,7 +92,9 @@ gnm_status gnm_plan_create(gnm_ctx* c, const gnm_records* rec, const uint64_t* o
         cudaMemset(p->d_done, 0, sizeof(uint32_t) * nw) != cudaSuccess ||
         (pr.wins.size() && cudaMemcpy(p->d_wins, pr.wins.data(), sizeof(WinDesc) * pr.wins.size(),
                                       cudaMemcpyHostToDevice) != cudaSuccess) ||
-        cudaEventCreateWithFlags(&p->ev, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&p->ev, cudaEventDisableTiming) != cudaSuccess ||
+        (pr.partial_words && cudaMalloc(&p->d_partials, pr.partial_words * 4) != cudaSuccess) ||
+        (pr.sh.split && pr.n && cudaMalloc(&p->d_keys, (pr.n + 4) * 4) != cudaSuccess))
         return bail(fail(GNM_E_CUDA, "plan allocation failed"));
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
@@ -96,7 +102,8 @@ gnm_status gnm_plan_create(gnm_ctx* c, const gnm_records* rec, const uint64_t* o
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        st = enqueue_prepared(c, pr, offsets, n_win, p->slots.data(), true, p->d_wins, p->d_done, cs, &p->launches);
+        st = enqueue_prepared(c, pr, offsets, n_win, p->slots.data(), true, p->d_wins, p->d_done, p->d_partials,
+                              p->d_keys, cs, &p->launches);
         e = cudaStreamEndCapture(cs, &g);
     }
     if (e == cudaSuccess && st == GNM_OK) e = cudaGraphInstantiate(&p->exec, g, 0);
@@ -174,6 +181,10 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
         else places_v.assign(std::begin(places), std::end(places));
     }
     const int cpss[] = {0, 1};
+    std::vector<int> splits_v;
+    if (base_shape.lookup == kLookupSmem) splits_v.push_back(GNM_SPLIT_FUSED);
+    else splits_v = {GNM_SPLIT_FUSED, GNM_SPLIT_TWO_KERNELS};
+    for (int sp : splits_v)
     for (int b : blocks)
         for (int u : unrolls)
             for (int a : aggs)
@@ -189,6 +200,7 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
                             if (c->cfg.placement == GNM_PLACE_AUTO) c->cfg.placement = pl;
                             if (c->cfg.radix_bits == 0) c->cfg.radix_bits = (uint32_t)rb;
                             if (c->cfg.ctas_per_sm == 0) c->cfg.ctas_per_sm = cps;
+                            if (c->cfg.split == GNM_SPLIT_AUTO) c->cfg.split = sp;
                             LaunchShape sh;
                             if (choose_shape(c, offsets[n_win] - offsets[0], &sh) != GNM_OK) continue;  // does not fit
                             double ms;
@@ -202,6 +214,7 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
                                 rep->placement = c->cfg.placement;
                                 rep->ctas_per_sm = sh.ctas_per_sm;
                                 rep->radix_bits = sh.radix_bits;
+                                rep->split = sh.split ? GNM_SPLIT_TWO_KERNELS : GNM_SPLIT_FUSED;
                             }
                         }
     c->cfg = saved;
@@ -217,6 +230,7 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
     c->tuned.placement = rep->placement;
     c->tuned.ctas_per_sm = rep->ctas_per_sm;
     c->tuned.radix_bits = rep->radix_bits;
+    c->tuned.split = rep->split;
     // leave the windows holding the results of the chosen shape
     return gnm_windows_process(c, rec, offsets, wids, n_win, st) == GNM_OK && cudaStreamSynchronize(st) == cudaSuccess
                ? GNM_OK

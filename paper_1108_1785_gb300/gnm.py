@@ -23,6 +23,7 @@ PLACE_AUTO, PLACE_SMEM, PLACE_L2, PLACE_STAGED = 0, 1, 2, 3
 AGG_AUTO, AGG_DIRECT, AGG_WARP = 0, 1, 2
 ADMIN_OR, ADMIN_AND = 0, 1
 TABLE_AUTO, TABLE_DIRECT, TABLE_HASH, TABLE_GLOBAL = 0, 1, 2, 3
+SPLIT_AUTO, SPLIT_FUSED, SPLIT_TWO_KERNELS = 0, 1, 2
 ROOT_LINEAR, ROOT_MLP = 0, 1
 FIELDS = ("srcaddr", "dstaddr", "dPkts", "dOctets", "first", "last")
 
@@ -42,7 +43,8 @@ class Config(C.Structure):
                 ("placement", C.c_int32), ("aggregation", C.c_int32), ("device", C.c_int32),
                 ("window_slots", C.c_uint32), ("threshold_bps", C.c_double), ("block_threads", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("unroll", C.c_int32), ("table_mode", C.c_int32),
-                ("hash_slots", C.c_uint32), ("radix_bits", C.c_uint32)]
+                ("hash_slots", C.c_uint32), ("radix_bits", C.c_uint32), ("split", C.c_int32),
+                ("key_directory", C.c_int32)]
 
 
 class RecordsC(C.Structure):
@@ -78,7 +80,8 @@ class RmiReport(C.Structure):
 class TuneReport(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("unroll", C.c_int32),
                 ("aggregation", C.c_int32), ("placement", C.c_int32), ("best_ms", C.c_double),
-                ("default_ms", C.c_double), ("n_tried", C.c_uint32), ("radix_bits", C.c_uint32)]
+                ("default_ms", C.c_double), ("n_tried", C.c_uint32), ("radix_bits", C.c_uint32),
+                ("split", C.c_int32)]
 
 
 _lib = None

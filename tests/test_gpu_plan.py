@@ -39,7 +39,7 @@ def test_plan_replays_match_oracle(gnm, batch):
     plan = ctx.plan(d, off, ids)
     for rep in range(3):
         plan.launch()
-        assert ctx.last_launch_count() == 1
+        assert ctx.last_launch_count() == 1  # shared-memory registry: one fused kernel
         for w in range(len(ids)):
             assert_window_matches(ctx.dense(int(ids[w])), expect[w])
     with pytest.raises(gnm.GnmError, match="plan"):

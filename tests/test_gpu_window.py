@@ -70,18 +70,21 @@ def test_hand_window(gnm):
 
 LOOKUPS = [("BSEARCH", "SMEM", 0), ("BSEARCH", "STAGED", 0), ("BSEARCH", "L2", 0), ("RADIX", "AUTO", 0),
            ("RADIX", "AUTO", 5)]
+SPLITS = ["AUTO", "TWO_KERNELS"]
 
 
 @pytest.mark.parametrize("table", ["DIRECT", "HASH", "GLOBAL"])
 @pytest.mark.parametrize("agg", ["DIRECT", "WARP"])
 @pytest.mark.parametrize("lookup", LOOKUPS, ids=lambda l: f"{l[0]}-{l[1]}-{l[2]}")
 @pytest.mark.parametrize("unroll,block", [(1, 256), (2, 512), (1, 1024)])
-def test_c1_window_all_variants(gnm, c1, table, agg, lookup, unroll, block):
+@pytest.mark.parametrize("split", SPLITS)
+def test_c1_window_all_variants(gnm, c1, table, agg, lookup, unroll, block, split):
     reg, rec, expect = c1
     mode, place, bits = lookup
     ctx = _ctx(gnm, reg, table_mode=getattr(gnm, "TABLE_" + table), aggregation=getattr(gnm, "AGG_" + agg),
                lookup_mode=getattr(gnm, "LOOKUP_" + mode), placement=getattr(gnm, "PLACE_" + place),
-               radix_bits=bits, unroll=unroll, block_threads=block, hash_slots=512 if table == "HASH" else 0)
+               radix_bits=bits, unroll=unroll, block_threads=block, hash_slots=512 if table == "HASH" else 0,
+               split=getattr(gnm, "SPLIT_" + split))
     d = gnm.Records.to_device(rec)
     ctx.process(d, 1)
     assert_window_matches(ctx.dense(1), expect)
@@ -112,11 +115,12 @@ def test_c1_host_records_and_site_stats(gnm, c1):
     ctx.close()
 
 
-def test_c1_ragged_and_unaligned(gnm, c1):
+@pytest.mark.parametrize("split", ["FUSED", "TWO_KERNELS"])
+def test_c1_ragged_and_unaligned(gnm, c1, split):
     """Windows of 0..9 records and arbitrary offsets (head/tail peeling), plus arrays
     whose 16-byte phases differ (element-wise path)."""
     reg, rec, _ = c1
-    ctx = _ctx(gnm, reg, window_slots=128)
+    ctx = _ctx(gnm, reg, window_slots=128, split=getattr(gnm, "SPLIT_" + split))
     d = gnm.Records.to_device(rec)
     lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
     wid = 100
@@ -150,9 +154,13 @@ def c2hour():
     return reg, rec, off, expect
 
 
-@pytest.mark.parametrize("cfg", [{}, {"lookup_mode": "BSEARCH"}, {"lookup_mode": "BSEARCH", "placement": "L2"},
+@pytest.mark.parametrize("cfg", [{}, {"split": "FUSED"}, {"lookup_mode": "BSEARCH"}, {"key_directory": 1},
+                                 {"key_directory": 1, "radix_bits": 16}, {"key_directory": 1, "radix_bits": 4},
+                                 {"radix_bits": 10}, {"radix_bits": 4},
+                                 {"lookup_mode": "BSEARCH", "placement": "L2", "split": "FUSED"},
                                  {"aggregation": "WARP"}, {"hash_slots": 1024}, {"table_mode": "GLOBAL"},
-                                 {"radix_bits": 12}])
+                                 {"radix_bits": 12, "split": "FUSED"}, {"table_mode": "HASH", "unroll": 2,
+                                                                          "block_threads": 512}])
 def test_c2_hour_batched_bitexact(gnm, c2hour, cfg):
     """Sixty one-minute windows (10M records, nested registry) in one launch -- the
     benchmark's workload and, with cfg {}, its launch configuration; every window equals
@@ -161,7 +169,7 @@ def test_c2_hour_batched_bitexact(gnm, c2hour, cfg):
     kw = {}
     for k, v in cfg.items():
         kw[k] = getattr(gnm, {"placement": "PLACE_", "aggregation": "AGG_", "table_mode": "TABLE_",
-                              "lookup_mode": "LOOKUP_"}[k] + v) if isinstance(v, str) else v
+                              "lookup_mode": "LOOKUP_", "split": "SPLIT_"}[k] + v) if isinstance(v, str) else v
     if "hash_slots" in kw:
         kw["table_mode"] = gnm.TABLE_HASH
     ctx = _ctx(gnm, reg, window_slots=64, **kw)
@@ -172,7 +180,8 @@ def test_c2_hour_batched_bitexact(gnm, c2hour, cfg):
     ids = np.arange(60) + 5000
     plan = ctx.plan(d, off, ids)  # the benchmark's path: a CUDA graph of one launch
     plan.launch()
-    assert ctx.last_launch_count() == 1
+    # fused: one kernel; split: keys + sums; 10,004 keys: a grid-wide finalisation after them
+    assert ctx.last_launch_count() == (1 if cfg.get("split") == "FUSED" else 2) + 1
     for w in range(60):
         assert_window_matches(ctx.dense(int(ids[w])), expect[w])
     plan.close()
@@ -228,6 +237,7 @@ def test_slot_eviction_and_release(gnm, c1):
                                                    ("c2", "BSEARCH", "STAGED", 0), ("c2", "BSEARCH", "L2", 0),
                                                    ("c1", "RADIX", "AUTO", 0), ("c2", "RADIX", "AUTO", 0),
                                                    ("c2", "RADIX", "AUTO", 4), ("c2", "RADIX", "AUTO", 15)])
+# (gnm_lookup runs the batch lookup kernel; the window tests below cover the key kernel)
 def test_lookup_matches_oracle(gnm, which, mode, place, bits):
     reg = fg.registry_c1() if which == "c1" else fg.registry_c2()
     ctx = _ctx(gnm, reg, lookup_mode=getattr(gnm, "LOOKUP_" + mode), placement=getattr(gnm, "PLACE_" + place),
@@ -256,7 +266,8 @@ def _ip(s):
 
 def test_radix_directory_must_fit(gnm):
     reg = fg.registry_c2()
-    ctx = _ctx(gnm, reg, lookup_mode=gnm.LOOKUP_RADIX, radix_bits=16)  # 256 KB > shared memory
+    # one fused kernel would need a 256 KB 32-bit directory next to its sums
+    ctx = _ctx(gnm, reg, lookup_mode=gnm.LOOKUP_RADIX, radix_bits=16, split=gnm.SPLIT_FUSED)
     d = gnm.Records.to_device(fg.make_records(reg, 1000, seed=3))
     with pytest.raises(gnm.GnmError, match="radix directory too large"):
         ctx.process(d, 1)
