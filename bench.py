@@ -58,7 +58,168 @@ def hbm_peak():
 def workload_desc(n_records, n_windows, reg, n_ranges):
     return (f"hour: {n_records:,} NetFlow-v5-shaped records in {n_windows} one-minute windows; "
             f"{reg.n_sites:,} sites / {reg.n:,} prefixes (/8-/30, 20% nested) -> {n_ranges:,} ranges; "
-            f"Zipf(1.0) sites, 85% registered, 30/70 in/out; plain binary search")
+            f"Zipf(1.0) sites, 85% registered, 30/70 in/out")
+
+
+LOOKUP_NAMES = {1: "binary search", 2: "learned index (RMI)", 3: "radix directory + binary search"}
+
+
+def learned_vs_plain(gnm, torch, local, steps, warmup, n_records=50_000_000):
+    """Same GPU, same records, 100,000-site / 1,000,000-prefix registry: one window of
+    n_records processed with the plain binary search, the radix-directed search and the
+    learned index. Results must be bit-exact across the three; throughput per lookup."""
+    import flowgen as fg
+    reg = fg.registry_c3()
+    rec = fg.make_records(reg, n_records, seed=2, p_reg=0.9, zipf_s=0.9)
+    dev = gnm.Records.to_device(rec)
+    # training keys: both addresses of 5,000,000 other records of the same distribution
+    tr = fg.make_records(reg, 5_000_000, seed=12, p_reg=0.9, zipf_s=0.9)
+    keys = torch.from_numpy(np.concatenate([tr["srcaddr"], tr["dstaddr"]]).view(np.int32)).cuda()
+    peak, peak_kind = hbm_peak()
+    stream = torch.cuda.current_stream()
+    res, dense, info_out = {}, {}, {}
+    for name, cfg in (("bsearch", dict(lookup_mode=gnm.LOOKUP_BSEARCH)),
+                      ("radix", dict(lookup_mode=gnm.LOOKUP_RADIX)),
+                      ("rmi", dict(lookup_mode=gnm.LOOKUP_RMI))):
+        ctx = gnm.Context(device=local, window_slots=4, **cfg)
+        ctx.load(reg)
+        if name == "rmi":
+            rep = ctx.rmi_train(keys, root_kind=gnm.ROOT_LINEAR, n_leaves=4096, leaf_iters=4)
+            info_out["rmi"] = {"leaves": 4096, "root": "linear", "eps_max": int(rep.eps_max),
+                               "eps_mean": round(float(rep.eps_mean), 2), "train_ms": round(float(rep.train_ms), 1),
+                               "sweep_ms": round(float(rep.sweep_ms), 1), "train_keys": int(keys.numel())}
+            ctx.rmi_violations(reset=True)
+        plan = ctx.plan(dev, [0, n_records], [1])
+        for _ in range(warmup):
+            plan.launch(stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            plan.launch(stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        info = ctx.registry_info()
+        alg = 24 * n_records + (2 * reg.n_sites * (48 + 8 + 1) + 4 * 48) + int(info.n_ranges) * 8
+        gbs = alg / (ms / 1e3) / 1e9
+        res[name] = {"records_per_s": n_records / (ms / 1e3), "ms": ms, "achieved_gbs": gbs,
+                     "frac": gbs / peak, "launches": ctx.last_launch_count(),
+                     "lookup": LOOKUP_NAMES.get(int(info.lookup_mode), str(int(info.lookup_mode)))}
+        if name == "rmi":
+            res[name]["violations"] = ctx.rmi_violations()
+        dense[name] = ctx.dense(1)
+        info_out["n_ranges"] = int(info.n_ranges)
+        plan.close()
+        ctx.close()
+    exact = all(np.array_equal(dense[k][i], dense["bsearch"][i], equal_nan=(i == 2))
+                for k in ("radix", "rmi") for i in range(4))
+    return {"workload": f"one window of {n_records:,} records; {reg.n_sites:,} sites / {reg.n:,} prefixes "
+                        f"(/16-/30, 30% nested) -> {info_out['n_ranges']:,} ranges; Zipf(0.9), 90% registered",
+            "peak_gbs": peak, "peak_kind": peak_kind, "bitexact_across_lookups": bool(exact),
+            "rmi_model": info_out.get("rmi"), **res,
+            "rmi_speedup_vs_bsearch": res["bsearch"]["ms"] / res["rmi"]["ms"]}
+
+
+def serve_c5(gnm, torch, local, minutes=30, speedup=600.0, pool_n=20_000_000, budget=4 << 30, check=2):
+    """Streaming replay: Poisson batch arrivals (1,000-500,000 records, 1e6 records/s on
+    average times the diurnal factor) over the learned-index 100,000-site registry, the
+    `minutes` around the daily peak replayed `speedup` times faster than real time. Host
+    batches (pinned) are cut at random offsets of a pool; one window per minute, closed at
+    the minute's end. Latency = window close -> rates and flags final on the device."""
+    import flowgen as fg
+    reg = fg.registry_c3()
+    pool = fg.make_records(reg, pool_n, seed=4, p_reg=0.9, zipf_s=0.9)
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(pool[k]).view(np.int32)).pin_memory() for k in gnm.FIELDS}
+    hpool = {k: v.numpy().view(np.uint32) for k, v in pinned.items()}
+    t_all, sz_all = fg.serving_schedule_c5(hours=24.0)
+    t0 = 6 * 3600.0 - minutes * 30.0  # centred on the daily peak of f(t)
+    sel = (t_all >= t0) & (t_all < t0 + minutes * 60.0)
+    times, sizes = t_all[sel] - t0, sz_all[sel]
+    rng = np.random.default_rng(5)
+    offs = rng.integers(0, pool_n - sizes + 1)
+    win_of = (times // 60.0).astype(np.int64)
+    ctx = gnm.Context(device=local, window_slots=16)
+    ctx.load(reg)
+    tr = fg.make_records(reg, 5_000_000, seed=12, p_reg=0.9, zipf_s=0.9)
+    keys = torch.from_numpy(np.concatenate([tr["srcaddr"], tr["dstaddr"]]).view(np.int32)).cuda()
+    ctx.rmi_train(keys, root_kind=gnm.ROOT_LINEAR, n_leaves=4096, leaf_iters=4)
+    checked = sorted({0, int(rng.integers(1, minutes))})[:check]
+    got = {}
+
+    def replay(srv, speedup, base):
+        """Submits the schedule (speedup None: as fast as possible); window w has id base + w."""
+        reports = []
+
+        def take(rs):
+            for r in rs:
+                reports.append(r)
+                if r[0] - base in checked and speedup is not None:
+                    got[r[0] - base] = ctx.dense(r[0])
+        nb, bi, wc = len(times), 0, 0
+        start = time.perf_counter()
+        while bi < nb or wc < minutes:
+            now = float("inf") if speedup is None else (time.perf_counter() - start) * speedup
+            ta = times[bi] if bi < nb else float("inf")
+            tc = (wc + 1) * 60.0
+            if min(ta, tc) <= now:
+                if ta <= tc:
+                    a = int(offs[bi])
+                    srv.submit(gnm.Records({k: v[a:a + int(sizes[bi])] for k, v in hpool.items()}),
+                               base + int(win_of[bi]))
+                    bi += 1
+                else:
+                    srv.close_window(base + wc)
+                    wc += 1
+            take(srv.poll())
+        take(srv.poll(wait_all=True))
+        return reports, time.perf_counter() - start
+
+    with gnm.Stream(ctx, budget_bytes=budget, n_cuda_streams=4) as srv:
+        # warm-up window (not reported): first use of the kernels and the arena
+        srv.submit(gnm.Records({k: v[:100_000] for k, v in hpool.items()}), 1 << 40, close=True)
+        srv.poll(wait_all=True)
+        torch.cuda.synchronize()
+        reports, wall = replay(srv, speedup, 0)
+        st = srv.stats()
+        sat_reports, sat_wall = replay(srv, None, 1 << 20)
+        sat_st = srv.stats()
+    # the sampled windows processed alone (one call over all their records) must give the
+    # same results as in the mix
+    ok = True
+    for w in checked:
+        idx = np.nonzero(win_of == w)[0]
+        rec = {k: np.concatenate([pool[k][offs[i]:offs[i] + sizes[i]] for i in idx]) for k in gnm.FIELDS}
+        ctx.process(gnm.Records.to_device(rec), (1 << 41) + w)
+        ast, aun, arate, afl = ctx.dense((1 << 41) + w)
+        gst, gun, grate, gfl = got[w]
+        ok = ok and (np.array_equal(gst, ast) and np.array_equal(gun, aun) and np.array_equal(gfl, afl)
+                     and np.array_equal(grate, arate, equal_nan=True))
+    ctx.close()
+    lat = [r[2] for r in reports if r[3] == 0]
+    n_rec = int(sizes.sum())
+    nb = len(times)
+    sat_lat = [r[2] for r in sat_reports if r[3] == 0]
+    return {"workload": f"{minutes} one-minute windows around the daily peak, {nb:,} Poisson batches of "
+                        f"1,000-500,000 records ({n_rec:,} records), replayed x{speedup:g} faster than real "
+                        f"time; {reg.n_sites:,}-site learned-index registry; host batches from a pinned "
+                        f"{pool_n:,}-record pool",
+            "records_per_s": n_rec / wall, "offered_records_per_s": n_rec / (minutes * 60.0 / speedup),
+            "wall_s": wall, "windows": len(lat),
+            "p50_ms": float(np.percentile(lat, 50, method="inverted_cdf")) if lat else None,
+            "p99_ms": float(np.percentile(lat, 99, method="inverted_cdf")) if lat else None,
+            "max_ms": max(lat) if lat else None, "latency": "window close -> rates and flags final (host clock)",
+            "budget_bytes": budget, "peak_inflight_bytes": int(st["peak_inflight_bytes"]),
+            "batches": int(st["batches"]), "batches_queued": int(st["batches_queued"]),
+            "checked_windows": checked, "mix_equals_alone": bool(ok),
+            "saturated": {"records_per_s": n_rec / sat_wall, "wall_s": sat_wall,
+                          "h2d_gbs": 24 * n_rec / sat_wall / 1e9,
+                          "p50_ms": float(np.percentile(sat_lat, 50, method="inverted_cdf")) if sat_lat else None,
+                          "p99_ms": float(np.percentile(sat_lat, 99, method="inverted_cdf")) if sat_lat else None,
+                          "peak_inflight_bytes": int(sat_st["peak_inflight_bytes"]),
+                          "batches_queued": int(sat_st["batches_queued"] - st["batches_queued"]),
+                          "note": "same schedule submitted as fast as the host loop can; latency includes "
+                                  "the queue behind the budget"}}
 
 
 class ClockSampler:
@@ -189,6 +350,10 @@ def main():
     ap.add_argument("--impl", default="gnm", choices=["gnm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the plain-vs-learned index comparison")
+    ap.add_argument("--no-serve", action="store_true", help="skip the streaming-server replay")
+    ap.add_argument("--serve-minutes", type=int, default=30)
+    ap.add_argument("--serve-speedup", type=float, default=600.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -260,11 +425,15 @@ def main():
         "config": {"workload": workload_desc(n, n_win, reg, int(info.n_ranges)),
                    "global_batch": n * world, "windows_per_step": n_win * world,
                    "parallelism": f"replicas x{world} (independent hours per GPU)",
-                   "lookup": "bsearch, registry " + {gnm.PLACE_SMEM: "in smem", gnm.PLACE_STAGED: "staged (block samples in smem, 64-B blocks in L2)", gnm.PLACE_L2: "in L2"}[info.placement],
+                   "lookup": LOOKUP_NAMES.get(int(info.lookup_mode), str(int(info.lookup_mode))),
                    "l2": "inputs 240 MB per GPU > 129 MB L2; no flush between steps",
-                   "launch": "CUDA graph: one persistent aggregation kernel per step (finalise fused)",
+                   "launch": f"CUDA graph per step: {launches // max(1, args.steps)} kernel launches "
+                             "(per-record site keys, persistent per-window aggregation, per-window finalise)"
+                             if launches // max(1, args.steps) == 3 else
+                             f"CUDA graph per step: {launches // max(1, args.steps)} kernel launch(es)",
                    "tuned": {"block_threads": tune.block_threads, "ctas_per_sm": tune.ctas_per_sm,
                              "unroll": tune.unroll, "aggregation": tune.aggregation, "placement": tune.placement,
+                             "radix_bits": tune.radix_bits, "split": tune.split,
                              "default_ms": round(tune.default_ms, 4), "tuned_ms": round(tune.best_ms, 4),
                              "candidates": tune.n_tried}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -304,10 +473,15 @@ def main():
         out["cpu_baseline"] = {"value": n / s, "unit": "records/s", "cores": cores, "kind": "oracle",
                                "sample": f"the whole step once: {n_win} windows, {n:,} records "
                                          f"({s:.2f} s on {cores} threads)"}
-    if rank == 0:
-        print(json.dumps(out), flush=True)
     plan.close()
     ctx.close()
+    del dev
+    if world == 1 and not args.no_learned:
+        out["learned_index"] = learned_vs_plain(gnm, torch, local, args.steps, args.warmup)
+    if world == 1 and not args.no_serve:
+        out["serving"] = serve_c5(gnm, torch, local, minutes=args.serve_minutes, speedup=args.serve_speedup)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -348,6 +348,91 @@ gnm_status gnm_autotune(gnm_ctx *ctx, const gnm_records *rec, const uint64_t *of
 /* Number of kernels the last processing call enqueued (for launch accounting). */
 uint32_t gnm_last_launch_count(const gnm_ctx *ctx);
 
+/* ------------------------------------------------------------------- serving */
+
+/* A streaming front end over one context. In the paper a receiver thread buffers arriving
+ * records in host memory and the monitoring thread hands each period's buffer to the GPU
+ * at once (Sec. III.B.1 "FlowData Receiver Thread", "NetPerf Monitoring Thread"); here
+ * batches go to the GPU as they arrive and are added to per-window device state, and a
+ * window's rates and flags (Sec. III.B.2.1) are final once its closing batch is processed.
+ *
+ * Admission: the records of admitted, unfinished batches (24 bytes each) never exceed
+ * budget_bytes. Host batches are copied into a device arena of budget_bytes owned by the
+ * server; device batches only count against the budget. A batch that does not fit waits
+ * in a FIFO queue; a window's first batch also waits while every result slot is held by
+ * an open window (later batches of open windows pass it). Queued batches are admitted in
+ * gnm_stream_submit and gnm_stream_poll as earlier batches finish (continuous batching).
+ * Each admitted batch is copied and processed on the next of n_cuda_streams CUDA streams,
+ * so the copies of some batches overlap the kernels of others; the kernels of one window
+ * run in submission order, those of different windows overlap.
+ *
+ * Window latency = host time from the gnm_stream_submit call that closes the window to
+ * the completion of its finalisation on the device (a host callback queued after it).
+ * Results of a reported window are read with gnm_window_dense / gnm_site_stats /
+ * gnm_flag_suboptimal on the context. A closed window keeps its result slot until the
+ * gnm_stream_submit or gnm_stream_poll call after the poll that reported it; from then on
+ * the context may reuse the slot for a newer window (oldest first).
+ *
+ * Threads: the server and its context are used from one host thread at a time; no other
+ * call may process windows on the context while the server is open. Host arrays of a
+ * batch must stay valid until gnm_stream_poll has reported its window. */
+typedef struct gnm_stream gnm_stream;
+
+typedef struct {
+    uint64_t budget_bytes;    /* device bytes of records in flight (default 4 GiB) */
+    uint32_t n_cuda_streams;  /* CUDA streams batches are spread over (default 4, 1..64) */
+    uint32_t max_queued;      /* queued batches before submit returns GNM_E_CAPACITY (65536) */
+} gnm_stream_config;
+
+typedef struct {
+    uint64_t window_id;
+    uint64_t records;         /* records added to the window */
+    double latency_ms;        /* closing submit -> rates and flags final */
+    int32_t status;           /* GNM_OK, or the first error of the window's work */
+    int32_t reserved;
+} gnm_window_done;
+
+typedef struct {
+    uint64_t batches;             /* submitted */
+    uint64_t batches_queued;      /* not admitted by the submit call that brought them */
+    uint64_t records;             /* submitted */
+    uint64_t windows_closed;
+    uint64_t windows_done;
+    uint64_t inflight_bytes;      /* now */
+    uint64_t peak_inflight_bytes; /* never above budget_bytes */
+    double p50_ms, p99_ms, max_ms, mean_ms;  /* window latency over the windows done */
+} gnm_stream_stats;
+
+void gnm_stream_config_default(gnm_stream_config *cfg);
+
+/* Opens a server on ctx, which must hold a registry. Allocates the arena (budget_bytes of
+ * device memory) and the streams: GNM_E_NOMEM / GNM_E_CUDA if that fails. */
+gnm_status gnm_stream_open(gnm_ctx *ctx, const gnm_stream_config *cfg, gnm_stream **out);
+
+/* Submits a batch of records (host or device SoA, fields as in gnm_window_process) for
+ * window `window_id`. The first batch of a window opens it; close_window = 1 closes the
+ * window after this batch (n = 0 closes it with no records). Errors: GNM_E_INVAL for a
+ * batch above the budget or malformed arrays, GNM_E_STATE for a batch of a window whose
+ * close was already submitted, GNM_E_CAPACITY when the batch cannot be admitted now and
+ * max_queued batches are waiting already (the batch is then not taken). */
+gnm_status gnm_stream_submit(gnm_stream *s, const gnm_records *batch, uint64_t window_id,
+                             int close_window);
+
+/* Admits what fits and reports up to cap windows completed since the last report
+ * (*n_out set; more stay for the next call). wait_all = 1 first waits until every
+ * submitted batch is processed and every closed window is done, or until the batches
+ * left wait for result slots held by the windows this call reports (call again after
+ * reading them); GNM_E_STATE when they wait for slots that only closing an open window
+ * frees. A failed window is reported with its error and has no results. */
+gnm_status gnm_stream_poll(gnm_stream *s, gnm_window_done *out, size_t cap, size_t *n_out,
+                           int wait_all);
+
+gnm_status gnm_stream_stats_get(gnm_stream *s, gnm_stream_stats *out);
+
+/* Waits for the work in flight, drops batches still queued, releases the server's memory
+ * and streams. Windows left open stay open (unpinned) in the context. */
+void gnm_stream_close(gnm_stream *s);
+
 /* ------------------------------------------------------------ without allocation */
 
 /* Largest n_sites gnm_window_process_noalloc accepts (its fixed scratch is 1 MiB). */

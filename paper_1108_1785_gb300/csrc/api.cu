@@ -22,7 +22,7 @@ std::string flatten_registry(const uint32_t* prefix, const uint8_t* len, const u
                              std::vector<uint32_t>* sites);
 bool local_overlaps(uint32_t lp, uint8_t ll, const uint32_t* prefix, const uint8_t* len, size_t n);
 
-constexpr uint32_t kRingSize = 16;
+constexpr uint32_t kRingSize = 32;
 constexpr size_t kRegistrySmemMax = 96 * 1024;   // bytes of ranges kept in shared memory
 constexpr size_t kSampleSmemMax = 96 * 1024;     // bytes of block samples (staged placement)
 constexpr size_t kDirectTableMax = 208 * 1024;   // direct-indexed per-CTA sums
@@ -59,7 +59,7 @@ static gnm_status acquire_slot_impl(gnm_ctx* c, uint64_t wid, cudaStream_t st, b
             uint64_t best = UINT64_MAX;
             for (uint32_t i = 0; i < c->n_slots; ++i)
                 if (!c->slots[i].pinned && c->slots[i].age < best) { best = c->slots[i].age; s = i; }
-            if (s == UINT32_MAX) return fail(GNM_E_CAPACITY, "every result slot is held by a plan");
+            if (s == UINT32_MAX) return fail(GNM_E_CAPACITY, "every result slot is held by a plan or an open served window");
             c->slot_of.erase(c->slots[s].window_id);
         }
         c->slot_of[wid] = s;
@@ -488,9 +488,9 @@ gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, s
 
 // Core of every processing call: windows k = [offsets[k], offsets[k+1]) of rec.
 // finalize: rates and flags at the end; open_add: add to already open windows.
-static gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets,
-                              const uint64_t* wids, size_t n_win, cudaStream_t st, bool finalize,
-                              bool open_add) {
+gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets,
+                       const uint64_t* wids, size_t n_win, cudaStream_t st, bool finalize,
+                       bool open_add) {
     if (n_win == 0) return GNM_OK;
     if (!wids) return fail(GNM_E_INVAL, "window ids are NULL");
     GNM_TRY(check_windows(c, rec, offsets, n_win));
@@ -549,6 +549,31 @@ static gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t
     lb->ev_recorded = true;
     for (size_t k = 0; k < n_win; ++k) c->slots[slot[k]].records += offsets[k + 1] - offsets[k];
     set_slots_done(c, slot.data(), n_win, lb->ev, finalize);
+    return GNM_OK;
+}
+
+gnm_status open_window(gnm_ctx* c, uint64_t wid, cudaStream_t st, bool pin, uint32_t* s) {
+    GNM_TRY(acquire_slot_impl(c, wid, st, pin, s));
+    cudaEvent_t ev;
+    GNM_TRY(record_event(c, st, &ev));
+    set_slots_done(c, s, 1, ev, false);
+    return GNM_OK;
+}
+
+gnm_status close_window(gnm_ctx* c, uint64_t wid, cudaStream_t st) {
+    uint32_t s;
+    GNM_TRY(find_window(c, wid, &s));
+    Slot& sl = c->slots[s];
+    if (!sl.open) return fail(GNM_E_STATE, "window is not open");
+    GNM_TRY(wait_slot_on_stream(c, s, st));
+    AggParams p;
+    gnm_records none{};
+    GNM_TRY(build_params(c, &none, &p));
+    GNM_CU(launch_finalize(p, s, st));
+    c->last_launches = 1;
+    cudaEvent_t ev;
+    GNM_TRY(record_event(c, st, &ev));
+    set_slots_done(c, &s, 1, ev, true);
     return GNM_OK;
 }
 
@@ -834,11 +859,7 @@ gnm_status gnm_window_open(gnm_ctx* c, uint64_t wid, void* stream) {
     if (!c->have_registry) return fail(GNM_E_STATE, "no registry loaded");
     GNM_CU(cudaSetDevice(c->device));
     uint32_t s;
-    GNM_TRY(acquire_slot(c, wid, (cudaStream_t)stream, &s));
-    cudaEvent_t ev;
-    GNM_TRY(record_event(c, (cudaStream_t)stream, &ev));
-    set_slots_done(c, &s, 1, ev, false);
-    return GNM_OK;
+    return open_window(c, wid, (cudaStream_t)stream, false, &s);
 }
 
 gnm_status gnm_window_add(gnm_ctx* c, const gnm_records* rec, uint64_t wid, void* stream) {
@@ -851,21 +872,7 @@ gnm_status gnm_window_add(gnm_ctx* c, const gnm_records* rec, uint64_t wid, void
 gnm_status gnm_window_close(gnm_ctx* c, uint64_t wid, void* stream) {
     if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
     GNM_CU(cudaSetDevice(c->device));
-    uint32_t s;
-    GNM_TRY(find_window(c, wid, &s));
-    Slot& sl = c->slots[s];
-    if (!sl.open) return fail(GNM_E_STATE, "window is not open");
-    cudaStream_t st = (cudaStream_t)stream;
-    GNM_TRY(wait_slot_on_stream(c, s, st));
-    AggParams p;
-    gnm_records none{};
-    GNM_TRY(build_params(c, &none, &p));
-    GNM_CU(launch_finalize(p, s, st));
-    c->last_launches = 1;
-    cudaEvent_t ev;
-    GNM_TRY(record_event(c, st, &ev));
-    set_slots_done(c, &s, 1, ev, true);
-    return GNM_OK;
+    return close_window(c, wid, (cudaStream_t)stream);
 }
 
 static gnm_status sync_slot(gnm_ctx* c, uint32_t s) {

@@ -160,4 +160,13 @@ gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, s
 // Next launch-scratch entry of the ring (waits for its previous use).
 gnm_status acquire_ring(gnm_ctx* c, uint32_t n_win, LaunchBuf** out);
 void set_slots_done(gnm_ctx* c, const uint32_t* slots, size_t n, cudaEvent_t ev, bool finalized);
+void unpin_slot(gnm_ctx* c, uint32_t s);
+// Windows k = [offsets[k], offsets[k+1]) of rec on stream st. finalize: rates and flags at
+// the end; open_add: add to windows already open instead of starting them.
+gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets, const uint64_t* wids,
+                       size_t n_win, cudaStream_t st, bool finalize, bool open_add);
+// Starts window wid with zero sums in a slot (pin: the slot is never evicted until unpinned).
+gnm_status open_window(gnm_ctx* c, uint64_t wid, cudaStream_t st, bool pin, uint32_t* slot_out);
+// Finalises an open window on st: rates and flags from its sums, which are zeroed.
+gnm_status close_window(gnm_ctx* c, uint64_t wid, cudaStream_t st);
 }  // namespace gnm

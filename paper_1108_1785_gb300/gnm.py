@@ -77,6 +77,22 @@ class RmiReport(C.Structure):
                 ("train_ms", C.c_double), ("sweep_ms", C.c_double)]
 
 
+class StreamConfig(C.Structure):
+    _fields_ = [("budget_bytes", C.c_uint64), ("n_cuda_streams", C.c_uint32), ("max_queued", C.c_uint32)]
+
+
+class WindowDone(C.Structure):
+    _fields_ = [("window_id", C.c_uint64), ("records", C.c_uint64), ("latency_ms", C.c_double),
+                ("status", C.c_int32), ("reserved", C.c_int32)]
+
+
+class StreamStats(C.Structure):
+    _fields_ = [("batches", C.c_uint64), ("batches_queued", C.c_uint64), ("records", C.c_uint64),
+                ("windows_closed", C.c_uint64), ("windows_done", C.c_uint64), ("inflight_bytes", C.c_uint64),
+                ("peak_inflight_bytes", C.c_uint64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("max_ms", C.c_double), ("mean_ms", C.c_double)]
+
+
 class TuneReport(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("unroll", C.c_int32),
                 ("aggregation", C.c_int32), ("placement", C.c_int32), ("best_ms", C.c_double),
@@ -130,6 +146,12 @@ def lib():
             "gnm_plan_destroy": (None, [P]),
             "gnm_autotune": (st, [P, C.POINTER(RecordsC), P, P, S, C.POINTER(TuneReport)]),
             "gnm_last_launch_count": (U32, [P]),
+            "gnm_stream_config_default": (None, [C.POINTER(StreamConfig)]),
+            "gnm_stream_open": (st, [P, C.POINTER(StreamConfig), C.POINTER(P)]),
+            "gnm_stream_submit": (st, [P, C.POINTER(RecordsC), U64, C.c_int]),
+            "gnm_stream_poll": (st, [P, C.POINTER(WindowDone), S, C.POINTER(S), C.c_int]),
+            "gnm_stream_stats_get": (st, [P, C.POINTER(StreamStats)]),
+            "gnm_stream_close": (None, [P]),
             "gnm_window_process_noalloc": (st, [C.POINTER(Config), P, P, U32, U32, P, P, S, C.POINTER(RecordsC),
                                                 P, P, P, P]),
         }
@@ -454,6 +476,72 @@ class Plan:
         if getattr(self, "h", None):
             lib().gnm_plan_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Stream:
+    """A streaming server over a context (gnm_stream_*): batches are admitted under a
+    device-memory budget and processed on several CUDA streams as they arrive."""
+
+    def __init__(self, ctx: Context, budget_bytes: int = 4 << 30, n_cuda_streams: int = 4,
+                 max_queued: int = 65536):
+        self.ctx = ctx
+        c = StreamConfig()
+        lib().gnm_stream_config_default(C.byref(c))
+        c.budget_bytes = budget_bytes
+        c.n_cuda_streams = n_cuda_streams
+        c.max_queued = max_queued
+        h = C.c_void_p()
+        ctx._c(lib().gnm_stream_open(ctx.h, C.byref(c), C.byref(h)))
+        self.h = h
+        self._held: Dict[int, list] = {}  # host batches kept alive until their window is reported
+        self._buf = (WindowDone * 1024)()
+
+    def submit(self, rec: "Records", window_id: int, close: bool = False):
+        self.ctx._c(lib().gnm_stream_submit(self.h, C.byref(rec.c), window_id, 1 if close else 0))
+        self._held.setdefault(window_id, []).append(rec)
+
+    def close_window(self, window_id: int):
+        """Closes a window with no further records."""
+        empty = RecordsC()
+        self.ctx._c(lib().gnm_stream_submit(self.h, C.byref(empty), window_id, 1))
+
+    def poll(self, wait_all: bool = False):
+        """Windows completed since the last poll: list of (window_id, records, latency_ms, status)."""
+        out = []
+        wait = 1 if wait_all else 0
+        while True:
+            n = C.c_size_t()
+            self.ctx._c(lib().gnm_stream_poll(self.h, self._buf, len(self._buf), C.byref(n), wait))
+            for i in range(n.value):
+                d = self._buf[i]
+                out.append((int(d.window_id), int(d.records), float(d.latency_ms), int(d.status)))
+                self._held.pop(int(d.window_id), None)
+            if n.value < len(self._buf):
+                return out
+            wait = 0
+
+    def stats(self) -> Dict[str, float]:
+        st = StreamStats()
+        self.ctx._c(lib().gnm_stream_stats_get(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in StreamStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gnm_stream_close(self.h)
+            self.h = None
+            self._held.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
     def __del__(self):
         try:

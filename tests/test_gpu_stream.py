@@ -1,0 +1,203 @@
+"""Streaming server (gnm_stream_*): every window's result is the same when its batches are
+served in a mix with other windows' batches -- interleaved, queued under a memory budget,
+spread over several CUDA streams -- as when the window is processed alone; sampled windows
+also match the CPU oracle. Integers bit-exact, rates within 1e-12 relative."""
+import numpy as np
+import pytest
+
+import flowgen as fg
+from helpers import assert_rates_close, assert_window_matches, oracle_full
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gnm():
+    from paper_1108_1785_gb300 import build, gnm as g
+    build.build()
+    return g
+
+
+@pytest.fixture(scope="module")
+def regs():
+    return {"c1": fg.registry_c1(), "c2": fg.registry_c2()}
+
+
+def _ctx(gnm, reg, **cfg):
+    ctx = gnm.Context(**cfg)
+    ctx.load(reg)
+    return ctx
+
+
+def _plan_mix(rng, n_windows, pool_n, max_batch, empty_close_every=4):
+    """Per window a list of pool slices (a, b); a submission order that interleaves the
+    windows while keeping each window's batches in order; the last batch closes."""
+    sizes_pick = [0, 1, 3, 17, 4096]
+    wins = {}
+    for w in range(n_windows):
+        k = int(rng.integers(2, 7))
+        sl = []
+        for _ in range(k):
+            n = int(rng.choice(sizes_pick)) if rng.random() < 0.3 else int(rng.integers(1, max_batch + 1))
+            a = int(rng.integers(0, pool_n - n + 1))
+            sl.append((a, a + n))
+        wins[100 + w] = sl
+    order = []
+    left = {w: list(range(len(s))) for w, s in wins.items()}
+    while left:
+        w = int(rng.choice(sorted(left)))
+        order.append((w, left[w].pop(0)))
+        if not left[w]:
+            del left[w]
+    empty_close = {w for i, w in enumerate(sorted(wins)) if i % empty_close_every == 0}
+    return wins, order, empty_close
+
+
+def _concat(pool, slices):
+    return {k: np.concatenate([v[a:b] for a, b in slices]) for k, v in pool.items()}
+
+
+def _serve(gnm, stream, pool_recs, wins, order, empty_close, read):
+    """Submits in `order`; `read(wid)` is called for each reported window before the next
+    server call (its results are guaranteed on the device until then)."""
+    done = {}
+    for w, j in order:
+        a, b = wins[w][j]
+        last = j == len(wins[w]) - 1
+        stream.submit(pool_recs(a, b), w, close=last and w not in empty_close)
+        if last and w in empty_close:
+            stream.close_window(w)
+        for wid, n, lat, status in stream.poll():
+            done[wid] = (n, lat, status, read(wid))
+    while len(done) < len(wins):
+        for wid, n, lat, status in stream.poll(wait_all=True):
+            done[wid] = (n, lat, status, read(wid))
+    return done
+
+
+@pytest.mark.parametrize("which,host,budget_batches,n_streams,slots", [
+    ("c1", True, 2, 3, 64),     # fused launches, host batches copied into the arena
+    ("c2", True, 3, 4, 64),     # split (key + aggregation) launches
+    ("c1", False, 2, 2, 64),    # device batches: only the budget is charged
+    ("c2", True, 2, 4, 3),      # three result slots for twelve interleaved windows
+])
+def test_mix_equals_alone(gnm, regs, which, host, budget_batches, n_streams, slots):
+    reg = regs[which]
+    rng = np.random.default_rng(11)
+    pool = fg.make_records(reg, 300_000, seed=21)
+    max_batch = 30_000
+    wins, order, empty_close = _plan_mix(rng, 12, 300_000, max_batch)
+    if host:
+        def recs(a, b):
+            return gnm.Records.host({k: v[a:b] for k, v in pool.items()})
+    else:
+        dpool = gnm.Records.to_device(pool)
+
+        def recs(a, b):
+            return gnm.Records({k: v[a:b] for k, v in dpool.fields.items()})
+    ctx = _ctx(gnm, reg, window_slots=slots)
+    budget = budget_batches * max_batch * 24
+    stream = gnm.Stream(ctx, budget_bytes=budget, n_cuda_streams=n_streams)
+    done = _serve(gnm, stream, recs, wins, order, empty_close, ctx.dense)
+    st = stream.stats()
+    stream.close()
+    assert sorted(done) == sorted(wins)
+    assert st["peak_inflight_bytes"] <= budget
+    assert st["inflight_bytes"] == 0
+    assert st["windows_done"] == len(wins) and st["batches"] == len(order) + len(empty_close)
+    assert 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
+    alone = _ctx(gnm, reg)
+    for w, sl in wins.items():
+        n, lat, status, dense = done[w]
+        assert status == 0 and lat > 0
+        rec = _concat(pool, sl)
+        assert n == rec["srcaddr"].size
+        alone.process(gnm.Records.to_device(rec), w)
+        st_a, un_a, r_a, f_a = alone.dense(w)
+        np.testing.assert_array_equal(dense[0], st_a)
+        np.testing.assert_array_equal(dense[1], un_a)
+        assert_rates_close(dense[2], r_a)
+        np.testing.assert_array_equal(dense[3], f_a)
+    for w in sorted(wins)[::5]:  # sampled windows against the oracle
+        assert_window_matches(done[w][3], oracle_full(reg, _concat(pool, wins[w])))
+    alone.close()
+    ctx.close()
+
+
+def test_empty_window_and_reuse_of_an_id(gnm, regs):
+    reg = regs["c1"]
+    ctx = _ctx(gnm, reg)
+    stream = gnm.Stream(ctx, budget_bytes=1 << 20)
+    stream.close_window(5)  # never received a record
+    (wid, n, lat, status), = stream.poll(wait_all=True)
+    assert (wid, n, status) == (5, 0, 0)
+    st, un, r, f = ctx.dense(5)
+    assert not st.any() and not un.any() and np.isnan(r).all() and not f.any()
+    pool = fg.window_records_c1(reg, n=5000)
+    stream.submit(gnm.Records.host(pool), 5, close=True)  # the id is free again once reported
+    (wid, n, lat, status), = stream.poll(wait_all=True)
+    assert (wid, n, status) == (5, 5000, 0)
+    assert_window_matches(ctx.dense(5), oracle_full(reg, pool))
+    stream.close()
+    ctx.close()
+
+
+def test_admission_errors_and_slot_wait(gnm, regs):
+    reg = regs["c1"]
+    ctx = _ctx(gnm, reg, window_slots=1)
+    pool = fg.window_records_c1(reg, n=4000)
+    part = lambda a, b: gnm.Records.host({k: v[a:b] for k, v in pool.items()})  # noqa: E731
+    stream = gnm.Stream(ctx, budget_bytes=2000 * 24, max_queued=2)
+    with pytest.raises(gnm.GnmError, match="INVAL"):
+        stream.submit(part(0, 2001), 1)  # larger than the whole budget
+    stream.submit(part(0, 1000), 1)      # window 1 takes the only slot
+    stream.submit(part(1000, 2000), 2)   # waits for a slot
+    stream.submit(part(2000, 3000), 3)   # waits too: the queue is full now
+    with pytest.raises(gnm.GnmError, match="CAPACITY"):
+        stream.submit(part(3000, 4000), 4)
+    with pytest.raises(gnm.GnmError, match="STATE"):
+        stream.poll(wait_all=True)       # only closing window 1 frees the slot
+    assert stream.stats()["batches_queued"] == 2
+    stream.close_window(1)
+    with pytest.raises(gnm.GnmError, match="STATE"):
+        stream.submit(part(0, 10), 1)    # a closed window takes no more batches
+    got = stream.poll(wait_all=True)     # window 1 done; 2 waits for its slot until the next call
+    assert [g[0] for g in got] == [1]
+    assert_window_matches(ctx.dense(1), oracle_full(reg, {k: v[0:1000] for k, v in pool.items()}))
+    stream.close_window(2)
+    stream.close_window(3)
+    seen = {}
+    while len(seen) < 2:
+        for wid, n, lat, status in stream.poll(wait_all=True):
+            seen[wid] = ctx.dense(wid)
+    for wid, (a, b) in ((2, (1000, 2000)), (3, (2000, 3000))):
+        assert_window_matches(seen[wid], oracle_full(reg, {k: v[a:b] for k, v in pool.items()}))
+    st = stream.stats()
+    assert st["peak_inflight_bytes"] <= 2000 * 24 and st["windows_done"] == 3
+    stream.close()
+    ctx.close()
+
+
+def test_window_of_a_plan_fails_alone(gnm, regs):
+    """A window whose slot cannot be taken (its id belongs to a plan) is reported with the
+    error; the other windows of the mix are unaffected."""
+    reg = regs["c1"]
+    ctx = _ctx(gnm, reg)
+    pool = fg.window_records_c1(reg, n=20000)
+    d = gnm.Records.to_device(pool)
+    plan = ctx.plan(d, [0, 10000], [77])
+    stream = gnm.Stream(ctx, budget_bytes=1 << 22)
+    stream.submit(gnm.Records.host({k: v[:5000] for k, v in pool.items()}), 77, close=True)
+    stream.submit(gnm.Records.host({k: v[5000:] for k, v in pool.items()}), 78, close=True)
+    got = {}
+    while len(got) < 2:
+        for wid, n, lat, status in stream.poll(wait_all=True):
+            got[wid] = status
+            if status == 0:
+                assert_window_matches(ctx.dense(wid), oracle_full(reg, {k: v[5000:] for k, v in pool.items()}))
+    assert got[77] == 4 and got[78] == 0  # GNM_E_STATE for the plan's window
+    stream.close()
+    plan.close()
+    ctx.close()
