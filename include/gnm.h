@@ -103,9 +103,12 @@ typedef struct {
     int32_t split;              /* GNM_SPLIT_*: one fused kernel, or a lookup kernel that
                                    writes a 4-byte key per record followed by the
                                    aggregation kernel (registries outside shared memory) */
-    int32_t key_directory;      /* split RADIX lookups: 0 = 32-bit range directory,
-                                   1 = 16-bit directory of 8-range blocks that carry their
-                                   sites (one 64-byte L2 load per lookup) */
+    int32_t key_directory;      /* split RADIX lookups: 3 (1) = the key kernel keeps the
+                                   first start of every 2-range (4-range) block in shared
+                                   memory beside a directory of block indices, and one
+                                   16-byte (32-byte) load of the block's (start, site)
+                                   pairs ends a lookup; 2 = the range directory and a
+                                   search over L2; 0 = 3, else 1, whichever fits first */
 } gnm_config;
 
 /* One struct-of-arrays batch of NetFlow v5 fields (Sec. IV.A.3: 48-byte v5 records; only
@@ -324,11 +327,28 @@ gnm_status gnm_rmi_import(gnm_ctx *ctx, int32_t root_kind, uint32_t n_leaves, co
 typedef struct gnm_plan gnm_plan;
 
 /* A reusable launch of gnm_windows_process over fixed device buffers and window shapes,
- * captured once into a CUDA graph (zeroing of the result slots + the persistent
- * aggregation kernel, which finalises each window). */
+ * captured once into a CUDA graph: the per-record key kernel (registries outside shared
+ * memory), the persistent aggregation kernel and, for registries of more than 4096 keys,
+ * the per-window finalisation kernel. The record buffers and window shapes stay fixed;
+ * their contents may change between launches. */
 gnm_status gnm_plan_create(gnm_ctx *ctx, const gnm_records *rec, const uint64_t *offsets,
                            const uint64_t *window_ids, size_t n_win, gnm_plan **out);
+
+/* gnm_plan_create with flags. GNM_PLAN_KERNEL_TIMES adds timing events between the
+ * graph's kernels (a few microseconds per launch), read by gnm_plan_kernel_times. */
+#define GNM_PLAN_KERNEL_TIMES 1u
+gnm_status gnm_plan_create_ex(gnm_ctx *ctx, const gnm_records *rec, const uint64_t *offsets,
+                              const uint64_t *window_ids, size_t n_win, uint32_t flags, gnm_plan **out);
 gnm_status gnm_plan_launch(gnm_plan *plan, void *stream);
+
+/* Kernels of a plan's launch, in order */
+typedef enum { GNM_KERNEL_KEYS = 0, GNM_KERNEL_AGGREGATE = 1, GNM_KERNEL_FINALIZE = 2 } gnm_kernel_kind;
+
+/* Device durations (ms, CUDA events) of each kernel of the plan's last launch, which it
+ * waits for; kind[i] names kernel i. *n_out = the plan's kernel count (GNM_E_CAPACITY
+ * if cap is smaller); GNM_E_STATE for a plan created without GNM_PLAN_KERNEL_TIMES or
+ * never launched. */
+gnm_status gnm_plan_kernel_times(gnm_plan *plan, float *ms, int32_t *kind, size_t cap, size_t *n_out);
 void gnm_plan_destroy(gnm_plan *plan);
 
 typedef struct {
@@ -337,11 +357,13 @@ typedef struct {
     uint32_t n_tried;
     uint32_t radix_bits;
     int32_t split;
+    int32_t key_directory;
 } gnm_tune_report;
 
 /* Times candidate launch shapes (block size, CTAs per SM, records per thread,
- * aggregation, registry placement) on these windows with CUDA events, keeps the fastest
- * in the context and reports it. Results of the windows are those of the last run. */
+ * aggregation, registry placement or radix directory bits, fused or split launches, key
+ * kernel directory) on these windows with CUDA events, keeps the fastest in the context
+ * and reports it. Results of the windows are those of the last run. */
 gnm_status gnm_autotune(gnm_ctx *ctx, const gnm_records *rec, const uint64_t *offsets,
                         const uint64_t *window_ids, size_t n_win, gnm_tune_report *report);
 

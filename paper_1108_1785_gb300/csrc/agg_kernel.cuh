@@ -99,22 +99,50 @@ __device__ __forceinline__ void radix_search(const uint32_t* __restrict__ dir, u
     }
 }
 
-// Block-directory search (key kernel): dirb[t] is the 8-range block holding the first
-// address of bucket t (the top `bits` bits), so x lies in blocks [dirb[t], dirb[t+1]];
-// usually one block, else a binary search over the blocks' first starts picks it. The
-// block's 8 starts and 8 sites come in one 64-byte load; padding past the last range is
-// start 0xFFFFFFFF with the last site.
+// Predecessor search over (start, site) pairs, R lookups in lock step: narrows each
+// [base, base + len) -- whose first start is <= x -- to one range, carrying the site of
+// the current base along, so that no separate site load follows the last probe.
 template <int R>
-__device__ __forceinline__ void radix_block_sites(const uint16_t* __restrict__ dirb, uint32_t bits,
-                                                  const uint32_t* __restrict__ sample8, const uint4* __restrict__ blk8,
-                                                  const uint32_t (&x)[R], uint32_t (&site)[R]) {
-    uint32_t b[R], len[R];
+__device__ __forceinline__ void pair_search(const uint2* __restrict__ pairs, const uint32_t (&x)[R],
+                                            uint32_t (&base)[R], uint32_t (&len)[R], uint32_t (&site)[R]) {
+    bool more = false;
+#pragma unroll
+    for (int j = 0; j < R; ++j) more |= len[j] > 1u;
+    while (more) {
+        more = false;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (len[j] > 1u) {
+                const uint32_t half = len[j] >> 1;
+                const uint2 v = __ldg(pairs + base[j] + half);
+                if (v.x <= x[j]) {
+                    base[j] += half;
+                    site[j] = v.y;
+                }
+                len[j] -= half;
+                more |= len[j] > 1u;
+            }
+        }
+    }
+}
+
+// Block-sample search (key kernel): dir[t] is the BR-range block holding the first address
+// of bucket t (the top `bits` bits), so x's block lies in [dir[t], dir[t+1]]; a search over
+// the blocks' first starts `smp` (shared memory) picks it, and one load of its BR (start,
+// site) pairs (16 bytes for BR = 2, 32 for BR = 4) gives the site. Pairs past the last
+// range are start 0xFFFFFFFF with the last range's site, so the count is right for every x.
+template <int BR, int R>
+__device__ __forceinline__ void radix_block(const uint32_t* dir, uint32_t bits, const uint32_t* smp,
+                                            const uint2* __restrict__ pairs, const uint32_t (&x)[R],
+                                            uint32_t (&site)[R]) {
+    static_assert(BR == 2 || BR == 4, "blocks of 2 or 4 ranges");
+    uint32_t g[R], len[R];
     bool more = false;
 #pragma unroll
     for (int j = 0; j < R; ++j) {
         const uint32_t t = x[j] >> (32u - bits);
-        b[j] = dirb[t];
-        len[j] = (uint32_t)dirb[t + 1] - b[j] + 1u;
+        g[j] = dir[t];
+        len[j] = dir[t + 1] - g[j] + 1u;
         more |= len[j] > 1u;
     }
     while (more) {
@@ -123,21 +151,27 @@ __device__ __forceinline__ void radix_block_sites(const uint16_t* __restrict__ d
         for (int j = 0; j < R; ++j) {
             if (len[j] > 1u) {
                 const uint32_t half = len[j] >> 1;
-                b[j] = (__ldg(sample8 + b[j] + half) <= x[j]) ? b[j] + half : b[j];
+                g[j] = smp[g[j] + half] <= x[j] ? g[j] + half : g[j];
                 len[j] -= half;
                 more |= len[j] > 1u;
             }
         }
     }
+    uint4 lo[R], hi[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-        const uint4* q = blk8 + 4 * (size_t)b[j];
-        const uint4 s0 = __ldg(q), s1 = __ldg(q + 1), w0 = __ldg(q + 2), w1 = __ldg(q + 3);
-        const uint32_t c = (s0.y <= x[j]) + (s0.z <= x[j]) + (s0.w <= x[j]) + (s1.x <= x[j]) + (s1.y <= x[j]) +
-                           (s1.z <= x[j]) + (s1.w <= x[j]);  // s0.x <= x: it is the block's first start
-        const uint4 w = c < 4 ? w0 : w1;
-        const uint32_t r = c & 3u;
-        site[j] = r == 0 ? w.x : (r == 1 ? w.y : (r == 2 ? w.z : w.w));
+        const uint4* q = reinterpret_cast<const uint4*>(pairs) + (BR / 2) * (size_t)g[j];
+        lo[j] = __ldg(q);                          // start0 site0 start1 site1
+        if (BR == 4) hi[j] = __ldg(q + 1);         // start2 site2 start3 site3
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        if (BR == 2) {
+            site[j] = lo[j].z <= x[j] ? lo[j].w : lo[j].y;
+        } else {
+            const uint32_t c = (lo[j].z <= x[j]) + (hi[j].x <= x[j]) + (hi[j].z <= x[j]);
+            site[j] = c == 0 ? lo[j].y : (c == 1 ? lo[j].w : (c == 2 ? hi[j].y : hi[j].w));
+        }
     }
 }
 
@@ -194,6 +228,52 @@ __device__ __forceinline__ uint32_t rmi_lookup(const RmiDev& m, const float* a, 
     if (ok) return r;
     atomicAdd(violations, 1ull);
     return pred_search1(starts, 0, n, x);
+}
+
+// Learned-index lookups of R addresses in lock step over the (start, site) pairs: the
+// model's window for each, one bounded search for all, then the same verification as
+// rmi_lookup (the window's lower end not above x, the answer below its upper end unless
+// that is the last range), with a full search for the lookups that fail it.
+template <int R>
+__device__ __forceinline__ void rmi_sites(const RmiDev& m, const float* a, const float* b, const uint32_t* x0,
+                                          const uint32_t* eps, const uint2* __restrict__ pairs, uint32_t n,
+                                          const bool (&valid)[R], const uint32_t (&x)[R], uint32_t (&site)[R],
+                                          unsigned long long* violations) {
+    uint32_t base[R], len[R], lo[R], hi[R];
+    uint32_t first[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const uint32_t l = rmi_root(m, x[j]);
+        const uint32_t e = eps[l];
+        if (!valid[j]) {
+            lo[j] = 0u;
+            hi[j] = 0u;
+        } else if (e == 0xFFFFFFFFu) {  // no proven bound for this leaf: full search
+            lo[j] = 0u;
+            hi[j] = n - 1u;
+        } else {
+            const uint32_t pi = rmi_leaf_pos(a, b, x0, l, x[j], n);
+            const uint32_t elo = e & 0xFFFFu, ehi = e >> 16;
+            lo[j] = pi > elo ? pi - elo : 0u;
+            hi[j] = min(pi + ehi + 1u, n - 1u);  // one past the bound, to verify it
+        }
+        const uint2 f = __ldg(pairs + lo[j]);
+        first[j] = f.x;
+        site[j] = f.y;
+        base[j] = lo[j];
+        len[j] = hi[j] - lo[j] + 1u;
+    }
+    pair_search<R>(pairs, x, base, len, site);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const bool ok = (lo[j] == 0u || first[j] <= x[j]) && (base[j] < hi[j] || hi[j] == n - 1u);
+        if (valid[j] && !ok) {
+            atomicAdd(violations, 1ull);
+            uint32_t xb[1] = {x[j]}, bb[1] = {0u}, lb[1] = {n}, sb[1] = {__ldg(pairs).y};
+            pair_search<1>(pairs, xb, bb, lb, sb);
+            site[j] = sb[0];
+        }
+    }
 }
 
 // Staged placement, last level: position of x inside the 64-byte block jb of 16 range
@@ -415,6 +495,19 @@ __device__ __forceinline__ void dump_rows(const Smem& sm, uint32_t* dst) {
     }
 }
 
+// Within a CTA's segment of a window whose rows go to a partial block at its end: adds
+// the rows' 16-bit counts to the window's global accumulators and clears them, so that
+// they cannot wrap; the sums (wrap-safe) keep accumulating.
+__device__ __forceinline__ void flush_counts(const Smem& sm, uint64_t* gacc) {
+    for (uint32_t r = threadIdx.x; r < sm.rows; r += blockDim.x) {
+        uint32_t* w = sm.t + r * kRowWords;
+        const uint32_t cnt = w[0];
+        if (cnt == 0) continue;
+        red_add(gacc + (size_t)r * kAccCols, ((uint64_t)(cnt & 0xFFFFu) << 32) | (cnt >> 16));
+        w[0] = 0;
+    }
+}
+
 // Adds the CTA's shared-memory sums to the window's global accumulators and clears them.
 template <int TABLE>
 __device__ __forceinline__ void flush(const Smem& sm, uint64_t* gacc) {
@@ -437,7 +530,10 @@ __device__ __forceinline__ void flush(const Smem& sm, uint64_t* gacc) {
 }
 
 // Rates and flags of one window from its accumulators (Sec. III.B.1: rates per site;
-// a site is sub-optimal when its rate is below the standard).
+// a site is sub-optimal when its rate is below the standard). kL1: the sums were written
+// by an earlier kernel, so loads may go through L1 (the 5 word loads of a row then fetch
+// its lines from L2 once); inside the aggregation kernel they bypass L1.
+template <bool kL1 = false>
 __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot, uint32_t k0,
                                               uint32_t step, const uint32_t* parts = nullptr,
                                               uint32_t n_parts = 0) {
@@ -450,19 +546,23 @@ __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot,
 #pragma unroll 1
     for (uint32_t k = k0; k < keys; k += step) {
         uint64_t* a = acc + (size_t)k * kAccCols;
-        uint64_t packed = __ldcg(reinterpret_cast<const unsigned long long*>(a));
-        uint64_t oc = __ldcg(reinterpret_cast<const unsigned long long*>(a + 1));
-        uint64_t pk = __ldcg(reinterpret_cast<const unsigned long long*>(a + 2));
-        uint64_t eo = __ldcg(reinterpret_cast<const unsigned long long*>(a + 3));
-        uint64_t ed = __ldcg(reinterpret_cast<const unsigned long long*>(a + 4));
+        auto ld64 = [](const uint64_t* q) -> uint64_t {
+            return kL1 ? *q : __ldcg(reinterpret_cast<const unsigned long long*>(q));
+        };
+        auto ld32 = [](const uint32_t* q) -> uint32_t { return kL1 ? __ldg(q) : __ldcg(q); };
+        uint64_t packed = ld64(a);
+        uint64_t oc = ld64(a + 1);
+        uint64_t pk = ld64(a + 2);
+        uint64_t eo = ld64(a + 3);
+        uint64_t ed = ld64(a + 4);
         for (uint32_t q = 0; q < n_parts; ++q) {  // partial blocks of the window's CTAs
             const uint32_t* w = parts + ((size_t)q * keys + k) * kRowWords;
-            const uint32_t cnt = __ldcg(w);
+            const uint32_t cnt = ld32(w);
             packed += ((uint64_t)(cnt & 0xFFFFu) << 32) | (cnt >> 16);
-            oc += __ldcg(w + 1);
-            pk += __ldcg(w + 2);
-            eo += __ldcg(w + 3);
-            ed += __ldcg(w + 4);
+            oc += ld32(w + 1);
+            pk += ld32(w + 2);
+            eo += ld32(w + 3);
+            ed += ld32(w + 4);
         }
         const uint64_t ef = packed & 0xFFFFFFFFull;
         // accumulators return to zero for the slot's next window
@@ -528,13 +628,32 @@ __device__ __forceinline__ void lookup_sites(const AggParams& p, const Smem& sm,
 #pragma unroll
         for (int j = 0; j < R; ++j) site[j] = sm.s_site[idx[j]];
     } else if (LOOKUP == kLookupL2) {
-        pred_search<R, false>(p.starts, p.n_ranges, x, idx);
+        if (p.pairs) {  // (the allocation-free entry point has plain arrays only)
+            uint32_t len[R];
+            const uint32_t s0 = __ldg(p.pairs).y;
 #pragma unroll
-        for (int j = 0; j < R; ++j) site[j] = __ldg(p.rsite + idx[j]);
+            for (int j = 0; j < R; ++j) {
+                idx[j] = 0u;
+                len[j] = p.n_ranges;
+                site[j] = s0;
+            }
+            pair_search<R>(p.pairs, x, idx, len, site);
+        } else {
+            pred_search<R, false>(p.starts, p.n_ranges, x, idx);
+#pragma unroll
+            for (int j = 0; j < R; ++j) site[j] = __ldg(p.rsite + idx[j]);
+        }
     } else if (LOOKUP == kLookupRadix) {
-        radix_search<R>(sm.s_starts, p.radix_bits, p.starts, x, idx);
+        // the directory gives x's bucket [dir[t], dir[t+1]] of ranges; search it
+        uint32_t len[R];
 #pragma unroll
-        for (int j = 0; j < R; ++j) site[j] = __ldg(p.rsite + idx[j]);
+        for (int j = 0; j < R; ++j) {
+            const uint32_t t = p.radix_bits ? x[j] >> (32u - p.radix_bits) : 0u;
+            idx[j] = sm.s_starts[t];
+            len[j] = sm.s_starts[t + 1] - idx[j] + 1u;
+            site[j] = __ldg(p.pairs + idx[j]).y;
+        }
+        pair_search<R>(p.pairs, x, idx, len, site);
     } else if (LOOKUP == kLookupStaged) {
         pred_search<R, true>(sm.s_starts, p.n_blocks, x, idx);  // block of x
 #pragma unroll
@@ -542,16 +661,11 @@ __device__ __forceinline__ void lookup_sites(const AggParams& p, const Smem& sm,
 #pragma unroll
         for (int j = 0; j < R; ++j) site[j] = __ldg(p.rsite + idx[j]);
     } else if (LOOKUP == kLookupRadixBlk) {
-        radix_block_sites<R>(reinterpret_cast<const uint16_t*>(sm.s_starts), p.radix_bits, p.sample8, p.blk8, x, site);
+        radix_block<4, R>(sm.s_starts, p.radix_bits, sm.s_site, p.pairs, x, site);
+    } else if (LOOKUP == kLookupRadixBlk2) {
+        radix_block<2, R>(sm.s_starts, p.radix_bits, sm.s_site, p.pairs, x, site);
     } else if (LOOKUP == kLookupRmi) {
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-            idx[j] = valid[j] ? rmi_lookup(p.rmi, sm.ra, sm.rb, sm.rx0, sm.reps, p.starts,
-                                           p.n_ranges, x[j], p.violations)
-                              : 0u;
-        }
-#pragma unroll
-        for (int j = 0; j < R; ++j) site[j] = __ldg(p.rsite + idx[j]);
+        rmi_sites<R>(p.rmi, sm.ra, sm.rb, sm.rx0, sm.reps, p.pairs, p.n_ranges, valid, x, site, p.violations);
     }
 }
 
@@ -695,11 +809,18 @@ __device__ __forceinline__ void stage_lookup(const AggParams& p, unsigned char* 
         for (uint32_t i = tid; i <= nd; i += B) d[i] = __ldg(p.dir16 + ((size_t)i << sh));
         sm.s_starts = d;
     }
-    if (LOOKUP == kLookupRadixBlk) {  // every 2^(16-bits)-th entry of the 16-bit block directory
-        uint16_t* d = reinterpret_cast<uint16_t*>(base);
+    if (LOOKUP == kLookupRadixBlk || LOOKUP == kLookupRadixBlk2) {
+        // block directory (from the range directory) and block samples
+        constexpr uint32_t lg = LOOKUP == kLookupRadixBlk ? 2u : 1u;  // log2(ranges per block)
+        const uint32_t* sample = LOOKUP == kLookupRadixBlk ? p.sample4 : p.sample2;
+        const uint32_t nb = LOOKUP == kLookupRadixBlk ? p.n_blk4 : p.n_blk2;
+        uint32_t* d = reinterpret_cast<uint32_t*>(base);
         const uint32_t nd = 1u << p.radix_bits, sh = 16u - p.radix_bits;
-        for (uint32_t i = tid; i <= nd; i += B) d[i] = p.dirb16[(size_t)i << sh];
-        sm.s_starts = reinterpret_cast<const uint32_t*>(d);
+        for (uint32_t i = tid; i <= nd; i += B) d[i] = __ldg(p.dir16 + ((size_t)i << sh)) >> lg;
+        uint32_t* smp = d + (((nd + 1u) + 3u) & ~3u);
+        for (uint32_t i = tid; i < nb; i += B) smp[i] = __ldg(sample + i);
+        sm.s_starts = d;
+        sm.s_site = smp;  // (here: the block samples)
     }
     if (LOOKUP == kLookupRmi) {
         const uint32_t L = p.rmi.n_leaves;
@@ -750,20 +871,12 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512)
         if (wd.begin >= hi) break;
         const uint64_t s0 = max(wd.begin, lo), e0 = min(wd.end, hi);
         uint64_t* gacc = p.acc + (size_t)wd.slot * p.keys * kAccCols;
-        // pieces of at most kFlushRecords records, so the 16-bit counts cannot wrap; with a
-        // partial-sum area every piece stores its own block: the blocks of earlier CTAs of
-        // the window come first (the first CTA's segment may be short, the others are full
-        // chunks)
-        uint32_t q = 0;
-        if (TABLE == kTableDirect && p.partials) {
-            const uint64_t f = wd.begin / p.chunk;
-            if (blockIdx.x > f) {
-                const uint64_t len_f = min(wd.end, (f + 1) * p.chunk) - wd.begin;
-                const uint64_t per_full = (p.chunk + kFlushRecords - 1) / kFlushRecords;
-                q = (uint32_t)((len_f + kFlushRecords - 1) / kFlushRecords + (blockIdx.x - f - 1) * per_full);
-            }
-        }
-        for (uint64_t s = s0; s < e0; s += kFlushRecords, ++q) {
+        // pieces of at most kFlushRecords records, so the 16-bit counts cannot wrap. With a
+        // partial-sum area the CTA's segment of the window ends in one block of its own
+        // (block q = the CTA's position among the window's CTAs), and the pieces before
+        // the last hand over only their counts
+        const uint32_t q = (uint32_t)(blockIdx.x - wd.begin / p.chunk);
+        for (uint64_t s = s0; s < e0; s += kFlushRecords) {
             const uint64_t e = min(e0, s + kFlushRecords);
             uint64_t a0 = e, a1 = e;
             if (p.vec_ok) {
@@ -777,7 +890,10 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512)
             if (TABLE != kTableGlobal) {
                 __syncthreads();
                 if (TABLE == kTableDirect && p.partials) {
-                    dump_rows(sm, p.partials + ((size_t)wd.part_base + q) * p.keys * kRowWords);
+                    if (e >= e0)
+                        dump_rows(sm, p.partials + ((size_t)wd.part_base + q) * p.keys * kRowWords);
+                    else
+                        flush_counts(sm, gacc);
                 } else {
                     flush<TABLE>(sm, gacc);
                 }

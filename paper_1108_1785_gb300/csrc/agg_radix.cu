@@ -11,4 +11,7 @@ cudaError_t launch_keys_radix(const AggParams& p, const LaunchShape& s, uint32_t
 cudaError_t launch_keys_radixblk(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st) {
     return dev::launch_keys_impl<kLookupRadixBlk>(p, s, keys, st);
 }
+cudaError_t launch_keys_radixblk2(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st) {
+    return dev::launch_keys_impl<kLookupRadixBlk2>(p, s, keys, st);
+}
 }  // namespace gnm

@@ -252,13 +252,35 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
     s->keys_smem = s->split ? (lookup_bytes + 15) / 16 * 16 : 0;
     s->keys_blk = 0;
     s->keys_bits = 0;
-    if (s->split && s->lookup == kLookupRadix && c->n_blk8 && cfg.key_directory == 1) {
-        // 16-bit block directory in the key kernel (it has shared memory to spare)
-        uint32_t kb = cfg.radix_bits ? cfg.radix_bits : (c->tuned.radix_bits ? c->tuned.radix_bits : 15);
-        if (kb < 4 || kb > 16) return fail(GNM_E_INVAL, "radix_bits must be 4..16");
-        s->keys_blk = 1;
-        s->keys_bits = kb;
-        s->keys_smem = ((((size_t)1 << kb) + 1) * 2 + 15) / 16 * 16;
+    if (cfg.key_directory < 0 || cfg.key_directory > 3) return fail(GNM_E_INVAL, "key_directory must be 0..3");
+    const int key_dir = cfg.key_directory ? cfg.key_directory : c->tuned.key_dir;
+    if (s->split && s->lookup == kLookupRadix && key_dir != 2) {
+        // block samples in the key kernel's shared memory next to a directory of block
+        // indices: 2-range blocks (one 16-byte load) when they fit, else 4-range blocks
+        // (32 bytes); else the plain directory
+        const size_t one = (size_t)c->smem_optin > 1024 ? (size_t)c->smem_optin - 1024 : 0;
+        auto bytes = [&](uint32_t kb, uint32_t nb) {
+            return ((((size_t)1 << kb) + 1) * 4 + 15) / 16 * 16 + ((size_t)nb * 4 + 15) / 16 * 16;
+        };
+        uint32_t kb0 = cfg.radix_bits ? cfg.radix_bits : c->tuned.radix_bits;
+        if (kb0 && (kb0 < 4 || kb0 > 16)) return fail(GNM_E_INVAL, "radix_bits must be 4..16");
+        for (int br : {2, 4}) {
+            if (key_dir == 1 && br == 2) continue;
+            if (key_dir == 3 && br == 4) continue;
+            const uint32_t nb = br == 2 ? c->n_blk2 : c->n_blk4;
+            uint32_t kb = kb0;
+            if (!kb)  // the largest directory (<= 14 bits) that fits beside the samples
+                for (kb = 14; kb > 8 && bytes(kb, nb) > one; --kb) {}
+            if (bytes(kb, nb) <= one) {
+                s->keys_blk = br;
+                s->keys_bits = kb;
+                s->keys_smem = bytes(kb, nb);
+                break;
+            }
+        }
+        if (!s->keys_blk && (key_dir == 1 || key_dir == 3))
+            return fail(GNM_E_INVAL, "block samples do not fit in shared memory (key_directory " +
+                                         std::to_string(key_dir) + ")");
     }
     if (s->split && s->keys_smem + 1024 > (size_t)c->smem_optin)
         return fail(GNM_E_INVAL, "lookup structure too large for shared memory");
@@ -336,13 +358,14 @@ gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p) {
     p->last = rec->last;
     p->starts = c->d_starts;
     p->rsite = c->d_site;
+    p->pairs = c->d_pairs;
     p->blocks = reinterpret_cast<const uint4*>(c->d_blocks);
     p->sample = c->d_sample;
     p->dir16 = c->d_dir16;
-    p->blk8 = reinterpret_cast<const uint4*>(c->d_blk8);
-    p->sample8 = c->d_sample8;
-    p->dirb16 = c->d_dirb16;
-    p->n_blk8 = c->n_blk8;
+    p->sample4 = c->d_sample4;
+    p->n_blk4 = c->n_blk4;
+    p->sample2 = c->d_sample2;
+    p->n_blk2 = c->n_blk2;
     p->n_blocks = c->n_blocks;
     p->n_ranges = (uint32_t)c->h_starts.size();
     p->n_sites = c->n_sites;
@@ -428,11 +451,7 @@ gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* off
         w.flags = out->fin_in_kernel ? kWinFinalize : 0u;
         w.ctas = (uint32_t)((e - 1) / chunk - b / chunk + 1);
         w.part_base = (uint32_t)parts;
-        uint64_t np = 0;  // one block per flush piece of every CTA segment of the window
-        for (uint64_t cta = b / chunk; cta <= (e - 1) / chunk; ++cta) {
-            const uint64_t len = std::min(e, (cta + 1) * chunk) - std::max(b, cta * chunk);
-            np += (len + kFlushRecords - 1) / kFlushRecords;
-        }
+        const uint64_t np = w.ctas;  // one partial block per CTA segment of the window
         w.n_parts = (uint32_t)np;
         w.pad = 0;
         parts += np;
@@ -449,19 +468,29 @@ gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* off
 
 gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, size_t n_win,
                             const uint32_t* slots, bool finalize, WinDesc* d_wins, uint32_t* d_done,
-                            uint32_t* d_partials, uint32_t* d_keys, cudaStream_t st, uint32_t* launches) {
+                            uint32_t* d_partials, uint32_t* d_keys, cudaStream_t st, uint32_t* launches,
+                            cudaEvent_t* marks, int32_t* kinds) {
     *launches = 0;
+    // an external event node when captured into a graph, so that the host can read it
+    auto mark = [&](int32_t kind) -> gnm_status {
+        if (!marks) return GNM_OK;
+        if (kind >= 0) kinds[*launches - 1] = kind;
+        GNM_CU(cudaEventRecordWithFlags(marks[*launches], st, cudaEventRecordExternal));
+        return GNM_OK;
+    };
     if (pr.n) {
         pr.p.wins = d_wins;
         pr.p.n_wins = (uint32_t)pr.wins.size();
         pr.p.done = d_done;
         pr.p.partials = pr.partial_words ? d_partials : nullptr;
+        GNM_TRY(mark(-1));
         if (pr.sh.split) {  // keys first (same 16-byte phase as the records), then the sums
             uint32_t* keys = d_keys + pr.p.phase;
             AggParams pk = pr.p;
             if (pr.sh.keys_blk) pk.radix_bits = pr.sh.keys_bits;
             GNM_CU(launch_keys(pk, pr.sh, keys, st));
             ++*launches;
+            GNM_TRY(mark(GNM_KERNEL_KEYS));
             AggParams pa = pr.p;
             pa.src = keys;
             pa.dst = keys;
@@ -470,9 +499,11 @@ gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, s
             GNM_CU(launch_aggregate(pr.p, pr.sh, st));
         }
         ++*launches;
+        GNM_TRY(mark(GNM_KERNEL_AGGREGATE));
         if (finalize && pr.fin_grid) {
             GNM_CU(launch_finalize_windows(pr.p, st));
             ++*launches;
+            GNM_TRY(mark(GNM_KERNEL_FINALIZE));
         }
     }
     // empty windows: zero sums, no rate, no flag
@@ -666,12 +697,12 @@ void gnm_destroy(gnm_ctx* c) {
     if (c->aux) cudaStreamDestroy(c->aux);
     free_dev(c->d_starts);
     free_dev(c->d_site);
+    free_dev(c->d_pairs);
     free_dev(c->d_blocks);
     free_dev(c->d_sample);
     free_dev(c->d_dir16);
-    free_dev(c->d_blk8);
-    free_dev(c->d_sample8);
-    free_dev(c->d_dirb16);
+    free_dev(c->d_sample4);
+    free_dev(c->d_sample2);
     free_dev(c->d_violations);
     free_dev(c->d_flag_count);
     free_dev(c->d_rmi_a);
@@ -709,19 +740,20 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     release_slots(c);
     free_dev(c->d_starts);
     free_dev(c->d_site);
+    free_dev(c->d_pairs);
     free_dev(c->d_blocks);
     free_dev(c->d_sample);
     free_dev(c->d_dir16);
-    free_dev(c->d_blk8);
-    free_dev(c->d_sample8);
-    free_dev(c->d_dirb16);
+    free_dev(c->d_sample4);
+    free_dev(c->d_sample2);
     c->d_dir16 = nullptr;
-    c->d_blk8 = nullptr;
-    c->d_sample8 = nullptr;
-    c->d_dirb16 = nullptr;
-    c->n_blk8 = 0;
+    c->d_sample4 = nullptr;
+    c->n_blk4 = 0;
+    c->d_sample2 = nullptr;
+    c->n_blk2 = 0;
     c->d_starts = nullptr;
     c->d_site = nullptr;
+    c->d_pairs = nullptr;
     c->d_blocks = nullptr;
     c->d_sample = nullptr;
     c->n_blocks = 0;
@@ -733,6 +765,13 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     GNM_CU(cudaMalloc(&c->d_site, nr * 4));
     GNM_CU(cudaMemcpy(c->d_starts, starts.data(), nr * 4, cudaMemcpyHostToDevice));
     GNM_CU(cudaMemcpy(c->d_site, sites.data(), nr * 4, cudaMemcpyHostToDevice));
+    {  // (start, site) pairs: a search probe brings the site of the range it lands on
+        std::vector<uint2> pr(nr + 16);
+        for (size_t i = 0; i < nr + 16; ++i)
+            pr[i] = i < nr ? make_uint2(starts[i], sites[i]) : make_uint2(0xFFFFFFFFu, sites[nr - 1]);
+        GNM_CU(cudaMalloc(&c->d_pairs, pr.size() * sizeof(uint2)));
+        GNM_CU(cudaMemcpy(c->d_pairs, pr.data(), pr.size() * sizeof(uint2), cudaMemcpyHostToDevice));
+    }
     // staged layout: blocks of 16 range starts (the last block padded with 0xFFFFFFFF)
     // and the first start of every block
     const size_t nb = (nr + kBlockRanges - 1) / kBlockRanges;
@@ -758,28 +797,14 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     }
     GNM_CU(cudaMalloc(&c->d_dir16, dir.size() * 4));
     GNM_CU(cudaMemcpy(c->d_dir16, dir.data(), dir.size() * 4, cudaMemcpyHostToDevice));
-    // key-kernel layout: 8-range blocks carrying their sites, and a 16-bit directory of
-    // block indices (when the block count fits 16 bits)
-    const size_t nb8 = (nr + 7) / 8;
-    if (nb8 < 65536) {
-        std::vector<uint32_t> b8(nb8 * 16), s8(nb8);
-        std::vector<uint16_t> db(65537);
-        for (size_t j = 0; j < nb8; ++j) {
-            for (size_t k = 0; k < 8; ++k) {
-                const size_t i = j * 8 + k;
-                b8[j * 16 + k] = i < nr ? starts[i] : 0xFFFFFFFFu;
-                b8[j * 16 + 8 + k] = i < nr ? sites[i] : sites[nr - 1];
-            }
-            s8[j] = starts[j * 8];
-        }
-        for (size_t t = 0; t <= 65536; ++t) db[t] = (uint16_t)(dir[t] / 8);
-        GNM_CU(cudaMalloc(&c->d_blk8, b8.size() * 4));
-        GNM_CU(cudaMalloc(&c->d_sample8, s8.size() * 4));
-        GNM_CU(cudaMalloc(&c->d_dirb16, db.size() * 2));
-        GNM_CU(cudaMemcpy(c->d_blk8, b8.data(), b8.size() * 4, cudaMemcpyHostToDevice));
-        GNM_CU(cudaMemcpy(c->d_sample8, s8.data(), s8.size() * 4, cudaMemcpyHostToDevice));
-        GNM_CU(cudaMemcpy(c->d_dirb16, db.data(), db.size() * 2, cudaMemcpyHostToDevice));
-        c->n_blk8 = (uint32_t)nb8;
+    for (size_t br : {(size_t)2, (size_t)4}) {  // key kernel: first start of every 2- and 4-range block
+        const size_t nb = (nr + br - 1) / br;
+        std::vector<uint32_t> sb(nb);
+        for (size_t g = 0; g < nb; ++g) sb[g] = starts[br * g];
+        uint32_t** d = br == 2 ? &c->d_sample2 : &c->d_sample4;
+        GNM_CU(cudaMalloc(d, nb * 4));
+        GNM_CU(cudaMemcpy(*d, sb.data(), nb * 4, cudaMemcpyHostToDevice));
+        (br == 2 ? c->n_blk2 : c->n_blk4) = (uint32_t)nb;
     }
     GNM_CU(cudaMalloc(&c->d_blocks, blk.size() * 4));
     GNM_CU(cudaMalloc(&c->d_sample, nb * 4));

@@ -69,7 +69,7 @@ struct Staging {
 };
 
 struct Tuned {
-    int block = 0, ctas_per_sm = 0, unroll = 0, agg = 0, placement = 0, split = 0;
+    int block = 0, ctas_per_sm = 0, unroll = 0, agg = 0, placement = 0, split = 0, key_dir = 0;
     uint32_t radix_bits = 0;
 };
 
@@ -89,14 +89,15 @@ struct gnm_ctx {
     std::vector<uint32_t> h_starts, h_site;
     uint32_t* d_starts = nullptr;
     uint32_t* d_site = nullptr;
+    uint2* d_pairs = nullptr;       // (start, site) interleaved, 16 padding entries at the end
     uint32_t* d_blocks = nullptr;   // staged placement: [n_blocks][8 starts, 8 sites]
     uint32_t* d_sample = nullptr;   // staged placement: first start of every block
     uint32_t n_blocks = 0;
     uint32_t* d_dir16 = nullptr;    // radix directory: range of each /16's first address
-    uint32_t* d_blk8 = nullptr;     // key kernel: blocks of 8 ranges (8 starts, 8 sites)
-    uint32_t* d_sample8 = nullptr;  // key kernel: first start of every 8-range block
-    uint16_t* d_dirb16 = nullptr;   // key kernel: 8-range block of each /16's first address
-    uint32_t n_blk8 = 0;
+    uint32_t* d_sample4 = nullptr;  // key kernel: first start of every 4-range block
+    uint32_t n_blk4 = 0;
+    uint32_t* d_sample2 = nullptr;  // key kernel: first start of every 2-range block
+    uint32_t n_blk2 = 0;
     uint32_t local_pfx[GNM_MAX_LOCAL] = {0};
     uint32_t local_mask[GNM_MAX_LOCAL] = {0};
     uint32_t n_local = 0;
@@ -154,9 +155,12 @@ struct Prepared {
 gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* offsets, size_t n_win,
                           const uint32_t* slots, bool finalize, Prepared* out);
 // Enqueues the kernels of a prepared launch (descriptors already on the device).
+// marks (optional, 4 timing events): recorded before the first kernel and after each
+// one; kinds[i] receives the gnm_kernel_kind of kernel i.
 gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, size_t n_win,
                             const uint32_t* slots, bool finalize, WinDesc* d_wins, uint32_t* d_done,
-                            uint32_t* d_partials, uint32_t* d_keys, cudaStream_t st, uint32_t* launches);
+                            uint32_t* d_partials, uint32_t* d_keys, cudaStream_t st, uint32_t* launches,
+                            cudaEvent_t* marks = nullptr, int32_t* kinds = nullptr);
 // Next launch-scratch entry of the ring (waits for its previous use).
 gnm_status acquire_ring(gnm_ctx* c, uint32_t n_win, LaunchBuf** out);
 void set_slots_done(gnm_ctx* c, const uint32_t* slots, size_t n, cudaEvent_t ev, bool finalized);

@@ -61,14 +61,15 @@ struct AggParams {
     // registry
     const uint32_t* starts;
     const uint32_t* rsite;
+    const uint2* pairs;          // (start, site) of every range, then 16 padding entries
     const uint4* blocks;         // staged placement: 16 starts per block (64 bytes)
     const uint32_t* sample;      // staged placement: first start of every block
     const uint32_t* dir16;       // radix directory over the top 16 bits (65537 entries)
     uint32_t radix_bits;         // directory bits used by this launch (<= 16)
-    const uint4* blk8;           // key kernel: blocks of 8 ranges (8 starts, then 8 sites)
-    const uint32_t* sample8;     // key kernel: first start of every 8-range block
-    const uint16_t* dirb16;      // key kernel: 8-range block of each /16's first address
-    uint32_t n_blk8;
+    const uint32_t* sample4;     // key kernel: first start of every 4-range block of pairs
+    uint32_t n_blk4;
+    const uint32_t* sample2;     // key kernel: first start of every 2-range block of pairs
+    uint32_t n_blk2;
     uint32_t n_blocks;
     uint32_t n_ranges;
     uint32_t n_sites;
@@ -100,10 +101,11 @@ struct AggParams {
 
 // kLookupKeys: the aggregation reads per-record keys that a lookup kernel wrote (split
 // launches), instead of addresses.
-// kLookupRadixBlk (key kernel only): 16-bit block directory in shared memory, one 64-byte
-// block of 8 starts and 8 sites from L2.
+// kLookupRadixBlk / kLookupRadixBlk2 (key kernel only): a directory of blocks of 4 (2)
+// ranges and the blocks' first starts in shared memory; one 32-byte (16-byte) load of the
+// block's (start, site) pairs ends the lookup.
 enum { kLookupL2 = 0, kLookupSmem = 1, kLookupRmi = 2, kLookupStaged = 3, kLookupRadix = 4, kLookupKeys = 5,
-       kLookupRadixBlk = 6 };
+       kLookupRadixBlk = 6, kLookupRadixBlk2 = 7 };
 constexpr uint32_t kBlockRanges = 16;  // ranges per staged block (16 starts, 64 bytes)
 enum { kTableDirect = 0, kTableHash = 1, kTableGlobal = 2 };
 
@@ -124,7 +126,7 @@ struct LaunchShape {
     int split;
     int keys_grid, keys_block;
     size_t keys_smem;
-    int keys_blk;          // radix key kernel uses the 16-bit block directory
+    int keys_blk;          // radix key kernel: ranges per block of its shared block samples (0: none)
     uint32_t keys_bits;    // its directory bits
 };
 

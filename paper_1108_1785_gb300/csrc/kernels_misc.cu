@@ -16,6 +16,7 @@ cudaError_t launch_keys_rmi(const AggParams& p, const LaunchShape& s, uint32_t* 
 cudaError_t launch_keys_staged(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
 cudaError_t launch_keys_radix(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
 cudaError_t launch_keys_radixblk(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
+cudaError_t launch_keys_radixblk2(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
 
 cudaError_t launch_keys(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st) {
     switch (s.lookup) {
@@ -23,7 +24,9 @@ cudaError_t launch_keys(const AggParams& p, const LaunchShape& s, uint32_t* keys
         case kLookupRmi: return launch_keys_rmi(p, s, keys, st);
         case kLookupStaged: return launch_keys_staged(p, s, keys, st);
         case kLookupRadix:
-            return s.keys_blk ? launch_keys_radixblk(p, s, keys, st) : launch_keys_radix(p, s, keys, st);
+            return s.keys_blk == 2   ? launch_keys_radixblk2(p, s, keys, st)
+                   : s.keys_blk == 4 ? launch_keys_radixblk(p, s, keys, st)
+                                     : launch_keys_radix(p, s, keys, st);
         default: return launch_keys_l2(p, s, keys, st);
     }
 }
@@ -48,15 +51,15 @@ size_t aggregate_smem_bytes(int lookup, int table, uint32_t n_ranges, uint32_t k
 namespace {
 
 __global__ void k_finalize(const __grid_constant__ AggParams p, uint32_t slot) {
-    dev::finalize_rows(p, slot, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    dev::finalize_rows<true>(p, slot, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // blockIdx.y: window of the launch; its keys are spread over blockIdx.x.
 __global__ void k_finalize_windows(const __grid_constant__ AggParams p) {
     const WinDesc wd = p.wins[blockIdx.y];
     const uint32_t* parts = p.partials ? p.partials + (size_t)wd.part_base * p.keys * 5 : nullptr;
-    dev::finalize_rows(p, wd.slot, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, parts,
-                       p.partials ? wd.n_parts : 0u);
+    dev::finalize_rows<true>(p, wd.slot, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, parts,
+                             p.partials ? wd.n_parts : 0u);
 }
 
 // Keys (site*2+dir) whose eligible flows reach min_flows and whose rate is strictly

@@ -26,6 +26,10 @@ struct gnm_plan {
     std::vector<uint32_t> slots;
     cudaEvent_t ev = nullptr;
     uint32_t launches = 0;
+    bool timed = false;
+    bool launched = false;
+    cudaEvent_t marks[4] = {nullptr, nullptr, nullptr, nullptr};  // around each kernel
+    int32_t kinds[3] = {0, 0, 0};
 };
 
 using namespace gnm;
@@ -47,6 +51,8 @@ static void plan_free(gnm_plan* p) {
     if (p->d_partials) cudaFree(p->d_partials);
     if (p->d_keys) cudaFree(p->d_keys);
     if (p->ev) cudaEventDestroy(p->ev);
+    for (auto e : p->marks)
+        if (e) cudaEventDestroy(e);
     delete p;
 }
 
@@ -54,7 +60,13 @@ extern "C" {
 
 gnm_status gnm_plan_create(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets,
                            const uint64_t* wids, size_t n_win, gnm_plan** out) {
+    return gnm_plan_create_ex(c, rec, offsets, wids, n_win, 0, out);
+}
+
+gnm_status gnm_plan_create_ex(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets,
+                              const uint64_t* wids, size_t n_win, uint32_t flags, gnm_plan** out) {
     if (!c || !out || !wids) return fail(GNM_E_INVAL, "NULL argument");
+    if (flags & ~GNM_PLAN_KERNEL_TIMES) return fail(GNM_E_INVAL, "unknown plan flags");
     *out = nullptr;
     if (n_win == 0) return fail(GNM_E_INVAL, "a plan needs at least one window");
     GNM_CU(cudaSetDevice(c->device));
@@ -67,10 +79,14 @@ gnm_status gnm_plan_create(gnm_ctx* c, const gnm_records* rec, const uint64_t* o
     gnm_plan* p = new (std::nothrow) gnm_plan();
     if (!p) return fail(GNM_E_NOMEM, "host allocation failed");
     p->c = c;
+    p->timed = (flags & GNM_PLAN_KERNEL_TIMES) != 0;
     auto bail = [&](gnm_status s) {
         plan_free(p);
         return s;
     };
+    if (p->timed)
+        for (auto& e : p->marks)
+            if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(GNM_E_CUDA, "event creation failed"));
     for (size_t k = 0; k < n_win; ++k) {
         uint32_t s;
         gnm_status st = acquire_slot_pinned(c, wids[k], c->aux, &s);
@@ -103,7 +119,7 @@ gnm_status gnm_plan_create(gnm_ctx* c, const gnm_records* rec, const uint64_t* o
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         st = enqueue_prepared(c, pr, offsets, n_win, p->slots.data(), true, p->d_wins, p->d_done, p->d_partials,
-                              p->d_keys, cs, &p->launches);
+                              p->d_keys, cs, &p->launches, p->timed ? p->marks : nullptr, p->kinds);
         e = cudaStreamEndCapture(cs, &g);
     }
     if (e == cudaSuccess && st == GNM_OK) e = cudaGraphInstantiate(&p->exec, g, 0);
@@ -126,6 +142,22 @@ gnm_status gnm_plan_launch(gnm_plan* p, void* stream) {
     GNM_CU(cudaEventRecord(p->ev, st));
     set_slots_done(c, p->slots.data(), p->slots.size(), p->ev, true);
     c->last_launches = p->launches;
+    p->launched = true;
+    return GNM_OK;
+}
+
+gnm_status gnm_plan_kernel_times(gnm_plan* p, float* ms, int32_t* kind, size_t cap, size_t* n_out) {
+    if (!p || !n_out) return fail(GNM_E_INVAL, "NULL argument");
+    if (!p->timed) return fail(GNM_E_STATE, "plan created without GNM_PLAN_KERNEL_TIMES");
+    if (!p->launched) return fail(GNM_E_STATE, "plan never launched");
+    *n_out = p->launches;
+    if (cap < p->launches) return fail(GNM_E_CAPACITY, "cap smaller than the plan's kernel count");
+    GNM_CU(cudaSetDevice(p->c->device));
+    GNM_CU(cudaEventSynchronize(p->ev));
+    for (uint32_t i = 0; i < p->launches; ++i) {
+        if (ms) GNM_CU(cudaEventElapsedTime(&ms[i], p->marks[i], p->marks[i + 1]));
+        if (kind) kind[i] = p->kinds[i];
+    }
     return GNM_OK;
 }
 
@@ -184,7 +216,10 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
     std::vector<int> splits_v;
     if (base_shape.lookup == kLookupSmem) splits_v.push_back(GNM_SPLIT_FUSED);
     else splits_v = {GNM_SPLIT_FUSED, GNM_SPLIT_TWO_KERNELS};
+    std::vector<int> kdirs_v = {0};
+    if (base_shape.lookup == kLookupRadix) kdirs_v = {3, 1, 2};
     for (int sp : splits_v)
+    for (int kd : kdirs_v)
     for (int b : blocks)
         for (int u : unrolls)
             for (int a : aggs)
@@ -201,6 +236,8 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
                             if (c->cfg.radix_bits == 0) c->cfg.radix_bits = (uint32_t)rb;
                             if (c->cfg.ctas_per_sm == 0) c->cfg.ctas_per_sm = cps;
                             if (c->cfg.split == GNM_SPLIT_AUTO) c->cfg.split = sp;
+                            if (sp == GNM_SPLIT_FUSED && kd == 2) continue;  // the key kernel's knob
+                            if (c->cfg.key_directory == 0) c->cfg.key_directory = kd;
                             LaunchShape sh;
                             if (choose_shape(c, offsets[n_win] - offsets[0], &sh) != GNM_OK) continue;  // does not fit
                             double ms;
@@ -215,6 +252,7 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
                                 rep->ctas_per_sm = sh.ctas_per_sm;
                                 rep->radix_bits = sh.radix_bits;
                                 rep->split = sh.split ? GNM_SPLIT_TWO_KERNELS : GNM_SPLIT_FUSED;
+                                rep->key_directory = c->cfg.key_directory;
                             }
                         }
     c->cfg = saved;
@@ -231,6 +269,7 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
     c->tuned.ctas_per_sm = rep->ctas_per_sm;
     c->tuned.radix_bits = rep->radix_bits;
     c->tuned.split = rep->split;
+    c->tuned.key_dir = rep->key_directory;
     // leave the windows holding the results of the chosen shape
     return gnm_windows_process(c, rec, offsets, wids, n_win, st) == GNM_OK && cudaStreamSynchronize(st) == cudaSuccess
                ? GNM_OK

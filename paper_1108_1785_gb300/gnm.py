@@ -25,6 +25,8 @@ ADMIN_OR, ADMIN_AND = 0, 1
 TABLE_AUTO, TABLE_DIRECT, TABLE_HASH, TABLE_GLOBAL = 0, 1, 2, 3
 SPLIT_AUTO, SPLIT_FUSED, SPLIT_TWO_KERNELS = 0, 1, 2
 ROOT_LINEAR, ROOT_MLP = 0, 1
+KERNEL_TIMES = 1  # GNM_PLAN_KERNEL_TIMES
+KERNEL_NAMES = {0: "k_keys", 1: "k_aggregate", 2: "k_finalize_windows"}
 FIELDS = ("srcaddr", "dstaddr", "dPkts", "dOctets", "first", "last")
 
 STATUS = {0: "GNM_OK", 1: "GNM_E_INVAL", 2: "GNM_E_NOMEM", 3: "GNM_E_CUDA", 4: "GNM_E_STATE",
@@ -97,7 +99,7 @@ class TuneReport(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("unroll", C.c_int32),
                 ("aggregation", C.c_int32), ("placement", C.c_int32), ("best_ms", C.c_double),
                 ("default_ms", C.c_double), ("n_tried", C.c_uint32), ("radix_bits", C.c_uint32),
-                ("split", C.c_int32)]
+                ("split", C.c_int32), ("key_directory", C.c_int32)]
 
 
 _lib = None
@@ -143,6 +145,8 @@ def lib():
             "gnm_rmi_import": (st, [P, C.c_int32, U32, P, P, P, P, P]),
             "gnm_plan_create": (st, [P, C.POINTER(RecordsC), P, P, S, C.POINTER(P)]),
             "gnm_plan_launch": (st, [P, P]),
+            "gnm_plan_create_ex": (st, [P, C.POINTER(RecordsC), P, P, S, U32, C.POINTER(P)]),
+            "gnm_plan_kernel_times": (st, [P, P, P, S, C.POINTER(S)]),
             "gnm_plan_destroy": (None, [P]),
             "gnm_autotune": (st, [P, C.POINTER(RecordsC), P, P, S, C.POINTER(TuneReport)]),
             "gnm_last_launch_count": (U32, [P]),
@@ -446,8 +450,8 @@ class Context:
                                      _stream_ptr(stream)))
 
     # ---------------------------------------------------------- plans / tuning
-    def plan(self, rec: Records, offsets, window_ids) -> "Plan":
-        return Plan(self, rec, offsets, window_ids)
+    def plan(self, rec: Records, offsets, window_ids, kernel_times: bool = False) -> "Plan":
+        return Plan(self, rec, offsets, window_ids, kernel_times)
 
     def autotune(self, rec: Records, offsets, window_ids) -> TuneReport:
         off = np.ascontiguousarray(offsets, np.uint64)
@@ -460,17 +464,26 @@ class Context:
 class Plan:
     """A CUDA-graph launch of many windows over fixed device buffers."""
 
-    def __init__(self, ctx: Context, rec: Records, offsets, window_ids):
+    def __init__(self, ctx: Context, rec: Records, offsets, window_ids, kernel_times: bool = False):
         self.ctx = ctx
         self.rec = rec
         off = np.ascontiguousarray(offsets, np.uint64)
         ids = np.ascontiguousarray(window_ids, np.uint64)
         h = C.c_void_p()
-        ctx._c(lib().gnm_plan_create(ctx.h, C.byref(rec.c), _ptr(off), _ptr(ids), ids.size, C.byref(h)))
+        ctx._c(lib().gnm_plan_create_ex(ctx.h, C.byref(rec.c), _ptr(off), _ptr(ids), ids.size,
+                                        KERNEL_TIMES if kernel_times else 0, C.byref(h)))
         self.h = h
 
     def launch(self, stream=None):
         self.ctx._c(lib().gnm_plan_launch(self.h, _stream_ptr(stream)))
+
+    def kernel_times(self):
+        """[(kernel name, ms)] of the last launch, in launch order (plans made with kernel_times)."""
+        ms = np.zeros(3, np.float32)
+        kind = np.zeros(3, np.int32)
+        n = C.c_size_t()
+        self.ctx._c(lib().gnm_plan_kernel_times(self.h, _ptr(ms), _ptr(kind), 3, C.byref(n)))
+        return [(KERNEL_NAMES[int(kind[i])], float(ms[i])) for i in range(n.value)]
 
     def close(self):
         if getattr(self, "h", None):

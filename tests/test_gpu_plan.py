@@ -104,3 +104,36 @@ def test_windows_results_batch_readout(gnm, batch):
     for w in range(W):
         assert_window_matches((st[w], un[w], r[w], f[w]), expect[w])
     ctx.close()
+
+
+@pytest.mark.parametrize("which", ["c1", "c2"])
+def test_plan_kernel_times(gnm, which):
+    """A plan made with kernel timing names its kernels in launch order, each with a positive
+    device duration, and still gives the oracle's results; without the flag it refuses."""
+    reg = fg.registry_c1() if which == "c1" else fg.registry_c2()
+    rec = fg.make_records(reg, 400_000, seed=31)
+    off = [0, 150_000, 150_000, 400_000]
+    ctx = gnm.Context(window_slots=8)
+    ctx.load(reg)
+    d = gnm.Records.to_device(rec)
+    plain = ctx.plan(d, off, [1, 2, 3])
+    plain.launch()
+    with pytest.raises(gnm.GnmError, match="STATE"):
+        plain.kernel_times()
+    plain.close()
+    plan = ctx.plan(d, off, [1, 2, 3], kernel_times=True)
+    with pytest.raises(gnm.GnmError, match="STATE"):
+        plan.kernel_times()  # not launched yet
+    for _ in range(2):
+        plan.launch()
+        kt = plan.kernel_times()
+        names = [k for k, _ in kt]
+        if which == "c1":  # registry in shared memory: one fused kernel
+            assert names == ["k_aggregate"]
+        else:
+            assert names == ["k_keys", "k_aggregate", "k_finalize_windows"]
+        assert all(ms > 0 for _, ms in kt)
+    for w, (a, b) in zip([1, 2, 3], zip(off[:-1], off[1:])):
+        assert_window_matches(ctx.dense(w), oracle_full(reg, {k: v[a:b] for k, v in rec.items()}))
+    plan.close()
+    ctx.close()

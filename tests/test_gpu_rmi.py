@@ -220,6 +220,34 @@ def test_rmi_sample_bounds_fall_back_exactly(gnm, c3):
     ctx.close()
 
 
+@pytest.mark.parametrize("split", ["SPLIT_TWO_KERNELS", "SPLIT_FUSED"])
+@pytest.mark.parametrize("unroll", [1, 2])
+def test_rmi_window_fallback_exact(gnm, c3, split, unroll):
+    """The window kernels' learned-index lookups (several in lock step per thread) with
+    bounds from a small sample: records whose address misses its model window take the full
+    search, the window stays equal to the oracle, and the misses are counted."""
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx = gnm.Context(window_slots=2, split=getattr(gnm, split), unroll=unroll)
+    ctx.load(reg)
+    ctx.rmi_train(to_dev(keys[:20000]), n_leaves=4096, exhaustive_eps=0)
+    assert ctx.registry_info().lookup_mode == gnm.LOOKUP_RMI
+    ctx.rmi_violations(reset=True)
+    rng = np.random.default_rng(4)
+    w = {k: v[:300_001] for k, v in rec.items()}
+    w["srcaddr"] = w["srcaddr"].copy()
+    w["dstaddr"] = w["dstaddr"].copy()
+    # uniformly random remote addresses in a third of the records: many fall outside the
+    # sampled key range of their leaves
+    sel = rng.random(w["srcaddr"].size) < 0.33
+    lp, ll = int(reg.local_prefix[0]), int(reg.local_len[0])
+    w["srcaddr"][sel] = rng.integers(0, 1 << 32, int(sel.sum()), dtype=np.uint64).astype(np.uint32)
+    w["dstaddr"][sel] = (lp | rng.integers(0, 1 << (32 - ll), int(sel.sum()))).astype(np.uint32)
+    ctx.process(gnm.Records.to_device(w), 1)
+    assert_window_matches(ctx.dense(1), oracle_full(reg, w, lpm=lpm))
+    assert ctx.rmi_violations() > 0
+    ctx.close()
+
+
 def test_mlp_root_rmi_exact(gnm, c3):
     reg, lpm, starts, sites, rec, keys = c3
     ctx = gnm.Context(window_slots=2)

@@ -155,7 +155,9 @@ def c2hour():
 
 
 @pytest.mark.parametrize("cfg", [{}, {"split": "FUSED"}, {"lookup_mode": "BSEARCH"}, {"key_directory": 1},
-                                 {"key_directory": 1, "radix_bits": 16}, {"key_directory": 1, "radix_bits": 4},
+                                 {"key_directory": 2}, {"key_directory": 3}, {"key_directory": 3, "radix_bits": 8},
+                                 {"key_directory": 1, "radix_bits": 15},
+                                 {"key_directory": 1, "radix_bits": 4}, {"key_directory": 2, "radix_bits": 14},
                                  {"radix_bits": 10}, {"radix_bits": 4},
                                  {"lookup_mode": "BSEARCH", "placement": "L2", "split": "FUSED"},
                                  {"aggregation": "WARP"}, {"hash_slots": 1024}, {"table_mode": "GLOBAL"},
@@ -270,6 +272,16 @@ def test_radix_directory_must_fit(gnm):
     ctx = _ctx(gnm, reg, lookup_mode=gnm.LOOKUP_RADIX, radix_bits=16, split=gnm.SPLIT_FUSED)
     d = gnm.Records.to_device(fg.make_records(reg, 1000, seed=3))
     with pytest.raises(gnm.GnmError, match="radix directory too large"):
+        ctx.process(d, 1)
+    ctx.close()
+
+
+def test_block_samples_must_fit(gnm):
+    reg = fg.registry_c2()
+    # a 16-bit block directory (256 KB) and the block samples exceed one CTA's shared memory
+    ctx = _ctx(gnm, reg, lookup_mode=gnm.LOOKUP_RADIX, radix_bits=16, key_directory=1)
+    d = gnm.Records.to_device(fg.make_records(reg, 1000, seed=3))
+    with pytest.raises(gnm.GnmError, match="block samples do not fit"):
         ctx.process(d, 1)
     ctx.close()
 
