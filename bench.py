@@ -67,7 +67,7 @@ def workload_desc(n_records, n_windows, reg, n_ranges):
 LOOKUP_NAMES = {1: "binary search", 2: "learned index (RMI)", 3: "radix directory + binary search"}
 
 
-def learned_vs_plain(gnm, torch, local, steps, warmup, n_records=50_000_000):
+def learned_vs_plain(gnm, torch, local, steps, warmup, n_records=50_000_000, modes=("bsearch", "radix", "rmi")):
     """Same GPU, same records, 100,000-site / 1,000,000-prefix registry: one window of
     n_records processed with the plain binary search, the radix-directed search and the
     learned index. Results must be bit-exact across the three; throughput per lookup."""
@@ -84,6 +84,8 @@ def learned_vs_plain(gnm, torch, local, steps, warmup, n_records=50_000_000):
     for name, cfg in (("bsearch", dict(lookup_mode=gnm.LOOKUP_BSEARCH)),
                       ("radix", dict(lookup_mode=gnm.LOOKUP_RADIX)),
                       ("rmi", dict(lookup_mode=gnm.LOOKUP_RMI))):
+        if name not in modes:
+            continue
         ctx = gnm.Context(device=local, window_slots=4, **cfg)
         ctx.load(reg)
         if name == "rmi":
@@ -120,13 +122,14 @@ def learned_vs_plain(gnm, torch, local, steps, warmup, n_records=50_000_000):
         info_out["n_ranges"] = int(info.n_ranges)
         plan.close()
         ctx.close()
-    exact = all(np.array_equal(dense[k][i], dense["bsearch"][i], equal_nan=(i == 2))
-                for k in ("radix", "rmi") for i in range(4))
+    ref = next(iter(dense))
+    exact = all(np.array_equal(dense[k][i], dense[ref][i], equal_nan=(i == 2)) for k in dense for i in range(4))
     return {"workload": f"one window of {n_records:,} records; {reg.n_sites:,} sites / {reg.n:,} prefixes "
                         f"(/16-/30, 30% nested) -> {info_out['n_ranges']:,} ranges; Zipf(0.9), 90% registered",
             "peak_gbs": peak, "peak_kind": peak_kind, "bitexact_across_lookups": bool(exact),
             "rmi_model": info_out.get("rmi"), **res,
-            "rmi_speedup_vs_bsearch": res["bsearch"]["ms"] / res["rmi"]["ms"]}
+            "rmi_speedup_vs_bsearch": (res["bsearch"]["ms"] / res["rmi"]["ms"]
+                                       if "bsearch" in res and "rmi" in res else None)}
 
 
 def serve_c5(gnm, torch, local, minutes=30, speedup=600.0, pool_n=20_000_000, budget=4 << 30, check=2):
@@ -360,6 +363,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the plain-vs-learned index comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the streaming-server replay")
+    ap.add_argument("--only", default="all", choices=["all", "learned", "serve"],
+                    help="run one leg alone (profiling): the learned-index comparison or the server replay")
+    ap.add_argument("--learned-records", type=int, default=50_000_000)
+    ap.add_argument("--learned-modes", default="bsearch,radix,rmi")
     ap.add_argument("--serve-minutes", type=int, default=30)
     ap.add_argument("--serve-speedup", type=float, default=600.0)
     args = ap.parse_args()
@@ -374,6 +381,14 @@ def main():
     world, rank, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     build.build()
+    if args.only != "all":  # one leg alone, for profiling; prints its own JSON object
+        if args.only == "learned":
+            leg = learned_vs_plain(gnm, torch, local, args.steps, args.warmup, args.learned_records,
+                                   tuple(args.learned_modes.split(",")))
+        else:
+            leg = serve_c5(gnm, torch, local, minutes=args.serve_minutes, speedup=args.serve_speedup)
+        print(json.dumps({"leg": args.only, **leg}), flush=True)
+        return 0
     reg = fg.registry_c2()
     rec, off = fg.hour_records_c2(reg, seed=1 + rank)
     n = int(off[-1])
@@ -522,7 +537,8 @@ def main():
     ctx.close()
     del dev
     if world == 1 and not args.no_learned:
-        out["learned_index"] = learned_vs_plain(gnm, torch, local, args.steps, args.warmup)
+        out["learned_index"] = learned_vs_plain(gnm, torch, local, args.steps, args.warmup, args.learned_records,
+                                                tuple(args.learned_modes.split(",")))
     if world == 1 and not args.no_serve:
         out["serving"] = serve_c5(gnm, torch, local, minutes=args.serve_minutes, speedup=args.serve_speedup)
     if rank == 0:
