@@ -81,18 +81,17 @@ def learned_vs_plain(gnm, torch, local, steps, warmup, n_records=50_000_000, mod
     peak, peak_kind = hbm_peak()
     stream = torch.cuda.current_stream()
     res, dense, info_out = {}, {}, {}
-    for name, cfg in (("bsearch", dict(lookup_mode=gnm.LOOKUP_BSEARCH)),
-                      ("radix", dict(lookup_mode=gnm.LOOKUP_RADIX)),
-                      ("rmi", dict(lookup_mode=gnm.LOOKUP_RMI))):
-        if name not in modes:
-            continue
-        ctx = gnm.Context(device=local, window_slots=4, **cfg)
+    # "rmi" is the 4,096-leaf model; "rmiL" a model of L leaves (same training otherwise)
+    for name in modes:
+        leaves = (int(name[3:]) if len(name) > 3 else 4096) if name.startswith("rmi") else 0
+        mode = {"bsearch": gnm.LOOKUP_BSEARCH, "radix": gnm.LOOKUP_RADIX}.get(name, gnm.LOOKUP_RMI)
+        ctx = gnm.Context(device=local, window_slots=4, lookup_mode=mode)
         ctx.load(reg)
-        if name == "rmi":
-            rep = ctx.rmi_train(keys, root_kind=gnm.ROOT_LINEAR, n_leaves=4096, leaf_iters=4)
-            info_out["rmi"] = {"leaves": 4096, "root": "linear", "eps_max": int(rep.eps_max),
-                               "eps_mean": round(float(rep.eps_mean), 2), "train_ms": round(float(rep.train_ms), 1),
-                               "sweep_ms": round(float(rep.sweep_ms), 1), "train_keys": int(keys.numel())}
+        if leaves:
+            rep = ctx.rmi_train(keys, root_kind=gnm.ROOT_LINEAR, n_leaves=leaves, leaf_iters=4)
+            info_out[name] = {"leaves": leaves, "root": "linear", "eps_max": int(rep.eps_max),
+                              "eps_mean": round(float(rep.eps_mean), 2), "train_ms": round(float(rep.train_ms), 1),
+                              "sweep_ms": round(float(rep.sweep_ms), 1), "train_keys": int(keys.numel())}
             ctx.rmi_violations(reset=True)
         plan = ctx.plan(dev, [0, n_records], [1], kernel_times=True)
         for _ in range(warmup):
@@ -116,8 +115,9 @@ def learned_vs_plain(gnm, torch, local, steps, warmup, n_records=50_000_000, mod
         res[name] = {"records_per_s": n_records / (ms / 1e3), "ms": ms, "achieved_gbs": gbs,
                      "frac": gbs / peak, "launches": ctx.last_launch_count(), "kernels_ms": kms,
                      "lookup": LOOKUP_NAMES.get(int(info.lookup_mode), str(int(info.lookup_mode)))}
-        if name == "rmi":
+        if leaves:
             res[name]["violations"] = ctx.rmi_violations()
+            res[name]["model"] = info_out[name]
         dense[name] = ctx.dense(1)
         info_out["n_ranges"] = int(info.n_ranges)
         plan.close()
@@ -127,9 +127,52 @@ def learned_vs_plain(gnm, torch, local, steps, warmup, n_records=50_000_000, mod
     return {"workload": f"one window of {n_records:,} records; {reg.n_sites:,} sites / {reg.n:,} prefixes "
                         f"(/16-/30, 30% nested) -> {info_out['n_ranges']:,} ranges; Zipf(0.9), 90% registered",
             "peak_gbs": peak, "peak_kind": peak_kind, "bitexact_across_lookups": bool(exact),
-            "rmi_model": info_out.get("rmi"), **res,
+            **res,
             "rmi_speedup_vs_bsearch": (res["bsearch"]["ms"] / res["rmi"]["ms"]
                                        if "bsearch" in res and "rmi" in res else None)}
+
+
+def batched_c4(gnm, torch, local, steps, warmup):
+    """256 uneven windows (lognormal sizes around 200,000 records, clamped to 10,000-2,000,000)
+    over the 500-site registry in one CUDA-graph launch, shape autotuned by the library."""
+    import flowgen as fg
+    reg = fg.registry_c1()
+    counts = fg.uneven_windows_c4()
+    rec, off = fg.batched_records_c4(reg, counts)
+    n, n_win = int(off[-1]), len(off) - 1
+    dev = gnm.Records.to_device(rec)
+    del rec
+    ctx = gnm.Context(device=local, window_slots=n_win + 8)
+    ctx.load(reg)
+    ids = np.arange(n_win, dtype=np.uint64)
+    tune = ctx.autotune(dev, off, ids)
+    plan = ctx.plan(dev, off, ids, kernel_times=True)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        plan.launch(stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        plan.launch(stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    plan.launch(stream)
+    kms = {k: round(v, 4) for k, v in plan.kernel_times()}
+    info = ctx.registry_info()
+    alg = 24 * n + n_win * (2 * reg.n_sites * (48 + 8 + 1) + 4 * 48) + int(info.n_ranges) * 8
+    peak, peak_kind = hbm_peak()
+    gbs = alg / (ms / 1e3) / 1e9
+    plan.close()
+    ctx.close()
+    return {"workload": f"{n_win} windows, {n:,} records (lognormal sizes, median 200,000, clamped "
+                        f"10,000-2,000,000); {reg.n_sites} sites / {reg.n:,} prefixes -> {int(info.n_ranges):,} "
+                        f"ranges (registry in shared memory); one CUDA-graph launch",
+            "records_per_s": n / (ms / 1e3), "ms": ms, "achieved_gbs": gbs, "frac": gbs / peak,
+            "peak_kind": peak_kind, "kernels_ms": kms,
+            "tuned": {"block_threads": tune.block_threads, "unroll": tune.unroll, "aggregation": tune.aggregation,
+                      "placement": tune.placement, "ctas_per_sm": tune.ctas_per_sm}}
 
 
 def serve_c5(gnm, torch, local, minutes=30, speedup=600.0, pool_n=20_000_000, budget=4 << 30, check=2):
@@ -363,8 +406,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the plain-vs-learned index comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the streaming-server replay")
-    ap.add_argument("--only", default="all", choices=["all", "learned", "serve"],
-                    help="run one leg alone (profiling): the learned-index comparison or the server replay")
+    ap.add_argument("--only", default="all", choices=["all", "learned", "serve", "batched"],
+                    help="run one leg alone (profiling): the learned-index comparison, the server replay "
+                         "or the batched windows")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-window batched launch")
     ap.add_argument("--learned-records", type=int, default=50_000_000)
     ap.add_argument("--learned-modes", default="bsearch,radix,rmi")
     ap.add_argument("--serve-minutes", type=int, default=30)
@@ -385,6 +430,8 @@ def main():
         if args.only == "learned":
             leg = learned_vs_plain(gnm, torch, local, args.steps, args.warmup, args.learned_records,
                                    tuple(args.learned_modes.split(",")))
+        elif args.only == "batched":
+            leg = batched_c4(gnm, torch, local, args.steps, args.warmup)
         else:
             leg = serve_c5(gnm, torch, local, minutes=args.serve_minutes, speedup=args.serve_speedup)
         print(json.dumps({"leg": args.only, **leg}), flush=True)
@@ -490,7 +537,7 @@ def main():
                              f"CUDA graph per step: {launches // max(1, args.steps)} kernel launch(es)",
                    "tuned": {"block_threads": tune.block_threads, "ctas_per_sm": tune.ctas_per_sm,
                              "unroll": tune.unroll, "aggregation": tune.aggregation, "placement": tune.placement,
-                             "radix_bits": tune.radix_bits, "split": tune.split, "key_directory": tune.key_directory,
+                             "radix_bits": tune.radix_bits, "split": tune.split, "key_directory": tune.key_directory, "keys_unroll": tune.keys_unroll,
                              "default_ms": round(tune.default_ms, 4), "tuned_ms": round(tune.best_ms, 4),
                              "candidates": tune.n_tried}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -539,6 +586,8 @@ def main():
     if world == 1 and not args.no_learned:
         out["learned_index"] = learned_vs_plain(gnm, torch, local, args.steps, args.warmup, args.learned_records,
                                                 tuple(args.learned_modes.split(",")))
+    if world == 1 and not args.no_batched:
+        out["batched"] = batched_c4(gnm, torch, local, args.steps, args.warmup)
     if world == 1 and not args.no_serve:
         out["serving"] = serve_c5(gnm, torch, local, minutes=args.serve_minutes, speedup=args.serve_speedup)
     if rank == 0:

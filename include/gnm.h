@@ -70,8 +70,12 @@ enum { GNM_AGG_AUTO = 0, GNM_AGG_DIRECT = 1, GNM_AGG_WARP = 2 };
 enum { GNM_ADMIN_OR = 0, GNM_ADMIN_AND = 1 };
 /* Per-CTA accumulation: a shared-memory row per key (DIRECT, when all keys fit), a
  * shared-memory hash table of the keys a CTA meets with global atomics for the overflow
- * (HASH), or warp-aggregated global atomics only (GLOBAL). */
-enum { GNM_TABLE_AUTO = 0, GNM_TABLE_DIRECT = 1, GNM_TABLE_HASH = 2, GNM_TABLE_GLOBAL = 3 };
+ * (HASH), warp-aggregated global atomics only (GLOBAL), or PARTITION (split launches):
+ * the records are first regrouped by (window, group of keys that one direct table holds),
+ * then every CTA segment meets one group only. AUTO: DIRECT when all keys fit, else
+ * PARTITION for split launches of at most 8192 (window, group) buckets, else HASH. */
+enum { GNM_TABLE_AUTO = 0, GNM_TABLE_DIRECT = 1, GNM_TABLE_HASH = 2, GNM_TABLE_GLOBAL = 3,
+       GNM_TABLE_PARTITION = 4 };
 enum { GNM_SPLIT_AUTO = 0, GNM_SPLIT_FUSED = 1, GNM_SPLIT_TWO_KERNELS = 2 };
 
 /* Filters and execution knobs. The paper fixes none of the filter constants
@@ -342,7 +346,8 @@ gnm_status gnm_plan_create_ex(gnm_ctx *ctx, const gnm_records *rec, const uint64
 gnm_status gnm_plan_launch(gnm_plan *plan, void *stream);
 
 /* Kernels of a plan's launch, in order */
-typedef enum { GNM_KERNEL_KEYS = 0, GNM_KERNEL_AGGREGATE = 1, GNM_KERNEL_FINALIZE = 2 } gnm_kernel_kind;
+typedef enum { GNM_KERNEL_KEYS = 0, GNM_KERNEL_AGGREGATE = 1, GNM_KERNEL_FINALIZE = 2, GNM_KERNEL_PART_COUNT = 3,
+               GNM_KERNEL_PART_SCAN = 4, GNM_KERNEL_PART_SCATTER = 5 } gnm_kernel_kind;
 
 /* Device durations (ms, CUDA events) of each kernel of the plan's last launch, which it
  * waits for; kind[i] names kernel i. *n_out = the plan's kernel count (GNM_E_CAPACITY
@@ -358,6 +363,7 @@ typedef struct {
     uint32_t radix_bits;
     int32_t split;
     int32_t key_directory;
+    int32_t keys_unroll;      /* key kernel: groups of 4 records per thread and step */
 } gnm_tune_report;
 
 /* Times candidate launch shapes (block size, CTAs per SM, records per thread,

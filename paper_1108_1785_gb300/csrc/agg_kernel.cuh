@@ -363,6 +363,7 @@ __device__ __forceinline__ void add_wrap64(uint32_t* lo, uint64_t* g, uint64_t v
 }
 
 struct Smem {
+    uint32_t key_base;  // keys of the current segment are relative to it (partitioned launches)
     uint32_t* t;        // table rows (kRowWords words each)
     uint32_t* tk;       // hash keys
     uint32_t rows;      // table rows
@@ -495,14 +496,16 @@ __device__ __forceinline__ void dump_rows(const Smem& sm, uint32_t* dst) {
     }
 }
 
-// Within a CTA's segment of a window whose rows go to a partial block at its end: adds
-// the rows' 16-bit counts to the window's global accumulators and clears them, so that
-// they cannot wrap; the sums (wrap-safe) keep accumulating.
+// Within a CTA's segment of a window whose rows go to a partial block at its end, between
+// pieces of at most kCountPiece records: a row whose 16-bit flows or e_flows count has
+// reached 2^15 adds its counts to the window's global accumulators and clears them. Every
+// count then starts a piece below 2^15 and ends it below 2^15 + kCountPiece < 2^16, so
+// none wraps; the sums (wrap-safe) keep accumulating, and rows with smaller counts too.
 __device__ __forceinline__ void flush_counts(const Smem& sm, uint64_t* gacc) {
     for (uint32_t r = threadIdx.x; r < sm.rows; r += blockDim.x) {
         uint32_t* w = sm.t + r * kRowWords;
         const uint32_t cnt = w[0];
-        if (cnt == 0) continue;
+        if ((cnt & 0x80008000u) == 0u) continue;
         red_add(gacc + (size_t)r * kAccCols, ((uint64_t)(cnt & 0xFFFFu) << 32) | (cnt >> 16));
         w[0] = 0;
     }
@@ -533,10 +536,13 @@ __device__ __forceinline__ void flush(const Smem& sm, uint64_t* gacc) {
 // a site is sub-optimal when its rate is below the standard). kL1: the sums were written
 // by an earlier kernel, so loads may go through L1 (the 5 word loads of a row then fetch
 // its lines from L2 once); inside the aggregation kernel they bypass L1.
+// Partitioned launches (p.part_groups > 0): every key group of window `win` has its own
+// run of partial blocks of table_rows rows (p.part_desc), and `parts`/`n_parts` are unused.
 template <bool kL1 = false>
 __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot, uint32_t k0,
                                               uint32_t step, const uint32_t* parts = nullptr,
-                                              uint32_t n_parts = 0) {
+                                              uint32_t n_parts = 0, uint32_t win = 0) {
+    const uint64_t pstride = part_stride_words(p.table_rows);
     const size_t keys = p.keys;
     uint64_t* acc = p.acc + (size_t)slot * keys * kAccCols;
     uint64_t* st = p.stats + (size_t)slot * keys * kNStat;
@@ -555,8 +561,16 @@ __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot,
         uint64_t pk = ld64(a + 2);
         uint64_t eo = ld64(a + 3);
         uint64_t ed = ld64(a + 4);
-        for (uint32_t q = 0; q < n_parts; ++q) {  // partial blocks of the window's CTAs
-            const uint32_t* w = parts + ((size_t)q * keys + k) * kRowWords;
+        const uint32_t* kp = parts + (size_t)k * kRowWords;
+        uint32_t np = n_parts;
+        if (p.part_groups) {
+            const uint32_t g = k / p.table_rows;
+            const uint2 pd = p.part_desc[(size_t)win * p.part_groups + g];
+            kp = p.partials + (size_t)pd.x * pstride + (size_t)(k - g * p.table_rows) * kRowWords;
+            np = p.partials ? pd.y : 0u;
+        }
+        for (uint32_t q = 0; q < np; ++q) {  // partial blocks of the window's CTAs
+            const uint32_t* w = kp + (size_t)q * pstride;
             const uint32_t cnt = ld32(w);
             packed += ((uint64_t)(cnt & 0xFFFFu) << 32) | (cnt >> 16);
             oc += ld32(w + 1);
@@ -680,15 +694,15 @@ __device__ __forceinline__ uint32_t record_key(const AggParams& p, bool sl, bool
 }
 
 // A record whose key is already known (split launches: a lookup kernel wrote it).
-__device__ __forceinline__ Item classify_key(const AggParams& p, bool valid, uint32_t key, uint32_t pk,
-                                             uint32_t oc, uint32_t fi, uint32_t la) {
+__device__ __forceinline__ Item classify_key(const AggParams& p, bool valid, uint32_t key, uint32_t key_base,
+                                             uint32_t pk, uint32_t oc, uint32_t fi, uint32_t la) {
     Item it;
     const uint32_t dur = la - fi;  // modulo 2^32
     const bool ack_ok = (uint64_t)oc >= (uint64_t)p.min_avg * (uint64_t)pk;
     const bool many = pk >= p.min_pkts, longd = dur >= p.min_dur;
     const bool admin_ok = p.admin_rule == GNM_ADMIN_OR ? (many && longd) : (many || longd);
     it.key = key;
-    it.elig = key < 2u * p.n_sites && dur != 0u && ack_ok && admin_ok;
+    it.elig = key + key_base < 2u * p.n_sites && dur != 0u && ack_ok && admin_ok;
     it.oc = oc;
     it.pk = pk;
     it.dur = dur;
@@ -708,7 +722,7 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
     if constexpr (LOOKUP == kLookupKeys) {
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-            const Item it = classify_key(p, valid[j], src[j], pk[j], oc[j], fi[j], la[j]);
+            const Item it = classify_key(p, valid[j], src[j], sm.key_base, pk[j], oc[j], fi[j], la[j]);
             accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
         }
     } else {
@@ -853,10 +867,11 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512)
     if (lo >= hi) return;  // whole CTA idle
 
     size_t off_keys, off_lookup;
-    smem_layout(LOOKUP, TABLE, p.n_ranges, p.keys, p.table_cap,
+    smem_layout(LOOKUP, TABLE, p.n_ranges, p.table_rows, p.table_cap,
                 LOOKUP == kLookupRmi ? p.rmi.n_leaves : 0u, p.radix_bits, &off_keys, &off_lookup);
     Smem sm;
-    sm.rows = TABLE == kTableDirect ? p.keys : (TABLE == kTableHash ? p.table_cap : 0u);
+    sm.key_base = 0u;
+    sm.rows = TABLE == kTableDirect ? p.table_rows : (TABLE == kTableHash ? p.table_cap : 0u);
     sm.t = reinterpret_cast<uint32_t*>(smem_raw);
     sm.tk = reinterpret_cast<uint32_t*>(smem_raw + off_keys);
     // stage the table (zero), the registry or the leaf parameters
@@ -870,14 +885,17 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512)
         const WinDesc wd = p.wins[w];
         if (wd.begin >= hi) break;
         const uint64_t s0 = max(wd.begin, lo), e0 = min(wd.end, hi);
-        uint64_t* gacc = p.acc + (size_t)wd.slot * p.keys * kAccCols;
+        // (a segment of a partitioned launch holds keys relative to its group's first key)
+        uint64_t* gacc = p.acc + ((size_t)wd.slot * p.keys + wd.key_base) * kAccCols;
+        sm.key_base = wd.key_base;
         // pieces of at most kFlushRecords records, so the 16-bit counts cannot wrap. With a
         // partial-sum area the CTA's segment of the window ends in one block of its own
         // (block q = the CTA's position among the window's CTAs), and the pieces before
         // the last hand over only their counts
         const uint32_t q = (uint32_t)(blockIdx.x - wd.begin / p.chunk);
-        for (uint64_t s = s0; s < e0; s += kFlushRecords) {
-            const uint64_t e = min(e0, s + kFlushRecords);
+        const uint64_t piece = (TABLE == kTableDirect && p.partials) ? kCountPiece : kFlushRecords;
+        for (uint64_t s = s0; s < e0; s += piece) {
+            const uint64_t e = min(e0, s + piece);
             uint64_t a0 = e, a1 = e;
             if (p.vec_ok) {
                 const uint32_t mis = (uint32_t)((s + p.phase) & 3u);
@@ -891,7 +909,7 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512)
                 __syncthreads();
                 if (TABLE == kTableDirect && p.partials) {
                     if (e >= e0)
-                        dump_rows(sm, p.partials + ((size_t)wd.part_base + q) * p.keys * kRowWords);
+                        dump_rows(sm, p.partials + ((size_t)wd.part_base + q) * part_stride_words(sm.rows));
                     else
                         flush_counts(sm, gacc);
                 } else {
@@ -913,7 +931,8 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512)
         __syncthreads();
         if (s_last && (wd.flags & kWinFinalize)) {
             if (TABLE == kTableDirect && p.partials)
-                finalize_rows(p, wd.slot, tid, B, p.partials + (size_t)wd.part_base * p.keys * kRowWords, wd.n_parts);
+                finalize_rows(p, wd.slot, tid, B, p.partials + (size_t)wd.part_base * part_stride_words(p.keys),
+                              wd.n_parts);
             else
                 finalize_rows(p, wd.slot, tid, B);
         }
@@ -925,10 +944,11 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512)
 // the shared memory holds just the lookup structure, so many CTAs fit per SM). The key
 // array has the same 16-byte phase as the record arrays.
 template <int LOOKUP, int U>
-__global__ void __launch_bounds__(U == 1 ? 1024 : 512) k_keys(const __grid_constant__ AggParams p,
-                                                             uint32_t* __restrict__ keys) {
+__global__ void __launch_bounds__(keys_block_max(LOOKUP, U)) k_keys(const __grid_constant__ AggParams p,
+                                                                    uint32_t* __restrict__ keys) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem sm;
+    sm.key_base = 0u;
     sm.t = nullptr;
     sm.tk = nullptr;
     sm.rows = 0;
@@ -997,12 +1017,12 @@ __global__ void __launch_bounds__(U == 1 ? 1024 : 512) k_keys(const __grid_const
 
 template <int LOOKUP>
 cudaError_t launch_keys_impl(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st) {
-    auto k = s.unroll == 2 ? k_keys<LOOKUP, 2> : k_keys<LOOKUP, 1>;
+    auto k = s.keys_unroll == 2 ? k_keys<LOOKUP, 2> : k_keys<LOOKUP, 1>;
     static int set_bytes[64][2];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    const int ui = s.unroll == 2 ? 1 : 0;
+    const int ui = s.keys_unroll == 2 ? 1 : 0;
     if (s.keys_smem >= 46 * 1024 && (dev >= 64 || set_bytes[dev][ui] < (int)s.keys_smem)) {
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.keys_smem);
         if (e != cudaSuccess) return e;

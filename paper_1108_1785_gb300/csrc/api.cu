@@ -189,7 +189,7 @@ static gnm_status stage_records(gnm_ctx* c, const gnm_records* rec, uint64_t lo,
 
 // ------------------------------------------------------------- shapes and params
 
-gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
+gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s, size_t n_win) {
     const gnm_config& cfg = c->cfg;
     const uint32_t nr = (uint32_t)c->h_starts.size();
     int mode = cfg.lookup_mode;
@@ -292,8 +292,31 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
     const size_t row = kSmemRowBytes + 4;
     uint32_t cap = 0;
     int tm = cfg.table_mode;
-    if (tm == GNM_TABLE_AUTO) tm = direct <= std::min(kDirectTableMax, budget) ? GNM_TABLE_DIRECT : GNM_TABLE_HASH;
-    if (tm == GNM_TABLE_DIRECT) {
+    // partitioned launches: groups of part_rows keys (a multiple of 256 that one direct
+    // table holds), at most kPartMaxBuckets (window, group) buckets, fewer than 2^32 records
+    const uint32_t part_rows = (uint32_t)(std::min(kDirectTableMax, budget) / kSmemRowBytes) & ~255u;
+    const uint32_t part_groups = part_rows ? (c->keys + part_rows - 1) / part_rows : 0u;
+    const bool part_ok = s->split && part_rows >= 256 &&
+                         (uint64_t)part_groups * std::max<size_t>(n_win, 1) <= kPartMaxBuckets && n < 0xFFFFFFFFull;
+    if (tm == GNM_TABLE_AUTO)
+        tm = direct <= std::min(kDirectTableMax, budget) ? GNM_TABLE_DIRECT
+             : part_ok && part_groups > 1                 ? GNM_TABLE_PARTITION
+                                                          : GNM_TABLE_HASH;
+    s->part = 0;
+    s->part_rows = 0;
+    s->part_groups = 0;
+    s->part_grid = 0;
+    uint32_t rows = c->keys;  // rows of a direct table
+    if (tm == GNM_TABLE_PARTITION) {
+        if (!part_ok)
+            return fail(GNM_E_INVAL, "table_mode PARTITION needs split launches, more keys than one table "
+                                     "holds, at most 8192 (window, key group) buckets and < 2^32 records");
+        s->table = kTableDirect;
+        s->part = 1;
+        s->part_rows = part_rows;
+        s->part_groups = part_groups;
+        rows = part_rows;
+    } else if (tm == GNM_TABLE_DIRECT) {
         if (direct > budget) return fail(GNM_E_INVAL, "per-site sums do not fit in shared memory (table_mode DIRECT)");
         s->table = kTableDirect;
     } else if (tm == GNM_TABLE_HASH) {
@@ -322,7 +345,7 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
     if (unroll == 2 && block > 512) unroll = 1;
     s->block = block;
     s->unroll = unroll;
-    s->smem = aggregate_smem_bytes(s->split ? kLookupKeys : s->lookup, s->table, nr, c->keys, cap,
+    s->smem = aggregate_smem_bytes(s->split ? kLookupKeys : s->lookup, s->table, nr, rows, cap,
                                    s->lookup == kLookupRmi ? c->rmi.n_leaves : 0, s->radix_bits);
     if (s->smem > (size_t)c->smem_optin) return fail(GNM_E_INVAL, "shared-memory layout exceeds the device limit");
     int cps = cfg.ctas_per_sm ? cfg.ctas_per_sm : c->tuned.ctas_per_sm;
@@ -336,11 +359,18 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s) {
     uint64_t grid = std::min<uint64_t>(resident, std::max<uint64_t>(1, ceil_div(n, min_per_cta)));
     s->grid = (int)grid;
     if (s->split) {  // key kernel: as many CTAs per SM as its shared memory allows
-        s->keys_block = s->unroll == 2 ? 512 : 1024;
+        int ku = c->tuned.keys_unroll ? c->tuned.keys_unroll : s->unroll;
+        if (ku != 1 && ku != 2) ku = 1;
+        const int lk = s->keys_blk == 2 ? kLookupRadixBlk2 : s->keys_blk == 4 ? kLookupRadixBlk : s->lookup;
+        s->keys_unroll = ku;
+        s->keys_block = keys_block_max(lk, ku);
         const int kfit = std::max(1, std::min(2048 / s->keys_block, (int)(c->smem_per_sm / (s->keys_smem + 1024))));
         const uint64_t kres = (uint64_t)c->sm_count * kfit;
-        s->keys_grid = (int)std::min<uint64_t>(kres, std::max<uint64_t>(1, ceil_div(n, (uint64_t)s->keys_block * 4 * s->unroll)));
+        s->keys_grid = (int)std::min<uint64_t>(kres, std::max<uint64_t>(1, ceil_div(n, (uint64_t)s->keys_block * 4 * ku)));
+        if (s->part)  // count and scatter: one 1024-thread CTA per SM, at least 4096 records each
+            s->part_grid = (int)std::min<uint64_t>((uint64_t)c->sm_count * 2, std::max<uint64_t>(1, ceil_div(n, 4096)));
     } else {
+        s->keys_unroll = 1;
         s->keys_block = 0;
         s->keys_grid = 0;
     }
@@ -384,6 +414,7 @@ gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p) {
     p->rate = c->d_rate;
     p->flag = c->d_flag;
     p->keys = c->keys;
+    p->table_rows = c->keys;
     p->min_flows = c->cfg.min_flows_to_flag;
     p->threshold = c->cfg.threshold_bps;
     p->violations = c->d_violations;
@@ -422,7 +453,7 @@ gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* off
     AggParams& p = out->p;
     GNM_TRY(build_params(c, dr, &p));
     LaunchShape& sh = out->sh;
-    GNM_TRY(choose_shape(c, N, &sh));
+    GNM_TRY(choose_shape(c, N, &sh, n_win));
     p.table_cap = sh.cap;
     p.radix_bits = sh.radix_bits;
     p.n_total = N;
@@ -453,23 +484,41 @@ gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* off
         w.part_base = (uint32_t)parts;
         const uint64_t np = w.ctas;  // one partial block per CTA segment of the window
         w.n_parts = (uint32_t)np;
-        w.pad = 0;
+        w.key_base = 0;
         parts += np;
         out->wins.push_back(w);
     }
     // direct tables of finalising launches hand their sums over through plain stores
     out->partial_words = 0;
-    if (sh.table == kTableDirect && (out->fin_in_kernel || out->fin_grid)) {
-        const uint64_t words = parts * c->keys * (kSmemRowBytes / 4);
+    out->n_buckets = 0;
+    out->part_bytes = 0;
+    if (sh.part) {
+        out->n_buckets = (uint32_t)(out->wins.size() * sh.part_groups);
+        out->part_bytes = part_layout(N, out->n_buckets).bytes;
+        // finalising launches: a block per (bucket, CTA) segment, at most one per CTA plus
+        // one per bucket; otherwise (or past the limit) the segments add to the accumulators
+        const uint64_t words = ((uint64_t)sh.grid + out->n_buckets) * part_stride_words(sh.part_rows);
+        if (out->fin_grid && words * 4 <= kPartialBytesMax) out->partial_words = words;
+    } else if (sh.table == kTableDirect && (out->fin_in_kernel || out->fin_grid)) {
+        const uint64_t words = parts * part_stride_words(c->keys);
         if (words * 4 <= kPartialBytesMax) out->partial_words = words;
     }
     return GNM_OK;
 }
 
+PartLayout part_layout(uint64_t n, uint32_t nb) {
+    PartLayout l;
+    l.cnt = 5 * part_array_stride(n) * 4;
+    l.descs = (l.cnt + (uint64_t)nb * 4 + 15) & ~15ull;
+    l.pdesc = l.descs + (uint64_t)nb * sizeof(WinDesc);
+    l.bytes = l.pdesc + (uint64_t)nb * sizeof(uint2);
+    return l;
+}
+
 gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, size_t n_win,
                             const uint32_t* slots, bool finalize, WinDesc* d_wins, uint32_t* d_done,
-                            uint32_t* d_partials, uint32_t* d_keys, cudaStream_t st, uint32_t* launches,
-                            cudaEvent_t* marks, int32_t* kinds) {
+                            uint32_t* d_partials, uint32_t* d_keys, unsigned char* d_part, cudaStream_t st,
+                            uint32_t* launches, cudaEvent_t* marks, int32_t* kinds) {
     *launches = 0;
     // an external event node when captured into a graph, so that the host can read it
     auto mark = [&](int32_t kind) -> gnm_status {
@@ -484,7 +533,57 @@ gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, s
         pr.p.done = d_done;
         pr.p.partials = pr.partial_words ? d_partials : nullptr;
         GNM_TRY(mark(-1));
-        if (pr.sh.split) {  // keys first (same 16-byte phase as the records), then the sums
+        if (pr.sh.part) {
+            // keys; regrouping by (window, key group); sums per group; grid finalisation
+            uint32_t* keys = d_keys + pr.p.phase;
+            AggParams pk = pr.p;
+            if (pr.sh.keys_blk) pk.radix_bits = pr.sh.keys_bits;
+            GNM_CU(launch_keys(pk, pr.sh, keys, st));
+            ++*launches;
+            GNM_TRY(mark(GNM_KERNEL_KEYS));
+            const PartLayout L = part_layout(pr.n, pr.n_buckets);
+            uint32_t* out = reinterpret_cast<uint32_t*>(d_part);
+            uint32_t* cnt = reinterpret_cast<uint32_t*>(d_part + L.cnt);
+            WinDesc* descs = reinterpret_cast<WinDesc*>(d_part + L.descs);
+            uint2* pdesc = reinterpret_cast<uint2*>(d_part + L.pdesc);
+            AggParams pp = pr.p;
+            pp.src = keys;
+            pp.dst = keys;
+            GNM_CU(launch_part_count(pp, pr.sh, cnt, st));
+            ++*launches;
+            GNM_TRY(mark(GNM_KERNEL_PART_COUNT));
+            GNM_CU(launch_part_scan(pp, pr.sh, pr.p.chunk, cnt, descs, pdesc, st));
+            ++*launches;
+            GNM_TRY(mark(GNM_KERNEL_PART_SCAN));
+            GNM_CU(launch_part_scatter(pp, pr.sh, cnt, out, st));
+            ++*launches;
+            GNM_TRY(mark(GNM_KERNEL_PART_SCATTER));
+            const uint64_t stride = part_array_stride(pr.n);
+            AggParams pa = pr.p;
+            pa.src = out;
+            pa.dst = out;
+            pa.pkts = out + stride;
+            pa.oct = out + 2 * stride;
+            pa.first = out + 3 * stride;
+            pa.last = out + 4 * stride;
+            pa.vec_ok = 1;
+            pa.phase = 0;
+            pa.wins = descs;
+            pa.n_wins = pr.n_buckets;
+            pa.table_rows = pr.sh.part_rows;
+            GNM_CU(launch_aggregate(pa, pr.sh, st));
+            ++*launches;
+            GNM_TRY(mark(GNM_KERNEL_AGGREGATE));
+            if (finalize) {
+                AggParams pf = pr.p;
+                pf.table_rows = pr.sh.part_rows;
+                pf.part_groups = pr.sh.part_groups;
+                pf.part_desc = pdesc;
+                GNM_CU(launch_finalize_windows(pf, st));
+                ++*launches;
+                GNM_TRY(mark(GNM_KERNEL_FINALIZE));
+            }
+        } else if (pr.sh.split) {  // keys first (same 16-byte phase as the records), then the sums
             uint32_t* keys = d_keys + pr.p.phase;
             AggParams pk = pr.p;
             if (pr.sh.keys_blk) pk.radix_bits = pr.sh.keys_bits;
@@ -498,12 +597,14 @@ gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, s
         } else {
             GNM_CU(launch_aggregate(pr.p, pr.sh, st));
         }
-        ++*launches;
-        GNM_TRY(mark(GNM_KERNEL_AGGREGATE));
-        if (finalize && pr.fin_grid) {
-            GNM_CU(launch_finalize_windows(pr.p, st));
+        if (!pr.sh.part) {
             ++*launches;
-            GNM_TRY(mark(GNM_KERNEL_FINALIZE));
+            GNM_TRY(mark(GNM_KERNEL_AGGREGATE));
+            if (finalize && pr.fin_grid) {
+                GNM_CU(launch_finalize_windows(pr.p, st));
+                ++*launches;
+                GNM_TRY(mark(GNM_KERNEL_FINALIZE));
+            }
         }
     }
     // empty windows: zero sums, no rate, no flag
@@ -554,8 +655,15 @@ gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offse
     Prepared pr;
     GNM_TRY(prepare_launch(c, &dr, offsets, n_win, slot.data(), finalize, &pr));
     LaunchBuf* lb;
-    GNM_TRY(acquire_ring(c, (uint32_t)n_win, &lb));
+    GNM_TRY(acquire_ring(c, (uint32_t)std::max<size_t>(n_win, pr.n_buckets), &lb));
     const uint64_t key_words = pr.sh.split ? pr.n + 4 : 0;
+    if (pr.part_bytes > lb->part_cap) {  // grow this entry's regrouping scratch
+        free_dev(lb->d_part);
+        lb->d_part = nullptr;
+        lb->part_cap = 0;
+        GNM_CU(cudaMalloc(&lb->d_part, pr.part_bytes));
+        lb->part_cap = pr.part_bytes;
+    }
     if (key_words > lb->keys_cap) {  // grow this entry's key array
         free_dev(lb->d_keys);
         lb->d_keys = nullptr;
@@ -575,7 +683,7 @@ gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offse
         GNM_CU(cudaMemcpyAsync(lb->d_wins, lb->h_wins, sizeof(WinDesc) * pr.wins.size(), cudaMemcpyHostToDevice, st));
     }
     GNM_TRY(enqueue_prepared(c, pr, offsets, n_win, slot.data(), finalize, lb->d_wins, lb->d_done,
-                             lb->d_partials, lb->d_keys, st, &c->last_launches));
+                             lb->d_partials, lb->d_keys, lb->d_part, st, &c->last_launches));
     GNM_CU(cudaEventRecord(lb->ev, st));
     lb->ev_recorded = true;
     for (size_t k = 0; k < n_win; ++k) c->slots[slot[k]].records += offsets[k + 1] - offsets[k];
@@ -690,6 +798,7 @@ void gnm_destroy(gnm_ctx* c) {
         free_dev(b.d_done);
         free_dev(b.d_partials);
         free_dev(b.d_keys);
+        free_dev(b.d_part);
         if (b.ev) cudaEventDestroy(b.ev);
     }
     for (auto* p : c->staging.d) free_dev(p);

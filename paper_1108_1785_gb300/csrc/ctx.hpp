@@ -57,6 +57,8 @@ struct LaunchBuf {
     uint64_t partial_cap = 0;        // in u32 words
     uint32_t* d_keys = nullptr;      // per-record keys of split launches
     uint64_t keys_cap = 0;           // in u32 words
+    unsigned char* d_part = nullptr; // regrouped records and bucket tables of partitioned launches
+    uint64_t part_cap = 0;           // in bytes
     cudaEvent_t ev = nullptr;
     bool ev_recorded = false;
 };
@@ -69,7 +71,7 @@ struct Staging {
 };
 
 struct Tuned {
-    int block = 0, ctas_per_sm = 0, unroll = 0, agg = 0, placement = 0, split = 0, key_dir = 0;
+    int block = 0, ctas_per_sm = 0, unroll = 0, agg = 0, placement = 0, split = 0, key_dir = 0, keys_unroll = 0;
     uint32_t radix_bits = 0;
 };
 
@@ -136,7 +138,7 @@ struct gnm_ctx {
 namespace gnm {
 // shared by api.cu, plan.cu and rmi_api.cu
 gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p);
-gnm_status choose_shape(gnm_ctx* c, uint64_t n_records, LaunchShape* s);
+gnm_status choose_shape(gnm_ctx* c, uint64_t n_records, LaunchShape* s, size_t n_win = 1);
 gnm_status acquire_slot(gnm_ctx* c, uint64_t window_id, cudaStream_t st, uint32_t* slot_out);
 void release_slots(gnm_ctx* c);
 gnm_status check_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets, size_t n_win);
@@ -151,7 +153,15 @@ struct Prepared {
     bool fin_grid = false;       // finalise in a grid-wide kernel after the aggregation
     uint64_t n = 0;
     uint64_t partial_words = 0;  // u32 words of per-(window, CTA) partial sums (0: none)
+    uint32_t n_buckets = 0;      // partitioned launches: (window, key group) buckets
+    uint64_t part_bytes = 0;     // partitioned launches: their scratch (part_layout)
 };
+// Scratch of a partitioned launch of n records and nb buckets: the five regrouped record
+// arrays, then the bucket counts, segment descriptors and partial-block ranges.
+struct PartLayout {
+    uint64_t cnt, descs, pdesc, bytes;
+};
+PartLayout part_layout(uint64_t n, uint32_t nb);
 gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* offsets, size_t n_win,
                           const uint32_t* slots, bool finalize, Prepared* out);
 // Enqueues the kernels of a prepared launch (descriptors already on the device).
@@ -159,8 +169,9 @@ gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* off
 // one; kinds[i] receives the gnm_kernel_kind of kernel i.
 gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, size_t n_win,
                             const uint32_t* slots, bool finalize, WinDesc* d_wins, uint32_t* d_done,
-                            uint32_t* d_partials, uint32_t* d_keys, cudaStream_t st, uint32_t* launches,
-                            cudaEvent_t* marks = nullptr, int32_t* kinds = nullptr);
+                            uint32_t* d_partials, uint32_t* d_keys, unsigned char* d_part, cudaStream_t st,
+                            uint32_t* launches, cudaEvent_t* marks = nullptr, int32_t* kinds = nullptr);
+constexpr int kMaxPlanKernels = 6;  // keys, count, scan, scatter, aggregate, finalise
 // Next launch-scratch entry of the ring (waits for its previous use).
 gnm_status acquire_ring(gnm_ctx* c, uint32_t n_win, LaunchBuf** out);
 void set_slots_done(gnm_ctx* c, const uint32_t* slots, size_t n, cudaEvent_t ev, bool finalized);

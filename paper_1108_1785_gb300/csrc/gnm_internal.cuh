@@ -25,10 +25,16 @@ struct WinDesc {
     uint32_t ctas;       // CTAs whose record range overlaps the window (ticket target)
     uint32_t part_base;  // first partial-sum block of the window (when partials are used)
     uint32_t n_parts;    // partial-sum blocks of the window (one per CTA piece)
-    uint32_t pad;
+    uint32_t key_base;   // first key of the segment's key group (partitioned launches), else 0
 };
+// Words between consecutive partial-sum blocks of `rows` 20-byte rows: padded to 16 bytes
+// so that the blocks can be read with 16-byte loads.
+__host__ __device__ constexpr uint64_t part_stride_words(uint64_t rows) { return (rows * 5u + 3u) & ~3ull; }
+
 // A CTA flushes its shared sums at least every kFlushRecords records (16-bit counts).
 constexpr uint64_t kFlushRecords = 65532;  // < 2^16, multiple of 4
+// Direct tables with partial blocks: pieces after which only rows with counts >= 2^15 flush.
+constexpr uint64_t kCountPiece = 32764;    // 2^15 + kCountPiece < 2^16, multiple of 4
 constexpr uint32_t kWinFinalize = 1u;
 
 // Learned index: root parameters by value, per-leaf arrays in device memory.
@@ -89,6 +95,10 @@ struct AggParams {
     double* rate;                // [slots][2*n_sites]
     uint8_t* flag;               // [slots][2*n_sites]
     uint32_t keys;               // 2*n_sites + 4
+    uint32_t table_rows;         // rows of a direct shared-memory table: keys, or one key group
+    uint32_t part_groups;        // key groups per window of a partitioned launch (0: none)
+    uint32_t pad2;
+    const uint2* part_desc;      // [window][group]: (first partial block, blocks) of a partitioned launch
     uint32_t table_cap;          // shared-memory hash slots (table mode 1)
     uint32_t min_flows;
     uint32_t pad0;
@@ -106,6 +116,12 @@ struct AggParams {
 // block's (start, site) pairs ends the lookup.
 enum { kLookupL2 = 0, kLookupSmem = 1, kLookupRmi = 2, kLookupStaged = 3, kLookupRadix = 4, kLookupKeys = 5,
        kLookupRadixBlk = 6, kLookupRadixBlk2 = 7 };
+
+// Largest block of the key kernel for a lookup and records-per-thread unroll: two groups
+// of lookups per thread fit 64 registers (1024 threads) only for the lighter lookups.
+__host__ __device__ constexpr int keys_block_max(int lookup, int unroll) {
+    return (unroll == 1 || lookup == kLookupRadixBlk2 || lookup == kLookupRadix || lookup == kLookupL2) ? 1024 : 512;
+}
 constexpr uint32_t kBlockRanges = 16;  // ranges per staged block (16 starts, 64 bytes)
 enum { kTableDirect = 0, kTableHash = 1, kTableGlobal = 2 };
 
@@ -128,7 +144,27 @@ struct LaunchShape {
     size_t keys_smem;
     int keys_blk;          // radix key kernel: ranges per block of its shared block samples (0: none)
     uint32_t keys_bits;    // its directory bits
+    int keys_unroll;       // key kernel: groups of 4 records per thread and step (1 or 2)
+    // partitioned launches (split launches whose keys exceed one direct table): records are
+    // regrouped by (window, group of part_rows keys) before the aggregation
+    int part;
+    uint32_t part_rows, part_groups;
+    int part_grid;
 };
+
+// partition.cu: count, scan and scatter of a partitioned launch. `p` is the launch's
+// parameters (records, windows, keys of the key kernel at p.src); cnt (n_wins * groups
+// words) holds the bucket sizes, then their next free places; `out` receives the
+// regrouped records (key within its group, pkts, octets, first, last: 5 arrays of
+// part_array_stride(n) words); `descs` the aggregation's segment descriptors (n_wins *
+// groups entries), `part_desc` the finalisation's partial-block ranges per bucket.
+constexpr uint32_t kPartMaxBuckets = 8192;
+uint64_t part_array_stride(uint64_t n);
+cudaError_t launch_part_count(const AggParams& p, const LaunchShape& s, uint32_t* cnt, cudaStream_t st);
+cudaError_t launch_part_scan(const AggParams& p, const LaunchShape& s, uint64_t agg_chunk, uint32_t* cnt,
+                             WinDesc* descs, uint2* part_desc, cudaStream_t st);
+cudaError_t launch_part_scatter(const AggParams& p, const LaunchShape& s, uint32_t* cnt, uint32_t* out,
+                                cudaStream_t st);
 
 // aggregate*.cu
 cudaError_t launch_aggregate(const AggParams& p, const LaunchShape& s, cudaStream_t st);

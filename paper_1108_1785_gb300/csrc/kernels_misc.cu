@@ -55,11 +55,14 @@ __global__ void k_finalize(const __grid_constant__ AggParams p, uint32_t slot) {
 }
 
 // blockIdx.y: window of the launch; its keys are spread over blockIdx.x.
-__global__ void k_finalize_windows(const __grid_constant__ AggParams p) {
+constexpr uint32_t kFinKeys = 256;
+
+__global__ void __launch_bounds__(kFinKeys) k_finalize_windows(const __grid_constant__ AggParams p) {
     const WinDesc wd = p.wins[blockIdx.y];
-    const uint32_t* parts = p.partials ? p.partials + (size_t)wd.part_base * p.keys * 5 : nullptr;
+    const uint32_t* parts =
+        p.partials ? p.partials + (size_t)wd.part_base * part_stride_words(p.table_rows) : nullptr;
     dev::finalize_rows<true>(p, wd.slot, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, parts,
-                             p.partials ? wd.n_parts : 0u);
+                             p.partials ? wd.n_parts : 0u, blockIdx.y);
 }
 
 // Keys (site*2+dir) whose eligible flows reach min_flows and whose rate is strictly
@@ -150,7 +153,7 @@ cudaError_t launch_finalize_windows(const AggParams& p, cudaStream_t st) {
     if (p.n_wins == 0) return cudaSuccess;
     const uint32_t bx = (p.keys + 255) / 256;
     (void)cudaGetLastError();
-    k_finalize_windows<<<dim3(bx > 64 ? 64 : bx, p.n_wins), 256, 0, st>>>(p);
+    k_finalize_windows<<<dim3(bx > 64 ? 64 : bx, p.n_wins), kFinKeys, 0, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -126,6 +126,7 @@ extern "C" gnm_status gnm_window_process_noalloc(const gnm_config* cfg_in, const
     p.rate = rate;
     p.flag = flag;
     p.keys = keys;
+    p.table_rows = keys;
     p.min_flows = cfg.min_flows_to_flag;
     p.threshold = cfg.threshold_bps;
     p.wins = reinterpret_cast<const WinDesc*>(scr);
@@ -186,7 +187,7 @@ extern "C" gnm_status gnm_window_process_noalloc(const gnm_config* cfg_in, const
     d.ctas = (uint32_t)grid;
     d.part_base = 0;
     d.n_parts = 0;
-    d.pad = 0;
+    d.key_base = 0;
     (void)cudaGetLastError();
     k_noalloc_desc<<<1, 1, 0, st>>>(d);
     GNM_CU(cudaGetLastError());

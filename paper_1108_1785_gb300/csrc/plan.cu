@@ -28,8 +28,9 @@ struct gnm_plan {
     uint32_t launches = 0;
     bool timed = false;
     bool launched = false;
-    cudaEvent_t marks[4] = {nullptr, nullptr, nullptr, nullptr};  // around each kernel
-    int32_t kinds[3] = {0, 0, 0};
+    cudaEvent_t marks[gnm::kMaxPlanKernels + 1] = {};  // before the first kernel and after each
+    int32_t kinds[gnm::kMaxPlanKernels] = {};
+    unsigned char* d_part = nullptr;
 };
 
 using namespace gnm;
@@ -50,6 +51,7 @@ static void plan_free(gnm_plan* p) {
     if (p->d_done) cudaFree(p->d_done);
     if (p->d_partials) cudaFree(p->d_partials);
     if (p->d_keys) cudaFree(p->d_keys);
+    if (p->d_part) cudaFree(p->d_part);
     if (p->ev) cudaEventDestroy(p->ev);
     for (auto e : p->marks)
         if (e) cudaEventDestroy(e);
@@ -102,7 +104,7 @@ gnm_status gnm_plan_create_ex(gnm_ctx* c, const gnm_records* rec, const uint64_t
     Prepared pr;
     gnm_status st = prepare_launch(c, &dr, offsets, n_win, p->slots.data(), true, &pr);
     if (st != GNM_OK) return bail(st);
-    const size_t nw = std::max<size_t>(pr.wins.size(), 1);
+    const size_t nw = std::max<size_t>(std::max<size_t>(pr.wins.size(), pr.n_buckets), 1);
     if (cudaMalloc(&p->d_wins, sizeof(WinDesc) * nw) != cudaSuccess ||
         cudaMalloc(&p->d_done, sizeof(uint32_t) * nw) != cudaSuccess ||
         cudaMemset(p->d_done, 0, sizeof(uint32_t) * nw) != cudaSuccess ||
@@ -110,7 +112,8 @@ gnm_status gnm_plan_create_ex(gnm_ctx* c, const gnm_records* rec, const uint64_t
                                       cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaEventCreateWithFlags(&p->ev, cudaEventDisableTiming) != cudaSuccess ||
         (pr.partial_words && cudaMalloc(&p->d_partials, pr.partial_words * 4) != cudaSuccess) ||
-        (pr.sh.split && pr.n && cudaMalloc(&p->d_keys, (pr.n + 4) * 4) != cudaSuccess))
+        (pr.sh.split && pr.n && cudaMalloc(&p->d_keys, (pr.n + 4) * 4) != cudaSuccess) ||
+        (pr.part_bytes && cudaMalloc(&p->d_part, pr.part_bytes) != cudaSuccess))
         return bail(fail(GNM_E_CUDA, "plan allocation failed"));
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)
@@ -119,7 +122,7 @@ gnm_status gnm_plan_create_ex(gnm_ctx* c, const gnm_records* rec, const uint64_t
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         st = enqueue_prepared(c, pr, offsets, n_win, p->slots.data(), true, p->d_wins, p->d_done, p->d_partials,
-                              p->d_keys, cs, &p->launches, p->timed ? p->marks : nullptr, p->kinds);
+                              p->d_keys, p->d_part, cs, &p->launches, p->timed ? p->marks : nullptr, p->kinds);
         e = cudaStreamEndCapture(cs, &g);
     }
     if (e == cudaSuccess && st == GNM_OK) e = cudaGraphInstantiate(&p->exec, g, 0);
@@ -220,6 +223,7 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
     if (base_shape.lookup == kLookupRadix) kdirs_v = {3, 1, 2};
     for (int sp : splits_v)
     for (int kd : kdirs_v)
+    for (int ku : {1, 2})
     for (int b : blocks)
         for (int u : unrolls)
             for (int a : aggs)
@@ -236,7 +240,8 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
                             if (c->cfg.radix_bits == 0) c->cfg.radix_bits = (uint32_t)rb;
                             if (c->cfg.ctas_per_sm == 0) c->cfg.ctas_per_sm = cps;
                             if (c->cfg.split == GNM_SPLIT_AUTO) c->cfg.split = sp;
-                            if (sp == GNM_SPLIT_FUSED && kd == 2) continue;  // the key kernel's knob
+                            if (sp == GNM_SPLIT_FUSED && (kd == 2 || ku == 2)) continue;  // key kernel knobs
+                            c->tuned.keys_unroll = ku;
                             if (c->cfg.key_directory == 0) c->cfg.key_directory = kd;
                             LaunchShape sh;
                             if (choose_shape(c, offsets[n_win] - offsets[0], &sh) != GNM_OK) continue;  // does not fit
@@ -253,6 +258,7 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
                                 rep->radix_bits = sh.radix_bits;
                                 rep->split = sh.split ? GNM_SPLIT_TWO_KERNELS : GNM_SPLIT_FUSED;
                                 rep->key_directory = c->cfg.key_directory;
+                                rep->keys_unroll = sh.split ? sh.keys_unroll : 0;
                             }
                         }
     c->cfg = saved;
@@ -270,6 +276,7 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
     c->tuned.radix_bits = rep->radix_bits;
     c->tuned.split = rep->split;
     c->tuned.key_dir = rep->key_directory;
+    c->tuned.keys_unroll = rep->keys_unroll;
     // leave the windows holding the results of the chosen shape
     return gnm_windows_process(c, rec, offsets, wids, n_win, st) == GNM_OK && cudaStreamSynchronize(st) == cudaSuccess
                ? GNM_OK

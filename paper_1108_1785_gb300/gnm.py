@@ -22,11 +22,12 @@ LOOKUP_AUTO, LOOKUP_BSEARCH, LOOKUP_RMI, LOOKUP_RADIX = 0, 1, 2, 3
 PLACE_AUTO, PLACE_SMEM, PLACE_L2, PLACE_STAGED = 0, 1, 2, 3
 AGG_AUTO, AGG_DIRECT, AGG_WARP = 0, 1, 2
 ADMIN_OR, ADMIN_AND = 0, 1
-TABLE_AUTO, TABLE_DIRECT, TABLE_HASH, TABLE_GLOBAL = 0, 1, 2, 3
+TABLE_AUTO, TABLE_DIRECT, TABLE_HASH, TABLE_GLOBAL, TABLE_PARTITION = 0, 1, 2, 3, 4
 SPLIT_AUTO, SPLIT_FUSED, SPLIT_TWO_KERNELS = 0, 1, 2
 ROOT_LINEAR, ROOT_MLP = 0, 1
 KERNEL_TIMES = 1  # GNM_PLAN_KERNEL_TIMES
-KERNEL_NAMES = {0: "k_keys", 1: "k_aggregate", 2: "k_finalize_windows"}
+KERNEL_NAMES = {0: "k_keys", 1: "k_aggregate", 2: "k_finalize_windows", 3: "k_part_count", 4: "k_part_scan",
+                5: "k_part_scatter"}
 FIELDS = ("srcaddr", "dstaddr", "dPkts", "dOctets", "first", "last")
 
 STATUS = {0: "GNM_OK", 1: "GNM_E_INVAL", 2: "GNM_E_NOMEM", 3: "GNM_E_CUDA", 4: "GNM_E_STATE",
@@ -99,7 +100,7 @@ class TuneReport(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("unroll", C.c_int32),
                 ("aggregation", C.c_int32), ("placement", C.c_int32), ("best_ms", C.c_double),
                 ("default_ms", C.c_double), ("n_tried", C.c_uint32), ("radix_bits", C.c_uint32),
-                ("split", C.c_int32), ("key_directory", C.c_int32)]
+                ("split", C.c_int32), ("key_directory", C.c_int32), ("keys_unroll", C.c_int32)]
 
 
 _lib = None
@@ -479,10 +480,10 @@ class Plan:
 
     def kernel_times(self):
         """[(kernel name, ms)] of the last launch, in launch order (plans made with kernel_times)."""
-        ms = np.zeros(3, np.float32)
-        kind = np.zeros(3, np.int32)
+        ms = np.zeros(8, np.float32)
+        kind = np.zeros(8, np.int32)
         n = C.c_size_t()
-        self.ctx._c(lib().gnm_plan_kernel_times(self.h, _ptr(ms), _ptr(kind), 3, C.byref(n)))
+        self.ctx._c(lib().gnm_plan_kernel_times(self.h, _ptr(ms), _ptr(kind), 8, C.byref(n)))
         return [(KERNEL_NAMES[int(kind[i])], float(ms[i])) for i in range(n.value)]
 
     def close(self):

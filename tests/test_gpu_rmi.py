@@ -248,6 +248,30 @@ def test_rmi_window_fallback_exact(gnm, c3, split, unroll):
     ctx.close()
 
 
+@pytest.mark.parametrize("table", ["PARTITION", "HASH"])
+def test_large_key_space_windows(gnm, c3, table):
+    """200,004 keys (100,000 sites): three uneven windows in one launch, with the records
+    regrouped by (window, key group) before the aggregation (20 groups per window) or with
+    the per-CTA hash cache; every window equals the oracle."""
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx = gnm.Context(window_slots=4, table_mode=getattr(gnm, "TABLE_" + table))
+    ctx.load(reg)
+    off = [0, 1, 700_001, 2_000_000]
+    d = gnm.Records.to_device(rec)
+    plan = ctx.plan(d, off, [7, 8, 9], kernel_times=True)
+    plan.launch()
+    names = [k for k, _ in plan.kernel_times()]
+    if table == "PARTITION":
+        assert names == ["k_keys", "k_part_count", "k_part_scan", "k_part_scatter", "k_aggregate",
+                         "k_finalize_windows"]
+    else:
+        assert names == ["k_keys", "k_aggregate", "k_finalize_windows"]
+    for w, (a, b) in zip([7, 8, 9], zip(off[:-1], off[1:])):
+        assert_window_matches(ctx.dense(w), oracle_full(reg, {k: v[a:b] for k, v in rec.items()}, lpm=lpm))
+    plan.close()
+    ctx.close()
+
+
 def test_mlp_root_rmi_exact(gnm, c3):
     reg, lpm, starts, sites, rec, keys = c3
     ctx = gnm.Context(window_slots=2)

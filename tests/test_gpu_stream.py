@@ -22,7 +22,8 @@ def gnm():
 
 @pytest.fixture(scope="module")
 def regs():
-    return {"c1": fg.registry_c1(), "c2": fg.registry_c2()}
+    # c3: 100,000 sites (200,004 keys): each batch regroups its records by key group
+    return {"c1": fg.registry_c1(), "c2": fg.registry_c2(), "c3": fg.registry_c3()}
 
 
 def _ctx(gnm, reg, **cfg):
@@ -82,6 +83,7 @@ def _serve(gnm, stream, pool_recs, wins, order, empty_close, read):
     ("c2", True, 3, 4, 64),     # split (key + aggregation) launches
     ("c1", False, 2, 2, 64),    # device batches: only the budget is charged
     ("c2", True, 2, 4, 3),      # three result slots for twelve interleaved windows
+    ("c3", True, 3, 4, 8),      # a key space larger than one shared-memory table
 ])
 def test_mix_equals_alone(gnm, regs, which, host, budget_batches, n_streams, slots):
     reg = regs[which]

@@ -162,7 +162,8 @@ def c2hour():
                                  {"lookup_mode": "BSEARCH", "placement": "L2", "split": "FUSED"},
                                  {"aggregation": "WARP"}, {"hash_slots": 1024}, {"table_mode": "GLOBAL"},
                                  {"radix_bits": 12, "split": "FUSED"}, {"table_mode": "HASH", "unroll": 2,
-                                                                          "block_threads": 512}])
+                                                                          "block_threads": 512},
+                                 {"table_mode": "PARTITION"}])
 def test_c2_hour_batched_bitexact(gnm, c2hour, cfg):
     """Sixty one-minute windows (10M records, nested registry) in one launch -- the
     benchmark's workload and, with cfg {}, its launch configuration; every window equals
@@ -182,8 +183,10 @@ def test_c2_hour_batched_bitexact(gnm, c2hour, cfg):
     ids = np.arange(60) + 5000
     plan = ctx.plan(d, off, ids)  # the benchmark's path: a CUDA graph of one launch
     plan.launch()
-    # fused: one kernel; split: keys + sums; 10,004 keys: a grid-wide finalisation after them
-    assert ctx.last_launch_count() == (1 if cfg.get("split") == "FUSED" else 2) + 1
+    # fused: one kernel; split: keys + sums; 10,004 keys: a grid-wide finalisation after them;
+    # partitioned: keys, count, scan, scatter, sums, finalisation
+    n_kernels = 6 if cfg.get("table_mode") == "PARTITION" else (1 if cfg.get("split") == "FUSED" else 2) + 1
+    assert ctx.last_launch_count() == n_kernels
     for w in range(60):
         assert_window_matches(ctx.dense(int(ids[w])), expect[w])
     plan.close()
@@ -272,6 +275,37 @@ def test_radix_directory_must_fit(gnm):
     ctx = _ctx(gnm, reg, lookup_mode=gnm.LOOKUP_RADIX, radix_bits=16, split=gnm.SPLIT_FUSED)
     d = gnm.Records.to_device(fg.make_records(reg, 1000, seed=3))
     with pytest.raises(gnm.GnmError, match="radix directory too large"):
+        ctx.process(d, 1)
+    ctx.close()
+
+
+@pytest.mark.parametrize("which", ["c1", "c2"])
+def test_hot_key_counts_do_not_wrap(gnm, which):
+    """90% of 12M records share one (site, direction): every CTA's segment gives that key
+    more than 2^16 records, so its 16-bit shared-memory counts must be handed over between
+    pieces; the window still equals the oracle."""
+    reg = fg.registry_c1() if which == "c1" else fg.registry_c2()
+    rec = fg.make_records(reg, 12_000_000, seed=41)
+    rng = np.random.default_rng(41)
+    hot = rng.random(rec["srcaddr"].size) < 0.9
+    inside = np.nonzero(reg.site == reg.site[0])[0][0]
+    remote = np.uint32(int(reg.prefix[inside]) + 1)
+    local = np.uint32(int(reg.local_prefix[0]) + 7)
+    rec["srcaddr"] = np.where(hot, remote, rec["srcaddr"]).astype(np.uint32)
+    rec["dstaddr"] = np.where(hot, local, rec["dstaddr"]).astype(np.uint32)
+    ctx = _ctx(gnm, reg)
+    ctx.process(gnm.Records.to_device(rec), 1)
+    st, un, r, f = ctx.dense(1)
+    assert st[:, 0].max() > 10_000_000  # the hot key
+    assert_window_matches((st, un, r, f), oracle_full(reg, rec))
+    ctx.close()
+
+
+def test_partition_needs_split_launches(gnm):
+    reg = fg.registry_c2()
+    ctx = _ctx(gnm, reg, table_mode=gnm.TABLE_PARTITION, split=gnm.SPLIT_FUSED)
+    d = gnm.Records.to_device(fg.make_records(reg, 1000, seed=3))
+    with pytest.raises(gnm.GnmError, match="PARTITION needs split"):
         ctx.process(d, 1)
     ctx.close()
 
