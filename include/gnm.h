@@ -113,7 +113,14 @@ typedef struct {
                                    16-byte (32-byte) load of the block's (start, site)
                                    pairs ends a lookup; 2 = the range directory and a
                                    search over L2; 0 = 3, else 1, whichever fits first */
+    int32_t host_records;       /* GNM_HOST_*: how kernels get host (on_device = 0) records */
 } gnm_config;
+
+/* Host records: AUTO reads them in place when every array is page-locked host memory that
+ * the device can address (cudaHostAlloc / cudaHostRegister; the kernels then read it over
+ * the host link, with no staging copy), else STAGE; STAGE copies them to a device staging
+ * buffer first; IN_PLACE requires addressable page-locked arrays (GNM_E_INVAL otherwise). */
+enum { GNM_HOST_AUTO = 0, GNM_HOST_STAGE = 1, GNM_HOST_IN_PLACE = 2 };
 
 /* One struct-of-arrays batch of NetFlow v5 fields (Sec. IV.A.3: 48-byte v5 records; only
  * the six fields below are read). Element i of every array is record i. Device arrays
@@ -410,6 +417,10 @@ typedef struct {
     uint64_t budget_bytes;    /* device bytes of records in flight (default 4 GiB) */
     uint32_t n_cuda_streams;  /* CUDA streams batches are spread over (default 4, 1..64) */
     uint32_t max_queued;      /* queued batches before submit returns GNM_E_CAPACITY (65536) */
+    uint64_t max_batch_records; /* largest batch expected: the context's launch scratch is
+                                   reserved for it at open, so that no allocation falls
+                                   between batches (default 1,048,576; larger batches still
+                                   work and grow it) */
 } gnm_stream_config;
 
 typedef struct {

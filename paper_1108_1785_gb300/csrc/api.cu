@@ -162,6 +162,24 @@ gnm_status acquire_ring(gnm_ctx* c, uint32_t n_win, LaunchBuf** out) {
     return GNM_OK;
 }
 
+// Host records that the kernels may read in place: page-locked host memory mapped for the
+// device (the runtime reports a device address for it). out[k]: the device address of
+// field k's element `base`.
+static bool host_addressable(gnm_ctx* c, const gnm_records* rec, uint64_t base, const uint32_t* out[6]) {
+    if (c->cfg.host_records == GNM_HOST_STAGE) return false;
+    const uint32_t* f[6] = {rec->srcaddr, rec->dstaddr, rec->dPkts, rec->dOctets, rec->first, rec->last};
+    for (int k = 0; k < 6; ++k) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, f[k] + base) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return false;
+        out[k] = static_cast<const uint32_t*>(a.devicePointer);
+    }
+    return true;
+}
+
 static gnm_status stage_records(gnm_ctx* c, const gnm_records* rec, uint64_t lo, uint64_t hi,
                                 cudaStream_t st, const uint32_t* out[6]) {
     Staging& g = c->staging;
@@ -628,7 +646,15 @@ gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offse
     GNM_TRY(check_windows(c, rec, offsets, n_win));
     const uint64_t base = offsets[0], N = offsets[n_win] - offsets[0];
     gnm_records dr = *rec;
-    if (N && !rec->on_device) {
+    const uint32_t* inplace[6];
+    if (N && !rec->on_device && host_addressable(c, rec, base, inplace)) {
+        dr.srcaddr = inplace[0]; dr.dstaddr = inplace[1]; dr.dPkts = inplace[2];
+        dr.dOctets = inplace[3]; dr.first = inplace[4]; dr.last = inplace[5];
+        dr.on_device = 1;
+    } else if (N && !rec->on_device) {
+        if (c->cfg.host_records == GNM_HOST_IN_PLACE)
+            return fail(GNM_E_INVAL, "host_records IN_PLACE: the record arrays are not device-addressable "
+                                     "page-locked host memory");
         const uint32_t* d[6];
         GNM_TRY(stage_records(c, rec, base, offsets[n_win], st, d));
         dr.srcaddr = d[0]; dr.dstaddr = d[1]; dr.dPkts = d[2]; dr.dOctets = d[3]; dr.first = d[4]; dr.last = d[5];
@@ -691,6 +717,32 @@ gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offse
     return GNM_OK;
 }
 
+gnm_status reserve_launch_scratch(gnm_ctx* c, uint64_t n) {
+    if (!n) return GNM_OK;
+    LaunchShape sh;
+    GNM_TRY(choose_shape(c, n, &sh, 1));
+    const uint64_t key_words = sh.split ? n + 4 : 0;
+    const uint64_t part_bytes = sh.part ? part_layout(n, sh.part_groups).bytes : 0;
+    for (auto& b : c->ring) {
+        if (b.ev_recorded) GNM_CU(cudaEventSynchronize(b.ev));
+        if (key_words > b.keys_cap) {
+            free_dev(b.d_keys);
+            b.d_keys = nullptr;
+            b.keys_cap = 0;
+            GNM_CU(cudaMalloc(&b.d_keys, key_words * 4));
+            b.keys_cap = key_words;
+        }
+        if (part_bytes > b.part_cap) {
+            free_dev(b.d_part);
+            b.d_part = nullptr;
+            b.part_cap = 0;
+            GNM_CU(cudaMalloc(&b.d_part, part_bytes));
+            b.part_cap = part_bytes;
+        }
+    }
+    return GNM_OK;
+}
+
 gnm_status open_window(gnm_ctx* c, uint64_t wid, cudaStream_t st, bool pin, uint32_t* s) {
     GNM_TRY(acquire_slot_impl(c, wid, st, pin, s));
     cudaEvent_t ev;
@@ -750,6 +802,10 @@ gnm_status gnm_create(const gnm_config* cfg, gnm_ctx** out) {
         return fail(GNM_E_INVAL, "admin_rule must be GNM_ADMIN_OR or GNM_ADMIN_AND");
     }
     if (c->cfg.window_slots == 0) c->cfg.window_slots = 64;
+    if (c->cfg.host_records < GNM_HOST_AUTO || c->cfg.host_records > GNM_HOST_IN_PLACE) {
+        delete c;
+        return fail(GNM_E_INVAL, "host_records must be GNM_HOST_AUTO, _STAGE or _IN_PLACE");
+    }
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || ndev == 0) {
@@ -1049,15 +1105,22 @@ gnm_status gnm_windows_results(gnm_ctx* c, const uint64_t* wids, size_t n, uint6
         GNM_TRY(wait_slot_on_stream(c, slot[k], c->aux));
     }
     std::vector<uint64_t> un6(unmatched ? n * kUnmatched * kNStat : 0);
-    for (size_t k = 0; k < n; ++k) {
+    for (size_t k = 0; k < n;) {
+        // windows k..k+m-1 in consecutive slots: one copy per array for the run (rates and
+        // flags are contiguous across slots; stats rows carry the unmatched rows between)
+        size_t m = 1;
+        while (k + m < n && slot[k + m] == slot[k] + m) ++m;
         const uint32_t s = slot[k];
-        const uint64_t* st = c->d_stats + (size_t)s * c->keys * kNStat;
-        if (stats) GNM_CU(cudaMemcpyAsync(stats + k * nk * kNStat, st, nk * kNStat * 8, cudaMemcpyDeviceToHost, c->aux));
-        if (unmatched)
-            GNM_CU(cudaMemcpyAsync(un6.data() + k * kUnmatched * kNStat, st + nk * kNStat, kUnmatched * kNStat * 8,
-                                   cudaMemcpyDeviceToHost, c->aux));
-        if (rate) GNM_CU(cudaMemcpyAsync(rate + k * nk, c->d_rate + (size_t)s * nk, nk * 8, cudaMemcpyDeviceToHost, c->aux));
-        if (flag) GNM_CU(cudaMemcpyAsync(flag + k * nk, c->d_flag + (size_t)s * nk, nk, cudaMemcpyDeviceToHost, c->aux));
+        if (rate) GNM_CU(cudaMemcpyAsync(rate + k * nk, c->d_rate + (size_t)s * nk, m * nk * 8, cudaMemcpyDeviceToHost, c->aux));
+        if (flag) GNM_CU(cudaMemcpyAsync(flag + k * nk, c->d_flag + (size_t)s * nk, m * nk, cudaMemcpyDeviceToHost, c->aux));
+        for (size_t j = k; j < k + m; ++j) {
+            const uint64_t* st = c->d_stats + (size_t)slot[j] * c->keys * kNStat;
+            if (stats) GNM_CU(cudaMemcpyAsync(stats + j * nk * kNStat, st, nk * kNStat * 8, cudaMemcpyDeviceToHost, c->aux));
+            if (unmatched)
+                GNM_CU(cudaMemcpyAsync(un6.data() + j * kUnmatched * kNStat, st + nk * kNStat, kUnmatched * kNStat * 8,
+                                       cudaMemcpyDeviceToHost, c->aux));
+        }
+        k += m;
     }
     GNM_CU(cudaStreamSynchronize(c->aux));
     if (unmatched)

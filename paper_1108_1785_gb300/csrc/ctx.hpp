@@ -176,6 +176,8 @@ constexpr int kMaxPlanKernels = 6;  // keys, count, scan, scatter, aggregate, fi
 gnm_status acquire_ring(gnm_ctx* c, uint32_t n_win, LaunchBuf** out);
 void set_slots_done(gnm_ctx* c, const uint32_t* slots, size_t n, cudaEvent_t ev, bool finalized);
 void unpin_slot(gnm_ctx* c, uint32_t s);
+// Grows every launch-ring entry's scratch for single-window launches of up to n records.
+gnm_status reserve_launch_scratch(gnm_ctx* c, uint64_t n);
 // Windows k = [offsets[k], offsets[k+1]) of rec on stream st. finalize: rates and flags at
 // the end; open_add: add to windows already open instead of starting them.
 gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets, const uint64_t* wids,

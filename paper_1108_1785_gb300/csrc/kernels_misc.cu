@@ -151,9 +151,11 @@ cudaError_t launch_finalize(const AggParams& p, uint32_t slot, cudaStream_t st) 
 
 cudaError_t launch_finalize_windows(const AggParams& p, cudaStream_t st) {
     if (p.n_wins == 0) return cudaSuccess;
-    const uint32_t bx = (p.keys + 255) / 256;
+    // key blocks per window: all of them, up to about 2048 CTAs over the windows
+    const uint32_t bx = (p.keys + kFinKeys - 1) / kFinKeys;
+    const uint32_t cap = std::max<uint32_t>(64u, 2048u / p.n_wins);
     (void)cudaGetLastError();
-    k_finalize_windows<<<dim3(bx > 64 ? 64 : bx, p.n_wins), kFinKeys, 0, st>>>(p);
+    k_finalize_windows<<<dim3(std::min(bx, cap), p.n_wins), kFinKeys, 0, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -331,6 +331,7 @@ void gnm_stream_config_default(gnm_stream_config* cfg) {
     cfg->budget_bytes = 4ull << 30;
     cfg->n_cuda_streams = 4;
     cfg->max_queued = 65536;
+    cfg->max_batch_records = 1u << 20;
 }
 
 gnm_status gnm_stream_open(gnm_ctx* c, const gnm_stream_config* cfg_in, gnm_stream** out) {
@@ -356,6 +357,13 @@ gnm_status gnm_stream_open(gnm_ctx* c, const gnm_stream_config* cfg_in, gnm_stre
         return fail(GNM_E_NOMEM, "device arena of " + std::to_string(arena) + " bytes");
     }
     s->arena.reset(arena);
+    if (const gnm_status r = reserve_launch_scratch(c, std::min<uint64_t>(cfg.max_batch_records,
+                                                                          cfg.budget_bytes / kRecordBytes));
+        r != GNM_OK) {
+        cudaFree(s->d_arena);
+        s->d_arena = nullptr;
+        return r;
+    }
     for (uint32_t k = 0; k < cfg.n_cuda_streams; ++k) {
         cudaStream_t st;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {

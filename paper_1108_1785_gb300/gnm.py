@@ -25,6 +25,7 @@ ADMIN_OR, ADMIN_AND = 0, 1
 TABLE_AUTO, TABLE_DIRECT, TABLE_HASH, TABLE_GLOBAL, TABLE_PARTITION = 0, 1, 2, 3, 4
 SPLIT_AUTO, SPLIT_FUSED, SPLIT_TWO_KERNELS = 0, 1, 2
 ROOT_LINEAR, ROOT_MLP = 0, 1
+HOST_AUTO, HOST_STAGE, HOST_IN_PLACE = 0, 1, 2
 KERNEL_TIMES = 1  # GNM_PLAN_KERNEL_TIMES
 KERNEL_NAMES = {0: "k_keys", 1: "k_aggregate", 2: "k_finalize_windows", 3: "k_part_count", 4: "k_part_scan",
                 5: "k_part_scatter"}
@@ -47,7 +48,7 @@ class Config(C.Structure):
                 ("window_slots", C.c_uint32), ("threshold_bps", C.c_double), ("block_threads", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("unroll", C.c_int32), ("table_mode", C.c_int32),
                 ("hash_slots", C.c_uint32), ("radix_bits", C.c_uint32), ("split", C.c_int32),
-                ("key_directory", C.c_int32)]
+                ("key_directory", C.c_int32), ("host_records", C.c_int32)]
 
 
 class RecordsC(C.Structure):
@@ -81,7 +82,8 @@ class RmiReport(C.Structure):
 
 
 class StreamConfig(C.Structure):
-    _fields_ = [("budget_bytes", C.c_uint64), ("n_cuda_streams", C.c_uint32), ("max_queued", C.c_uint32)]
+    _fields_ = [("budget_bytes", C.c_uint64), ("n_cuda_streams", C.c_uint32), ("max_queued", C.c_uint32),
+                ("max_batch_records", C.c_uint64)]
 
 
 class WindowDone(C.Structure):
@@ -503,13 +505,14 @@ class Stream:
     device-memory budget and processed on several CUDA streams as they arrive."""
 
     def __init__(self, ctx: Context, budget_bytes: int = 4 << 30, n_cuda_streams: int = 4,
-                 max_queued: int = 65536):
+                 max_queued: int = 65536, max_batch_records: int = 1 << 20):
         self.ctx = ctx
         c = StreamConfig()
         lib().gnm_stream_config_default(C.byref(c))
         c.budget_bytes = budget_bytes
         c.n_cuda_streams = n_cuda_streams
         c.max_queued = max_queued
+        c.max_batch_records = max_batch_records
         h = C.c_void_p()
         ctx._c(lib().gnm_stream_open(ctx.h, C.byref(c), C.byref(h)))
         self.h = h

@@ -103,6 +103,13 @@ def test_windows_results_batch_readout(gnm, batch):
     ctx.windows_results(ids, st, un, r, f)
     for w in range(W):
         assert_window_matches((st[w], un[w], r[w], f[w]), expect[w])
+    # any order and subset (runs of consecutive result slots are read with one copy each)
+    perm = np.concatenate([np.random.default_rng(2).permutation(W)[:20], np.arange(30, 40)])
+    st2, un2 = np.empty((perm.size, nk, 6), np.uint64), np.empty((perm.size, 4, 3), np.uint64)
+    r2, f2 = np.empty((perm.size, nk), np.float64), np.empty((perm.size, nk), np.uint8)
+    ctx.windows_results(ids[perm], st2, un2, r2, f2)
+    for j, w in enumerate(perm):
+        assert_window_matches((st2[j], un2[j], r2[j], f2[j]), expect[w])
     ctx.close()
 
 

@@ -301,6 +301,31 @@ def test_hot_key_counts_do_not_wrap(gnm, which):
     ctx.close()
 
 
+@pytest.mark.parametrize("which", ["c1", "c2"])
+def test_host_records_in_place_and_staged(gnm, c1, which):
+    """Page-locked host records read in place by the kernels, the same staged through a
+    device copy, and pageable records (staged under AUTO, refused under IN_PLACE): every
+    window equals the oracle."""
+    reg = fg.registry_c1() if which == "c1" else fg.registry_c2()
+    rec = fg.window_records_c1(reg, n=200_001) if which == "c1" else fg.make_records(reg, 200_001, seed=5)
+    off = [0, 3, 100_000, 200_001]
+    expect = [oracle_full(reg, {k: v[a:b] for k, v in rec.items()}) for a, b in zip(off[:-1], off[1:])]
+    pinned = gnm.Records({k: torch.from_numpy(np.ascontiguousarray(rec[k]).view(np.int32)).pin_memory()
+                          for k in gnm.FIELDS})
+    pageable = gnm.Records.host(rec)
+    for mode, recs, ok in (("IN_PLACE", pinned, True), ("STAGE", pinned, True), ("AUTO", pinned, True),
+                           ("AUTO", pageable, True), ("IN_PLACE", pageable, False)):
+        ctx = _ctx(gnm, reg, host_records=getattr(gnm, "HOST_" + mode))
+        if not ok:
+            with pytest.raises(gnm.GnmError, match="IN_PLACE"):
+                ctx.process_windows(recs, off, [1, 2, 3])
+        else:
+            ctx.process_windows(recs, off, [1, 2, 3])
+            for w, e in zip([1, 2, 3], expect):
+                assert_window_matches(ctx.dense(w), e)
+        ctx.close()
+
+
 def test_partition_needs_split_launches(gnm):
     reg = fg.registry_c2()
     ctx = _ctx(gnm, reg, table_mode=gnm.TABLE_PARTITION, split=gnm.SPLIT_FUSED)
