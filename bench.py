@@ -133,6 +133,47 @@ def learned_vs_plain(gnm, torch, local, steps, warmup, n_records=50_000_000,
                                        if "bsearch" in res and "rmi" in res else None)}
 
 
+def window_c1(gnm, torch, local, reps=1000):
+    """One window of 100,000 records against the 500-site registry: per-window latency of
+    the CUDA-graph launch with L2 warm (launches back to back) and cold (a 2x L2 write
+    before every launch, timed apart from it)."""
+    import flowgen as fg
+    reg = fg.registry_c1()
+    rec = fg.window_records_c1(reg)
+    n = rec["srcaddr"].size
+    ctx = gnm.Context(device=local, window_slots=4)
+    ctx.load(reg)
+    dev = gnm.Records.to_device(rec)
+    plan = ctx.plan(dev, [0, n], [1])
+    stream = torch.cuda.current_stream()
+    for _ in range(20):
+        plan.launch(stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        plan.launch(stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    warm_us = a.elapsed_time(b) * 1e3 / reps
+    flush = torch.empty(2 * 129 * (1 << 20) // 4, dtype=torch.int32, device=f"cuda:{local}")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps // 10)]
+    for e0, e1 in ev:
+        flush.fill_(1)
+        e0.record(stream)
+        plan.launch(stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    cold_us = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev])) * 1e3
+    plan.close()
+    ctx.close()
+    return {"workload": f"one window of {n:,} records; {reg.n_sites} sites / {reg.n:,} prefixes (registry in "
+                        "shared memory); CUDA-graph launch",
+            "warm_us": warm_us, "warm_records_per_s": n / (warm_us * 1e-6), "warm_reps": reps,
+            "cold_us": cold_us, "cold_records_per_s": n / (cold_us * 1e-6), "cold_reps": len(ev),
+            "cold": "a 258 MB write (2x L2) before every timed launch"}
+
+
 def batched_c4(gnm, torch, local, steps, warmup):
     """256 uneven windows (lognormal sizes around 200,000 records, clamped to 10,000-2,000,000)
     over the 500-site registry in one CUDA-graph launch, shape autotuned by the library."""
@@ -264,6 +305,7 @@ def serve_c5(gnm, torch, local, minutes=30, speedup=600.0, pool_n=20_000_000, bu
             "p50_ms": float(np.percentile(lat, 50, method="inverted_cdf")) if lat else None,
             "p99_ms": float(np.percentile(lat, 99, method="inverted_cdf")) if lat else None,
             "max_ms": max(lat) if lat else None, "latency": "window close -> rates and flags final (host clock)",
+            "slowest_windows_ms": sorted(((r[2], r[0]) for r in reports if r[3] == 0), reverse=True)[:3],
             "budget_bytes": budget, "peak_inflight_bytes": int(st["peak_inflight_bytes"]),
             "batches": int(st["batches"]), "batches_queued": int(st["batches_queued"]),
             "checked_windows": checked, "mix_equals_alone": bool(ok),
@@ -367,6 +409,22 @@ def cpu_oracle_hour(reg, rec, off, n_threads):
     return time.perf_counter() - t0
 
 
+def cpu_oracle_c3(cores, n=5_000_000):
+    """The oracle on a sample of the learned-index workload (100,000-site registry): one
+    window of n records on all host threads; records/s (scaled from the sample)."""
+    import flowgen as fg
+    import oracle
+    reg = fg.registry_c3()
+    rec = fg.make_records(reg, n, seed=2, p_reg=0.9, zipf_s=0.9)
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    t0 = time.perf_counter()
+    st, _ = oracle.window(lpm, reg.local_prefix, reg.local_len, reg.n_sites, rec, n_threads=cores)
+    oracle.flags(st, oracle.rates(st), 1e8)
+    t = time.perf_counter() - t0
+    return {"value": n / t, "unit": "records/s", "cores": cores,
+            "sample": f"one window of {n:,} records (the learned-index registry), {t:.2f} s"}
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle on this host's cores, same workload and metric."""
     world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
@@ -407,7 +465,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the plain-vs-learned index comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the streaming-server replay")
-    ap.add_argument("--only", default="all", choices=["all", "learned", "serve", "batched"],
+    ap.add_argument("--only", default="all", choices=["all", "learned", "serve", "batched", "window"],
                     help="run one leg alone (profiling): the learned-index comparison, the server replay "
                          "or the batched windows")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-window batched launch")
@@ -433,6 +491,8 @@ def main():
                                    tuple(args.learned_modes.split(",")))
         elif args.only == "batched":
             leg = batched_c4(gnm, torch, local, args.steps, args.warmup)
+        elif args.only == "window":
+            leg = window_c1(gnm, torch, local)
         else:
             leg = serve_c5(gnm, torch, local, minutes=args.serve_minutes, speedup=args.serve_speedup)
         print(json.dumps({"leg": args.only, **leg}), flush=True)
@@ -580,15 +640,22 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         s = cpu_oracle_hour(reg, rec, off, cores)
+        # one thread (the paper's CPU baseline ran on one core) on the first 10 windows
+        off10 = off[:11]
+        s1 = cpu_oracle_hour(reg, {k: v[:int(off10[-1])] for k, v in rec.items()}, off10, 1)
         out["cpu_baseline"] = {"value": n / s, "unit": "records/s", "cores": cores, "kind": "oracle",
                                "sample": f"the whole step once: {n_win} windows, {n:,} records "
-                                         f"({s:.2f} s on {cores} threads)"}
+                                         f"({s:.2f} s on {cores} threads)",
+                               "single_thread": {"value": int(off10[-1]) / s1, "unit": "records/s",
+                                                 "sample": f"first 10 windows, {int(off10[-1]):,} records, 1 thread"},
+                               "learned_registry": cpu_oracle_c3(cores)}
     ctx.close()
     del dev
     if world == 1 and not args.no_learned:
         out["learned_index"] = learned_vs_plain(gnm, torch, local, args.steps, args.warmup, args.learned_records,
                                                 tuple(args.learned_modes.split(",")))
     if world == 1 and not args.no_batched:
+        out["window"] = window_c1(gnm, torch, local)
         out["batched"] = batched_c4(gnm, torch, local, args.steps, args.warmup)
     if world == 1 and not args.no_serve:
         out["serving"] = serve_c5(gnm, torch, local, minutes=args.serve_minutes, speedup=args.serve_speedup)

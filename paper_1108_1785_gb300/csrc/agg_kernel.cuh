@@ -856,7 +856,7 @@ __device__ __forceinline__ void stage_lookup(const AggParams& p, unsigned char* 
 }
 
 template <int LOOKUP, int TABLE, int AGG, int U>
-__global__ void __launch_bounds__(U == 1 ? 1024 : 512)
+__global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
     k_aggregate(const __grid_constant__ AggParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_last;

@@ -360,7 +360,7 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s, size_t n_win) {
     int unroll = cfg.unroll ? cfg.unroll : (c->tuned.unroll ? c->tuned.unroll : 1);
     if (block < 64 || block > 1024 || block % 32) return fail(GNM_E_INVAL, "block_threads must be 64..1024, multiple of 32");
     if (unroll != 1 && unroll != 2) return fail(GNM_E_INVAL, "unroll must be 1 or 2");
-    if (unroll == 2 && block > 512) unroll = 1;
+    if (unroll == 2 && block > agg_block_max(s->split ? kLookupKeys : s->lookup, s->table, s->agg, 2)) unroll = 1;
     s->block = block;
     s->unroll = unroll;
     s->smem = aggregate_smem_bytes(s->split ? kLookupKeys : s->lookup, s->table, nr, rows, cap,

@@ -231,7 +231,7 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
                     for (int rb : bits_v)
                         for (int cps : cpss) {
                             if (status != GNM_OK) break;
-                            if (u == 2 && b > 512) continue;
+                            if (u == 2 && b > 512 && !(sp == GNM_SPLIT_TWO_KERNELS && a == GNM_AGG_DIRECT)) continue;
                             c->cfg = saved;
                             if (c->cfg.block_threads == 0) c->cfg.block_threads = b;
                             if (c->cfg.unroll == 0) c->cfg.unroll = u;
