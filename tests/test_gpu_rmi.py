@@ -291,6 +291,23 @@ def test_mlp_root_rmi_exact(gnm, c3):
     ctx.close()
 
 
+def test_mlp_root_window_exact(gnm, c3):
+    """The MLP-root model inside the window kernels (key kernel, regrouping, aggregation):
+    two windows equal the oracle and no lookup leaves its proven window."""
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx = gnm.Context(window_slots=4)
+    ctx.load(reg)
+    ctx.rmi_train(to_dev(keys), root_kind=gnm.ROOT_MLP, hidden=16, mlp_steps=200, n_leaves=2048)
+    assert ctx.registry_info().lookup_mode == gnm.LOOKUP_RMI
+    ctx.rmi_violations(reset=True)
+    off = [0, 123_457, 400_000]
+    ctx.process_windows(gnm.Records.to_device({k: v[:400_000] for k, v in rec.items()}), off, [1, 2])
+    for w, (a, b) in zip([1, 2], zip(off[:-1], off[1:])):
+        assert_window_matches(ctx.dense(w), oracle_full(reg, {k: v[a:b] for k, v in rec.items()}, lpm=lpm))
+    assert ctx.rmi_violations() == 0
+    ctx.close()
+
+
 def test_rmi_export_import_roundtrip(gnm, c3, trained_linear):
     reg, lpm, starts, sites, rec, keys = c3
     ctx, _ = trained_linear
