@@ -393,3 +393,57 @@ uint32_t orc_rate_bucket(uint32_t octets, uint32_t dur) {
     uint64_t n = ((uint64_t)octets * 4u) / ((uint64_t)dur * 5u);
     return n > 10000u ? 10000u : (uint32_t)n;
 }
+
+/* Per-flow transfer-rate statistics of a window (Sec. III.B.2.1: maximum, minimum and
+ * median of the rates of each site's flows; the median from the 10001-bucket histogram).
+ * Over the eligible flows of each key (site*2 + dir, as in orc_window):
+ *   hist[key * 10001 + b]  flows whose rate falls in bucket b (orc_rate_bucket)
+ *   rmin[key], rmax[key]   least and greatest (double)octets * 8000.0 / (double)dur,
+ *                          NaN when the key has no eligible flow
+ *   med[key]               the bucket holding the ceil(n/2)-th smallest of the key's n
+ *                          rates (the lower median), 0xFFFFFFFF when n = 0
+ * Records of unmatched classes carry no rate statistics. */
+int orc_rate_stats(const orc_lpm *m, const uint32_t *local_pfx, const uint8_t *local_len,
+                   size_t n_local, uint32_t n_sites, uint32_t min_avg_pkt_bytes, uint32_t min_pkts,
+                   uint32_t min_dur_ms, int admin_rule, const uint32_t *src, const uint32_t *dst,
+                   const uint32_t *pkts, const uint32_t *octets, const uint32_t *first,
+                   const uint32_t *last, size_t n, uint32_t *hist, double *rmin, double *rmax,
+                   uint32_t *med) {
+    orc_params p = {local_pfx, local_len, n_local, n_sites, min_avg_pkt_bytes, min_pkts,
+                    min_dur_ms, admin_rule, 0};
+    const size_t nk = (size_t)n_sites * 2;
+    memset(hist, 0, nk * 10001u * sizeof(uint32_t));
+    for (size_t k = 0; k < nk; k++) {
+        rmin[k] = NAN;
+        rmax[k] = NAN;
+    }
+    for (size_t i = 0; i < n; i++) {
+        int sl = orc_is_local(&p, src[i]);
+        int dl = orc_is_local(&p, dst[i]);
+        if (sl == dl) continue;                    /* neither or both local */
+        uint32_t s = orc_hash_one(m, sl ? dst[i] : src[i]);
+        if (s == ORC_NO_SITE) continue;            /* remote endpoint unregistered */
+        uint32_t dur = last[i] - first[i];
+        if (!orc_eligible(&p, pkts[i], octets[i], dur)) continue;
+        size_t k = (size_t)s * 2 + (sl ? 1 : 0);
+        hist[k * 10001u + orc_rate_bucket(octets[i], dur)] += 1;
+        double r = (double)octets[i] * 8000.0 / (double)dur;
+        if (isnan(rmin[k]) || r < rmin[k]) rmin[k] = r;
+        if (isnan(rmax[k]) || r > rmax[k]) rmax[k] = r;
+    }
+    for (size_t k = 0; k < nk; k++) {
+        uint64_t total = 0;
+        for (uint32_t b = 0; b <= 10000u; b++) total += hist[k * 10001u + b];
+        med[k] = 0xFFFFFFFFu;
+        if (total == 0) continue;
+        uint64_t want = (total + 1) / 2, cum = 0;
+        for (uint32_t b = 0; b <= 10000u; b++) {
+            cum += hist[k * 10001u + b];
+            if (cum >= want) {
+                med[k] = b;
+                break;
+            }
+        }
+    }
+    return 0;
+}

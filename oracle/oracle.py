@@ -58,6 +58,8 @@ def _load():
             lib.orc_flags.argtypes = [P, P, C.c_size_t, C.c_double, C.c_uint32, P]
             lib.orc_rate_bucket.restype = C.c_uint32
             lib.orc_rate_bucket.argtypes = [C.c_uint32, C.c_uint32]
+            lib.orc_rate_stats.argtypes = [P, P, P, C.c_size_t, C.c_uint32, C.c_uint32, C.c_uint32,
+                                           C.c_uint32, C.c_int] + [P] * 6 + [C.c_size_t, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -161,6 +163,31 @@ def flags(stats: np.ndarray, rate: np.ndarray, threshold: float, min_flows: int 
 
 def rate_bucket(octets: int, dur: int) -> int:
     return int(_load().orc_rate_bucket(int(octets), int(dur)))
+
+
+N_BUCKETS = 10001  # rate histogram buckets of 10 kb/s, the last one for rates >= 100 Mb/s
+NO_MEDIAN = 0xFFFFFFFF
+
+
+def rate_stats(lpm: LPM, local_prefix, local_len, n_sites: int, rec: Dict[str, np.ndarray],
+               min_avg_pkt_bytes: int = 100, min_pkts: int = 10, min_dur_ms: int = 1000, admin_rule: int = 0):
+    """Per-flow rate statistics of a window (Sec. III.B.2.1). Returns (hist[2S, 10001] u32,
+    rmin[2S] f64, rmax[2S] f64, median_bucket[2S] u32): over the eligible flows of each key,
+    the rate histogram, the least and greatest rate (NaN without eligible flows) and the
+    bucket of the lower median (NO_MEDIAN without eligible flows)."""
+    lib = _load()
+    lp = _c(local_prefix, np.uint32)
+    ll = _c(local_len, np.uint8)
+    f = [_c(rec[k], np.uint32) for k in ("srcaddr", "dstaddr", "dPkts", "dOctets", "first", "last")]
+    nk = 2 * n_sites
+    hist = np.zeros((nk, N_BUCKETS), np.uint32)
+    rmin = np.empty(nk, np.float64)
+    rmax = np.empty(nk, np.float64)
+    med = np.empty(nk, np.uint32)
+    rc = lib.orc_rate_stats(lpm._h, _p(lp), _p(ll), lp.size, n_sites, min_avg_pkt_bytes, min_pkts, min_dur_ms,
+                            admin_rule, *[_p(a) for a in f], f[0].size, _p(hist), _p(rmin), _p(rmax), _p(med))
+    assert rc == 0
+    return hist, rmin, rmax, med
 
 
 def full_window(lpm: LPM, reg, rec, threshold: float = 1e8, min_flows: int = 1, **kw):

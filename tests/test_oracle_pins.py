@@ -312,6 +312,66 @@ def test_rate_bucket_closed_form():
 
 # ---------------------------------------------------------- learned-index maths
 
+def test_rate_stats_hand_case():
+    """Three eligible outbound flows to one site plus one that the filters drop: rates 1, 3
+    and 2 Mb/s (buckets 100, 300, 200), min 1e6, max 3e6, lower median the 2nd smallest
+    (2 Mb/s, bucket 200); the other key has none."""
+    reg = np.array([[ip("10.0.0.0"), 8, 0]])
+    m = oracle.LPM(reg[:, 0], reg[:, 1], reg[:, 2])
+    loc = ip("131.225.0.0")
+    # octets, dur: 125,000 B in 1 s = 1 Mb/s; 375,000 B in 1 s = 3 Mb/s; 500,000 B in 2 s = 2 Mb/s
+    oc = np.array([125_000, 375_000, 500_000, 125_000], np.uint32)
+    dur = np.array([1000, 1000, 2000, 10], np.uint32)  # the last lasts 10 ms: administrative
+    rec = {"srcaddr": np.full(4, loc + 5, np.uint32), "dstaddr": np.full(4, ip("10.1.2.3"), np.uint32),
+           "dPkts": np.full(4, 100, np.uint32), "dOctets": oc, "first": np.full(4, 7, np.uint32),
+           "last": (7 + dur).astype(np.uint32)}
+    hist, rmin, rmax, med = oracle.rate_stats(m, [loc], [16], 1, rec)
+    want = np.zeros((2, oracle.N_BUCKETS), np.uint32)
+    want[1, [100, 200, 300]] = 1
+    np.testing.assert_array_equal(hist, want)
+    assert rmin[1] == 1e6 and rmax[1] == 3e6 and med[1] == 200
+    assert np.isnan(rmin[0]) and np.isnan(rmax[0]) and med[0] == oracle.NO_MEDIAN
+
+
+def test_rate_stats_against_sorted_rates():
+    """Independent numpy restatement on C1 data: per key, the eligible flows' rates sorted,
+    their least, greatest and ceil(n/2)-th values and its bucket; the histogram from numpy's
+    bincount; histogram totals equal the window's eligible-flow counts."""
+    reg, rec, m = _c1_window(n=30000, seed=9)
+    hist, rmin, rmax, med = oracle.rate_stats(m, reg.local_prefix, reg.local_len, reg.n_sites, rec)
+    st, _ = oracle.window(m, reg.local_prefix, reg.local_len, reg.n_sites, rec)
+    np.testing.assert_array_equal(hist.sum(axis=1), st[:, 3])
+    src, dst = rec["srcaddr"].astype(np.int64), rec["dstaddr"].astype(np.int64)
+
+    def local(a):
+        out = np.zeros(a.shape, bool)
+        for p, l in zip(reg.local_prefix, reg.local_len):
+            out |= (a >> (32 - int(l))) == (int(p) >> (32 - int(l)))
+        return out
+
+    sl, dl = local(src), local(dst)
+    flat_s, flat_site = m.flatten()
+    remote = np.where(sl & ~dl, dst, src).astype(np.uint32)
+    site = flat_site[np.searchsorted(flat_s, remote, side="right") - 1]
+    o = rec["dOctets"].astype(np.int64)
+    pk = rec["dPkts"].astype(np.int64)
+    d = (rec["last"].astype(np.int64) - rec["first"].astype(np.int64)) % (1 << 32)
+    elig = (sl != dl) & (site != oracle.NO_SITE) & (d > 0) & (o >= 100 * pk) & (pk >= 10) & (d >= 1000)
+    key = site.astype(np.int64) * 2 + (sl & ~dl)
+    rate = o * 8000.0 / np.where(d > 0, d, 1)
+    bucket = np.minimum(10000, (4 * o) // (5 * np.where(d > 0, d, 1)))
+    for k in range(2 * reg.n_sites):
+        sel = elig & (key == k)
+        if not sel.any():
+            assert np.isnan(rmin[k]) and med[k] == oracle.NO_MEDIAN
+            continue
+        r = np.sort(rate[sel])
+        b = np.sort(bucket[sel])
+        assert rmin[k] == r[0] and rmax[k] == r[-1]
+        assert med[k] == b[(sel.sum() + 1) // 2 - 1]
+        np.testing.assert_array_equal(hist[k], np.bincount(bucket[sel], minlength=oracle.N_BUCKETS))
+
+
 def test_lstsq_line_equals_polyfit():
     rng = np.random.default_rng(0)
     x = rng.random(5000) * 1e6
