@@ -114,6 +114,9 @@ typedef struct {
                                    pairs ends a lookup; 2 = the range directory and a
                                    search over L2; 0 = 3, else 1, whichever fits first */
     int32_t host_records;       /* GNM_HOST_*: how kernels get host (on_device = 0) records */
+    int32_t rate_stats;         /* 1: per-flow rate statistics per window (gnm_window_rate_stats):
+                                   each result slot also holds a 10001-bucket histogram per key
+                                   (40 KB per key); 0: off */
 } gnm_config;
 
 /* Host records: AUTO reads them in place when every array is page-locked host memory that
@@ -234,6 +237,23 @@ gnm_status gnm_site_stats(gnm_ctx *ctx, uint64_t window_id, gnm_site_stat *out, 
  * on the device against this threshold, compacted, then copied to site_out/dir_out. */
 gnm_status gnm_flag_suboptimal(gnm_ctx *ctx, uint64_t window_id, double threshold_bps,
                                uint32_t *site_out, uint8_t *dir_out, size_t cap, size_t *n_out);
+
+/* Per-flow transfer-rate statistics of a finalised window (contexts created with
+ * rate_stats = 1; GNM_E_STATE otherwise). Sec. III.B.2.1: the maximum, minimum and median
+ * of the rates of each (site, dir)'s flows, the median from a histogram of 10 kb/s buckets
+ * whose last bucket holds every rate from 100 Mb/s up. Over the eligible flows of key
+ * site*2+dir, with rate = (double)octets * 8000.0 / (double)duration_ms (one rounding per
+ * operation) and bucket = min(10000, floor(4 * octets / (5 * duration_ms))):
+ *   rmin[k], rmax[k]     least and greatest rate; NaN without eligible flows
+ *   median_bucket[k]     bucket of the ceil(n/2)-th smallest of the key's n rates (the
+ *                        lower median): its rate lies in [10 kb/s * b, 10 kb/s * (b+1));
+ *                        GNM_NO_MEDIAN without eligible flows
+ *   hist[k * 10001 + b]  flows of key k in bucket b
+ * Arrays have 2*n_sites entries (hist 2*n_sites*10001); each may be NULL. */
+#define GNM_RATE_BUCKETS 10001u
+#define GNM_NO_MEDIAN 0xFFFFFFFFu
+gnm_status gnm_window_rate_stats(gnm_ctx *ctx, uint64_t window_id, double *rmin, double *rmax,
+                                 uint32_t *median_bucket, uint32_t *hist);
 
 /* Dense copies of a window's results to host arrays (each may be NULL):
  * stats[(2*n_sites) x GNM_NSTAT] (row site*2+dir), unmatched[12], rate[2*n_sites],

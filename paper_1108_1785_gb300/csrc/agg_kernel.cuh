@@ -364,6 +364,9 @@ __device__ __forceinline__ void add_wrap64(uint32_t* lo, uint64_t* g, uint64_t v
 
 struct Smem {
     uint32_t key_base;  // keys of the current segment are relative to it (partitioned launches)
+    uint32_t* hist;     // rate statistics of the current window, offset by key_base (or null)
+    unsigned long long* rmin;
+    unsigned long long* rmax;
     uint32_t* t;        // table rows (kRowWords words each)
     uint32_t* tk;       // hash keys
     uint32_t rows;      // table rows
@@ -710,6 +713,19 @@ __device__ __forceinline__ Item classify_key(const AggParams& p, bool valid, uin
     return it;
 }
 
+// Per-flow rate statistics (Sec. III.B.2.1: minimum, maximum and the median's 10 kb/s
+// histogram) of one eligible record of key `key`: bucket = min(10000, floor(4 o / (5 d))),
+// rate = o * 8000 / d in FP64 (one rounding per operation). Rates are >= 0, so their bit
+// patterns order like the values; a read first skips the atomics that cannot change them.
+__device__ __forceinline__ void rate_stat_add(const Smem& sm, uint32_t key, uint32_t oc, uint32_t dur) {
+    const uint64_t b = ((uint64_t)oc * 4u) / ((uint64_t)dur * 5u);
+    atomicAdd(sm.hist + (size_t)key * kRateBuckets + (b < 10000u ? b : 10000u), 1u);
+    const double r = __ddiv_rn(__dmul_rn(__uint2double_rn(oc), 8000.0), __uint2double_rn(dur));
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(r);
+    if (bits > __ldcg(sm.rmax + key)) atomicMax(sm.rmax + key, bits);
+    if (bits < __ldcg(sm.rmin + key)) atomicMin(sm.rmin + key, bits);
+}
+
 // Processes R records per thread: lookups for all of them first (independent loads in
 // flight together), then classification and accumulation. With LOOKUP == kLookupKeys the
 // `src` field carries each record's precomputed key instead of an address.
@@ -724,6 +740,7 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
         for (int j = 0; j < R; ++j) {
             const Item it = classify_key(p, valid[j], src[j], sm.key_base, pk[j], oc[j], fi[j], la[j]);
             accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
+            if (sm.hist && it.valid && it.elig) rate_stat_add(sm, it.key, it.oc, it.dur);
         }
     } else {
         uint32_t x[R], site[R];
@@ -738,6 +755,7 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
         for (int j = 0; j < R; ++j) {
             const Item it = classify(p, valid[j], sl[j], dl[j], pk[j], oc[j], fi[j], la[j], site[j]);
             accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
+            if (sm.hist && it.valid && it.elig) rate_stat_add(sm, it.key, it.oc, it.dur);
         }
     }
 }
@@ -871,6 +889,9 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
                 LOOKUP == kLookupRmi ? p.rmi.n_leaves : 0u, p.radix_bits, &off_keys, &off_lookup);
     Smem sm;
     sm.key_base = 0u;
+    sm.hist = nullptr;
+    sm.rmin = nullptr;
+    sm.rmax = nullptr;
     sm.rows = TABLE == kTableDirect ? p.table_rows : (TABLE == kTableHash ? p.table_cap : 0u);
     sm.t = reinterpret_cast<uint32_t*>(smem_raw);
     sm.tk = reinterpret_cast<uint32_t*>(smem_raw + off_keys);
@@ -888,6 +909,12 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
         // (a segment of a partitioned launch holds keys relative to its group's first key)
         uint64_t* gacc = p.acc + ((size_t)wd.slot * p.keys + wd.key_base) * kAccCols;
         sm.key_base = wd.key_base;
+        if (p.hist) {
+            const size_t k0 = (size_t)wd.slot * 2u * p.n_sites + wd.key_base;
+            sm.hist = p.hist + k0 * kRateBuckets;
+            sm.rmin = p.rmin + k0;
+            sm.rmax = p.rmax + k0;
+        }
         // pieces of at most kFlushRecords records, so the 16-bit counts cannot wrap. With a
         // partial-sum area the CTA's segment of the window ends in one block of its own
         // (block q = the CTA's position among the window's CTAs), and the pieces before
@@ -949,6 +976,9 @@ __global__ void __launch_bounds__(keys_block_max(LOOKUP, U)) k_keys(const __grid
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem sm;
     sm.key_base = 0u;
+    sm.hist = nullptr;
+    sm.rmin = nullptr;
+    sm.rmax = nullptr;
     sm.t = nullptr;
     sm.tk = nullptr;
     sm.rows = 0;

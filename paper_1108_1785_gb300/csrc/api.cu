@@ -1,5 +1,6 @@
 // api.cu -- the C ABI: contexts, registry upload, window processing and result readout.
 #include <algorithm>
+#include <limits>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -120,6 +121,16 @@ void release_slots(gnm_ctx* c) {
     free_dev(c->d_rate);
     free_dev(c->d_flag);
     free_dev(c->d_flag_keys);
+    free_dev(c->d_hist);
+    free_dev(c->d_rmin);
+    free_dev(c->d_rmax);
+    free_dev(c->d_med);
+    free_dev(c->d_mcnt);
+    c->d_hist = nullptr;
+    c->d_rmin = nullptr;
+    c->d_rmax = nullptr;
+    c->d_med = nullptr;
+    c->d_mcnt = nullptr;
     c->d_acc = nullptr;
     c->d_stats = nullptr;
     c->d_rate = nullptr;
@@ -433,6 +444,9 @@ gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p) {
     p->flag = c->d_flag;
     p->keys = c->keys;
     p->table_rows = c->keys;
+    p->hist = c->d_hist;
+    p->rmin = c->d_rmin;
+    p->rmax = c->d_rmax;
     p->min_flows = c->cfg.min_flows_to_flag;
     p->threshold = c->cfg.threshold_bps;
     p->violations = c->d_violations;
@@ -533,11 +547,27 @@ PartLayout part_layout(uint64_t n, uint32_t nb) {
     return l;
 }
 
+gnm_status clear_rate_stats(gnm_ctx* c, const uint32_t* slots, size_t n, cudaStream_t st) {
+    if (!c->d_hist) return GNM_OK;
+    const size_t nk = (size_t)2 * c->n_sites;
+    for (size_t k = 0; k < n;) {  // runs of consecutive slots: one memset per array
+        size_t m = 1;
+        while (k + m < n && slots[k + m] == slots[k] + m) ++m;
+        const size_t s0 = slots[k];
+        GNM_CU(cudaMemsetAsync(c->d_hist + s0 * nk * kRateBuckets, 0, m * nk * kRateBuckets * 4, st));
+        GNM_CU(cudaMemsetAsync(c->d_rmax + s0 * nk, 0, m * nk * 8, st));
+        GNM_CU(cudaMemsetAsync(c->d_rmin + s0 * nk, 0xFF, m * nk * 8, st));  // above every rate
+        k += m;
+    }
+    return GNM_OK;
+}
+
 gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, size_t n_win,
                             const uint32_t* slots, bool finalize, WinDesc* d_wins, uint32_t* d_done,
                             uint32_t* d_partials, uint32_t* d_keys, unsigned char* d_part, cudaStream_t st,
-                            uint32_t* launches, cudaEvent_t* marks, int32_t* kinds) {
+                            uint32_t* launches, cudaEvent_t* marks, int32_t* kinds, bool fresh) {
     *launches = 0;
+    if (fresh) GNM_TRY(clear_rate_stats(c, slots, n_win, st));
     // an external event node when captured into a graph, so that the host can read it
     auto mark = [&](int32_t kind) -> gnm_status {
         if (!marks) return GNM_OK;
@@ -709,7 +739,8 @@ gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offse
         GNM_CU(cudaMemcpyAsync(lb->d_wins, lb->h_wins, sizeof(WinDesc) * pr.wins.size(), cudaMemcpyHostToDevice, st));
     }
     GNM_TRY(enqueue_prepared(c, pr, offsets, n_win, slot.data(), finalize, lb->d_wins, lb->d_done,
-                             lb->d_partials, lb->d_keys, lb->d_part, st, &c->last_launches));
+                             lb->d_partials, lb->d_keys, lb->d_part, st, &c->last_launches, nullptr, nullptr,
+                             !open_add));
     GNM_CU(cudaEventRecord(lb->ev, st));
     lb->ev_recorded = true;
     for (size_t k = 0; k < n_win; ++k) c->slots[slot[k]].records += offsets[k + 1] - offsets[k];
@@ -745,6 +776,7 @@ gnm_status reserve_launch_scratch(gnm_ctx* c, uint64_t n) {
 
 gnm_status open_window(gnm_ctx* c, uint64_t wid, cudaStream_t st, bool pin, uint32_t* s) {
     GNM_TRY(acquire_slot_impl(c, wid, st, pin, s));
+    GNM_TRY(clear_rate_stats(c, s, 1, st));
     cudaEvent_t ev;
     GNM_TRY(record_event(c, st, &ev));
     set_slots_done(c, s, 1, ev, false);
@@ -995,6 +1027,14 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     GNM_CU(cudaMalloc(&c->d_flag, slots * 2 * n_sites));
     GNM_CU(cudaMalloc(&c->d_flag_keys, (size_t)2 * n_sites * 4));
     GNM_CU(cudaMemset(c->d_acc, 0, slots * keys * kAccCols * 8));
+    if (c->cfg.rate_stats) {  // per-flow rate statistics: a histogram per site key and slot
+        const size_t nk = (size_t)2 * n_sites;
+        GNM_CU(cudaMalloc(&c->d_hist, slots * nk * kRateBuckets * 4));
+        GNM_CU(cudaMalloc(&c->d_rmin, slots * nk * 8));
+        GNM_CU(cudaMalloc(&c->d_rmax, slots * nk * 8));
+        GNM_CU(cudaMalloc(&c->d_med, nk * 4));
+        GNM_CU(cudaMalloc(&c->d_mcnt, nk * 4));
+    }
     c->slots.resize(slots);
     c->have_registry = true;
     return GNM_OK;
@@ -1069,6 +1109,41 @@ static gnm_status sync_slot(gnm_ctx* c, uint32_t s) {
     Slot& sl = c->slots[s];
     if (!sl.finalized) return fail(GNM_E_STATE, "window is open (not finalised)");
     if (sl.ev) GNM_CU(cudaEventSynchronize(sl.ev));
+    return GNM_OK;
+}
+
+gnm_status gnm_window_rate_stats(gnm_ctx* c, uint64_t wid, double* rmin, double* rmax, uint32_t* median_bucket,
+                                 uint32_t* hist) {
+    if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
+    if (!c->d_hist) return fail(GNM_E_STATE, "the context keeps no rate statistics (rate_stats = 0)");
+    GNM_CU(cudaSetDevice(c->device));
+    uint32_t s;
+    GNM_TRY(find_window(c, wid, &s));
+    if (!c->slots[s].finalized) return fail(GNM_E_STATE, "window is open (not finalised)");
+    GNM_TRY(wait_slot_on_stream(c, s, c->aux));
+    const size_t nk = (size_t)2 * c->n_sites;
+    const uint32_t* h = c->d_hist + (size_t)s * nk * kRateBuckets;
+    GNM_CU(launch_rate_median(h, (uint32_t)nk, c->d_med, c->d_mcnt, c->aux));
+    std::vector<uint32_t> cnt(nk);
+    std::vector<unsigned long long> lo(rmin ? nk : 0), hi(rmax ? nk : 0);
+    GNM_CU(cudaMemcpyAsync(cnt.data(), c->d_mcnt, nk * 4, cudaMemcpyDeviceToHost, c->aux));
+    if (median_bucket) GNM_CU(cudaMemcpyAsync(median_bucket, c->d_med, nk * 4, cudaMemcpyDeviceToHost, c->aux));
+    if (rmin) GNM_CU(cudaMemcpyAsync(lo.data(), c->d_rmin + (size_t)s * nk, nk * 8, cudaMemcpyDeviceToHost, c->aux));
+    if (rmax) GNM_CU(cudaMemcpyAsync(hi.data(), c->d_rmax + (size_t)s * nk, nk * 8, cudaMemcpyDeviceToHost, c->aux));
+    if (hist) GNM_CU(cudaMemcpyAsync(hist, h, nk * kRateBuckets * 4, cudaMemcpyDeviceToHost, c->aux));
+    GNM_CU(cudaStreamSynchronize(c->aux));
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    for (size_t k = 0; k < nk; ++k) {
+        double v;
+        if (rmin) {
+            std::memcpy(&v, &lo[k], 8);
+            rmin[k] = cnt[k] ? v : nan;
+        }
+        if (rmax) {
+            std::memcpy(&v, &hi[k], 8);
+            rmax[k] = cnt[k] ? v : nan;
+        }
+    }
     return GNM_OK;
 }
 

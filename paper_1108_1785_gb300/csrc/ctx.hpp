@@ -109,6 +109,11 @@ struct gnm_ctx {
     uint64_t* d_stats = nullptr;
     double* d_rate = nullptr;
     uint8_t* d_flag = nullptr;
+    uint32_t* d_hist = nullptr;           // rate statistics (cfg.rate_stats): [slots][2S][10001]
+    unsigned long long* d_rmin = nullptr; // [slots][2S]
+    unsigned long long* d_rmax = nullptr; // [slots][2S]
+    uint32_t* d_med = nullptr;            // [2S] readout scratch: median buckets
+    uint32_t* d_mcnt = nullptr;           // [2S] readout scratch: eligible flows
     std::vector<gnm::Slot> slots;
     std::unordered_map<uint64_t, uint32_t> slot_of;
     uint64_t age = 0;
@@ -167,10 +172,12 @@ gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* off
 // Enqueues the kernels of a prepared launch (descriptors already on the device).
 // marks (optional, 4 timing events): recorded before the first kernel and after each
 // one; kinds[i] receives the gnm_kernel_kind of kernel i.
+// fresh: the windows start in this launch (their rate statistics are cleared first).
 gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, size_t n_win,
                             const uint32_t* slots, bool finalize, WinDesc* d_wins, uint32_t* d_done,
                             uint32_t* d_partials, uint32_t* d_keys, unsigned char* d_part, cudaStream_t st,
-                            uint32_t* launches, cudaEvent_t* marks = nullptr, int32_t* kinds = nullptr);
+                            uint32_t* launches, cudaEvent_t* marks = nullptr, int32_t* kinds = nullptr,
+                            bool fresh = true);
 constexpr int kMaxPlanKernels = 6;  // keys, count, scan, scatter, aggregate, finalise
 // Next launch-scratch entry of the ring (waits for its previous use).
 gnm_status acquire_ring(gnm_ctx* c, uint32_t n_win, LaunchBuf** out);
@@ -178,6 +185,8 @@ void set_slots_done(gnm_ctx* c, const uint32_t* slots, size_t n, cudaEvent_t ev,
 void unpin_slot(gnm_ctx* c, uint32_t s);
 // Grows every launch-ring entry's scratch for single-window launches of up to n records.
 gnm_status reserve_launch_scratch(gnm_ctx* c, uint64_t n);
+// Clears the rate statistics of slots[0..n) on st (windows that start there).
+gnm_status clear_rate_stats(gnm_ctx* c, const uint32_t* slots, size_t n, cudaStream_t st);
 // Windows k = [offsets[k], offsets[k+1]) of rec on stream st. finalize: rates and flags at
 // the end; open_add: add to windows already open instead of starting them.
 gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets, const uint64_t* wids,

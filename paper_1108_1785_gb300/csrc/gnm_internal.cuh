@@ -10,6 +10,7 @@ namespace gnm {
 
 constexpr uint32_t kNoSite = GNM_NO_SITE;
 constexpr int kNStat = GNM_NSTAT;   // columns of a user-facing stats row
+constexpr uint32_t kRateBuckets = GNM_RATE_BUCKETS;  // 10 kb/s buckets, the last for >= 100 Mb/s
 constexpr int kAccCols = 5;         // accumulator row: flows<<32|e_flows, oct, pkts, e_oct, e_dur
 constexpr size_t kSmemRowBytes = 20;  // per-CTA shared-memory row: packed counts + 4 low words
 constexpr int kUnmatched = 4;       // classes appended after the 2*n_sites site rows
@@ -92,6 +93,9 @@ struct AggParams {
     // results
     uint64_t* acc;               // [slots][keys][kAccCols] accumulators (zeroed per window)
     uint64_t* stats;             // [slots][keys][kNStat] finalised sums
+    uint32_t* hist;              // [slots][2*n_sites][kRateBuckets] rate histograms, or null
+    unsigned long long* rmin;    // [slots][2*n_sites] least rate (bits of a double >= 0)
+    unsigned long long* rmax;    // [slots][2*n_sites] greatest rate
     double* rate;                // [slots][2*n_sites]
     uint8_t* flag;               // [slots][2*n_sites]
     uint32_t keys;               // 2*n_sites + 4
@@ -180,6 +184,9 @@ size_t aggregate_smem_bytes(int lookup, int table, uint32_t n_ranges, uint32_t k
 cudaError_t launch_finalize(const AggParams& p, uint32_t slot, cudaStream_t st);
 // Finalises every window of a launch from its partial-sum blocks (grid over windows x keys).
 cudaError_t launch_finalize_windows(const AggParams& p, cudaStream_t st);
+// Lower-median bucket and eligible-flow count of every site key of one slot's histograms.
+cudaError_t launch_rate_median(const uint32_t* hist, uint32_t n_keys, uint32_t* med, uint32_t* count,
+                               cudaStream_t st);
 cudaError_t launch_flag_compact(const double* rate, const uint64_t* stats, uint32_t n_site_keys,
                                 double thr, uint32_t min_flows, uint32_t* out_keys,
                                 uint32_t* out_count, cudaStream_t st);

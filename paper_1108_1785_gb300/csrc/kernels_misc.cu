@@ -65,6 +65,47 @@ __global__ void __launch_bounds__(kFinKeys) k_finalize_windows(const __grid_cons
                              p.partials ? wd.n_parts : 0u, blockIdx.y);
 }
 
+// One warp per key: the key's eligible flows (the histogram's total) and the bucket where
+// the running count first reaches ceil(n/2) -- the bucket of the lower median.
+constexpr uint32_t kMedWarps = 8;
+
+__global__ void __launch_bounds__(kMedWarps * 32) k_rate_median(const uint32_t* __restrict__ hist, uint32_t n_keys,
+                                                                uint32_t* __restrict__ med,
+                                                                uint32_t* __restrict__ count) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t k = blockIdx.x * kMedWarps + (threadIdx.x >> 5);
+    if (k >= n_keys) return;  // whole warps leave together
+    const uint32_t* h = hist + (size_t)k * kRateBuckets;
+    uint32_t total = 0;
+    for (uint32_t b = lane; b < kRateBuckets; b += 32u) total += __ldg(h + b);
+    total = __reduce_add_sync(0xFFFFFFFFu, total);
+    uint32_t m = GNM_NO_MEDIAN;
+    if (total) {
+        const uint32_t want = (uint32_t)(((uint64_t)total + 1u) / 2u);
+        uint32_t base = 0;  // flows in the buckets before this round's 32
+        for (uint32_t b0 = 0; b0 < kRateBuckets; b0 += 32u) {
+            const uint32_t b = b0 + lane;
+            const uint32_t v = b < kRateBuckets ? __ldg(h + b) : 0u;
+            uint32_t incl = v;  // inclusive scan over the warp
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+                if ((int)lane >= d) incl += y;
+            }
+            const unsigned hit = __ballot_sync(0xFFFFFFFFu, base + incl >= want);
+            if (hit) {
+                m = b0 + (uint32_t)(__ffs(hit) - 1);
+                break;
+            }
+            base += __shfl_sync(0xFFFFFFFFu, incl, 31);
+        }
+    }
+    if (lane == 0) {
+        med[k] = m;
+        count[k] = total;
+    }
+}
+
 // Keys (site*2+dir) whose eligible flows reach min_flows and whose rate is strictly
 // below thr (Sec. III.B.1; Sec. IV.B "less than"); order is restored on the host.
 __global__ void k_flag_compact(const double* __restrict__ rate, const uint64_t* __restrict__ stats,
@@ -156,6 +197,14 @@ cudaError_t launch_finalize_windows(const AggParams& p, cudaStream_t st) {
     const uint32_t cap = std::max<uint32_t>(64u, 2048u / p.n_wins);
     (void)cudaGetLastError();
     k_finalize_windows<<<dim3(std::min(bx, cap), p.n_wins), kFinKeys, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rate_median(const uint32_t* hist, uint32_t n_keys, uint32_t* med, uint32_t* count,
+                               cudaStream_t st) {
+    if (n_keys == 0) return cudaSuccess;
+    (void)cudaGetLastError();
+    k_rate_median<<<(n_keys + kMedWarps - 1) / kMedWarps, kMedWarps * 32, 0, st>>>(hist, n_keys, med, count);
     return cudaGetLastError();
 }
 

@@ -26,6 +26,8 @@ TABLE_AUTO, TABLE_DIRECT, TABLE_HASH, TABLE_GLOBAL, TABLE_PARTITION = 0, 1, 2, 3
 SPLIT_AUTO, SPLIT_FUSED, SPLIT_TWO_KERNELS = 0, 1, 2
 ROOT_LINEAR, ROOT_MLP = 0, 1
 HOST_AUTO, HOST_STAGE, HOST_IN_PLACE = 0, 1, 2
+RATE_BUCKETS = 10001
+NO_MEDIAN = 0xFFFFFFFF
 KERNEL_TIMES = 1  # GNM_PLAN_KERNEL_TIMES
 KERNEL_NAMES = {0: "k_keys", 1: "k_aggregate", 2: "k_finalize_windows", 3: "k_part_count", 4: "k_part_scan",
                 5: "k_part_scatter"}
@@ -48,7 +50,7 @@ class Config(C.Structure):
                 ("window_slots", C.c_uint32), ("threshold_bps", C.c_double), ("block_threads", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("unroll", C.c_int32), ("table_mode", C.c_int32),
                 ("hash_slots", C.c_uint32), ("radix_bits", C.c_uint32), ("split", C.c_int32),
-                ("key_directory", C.c_int32), ("host_records", C.c_int32)]
+                ("key_directory", C.c_int32), ("host_records", C.c_int32), ("rate_stats", C.c_int32)]
 
 
 class RecordsC(C.Structure):
@@ -153,6 +155,7 @@ def lib():
             "gnm_plan_destroy": (None, [P]),
             "gnm_autotune": (st, [P, C.POINTER(RecordsC), P, P, S, C.POINTER(TuneReport)]),
             "gnm_last_launch_count": (U32, [P]),
+            "gnm_window_rate_stats": (st, [P, U64, P, P, P, P]),
             "gnm_stream_config_default": (None, [C.POINTER(StreamConfig)]),
             "gnm_stream_open": (st, [P, C.POINTER(StreamConfig), C.POINTER(P)]),
             "gnm_stream_submit": (st, [P, C.POINTER(RecordsC), U64, C.c_int]),
@@ -366,6 +369,17 @@ class Context:
         ids = np.ascontiguousarray(window_ids, np.uint64)
         self._c(lib().gnm_windows_results(self.h, _ptr(ids), ids.size, _ptr(stats), _ptr(unmatched), _ptr(rate),
                                           _ptr(flag)))
+
+    def rate_stats(self, window_id: int, hist: bool = False):
+        """(rmin[2S], rmax[2S], median_bucket[2S], hist[2S, 10001] or None) of a finalised
+        window of a context made with rate_stats=1."""
+        nk = 2 * self.n_sites
+        rmin = np.empty(nk, np.float64)
+        rmax = np.empty(nk, np.float64)
+        med = np.empty(nk, np.uint32)
+        h = np.empty((nk, RATE_BUCKETS), np.uint32) if hist else None
+        self._c(lib().gnm_window_rate_stats(self.h, window_id, _ptr(rmin), _ptr(rmax), _ptr(med), _ptr(h)))
+        return rmin, rmax, med, h
 
     def device_results(self, window_id: int):
         """Raw device addresses (stats, rate, flag) of a window's dense results."""

@@ -1,0 +1,75 @@
+"""Per-flow rate statistics (Sec. III.B.2.1: minimum, maximum, and the median from a
+histogram of 10 kb/s buckets) against the oracle: histograms and median buckets bit-exact,
+minimum and maximum rates bit-exact (the same FP64 operations in the same order)."""
+import numpy as np
+import pytest
+
+import flowgen as fg
+import oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gnm():
+    from paper_1108_1785_gb300 import build, gnm as g
+    build.build()
+    return g
+
+
+def _expect(reg, rec, lpm=None):
+    lpm = lpm or oracle.LPM(reg.prefix, reg.plen, reg.site)
+    return oracle.rate_stats(lpm, reg.local_prefix, reg.local_len, reg.n_sites, rec)
+
+
+def _check(got, want):
+    rmin, rmax, med, hist = got
+    h, lo, hi, m = want
+    np.testing.assert_array_equal(hist, h)
+    np.testing.assert_array_equal(med, m)
+    np.testing.assert_array_equal(rmin, lo)  # NaN where there is no eligible flow, on both sides
+    np.testing.assert_array_equal(rmax, hi)
+
+
+@pytest.mark.parametrize("which,cfg", [("c1", {}),                                   # fused, direct table
+                                       ("c2", {}),                                   # split, direct table
+                                       ("c2", {"table_mode": "PARTITION"}),          # regrouped records
+                                       ("c2", {"table_mode": "HASH", "split": "FUSED"})])
+def test_rate_stats_match_oracle(gnm, which, cfg):
+    reg = fg.registry_c1() if which == "c1" else fg.registry_c2()
+    rec = fg.make_records(reg, 600_001, seed=17)
+    off = [0, 250_000, 600_001]
+    kw = {k: getattr(gnm, {"table_mode": "TABLE_", "split": "SPLIT_"}[k] + v) for k, v in cfg.items()}
+    ctx = gnm.Context(window_slots=4, rate_stats=1, **kw)
+    ctx.load(reg)
+    plan = ctx.plan(gnm.Records.to_device(rec), off, [3, 4])
+    for _ in range(2):  # replays clear the statistics first
+        plan.launch()
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    for w, (a, b) in zip([3, 4], zip(off[:-1], off[1:])):
+        _check(ctx.rate_stats(w, hist=True), _expect(reg, {k: v[a:b] for k, v in rec.items()}, lpm))
+    plan.close()
+    ctx.close()
+
+
+def test_rate_stats_open_add_close_and_refusal(gnm):
+    reg = fg.registry_c1()
+    rec = fg.window_records_c1(reg, n=90_000)
+    ctx = gnm.Context(window_slots=4, rate_stats=1)
+    ctx.load(reg)
+    d = gnm.Records.to_device(rec)
+    ctx.open(9)
+    for a, b in ((0, 1), (1, 40_000), (40_000, 90_000)):
+        ctx.add(gnm.Records({k: v[a:b] for k, v in d.fields.items()}), 9)
+    ctx.close_window(9)
+    _check(ctx.rate_stats(9, hist=True), _expect(reg, rec))
+    ctx.process(d, 9)  # the same id again: the statistics start over
+    _check(ctx.rate_stats(9, hist=True), _expect(reg, rec))
+    ctx.close()
+    off = gnm.Context(window_slots=2)
+    off.load(reg)
+    off.process(d, 1)
+    with pytest.raises(gnm.GnmError, match="STATE"):
+        off.rate_stats(1)
+    off.close()
