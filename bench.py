@@ -167,11 +167,28 @@ def window_c1(gnm, torch, local, reps=1000):
     cold_us = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev])) * 1e3
     plan.close()
     ctx.close()
+    # the same window with per-flow rate statistics (histograms, min, max) kept as well
+    ctx = gnm.Context(device=local, window_slots=4, rate_stats=1)
+    ctx.load(reg)
+    plan = ctx.plan(dev, [0, n], [1])
+    for _ in range(20):
+        plan.launch(stream)
+    a.record(stream)
+    for _ in range(reps):
+        plan.launch(stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    rs_us = a.elapsed_time(b) * 1e3 / reps
+    plan.close()
+    ctx.close()
     return {"workload": f"one window of {n:,} records; {reg.n_sites} sites / {reg.n:,} prefixes (registry in "
                         "shared memory); CUDA-graph launch",
             "warm_us": warm_us, "warm_records_per_s": n / (warm_us * 1e-6), "warm_reps": reps,
             "cold_us": cold_us, "cold_records_per_s": n / (cold_us * 1e-6), "cold_reps": len(ev),
-            "cold": "a 258 MB write (2x L2) before every timed launch"}
+            "cold": "a 258 MB write (2x L2) before every timed launch",
+            "warm_us_with_rate_stats": rs_us,
+            "rate_stats": "per-flow 10 kb/s histograms (1,000 keys x 10,001 buckets, cleared every launch), "
+                          "least and greatest rate"}
 
 
 def batched_c4(gnm, torch, local, steps, warmup):

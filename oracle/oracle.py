@@ -190,6 +190,21 @@ def rate_stats(lpm: LPM, local_prefix, local_len, n_sites: int, rec: Dict[str, n
     return hist, rmin, rmax, med
 
 
+def warnings(median_buckets, below_bucket: int = 100, consecutive: int = 2):
+    """Sec. III.B.1 / Sec. IV.B: a warning for a (site, dir) key when its median transfer
+    rate was below a standard (1 Mb/s: median bucket < 100) in `consecutive` consecutive
+    windows. median_buckets: one array of lower-median buckets per window, in time order
+    (NO_MEDIAN, no eligible flow, is not below). Returns one boolean array per window."""
+    streak = None
+    out = []
+    for m in median_buckets:
+        m = np.asarray(m, np.uint32)
+        below = (m != NO_MEDIAN) & (m < below_bucket)
+        streak = np.where(below, (streak if streak is not None else 0) + 1, 0)
+        out.append(streak >= consecutive)
+    return out
+
+
 def full_window(lpm: LPM, reg, rec, threshold: float = 1e8, min_flows: int = 1, **kw):
     """stats, unmatched, rate and flag of one window (the whole per-window definition)."""
     st, un = window(lpm, reg.local_prefix, reg.local_len, reg.n_sites, rec, **kw)

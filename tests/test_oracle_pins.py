@@ -372,6 +372,23 @@ def test_rate_stats_against_sorted_rates():
         np.testing.assert_array_equal(hist[k], np.bincount(bucket[sel], minlength=oracle.N_BUCKETS))
 
 
+def test_warnings_hand_sequence():
+    """Four keys over five windows (median buckets; 99 is below 1 Mb/s, 100 is not):
+    key 0 below in windows 1-3, key 1 alternates, key 2 below then without flows then
+    below, key 3 below in every window."""
+    N = oracle.NO_MEDIAN
+    seq = [[100, 5, 99, 0], [99, 100, 99, 0], [50, 7, N, 0], [0, 100, 99, 0], [100, 8, 99, 0]]
+    got = [w.tolist() for w in oracle.warnings(seq)]
+    assert got == [[False, False, False, False],
+                   [False, False, True, True],
+                   [True, False, False, True],
+                   [True, False, False, True],
+                   [False, False, True, True]]
+    # three windows in a row
+    got3 = [w.tolist() for w in oracle.warnings(seq, consecutive=3)]
+    assert got3[2] == [False, False, False, True] and got3[3] == [True, False, False, True]
+
+
 def test_lstsq_line_equals_polyfit():
     rng = np.random.default_rng(0)
     x = rng.random(5000) * 1e6
