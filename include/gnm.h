@@ -255,6 +255,19 @@ gnm_status gnm_flag_suboptimal(gnm_ctx *ctx, uint64_t window_id, double threshol
 gnm_status gnm_window_rate_stats(gnm_ctx *ctx, uint64_t window_id, double *rmin, double *rmax,
                                  uint32_t *median_bucket, uint32_t *hist);
 
+/* Median-rate warnings across windows (Sec. III.B.1, Sec. IV.B: a warning for a site
+ * whose median transfer rate stays below a standard, 1 Mb/s, for two consecutive periods).
+ * The context keeps a run length per (site, dir) key on the device. Each call takes the
+ * next window in time order (finalised, rate_stats = 1): a key whose lower-median bucket
+ * is below `below_bucket` (100 for 1 Mb/s) extends its run, any other key -- including one
+ * without eligible flows -- restarts at zero. Keys whose run has reached `consecutive`
+ * windows are written, ascending, to keys_out (key = site*2+dir; a site is warned about when
+ * either direction is); *n_out gets their number (GNM_E_CAPACITY when cap is smaller, the
+ * runs being updated all the same). gnm_warnings_reset sets every run to zero. */
+gnm_status gnm_warnings_update(gnm_ctx *ctx, uint64_t window_id, uint32_t below_bucket, uint32_t consecutive,
+                               uint32_t *keys_out, size_t cap, size_t *n_out);
+gnm_status gnm_warnings_reset(gnm_ctx *ctx);
+
 /* Dense copies of a window's results to host arrays (each may be NULL):
  * stats[(2*n_sites) x GNM_NSTAT] (row site*2+dir), unmatched[12], rate[2*n_sites],
  * flag[2*n_sites] (against the context threshold). Synchronises with the window. */

@@ -126,6 +126,8 @@ void release_slots(gnm_ctx* c) {
     free_dev(c->d_rmax);
     free_dev(c->d_med);
     free_dev(c->d_mcnt);
+    free_dev(c->d_warn_run);
+    c->d_warn_run = nullptr;
     c->d_hist = nullptr;
     c->d_rmin = nullptr;
     c->d_rmax = nullptr;
@@ -1034,6 +1036,8 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
         GNM_CU(cudaMalloc(&c->d_rmax, slots * nk * 8));
         GNM_CU(cudaMalloc(&c->d_med, nk * 4));
         GNM_CU(cudaMalloc(&c->d_mcnt, nk * 4));
+        GNM_CU(cudaMalloc(&c->d_warn_run, nk * 4));
+        GNM_CU(cudaMemset(c->d_warn_run, 0, nk * 4));
     }
     c->slots.resize(slots);
     c->have_registry = true;
@@ -1144,6 +1148,42 @@ gnm_status gnm_window_rate_stats(gnm_ctx* c, uint64_t wid, double* rmin, double*
             rmax[k] = cnt[k] ? v : nan;
         }
     }
+    return GNM_OK;
+}
+
+gnm_status gnm_warnings_update(gnm_ctx* c, uint64_t wid, uint32_t below_bucket, uint32_t consecutive,
+                               uint32_t* keys_out, size_t cap, size_t* n_out) {
+    if (!c || !n_out) return fail(GNM_E_INVAL, "NULL argument");
+    if (!c->d_hist) return fail(GNM_E_STATE, "the context keeps no rate statistics (rate_stats = 0)");
+    if (consecutive == 0) return fail(GNM_E_INVAL, "consecutive must be at least 1");
+    GNM_CU(cudaSetDevice(c->device));
+    uint32_t s;
+    GNM_TRY(find_window(c, wid, &s));
+    if (!c->slots[s].finalized) return fail(GNM_E_STATE, "window is open (not finalised)");
+    GNM_TRY(wait_slot_on_stream(c, s, c->aux));
+    const uint32_t nk = 2u * c->n_sites;
+    GNM_CU(launch_rate_median(c->d_hist + (size_t)s * nk * kRateBuckets, nk, c->d_med, c->d_mcnt, c->aux));
+    GNM_CU(launch_warn_runs(c->d_med, nk, below_bucket, consecutive, c->d_warn_run, c->d_flag_keys, c->d_flag_count,
+                            c->aux));
+    uint32_t cnt = 0;
+    GNM_CU(cudaMemcpyAsync(&cnt, c->d_flag_count, 4, cudaMemcpyDeviceToHost, c->aux));
+    GNM_CU(cudaStreamSynchronize(c->aux));
+    std::vector<uint32_t> keys(cnt);
+    if (cnt) GNM_CU(cudaMemcpyAsync(keys.data(), c->d_flag_keys, cnt * 4, cudaMemcpyDeviceToHost, c->aux));
+    GNM_CU(cudaStreamSynchronize(c->aux));
+    *n_out = cnt;
+    if (cap < cnt) return fail(GNM_E_CAPACITY, "cap smaller than the number of warned keys");
+    std::sort(keys.begin(), keys.end());
+    if (keys_out && cnt) std::memcpy(keys_out, keys.data(), cnt * 4);
+    return GNM_OK;
+}
+
+gnm_status gnm_warnings_reset(gnm_ctx* c) {
+    if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
+    if (!c->d_warn_run) return fail(GNM_E_STATE, "the context keeps no rate statistics (rate_stats = 0)");
+    GNM_CU(cudaSetDevice(c->device));
+    GNM_CU(cudaMemsetAsync(c->d_warn_run, 0, (size_t)2 * c->n_sites * 4, c->aux));
+    GNM_CU(cudaStreamSynchronize(c->aux));
     return GNM_OK;
 }
 

@@ -114,6 +114,7 @@ struct gnm_ctx {
     unsigned long long* d_rmax = nullptr; // [slots][2S]
     uint32_t* d_med = nullptr;            // [2S] readout scratch: median buckets
     uint32_t* d_mcnt = nullptr;           // [2S] readout scratch: eligible flows
+    uint32_t* d_warn_run = nullptr;       // [2S] windows in a row with a below-standard median
     std::vector<gnm::Slot> slots;
     std::unordered_map<uint64_t, uint32_t> slot_of;
     uint64_t age = 0;

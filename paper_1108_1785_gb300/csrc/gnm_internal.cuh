@@ -184,6 +184,10 @@ size_t aggregate_smem_bytes(int lookup, int table, uint32_t n_ranges, uint32_t k
 cudaError_t launch_finalize(const AggParams& p, uint32_t slot, cudaStream_t st);
 // Finalises every window of a launch from its partial-sum blocks (grid over windows x keys).
 cudaError_t launch_finalize_windows(const AggParams& p, cudaStream_t st);
+// Runs of below-standard medians: run[k] = med[k] < below ? run[k] + 1 : 0; keys whose run
+// reaches `consecutive` are appended to out (count via *n).
+cudaError_t launch_warn_runs(const uint32_t* med, uint32_t n_keys, uint32_t below, uint32_t consecutive,
+                             uint32_t* run, uint32_t* out, uint32_t* n, cudaStream_t st);
 // Lower-median bucket and eligible-flow count of every site key of one slot's histograms.
 cudaError_t launch_rate_median(const uint32_t* hist, uint32_t n_keys, uint32_t* med, uint32_t* count,
                                cudaStream_t st);

@@ -106,6 +106,18 @@ __global__ void __launch_bounds__(kMedWarps * 32) k_rate_median(const uint32_t* 
     }
 }
 
+__global__ void k_warn_runs(const uint32_t* __restrict__ med, uint32_t n_keys, uint32_t below,
+                            uint32_t consecutive, uint32_t* __restrict__ run, uint32_t* __restrict__ out,
+                            uint32_t* __restrict__ n) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_keys; k += stride) {
+        const uint32_t m = med[k];
+        const uint32_t r = (m != GNM_NO_MEDIAN && m < below) ? run[k] + 1u : 0u;
+        run[k] = r;
+        if (r >= consecutive) out[atomicAdd(n, 1u)] = k;
+    }
+}
+
 // Keys (site*2+dir) whose eligible flows reach min_flows and whose rate is strictly
 // below thr (Sec. III.B.1; Sec. IV.B "less than"); order is restored on the host.
 __global__ void k_flag_compact(const double* __restrict__ rate, const uint64_t* __restrict__ stats,
@@ -197,6 +209,16 @@ cudaError_t launch_finalize_windows(const AggParams& p, cudaStream_t st) {
     const uint32_t cap = std::max<uint32_t>(64u, 2048u / p.n_wins);
     (void)cudaGetLastError();
     k_finalize_windows<<<dim3(std::min(bx, cap), p.n_wins), kFinKeys, 0, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warn_runs(const uint32_t* med, uint32_t n_keys, uint32_t below, uint32_t consecutive,
+                             uint32_t* run, uint32_t* out, uint32_t* n, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(n, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess || n_keys == 0) return e;
+    const uint32_t blocks = std::min<uint32_t>((n_keys + 255) / 256, 4096);
+    (void)cudaGetLastError();
+    k_warn_runs<<<blocks, 256, 0, st>>>(med, n_keys, below, consecutive, run, out, n);
     return cudaGetLastError();
 }
 

@@ -156,6 +156,8 @@ def lib():
             "gnm_autotune": (st, [P, C.POINTER(RecordsC), P, P, S, C.POINTER(TuneReport)]),
             "gnm_last_launch_count": (U32, [P]),
             "gnm_window_rate_stats": (st, [P, U64, P, P, P, P]),
+            "gnm_warnings_update": (st, [P, U64, U32, U32, P, S, C.POINTER(S)]),
+            "gnm_warnings_reset": (st, [P]),
             "gnm_stream_config_default": (None, [C.POINTER(StreamConfig)]),
             "gnm_stream_open": (st, [P, C.POINTER(StreamConfig), C.POINTER(P)]),
             "gnm_stream_submit": (st, [P, C.POINTER(RecordsC), U64, C.c_int]),
@@ -380,6 +382,17 @@ class Context:
         h = np.empty((nk, RATE_BUCKETS), np.uint32) if hist else None
         self._c(lib().gnm_window_rate_stats(self.h, window_id, _ptr(rmin), _ptr(rmax), _ptr(med), _ptr(h)))
         return rmin, rmax, med, h
+
+    def warnings_update(self, window_id: int, below_bucket: int = 100, consecutive: int = 2) -> np.ndarray:
+        """Keys (site*2+dir) warned about after this window (the next one in time order)."""
+        out = np.empty(2 * self.n_sites, np.uint32)
+        n = C.c_size_t()
+        self._c(lib().gnm_warnings_update(self.h, window_id, below_bucket, consecutive, _ptr(out), out.size,
+                                          C.byref(n)))
+        return out[:n.value].copy()
+
+    def warnings_reset(self):
+        self._c(lib().gnm_warnings_reset(self.h))
 
     def device_results(self, window_id: int):
         """Raw device addresses (stats, rate, flag) of a window's dense results."""

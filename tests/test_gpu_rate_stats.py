@@ -73,3 +73,26 @@ def test_rate_stats_open_add_close_and_refusal(gnm):
     with pytest.raises(gnm.GnmError, match="STATE"):
         off.rate_stats(1)
     off.close()
+
+
+@pytest.mark.parametrize("consecutive", [1, 2, 3])
+def test_warnings_follow_oracle_over_windows(gnm, consecutive):
+    """Five windows in time order: after each, the keys whose median bucket stayed below 100
+    (1 Mb/s) for `consecutive` windows in a row equal the oracle's warnings; a reset starts
+    every run over."""
+    reg = fg.registry_c1()
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    wins = [fg.make_records(reg, 60_000, seed=100 + w, zipf_s=1.1) for w in range(5)]
+    meds = [_expect(reg, r, lpm)[3] for r in wins]
+    want = oracle.warnings(meds, below_bucket=100, consecutive=consecutive)
+    ctx = gnm.Context(window_slots=8, rate_stats=1)
+    ctx.load(reg)
+    for w, r in enumerate(wins):
+        ctx.process(gnm.Records.to_device(r), 50 + w)
+        got = ctx.warnings_update(50 + w, below_bucket=100, consecutive=consecutive)
+        np.testing.assert_array_equal(got, np.nonzero(want[w])[0])
+    assert any(x.any() for x in want)  # the workload does raise warnings
+    ctx.warnings_reset()
+    got = ctx.warnings_update(54, below_bucket=100, consecutive=consecutive)
+    np.testing.assert_array_equal(got, np.nonzero(oracle.warnings(meds[4:], consecutive=consecutive)[0])[0])
+    ctx.close()
