@@ -133,6 +133,49 @@ def learned_vs_plain(gnm, torch, local, steps, warmup, n_records=50_000_000,
                                        if "bsearch" in res and "rmi" in res else None)}
 
 
+def paper_lookup(gnm, torch, local, steps, warmup):
+    """The paper's GPU Site Catalog (every registered network expanded into /24 subnets in
+    a hash table) against this library's lookups, on the hour's workload shape with the
+    prefix lengths such a catalog can hold (/8-/24): same GPU, same records, each shape
+    autotuned, results bit-exact across the three."""
+    import flowgen as fg
+    reg = fg.registry_c2_24()
+    rec, off = fg.hour_records_c2(reg, seed=1)
+    n, n_win = int(off[-1]), len(off) - 1
+    dev = gnm.Records.to_device(rec)
+    ids = np.arange(n_win, dtype=np.uint64)
+    stream = torch.cuda.current_stream()
+    res, dense = {}, {}
+    for name, mode in (("hash24", gnm.LOOKUP_HASH24), ("bsearch", gnm.LOOKUP_BSEARCH), ("radix", gnm.LOOKUP_RADIX)):
+        ctx = gnm.Context(device=local, window_slots=n_win + 8, lookup_mode=mode)
+        ctx.load(reg)
+        ctx.autotune(dev, off, ids)
+        plan = ctx.plan(dev, off, ids, kernel_times=True)
+        for _ in range(warmup):
+            plan.launch(stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            plan.launch(stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        plan.launch(stream)
+        res[name] = {"records_per_s": n / (ms / 1e3), "ms": ms,
+                     "kernels_ms": {k: round(v, 4) for k, v in plan.kernel_times()}}
+        dense[name] = [ctx.dense(int(w)) for w in (0, 29, 59)]
+        plan.close()
+        ctx.close()
+    exact = all(np.array_equal(x, y, equal_nan=True) for k in dense for a_, b_ in zip(dense[k], dense["hash24"])
+                for x, y in zip(a_, b_))
+    return {"workload": f"hour: {n:,} records in {n_win} windows; {reg.n_sites:,} sites / {reg.n:,} prefixes "
+                        "/8-/24 (20% nested) -> a /24 subnet table of "
+                        f"{int((np.int64(1) << (24 - reg.plen.astype(np.int64))).sum()):,} subnets",
+            "bitexact_across_lookups": bool(exact), **res,
+            "hash24_vs_best": min(res["bsearch"]["ms"], res["radix"]["ms"]) / res["hash24"]["ms"]}
+
+
 def window_c1(gnm, torch, local, reps=1000):
     """One window of 100,000 records against the 500-site registry: per-window latency of
     the CUDA-graph launch with L2 warm (launches back to back) and cold (a 2x L2 write
@@ -482,7 +525,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the plain-vs-learned index comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the streaming-server replay")
-    ap.add_argument("--only", default="all", choices=["all", "learned", "serve", "batched", "window"],
+    ap.add_argument("--only", default="all", choices=["all", "learned", "serve", "batched", "window", "paper"],
                     help="run one leg alone (profiling): the learned-index comparison, the server replay "
                          "or the batched windows")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-window batched launch")
@@ -510,6 +553,8 @@ def main():
             leg = batched_c4(gnm, torch, local, args.steps, args.warmup)
         elif args.only == "window":
             leg = window_c1(gnm, torch, local)
+        elif args.only == "paper":
+            leg = paper_lookup(gnm, torch, local, args.steps, args.warmup)
         else:
             leg = serve_c5(gnm, torch, local, minutes=args.serve_minutes, speedup=args.serve_speedup)
         print(json.dumps({"leg": args.only, **leg}), flush=True)
@@ -673,6 +718,7 @@ def main():
                                                 tuple(args.learned_modes.split(",")))
     if world == 1 and not args.no_batched:
         out["window"] = window_c1(gnm, torch, local)
+        out["paper_lookup"] = paper_lookup(gnm, torch, local, args.steps, args.warmup)
         out["batched"] = batched_c4(gnm, torch, local, args.steps, args.warmup)
     if world == 1 and not args.no_serve:
         out["serving"] = serve_c5(gnm, torch, local, minutes=args.serve_minutes, speedup=args.serve_speedup)

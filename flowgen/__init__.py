@@ -120,7 +120,7 @@ def length_weights_peaked(lo: int, hi: int, peak: int, up: float = 0.6, down: fl
 
 def make_registry(n_sites: int, n_prefixes: int, len_weights: Dict[int, float],
                   nest_frac: float, seed: int, n_local: int = 2, local_len: int = 16,
-                  n_holes: int = 8, hole_len: int = 12) -> Registry:
+                  n_holes: int = 8, hole_len: int = 12, max_nested_len: int = 30) -> Registry:
     """Registry of ``n_prefixes`` prefixes for ``n_sites`` sites.
 
     ``1 - nest_frac`` of the prefixes are mutually disjoint; the rest are placed inside
@@ -158,11 +158,12 @@ def make_registry(n_sites: int, n_prefixes: int, len_weights: Dict[int, float],
     nest_l = np.zeros(0, np.int64)
     nest_site = np.zeros(0, np.int64)
     if n_nested:
-        parent_ok = np.nonzero(top_lens <= 29)[0]
+        L = max_nested_len
+        parent_ok = np.nonzero(top_lens <= L - 1)[0]
         par = parent_ok[rng.integers(0, parent_ok.size, size=n_nested)]
         pl = top_lens[par]
-        cl = pl + 1 + (rng.random(n_nested) * (30 - pl)).astype(np.int64)
-        cl = np.minimum(cl, 30)
+        cl = pl + 1 + (rng.random(n_nested) * (L - pl)).astype(np.int64)
+        cl = np.minimum(cl, L)
         nest_s = np.full(n_nested, -1, np.int64)
         todo = np.arange(n_nested)
         occ_cs = np.zeros(0, np.int64)
@@ -173,7 +174,7 @@ def make_registry(n_sites: int, n_prefixes: int, len_weights: Dict[int, float],
             if rnd % 10 == 9:  # a crowded parent: draw another parent and length
                 par[todo] = parent_ok[rng.integers(0, parent_ok.size, size=todo.size)]
                 pl[todo] = top_lens[par[todo]]
-                cl[todo] = np.minimum(pl[todo] + 1 + (rng.random(todo.size) * (30 - pl[todo])).astype(np.int64), 30)
+                cl[todo] = np.minimum(pl[todo] + 1 + (rng.random(todo.size) * (L - pl[todo])).astype(np.int64), L)
             size = _size(cl[todo])
             psize = _size(pl[todo])
             slot = (rng.random(todo.size) * (psize // size)).astype(np.int64)
@@ -282,6 +283,15 @@ def registry_c1(seed: int = 0) -> Registry:
 def registry_c2(seed: int = 1) -> Registry:
     """5,000 sites, 40,000 prefixes /8-/30, 20% nested inside another site's prefix."""
     return make_registry(5000, 40000, C2_LEN, 0.2, seed)
+
+
+C2_24_LEN = length_weights_peaked(8, 24, peak=24)  # /8../24: what a /24 subnet catalog can hold
+
+
+def registry_c2_24(seed: int = 1) -> Registry:
+    """5,000 sites, 40,000 prefixes /8-/24, 20% nested: the hour's registry shape limited to
+    the prefix lengths a /24 subnet hash table can expand."""
+    return make_registry(5000, 40000, C2_24_LEN, 0.2, seed, max_nested_len=24)
 
 
 def registry_c3(seed: int = 2, n_prefixes: int = 1_000_000, n_sites: int = 100_000) -> Registry:

@@ -59,9 +59,14 @@ typedef enum {
  * RMI: the learned index (gnm_rmi_train). RADIX: a directory indexed by the top
  * `radix_bits` address bits -- the paper's direct-indexed site catalog (Sec. III.B.2.1
  * hashes /24 subnets) generalised to any prefix length -- gives each bucket's range
- * interval, and a binary search inside the bucket finishes. AUTO: RMI when trained, else
- * BSEARCH when the registry fits shared memory, else RADIX. */
-enum { GNM_LOOKUP_AUTO = 0, GNM_LOOKUP_BSEARCH = 1, GNM_LOOKUP_RMI = 2, GNM_LOOKUP_RADIX = 3 };
+ * interval, and a binary search inside the bucket finishes. HASH24: the paper's own GPU
+ * Site Catalog (Sec. III.B.2.1): every registered network expanded into its /24 subnets
+ * in a hash table (the longest registered prefix wins each subnet), one probe sequence per
+ * lookup; only for registries whose prefixes are all /24 or shorter (GNM_E_INVAL
+ * otherwise), and gnm_lookup gives sites but no range positions with it. AUTO: RMI when
+ * trained, else BSEARCH when the registry fits shared memory, else RADIX. */
+enum { GNM_LOOKUP_AUTO = 0, GNM_LOOKUP_BSEARCH = 1, GNM_LOOKUP_RMI = 2, GNM_LOOKUP_RADIX = 3,
+       GNM_LOOKUP_HASH24 = 4 };
 /* Where the flattened registry is searched: wholly in shared memory (SMEM), wholly in L2
  * (L2), or STAGED: the first start of every block of 16 ranges in shared memory, the
  * 64-byte blocks of 16 starts and the sites in L2 (two L2 accesses per lookup). */

@@ -175,6 +175,41 @@ __device__ __forceinline__ void radix_block(const uint32_t* dir, uint32_t bits, 
     }
 }
 
+// The paper's lookup (Sec. III.B.2.1): the site of x's /24 subnet from the hash table of
+// the registered networks' /24 subnets (kNoSite when absent). Linear probing; the table is
+// at most half full, so every probe sequence ends at the key or at an empty slot.
+template <int R>
+__device__ __forceinline__ void hash24_sites(const uint2* __restrict__ t, uint32_t mask, const uint32_t (&x)[R],
+                                             uint32_t (&site)[R]) {
+    uint32_t h[R];
+    bool open[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        h[j] = hash24(x[j] >> 8) & mask;
+        open[j] = true;
+        site[j] = kNoSite;
+    }
+    bool more = true;
+    while (more) {
+        more = false;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (open[j]) {
+                const uint2 e = __ldg(t + h[j]);
+                if (e.x == (x[j] >> 8) + 1u) {
+                    site[j] = e.y;
+                    open[j] = false;
+                } else if (e.x == 0u) {
+                    open[j] = false;
+                } else {
+                    h[j] = (h[j] + 1u) & mask;
+                    more = true;
+                }
+            }
+        }
+    }
+}
+
 // floor(v) clamped to [0, n-1] (n - 1 < 2^24, so the comparison is exact); NaN -> 0.
 __device__ __forceinline__ uint32_t clamp_floor(float v, uint32_t n) {
     if (!(v >= 0.f)) return 0u;
@@ -683,6 +718,8 @@ __device__ __forceinline__ void lookup_sites(const AggParams& p, const Smem& sm,
         radix_block<2, R>(sm.s_starts, p.radix_bits, sm.s_site, p.pairs, x, site);
     } else if (LOOKUP == kLookupRmi) {
         rmi_sites<R>(p.rmi, sm.ra, sm.rb, sm.rx0, sm.reps, p.pairs, p.n_ranges, valid, x, site, p.violations);
+    } else if (LOOKUP == kLookupHash24) {
+        hash24_sites<R>(p.h24, p.h24_mask, x, site);
     }
 }
 

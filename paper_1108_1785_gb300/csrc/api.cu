@@ -22,6 +22,8 @@ std::string flatten_registry(const uint32_t* prefix, const uint8_t* len, const u
                              size_t n, uint32_t n_sites, std::vector<uint32_t>* starts,
                              std::vector<uint32_t>* sites);
 bool local_overlaps(uint32_t lp, uint8_t ll, const uint32_t* prefix, const uint8_t* len, size_t n);
+bool build_hash24(const uint32_t* prefix, const uint8_t* len, const uint32_t* site, size_t n,
+                  std::vector<uint32_t>* table, uint32_t* mask);
 
 constexpr uint32_t kRingSize = 32;
 constexpr size_t kRegistrySmemMax = 96 * 1024;   // bytes of ranges kept in shared memory
@@ -231,7 +233,10 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s, size_t n_win) {
         return fail(GNM_E_STATE, "lookup mode RMI requested but no learned index is trained");
     size_t lookup_bytes = 0;
     s->radix_bits = 0;
-    if (mode == GNM_LOOKUP_RMI) {
+    if (mode == GNM_LOOKUP_HASH24) {
+        if (!c->d_h24) return fail(GNM_E_INVAL, "lookup mode HASH24: the registry has prefixes longer than /24");
+        s->lookup = kLookupHash24;
+    } else if (mode == GNM_LOOKUP_RMI) {
         s->lookup = kLookupRmi;
         lookup_bytes = (size_t)c->rmi.n_leaves * 16;
     } else if (mode == GNM_LOOKUP_RADIX) {
@@ -427,6 +432,8 @@ gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p) {
     p->n_blk4 = c->n_blk4;
     p->sample2 = c->d_sample2;
     p->n_blk2 = c->n_blk2;
+    p->h24 = c->d_h24;
+    p->h24_mask = c->h24_mask;
     p->n_blocks = c->n_blocks;
     p->n_ranges = (uint32_t)c->h_starts.size();
     p->n_sites = c->n_sites;
@@ -902,6 +909,7 @@ void gnm_destroy(gnm_ctx* c) {
     free_dev(c->d_dir16);
     free_dev(c->d_sample4);
     free_dev(c->d_sample2);
+    free_dev(c->d_h24);
     free_dev(c->d_violations);
     free_dev(c->d_flag_count);
     free_dev(c->d_rmi_a);
@@ -945,11 +953,14 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     free_dev(c->d_dir16);
     free_dev(c->d_sample4);
     free_dev(c->d_sample2);
+    free_dev(c->d_h24);
     c->d_dir16 = nullptr;
     c->d_sample4 = nullptr;
     c->n_blk4 = 0;
     c->d_sample2 = nullptr;
     c->n_blk2 = 0;
+    c->d_h24 = nullptr;
+    c->h24_mask = 0;
     c->d_starts = nullptr;
     c->d_site = nullptr;
     c->d_pairs = nullptr;
@@ -996,6 +1007,15 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     }
     GNM_CU(cudaMalloc(&c->d_dir16, dir.size() * 4));
     GNM_CU(cudaMemcpy(c->d_dir16, dir.data(), dir.size() * 4, cudaMemcpyHostToDevice));
+    {  // the paper's /24 subnet hash table, for registries of prefixes up to /24
+        std::vector<uint32_t> t;
+        uint32_t mask = 0;
+        if (build_hash24(prefix, len, site_id, n, &t, &mask)) {
+            GNM_CU(cudaMalloc(&c->d_h24, t.size() * 4));
+            GNM_CU(cudaMemcpy(c->d_h24, t.data(), t.size() * 4, cudaMemcpyHostToDevice));
+            c->h24_mask = mask;
+        }
+    }
     for (size_t br : {(size_t)2, (size_t)4}) {  // key kernel: first start of every 2- and 4-range block
         const size_t nb = (nr + br - 1) / br;
         std::vector<uint32_t> sb(nb);
@@ -1056,8 +1076,10 @@ gnm_status gnm_registry_info_get(gnm_ctx* c, gnm_registry_info* out) {
     if (choose_shape(c, 1u << 20, &sh) == GNM_OK) {
         out->placement = sh.lookup == kLookupSmem ? GNM_PLACE_SMEM
                          : sh.lookup == kLookupStaged ? GNM_PLACE_STAGED : GNM_PLACE_L2;
-        out->lookup_mode = sh.lookup == kLookupRmi ? GNM_LOOKUP_RMI
-                           : sh.lookup == kLookupRadix ? GNM_LOOKUP_RADIX : GNM_LOOKUP_BSEARCH;
+        out->lookup_mode = sh.lookup == kLookupRmi      ? GNM_LOOKUP_RMI
+                           : sh.lookup == kLookupRadix  ? GNM_LOOKUP_RADIX
+                           : sh.lookup == kLookupHash24 ? GNM_LOOKUP_HASH24
+                                                        : GNM_LOOKUP_BSEARCH;
         out->privatized = sh.table != kTableGlobal;
     }
     out->rmi_ready = c->rmi_ready;
@@ -1344,6 +1366,8 @@ gnm_status gnm_lookup(gnm_ctx* c, const uint32_t* addr, uint64_t n, uint32_t* si
     GNM_CU(cudaSetDevice(c->device));
     LaunchShape sh;
     GNM_TRY(choose_shape(c, n ? n : 1, &sh));
+    if (sh.lookup == kLookupHash24 && pos_out)
+        return fail(GNM_E_INVAL, "lookup mode HASH24 gives sites, not range positions (pos_out must be NULL)");
     AggParams p;
     gnm_records none{};
     GNM_TRY(build_params(c, &none, &p));

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "gnm.h"
+#include "hash24.hpp"
 
 namespace gnm {
 
@@ -77,6 +78,8 @@ struct AggParams {
     uint32_t n_blk4;
     const uint32_t* sample2;     // key kernel: first start of every 2-range block of pairs
     uint32_t n_blk2;
+    const uint2* h24;            // /24 subnet hash table: (subnet + 1, site), 0 = empty
+    uint32_t h24_mask;           // table slots - 1
     uint32_t n_blocks;
     uint32_t n_ranges;
     uint32_t n_sites;
@@ -118,8 +121,10 @@ struct AggParams {
 // kLookupRadixBlk / kLookupRadixBlk2 (key kernel only): a directory of blocks of 4 (2)
 // ranges and the blocks' first starts in shared memory; one 32-byte (16-byte) load of the
 // block's (start, site) pairs ends the lookup.
+// kLookupHash24: the paper's /24 subnet hash table (registries of prefixes up to /24).
 enum { kLookupL2 = 0, kLookupSmem = 1, kLookupRmi = 2, kLookupStaged = 3, kLookupRadix = 4, kLookupKeys = 5,
-       kLookupRadixBlk = 6, kLookupRadixBlk2 = 7 };
+       kLookupRadixBlk = 6, kLookupRadixBlk2 = 7, kLookupHash24 = 8 };
+
 
 // Largest block of the key kernel for a lookup and records-per-thread unroll: two groups
 // of lookups per thread fit 64 registers (1024 threads) only for the lighter lookups.

@@ -17,12 +17,15 @@ cudaError_t launch_keys_staged(const AggParams& p, const LaunchShape& s, uint32_
 cudaError_t launch_keys_radix(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
 cudaError_t launch_keys_radixblk(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
 cudaError_t launch_keys_radixblk2(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
+cudaError_t launch_keys_hash24(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
+cudaError_t launch_aggregate_hash24(const AggParams& p, const LaunchShape& s, cudaStream_t st);
 
 cudaError_t launch_keys(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st) {
     switch (s.lookup) {
         case kLookupSmem: return launch_keys_smem(p, s, keys, st);
         case kLookupRmi: return launch_keys_rmi(p, s, keys, st);
         case kLookupStaged: return launch_keys_staged(p, s, keys, st);
+        case kLookupHash24: return launch_keys_hash24(p, s, keys, st);
         case kLookupRadix:
             return s.keys_blk == 2   ? launch_keys_radixblk2(p, s, keys, st)
                    : s.keys_blk == 4 ? launch_keys_radixblk(p, s, keys, st)
@@ -38,6 +41,7 @@ cudaError_t launch_aggregate(const AggParams& p, const LaunchShape& s, cudaStrea
         case kLookupRmi: return launch_aggregate_rmi(p, s, st);
         case kLookupStaged: return launch_aggregate_staged(p, s, st);
         case kLookupRadix: return launch_aggregate_radix(p, s, st);
+        case kLookupHash24: return launch_aggregate_hash24(p, s, st);
         default: return launch_aggregate_l2(p, s, st);
     }
 }
@@ -172,6 +176,12 @@ __global__ void k_lookup(const __grid_constant__ AggParams p, const uint32_t* __
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint32_t x = __ldg(addr + i);
         uint32_t idx;
+        if (LOOKUP == kLookupHash24) {  // the /24 table has sites, not range positions
+            uint32_t xs[1] = {x}, st[1];
+            dev::hash24_sites<1>(p.h24, p.h24_mask, xs, st);
+            if (site_out) site_out[i] = st[0];
+            continue;
+        }
         if (LOOKUP == kLookupRmi) {
             idx = dev::rmi_lookup(p.rmi, ra, rb, rx0, reps, p.starts, p.n_ranges, x, p.violations);
         } else if (LOOKUP == kLookupRadix) {
@@ -267,6 +277,9 @@ cudaError_t launch_lookup(const AggParams& p, int lookup, const uint32_t* addr, 
             e = cudaFuncSetAttribute(k_lookup<kLookupRmi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             k_lookup<kLookupRmi><<<blocks, 256, smem, st>>>(p, addr, n, site_out, pos_out);
+            break;
+        case kLookupHash24:
+            k_lookup<kLookupHash24><<<blocks, 256, 0, st>>>(p, addr, n, site_out, pos_out);
             break;
         case kLookupStaged:
             e = cudaFuncSetAttribute(k_lookup<kLookupStaged>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "gnm.h"
+#include "hash24.hpp"
 
 namespace gnm {
 
@@ -76,6 +77,39 @@ std::string flatten_registry(const uint32_t* prefix, const uint8_t* len, const u
         emit(e, open.empty() ? GNM_NO_SITE : open.back().site);
     }
     return std::string();
+}
+
+// The paper's GPU Site Catalog (Sec. III.B.2.1): every registered network expanded into
+// its /24 subnets, entered in a hash table keyed by the subnet (address >> 8). Shorter
+// prefixes are entered first, so a nested longer prefix overwrites its parent's subnets and
+// the table holds the longest match of every /24. Open addressing with linear probing over
+// a power-of-two table at most half full; an entry is (subnet + 1, site), 0 = empty.
+// Only registries whose prefixes are all /24 or shorter can be expanded (false otherwise).
+bool build_hash24(const uint32_t* prefix, const uint8_t* len, const uint32_t* site, size_t n,
+                  std::vector<uint32_t>* table, uint32_t* mask) {
+    uint64_t subnets = 0;
+    for (size_t i = 0; i < n; ++i) {
+        if (len[i] > 24) return false;
+        subnets += 1ull << (24u - len[i]);
+    }
+    uint64_t cap = 1024;
+    while (cap < 2 * subnets) cap <<= 1;
+    if (cap > (1ull << 26)) return false;  // beyond 2^25 subnets: more than the catalog's purpose
+    table->assign(2 * cap, 0u);
+    std::vector<size_t> order(n);
+    for (size_t i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return len[a] < len[b]; });
+    for (size_t i : order) {
+        const uint32_t first = prefix[i] >> 8, count = 1u << (24u - len[i]);
+        for (uint32_t k = first; k < first + count; ++k) {
+            uint64_t h = hash24(k) & (cap - 1);
+            while ((*table)[2 * h] != 0u && (*table)[2 * h] != k + 1u) h = (h + 1) & (cap - 1);
+            (*table)[2 * h] = k + 1u;
+            (*table)[2 * h + 1] = site[i];
+        }
+    }
+    *mask = (uint32_t)(cap - 1);
+    return true;
 }
 
 // True when the local prefix overlaps any registered prefix (one contains the other).

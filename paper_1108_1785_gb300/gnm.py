@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libgnm.so")
 
 NO_SITE = 0xFFFFFFFF
 NSTAT = 6
-LOOKUP_AUTO, LOOKUP_BSEARCH, LOOKUP_RMI, LOOKUP_RADIX = 0, 1, 2, 3
+LOOKUP_AUTO, LOOKUP_BSEARCH, LOOKUP_RMI, LOOKUP_RADIX, LOOKUP_HASH24 = 0, 1, 2, 3, 4
 PLACE_AUTO, PLACE_SMEM, PLACE_L2, PLACE_STAGED = 0, 1, 2, 3
 AGG_AUTO, AGG_DIRECT, AGG_WARP = 0, 1, 2
 ADMIN_OR, ADMIN_AND = 0, 1

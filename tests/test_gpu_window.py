@@ -362,3 +362,47 @@ def test_registry_validation(gnm):
     with pytest.raises(gnm.GnmError, match="STATE"):
         ctx.dense(0)
     ctx.close()
+
+
+@pytest.fixture(scope="module")
+def reg24():
+    return fg.registry_c2_24()
+
+
+@pytest.mark.parametrize("split", ["AUTO", "FUSED"])
+def test_hash24_lookup_windows_match_oracle(gnm, reg24, split):
+    """The paper's /24 subnet hash table as the lookup (registry of /8-/24 prefixes, 20%
+    nested): windows equal the oracle and equal the binary-search lookup."""
+    reg = reg24
+    rec = fg.make_records(reg, 400_003, seed=13)
+    off = [0, 150_000, 400_003]
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    ctx = _ctx(gnm, reg, lookup_mode=gnm.LOOKUP_HASH24, split=getattr(gnm, "SPLIT_" + split))
+    assert ctx.registry_info().lookup_mode == gnm.LOOKUP_HASH24
+    ctx.process_windows(gnm.Records.to_device(rec), off, [1, 2])
+    for w, (a, b) in zip([1, 2], zip(off[:-1], off[1:])):
+        assert_window_matches(ctx.dense(w), oracle_full(reg, {k: v[a:b] for k, v in rec.items()}, lpm=lpm))
+    ctx.close()
+
+
+def test_hash24_batch_lookup_and_limits(gnm, reg24):
+    reg = reg24
+    ctx = _ctx(gnm, reg, lookup_mode=gnm.LOOKUP_HASH24)
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    st, _ = lpm.flatten()
+    s64 = st.astype(np.int64)
+    x = np.concatenate([s64, s64 - 1, s64 + 1, s64 + 255, [0, 0xFFFFFFFF],
+                        np.random.default_rng(8).integers(0, 1 << 32, 300_000)])
+    x = x[(x >= 0) & (x < (1 << 32))].astype(np.uint32)
+    dx = torch.from_numpy(x.view(np.int32)).cuda()
+    site = torch.empty_like(dx)
+    ctx.lookup(dx, site)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(site.cpu().numpy().view(np.uint32), lpm.lookup(x))
+    with pytest.raises(gnm.GnmError, match="positions"):
+        ctx.lookup(dx, site, torch.empty_like(dx))
+    ctx.close()
+    longer = _ctx(gnm, fg.registry_c2(), lookup_mode=gnm.LOOKUP_HASH24)  # has /25-/30 prefixes
+    with pytest.raises(gnm.GnmError, match="longer than /24"):
+        longer.process(gnm.Records.to_device(fg.make_records(fg.registry_c2(), 1000, seed=2)), 1)
+    longer.close()
