@@ -190,6 +190,53 @@ def rate_stats(lpm: LPM, local_prefix, local_len, n_sites: int, rec: Dict[str, n
     return hist, rmin, rmax, med
 
 
+def host_stats(lpm: LPM, local_prefix, local_len, n_sites: int, rec: Dict[str, np.ndarray],
+               min_avg_pkt_bytes: int = 100, min_pkts: int = 10, min_dur_ms: int = 1000, admin_rule: int = 0):
+    """Per-host sums of a window (Sec. III.B.2.1: statistics "for each host in a registered
+    site"): for every remote address of a registered site and direction, the same six sums
+    as a site key (flows, octets, pkts, e_flows, e_octets, e_dur_ms). Returns (addr u32,
+    site u32, dir u8, sums[n, 6] u64) sorted by (site, dir, addr)."""
+    src = np.asarray(rec["srcaddr"], np.uint32)
+    dst = np.asarray(rec["dstaddr"], np.uint32)
+    pk = np.asarray(rec["dPkts"], np.uint64)
+    oc = np.asarray(rec["dOctets"], np.uint64)
+    dur = (np.asarray(rec["last"], np.uint32) - np.asarray(rec["first"], np.uint32)).astype(np.uint64)
+
+    def local(a):
+        out = np.zeros(a.shape, bool)
+        for p, l in zip(local_prefix, local_len):
+            m = np.uint32(0) if int(l) == 0 else np.uint32((0xFFFFFFFF << (32 - int(l))) & 0xFFFFFFFF)
+            out |= (a & m) == np.uint32(p)
+        return out
+
+    sl, dl = local(src), local(dst)
+    out_ = sl & ~dl
+    mixed = sl != dl
+    remote = np.where(out_, dst, src)
+    site = lpm.lookup(remote)
+    keep = mixed & (site != NO_SITE)
+    if min_avg_pkt_bytes is None:
+        min_avg_pkt_bytes = 0
+    few, short = pk < min_pkts, dur < min_dur_ms
+    admin = ~(few | short) if admin_rule == 0 else ~(few & short)
+    elig = keep & (dur > 0) & (oc >= np.uint64(min_avg_pkt_bytes) * pk) & admin
+    key = (remote.astype(np.uint64) << np.uint64(1)) | out_.astype(np.uint64)
+    uk, inv = np.unique(key[keep], return_inverse=True)
+    sums = np.zeros((uk.size, NSTAT), np.uint64)
+    e = elig[keep]
+    np.add.at(sums[:, 0], inv, np.uint64(1))
+    np.add.at(sums[:, 1], inv, oc[keep])
+    np.add.at(sums[:, 2], inv, pk[keep])
+    np.add.at(sums[:, 3], inv[e], np.uint64(1))
+    np.add.at(sums[:, 4], inv[e], oc[keep][e])
+    np.add.at(sums[:, 5], inv[e], dur[keep][e])
+    addr = (uk >> np.uint64(1)).astype(np.uint32)
+    d = (uk & np.uint64(1)).astype(np.uint8)
+    hsite = lpm.lookup(addr)
+    order = np.lexsort((addr, d, hsite))
+    return addr[order], hsite[order], d[order], sums[order]
+
+
 def warnings(median_buckets, below_bucket: int = 100, consecutive: int = 2):
     """Sec. III.B.1 / Sec. IV.B: a warning for a (site, dir) key when its median transfer
     rate was below a standard (1 Mb/s: median bucket < 100) in `consecutive` consecutive

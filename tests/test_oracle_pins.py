@@ -372,6 +372,29 @@ def test_rate_stats_against_sorted_rates():
         np.testing.assert_array_equal(hist[k], np.bincount(bucket[sel], minlength=oracle.N_BUCKETS))
 
 
+def test_host_stats_sum_to_site_rows_and_hand_case():
+    """Per-host sums: on the 500-site workload they add up, host by host, to the C oracle's
+    per-site rows; a hand case gives two hosts of one site."""
+    reg, rec, m = _c1_window(n=40000, seed=12)
+    addr, site, d, sums = oracle.host_stats(m, reg.local_prefix, reg.local_len, reg.n_sites, rec)
+    st, _ = oracle.window(m, reg.local_prefix, reg.local_len, reg.n_sites, rec)
+    per_key = np.zeros_like(st)
+    np.add.at(per_key, site.astype(np.int64) * 2 + d, sums)
+    np.testing.assert_array_equal(per_key, st)
+    assert len(np.unique(addr.astype(np.uint64) * 2 + d)) == addr.size  # one row per (host, dir)
+    regh = np.array([[ip("10.0.0.0"), 8, 3]])
+    mh = oracle.LPM(regh[:, 0], regh[:, 1], regh[:, 2])
+    loc = ip("131.225.0.0")
+    a, b = ip("10.0.0.1"), ip("10.0.0.2")
+    rec = {"srcaddr": np.array([loc + 1, loc + 2, b, loc + 1], np.uint32),
+           "dstaddr": np.array([a, a, loc + 9, ip("11.0.0.1")], np.uint32),
+           "dPkts": np.array([10, 20, 30, 40], np.uint32), "dOctets": np.array([2000, 3000, 5000, 7000], np.uint32),
+           "first": np.zeros(4, np.uint32), "last": np.array([1000, 500, 4000, 1000], np.uint32)}
+    addr, site, d, sums = oracle.host_stats(mh, [loc], [16], 4, rec)
+    assert addr.tolist() == [b, a] and site.tolist() == [3, 3] and d.tolist() == [0, 1]
+    np.testing.assert_array_equal(sums, [[1, 5000, 30, 1, 5000, 4000], [2, 5000, 30, 1, 2000, 1000]])
+
+
 def test_warnings_hand_sequence():
     """Four keys over five windows (median buckets; 99 is below 1 Mb/s, 100 is not):
     key 0 below in windows 1-3, key 1 alternates, key 2 below then without flows then
