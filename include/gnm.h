@@ -122,6 +122,10 @@ typedef struct {
     int32_t rate_stats;         /* 1: per-flow rate statistics per window (gnm_window_rate_stats):
                                    each result slot also holds a 10001-bucket histogram per key
                                    (40 KB per key); 0: off */
+    uint32_t host_capacity;     /* > 0: per-host sums per window (gnm_window_hosts) for up to
+                                   this many (remote host, dir) pairs per window; each result
+                                   slot holds a table of 2^ceil(log2(2 * capacity)) entries of
+                                   56 bytes; launches then run the key kernel first. 0: off */
 } gnm_config;
 
 /* Host records: AUTO reads them in place when every array is page-locked host memory that
@@ -273,6 +277,22 @@ gnm_status gnm_warnings_update(gnm_ctx *ctx, uint64_t window_id, uint32_t below_
                                uint32_t *keys_out, size_t cap, size_t *n_out);
 gnm_status gnm_warnings_reset(gnm_ctx *ctx);
 
+/* Per-host sums of a finalised window (contexts with host_capacity > 0; Sec. III.B.2.1:
+ * statistics "for each host in a registered site"): one row per remote address of a
+ * registered site and direction, with the six sums of a site key and the rate of its
+ * eligible flows (as gnm_site_stats), sorted by (site, dir, addr). GNM_E_CAPACITY when cap
+ * is smaller than the number of rows (*n_out set), or when the window met more hosts than
+ * host_capacity (its rows are then incomplete; *n_out = the rows kept). */
+typedef struct {
+    uint32_t addr;
+    uint32_t site;
+    uint32_t dir;
+    uint32_t reserved;
+    uint64_t flows, octets, pkts, e_flows, e_octets, e_dur_ms;
+    double rate_bps;
+} gnm_host_stat;
+gnm_status gnm_window_hosts(gnm_ctx *ctx, uint64_t window_id, gnm_host_stat *out, size_t cap, size_t *n_out);
+
 /* Dense copies of a window's results to host arrays (each may be NULL):
  * stats[(2*n_sites) x GNM_NSTAT] (row site*2+dir), unmatched[12], rate[2*n_sites],
  * flag[2*n_sites] (against the context threshold). Synchronises with the window. */
@@ -392,7 +412,7 @@ gnm_status gnm_plan_launch(gnm_plan *plan, void *stream);
 
 /* Kernels of a plan's launch, in order */
 typedef enum { GNM_KERNEL_KEYS = 0, GNM_KERNEL_AGGREGATE = 1, GNM_KERNEL_FINALIZE = 2, GNM_KERNEL_PART_COUNT = 3,
-               GNM_KERNEL_PART_SCAN = 4, GNM_KERNEL_PART_SCATTER = 5 } gnm_kernel_kind;
+               GNM_KERNEL_PART_SCAN = 4, GNM_KERNEL_PART_SCATTER = 5, GNM_KERNEL_HOSTS = 6 } gnm_kernel_kind;
 
 /* Device durations (ms, CUDA events) of each kernel of the plan's last launch, which it
  * waits for; kind[i] names kernel i. *n_out = the plan's kernel count (GNM_E_CAPACITY

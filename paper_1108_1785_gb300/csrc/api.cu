@@ -130,6 +130,15 @@ void release_slots(gnm_ctx* c) {
     free_dev(c->d_mcnt);
     free_dev(c->d_warn_run);
     c->d_warn_run = nullptr;
+    free_dev(c->d_hkeys);
+    free_dev(c->d_hrows);
+    free_dev(c->d_hover);
+    free_dev(c->d_hrate);
+    c->d_hrate = nullptr;
+    c->d_hkeys = nullptr;
+    c->d_hrows = nullptr;
+    c->d_hover = nullptr;
+    c->hcap = 0;
     c->d_hist = nullptr;
     c->d_rmin = nullptr;
     c->d_rmax = nullptr;
@@ -283,6 +292,10 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s, size_t n_win) {
     // split launches: the lookup structure lives in the key kernel only
     int split = cfg.split != GNM_SPLIT_AUTO ? cfg.split : c->tuned.split;
     if (split == GNM_SPLIT_AUTO) split = s->lookup == kLookupSmem ? GNM_SPLIT_FUSED : GNM_SPLIT_TWO_KERNELS;
+    if (c->hcap) {  // per-host sums read the key kernel's keys
+        if (cfg.split == GNM_SPLIT_FUSED) return fail(GNM_E_INVAL, "per-host statistics need split launches");
+        split = GNM_SPLIT_TWO_KERNELS;
+    }
     if (split != GNM_SPLIT_FUSED && split != GNM_SPLIT_TWO_KERNELS) return fail(GNM_E_INVAL, "unknown split mode");
     s->split = split == GNM_SPLIT_TWO_KERNELS;
     s->keys_smem = s->split ? (lookup_bytes + 15) / 16 * 16 : 0;
@@ -456,6 +469,10 @@ gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p) {
     p->hist = c->d_hist;
     p->rmin = c->d_rmin;
     p->rmax = c->d_rmax;
+    p->hkeys = c->d_hkeys;
+    p->hrows = c->d_hrows;
+    p->hover = c->d_hover;
+    p->hcap = c->hcap;
     p->min_flows = c->cfg.min_flows_to_flag;
     p->threshold = c->cfg.threshold_bps;
     p->violations = c->d_violations;
@@ -557,15 +574,22 @@ PartLayout part_layout(uint64_t n, uint32_t nb) {
 }
 
 gnm_status clear_rate_stats(gnm_ctx* c, const uint32_t* slots, size_t n, cudaStream_t st) {
-    if (!c->d_hist) return GNM_OK;
-    const size_t nk = (size_t)2 * c->n_sites;
+    if (!c->d_hist && !c->d_hkeys) return GNM_OK;
+    const size_t nk = (size_t)2 * c->n_sites, hc = c->hcap;
     for (size_t k = 0; k < n;) {  // runs of consecutive slots: one memset per array
         size_t m = 1;
         while (k + m < n && slots[k + m] == slots[k] + m) ++m;
         const size_t s0 = slots[k];
-        GNM_CU(cudaMemsetAsync(c->d_hist + s0 * nk * kRateBuckets, 0, m * nk * kRateBuckets * 4, st));
-        GNM_CU(cudaMemsetAsync(c->d_rmax + s0 * nk, 0, m * nk * 8, st));
-        GNM_CU(cudaMemsetAsync(c->d_rmin + s0 * nk, 0xFF, m * nk * 8, st));  // above every rate
+        if (c->d_hist) {
+            GNM_CU(cudaMemsetAsync(c->d_hist + s0 * nk * kRateBuckets, 0, m * nk * kRateBuckets * 4, st));
+            GNM_CU(cudaMemsetAsync(c->d_rmax + s0 * nk, 0, m * nk * 8, st));
+            GNM_CU(cudaMemsetAsync(c->d_rmin + s0 * nk, 0xFF, m * nk * 8, st));  // above every rate
+        }
+        if (c->d_hkeys) {
+            GNM_CU(cudaMemsetAsync(c->d_hkeys + s0 * hc, 0, m * hc * 8, st));
+            GNM_CU(cudaMemsetAsync(c->d_hrows + s0 * hc * kNStat, 0, m * hc * kNStat * 8, st));
+            GNM_CU(cudaMemsetAsync(c->d_hover + s0, 0, m * 4, st));
+        }
         k += m;
     }
     return GNM_OK;
@@ -598,6 +622,11 @@ gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, s
             GNM_CU(launch_keys(pk, pr.sh, keys, st));
             ++*launches;
             GNM_TRY(mark(GNM_KERNEL_KEYS));
+            if (pr.p.hkeys) {
+                GNM_CU(launch_host_stats(pr.p, keys, c->sm_count * 4, st));
+                ++*launches;
+                GNM_TRY(mark(GNM_KERNEL_HOSTS));
+            }
             const PartLayout L = part_layout(pr.n, pr.n_buckets);
             uint32_t* out = reinterpret_cast<uint32_t*>(d_part);
             uint32_t* cnt = reinterpret_cast<uint32_t*>(d_part + L.cnt);
@@ -647,6 +676,11 @@ gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, s
             GNM_CU(launch_keys(pk, pr.sh, keys, st));
             ++*launches;
             GNM_TRY(mark(GNM_KERNEL_KEYS));
+            if (pr.p.hkeys) {
+                GNM_CU(launch_host_stats(pr.p, keys, c->sm_count * 4, st));
+                ++*launches;
+                GNM_TRY(mark(GNM_KERNEL_HOSTS));
+            }
             AggParams pa = pr.p;
             pa.src = keys;
             pa.dst = keys;
@@ -1059,6 +1093,16 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
         GNM_CU(cudaMalloc(&c->d_warn_run, nk * 4));
         GNM_CU(cudaMemset(c->d_warn_run, 0, nk * 4));
     }
+    if (c->cfg.host_capacity) {  // per-host sums: a table at most half full per slot
+        uint64_t hc = 1024;
+        while (hc < 2ull * c->cfg.host_capacity) hc <<= 1;
+        if (hc > (1ull << 31)) return fail(GNM_E_INVAL, "host_capacity too large");
+        c->hcap = (uint32_t)hc;
+        GNM_CU(cudaMalloc(&c->d_hkeys, slots * hc * 8));
+        GNM_CU(cudaMalloc(&c->d_hrows, slots * hc * kNStat * 8));
+        GNM_CU(cudaMalloc(&c->d_hover, slots * 4));
+        GNM_CU(cudaMalloc(&c->d_hrate, hc * 8));
+    }
     c->slots.resize(slots);
     c->have_registry = true;
     return GNM_OK;
@@ -1170,6 +1214,57 @@ gnm_status gnm_window_rate_stats(gnm_ctx* c, uint64_t wid, double* rmin, double*
             rmax[k] = cnt[k] ? v : nan;
         }
     }
+    return GNM_OK;
+}
+
+gnm_status gnm_window_hosts(gnm_ctx* c, uint64_t wid, gnm_host_stat* out, size_t cap, size_t* n_out) {
+    if (!c || !n_out) return fail(GNM_E_INVAL, "NULL argument");
+    if (!c->d_hkeys) return fail(GNM_E_STATE, "the context keeps no per-host sums (host_capacity = 0)");
+    GNM_CU(cudaSetDevice(c->device));
+    uint32_t s;
+    GNM_TRY(find_window(c, wid, &s));
+    if (!c->slots[s].finalized) return fail(GNM_E_STATE, "window is open (not finalised)");
+    GNM_TRY(sync_slot(c, s));
+    const size_t hc = c->hcap;
+    std::vector<unsigned long long> keys(hc), rows(hc * kNStat);
+    std::vector<double> rate(hc);
+    uint32_t lost = 0;
+    const unsigned long long* d_rows = c->d_hrows + (size_t)s * hc * kNStat;
+    GNM_CU(launch_host_rates(d_rows, (uint32_t)hc, c->d_hrate, c->aux));
+    GNM_CU(cudaStreamSynchronize(c->aux));
+    GNM_CU(cudaMemcpy(keys.data(), c->d_hkeys + (size_t)s * hc, hc * 8, cudaMemcpyDeviceToHost));
+    GNM_CU(cudaMemcpy(rows.data(), d_rows, hc * kNStat * 8, cudaMemcpyDeviceToHost));
+    GNM_CU(cudaMemcpy(rate.data(), c->d_hrate, hc * 8, cudaMemcpyDeviceToHost));
+    GNM_CU(cudaMemcpy(&lost, c->d_hover + s, 4, cudaMemcpyDeviceToHost));
+    std::vector<gnm_host_stat> v;
+    for (size_t h = 0; h < hc; ++h) {
+        if (!keys[h]) continue;
+        const unsigned long long k = keys[h] - 1ull;
+        gnm_host_stat r;
+        r.addr = (uint32_t)(k >> 1);
+        r.dir = (uint32_t)(k & 1ull);
+        // the host's site: the flattened range holding its address
+        const size_t i = (size_t)(std::upper_bound(c->h_starts.begin(), c->h_starts.end(), r.addr) -
+                                  c->h_starts.begin()) - 1;
+        r.site = c->h_site[i];
+        r.reserved = 0;
+        const unsigned long long* q = &rows[h * kNStat];
+        r.flows = q[0];
+        r.octets = q[1];
+        r.pkts = q[2];
+        r.e_flows = q[3];
+        r.e_octets = q[4];
+        r.e_dur_ms = q[5];
+        r.rate_bps = rate[h];
+        v.push_back(r);
+    }
+    std::sort(v.begin(), v.end(), [](const gnm_host_stat& a, const gnm_host_stat& b) {
+        return a.site != b.site ? a.site < b.site : a.dir != b.dir ? a.dir < b.dir : a.addr < b.addr;
+    });
+    *n_out = v.size();
+    if (cap < v.size()) return fail(GNM_E_CAPACITY, "cap smaller than the number of host rows");
+    if (out && !v.empty()) std::memcpy(out, v.data(), v.size() * sizeof(gnm_host_stat));
+    if (lost) return fail(GNM_E_CAPACITY, std::to_string(lost) + " records met a full host table (host_capacity)");
     return GNM_OK;
 }
 

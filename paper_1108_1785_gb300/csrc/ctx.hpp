@@ -117,6 +117,11 @@ struct gnm_ctx {
     uint32_t* d_med = nullptr;            // [2S] readout scratch: median buckets
     uint32_t* d_mcnt = nullptr;           // [2S] readout scratch: eligible flows
     uint32_t* d_warn_run = nullptr;       // [2S] windows in a row with a below-standard median
+    unsigned long long* d_hkeys = nullptr; // per-host sums (cfg.host_capacity): [slots][hcap] keys
+    unsigned long long* d_hrows = nullptr; // [slots][hcap][6] sums
+    uint32_t* d_hover = nullptr;           // [slots] hosts lost to a full table
+    double* d_hrate = nullptr;             // [hcap] readout scratch: host rates
+    uint32_t hcap = 0;
     std::vector<gnm::Slot> slots;
     std::unordered_map<uint64_t, uint32_t> slot_of;
     uint64_t age = 0;
@@ -181,7 +186,7 @@ gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, s
                             uint32_t* d_partials, uint32_t* d_keys, unsigned char* d_part, cudaStream_t st,
                             uint32_t* launches, cudaEvent_t* marks = nullptr, int32_t* kinds = nullptr,
                             bool fresh = true);
-constexpr int kMaxPlanKernels = 6;  // keys, count, scan, scatter, aggregate, finalise
+constexpr int kMaxPlanKernels = 7;  // keys, hosts, count, scan, scatter, aggregate, finalise
 // Next launch-scratch entry of the ring (waits for its previous use).
 gnm_status acquire_ring(gnm_ctx* c, uint32_t n_win, LaunchBuf** out);
 void set_slots_done(gnm_ctx* c, const uint32_t* slots, size_t n, cudaEvent_t ev, bool finalized);

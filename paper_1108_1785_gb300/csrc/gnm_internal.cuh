@@ -99,6 +99,10 @@ struct AggParams {
     uint32_t* hist;              // [slots][2*n_sites][kRateBuckets] rate histograms, or null
     unsigned long long* rmin;    // [slots][2*n_sites] least rate (bits of a double >= 0)
     unsigned long long* rmax;    // [slots][2*n_sites] greatest rate
+    unsigned long long* hkeys;   // [slots][hcap] host table keys ((addr << 1 | dir) + 1; 0 empty), or null
+    unsigned long long* hrows;   // [slots][hcap][kNStat] host sums
+    uint32_t* hover;             // [slots] hosts that found no free entry
+    uint32_t hcap;               // host table entries per slot (power of two)
     double* rate;                // [slots][2*n_sites]
     uint8_t* flag;               // [slots][2*n_sites]
     uint32_t keys;               // 2*n_sites + 4
@@ -193,6 +197,12 @@ cudaError_t launch_finalize_windows(const AggParams& p, cudaStream_t st);
 // reaches `consecutive` are appended to out (count via *n).
 cudaError_t launch_warn_runs(const uint32_t* med, uint32_t n_keys, uint32_t below, uint32_t consecutive,
                              uint32_t* run, uint32_t* out, uint32_t* n, cudaStream_t st);
+// Per-host sums of a split launch: after the key kernel (keys at `keys`, same phase as the
+// records), every record of a registered site adds to its (remote host, dir) entry of its
+// window's host table.
+cudaError_t launch_host_stats(const AggParams& p, const uint32_t* keys, int grid, cudaStream_t st);
+// FP64 rate of each of n host entries (rows of kNStat sums).
+cudaError_t launch_host_rates(const unsigned long long* rows, uint32_t n, double* rate, cudaStream_t st);
 // Lower-median bucket and eligible-flow count of every site key of one slot's histograms.
 cudaError_t launch_rate_median(const uint32_t* hist, uint32_t n_keys, uint32_t* med, uint32_t* count,
                                cudaStream_t st);

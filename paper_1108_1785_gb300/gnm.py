@@ -50,7 +50,8 @@ class Config(C.Structure):
                 ("window_slots", C.c_uint32), ("threshold_bps", C.c_double), ("block_threads", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("unroll", C.c_int32), ("table_mode", C.c_int32),
                 ("hash_slots", C.c_uint32), ("radix_bits", C.c_uint32), ("split", C.c_int32),
-                ("key_directory", C.c_int32), ("host_records", C.c_int32), ("rate_stats", C.c_int32)]
+                ("key_directory", C.c_int32), ("host_records", C.c_int32), ("rate_stats", C.c_int32),
+                ("host_capacity", C.c_uint32)]
 
 
 class RecordsC(C.Structure):
@@ -98,6 +99,12 @@ class StreamStats(C.Structure):
                 ("windows_closed", C.c_uint64), ("windows_done", C.c_uint64), ("inflight_bytes", C.c_uint64),
                 ("peak_inflight_bytes", C.c_uint64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
                 ("max_ms", C.c_double), ("mean_ms", C.c_double)]
+
+
+class HostStat(C.Structure):
+    _fields_ = [("addr", C.c_uint32), ("site", C.c_uint32), ("dir", C.c_uint32), ("reserved", C.c_uint32),
+                ("flows", C.c_uint64), ("octets", C.c_uint64), ("pkts", C.c_uint64), ("e_flows", C.c_uint64),
+                ("e_octets", C.c_uint64), ("e_dur_ms", C.c_uint64), ("rate_bps", C.c_double)]
 
 
 class TuneReport(C.Structure):
@@ -158,6 +165,7 @@ def lib():
             "gnm_window_rate_stats": (st, [P, U64, P, P, P, P]),
             "gnm_warnings_update": (st, [P, U64, U32, U32, P, S, C.POINTER(S)]),
             "gnm_warnings_reset": (st, [P]),
+            "gnm_window_hosts": (st, [P, U64, P, S, C.POINTER(S)]),
             "gnm_stream_config_default": (None, [C.POINTER(StreamConfig)]),
             "gnm_stream_open": (st, [P, C.POINTER(StreamConfig), C.POINTER(P)]),
             "gnm_stream_submit": (st, [P, C.POINTER(RecordsC), U64, C.c_int]),
@@ -382,6 +390,22 @@ class Context:
         h = np.empty((nk, RATE_BUCKETS), np.uint32) if hist else None
         self._c(lib().gnm_window_rate_stats(self.h, window_id, _ptr(rmin), _ptr(rmax), _ptr(med), _ptr(h)))
         return rmin, rmax, med, h
+
+    def hosts(self, window_id: int):
+        """Per-host rows of a window: (addr u32, site u32, dir u8, sums[n, 6] u64, rate f64),
+        sorted by (site, dir, addr)."""
+        n = C.c_size_t()
+        st = lib().gnm_window_hosts(self.h, window_id, None, 0, C.byref(n))
+        if st not in (0, 5):
+            self._c(st)
+        buf = (HostStat * max(n.value, 1))()
+        self._c(lib().gnm_window_hosts(self.h, window_id, buf, n.value, C.byref(n)))
+        a = np.frombuffer(buf, dtype=np.dtype([(f, np.uint32) for f in ("addr", "site", "dir", "reserved")] +
+                                             [(f, np.uint64) for f in ("flows", "octets", "pkts", "e_flows",
+                                                                       "e_octets", "e_dur_ms")] +
+                                             [("rate_bps", np.float64)]), count=n.value)
+        sums = np.stack([a[f] for f in ("flows", "octets", "pkts", "e_flows", "e_octets", "e_dur_ms")], axis=1)
+        return a["addr"].copy(), a["site"].copy(), a["dir"].astype(np.uint8), sums, a["rate_bps"].copy()
 
     def warnings_update(self, window_id: int, below_bucket: int = 100, consecutive: int = 2) -> np.ndarray:
         """Keys (site*2+dir) warned about after this window (the next one in time order)."""
