@@ -277,7 +277,7 @@ def batched_c4(gnm, torch, local, steps, warmup):
                       "placement": tune.placement, "ctas_per_sm": tune.ctas_per_sm}}
 
 
-def serve_c5(gnm, torch, local, minutes=30, speedup=600.0, pool_n=20_000_000, budget=4 << 30, check=2):
+def serve_c5(gnm, torch, local, minutes=120, speedup=600.0, pool_n=20_000_000, budget=4 << 30, check=2):
     """Streaming replay: Poisson batch arrivals (1,000-500,000 records, 1e6 records/s on
     average times the diurnal factor) over the learned-index 100,000-site registry, the
     `minutes` around the daily peak replayed `speedup` times faster than real time. Host
@@ -531,7 +531,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-window batched launch")
     ap.add_argument("--learned-records", type=int, default=50_000_000)
     ap.add_argument("--learned-modes", default="bsearch,radix,rmi,rmi8192")
-    ap.add_argument("--serve-minutes", type=int, default=30)
+    ap.add_argument("--serve-minutes", type=int, default=120)
     ap.add_argument("--serve-speedup", type=float, default=600.0)
     args = ap.parse_args()
     if args.impl == "reference":

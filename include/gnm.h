@@ -276,6 +276,11 @@ gnm_status gnm_window_rate_stats(gnm_ctx *ctx, uint64_t window_id, double *rmin,
 gnm_status gnm_warnings_update(gnm_ctx *ctx, uint64_t window_id, uint32_t below_bucket, uint32_t consecutive,
                                uint32_t *keys_out, size_t cap, size_t *n_out);
 gnm_status gnm_warnings_reset(gnm_ctx *ctx);
+/* The warning runs as host arrays of 2*n_sites u32 (export), or set from them (import):
+ * monitoring stopped after some window resumes, in another context over the same registry,
+ * with the next window as if it had never stopped. */
+gnm_status gnm_warnings_export(gnm_ctx *ctx, uint32_t *runs);
+gnm_status gnm_warnings_import(gnm_ctx *ctx, const uint32_t *runs);
 
 /* Per-host sums of a finalised window (contexts with host_capacity > 0; Sec. III.B.2.1:
  * statistics "for each host in a registered site"): one row per remote address of a

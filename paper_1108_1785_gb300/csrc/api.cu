@@ -1304,6 +1304,24 @@ gnm_status gnm_warnings_reset(gnm_ctx* c) {
     return GNM_OK;
 }
 
+gnm_status gnm_warnings_export(gnm_ctx* c, uint32_t* runs) {
+    if (!c || !runs) return fail(GNM_E_INVAL, "NULL argument");
+    if (!c->d_warn_run) return fail(GNM_E_STATE, "the context keeps no rate statistics (rate_stats = 0)");
+    GNM_CU(cudaSetDevice(c->device));
+    GNM_CU(cudaMemcpyAsync(runs, c->d_warn_run, (size_t)2 * c->n_sites * 4, cudaMemcpyDeviceToHost, c->aux));
+    GNM_CU(cudaStreamSynchronize(c->aux));
+    return GNM_OK;
+}
+
+gnm_status gnm_warnings_import(gnm_ctx* c, const uint32_t* runs) {
+    if (!c || !runs) return fail(GNM_E_INVAL, "NULL argument");
+    if (!c->d_warn_run) return fail(GNM_E_STATE, "the context keeps no rate statistics (rate_stats = 0)");
+    GNM_CU(cudaSetDevice(c->device));
+    GNM_CU(cudaMemcpyAsync(c->d_warn_run, runs, (size_t)2 * c->n_sites * 4, cudaMemcpyHostToDevice, c->aux));
+    GNM_CU(cudaStreamSynchronize(c->aux));
+    return GNM_OK;
+}
+
 gnm_status gnm_window_dense(gnm_ctx* c, uint64_t wid, uint64_t* stats, uint64_t* unmatched,
                             double* rate, uint8_t* flag) {
     if (!c) return fail(GNM_E_INVAL, "ctx is NULL");

@@ -165,6 +165,8 @@ def lib():
             "gnm_window_rate_stats": (st, [P, U64, P, P, P, P]),
             "gnm_warnings_update": (st, [P, U64, U32, U32, P, S, C.POINTER(S)]),
             "gnm_warnings_reset": (st, [P]),
+            "gnm_warnings_export": (st, [P, P]),
+            "gnm_warnings_import": (st, [P, P]),
             "gnm_window_hosts": (st, [P, U64, P, S, C.POINTER(S)]),
             "gnm_stream_config_default": (None, [C.POINTER(StreamConfig)]),
             "gnm_stream_open": (st, [P, C.POINTER(StreamConfig), C.POINTER(P)]),
@@ -417,6 +419,17 @@ class Context:
 
     def warnings_reset(self):
         self._c(lib().gnm_warnings_reset(self.h))
+
+    def warnings_export(self) -> np.ndarray:
+        runs = np.empty(2 * self.n_sites, np.uint32)
+        self._c(lib().gnm_warnings_export(self.h, _ptr(runs)))
+        return runs
+
+    def warnings_import(self, runs):
+        r = np.ascontiguousarray(runs, np.uint32)
+        if r.size != 2 * self.n_sites:
+            raise ValueError("runs must have 2 * n_sites entries")
+        self._c(lib().gnm_warnings_import(self.h, _ptr(r)))
 
     def device_results(self, window_id: int):
         """Raw device addresses (stats, rate, flag) of a window's dense results."""

@@ -96,3 +96,26 @@ def test_warnings_follow_oracle_over_windows(gnm, consecutive):
     got = ctx.warnings_update(54, below_bucket=100, consecutive=consecutive)
     np.testing.assert_array_equal(got, np.nonzero(oracle.warnings(meds[4:], consecutive=consecutive)[0])[0])
     ctx.close()
+
+
+def test_warnings_resume_from_exported_runs(gnm):
+    """Monitoring stopped after window 2 and resumed in a new context from the exported runs
+    gives, for windows 3 and 4, the warnings of the uninterrupted sequence."""
+    reg = fg.registry_c1()
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    wins = [fg.make_records(reg, 60_000, seed=200 + w, zipf_s=1.1) for w in range(5)]
+    want = oracle.warnings([_expect(reg, r, lpm)[3] for r in wins], below_bucket=100, consecutive=2)
+    first = gnm.Context(window_slots=4, rate_stats=1)
+    first.load(reg)
+    for w in range(3):
+        first.process(gnm.Records.to_device(wins[w]), w)
+        first.warnings_update(w)
+    runs = first.warnings_export()
+    first.close()
+    second = gnm.Context(window_slots=4, rate_stats=1)
+    second.load(reg)
+    second.warnings_import(runs)
+    for w in (3, 4):
+        second.process(gnm.Records.to_device(wins[w]), w)
+        np.testing.assert_array_equal(second.warnings_update(w), np.nonzero(want[w])[0])
+    second.close()

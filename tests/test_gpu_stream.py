@@ -203,3 +203,35 @@ def test_window_of_a_plan_fails_alone(gnm, regs):
     stream.close()
     plan.close()
     ctx.close()
+
+
+def test_served_windows_keep_rate_and_host_statistics(gnm, regs):
+    """A context that also keeps per-flow rate statistics and per-host sums: every served
+    window (interleaved batches) has the same statistics as the window processed alone."""
+    reg = regs["c2"]
+    rng = np.random.default_rng(19)
+    pool = fg.make_records(reg, 200_000, seed=29)
+    wins, order, empty_close = _plan_mix(rng, 6, 200_000, 20_000)
+    cfg = dict(window_slots=16, rate_stats=1, host_capacity=100_000)
+    ctx = gnm.Context(**cfg)
+    ctx.load(reg)
+
+    def read(w):
+        return ctx.dense(w), ctx.rate_stats(w, hist=True), ctx.hosts(w)
+    stream = gnm.Stream(ctx, budget_bytes=3 * 20_000 * 24, n_cuda_streams=3)
+    done = _serve(gnm, stream, lambda a, b: gnm.Records.host({k: v[a:b] for k, v in pool.items()}),
+                  wins, order, empty_close, read)
+    stream.close()
+    alone = gnm.Context(**cfg)
+    alone.load(reg)
+    for w, sl in wins.items():
+        dense, rs, hosts = done[w][3]
+        alone.process(gnm.Records.to_device(_concat(pool, sl)), w)
+        for x, y in zip(dense, alone.dense(w)):
+            np.testing.assert_array_equal(x, y)
+        for x, y in zip(rs, alone.rate_stats(w, hist=True)):
+            np.testing.assert_array_equal(x, y)
+        for x, y in zip(hosts, alone.hosts(w)):
+            np.testing.assert_array_equal(x, y)
+    alone.close()
+    ctx.close()
