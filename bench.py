@@ -303,13 +303,17 @@ def serve_c5(gnm, torch, local, minutes=120, speedup=600.0, pool_n=20_000_000, b
     checked = sorted({0, int(rng.integers(1, minutes))})[:check]
     got = {}
 
+    queued = []
+
     def replay(srv, speedup, base):
         """Submits the schedule (speedup None: as fast as possible); window w has id base + w."""
         reports = []
+        queued.clear()
 
         def take(rs):
             for r in rs:
                 reports.append(r)
+                queued.append(r[4])
                 if r[0] - base in checked and speedup is not None:
                     got[r[0] - base] = ctx.dense(r[0])
         nb, bi, wc = len(times), 0, 0
@@ -327,8 +331,8 @@ def serve_c5(gnm, torch, local, minutes=120, speedup=600.0, pool_n=20_000_000, b
                 else:
                     srv.close_window(base + wc)
                     wc += 1
-            take(srv.poll())
-        take(srv.poll(wait_all=True))
+            take(srv.poll(queued=True))
+        take(srv.poll(wait_all=True, queued=True))
         return reports, time.perf_counter() - start
 
     with gnm.Stream(ctx, budget_bytes=budget, n_cuda_streams=4) as srv:
@@ -337,6 +341,7 @@ def serve_c5(gnm, torch, local, minutes=120, speedup=600.0, pool_n=20_000_000, b
         srv.poll(wait_all=True)
         torch.cuda.synchronize()
         reports, wall = replay(srv, speedup, 0)
+        q_ms = list(queued)
         st = srv.stats()
         sat_reports, sat_wall = replay(srv, None, 1 << 20)
         sat_st = srv.stats()
@@ -365,7 +370,10 @@ def serve_c5(gnm, torch, local, minutes=120, speedup=600.0, pool_n=20_000_000, b
             "p50_ms": float(np.percentile(lat, 50, method="inverted_cdf")) if lat else None,
             "p99_ms": float(np.percentile(lat, 99, method="inverted_cdf")) if lat else None,
             "max_ms": max(lat) if lat else None, "latency": "window close -> rates and flags final (host clock)",
-            "slowest_windows_ms": sorted(((r[2], r[0]) for r in reports if r[3] == 0), reverse=True)[:3],
+            "slowest_windows_ms": sorted(((r[2], r[0], r[4]) for r in reports if r[3] == 0), reverse=True)[:3],
+            "queued_p50_ms": float(np.percentile(q_ms, 50)) if q_ms else None,
+            "queued_p99_ms": float(np.percentile(q_ms, 99)) if q_ms else None,
+            "queued": "closing submit -> finalisation enqueued (host side of the latency)",
             "budget_bytes": budget, "peak_inflight_bytes": int(st["peak_inflight_bytes"]),
             "batches": int(st["batches"]), "batches_queued": int(st["batches_queued"]),
             "checked_windows": checked, "mix_equals_alone": bool(ok),

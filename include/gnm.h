@@ -492,6 +492,8 @@ typedef struct {
     double latency_ms;        /* closing submit -> rates and flags final */
     int32_t status;           /* GNM_OK, or the first error of the window's work */
     int32_t reserved;
+    double queued_ms;         /* closing submit -> its finalisation enqueued (the part of the
+                                 latency spent on the host: admission queue, submission) */
 } gnm_window_done;
 
 typedef struct {

@@ -86,6 +86,7 @@ struct Win {
     uint32_t slot = 0;
     uint64_t records = 0;
     int64_t t_close = 0;        // host time of the closing submit
+    int64_t t_enq = 0;          // host time its finalisation was enqueued
     int32_t status = GNM_OK;
     std::atomic<int64_t> t_done{0};  // set by the completion callback (or on failure)
 };
@@ -238,6 +239,7 @@ gnm_status enqueue(gnm_stream* s, Batch& b, Win& w) {
         finish_failed(s, w);
     } else if (b.close) {
         GNM_TRY(close_window(c, b.wid, st));  // the slot stays pinned until the window is reported
+        w.t_enq = now_ns();
         w.open = false;
         w.closed = true;
         s->closing.push_back(&w);
@@ -466,6 +468,7 @@ gnm_status gnm_stream_poll(gnm_stream* s, gnm_window_done* out, size_t cap, size
         d.latency_ms = (double)(t - w->t_close) * 1e-6;
         d.status = w->status;
         d.reserved = 0;
+        d.queued_ms = w->t_enq ? (double)(w->t_enq - w->t_close) * 1e-6 : 0.0;
         if (w->status == GNM_OK) {
             s->latencies_ms.push_back(d.latency_ms);
             s->to_unpin.push_back(w->slot);

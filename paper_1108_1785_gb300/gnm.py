@@ -91,7 +91,7 @@ class StreamConfig(C.Structure):
 
 class WindowDone(C.Structure):
     _fields_ = [("window_id", C.c_uint64), ("records", C.c_uint64), ("latency_ms", C.c_double),
-                ("status", C.c_int32), ("reserved", C.c_int32)]
+                ("status", C.c_int32), ("reserved", C.c_int32), ("queued_ms", C.c_double)]
 
 
 class StreamStats(C.Structure):
@@ -592,8 +592,9 @@ class Stream:
         empty = RecordsC()
         self.ctx._c(lib().gnm_stream_submit(self.h, C.byref(empty), window_id, 1))
 
-    def poll(self, wait_all: bool = False):
-        """Windows completed since the last poll: list of (window_id, records, latency_ms, status)."""
+    def poll(self, wait_all: bool = False, queued: bool = False):
+        """Windows completed since the last poll: list of (window_id, records, latency_ms, status)
+        (with queued=True a fifth item: queued_ms)."""
         out = []
         wait = 1 if wait_all else 0
         while True:
@@ -601,7 +602,8 @@ class Stream:
             self.ctx._c(lib().gnm_stream_poll(self.h, self._buf, len(self._buf), C.byref(n), wait))
             for i in range(n.value):
                 d = self._buf[i]
-                out.append((int(d.window_id), int(d.records), float(d.latency_ms), int(d.status)))
+                r = (int(d.window_id), int(d.records), float(d.latency_ms), int(d.status))
+                out.append(r + (float(d.queued_ms),) if queued else r)
                 self._held.pop(int(d.window_id), None)
             if n.value < len(self._buf):
                 return out
