@@ -318,6 +318,22 @@ def serve_c5(gnm, torch, local, minutes=120, speedup=600.0, pool_n=20_000_000, b
                     got[r[0] - base] = ctx.dense(r[0])
         nb, bi, wc = len(times), 0, 0
         start = time.perf_counter()
+        if speedup is None:  # as fast as possible: the schedule in submit_many calls of 512 events
+            ev_b, ev_c, ev_w, ev_f = [], [], [], []
+            while bi < nb or wc < minutes:
+                if bi < nb and times[bi] <= (wc + 1) * 60.0:
+                    ev_b.append(int(offs[bi])), ev_c.append(int(sizes[bi]))
+                    ev_w.append(base + int(win_of[bi])), ev_f.append(0)
+                    bi += 1
+                else:
+                    ev_b.append(0), ev_c.append(0), ev_w.append(base + wc), ev_f.append(1)
+                    wc += 1
+            start = time.perf_counter()
+            for k in range(0, len(ev_b), 512):
+                srv.submit_many(pool_recs, ev_b[k:k + 512], ev_c[k:k + 512], ev_w[k:k + 512], ev_f[k:k + 512])
+                take(srv.poll(queued=True))
+            take(srv.poll(wait_all=True, queued=True))
+            return reports, time.perf_counter() - start
         while bi < nb or wc < minutes:
             now = float("inf") if speedup is None else (time.perf_counter() - start) * speedup
             ta = times[bi] if bi < nb else float("inf")
@@ -335,6 +351,7 @@ def serve_c5(gnm, torch, local, minutes=120, speedup=600.0, pool_n=20_000_000, b
         take(srv.poll(wait_all=True, queued=True))
         return reports, time.perf_counter() - start
 
+    pool_recs = gnm.Records(hpool)
     with gnm.Stream(ctx, budget_bytes=budget, n_cuda_streams=4) as srv:
         # warm-up window (not reported): first use of the kernels and the arena
         srv.submit(gnm.Records({k: v[:100_000] for k, v in hpool.items()}), 1 << 40, close=True)
@@ -383,8 +400,8 @@ def serve_c5(gnm, torch, local, minutes=120, speedup=600.0, pool_n=20_000_000, b
                           "p99_ms": float(np.percentile(sat_lat, 99, method="inverted_cdf")) if sat_lat else None,
                           "peak_inflight_bytes": int(sat_st["peak_inflight_bytes"]),
                           "batches_queued": int(sat_st["batches_queued"] - st["batches_queued"]),
-                          "note": "same schedule submitted as fast as the host loop can; latency includes "
-                                  "the queue behind the budget"}}
+                          "note": "same schedule submitted as fast as possible (gnm_stream_submit_many, 512 "
+                                  "batches or closes per call); latency includes the queue behind the budget"}}
 
 
 class ClockSampler:

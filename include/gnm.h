@@ -522,6 +522,15 @@ gnm_status gnm_stream_open(gnm_ctx *ctx, const gnm_stream_config *cfg, gnm_strea
 gnm_status gnm_stream_submit(gnm_stream *s, const gnm_records *batch, uint64_t window_id,
                              int close_window);
 
+/* Submits n_batches batches that are slices of one record pool (host or device):
+ * batch i = records [begin[i], begin[i] + count[i]) of `pool` for window wids[i], closing it
+ * when close_flags[i] (close_flags may be NULL: none close). The batches are taken in order
+ * as by gnm_stream_submit; at the first error it stops and returns it, *n_accepted holding
+ * the batches taken. Host pool arrays must stay valid until their windows are reported. */
+gnm_status gnm_stream_submit_many(gnm_stream *s, const gnm_records *pool, const uint64_t *begin,
+                                  const uint64_t *count, const uint64_t *window_ids, const uint8_t *close_flags,
+                                  size_t n_batches, size_t *n_accepted);
+
 /* Admits what fits and reports up to cap windows completed since the last report
  * (*n_out set; more stay for the next call). wait_all = 1 first waits until every
  * submitted batch is processed and every closed window is done, or until the batches

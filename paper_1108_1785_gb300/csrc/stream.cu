@@ -379,6 +379,31 @@ gnm_status gnm_stream_open(gnm_ctx* c, const gnm_stream_config* cfg_in, gnm_stre
     return GNM_OK;
 }
 
+gnm_status gnm_stream_submit_many(gnm_stream* s, const gnm_records* pool, const uint64_t* begin,
+                                  const uint64_t* count, const uint64_t* wids, const uint8_t* close_flags,
+                                  size_t n_batches, size_t* n_accepted) {
+    if (!s || !pool || !n_accepted || (n_batches && (!begin || !count || !wids)))
+        return fail(GNM_E_INVAL, "NULL argument");
+    *n_accepted = 0;
+    for (size_t i = 0; i < n_batches; ++i) {
+        if (count[i] && (begin[i] > pool->n || count[i] > pool->n - begin[i]))
+            return fail(GNM_E_INVAL, "batch " + std::to_string(i) + " lies outside the pool");
+        gnm_records b = *pool;
+        b.n = count[i];
+        if (count[i]) {
+            b.srcaddr += begin[i];
+            b.dstaddr += begin[i];
+            b.dPkts += begin[i];
+            b.dOctets += begin[i];
+            b.first += begin[i];
+            b.last += begin[i];
+        }
+        GNM_TRY(gnm_stream_submit(s, &b, wids[i], close_flags ? close_flags[i] : 0));
+        *n_accepted = i + 1;
+    }
+    return GNM_OK;
+}
+
 gnm_status gnm_stream_submit(gnm_stream* s, const gnm_records* b, uint64_t wid, int close_window) {
     if (!s || !b) return fail(GNM_E_INVAL, "NULL argument");
     if (b->n > 0xFFFFFFFFull) return fail(GNM_E_INVAL, "a batch holds 2^32 records or more");

@@ -172,6 +172,7 @@ def lib():
             "gnm_stream_open": (st, [P, C.POINTER(StreamConfig), C.POINTER(P)]),
             "gnm_stream_submit": (st, [P, C.POINTER(RecordsC), U64, C.c_int]),
             "gnm_stream_poll": (st, [P, C.POINTER(WindowDone), S, C.POINTER(S), C.c_int]),
+            "gnm_stream_submit_many": (st, [P, C.POINTER(RecordsC), P, P, P, P, S, C.POINTER(S)]),
             "gnm_stream_stats_get": (st, [P, C.POINTER(StreamStats)]),
             "gnm_stream_close": (None, [P]),
             "gnm_window_process_noalloc": (st, [C.POINTER(Config), P, P, U32, U32, P, P, S, C.POINTER(RecordsC),
@@ -591,6 +592,21 @@ class Stream:
         """Closes a window with no further records."""
         empty = RecordsC()
         self.ctx._c(lib().gnm_stream_submit(self.h, C.byref(empty), window_id, 1))
+
+    def submit_many(self, pool: "Records", begin, count, window_ids, close=None) -> int:
+        """Batches that are slices [begin[i], begin[i] + count[i]) of one pool, for window_ids[i]
+        (closing it when close[i]); returns how many were taken (all, unless an error is raised)."""
+        b = np.ascontiguousarray(begin, np.uint64)
+        c = np.ascontiguousarray(count, np.uint64)
+        w = np.ascontiguousarray(window_ids, np.uint64)
+        f = None if close is None else np.ascontiguousarray(close, np.uint8)
+        n = C.c_size_t()
+        st = lib().gnm_stream_submit_many(self.h, C.byref(pool.c), _ptr(b), _ptr(c), _ptr(w), _ptr(f), b.size,
+                                          C.byref(n))
+        for wid in np.unique(w[:n.value]):
+            self._held.setdefault(int(wid), []).append(pool)
+        self.ctx._c(st)
+        return n.value
 
     def poll(self, wait_all: bool = False, queued: bool = False):
         """Windows completed since the last poll: list of (window_id, records, latency_ms, status)

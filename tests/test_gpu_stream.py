@@ -235,3 +235,46 @@ def test_served_windows_keep_rate_and_host_statistics(gnm, regs):
             np.testing.assert_array_equal(x, y)
     alone.close()
     ctx.close()
+
+
+def test_submit_many_equals_alone(gnm, regs):
+    """Batches given as slices of one pool in submit_many calls (closes among them) serve
+    every window as when it is processed alone."""
+    reg = regs["c1"]
+    rng = np.random.default_rng(23)
+    pool = fg.make_records(reg, 200_000, seed=31)
+    wins, order, empty_close = _plan_mix(rng, 8, 200_000, 20_000, empty_close_every=3)
+    ev = []
+    for w, j in order:
+        a, b = wins[w][j]
+        last = j == len(wins[w]) - 1
+        ev.append((a, b - a, w, int(last and w not in empty_close)))
+        if last and w in empty_close:
+            ev.append((0, 0, w, 1))
+    ctx = gnm.Context(window_slots=16)
+    ctx.load(reg)
+    stream = gnm.Stream(ctx, budget_bytes=2 * 20_000 * 24, n_cuda_streams=3)
+    recs = gnm.Records.host(pool)
+    done = {}
+    for k in range(0, len(ev), 5):
+        part = ev[k:k + 5]
+        n = stream.submit_many(recs, [e[0] for e in part], [e[1] for e in part], [e[2] for e in part],
+                               [e[3] for e in part])
+        assert n == len(part)
+        for wid, *_ in stream.poll():
+            done[wid] = ctx.dense(wid)
+    while len(done) < len(wins):
+        for wid, *_ in stream.poll(wait_all=True):
+            done[wid] = ctx.dense(wid)
+    stream.close()
+    alone = gnm.Context(window_slots=16)
+    alone.load(reg)
+    for w, sl in wins.items():
+        alone.process(gnm.Records.to_device(_concat(pool, sl)), w)
+        st_a, un_a, r_a, f_a = alone.dense(w)
+        np.testing.assert_array_equal(done[w][0], st_a)
+        np.testing.assert_array_equal(done[w][1], un_a)
+        assert_rates_close(done[w][2], r_a)
+        np.testing.assert_array_equal(done[w][3], f_a)
+    alone.close()
+    ctx.close()
