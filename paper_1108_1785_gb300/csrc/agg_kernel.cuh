@@ -384,21 +384,26 @@ static_assert(kRowWords * 4 == kSmemRowBytes, "host and device disagree on the s
 
 __device__ __forceinline__ void red32(uint32_t* a, uint32_t v) { atomicAdd(a, v); }
 
-// lo += v (mod 2^32); a wrap adds 2^32 to the global column g.
-__device__ __forceinline__ void add_wrap(uint32_t* lo, uint64_t* g, uint32_t v) {
+// lo += v (mod 2^32); a wrap adds 2^32 to the global column g (true then).
+__device__ __forceinline__ bool add_wrap(uint32_t* lo, uint64_t* g, uint32_t v) {
     const uint32_t old = atomicAdd(lo, v);
-    if (old > ~v) red_add(g, 1ull << 32);  // old + v >= 2^32
+    if (old <= ~v) return false;
+    red_add(g, 1ull << 32);  // old + v >= 2^32
+    return true;
 }
 
-__device__ __forceinline__ void add_wrap64(uint32_t* lo, uint64_t* g, uint64_t v) {
+__device__ __forceinline__ bool add_wrap64(uint32_t* lo, uint64_t* g, uint64_t v) {
     const uint32_t vl = (uint32_t)v;
     const uint32_t old = atomicAdd(lo, vl);
     const uint64_t h = (v >> 32) + (old > ~vl ? 1ull : 0ull);
-    if (h) red_add(g, h << 32);
+    if (!h) return false;
+    red_add(g, h << 32);
+    return true;
 }
 
 struct Smem {
     uint32_t key_base;  // keys of the current segment are relative to it (partitioned launches)
+    uint8_t* dirty;     // the window's dirty marks of 32-key accumulator groups, or null
     uint32_t* hist;     // rate statistics of the current window, offset by key_base (or null)
     unsigned long long* rmin;
     unsigned long long* rmax;
@@ -413,28 +418,36 @@ struct Smem {
     const uint32_t* reps;
 };
 
+// Marks the accumulator group of `key` (relative to sm.key_base) as written; finalisation
+// reads and clears only the rows of marked groups (the others are zero).
+__device__ __forceinline__ void touch(const Smem& sm, uint32_t key) {
+    if (sm.dirty) sm.dirty[(sm.key_base + key) >> 5] = 1;
+}
+
 // One record's contribution to shared-memory row r (gk: the key's global row).
 __device__ __forceinline__ void srow_add(const Smem& sm, int r, const Item& it, uint64_t* gk) {
     uint32_t* w = sm.t + r * kRowWords;
     red32(w, it.elig ? 0x10001u : 1u);
-    add_wrap(w + 1, gk + 1, it.oc);
-    add_wrap(w + 2, gk + 2, it.pk);
+    bool g = add_wrap(w + 1, gk + 1, it.oc);
+    g |= add_wrap(w + 2, gk + 2, it.pk);
     if (it.elig) {
-        add_wrap(w + 3, gk + 3, it.oc);
-        add_wrap(w + 4, gk + 4, it.dur);
+        g |= add_wrap(w + 3, gk + 3, it.oc);
+        g |= add_wrap(w + 4, gk + 4, it.dur);
     }
+    if (g) touch(sm, it.key);
 }
 
-__device__ __forceinline__ void srow_add_sums(const Smem& sm, int r, uint32_t n, uint32_t ne, uint64_t oc,
-                                              uint64_t pk, uint64_t eoc, uint64_t edur, uint64_t* gk) {
+__device__ __forceinline__ void srow_add_sums(const Smem& sm, int r, uint32_t key, uint32_t n, uint32_t ne,
+                                              uint64_t oc, uint64_t pk, uint64_t eoc, uint64_t edur, uint64_t* gk) {
     uint32_t* w = sm.t + r * kRowWords;
     red32(w, n | (ne << 16));
-    add_wrap64(w + 1, gk + 1, oc);
-    add_wrap64(w + 2, gk + 2, pk);
+    bool g = add_wrap64(w + 1, gk + 1, oc);
+    g |= add_wrap64(w + 2, gk + 2, pk);
     if (ne) {
-        add_wrap64(w + 3, gk + 3, eoc);
-        add_wrap64(w + 4, gk + 4, edur);
+        g |= add_wrap64(w + 3, gk + 3, eoc);
+        g |= add_wrap64(w + 4, gk + 4, edur);
     }
+    if (g) touch(sm, key);
 }
 
 // Sum of a 32-bit value over the lanes of `peers`, exact in 64 bits (16-bit halves).
@@ -490,8 +503,12 @@ __device__ __forceinline__ void group_add(const Item& it, unsigned peers, int r,
     }
     if ((int)(threadIdx.x & 31u) != __ffs(peers) - 1) return;
     uint64_t* gk = gacc + (size_t)it.key * kAccCols;
-    if (r >= 0) srow_add_sums(sm, r, n, ne, oc, pk, eoc, edur, gk);
-    else row_add_sums(gk, ((uint64_t)n << 32) | ne, oc, pk, eoc, edur, ne != 0);
+    if (r >= 0) {
+        srow_add_sums(sm, r, it.key, n, ne, oc, pk, eoc, edur, gk);
+    } else {
+        touch(sm, it.key);
+        row_add_sums(gk, ((uint64_t)n << 32) | ne, oc, pk, eoc, edur, ne != 0);
+    }
 }
 
 // Accumulate one item per lane. Warp-collective: every lane of the warp calls it
@@ -544,6 +561,7 @@ __device__ __forceinline__ void flush_counts(const Smem& sm, uint64_t* gacc) {
         uint32_t* w = sm.t + r * kRowWords;
         const uint32_t cnt = w[0];
         if ((cnt & 0x80008000u) == 0u) continue;
+        touch(sm, r);
         red_add(gacc + (size_t)r * kAccCols, ((uint64_t)(cnt & 0xFFFFu) << 32) | (cnt >> 16));
         w[0] = 0;
     }
@@ -563,6 +581,7 @@ __device__ __forceinline__ void flush(const Smem& sm, uint64_t* gacc) {
         // a row can hold only wrap-carried sums (count 0 is impossible after an add)
         if (cnt == 0 && (w[1] | w[2] | w[3] | w[4]) == 0) continue;
         const uint32_t ef = cnt >> 16;
+        touch(sm, key);
         row_add_sums(gacc + (size_t)key * kAccCols, ((uint64_t)(cnt & 0xFFFFu) << 32) | ef, w[1], w[2], w[3], w[4],
                      ef != 0 || (w[3] | w[4]) != 0);
 #pragma unroll
@@ -587,18 +606,34 @@ __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot,
     const uint32_t nk = 2u * p.n_sites;
     double* rate = p.rate + (size_t)slot * nk;
     uint8_t* flag = p.flag + (size_t)slot * nk;
+    uint8_t* dg = p.dirty ? p.dirty + (size_t)slot * p.dirty_groups : nullptr;
+    // k0 and step are such that a warp's lanes take the 32 keys of one group per pass (k0 is
+    // a multiple of 32 plus the lane, step a multiple of 32); the loop is warp-uniform
+    const uint32_t lane = threadIdx.x & 31u;
 #pragma unroll 1
-    for (uint32_t k = k0; k < keys; k += step) {
+    for (uint32_t kb = k0 - lane; kb < keys; kb += step) {
+        const uint32_t k = kb + lane;
+        // accumulator rows of an unmarked group are zero: neither read nor cleared
+        const bool dirty = !dg || (kL1 ? dg[kb >> 5] : __ldcg(dg + (kb >> 5))) != 0;
+        __syncwarp();
+        if (dg && dirty && lane == 0) dg[kb >> 5] = 0;
+        if (k >= keys) continue;
         uint64_t* a = acc + (size_t)k * kAccCols;
         auto ld64 = [](const uint64_t* q) -> uint64_t {
             return kL1 ? *q : __ldcg(reinterpret_cast<const unsigned long long*>(q));
         };
         auto ld32 = [](const uint32_t* q) -> uint32_t { return kL1 ? __ldg(q) : __ldcg(q); };
-        uint64_t packed = ld64(a);
-        uint64_t oc = ld64(a + 1);
-        uint64_t pk = ld64(a + 2);
-        uint64_t eo = ld64(a + 3);
-        uint64_t ed = ld64(a + 4);
+        uint64_t packed = 0, oc = 0, pk = 0, eo = 0, ed = 0;
+        if (dirty) {
+            packed = ld64(a);
+            oc = ld64(a + 1);
+            pk = ld64(a + 2);
+            eo = ld64(a + 3);
+            ed = ld64(a + 4);
+            // accumulators return to zero for the slot's next window
+#pragma unroll
+            for (int c = 0; c < kAccCols; ++c) a[c] = 0;
+        }
         const uint32_t* kp = parts + (size_t)k * kRowWords;
         uint32_t np = n_parts;
         if (p.part_groups) {
@@ -617,9 +652,6 @@ __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot,
             ed += ld32(w + 4);
         }
         const uint64_t ef = packed & 0xFFFFFFFFull;
-        // accumulators return to zero for the slot's next window
-#pragma unroll
-        for (int c = 0; c < kAccCols; ++c) a[c] = 0;
         uint64_t* s = st + (size_t)k * kNStat;
         s[0] = packed >> 32;
         s[1] = oc;
@@ -926,6 +958,7 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
                 LOOKUP == kLookupRmi ? p.rmi.n_leaves : 0u, p.radix_bits, &off_keys, &off_lookup);
     Smem sm;
     sm.key_base = 0u;
+    sm.dirty = nullptr;
     sm.hist = nullptr;
     sm.rmin = nullptr;
     sm.rmax = nullptr;
@@ -946,6 +979,7 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
         // (a segment of a partitioned launch holds keys relative to its group's first key)
         uint64_t* gacc = p.acc + ((size_t)wd.slot * p.keys + wd.key_base) * kAccCols;
         sm.key_base = wd.key_base;
+        sm.dirty = p.dirty ? p.dirty + (size_t)wd.slot * p.dirty_groups : nullptr;
         if (p.hist) {
             const size_t k0 = (size_t)wd.slot * 2u * p.n_sites + wd.key_base;
             sm.hist = p.hist + k0 * kRateBuckets;
@@ -1013,6 +1047,7 @@ __global__ void __launch_bounds__(keys_block_max(LOOKUP, U)) k_keys(const __grid
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem sm;
     sm.key_base = 0u;
+    sm.dirty = nullptr;
     sm.hist = nullptr;
     sm.rmin = nullptr;
     sm.rmax = nullptr;
@@ -1046,16 +1081,30 @@ __global__ void __launch_bounds__(keys_block_max(LOOKUP, U)) k_keys(const __grid
     }
     constexpr int R = 4 * U;
     const uint64_t G = (a1 - a0) >> 2;
+    // one group per thread: the next step's addresses are loaded before this step's
+    // lookups, so that their memory latency overlaps them (two groups per thread have no
+    // registers left for it)
+    constexpr bool kPre = U == 1;
+    uint4 pre_s = make_uint4(0, 0, 0, 0), pre_d = pre_s;
+    auto fetch = [&](uint64_t gb) {
+        const uint64_t g = gb + tid;
+        const uint64_t i = a0 + 4u * (g < G ? g : 0u);
+        pre_s = ld_stream4(p.src + i);
+        pre_d = ld_stream4(p.dst + i);
+    };
+    if (kPre && G) fetch(0);
     for (uint64_t gb = 0; gb < G; gb += T * U) {
         bool v[R];
         uint32_t s[R], d[R], x[R], site[R];
         bool sl[R], dl[R];
+        const uint4 cur_s = pre_s, cur_d = pre_d;
+        if (kPre && gb + T < G) fetch(gb + T);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint64_t g = gb + (uint64_t)u * T + tid;
             const bool ok = g < G;
             const uint64_t i = a0 + 4u * (ok ? g : 0u);
-            const uint4 vs = ld_stream4(p.src + i), vd = ld_stream4(p.dst + i);
+            const uint4 vs = kPre ? cur_s : ld_stream4(p.src + i), vd = kPre ? cur_d : ld_stream4(p.dst + i);
             s[4 * u + 0] = vs.x; s[4 * u + 1] = vs.y; s[4 * u + 2] = vs.z; s[4 * u + 3] = vs.w;
             d[4 * u + 0] = vd.x; d[4 * u + 1] = vd.y; d[4 * u + 2] = vd.z; d[4 * u + 3] = vd.w;
 #pragma unroll

@@ -119,6 +119,7 @@ void release_slots(gnm_ctx* c) {
     c->slots.clear();
     c->slot_of.clear();
     free_dev(c->d_acc);
+    free_dev(c->d_dirty);
     free_dev(c->d_stats);
     free_dev(c->d_rate);
     free_dev(c->d_flag);
@@ -145,6 +146,7 @@ void release_slots(gnm_ctx* c) {
     c->d_med = nullptr;
     c->d_mcnt = nullptr;
     c->d_acc = nullptr;
+    c->d_dirty = nullptr;
     c->d_stats = nullptr;
     c->d_rate = nullptr;
     c->d_flag = nullptr;
@@ -461,6 +463,8 @@ gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p) {
     p->min_dur = c->cfg.min_dur_ms;
     p->admin_rule = c->cfg.admin_rule;
     p->acc = c->d_acc;
+    p->dirty = c->d_dirty;
+    p->dirty_groups = (c->keys + 31) / 32;
     p->stats = c->d_stats;
     p->rate = c->d_rate;
     p->flag = c->d_flag;
@@ -1083,6 +1087,8 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     GNM_CU(cudaMalloc(&c->d_flag, slots * 2 * n_sites));
     GNM_CU(cudaMalloc(&c->d_flag_keys, (size_t)2 * n_sites * 4));
     GNM_CU(cudaMemset(c->d_acc, 0, slots * keys * kAccCols * 8));
+    GNM_CU(cudaMalloc(&c->d_dirty, slots * ((keys + 31) / 32)));
+    GNM_CU(cudaMemset(c->d_dirty, 0, slots * ((keys + 31) / 32)));
     if (c->cfg.rate_stats) {  // per-flow rate statistics: a histogram per site key and slot
         const size_t nk = (size_t)2 * n_sites;
         GNM_CU(cudaMalloc(&c->d_hist, slots * nk * kRateBuckets * 4));

@@ -108,6 +108,7 @@ struct gnm_ctx {
     // window results
     uint32_t n_slots = 0;
     uint64_t* d_acc = nullptr;
+    uint8_t* d_dirty = nullptr;   // [slots][ceil(keys / 32)] written-group marks of d_acc
     uint64_t* d_stats = nullptr;
     double* d_rate = nullptr;
     uint8_t* d_flag = nullptr;

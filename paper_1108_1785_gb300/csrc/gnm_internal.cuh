@@ -95,6 +95,9 @@ struct AggParams {
     int32_t admin_rule;
     // results
     uint64_t* acc;               // [slots][keys][kAccCols] accumulators (zeroed per window)
+    uint8_t* dirty;              // [slots][dirty_groups]: nonzero when a launch may have written an
+                                 // accumulator row of the 32-key group since it was last finalised
+                                 // (null: every row is read)
     uint64_t* stats;             // [slots][keys][kNStat] finalised sums
     uint32_t* hist;              // [slots][2*n_sites][kRateBuckets] rate histograms, or null
     unsigned long long* rmin;    // [slots][2*n_sites] least rate (bits of a double >= 0)
@@ -108,7 +111,7 @@ struct AggParams {
     uint32_t keys;               // 2*n_sites + 4
     uint32_t table_rows;         // rows of a direct shared-memory table: keys, or one key group
     uint32_t part_groups;        // key groups per window of a partitioned launch (0: none)
-    uint32_t pad2;
+    uint32_t dirty_groups;       // ceil(keys / 32)
     const uint2* part_desc;      // [window][group]: (first partial block, blocks) of a partitioned launch
     uint32_t table_cap;          // shared-memory hash slots (table mode 1)
     uint32_t min_flows;

@@ -301,6 +301,34 @@ def test_hot_key_counts_do_not_wrap(gnm, which):
     ctx.close()
 
 
+@pytest.mark.parametrize("cfg", [{}, {"table_mode": "PARTITION"}, {"table_mode": "HASH", "hash_slots": 1024},
+                                 {"table_mode": "GLOBAL"}])
+def test_one_slot_reused_after_global_sums(gnm, cfg):
+    """One result slot for a sequence of windows: a hot key whose counts are handed to the
+    global accumulators between pieces, 32-bit sums that wrap (octets near 2^32), a tiny
+    window and a plain one. Finalisation reads only the accumulator groups that a launch
+    wrote, and clears them, so every window equals the oracle."""
+    reg = fg.registry_c2()
+    kw = {k: getattr(gnm, "TABLE_" + v) if k == "table_mode" else v for k, v in cfg.items()}
+    if kw.get("table_mode") == gnm.TABLE_PARTITION:
+        reg = fg.registry_c3()
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    rng = np.random.default_rng(61)
+    hot = fg.make_records(reg, 3_000_000, seed=62)
+    pick = rng.random(hot["srcaddr"].size) < 0.8
+    inside = np.nonzero(reg.site == reg.site[-1])[0][0]
+    hot["srcaddr"] = np.where(pick, np.uint32(int(reg.prefix[inside]) + 1), hot["srcaddr"]).astype(np.uint32)
+    hot["dstaddr"] = np.where(pick, np.uint32(int(reg.local_prefix[0]) + 9), hot["dstaddr"]).astype(np.uint32)
+    big = fg.make_records(reg, 400_000, seed=63)
+    big["dOctets"] = (np.uint32(0xFFFF0000) + (big["dOctets"] & np.uint32(0xFFFF))).astype(np.uint32)
+    wins = [hot, big, fg.make_records(reg, 37, seed=64), fg.make_records(reg, 500_000, seed=65), hot]
+    ctx = _ctx(gnm, reg, window_slots=1, **kw)
+    for w, rec in enumerate(wins):
+        ctx.process(gnm.Records.to_device(rec), 700 + w)
+        assert_window_matches(ctx.dense(700 + w), oracle_full(reg, rec, lpm=lpm))
+    ctx.close()
+
+
 @pytest.mark.parametrize("which", ["c1", "c2"])
 def test_host_records_in_place_and_staged(gnm, c1, which):
     """Page-locked host records read in place by the kernels, the same staged through a
