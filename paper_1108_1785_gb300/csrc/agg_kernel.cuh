@@ -358,11 +358,12 @@ __device__ __forceinline__ void red_add(uint64_t* a, uint64_t v) {
 }
 
 // Adds summed contributions to a key's global accumulator row (5 u64 columns; column 0
-// packs flows << 32 | e_flows, which cannot carry: a window holds < 2^32 records).
-__device__ __forceinline__ void row_add_sums(uint64_t* row, uint64_t packed, uint64_t oc,
+// packs flows << 32 | e_flows, which cannot carry: a window holds < 2^32 records; column
+// 1 holds the octets of ineligible flows, column 3 those of eligible ones).
+__device__ __forceinline__ void row_add_sums(uint64_t* row, uint64_t packed, uint64_t neoc,
                                              uint64_t pk, uint64_t eoc, uint64_t edur, bool any_e) {
     red_add(row + 0, packed);
-    red_add(row + 1, oc);
+    red_add(row + 1, neoc);
     red_add(row + 2, pk);
     if (any_e) {
         red_add(row + 3, eoc);
@@ -373,8 +374,10 @@ __device__ __forceinline__ void row_add_sums(uint64_t* row, uint64_t packed, uin
 // Per-CTA sums in shared memory use 32-bit atomics (64-bit shared atomics serialise the
 // lanes of a warp). A row is 5 words, stride 5 (odd, so random rows spread over the 32
 // banks):
-//   [0] flows (bits 0-15) | e_flows (bits 16-31)   [1] octets  [2] pkts  [3] e_octets
-//   [4] e_dur
+//   [0] flows (bits 0-15) | e_flows (bits 16-31)   [1] octets of ineligible flows
+//   [2] pkts  [3] e_octets  [4] e_dur
+// A flow's octets go to [1] or [3] (one atomic, its address picked per lane); the total
+// is [1] + [3], formed at finalisation.
 // The counts cannot wrap because a CTA flushes at least every kFlushRecords records. The
 // sums keep their low 32 bits; the lane whose add wraps a word adds 2^32 to the key's
 // global accumulator column directly (rare: a word wraps once per ~4 GB of octets), so
@@ -428,12 +431,10 @@ __device__ __forceinline__ void touch(const Smem& sm, uint32_t key) {
 __device__ __forceinline__ void srow_add(const Smem& sm, int r, const Item& it, uint64_t* gk) {
     uint32_t* w = sm.t + r * kRowWords;
     red32(w, it.elig ? 0x10001u : 1u);
-    bool g = add_wrap(w + 1, gk + 1, it.oc);
+    const int co = it.elig ? 3 : 1;
+    bool g = add_wrap(w + co, gk + co, it.oc);
     g |= add_wrap(w + 2, gk + 2, it.pk);
-    if (it.elig) {
-        g |= add_wrap(w + 3, gk + 3, it.oc);
-        g |= add_wrap(w + 4, gk + 4, it.dur);
-    }
+    if (it.elig) g |= add_wrap(w + 4, gk + 4, it.dur);
     if (g) touch(sm, it.key);
 }
 
@@ -441,7 +442,7 @@ __device__ __forceinline__ void srow_add_sums(const Smem& sm, int r, uint32_t ke
                                               uint64_t oc, uint64_t pk, uint64_t eoc, uint64_t edur, uint64_t* gk) {
     uint32_t* w = sm.t + r * kRowWords;
     red32(w, n | (ne << 16));
-    bool g = add_wrap64(w + 1, gk + 1, oc);
+    bool g = add_wrap64(w + 1, gk + 1, oc - eoc);
     g |= add_wrap64(w + 2, gk + 2, pk);
     if (ne) {
         g |= add_wrap64(w + 3, gk + 3, eoc);
@@ -507,7 +508,7 @@ __device__ __forceinline__ void group_add(const Item& it, unsigned peers, int r,
         srow_add_sums(sm, r, it.key, n, ne, oc, pk, eoc, edur, gk);
     } else {
         touch(sm, it.key);
-        row_add_sums(gk, ((uint64_t)n << 32) | ne, oc, pk, eoc, edur, ne != 0);
+        row_add_sums(gk, ((uint64_t)n << 32) | ne, oc - eoc, pk, eoc, edur, ne != 0);
     }
 }
 
@@ -541,14 +542,17 @@ __device__ __forceinline__ void accumulate(const Item& it, const Smem& sm, uint3
 }
 
 // Direct tables with a partial-sum area: the CTA stores its rows (as they are, 16-bit
-// counts and low 32-bit sums) to its own block of the area with plain coalesced stores
-// and clears them; the window's last CTA adds the blocks up when it finalises.
+// counts and low 32-bit sums) to its own block of the area, column by column (word c of
+// row r at c * rows + r, so that finalisation reads each column coalesced), and clears
+// them; the window's finalisation adds the blocks up. Row stride 5 is odd: lanes reading
+// consecutive rows of one column hit 32 different banks.
 __device__ __forceinline__ void dump_rows(const Smem& sm, uint32_t* dst) {
-    const uint32_t words = sm.rows * kRowWords;
-    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) {
-        __stcg(dst + i, sm.t[i]);
-        sm.t[i] = 0;
-    }
+#pragma unroll 1
+    for (int c = 0; c < kRowWords; ++c)
+        for (uint32_t r = threadIdx.x; r < sm.rows; r += blockDim.x) {
+            __stcg(dst + (size_t)c * sm.rows + r, sm.t[r * kRowWords + c]);
+            sm.t[r * kRowWords + c] = 0;
+        }
 }
 
 // Within a CTA's segment of a window whose rows go to a partial block at its end, between
@@ -591,15 +595,19 @@ __device__ __forceinline__ void flush(const Smem& sm, uint64_t* gacc) {
 
 // Rates and flags of one window from its accumulators (Sec. III.B.1: rates per site;
 // a site is sub-optimal when its rate is below the standard). kL1: the sums were written
-// by an earlier kernel, so loads may go through L1 (the 5 word loads of a row then fetch
-// its lines from L2 once); inside the aggregation kernel they bypass L1.
+// by an earlier kernel, so loads may go through L1; inside the aggregation kernel they
+// bypass L1. Partial blocks hold table_rows rows column by column.
 // Partitioned launches (p.part_groups > 0): every key group of window `win` has its own
 // run of partial blocks of table_rows rows (p.part_desc), and `parts`/`n_parts` are unused.
+// `stage` (kNStat * 32 words of shared memory per warp, or null): a warp writes its 32
+// keys' stats rows there and stores them as one contiguous run of 16-byte words.
 template <bool kL1 = false>
 __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot, uint32_t k0,
                                               uint32_t step, const uint32_t* parts = nullptr,
-                                              uint32_t n_parts = 0, uint32_t win = 0) {
-    const uint64_t pstride = part_stride_words(p.table_rows);
+                                              uint32_t n_parts = 0, uint32_t win = 0,
+                                              uint64_t* stage = nullptr) {
+    const uint32_t rows = p.table_rows;
+    const uint64_t pstride = part_stride_words(rows);
     const size_t keys = p.keys;
     uint64_t* acc = p.acc + (size_t)slot * keys * kAccCols;
     uint64_t* st = p.stats + (size_t)slot * keys * kNStat;
@@ -607,65 +615,90 @@ __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot,
     double* rate = p.rate + (size_t)slot * nk;
     uint8_t* flag = p.flag + (size_t)slot * nk;
     uint8_t* dg = p.dirty ? p.dirty + (size_t)slot * p.dirty_groups : nullptr;
+    auto ld64 = [](const uint64_t* q) -> uint64_t {
+        return kL1 ? *q : __ldcg(reinterpret_cast<const unsigned long long*>(q));
+    };
+    auto ld32 = [](const uint32_t* q) -> uint32_t { return kL1 ? __ldg(q) : __ldcg(q); };
     // k0 and step are such that a warp's lanes take the 32 keys of one group per pass (k0 is
     // a multiple of 32 plus the lane, step a multiple of 32); the loop is warp-uniform
     const uint32_t lane = threadIdx.x & 31u;
 #pragma unroll 1
     for (uint32_t kb = k0 - lane; kb < keys; kb += step) {
         const uint32_t k = kb + lane;
+        const bool act = k < keys;
         // accumulator rows of an unmarked group are zero: neither read nor cleared
         const bool dirty = !dg || (kL1 ? dg[kb >> 5] : __ldcg(dg + (kb >> 5))) != 0;
         __syncwarp();
         if (dg && dirty && lane == 0) dg[kb >> 5] = 0;
-        if (k >= keys) continue;
-        uint64_t* a = acc + (size_t)k * kAccCols;
-        auto ld64 = [](const uint64_t* q) -> uint64_t {
-            return kL1 ? *q : __ldcg(reinterpret_cast<const unsigned long long*>(q));
-        };
-        auto ld32 = [](const uint32_t* q) -> uint32_t { return kL1 ? __ldg(q) : __ldcg(q); };
-        uint64_t packed = 0, oc = 0, pk = 0, eo = 0, ed = 0;
-        if (dirty) {
-            packed = ld64(a);
-            oc = ld64(a + 1);
-            pk = ld64(a + 2);
-            eo = ld64(a + 3);
-            ed = ld64(a + 4);
-            // accumulators return to zero for the slot's next window
+        uint64_t sv[kNStat] = {0, 0, 0, 0, 0, 0};
+        if (act) {
+            uint64_t* a = acc + (size_t)k * kAccCols;
+            uint64_t packed = 0, oc = 0, pk = 0, eo = 0, ed = 0;
+            if (dirty) {
+                packed = ld64(a);
+                oc = ld64(a + 1);
+                pk = ld64(a + 2);
+                eo = ld64(a + 3);
+                ed = ld64(a + 4);
+                // accumulators return to zero for the slot's next window
 #pragma unroll
-            for (int c = 0; c < kAccCols; ++c) a[c] = 0;
+                for (int c = 0; c < kAccCols; ++c) a[c] = 0;
+            }
+            const uint32_t* kp = parts + k;
+            uint32_t np = n_parts;
+            if (p.part_groups) {
+                const uint32_t g = k / rows;
+                const uint2 pd = p.part_desc[(size_t)win * p.part_groups + g];
+                kp = p.partials + (size_t)pd.x * pstride + (k - g * rows);
+                np = p.partials ? pd.y : 0u;
+            }
+            // partial blocks of the window's CTAs, four at a time (their loads in flight together)
+            for (uint32_t q0 = 0; q0 < np; q0 += 4) {
+                uint32_t v[4][kRowWords];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t* w = kp + (size_t)(q0 + j) * pstride;
+#pragma unroll
+                    for (int c = 0; c < kRowWords; ++c) v[j][c] = q0 + j < np ? ld32(w + (size_t)c * rows) : 0u;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    packed += ((uint64_t)(v[j][0] & 0xFFFFu) << 32) | (v[j][0] >> 16);
+                    oc += v[j][1];
+                    pk += v[j][2];
+                    eo += v[j][3];
+                    ed += v[j][4];
+                }
+            }
+            const uint64_t ef = packed & 0xFFFFFFFFull;
+            sv[0] = packed >> 32;
+            sv[1] = oc + eo;  // ineligible and eligible flows' octets
+            sv[2] = pk;
+            sv[3] = ef;
+            sv[4] = eo;
+            sv[5] = ed;
+            if (k < nk) {
+                // rate = (octets * 8 bits) / (ms / 1000), one rounding per operation
+                const double r = ed ? __ddiv_rn(__dmul_rn(__ull2double_rn(eo), 8000.0),
+                                                __ull2double_rn(ed))
+                                    : __longlong_as_double(0x7FF8000000000000ll);
+                rate[k] = r;
+                flag[k] = (ef >= (uint64_t)p.min_flows && r < p.threshold) ? 1 : 0;
+            }
         }
-        const uint32_t* kp = parts + (size_t)k * kRowWords;
-        uint32_t np = n_parts;
-        if (p.part_groups) {
-            const uint32_t g = k / p.table_rows;
-            const uint2 pd = p.part_desc[(size_t)win * p.part_groups + g];
-            kp = p.partials + (size_t)pd.x * pstride + (size_t)(k - g * p.table_rows) * kRowWords;
-            np = p.partials ? pd.y : 0u;
-        }
-        for (uint32_t q = 0; q < np; ++q) {  // partial blocks of the window's CTAs
-            const uint32_t* w = kp + (size_t)q * pstride;
-            const uint32_t cnt = ld32(w);
-            packed += ((uint64_t)(cnt & 0xFFFFu) << 32) | (cnt >> 16);
-            oc += ld32(w + 1);
-            pk += ld32(w + 2);
-            eo += ld32(w + 3);
-            ed += ld32(w + 4);
-        }
-        const uint64_t ef = packed & 0xFFFFFFFFull;
-        uint64_t* s = st + (size_t)k * kNStat;
-        s[0] = packed >> 32;
-        s[1] = oc;
-        s[2] = pk;
-        s[3] = ef;
-        s[4] = eo;
-        s[5] = ed;
-        if (k < nk) {
-            // rate = (octets * 8 bits) / (ms / 1000), one rounding per operation
-            const double r = ed ? __ddiv_rn(__dmul_rn(__ull2double_rn(eo), 8000.0),
-                                            __ull2double_rn(ed))
-                                : __longlong_as_double(0x7FF8000000000000ll);
-            rate[k] = r;
-            flag[k] = (ef >= (uint64_t)p.min_flows && r < p.threshold) ? 1 : 0;
+        if (stage) {  // the warp's keys [kb, kb + n) are kNStat * 8 * n contiguous bytes
+            const uint32_t n = (uint32_t)min((size_t)32, keys - kb);
+#pragma unroll
+            for (int c = 0; c < kNStat; ++c) stage[lane * kNStat + c] = sv[c];
+            __syncwarp();
+            const uint4* src4 = reinterpret_cast<const uint4*>(stage);
+            uint4* dst4 = reinterpret_cast<uint4*>(st + (size_t)kb * kNStat);
+            for (uint32_t i = lane; i < n * (kNStat / 2); i += 32u) dst4[i] = src4[i];
+            __syncwarp();
+        } else if (act) {
+            uint64_t* s = st + (size_t)k * kNStat;
+#pragma unroll
+            for (int c = 0; c < kNStat; ++c) s[c] = sv[c];
         }
     }
 }
@@ -1029,7 +1062,7 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
         __syncthreads();
         if (s_last && (wd.flags & kWinFinalize)) {
             if (TABLE == kTableDirect && p.partials)
-                finalize_rows(p, wd.slot, tid, B, p.partials + (size_t)wd.part_base * part_stride_words(p.keys),
+                finalize_rows(p, wd.slot, tid, B, p.partials + (size_t)wd.part_base * part_stride_words(p.table_rows),
                               wd.n_parts);
             else
                 finalize_rows(p, wd.slot, tid, B);

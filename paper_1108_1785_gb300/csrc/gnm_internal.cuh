@@ -12,7 +12,7 @@ namespace gnm {
 constexpr uint32_t kNoSite = GNM_NO_SITE;
 constexpr int kNStat = GNM_NSTAT;   // columns of a user-facing stats row
 constexpr uint32_t kRateBuckets = GNM_RATE_BUCKETS;  // 10 kb/s buckets, the last for >= 100 Mb/s
-constexpr int kAccCols = 5;         // accumulator row: flows<<32|e_flows, oct, pkts, e_oct, e_dur
+constexpr int kAccCols = 5;         // accumulator row: flows<<32|e_flows, ineligible oct, pkts, e_oct, e_dur
 constexpr size_t kSmemRowBytes = 20;  // per-CTA shared-memory row: packed counts + 4 low words
 constexpr int kUnmatched = 4;       // classes appended after the 2*n_sites site rows
 constexpr int kMaxLeaves = 65536;

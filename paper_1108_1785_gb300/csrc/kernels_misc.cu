@@ -62,11 +62,12 @@ __global__ void k_finalize(const __grid_constant__ AggParams p, uint32_t slot) {
 constexpr uint32_t kFinKeys = 256;
 
 __global__ void __launch_bounds__(kFinKeys) k_finalize_windows(const __grid_constant__ AggParams p) {
+    __shared__ __align__(16) uint64_t stage[kFinKeys * kNStat];  // per warp: 32 keys' stats rows
     const WinDesc wd = p.wins[blockIdx.y];
     const uint32_t* parts =
         p.partials ? p.partials + (size_t)wd.part_base * part_stride_words(p.table_rows) : nullptr;
     dev::finalize_rows<true>(p, wd.slot, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, parts,
-                             p.partials ? wd.n_parts : 0u, blockIdx.y);
+                             p.partials ? wd.n_parts : 0u, blockIdx.y, stage + (threadIdx.x & ~31u) * kNStat);
 }
 
 // One warp per key: the key's eligible flows (the histogram's total) and the bucket where
@@ -214,9 +215,25 @@ cudaError_t launch_finalize(const AggParams& p, uint32_t slot, cudaStream_t st) 
 
 cudaError_t launch_finalize_windows(const AggParams& p, cudaStream_t st) {
     if (p.n_wins == 0) return cudaSuccess;
-    // key blocks per window: all of them, up to about 2048 CTAs over the windows
+    // key blocks per window: all of them, up to one wave of resident CTAs over the windows
+    // (the threads then loop over their keys, so that the warps of an SM are in different
+    // phases -- loads, FP64 rates, stores -- instead of moving through waves in step)
+    static int resident[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int res = dev < 64 ? resident[dev] : 0;
+    if (res == 0) {
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_finalize_windows, kFinKeys, 0);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        res = std::max(1, per_sm * sms);
+        if (dev < 64) resident[dev] = res;
+    }
     const uint32_t bx = (p.keys + kFinKeys - 1) / kFinKeys;
-    const uint32_t cap = std::max<uint32_t>(64u, 2048u / p.n_wins);
+    const uint32_t cap = std::max<uint32_t>(1u, (uint32_t)res / p.n_wins);
     (void)cudaGetLastError();
     k_finalize_windows<<<dim3(std::min(bx, cap), p.n_wins), kFinKeys, 0, st>>>(p);
     return cudaGetLastError();
