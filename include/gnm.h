@@ -455,14 +455,18 @@ uint32_t gnm_last_launch_count(const gnm_ctx *ctx);
  * window's rates and flags (Sec. III.B.2.1) are final once its closing batch is processed.
  *
  * Admission: the records of admitted, unfinished batches (24 bytes each) never exceed
- * budget_bytes. Host batches are copied into a device arena of budget_bytes owned by the
- * server; device batches only count against the budget. A batch that does not fit waits
+ * budget_bytes. Host batches in page-locked, device-mapped memory are read in place by the
+ * kernels over the host link when the context's host_records is AUTO or IN_PLACE (no copy,
+ * no arena space); other host batches are copied into a device arena of budget_bytes owned
+ * by the server (IN_PLACE refuses them with GNM_E_INVAL); device batches only count
+ * against the budget. A batch that does not fit waits
  * in a FIFO queue; a window's first batch also waits while every result slot is held by
  * an open window (later batches of open windows pass it). Queued batches are admitted in
  * gnm_stream_submit and gnm_stream_poll as earlier batches finish (continuous batching).
- * Each admitted batch is copied and processed on the next of n_cuda_streams CUDA streams,
- * so the copies of some batches overlap the kernels of others; the kernels of one window
- * run in submission order, those of different windows overlap.
+ * Each admitted batch is copied (if staged) and processed on the next of n_cuda_streams
+ * CUDA streams, so the copies of some batches overlap the kernels of others; the kernels of
+ * one window run in submission order, those of different windows overlap. The caller keeps
+ * a host batch's arrays unchanged until its window is reported.
  *
  * Window latency = host time from the gnm_stream_submit call that closes the window to
  * the completion of its finalisation on the device (a host callback queued after it).

@@ -100,7 +100,25 @@ struct Batch {
     uint64_t arena_off = 0, arena_bytes = 0;
     cudaEvent_t ev = nullptr;   // recorded after the batch's kernels
     int stream = 0;
+    bool in_place = false;      // host batch read by the kernels at dev[] (mapped memory)
+    const uint32_t* dev[6] = {};
 };
+
+// Device addresses of a host batch's six arrays when all of them are page-locked host
+// memory mapped for the device; false otherwise.
+bool mapped_fields(const gnm_records* r, const uint32_t* out[6]) {
+    const uint32_t* f[6] = {r->srcaddr, r->dstaddr, r->dPkts, r->dOctets, r->first, r->last};
+    for (int k = 0; k < 6; ++k) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, f[k]) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return false;
+        out[k] = static_cast<const uint32_t*>(a.devicePointer);
+    }
+    return true;
+}
 
 void CUDART_CB on_window_done(void* arg) {
     // runs on the CUDA callback thread once the finalisation has completed; no CUDA calls
@@ -215,7 +233,11 @@ gnm_status enqueue(gnm_stream* s, Batch& b, Win& w) {
     const uint64_t n = b.rec.n;
     if (n && !w.failed) {
         gnm_records dr = b.rec;
-        if (!b.rec.on_device) {
+        if (b.in_place) {
+            dr.srcaddr = b.dev[0]; dr.dstaddr = b.dev[1]; dr.dPkts = b.dev[2];
+            dr.dOctets = b.dev[3]; dr.first = b.dev[4]; dr.last = b.dev[5];
+            dr.on_device = 1;
+        } else if (!b.rec.on_device) {
             const uint32_t* src[6] = {b.rec.srcaddr, b.rec.dstaddr, b.rec.dPkts, b.rec.dOctets, b.rec.first, b.rec.last};
             const uint32_t* dst[6];
             const uint64_t field = round_up(n * 4, kArenaAlign);
@@ -264,7 +286,7 @@ gnm_status admit(gnm_stream* s, bool* progressed) {
         }
         if (s->inflight_bytes + b.bytes > s->cfg.budget_bytes) break;
         b.arena_bytes = 0;
-        if (b.rec.n && !b.rec.on_device && !w.failed) {
+        if (b.rec.n && !b.rec.on_device && !b.in_place && !w.failed) {
             const uint64_t need = 6 * round_up(b.rec.n * 4, kArenaAlign);
             if (!s->arena.alloc(need, &b.arena_off)) break;
             b.arena_bytes = need;
@@ -312,6 +334,76 @@ gnm_status pump(gnm_stream* s, bool* progressed) {
     s->to_unpin.clear();
     GNM_TRY(retire(s));
     return admit(s, progressed);
+}
+
+// Placement of a host batch under the context's host_records: in place (dev filled) when
+// mapped and allowed, else staged; IN_PLACE refuses unmapped arrays.
+gnm_status host_placement(gnm_stream* s, const gnm_records* b, bool* in_place, const uint32_t* dev[6]) {
+    *in_place = false;
+    if (!b->n || b->on_device || s->c->cfg.host_records == GNM_HOST_STAGE) return GNM_OK;
+    *in_place = mapped_fields(b, dev);
+    if (!*in_place && s->c->cfg.host_records == GNM_HOST_IN_PLACE)
+        return fail(GNM_E_INVAL, "host_records IN_PLACE: the batch's arrays are not device-addressable "
+                                 "page-locked host memory");
+    return GNM_OK;
+}
+
+// Takes a batch (checked here); dev: the device addresses of a host batch read in place, or null.
+gnm_status submit_batch(gnm_stream* s, const gnm_records* b, uint64_t wid, int close_window,
+                        const uint32_t* const* dev) {
+    if (b->n > 0xFFFFFFFFull) return fail(GNM_E_INVAL, "a batch holds 2^32 records or more");
+    if (b->n * kRecordBytes > s->cfg.budget_bytes)
+        return fail(GNM_E_INVAL, "batch of " + std::to_string(b->n) + " records exceeds the budget");
+    if (b->n) {
+        const uint32_t* f[6] = {b->srcaddr, b->dstaddr, b->dPkts, b->dOctets, b->first, b->last};
+        for (auto* q : f)
+            if (!q || ((uintptr_t)q & 3u)) return fail(GNM_E_INVAL, "record arrays must be non-NULL and 4-byte aligned");
+    }
+    auto it = s->wins.find(wid);
+    if (it != s->wins.end() && it->second->close_submitted)
+        return fail(GNM_E_STATE, "window " + std::to_string(wid) + " is already closed");
+    GNM_CU(cudaSetDevice(s->c->device));
+    const bool new_window = it == s->wins.end();
+    if (new_window) {
+        auto w = std::make_unique<Win>();
+        w->wid = wid;
+        it = s->wins.emplace(wid, std::move(w)).first;
+    }
+    Win& w = *it->second;
+    Batch q;
+    q.rec = *b;
+    q.wid = wid;
+    q.seq = ++s->seq;
+    q.close = close_window != 0;
+    q.bytes = b->n * kRecordBytes;
+    if (dev) {
+        q.in_place = true;
+        for (int k = 0; k < 6; ++k) q.dev[k] = dev[k];
+    }
+    if (q.close) {
+        w.close_submitted = true;
+        w.t_close = now_ns();
+    }
+    s->queue.push_back(q);
+    ++s->st.batches;
+    s->st.records += b->n;
+    bool progressed;
+    GNM_TRY(pump(s, &progressed));
+    if (!s->queue.empty() && s->queue.back().seq == q.seq) {  // not admitted: it has to wait
+        if (s->queue.size() > s->cfg.max_queued) {  // no room: take it back
+            s->queue.pop_back();
+            --s->st.batches;
+            s->st.records -= b->n;
+            if (q.close) {
+                w.close_submitted = false;
+                w.t_close = 0;
+            }
+            if (new_window) s->wins.erase(wid);
+            return fail(GNM_E_CAPACITY, "admission queue is full");
+        }
+        ++s->st.batches_queued;
+    }
+    return GNM_OK;
 }
 
 double percentile(std::vector<double> v, double q) {  // nearest rank
@@ -385,11 +477,18 @@ gnm_status gnm_stream_submit_many(gnm_stream* s, const gnm_records* pool, const 
     if (!s || !pool || !n_accepted || (n_batches && (!begin || !count || !wids)))
         return fail(GNM_E_INVAL, "NULL argument");
     *n_accepted = 0;
+    GNM_CU(cudaSetDevice(s->c->device));
+    // the pool's placement is decided once for all its slices
+    bool in_place = false;
+    const uint32_t* pdev[6];
+    const bool fields = pool->srcaddr && pool->dstaddr && pool->dPkts && pool->dOctets && pool->first && pool->last;
+    if (pool->n && fields) GNM_TRY(host_placement(s, pool, &in_place, pdev));
     for (size_t i = 0; i < n_batches; ++i) {
         if (count[i] && (begin[i] > pool->n || count[i] > pool->n - begin[i]))
             return fail(GNM_E_INVAL, "batch " + std::to_string(i) + " lies outside the pool");
         gnm_records b = *pool;
         b.n = count[i];
+        const uint32_t* dev[6];
         if (count[i]) {
             b.srcaddr += begin[i];
             b.dstaddr += begin[i];
@@ -397,65 +496,27 @@ gnm_status gnm_stream_submit_many(gnm_stream* s, const gnm_records* pool, const 
             b.dOctets += begin[i];
             b.first += begin[i];
             b.last += begin[i];
+            for (int k = 0; k < 6; ++k) dev[k] = in_place ? pdev[k] + begin[i] : nullptr;
         }
-        GNM_TRY(gnm_stream_submit(s, &b, wids[i], close_flags ? close_flags[i] : 0));
+        GNM_TRY(submit_batch(s, &b, wids[i], close_flags ? close_flags[i] : 0, count[i] && in_place ? dev : nullptr));
         *n_accepted = i + 1;
     }
     return GNM_OK;
 }
 
+
 gnm_status gnm_stream_submit(gnm_stream* s, const gnm_records* b, uint64_t wid, int close_window) {
     if (!s || !b) return fail(GNM_E_INVAL, "NULL argument");
-    if (b->n > 0xFFFFFFFFull) return fail(GNM_E_INVAL, "a batch holds 2^32 records or more");
-    if (b->n * kRecordBytes > s->cfg.budget_bytes)
-        return fail(GNM_E_INVAL, "batch of " + std::to_string(b->n) + " records exceeds the budget");
-    if (b->n) {
-        const uint32_t* f[6] = {b->srcaddr, b->dstaddr, b->dPkts, b->dOctets, b->first, b->last};
-        for (auto* q : f)
-            if (!q || ((uintptr_t)q & 3u)) return fail(GNM_E_INVAL, "record arrays must be non-NULL and 4-byte aligned");
-    }
-    auto it = s->wins.find(wid);
-    if (it != s->wins.end() && it->second->close_submitted)
-        return fail(GNM_E_STATE, "window " + std::to_string(wid) + " is already closed");
     GNM_CU(cudaSetDevice(s->c->device));
-    const bool new_window = it == s->wins.end();
-    if (new_window) {
-        auto w = std::make_unique<Win>();
-        w->wid = wid;
-        it = s->wins.emplace(wid, std::move(w)).first;
-    }
-    Win& w = *it->second;
-    Batch q;
-    q.rec = *b;
-    q.wid = wid;
-    q.seq = ++s->seq;
-    q.close = close_window != 0;
-    q.bytes = b->n * kRecordBytes;
-    if (q.close) {
-        w.close_submitted = true;
-        w.t_close = now_ns();
-    }
-    s->queue.push_back(q);
-    ++s->st.batches;
-    s->st.records += b->n;
-    bool progressed;
-    GNM_TRY(pump(s, &progressed));
-    if (!s->queue.empty() && s->queue.back().seq == q.seq) {  // not admitted: it has to wait
-        if (s->queue.size() > s->cfg.max_queued) {  // no room: take it back
-            s->queue.pop_back();
-            --s->st.batches;
-            s->st.records -= b->n;
-            if (q.close) {
-                w.close_submitted = false;
-                w.t_close = 0;
-            }
-            if (new_window) s->wins.erase(wid);
-            return fail(GNM_E_CAPACITY, "admission queue is full");
-        }
-        ++s->st.batches_queued;
-    }
-    return GNM_OK;
+    bool in_place;
+    const uint32_t* dev[6];
+    if (b->n && !b->on_device && b->srcaddr && b->dstaddr && b->dPkts && b->dOctets && b->first && b->last)
+        GNM_TRY(host_placement(s, b, &in_place, dev));
+    else
+        in_place = false;
+    return submit_batch(s, b, wid, close_window, in_place ? dev : nullptr);
 }
+
 
 gnm_status gnm_stream_poll(gnm_stream* s, gnm_window_done* out, size_t cap, size_t* n_out, int wait_all) {
     if (!s || !n_out || (cap && !out)) return fail(GNM_E_INVAL, "NULL argument");

@@ -56,6 +56,13 @@ def _plan_mix(rng, n_windows, pool_n, max_batch, empty_close_every=4):
     return wins, order, empty_close
 
 
+def _pinned(pool):
+    """The pool in page-locked host memory (numpy views of pinned tensors, kept alive by the
+    returned tensors)."""
+    t = {k: torch.from_numpy(np.ascontiguousarray(pool[k]).view(np.int32)).pin_memory() for k in fg.FIELDS}
+    return t, {k: v.numpy().view(np.uint32) for k, v in t.items()}
+
+
 def _concat(pool, slices):
     return {k: np.concatenate([v[a:b] for a, b in slices]) for k, v in pool.items()}
 
@@ -84,6 +91,8 @@ def _serve(gnm, stream, pool_recs, wins, order, empty_close, read):
     ("c1", False, 2, 2, 64),    # device batches: only the budget is charged
     ("c2", True, 2, 4, 3),      # three result slots for twelve interleaved windows
     ("c3", True, 3, 4, 8),      # a key space larger than one shared-memory table
+    ("c2", "pinned", 3, 4, 64),  # page-locked host batches: read in place by the kernels
+    ("c3", "pinned", 3, 4, 8),
 ])
 def test_mix_equals_alone(gnm, regs, which, host, budget_batches, n_streams, slots):
     reg = regs[which]
@@ -91,7 +100,12 @@ def test_mix_equals_alone(gnm, regs, which, host, budget_batches, n_streams, slo
     pool = fg.make_records(reg, 300_000, seed=21)
     max_batch = 30_000
     wins, order, empty_close = _plan_mix(rng, 12, 300_000, max_batch)
-    if host:
+    if host == "pinned":
+        hold, ppool = _pinned(pool)
+
+        def recs(a, b):
+            return gnm.Records({k: v[a:b] for k, v in ppool.items()})
+    elif host:
         def recs(a, b):
             return gnm.Records.host({k: v[a:b] for k, v in pool.items()})
     else:
@@ -237,9 +251,12 @@ def test_served_windows_keep_rate_and_host_statistics(gnm, regs):
     ctx.close()
 
 
-def test_submit_many_equals_alone(gnm, regs):
+@pytest.mark.parametrize("pool_kind,host_records", [("pageable", "AUTO"), ("pinned", "AUTO"),
+                                                    ("pinned", "STAGE"), ("pinned", "IN_PLACE")])
+def test_submit_many_equals_alone(gnm, regs, pool_kind, host_records):
     """Batches given as slices of one pool in submit_many calls (closes among them) serve
-    every window as when it is processed alone."""
+    every window as when it is processed alone: a pageable pool is staged, a page-locked one
+    is read in place unless the context stages host records."""
     reg = regs["c1"]
     rng = np.random.default_rng(23)
     pool = fg.make_records(reg, 200_000, seed=31)
@@ -251,10 +268,15 @@ def test_submit_many_equals_alone(gnm, regs):
         ev.append((a, b - a, w, int(last and w not in empty_close)))
         if last and w in empty_close:
             ev.append((0, 0, w, 1))
-    ctx = gnm.Context(window_slots=16)
+    ctx = gnm.Context(window_slots=16, host_records=getattr(gnm, "HOST_" + host_records))
     ctx.load(reg)
     stream = gnm.Stream(ctx, budget_bytes=2 * 20_000 * 24, n_cuda_streams=3)
-    recs = gnm.Records.host(pool)
+    hold = None
+    if pool_kind == "pinned":
+        hold, ppool = _pinned(pool)
+        recs = gnm.Records(ppool)
+    else:
+        recs = gnm.Records.host(pool)
     done = {}
     for k in range(0, len(ev), 5):
         part = ev[k:k + 5]
@@ -276,5 +298,31 @@ def test_submit_many_equals_alone(gnm, regs):
         np.testing.assert_array_equal(done[w][1], un_a)
         assert_rates_close(done[w][2], r_a)
         np.testing.assert_array_equal(done[w][3], f_a)
+    alone.close()
+    ctx.close()
+
+
+def test_in_place_server_refuses_pageable_batches(gnm, regs):
+    """A context that reads host records only in place refuses a pageable host batch (and a
+    pool of them) and still serves page-locked ones."""
+    reg = regs["c1"]
+    pool = fg.make_records(reg, 50_000, seed=7)
+    ctx = gnm.Context(window_slots=4, host_records=gnm.HOST_IN_PLACE)
+    ctx.load(reg)
+    stream = gnm.Stream(ctx, budget_bytes=1 << 24, n_cuda_streams=2)
+    with pytest.raises(gnm.GnmError, match="INVAL"):
+        stream.submit(gnm.Records.host(pool), 1, close=True)
+    with pytest.raises(gnm.GnmError, match="INVAL"):
+        stream.submit_many(gnm.Records.host(pool), [0], [10], [1], [1])
+    hold, ppool = _pinned(pool)
+    stream.submit(gnm.Records(ppool), 2, close=True)
+    done = {wid for wid, *_ in stream.poll(wait_all=True)}
+    assert done == {2}
+    alone = gnm.Context(window_slots=4)
+    alone.load(reg)
+    alone.process(gnm.Records.to_device(pool), 2)
+    for x, y in zip(ctx.dense(2), alone.dense(2)):
+        np.testing.assert_array_equal(x, y)
+    stream.close()
     alone.close()
     ctx.close()
