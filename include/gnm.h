@@ -233,6 +233,25 @@ gnm_status gnm_window_add(gnm_ctx *ctx, const gnm_records *rec, uint64_t window_
                           void *stream);
 gnm_status gnm_window_close(gnm_ctx *ctx, uint64_t window_id, void *stream);
 
+/* Checkpoint of an open window (the paper's receiver keeps the period's records on disk
+ * until they are processed, Sec. III.B.1; here the state to keep is the window's partial
+ * sums). gnm_window_export copies the sums accumulated so far to `rows`: keys rows (keys =
+ * 2*n_sites + 4: the site keys site*2+dir, then the four unmatched classes) of GNM_NSTAT
+ * uint64 in the gnm_window_dense order (flows, octets, pkts, e_flows, e_octets, e_dur_ms).
+ * Synchronous; host memory; the window stays open. gnm_window_import opens `window_id` (as
+ * gnm_window_open) with `rows` (n_rows = keys, as exported, possibly by another context over
+ * the same registry and filters) as its sums so far; gnm_window_add then continues it and
+ * gnm_window_close finalises it exactly as if every record had been added here. Returns
+ * when the sums are on the device. Errors: GNM_E_STATE for an unknown, evicted or closed
+ * window (export), and in contexts keeping per-flow rate or per-host statistics (those are
+ * not carried); GNM_E_CAPACITY when cap < keys (*n_out = keys); GNM_E_INVAL when n_rows !=
+ * keys or a row is inconsistent (e_flows > flows, e_octets > octets, flows >= 2^32, or the
+ * flows of all rows reach 2^32). */
+gnm_status gnm_window_export(gnm_ctx *ctx, uint64_t window_id, uint64_t *rows, size_t cap,
+                             size_t *n_out);
+gnm_status gnm_window_import(gnm_ctx *ctx, uint64_t window_id, const uint64_t *rows, size_t n_rows,
+                             void *stream);
+
 /* Per-site statistics of a window (synchronises with the window's work). Writes the
  * keys with at least one flow, ordered by (site, dir), into out[0..*n_out). unmatched,
  * if not NULL, receives 4 classes x {flows, octets, pkts}: 0 neither endpoint local,

@@ -141,6 +141,8 @@ def lib():
             "gnm_window_open": (st, [P, U64, P]),
             "gnm_window_add": (st, [P, C.POINTER(RecordsC), U64, P]),
             "gnm_window_close": (st, [P, U64, P]),
+            "gnm_window_export": (st, [P, U64, P, S, C.POINTER(S)]),
+            "gnm_window_import": (st, [P, U64, P, S, P]),
             "gnm_site_stats": (st, [P, U64, C.POINTER(SiteStat), S, C.POINTER(S), P]),
             "gnm_flag_suboptimal": (st, [P, U64, C.c_double, P, P, S, C.POINTER(S)]),
             "gnm_window_dense": (st, [P, U64, P, P, P, P]),
@@ -363,6 +365,22 @@ class Context:
 
     def close_window(self, window_id: int, stream=None):
         self._c(lib().gnm_window_close(self.h, window_id, _stream_ptr(stream)))
+
+    def window_export(self, window_id: int) -> np.ndarray:
+        """The sums an open window holds so far: (2*n_sites + 4, 6) uint64 rows (flows,
+        octets, pkts, e_flows, e_octets, e_dur_ms), site keys then the unmatched classes."""
+        n = C.c_size_t()
+        st = lib().gnm_window_export(self.h, window_id, None, 0, C.byref(n))
+        if st != 5:  # GNM_E_CAPACITY: the size is in n
+            self._c(st)
+        rows = np.empty((n.value, 6), np.uint64)
+        self._c(lib().gnm_window_export(self.h, window_id, _ptr(rows), n.value, C.byref(n)))
+        return rows
+
+    def window_import(self, window_id: int, rows, stream=None):
+        """Opens `window_id` with `rows` (as window_export gives them) as its sums so far."""
+        r = np.ascontiguousarray(rows, np.uint64)
+        self._c(lib().gnm_window_import(self.h, window_id, _ptr(r), r.shape[0], _stream_ptr(stream)))
 
     def release(self, window_id: int):
         self._c(lib().gnm_window_release(self.h, window_id))
