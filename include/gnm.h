@@ -116,8 +116,11 @@ typedef struct {
                                    first start of every 2-range (4-range) block in shared
                                    memory beside a directory of block indices, and one
                                    16-byte (32-byte) load of the block's (start, site)
-                                   pairs ends a lookup; 2 = the range directory and a
-                                   search over L2; 0 = 3, else 1, whichever fits first */
+                                   pairs ends a lookup; 4 = as 3 with a 16-bit directory
+                                   over the top 16 address bits and the blocks' low 16
+                                   start bits (fewer than 65,536 blocks; GNM_E_INVAL
+                                   otherwise); 2 = the range directory and a search over
+                                   L2; 0 = 3, else 1, whichever fits first */
     int32_t host_records;       /* GNM_HOST_*: how kernels get host (on_device = 0) records */
     int32_t rate_stats;         /* 1: per-flow rate statistics per window (gnm_window_rate_stats):
                                    each result slot also holds a 10001-bucket histogram per key

@@ -175,6 +175,49 @@ __device__ __forceinline__ void radix_block(const uint32_t* dir, uint32_t bits, 
     }
 }
 
+// Block-sample search with 16-bit tables (key kernel, fewer than 2^16 blocks of 2 ranges):
+// dh[t] is the first block whose first start is >= t << 16 for the /16 bucket t of x, so the
+// block before it holds the bucket's first address and blocks dh[t] .. dh[t+1]-1 start inside
+// the bucket, where their low 16 start bits `s16` order them exactly. The last of those with
+// low bits <= x's (or the block before them) holds x; one 16-byte load of its two (start,
+// site) pairs gives the site. R lookups in lock step.
+template <int R>
+__device__ __forceinline__ void radix_block16(const uint16_t* dh, const uint16_t* s16,
+                                              const uint2* __restrict__ pairs, const uint32_t (&x)[R],
+                                              uint32_t (&site)[R]) {
+    uint32_t l[R], n[R];
+    bool more = false;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const uint32_t t = x[j] >> 16;
+        l[j] = dh[t];
+        n[j] = (uint32_t)dh[t + 1] - l[j];
+        more |= n[j] > 0u;
+    }
+    while (more) {  // l: first candidate whose low bits exceed x's, within [l, l + n)
+        more = false;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (n[j] > 0u) {
+                const uint32_t half = n[j] >> 1;
+                if (s16[l[j] + half] <= (x[j] & 0xFFFFu)) {
+                    l[j] += half + 1u;
+                    n[j] -= half + 1u;
+                } else {
+                    n[j] = half;
+                }
+                more |= n[j] > 0u;
+            }
+        }
+    }
+    uint4 v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j)  // l >= 1: block 0 starts at address 0, inside bucket 0
+        v[j] = __ldg(reinterpret_cast<const uint4*>(pairs) + (l[j] - 1u));
+#pragma unroll
+    for (int j = 0; j < R; ++j) site[j] = v[j].z <= x[j] ? v[j].w : v[j].y;
+}
+
 // The paper's lookup (Sec. III.B.2.1): the site of x's /24 subnet from the hash table of
 // the registered networks' /24 subnets (kNoSite when absent). Linear probing; the table is
 // at most half full, so every probe sequence ends at the key or at an empty slot.
@@ -415,6 +458,8 @@ struct Smem {
     uint32_t rows;      // table rows
     const uint32_t* s_starts;
     const uint32_t* s_site;
+    const uint16_t* dh;    // 16-bit block directory and samples (kLookupRadixBlk2H)
+    const uint16_t* s16;
     const float* ra;    // learned index leaf arrays
     const float* rb;
     const uint32_t* rx0;
@@ -593,6 +638,42 @@ __device__ __forceinline__ void flush(const Smem& sm, uint64_t* gacc) {
     }
 }
 
+// IEEE 754 binary64 bits of the integer v rounded to nearest, ties to even, on the integer
+// units: the leading 53 bits of v, rounded up when the bits shifted out exceed half a unit
+// in the last place (or equal it and the kept last bit is odd).
+__device__ __forceinline__ uint64_t f64_bits_rn(uint64_t v) {
+    if (v == 0) return 0;
+    const int e = 63 - __clzll((long long)v);  // position of the leading one
+    uint64_t m;
+    int ex = e;
+    if (e <= 52) {
+        m = v << (52 - e);
+    } else {
+        const int sh = e - 52;  // 1..11 bits shifted out
+        m = v >> sh;
+        const uint64_t rem = v & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (m & 1ull))) {
+            ++m;
+            if (m == (1ull << 53)) {
+                m >>= 1;
+                ++ex;
+            }
+        }
+    }
+    return ((uint64_t)(ex + 1023) << 52) | (m & ((1ull << 52) - 1ull));
+}
+
+// Bits of RN(RN(o) * 8000). RN(o) = m * 2^k with a 53-bit integer m, and m * 8000 =
+// (m * 125) * 2^(k+6) with m * 125 < 2^60: the product rounds as the integer m * 125 does,
+// then 2^(k+6) only moves the exponent (the result is at least 8000, far from the limits).
+__device__ __forceinline__ uint64_t f64_bits_times8000(uint64_t o) {
+    const uint64_t a = f64_bits_rn(o);
+    if (a == 0) return 0;
+    const uint64_t m = (a & ((1ull << 52) - 1ull)) | (1ull << 52);
+    const int64_t k = (int64_t)(a >> 52) - 1075;
+    return f64_bits_rn(m * 125u) + ((uint64_t)(k + 6) << 52);
+}
+
 // Rates and flags of one window from its accumulators (Sec. III.B.1: rates per site;
 // a site is sub-optimal when its rate is below the standard). kL1: the sums were written
 // by an earlier kernel, so loads may go through L1; inside the aggregation kernel they
@@ -678,9 +759,11 @@ __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot,
             sv[4] = eo;
             sv[5] = ed;
             if (k < nk) {
-                // rate = (octets * 8 bits) / (ms / 1000), one rounding per operation
-                const double r = ed ? __ddiv_rn(__dmul_rn(__ull2double_rn(eo), 8000.0),
-                                                __ull2double_rn(ed))
+                // rate = (octets * 8 bits) / (ms / 1000), one rounding per operation; the
+                // conversions and the product are formed exactly on the integer units, so the
+                // division is the only FP64 operation
+                const double r = ed ? __ddiv_rn(__longlong_as_double((long long)f64_bits_times8000(eo)),
+                                                __longlong_as_double((long long)f64_bits_rn(ed)))
                                     : __longlong_as_double(0x7FF8000000000000ll);
                 rate[k] = r;
                 flag[k] = (ef >= (uint64_t)p.min_flows && r < p.threshold) ? 1 : 0;
@@ -781,6 +864,8 @@ __device__ __forceinline__ void lookup_sites(const AggParams& p, const Smem& sm,
         radix_block<4, R>(sm.s_starts, p.radix_bits, sm.s_site, p.pairs, x, site);
     } else if (LOOKUP == kLookupRadixBlk2) {
         radix_block<2, R>(sm.s_starts, p.radix_bits, sm.s_site, p.pairs, x, site);
+    } else if (LOOKUP == kLookupRadixBlk2H) {
+        radix_block16<R>(sm.dh, sm.s16, p.pairs, x, site);
     } else if (LOOKUP == kLookupRmi) {
         rmi_sites<R>(p.rmi, sm.ra, sm.rb, sm.rx0, sm.reps, p.pairs, p.n_ranges, valid, x, site, p.violations);
     } else if (LOOKUP == kLookupHash24) {
@@ -955,6 +1040,16 @@ __device__ __forceinline__ void stage_lookup(const AggParams& p, unsigned char* 
         for (uint32_t i = tid; i < nb; i += B) smp[i] = __ldg(sample + i);
         sm.s_starts = d;
         sm.s_site = smp;  // (here: the block samples)
+    }
+    if (LOOKUP == kLookupRadixBlk2H) {  // 16-bit directory (65537 entries) and block samples
+        uint32_t* d = reinterpret_cast<uint32_t*>(base);
+        const uint32_t* gd = reinterpret_cast<const uint32_t*>(p.dirh);
+        constexpr uint32_t nd = (65537u + 1u) / 2u;  // 32-bit words (the last one half used)
+        for (uint32_t i = tid; i < nd; i += B) d[i] = i + 1u < nd ? __ldg(gd + i) : (uint32_t)__ldg(p.dirh + 65536);
+        uint16_t* s = reinterpret_cast<uint16_t*>(base + (65537u * 2u + 15u) / 16u * 16u);
+        for (uint32_t i = tid; i < p.n_blk2; i += B) s[i] = __ldg(p.smp16 + i);
+        sm.dh = reinterpret_cast<const uint16_t*>(d);
+        sm.s16 = s;
     }
     if (LOOKUP == kLookupRmi) {
         const uint32_t L = p.rmi.n_leaves;

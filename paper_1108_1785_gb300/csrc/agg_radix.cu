@@ -14,4 +14,7 @@ cudaError_t launch_keys_radixblk(const AggParams& p, const LaunchShape& s, uint3
 cudaError_t launch_keys_radixblk2(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st) {
     return dev::launch_keys_impl<kLookupRadixBlk2>(p, s, keys, st);
 }
+cudaError_t launch_keys_radixblk2h(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st) {
+    return dev::launch_keys_impl<kLookupRadixBlk2H>(p, s, keys, st);
+}
 }  // namespace gnm

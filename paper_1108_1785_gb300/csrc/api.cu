@@ -302,10 +302,25 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s, size_t n_win) {
     s->split = split == GNM_SPLIT_TWO_KERNELS;
     s->keys_smem = s->split ? (lookup_bytes + 15) / 16 * 16 : 0;
     s->keys_blk = 0;
+    s->keys_h16 = 0;
     s->keys_bits = 0;
-    if (cfg.key_directory < 0 || cfg.key_directory > 3) return fail(GNM_E_INVAL, "key_directory must be 0..3");
+    if (cfg.key_directory < 0 || cfg.key_directory > 4) return fail(GNM_E_INVAL, "key_directory must be 0..4");
     const int key_dir = cfg.key_directory ? cfg.key_directory : c->tuned.key_dir;
-    if (s->split && s->lookup == kLookupRadix && key_dir != 2) {
+    if (s->split && s->lookup == kLookupRadix && key_dir == 4) {
+        // 16-bit directory and samples of 2-range blocks (block indices below 2^16)
+        const size_t one = (size_t)c->smem_optin > 1024 ? (size_t)c->smem_optin - 1024 : 0;
+        const size_t bytes = (65537 * 2 + 15) / 16 * 16 + ((size_t)c->n_blk2 * 2 + 15) / 16 * 16;
+        if (c->d_dirh && bytes <= one) {
+            s->keys_blk = 2;
+            s->keys_h16 = 1;
+            s->keys_bits = 16;
+            s->keys_smem = bytes;
+        } else {
+            return fail(GNM_E_INVAL, "key_directory 4 needs fewer than 65,536 two-range blocks that fit in "
+                                     "shared memory");
+        }
+    }
+    if (s->split && s->lookup == kLookupRadix && key_dir != 2 && key_dir != 4 && !s->keys_h16) {
         // block samples in the key kernel's shared memory next to a directory of block
         // indices: 2-range blocks (one 16-byte load) when they fit, else 4-range blocks
         // (32 bytes); else the plain directory
@@ -412,7 +427,8 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s, size_t n_win) {
     if (s->split) {  // key kernel: as many CTAs per SM as its shared memory allows
         int ku = c->tuned.keys_unroll ? c->tuned.keys_unroll : s->unroll;
         if (ku != 1 && ku != 2) ku = 1;
-        const int lk = s->keys_blk == 2 ? kLookupRadixBlk2 : s->keys_blk == 4 ? kLookupRadixBlk : s->lookup;
+        const int lk = s->keys_h16 ? kLookupRadixBlk2H
+                       : s->keys_blk == 2 ? kLookupRadixBlk2 : s->keys_blk == 4 ? kLookupRadixBlk : s->lookup;
         s->keys_unroll = ku;
         s->keys_block = keys_block_max(lk, ku);
         const int kfit = std::max(1, std::min(2048 / s->keys_block, (int)(c->smem_per_sm / (s->keys_smem + 1024))));
@@ -447,6 +463,8 @@ gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p) {
     p->n_blk4 = c->n_blk4;
     p->sample2 = c->d_sample2;
     p->n_blk2 = c->n_blk2;
+    p->dirh = c->d_dirh;
+    p->smp16 = c->d_smp16;
     p->h24 = c->d_h24;
     p->h24_mask = c->h24_mask;
     p->n_blocks = c->n_blocks;
@@ -947,6 +965,8 @@ void gnm_destroy(gnm_ctx* c) {
     free_dev(c->d_dir16);
     free_dev(c->d_sample4);
     free_dev(c->d_sample2);
+    free_dev(c->d_dirh);
+    free_dev(c->d_smp16);
     free_dev(c->d_h24);
     free_dev(c->d_violations);
     free_dev(c->d_flag_count);
@@ -991,12 +1011,16 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     free_dev(c->d_dir16);
     free_dev(c->d_sample4);
     free_dev(c->d_sample2);
+    free_dev(c->d_dirh);
+    free_dev(c->d_smp16);
     free_dev(c->d_h24);
     c->d_dir16 = nullptr;
     c->d_sample4 = nullptr;
     c->n_blk4 = 0;
     c->d_sample2 = nullptr;
     c->n_blk2 = 0;
+    c->d_dirh = nullptr;
+    c->d_smp16 = nullptr;
     c->d_h24 = nullptr;
     c->h24_mask = 0;
     c->d_starts = nullptr;
@@ -1062,6 +1086,23 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
         GNM_CU(cudaMalloc(d, nb * 4));
         GNM_CU(cudaMemcpy(*d, sb.data(), nb * 4, cudaMemcpyHostToDevice));
         (br == 2 ? c->n_blk2 : c->n_blk4) = (uint32_t)nb;
+        if (br == 2 && nb < 65536) {
+            // 16-bit form: per /16 bucket t the first block starting at or after t << 16 (the
+            // block before it holds the bucket's first address; the blocks up to the next
+            // bucket's entry start inside the bucket, so their low 16 bits order them)
+            std::vector<uint16_t> dh(65537), s16(nb);
+            size_t g = 0;
+            for (uint64_t t = 0; t < 65536; ++t) {
+                while (g < nb && (uint64_t)sb[g] < (t << 16)) ++g;
+                dh[t] = (uint16_t)g;
+            }
+            dh[65536] = (uint16_t)nb;
+            for (size_t b = 0; b < nb; ++b) s16[b] = (uint16_t)(sb[b] & 0xFFFFu);
+            GNM_CU(cudaMalloc(&c->d_dirh, dh.size() * 2));
+            GNM_CU(cudaMemcpy(c->d_dirh, dh.data(), dh.size() * 2, cudaMemcpyHostToDevice));
+            GNM_CU(cudaMalloc(&c->d_smp16, nb * 2));
+            GNM_CU(cudaMemcpy(c->d_smp16, s16.data(), nb * 2, cudaMemcpyHostToDevice));
+        }
     }
     GNM_CU(cudaMalloc(&c->d_blocks, blk.size() * 4));
     GNM_CU(cudaMalloc(&c->d_sample, nb * 4));

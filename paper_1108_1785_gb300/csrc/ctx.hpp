@@ -100,6 +100,8 @@ struct gnm_ctx {
     uint32_t n_blk4 = 0;
     uint32_t* d_sample2 = nullptr;  // key kernel: first start of every 2-range block
     uint32_t n_blk2 = 0;
+    uint16_t* d_dirh = nullptr;     // key kernel, n_blk2 < 2^16: 16-bit directory of 2-range blocks
+    uint16_t* d_smp16 = nullptr;    // ... and the low 16 bits of their first starts
     uint2* d_h24 = nullptr;         // /24 subnet hash table (registries of prefixes up to /24)
     uint32_t h24_mask = 0;
     uint32_t local_pfx[GNM_MAX_LOCAL] = {0};

@@ -78,6 +78,9 @@ struct AggParams {
     uint32_t n_blk4;
     const uint32_t* sample2;     // key kernel: first start of every 2-range block of pairs
     uint32_t n_blk2;
+    const uint16_t* dirh;        // key kernel (n_blk2 < 2^16): per /16 bucket t, the first 2-range
+                                 // block whose first start is >= t << 16 (65537 entries)
+    const uint16_t* smp16;       // the low 16 bits of every 2-range block's first start
     const uint2* h24;            // /24 subnet hash table: (subnet + 1, site), 0 = empty
     uint32_t h24_mask;           // table slots - 1
     uint32_t n_blocks;
@@ -128,15 +131,20 @@ struct AggParams {
 // kLookupRadixBlk / kLookupRadixBlk2 (key kernel only): a directory of blocks of 4 (2)
 // ranges and the blocks' first starts in shared memory; one 32-byte (16-byte) load of the
 // block's (start, site) pairs ends the lookup.
+// kLookupRadixBlk2H (key kernel only): 2-range blocks found through a directory over the top
+// 16 address bits and the blocks' low 16 start bits, both 16-bit, in shared memory.
 // kLookupHash24: the paper's /24 subnet hash table (registries of prefixes up to /24).
 enum { kLookupL2 = 0, kLookupSmem = 1, kLookupRmi = 2, kLookupStaged = 3, kLookupRadix = 4, kLookupKeys = 5,
-       kLookupRadixBlk = 6, kLookupRadixBlk2 = 7, kLookupHash24 = 8 };
+       kLookupRadixBlk = 6, kLookupRadixBlk2 = 7, kLookupHash24 = 8, kLookupRadixBlk2H = 9 };
 
 
 // Largest block of the key kernel for a lookup and records-per-thread unroll: two groups
 // of lookups per thread fit 64 registers (1024 threads) only for the lighter lookups.
 __host__ __device__ constexpr int keys_block_max(int lookup, int unroll) {
-    return (unroll == 1 || lookup == kLookupRadixBlk2 || lookup == kLookupRadix || lookup == kLookupL2) ? 1024 : 512;
+    return (unroll == 1 || lookup == kLookupRadixBlk2 || lookup == kLookupRadixBlk2H || lookup == kLookupRadix ||
+            lookup == kLookupL2)
+               ? 1024
+               : 512;
 }
 constexpr uint32_t kBlockRanges = 16;  // ranges per staged block (16 starts, 64 bytes)
 enum { kTableDirect = 0, kTableHash = 1, kTableGlobal = 2 };
@@ -165,6 +173,7 @@ struct LaunchShape {
     int keys_grid, keys_block;
     size_t keys_smem;
     int keys_blk;          // radix key kernel: ranges per block of its shared block samples (0: none)
+    int keys_h16;          // ... with the 16-bit directory and 16-bit samples (2-range blocks)
     uint32_t keys_bits;    // its directory bits
     int keys_unroll;       // key kernel: groups of 4 records per thread and step (1 or 2)
     // partitioned launches (split launches whose keys exceed one direct table): records are

@@ -17,6 +17,7 @@ cudaError_t launch_keys_staged(const AggParams& p, const LaunchShape& s, uint32_
 cudaError_t launch_keys_radix(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
 cudaError_t launch_keys_radixblk(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
 cudaError_t launch_keys_radixblk2(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
+cudaError_t launch_keys_radixblk2h(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
 cudaError_t launch_keys_hash24(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st);
 cudaError_t launch_aggregate_hash24(const AggParams& p, const LaunchShape& s, cudaStream_t st);
 
@@ -27,7 +28,8 @@ cudaError_t launch_keys(const AggParams& p, const LaunchShape& s, uint32_t* keys
         case kLookupStaged: return launch_keys_staged(p, s, keys, st);
         case kLookupHash24: return launch_keys_hash24(p, s, keys, st);
         case kLookupRadix:
-            return s.keys_blk == 2   ? launch_keys_radixblk2(p, s, keys, st)
+            return s.keys_h16        ? launch_keys_radixblk2h(p, s, keys, st)
+                   : s.keys_blk == 2 ? launch_keys_radixblk2(p, s, keys, st)
                    : s.keys_blk == 4 ? launch_keys_radixblk(p, s, keys, st)
                                      : launch_keys_radix(p, s, keys, st);
         default: return launch_keys_l2(p, s, keys, st);

@@ -220,7 +220,7 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
     if (base_shape.lookup == kLookupSmem) splits_v.push_back(GNM_SPLIT_FUSED);
     else splits_v = {GNM_SPLIT_FUSED, GNM_SPLIT_TWO_KERNELS};
     std::vector<int> kdirs_v = {0};
-    if (base_shape.lookup == kLookupRadix) kdirs_v = {3, 1, 2};
+    if (base_shape.lookup == kLookupRadix) kdirs_v = {3, 1, 4, 2};
     for (int sp : splits_v)
     for (int kd : kdirs_v)
     for (int ku : {1, 2})
@@ -240,7 +240,10 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
                             if (c->cfg.radix_bits == 0) c->cfg.radix_bits = (uint32_t)rb;
                             if (c->cfg.ctas_per_sm == 0) c->cfg.ctas_per_sm = cps;
                             if (c->cfg.split == GNM_SPLIT_AUTO) c->cfg.split = sp;
-                            if (sp == GNM_SPLIT_FUSED && (kd == 2 || ku == 2)) continue;  // key kernel knobs
+                            // key kernel knobs: none in fused launches; the 16-bit directory
+                            // has no size to tune
+                            if (sp == GNM_SPLIT_FUSED && (kd != kdirs_v[0] || ku == 2)) continue;
+                            if (kd == 4 && rb != bits_v[0]) continue;
                             c->tuned.keys_unroll = ku;
                             if (c->cfg.key_directory == 0) c->cfg.key_directory = kd;
                             LaunchShape sh;

@@ -155,7 +155,7 @@ def c2hour():
 
 
 @pytest.mark.parametrize("cfg", [{}, {"split": "FUSED"}, {"lookup_mode": "BSEARCH"}, {"key_directory": 1},
-                                 {"key_directory": 2}, {"key_directory": 3}, {"key_directory": 3, "radix_bits": 8},
+                                 {"key_directory": 2}, {"key_directory": 3}, {"key_directory": 4}, {"key_directory": 3, "radix_bits": 8},
                                  {"key_directory": 1, "radix_bits": 15},
                                  {"key_directory": 1, "radix_bits": 4}, {"key_directory": 2, "radix_bits": 14},
                                  {"radix_bits": 10}, {"radix_bits": 4},
@@ -329,6 +329,40 @@ def test_one_slot_reused_after_global_sums(gnm, cfg):
     ctx.close()
 
 
+def test_rates_bit_exact_when_the_sums_pass_2_53(gnm):
+    """2.5 M eligible flows of one (site, direction) with octets and durations near 2^32: the
+    key's sums of eligible octets and durations pass 2^53, so converting them to FP64 rounds.
+    The rates equal the FP64 oracle's bit for bit (the conversions and the x8000 are formed
+    exactly on the integer units, the division is the FP64 one), on every key."""
+    reg = fg.registry_c1()
+    n = 2_500_000
+    rec = fg.make_records(reg, n, seed=91)
+    rng = np.random.default_rng(91)
+    hot = rng.random(n) < 0.9
+    inside = np.nonzero(reg.site == reg.site[3])[0][0]
+    remote = np.uint32(int(reg.prefix[inside]) + 3)
+    local = np.uint32(int(reg.local_prefix[0]) + 11)
+    rec["srcaddr"] = np.where(hot, remote, rec["srcaddr"]).astype(np.uint32)
+    rec["dstaddr"] = np.where(hot, local, rec["dstaddr"]).astype(np.uint32)
+    big = (np.uint64(0xFFFFFFFF) - rng.integers(0, 1 << 24, size=n).astype(np.uint64)).astype(np.uint32)
+    rec["dOctets"] = np.where(hot, big, rec["dOctets"]).astype(np.uint32)
+    rec["dPkts"] = np.where(hot, rng.integers(10, 40, size=n), rec["dPkts"]).astype(np.uint32)
+    dur = (np.uint64(0xFFFFFFFF) - rng.integers(0, 1 << 24, size=n).astype(np.uint64)).astype(np.uint32)
+    rec["last"] = np.where(hot, rec["first"] + dur, rec["last"]).astype(np.uint32)  # mod 2^32
+    ctx = _ctx(gnm, reg)
+    ctx.process(gnm.Records.to_device(rec), 1)
+    got = ctx.dense(1)
+    want = oracle_full(reg, rec)
+    key = int(reg.site[3]) * 2 + 0  # inbound: the remote end is the source
+    assert want[0][key, 4] > 2 ** 53 and want[0][key, 5] > 2 ** 53
+    assert_window_matches(got, want)
+    gr, wr = np.asarray(got[2], np.float64), np.asarray(want[2], np.float64)
+    np.testing.assert_array_equal(np.isnan(gr), np.isnan(wr))
+    ok = ~np.isnan(wr)
+    np.testing.assert_array_equal(gr[ok].view(np.uint64), wr[ok].view(np.uint64))
+    ctx.close()
+
+
 @pytest.mark.parametrize("which", ["c1", "c2"])
 def test_host_records_in_place_and_staged(gnm, c1, which):
     """Page-locked host records read in place by the kernels, the same staged through a
@@ -370,6 +404,36 @@ def test_block_samples_must_fit(gnm):
     d = gnm.Records.to_device(fg.make_records(reg, 1000, seed=3))
     with pytest.raises(gnm.GnmError, match="block samples do not fit"):
         ctx.process(d, 1)
+    ctx.close()
+
+
+def test_sixteen_bit_block_directory_limits(gnm):
+    """The 16-bit block directory holds block indices below 2^16: the 100,000-site registry
+    (about 910,000 two-range blocks) refuses it when asked for and falls back to another
+    directory by default; near the bucket edges (addresses t << 16 and t << 16 - 1 around
+    registered prefixes) its lookups equal the oracle."""
+    big = fg.registry_c3()
+    d = gnm.Records.to_device(fg.make_records(big, 1000, seed=3))
+    ctx = _ctx(gnm, big, lookup_mode=gnm.LOOKUP_RADIX, split=gnm.SPLIT_TWO_KERNELS, key_directory=4)
+    with pytest.raises(gnm.GnmError, match="key_directory 4"):
+        ctx.process(d, 1)
+    ctx.close()
+    reg = fg.registry_c2()
+    rec = fg.make_records(reg, 200_000, seed=5)
+    rng = np.random.default_rng(5)
+    # remote ends on /16 bucket edges and on range starts and their predecessors
+    starts, _ = gnm.registry_flatten(reg.prefix, reg.plen, reg.site, reg.n_sites)
+    edges = np.concatenate([(np.arange(0, 1 << 16, dtype=np.uint64) << np.uint64(16)),
+                            (np.arange(1, 1 << 16, dtype=np.uint64) << np.uint64(16)) - np.uint64(1),
+                            starts.astype(np.uint64), starts[1:].astype(np.uint64) - np.uint64(1)])
+    remote = edges[rng.integers(0, edges.size, size=rec["srcaddr"].size)].astype(np.uint32)
+    inbound = rng.random(rec["srcaddr"].size) < 0.5
+    local = np.uint32(int(reg.local_prefix[0]) + 5)
+    rec["srcaddr"] = np.where(inbound, remote, local).astype(np.uint32)
+    rec["dstaddr"] = np.where(inbound, local, remote).astype(np.uint32)
+    ctx = _ctx(gnm, reg, lookup_mode=gnm.LOOKUP_RADIX, split=gnm.SPLIT_TWO_KERNELS, key_directory=4)
+    ctx.process(gnm.Records.to_device(rec), 1)
+    assert_window_matches(ctx.dense(1), oracle_full(reg, rec))
     ctx.close()
 
 
