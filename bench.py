@@ -274,6 +274,7 @@ def batched_c4(gnm, torch, local, steps, warmup):
             "records_per_s": n / (ms / 1e3), "ms": ms, "achieved_gbs": gbs, "frac": gbs / peak,
             "peak_kind": peak_kind, "kernels_ms": kms,
             "tuned": {"block_threads": tune.block_threads, "unroll": tune.unroll, "aggregation": tune.aggregation,
+                      "radix_bits": tune.radix_bits,
                       "placement": tune.placement, "ctas_per_sm": tune.ctas_per_sm}}
 
 

@@ -108,7 +108,9 @@ typedef struct {
     uint32_t hash_slots;        /* GNM_TABLE_HASH size: 0 = largest that fits, else an
                                    even number in 256..65536 */
     uint32_t radix_bits;        /* GNM_LOOKUP_RADIX directory bits: 0 = sized from the
-                                   registry, else 4..16 */
+                                   registry, else 4..16. With the shared-memory placement of
+                                   GNM_LOOKUP_BSEARCH: 4..16 = a directory of that many bits in
+                                   front of the search (when it fits), 0 = none */
     int32_t split;              /* GNM_SPLIT_*: one fused kernel, or a lookup kernel that
                                    writes a 4-byte key per record followed by the
                                    aggregation kernel (registries outside shared memory) */

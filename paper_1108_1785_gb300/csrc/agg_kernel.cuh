@@ -72,7 +72,7 @@ __device__ __forceinline__ uint32_t pred_search1(const uint32_t* __restrict__ s,
 // top `bits` bits of an address), so x's range lies in [dir[t], dir[t+1]]; a binary search
 // over the starts inside that interval finishes (R lookups in lock step, each stopping
 // when its interval has one entry).
-template <int R>
+template <int R, bool kShared = false>
 __device__ __forceinline__ void radix_search(const uint32_t* __restrict__ dir, uint32_t bits,
                                              const uint32_t* __restrict__ starts, const uint32_t (&x)[R],
                                              uint32_t (&base)[R]) {
@@ -91,7 +91,8 @@ __device__ __forceinline__ void radix_search(const uint32_t* __restrict__ dir, u
         for (int j = 0; j < R; ++j) {
             if (len[j] > 1u) {
                 const uint32_t half = len[j] >> 1;
-                base[j] = (__ldg(starts + base[j] + half) <= x[j]) ? base[j] + half : base[j];
+                const uint32_t v = kShared ? starts[base[j] + half] : __ldg(starts + base[j] + half);
+                base[j] = v <= x[j] ? base[j] + half : base[j];
                 len[j] -= half;
                 more |= len[j] > 1u;
             }
@@ -458,6 +459,7 @@ struct Smem {
     uint32_t rows;      // table rows
     const uint32_t* s_starts;
     const uint32_t* s_site;
+    const uint32_t* s_dir; // kLookupSmem: directory over the top radix_bits bits, or null
     const uint16_t* dh;    // 16-bit block directory and samples (kLookupRadixBlk2H)
     const uint16_t* s16;
     const float* ra;    // learned index leaf arrays
@@ -810,7 +812,7 @@ __host__ __device__ inline size_t smem_layout(int lookup, int table, uint32_t n_
     if (table == kTableHash) o += (size_t)cap * 4;
     o = align_up(o, 16);
     *off_lookup = o;
-    if (lookup == kLookupSmem) o += (size_t)n_ranges * 8;
+    if (lookup == kLookupSmem) o += (size_t)n_ranges * 8 + (radix_bits ? (((size_t)1 << radix_bits) + 1) * 4 : 0);
     if (lookup == kLookupStaged) o += (size_t)((n_ranges + kBlockRanges - 1) / kBlockRanges) * 4;
     if (lookup == kLookupRmi) o += (size_t)n_leaves * 16;
     if (lookup == kLookupRadix) o += ((size_t)1 << radix_bits) * 4 + 4;
@@ -824,7 +826,10 @@ __device__ __forceinline__ void lookup_sites(const AggParams& p, const Smem& sm,
                                              const uint32_t (&x)[R], uint32_t (&site)[R]) {
     uint32_t idx[R];
     if (LOOKUP == kLookupSmem) {
-        pred_search<R, true>(sm.s_starts, p.n_ranges, x, idx);
+        if (sm.s_dir)  // a directory over the top radix_bits bits narrows the search first
+            radix_search<R, true>(sm.s_dir, p.radix_bits, sm.s_starts, x, idx);
+        else
+            pred_search<R, true>(sm.s_starts, p.n_ranges, x, idx);
 #pragma unroll
         for (int j = 0; j < R; ++j) site[j] = sm.s_site[idx[j]];
     } else if (LOOKUP == kLookupL2) {
@@ -1016,6 +1021,13 @@ __device__ __forceinline__ void stage_lookup(const AggParams& p, unsigned char* 
         }
         sm.s_starts = st;
         sm.s_site = si;
+        sm.s_dir = nullptr;
+        if (p.radix_bits && p.dir16) {  // every 2^(16-bits)-th entry of the 16-bit directory
+            uint32_t* d = si + p.n_ranges;
+            const uint32_t nd = 1u << p.radix_bits, sh = 16u - p.radix_bits;
+            for (uint32_t i = tid; i <= nd; i += B) d[i] = __ldg(p.dir16 + ((size_t)i << sh));
+            sm.s_dir = d;
+        }
     }
     if (LOOKUP == kLookupStaged) {
         uint32_t* st = reinterpret_cast<uint32_t*>(base);

@@ -280,6 +280,15 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s, size_t n_win) {
         if (place == GNM_PLACE_SMEM) {
             s->lookup = kLookupSmem;
             lookup_bytes = (size_t)nr * 8;
+            // radix_bits > 0: a directory over the top bits in front of the search, when it
+            // fits beside the ranges (0: the search covers all ranges)
+            const uint32_t bits = cfg.radix_bits ? cfg.radix_bits : c->tuned.radix_bits;
+            if (bits && (bits < 4 || bits > 16)) return fail(GNM_E_INVAL, "radix_bits must be 4..16");
+            const size_t dir_bytes = (((size_t)1 << bits) + 1) * 4;
+            if (bits && lookup_bytes + dir_bytes + 1024 <= (size_t)c->smem_optin) {
+                s->radix_bits = bits;
+                lookup_bytes += dir_bytes;
+            }
         } else if (place == GNM_PLACE_STAGED) {
             s->lookup = kLookupStaged;
             lookup_bytes = sample_bytes;

@@ -212,6 +212,12 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
             if (b0 + d >= 4 && b0 + d <= 16) bits_v.push_back(b0 + d);
     } else {
         bits_v.push_back(0);
+        if (base_shape.lookup == kLookupSmem) {  // no directory (0), or one of 2..8 ranges per bucket
+            uint32_t lg = 0;
+            while ((1ull << lg) < c->h_starts.size()) ++lg;
+            for (int d : {1, 2, 3})
+                if ((int)lg - d >= 4 && (int)lg - d <= 14) bits_v.push_back((int)lg - d);
+        }
         if (base_shape.lookup == kLookupRmi) places_v.push_back(GNM_PLACE_AUTO);
         else places_v.assign(std::begin(places), std::end(places));
     }
@@ -244,6 +250,8 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
                             // has no size to tune
                             if (sp == GNM_SPLIT_FUSED && (kd != kdirs_v[0] || ku == 2)) continue;
                             if (kd == 4 && rb != bits_v[0]) continue;
+                            // directory sizes matter to the shared-memory placement only
+                            if (base_shape.lookup == kLookupSmem && rb != 0 && pl != GNM_PLACE_SMEM) continue;
                             c->tuned.keys_unroll = ku;
                             if (c->cfg.key_directory == 0) c->cfg.key_directory = kd;
                             LaunchShape sh;

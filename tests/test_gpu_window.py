@@ -68,8 +68,10 @@ def test_hand_window(gnm):
         ctx.close()
 
 
-LOOKUPS = [("BSEARCH", "SMEM", 0), ("BSEARCH", "STAGED", 0), ("BSEARCH", "L2", 0), ("RADIX", "AUTO", 0),
-           ("RADIX", "AUTO", 5)]
+# (BSEARCH, SMEM, bits): the ranges in shared memory behind a directory of `bits` bits (0: none;
+# 16: too large to fit beside the ranges, so the whole range array is searched)
+LOOKUPS = [("BSEARCH", "SMEM", 0), ("BSEARCH", "SMEM", 4), ("BSEARCH", "SMEM", 14), ("BSEARCH", "SMEM", 16),
+           ("BSEARCH", "STAGED", 0), ("BSEARCH", "L2", 0), ("RADIX", "AUTO", 0), ("RADIX", "AUTO", 5)]
 SPLITS = ["AUTO", "TWO_KERNELS"]
 
 
