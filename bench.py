@@ -254,11 +254,13 @@ def batched_c4(gnm, torch, local, steps, warmup):
         plan.launch(stream)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     a.record(stream)
     for _ in range(steps):
         plan.launch(stream)
     b.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     ms = a.elapsed_time(b) / steps
     plan.launch(stream)
     kms = {k: round(v, 4) for k, v in plan.kernel_times()}
