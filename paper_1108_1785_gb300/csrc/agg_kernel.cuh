@@ -826,10 +826,28 @@ __device__ __forceinline__ void lookup_sites(const AggParams& p, const Smem& sm,
                                              const uint32_t (&x)[R], uint32_t (&site)[R]) {
     uint32_t idx[R];
     if (LOOKUP == kLookupSmem) {
-        if (sm.s_dir)  // a directory over the top radix_bits bits narrows the search first
-            radix_search<R, true>(sm.s_dir, p.radix_bits, sm.s_starts, x, idx);
-        else
+        if (sm.s_dir) {  // a directory over the top radix_bits bits narrows the search first
+            // the same number of steps for every lane (enough for the largest bucket), so the
+            // loop has no per-lane exit; a step on a one-range interval keeps it
+            uint32_t len[R];
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const uint32_t t = x[j] >> (32u - p.radix_bits);
+                idx[j] = sm.s_dir[t];
+                len[j] = sm.s_dir[t + 1] - idx[j] + 1u;
+            }
+#pragma unroll 1
+            for (uint32_t it = 0; it < p.dir_iters; ++it) {
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const uint32_t half = len[j] >> 1;
+                    idx[j] = sm.s_starts[idx[j] + half] <= x[j] ? idx[j] + half : idx[j];
+                    len[j] -= half;
+                }
+            }
+        } else {
             pred_search<R, true>(sm.s_starts, p.n_ranges, x, idx);
+        }
 #pragma unroll
         for (int j = 0; j < R; ++j) site[j] = sm.s_site[idx[j]];
     } else if (LOOKUP == kLookupL2) {

@@ -244,6 +244,7 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s, size_t n_win) {
         return fail(GNM_E_STATE, "lookup mode RMI requested but no learned index is trained");
     size_t lookup_bytes = 0;
     s->radix_bits = 0;
+    s->dir_iters = 0;
     if (mode == GNM_LOOKUP_HASH24) {
         if (!c->d_h24) return fail(GNM_E_INVAL, "lookup mode HASH24: the registry has prefixes longer than /24");
         s->lookup = kLookupHash24;
@@ -288,6 +289,21 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s, size_t n_win) {
             if (bits && lookup_bytes + dir_bytes + 1024 <= (size_t)c->smem_optin) {
                 s->radix_bits = bits;
                 lookup_bytes += dir_bytes;
+                // every lane takes the same number of search steps: enough for the largest
+                // bucket (ranges [first range of bucket t, first range of bucket t+1])
+                const std::vector<uint32_t>& st = c->h_starts;
+                uint32_t longest = 1, prev = 0;
+                for (uint64_t t = 1; t <= ((uint64_t)1 << bits); ++t) {
+                    const uint64_t a = t << (32 - bits);
+                    const uint32_t i = a >> 32 ? nr - 1u
+                                               : (uint32_t)(std::upper_bound(st.begin(), st.end(), (uint32_t)a) -
+                                                            st.begin()) - 1u;
+                    longest = std::max(longest, i - prev + 1u);
+                    prev = i;
+                }
+                uint32_t it = 0;
+                while ((1u << it) < longest) ++it;
+                s->dir_iters = it;
             }
         } else if (place == GNM_PLACE_STAGED) {
             s->lookup = kLookupStaged;
@@ -545,6 +561,7 @@ gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* off
     GNM_TRY(choose_shape(c, N, &sh, n_win));
     p.table_cap = sh.cap;
     p.radix_bits = sh.radix_bits;
+    p.dir_iters = sh.dir_iters;
     p.n_total = N;
     uint64_t chunk = ceil_div(N, (uint64_t)sh.grid);
     chunk = (chunk + 3) & ~3ull;

@@ -74,6 +74,8 @@ struct AggParams {
     const uint32_t* sample;      // staged placement: first start of every block
     const uint32_t* dir16;       // radix directory over the top 16 bits (65537 entries)
     uint32_t radix_bits;         // directory bits used by this launch (<= 16)
+    uint32_t dir_iters;          // shared-memory registry behind a directory: search steps that
+                                 // narrow its largest bucket to one range
     const uint32_t* sample4;     // key kernel: first start of every 4-range block of pairs
     uint32_t n_blk4;
     const uint32_t* sample2;     // key kernel: first start of every 2-range block of pairs
@@ -166,6 +168,7 @@ struct LaunchShape {
     int grid;
     uint32_t cap;    // hash-table slots (kTableHash)
     uint32_t radix_bits;  // kLookupRadix directory bits
+    uint32_t dir_iters;   // kLookupSmem with a directory: fixed search steps (see AggParams)
     size_t smem;
     // split launches: a lookup kernel (this lookup method) writes keys, then the
     // aggregation kernel reads them (kLookupKeys)

@@ -212,10 +212,10 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
             if (b0 + d >= 4 && b0 + d <= 16) bits_v.push_back(b0 + d);
     } else {
         bits_v.push_back(0);
-        if (base_shape.lookup == kLookupSmem) {  // no directory (0), or one of 2..8 ranges per bucket
+        if (base_shape.lookup == kLookupSmem) {  // no directory (0), or one of 2..32 ranges per bucket
             uint32_t lg = 0;
             while ((1ull << lg) < c->h_starts.size()) ++lg;
-            for (int d : {1, 2, 3})
+            for (int d : {1, 2, 3, 4, 5})
                 if ((int)lg - d >= 4 && (int)lg - d <= 14) bits_v.push_back((int)lg - d);
         }
         if (base_shape.lookup == kLookupRmi) places_v.push_back(GNM_PLACE_AUTO);
