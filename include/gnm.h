@@ -69,7 +69,11 @@ enum { GNM_LOOKUP_AUTO = 0, GNM_LOOKUP_BSEARCH = 1, GNM_LOOKUP_RMI = 2, GNM_LOOK
        GNM_LOOKUP_HASH24 = 4 };
 /* Where the flattened registry is searched: wholly in shared memory (SMEM), wholly in L2
  * (L2), or STAGED: the first start of every block of 16 ranges in shared memory, the
- * 64-byte blocks of 16 starts and the sites in L2 (two L2 accesses per lookup). */
+ * 64-byte blocks of 16 starts and the sites in L2 (two L2 accesses per lookup). With RMI
+ * the ranges are always searched in L2 and the placement is that of the learned index's
+ * leaf parameters: staged in shared memory (SMEM; GNM_E_INVAL when they do not fit), read
+ * from global memory with one 16-byte load per lookup (L2), or AUTO: staged when they fit
+ * (up to about 14,000 leaves), else read from global memory. */
 enum { GNM_PLACE_AUTO = 0, GNM_PLACE_SMEM = 1, GNM_PLACE_L2 = 2, GNM_PLACE_STAGED = 3 };
 enum { GNM_AGG_AUTO = 0, GNM_AGG_DIRECT = 1, GNM_AGG_WARP = 2 };
 enum { GNM_ADMIN_OR = 0, GNM_ADMIN_AND = 1 };

@@ -282,12 +282,34 @@ __device__ __forceinline__ uint32_t rmi_root(const RmiDev& m, uint32_t x) {
     return clamp_floor(r, m.n_leaves);
 }
 
-// Predicted position of x inside leaf l.
-__device__ __forceinline__ uint32_t rmi_leaf_pos(const float* a, const float* b,
-                                                 const uint32_t* x0, uint32_t l, uint32_t x,
-                                                 uint32_t n) {
-    const float d = __ll2float_rn((long long)x - (long long)x0[l]);
-    return clamp_floor(__fadd_rn(__fmul_rn(a[l], d), b[l]), n);
+// Parameters of leaf l: from the staged shared-memory arrays, or (a == null) with one
+// 16-byte load of the interleaved global copy.
+struct RmiLeaf {
+    float a, b;
+    uint32_t x0, eps;
+};
+__device__ __forceinline__ RmiLeaf rmi_leaf(const RmiDev& m, const float* a, const float* b, const uint32_t* x0,
+                                            const uint32_t* eps, uint32_t l) {
+    RmiLeaf f;
+    if (a) {
+        f.a = a[l];
+        f.b = b[l];
+        f.x0 = x0[l];
+        f.eps = eps[l];
+    } else {
+        const uint4 v = __ldg(m.leaf4 + l);
+        f.a = __uint_as_float(v.x);
+        f.b = __uint_as_float(v.y);
+        f.x0 = v.z;
+        f.eps = v.w;
+    }
+    return f;
+}
+
+// Predicted position of x inside its leaf.
+__device__ __forceinline__ uint32_t rmi_leaf_pos(const RmiLeaf& f, uint32_t x, uint32_t n) {
+    const float d = __ll2float_rn((long long)x - (long long)f.x0);
+    return clamp_floor(__fadd_rn(__fmul_rn(f.a, d), f.b), n);
 }
 
 // Learned-index lookup: model window, exact search inside it, verification, fallback.
@@ -295,10 +317,10 @@ __device__ __forceinline__ uint32_t rmi_lookup(const RmiDev& m, const float* a, 
                                                const uint32_t* x0, const uint32_t* eps,
                                                const uint32_t* __restrict__ starts, uint32_t n,
                                                uint32_t x, unsigned long long* violations) {
-    const uint32_t l = rmi_root(m, x);
-    const uint32_t e = eps[l];
+    const RmiLeaf f = rmi_leaf(m, a, b, x0, eps, rmi_root(m, x));
+    const uint32_t e = f.eps;
     if (e == 0xFFFFFFFFu) return pred_search1(starts, 0, n, x);
-    const uint32_t pi = rmi_leaf_pos(a, b, x0, l, x, n);
+    const uint32_t pi = rmi_leaf_pos(f, x, n);
     const uint32_t elo = e & 0xFFFFu, ehi = e >> 16;
     const uint32_t lo = pi > elo ? pi - elo : 0u;
     const uint32_t hi = min(pi + ehi + 1u, n - 1u);  // one past the bound, to verify it
@@ -322,8 +344,8 @@ __device__ __forceinline__ void rmi_sites(const RmiDev& m, const float* a, const
     uint32_t first[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-        const uint32_t l = rmi_root(m, x[j]);
-        const uint32_t e = eps[l];
+        const RmiLeaf lf = rmi_leaf(m, a, b, x0, eps, rmi_root(m, x[j]));
+        const uint32_t e = lf.eps;
         if (!valid[j]) {
             lo[j] = 0u;
             hi[j] = 0u;
@@ -331,7 +353,7 @@ __device__ __forceinline__ void rmi_sites(const RmiDev& m, const float* a, const
             lo[j] = 0u;
             hi[j] = n - 1u;
         } else {
-            const uint32_t pi = rmi_leaf_pos(a, b, x0, l, x[j], n);
+            const uint32_t pi = rmi_leaf_pos(lf, x[j], n);
             const uint32_t elo = e & 0xFFFFu, ehi = e >> 16;
             lo[j] = pi > elo ? pi - elo : 0u;
             hi[j] = min(pi + ehi + 1u, n - 1u);  // one past the bound, to verify it
@@ -1081,7 +1103,12 @@ __device__ __forceinline__ void stage_lookup(const AggParams& p, unsigned char* 
         sm.dh = reinterpret_cast<const uint16_t*>(d);
         sm.s16 = s;
     }
-    if (LOOKUP == kLookupRmi) {
+    if (LOOKUP == kLookupRmi && p.rmi.leaves_global) {  // leaves read from global memory
+        sm.ra = nullptr;
+        sm.rb = nullptr;
+        sm.rx0 = nullptr;
+        sm.reps = nullptr;
+    } else if (LOOKUP == kLookupRmi) {
         const uint32_t L = p.rmi.n_leaves;
         float* a = reinterpret_cast<float*>(base);
         float* b = a + L;
@@ -1113,7 +1140,8 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
 
     size_t off_keys, off_lookup;
     smem_layout(LOOKUP, TABLE, p.n_ranges, p.table_rows, p.table_cap,
-                LOOKUP == kLookupRmi ? p.rmi.n_leaves : 0u, p.radix_bits, &off_keys, &off_lookup);
+                LOOKUP == kLookupRmi && !p.rmi.leaves_global ? p.rmi.n_leaves : 0u, p.radix_bits, &off_keys,
+                &off_lookup);
     Smem sm;
     sm.key_base = 0u;
     sm.dirty = nullptr;

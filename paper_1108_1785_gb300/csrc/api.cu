@@ -245,12 +245,22 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s, size_t n_win) {
     size_t lookup_bytes = 0;
     s->radix_bits = 0;
     s->dir_iters = 0;
+    s->rmi_global = 0;
     if (mode == GNM_LOOKUP_HASH24) {
         if (!c->d_h24) return fail(GNM_E_INVAL, "lookup mode HASH24: the registry has prefixes longer than /24");
         s->lookup = kLookupHash24;
     } else if (mode == GNM_LOOKUP_RMI) {
         s->lookup = kLookupRmi;
-        lookup_bytes = (size_t)c->rmi.n_leaves * 16;
+        // leaf parameters staged in shared memory, or read (16 bytes per lookup) from global
+        // memory: placement L2, or AUTO when they do not fit
+        const size_t leaf_bytes = (size_t)c->rmi.n_leaves * 16;
+        int place = cfg.placement != GNM_PLACE_AUTO ? cfg.placement : c->tuned.placement;
+        if (place == GNM_PLACE_STAGED) place = GNM_PLACE_AUTO;
+        const bool fits = leaf_bytes + 1024 <= (size_t)c->smem_optin;
+        if (place == GNM_PLACE_SMEM && !fits)
+            return fail(GNM_E_INVAL, "learned-index leaves too large for shared memory");
+        s->rmi_global = place == GNM_PLACE_L2 || !fits;
+        lookup_bytes = s->rmi_global ? 0 : leaf_bytes;
     } else if (mode == GNM_LOOKUP_RADIX) {
         uint32_t bits = cfg.radix_bits ? cfg.radix_bits : c->tuned.radix_bits;
         if (bits && (bits < 4 || bits > 16)) return fail(GNM_E_INVAL, "radix_bits must be 4..16");
@@ -437,7 +447,7 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s, size_t n_win) {
     s->block = block;
     s->unroll = unroll;
     s->smem = aggregate_smem_bytes(s->split ? kLookupKeys : s->lookup, s->table, nr, rows, cap,
-                                   s->lookup == kLookupRmi ? c->rmi.n_leaves : 0, s->radix_bits);
+                                   s->lookup == kLookupRmi && !s->rmi_global ? c->rmi.n_leaves : 0, s->radix_bits);
     if (s->smem > (size_t)c->smem_optin) return fail(GNM_E_INVAL, "shared-memory layout exceeds the device limit");
     int cps = cfg.ctas_per_sm ? cfg.ctas_per_sm : c->tuned.ctas_per_sm;
     const int by_threads = std::max(1, 2048 / block);
@@ -562,6 +572,7 @@ gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* off
     p.table_cap = sh.cap;
     p.radix_bits = sh.radix_bits;
     p.dir_iters = sh.dir_iters;
+    p.rmi.leaves_global = sh.rmi_global ? 1u : 0u;
     p.n_total = N;
     uint64_t chunk = ceil_div(N, (uint64_t)sh.grid);
     chunk = (chunk + 3) & ~3ull;
@@ -1002,6 +1013,7 @@ void gnm_destroy(gnm_ctx* c) {
     free_dev(c->d_rmi_eps);
     free_dev(c->d_rmi_elo);
     free_dev(c->d_rmi_ehi);
+    free_dev(c->d_rmi_leaf4);
     delete c;
 }
 
@@ -1558,6 +1570,7 @@ gnm_status gnm_lookup(gnm_ctx* c, const uint32_t* addr, uint64_t n, uint32_t* si
     gnm_records none{};
     GNM_TRY(build_params(c, &none, &p));
     p.radix_bits = sh.radix_bits;
+    p.rmi.leaves_global = sh.rmi_global ? 1u : 0u;
     GNM_CU(launch_lookup(p, sh.lookup, addr, n, site_out, pos_out, (cudaStream_t)stream));
     c->last_launches = 1;
     return GNM_OK;

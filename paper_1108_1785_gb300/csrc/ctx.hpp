@@ -141,6 +141,7 @@ struct gnm_ctx {
     float* d_rmi_a = nullptr;
     float* d_rmi_b = nullptr;
     uint32_t* d_rmi_x0 = nullptr;
+    uint4* d_rmi_leaf4 = nullptr;  // leaf parameters interleaved (16 bytes per leaf)
     uint32_t* d_rmi_eps = nullptr;  // packed
     uint32_t* d_rmi_elo = nullptr;
     uint32_t* d_rmi_ehi = nullptr;

@@ -50,6 +50,8 @@ struct RmiDev {
     const float* b;
     const uint32_t* x0;
     const uint32_t* eps;   // packed eps_lo | eps_hi << 16; 0xFFFFFFFF: always full search
+    const uint4* leaf4;    // per leaf (a bits, b bits, x0, eps) interleaved: one 16-byte load
+    uint32_t leaves_global;  // this launch reads leaf4 from global memory instead of staging
 };
 
 struct AggParams {
@@ -169,6 +171,7 @@ struct LaunchShape {
     uint32_t cap;    // hash-table slots (kTableHash)
     uint32_t radix_bits;  // kLookupRadix directory bits
     uint32_t dir_iters;   // kLookupSmem with a directory: fixed search steps (see AggParams)
+    int rmi_global;       // kLookupRmi: leaf parameters read from global memory (L2/L1)
     size_t smem;
     // split launches: a lookup kernel (this lookup method) writes keys, then the
     // aggregation kernel reads them (kLookupKeys)
@@ -244,6 +247,8 @@ cudaError_t rmi_eps_from_samples(const RmiDev& model, const uint32_t* keys, cons
                                  uint32_t* d_eps_hi, cudaStream_t st);
 cudaError_t rmi_pack_eps(const uint32_t* lo, const uint32_t* hi, uint32_t* packed,
                          uint32_t n_leaves, cudaStream_t st);
+cudaError_t rmi_pack_leaf4(const float* a, const float* b, const uint32_t* x0, const uint32_t* eps, uint4* out,
+                           uint32_t L, cudaStream_t st);
 cudaError_t rmi_linear_grad(const float* z, const float* y, uint64_t n, float w, float c,
                             double* d_acc3, cudaStream_t st);
 cudaError_t rmi_mlp_grad(const float* xn, const float* y, uint64_t n, uint32_t hidden,

@@ -160,7 +160,7 @@ __global__ void k_lookup(const __grid_constant__ AggParams p, const uint32_t* __
         for (uint32_t i = threadIdx.x; i <= nd; i += blockDim.x) d[i] = __ldg(p.dir16 + ((size_t)i << sh));
         s_starts = d;
     }
-    if (LOOKUP == kLookupRmi) {
+    if (LOOKUP == kLookupRmi && !p.rmi.leaves_global) {
         const uint32_t L = p.rmi.n_leaves;
         float* a = reinterpret_cast<float*>(smem_raw);
         float* b = a + L;
@@ -284,7 +284,7 @@ cudaError_t launch_lookup(const AggParams& p, int lookup, const uint32_t* addr, 
     if (lookup == kLookupSmem) smem = (size_t)p.n_ranges * 4;
     if (lookup == kLookupStaged) smem = (size_t)p.n_blocks * 4;
     if (lookup == kLookupRadix) smem = ((size_t)1 << p.radix_bits) * 4 + 4;
-    if (lookup == kLookupRmi) smem = (size_t)p.rmi.n_leaves * 16;
+    if (lookup == kLookupRmi) smem = p.rmi.leaves_global ? 0 : (size_t)p.rmi.n_leaves * 16;
     cudaError_t e;
     switch (lookup) {
         case kLookupSmem:

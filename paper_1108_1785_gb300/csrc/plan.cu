@@ -218,7 +218,7 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
             for (int d : {1, 2, 3, 4, 5})
                 if ((int)lg - d >= 4 && (int)lg - d <= 14) bits_v.push_back((int)lg - d);
         }
-        if (base_shape.lookup == kLookupRmi) places_v.push_back(GNM_PLACE_AUTO);
+        if (base_shape.lookup == kLookupRmi) places_v = {GNM_PLACE_AUTO, GNM_PLACE_L2};  // leaves staged or not
         else places_v.assign(std::begin(places), std::end(places));
     }
     const int cpss[] = {0, 1};

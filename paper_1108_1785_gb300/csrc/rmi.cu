@@ -307,7 +307,8 @@ __global__ void k_eps_samples(const RmiDev m, const uint32_t* __restrict__ keys,
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_s; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t x = __ldg(keys + i), t = __ldg(pos + i);
         const uint32_t l = dev::rmi_root(m, x);
-        const uint32_t p = dev::rmi_leaf_pos(m.a, m.b, m.x0, l, x, n);
+        const dev::RmiLeaf f{__ldg(m.a + l), __ldg(m.b + l), __ldg(m.x0 + l), 0u};
+        const uint32_t p = dev::rmi_leaf_pos(f, x, n);
         flush_eps(l, p > t ? p - t : 0u, t > p ? t - p : 0u, elo, ehi);
     }
 }
@@ -316,6 +317,14 @@ __global__ void k_pack_eps(const uint32_t* lo, const uint32_t* hi, uint32_t* pac
     const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= L) return;
     packed[l] = (lo[l] > 0xFFFFu || hi[l] > 0xFFFFu) ? 0xFFFFFFFFu : (lo[l] | (hi[l] << 16));
+}
+
+// Leaf parameters interleaved for lookups that read them from global memory.
+__global__ void k_pack_leaf4(const float* a, const float* b, const uint32_t* x0, const uint32_t* eps, uint4* out,
+                             uint32_t L) {
+    const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= L) return;
+    out[l] = make_uint4(__float_as_uint(a[l]), __float_as_uint(b[l]), x0[l], eps[l]);
 }
 
 int grid_for(uint64_t n) {
@@ -527,6 +536,12 @@ cudaError_t rmi_eps_from_samples(const RmiDev& m, const uint32_t* keys, const ui
     RMI_CU(cudaMemsetAsync(elo, 0, (size_t)m.n_leaves * 4, st));
     RMI_CU(cudaMemsetAsync(ehi, 0, (size_t)m.n_leaves * 4, st));
     k_eps_samples<<<grid_for(n_s), kThreads, 0, st>>>(m, keys, pos, n_s, n, elo, ehi);
+    return cudaGetLastError();
+}
+
+cudaError_t rmi_pack_leaf4(const float* a, const float* b, const uint32_t* x0, const uint32_t* eps, uint4* out,
+                           uint32_t L, cudaStream_t st) {
+    k_pack_leaf4<<<(L + 255) / 256, 256, 0, st>>>(a, b, x0, eps, out, L);
     return cudaGetLastError();
 }
 

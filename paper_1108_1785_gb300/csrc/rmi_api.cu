@@ -18,6 +18,8 @@ gnm_status ensure_leaves(gnm_ctx* c, uint32_t L) {
     cudaFree(c->d_rmi_eps);
     cudaFree(c->d_rmi_elo);
     cudaFree(c->d_rmi_ehi);
+    cudaFree(c->d_rmi_leaf4);
+    c->d_rmi_leaf4 = nullptr;
     c->d_rmi_a = c->d_rmi_b = nullptr;
     c->d_rmi_x0 = c->d_rmi_eps = c->d_rmi_elo = c->d_rmi_ehi = nullptr;
     c->rmi_cap = 0;
@@ -27,6 +29,7 @@ gnm_status ensure_leaves(gnm_ctx* c, uint32_t L) {
     GNM_CU(cudaMalloc(&c->d_rmi_eps, (size_t)L * 4));
     GNM_CU(cudaMalloc(&c->d_rmi_elo, (size_t)L * 4));
     GNM_CU(cudaMalloc(&c->d_rmi_ehi, (size_t)L * 4));
+    GNM_CU(cudaMalloc(&c->d_rmi_leaf4, (size_t)L * 16));
     c->rmi_cap = L;
     return GNM_OK;
 }
@@ -42,6 +45,7 @@ gnm_status finish_model(gnm_ctx* c, RmiDev& m, bool exhaustive, const uint32_t* 
     if (exhaustive) GNM_CU(rmi_eps_sweep(m, c->d_starts, nr, c->d_rmi_elo, c->d_rmi_ehi, c->sm_count, st));
     else GNM_CU(rmi_eps_from_samples(m, keys, pos, n, nr, c->d_rmi_elo, c->d_rmi_ehi, st));
     GNM_CU(rmi_pack_eps(c->d_rmi_elo, c->d_rmi_ehi, c->d_rmi_eps, m.n_leaves, st));
+    GNM_CU(rmi_pack_leaf4(m.a, m.b, m.x0, c->d_rmi_eps, c->d_rmi_leaf4, m.n_leaves, st));
     GNM_CU(cudaEventRecord(e1, st));
     GNM_CU(cudaEventSynchronize(e1));
     float ms = 0;
@@ -50,6 +54,8 @@ gnm_status finish_model(gnm_ctx* c, RmiDev& m, bool exhaustive, const uint32_t* 
     cudaEventDestroy(e1);
     if (sweep_ms) *sweep_ms = ms;
     m.eps = c->d_rmi_eps;
+    m.leaf4 = c->d_rmi_leaf4;
+    m.leaves_global = 0;
     c->rmi = m;
     c->rmi_ready = true;
     return GNM_OK;

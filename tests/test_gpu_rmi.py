@@ -319,3 +319,41 @@ def test_rmi_export_import_roundtrip(gnm, c3, trained_linear):
     for k in ("a", "b", "x0", "eps_lo", "eps_hi"):
         np.testing.assert_array_equal(m[k], m2[k])
     other.close()
+
+
+@pytest.mark.parametrize("leaves,placement,split", [(4096, "L2", "TWO_KERNELS"), (4096, "L2", "FUSED"),
+                                                    (65536, "AUTO", "TWO_KERNELS")])
+def test_rmi_leaves_in_global_memory(gnm, c3, trained_linear, leaves, placement, split):
+    """Leaf parameters read from global memory, one interleaved 16-byte load per lookup: asked
+    for with the L2 placement, and automatic for 65,536 leaves (1 MB, beyond shared memory).
+    Batch lookups and windows are exact, with no fallback; more leaves give tighter bounds."""
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx = gnm.Context(window_slots=4, placement=getattr(gnm, "PLACE_" + placement),
+                      split=getattr(gnm, "SPLIT_" + split))
+    ctx.load(reg)
+    rep = ctx.rmi_train(to_dev(keys), root_kind=gnm.ROOT_LINEAR, n_leaves=leaves, leaf_iters=4)
+    if leaves == 65536:  # tighter than the 4,096-leaf model trained on the same keys
+        assert rep.eps_mean < trained_linear[1].eps_mean
+    ctx.rmi_violations(reset=True)
+    x = probe_set(starts, n_random=200_000)
+    dx = to_dev(x)
+    site = torch.empty_like(dx)
+    pos = torch.empty_like(dx)
+    ctx.lookup(dx, site, pos)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(pos.cpu().numpy().view(np.uint32), np.searchsorted(starts, x, side="right") - 1)
+    np.testing.assert_array_equal(site.cpu().numpy().view(np.uint32), lpm.lookup(x))
+    ctx.process(gnm.Records.to_device(rec), 1)
+    assert_window_matches(ctx.dense(1), oracle_full(reg, rec, lpm=lpm))
+    assert ctx.rmi_violations() == 0
+    ctx.close()
+
+
+def test_rmi_leaves_too_large_for_shared_memory(gnm, c3):
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx = gnm.Context(window_slots=2, placement=gnm.PLACE_SMEM)
+    ctx.load(reg)
+    ctx.rmi_train(to_dev(keys), root_kind=gnm.ROOT_LINEAR, n_leaves=65536, leaf_iters=2)
+    with pytest.raises(gnm.GnmError, match="too large for shared memory"):
+        ctx.process(gnm.Records.to_device({k: v[:1000] for k, v in rec.items()}), 1)
+    ctx.close()
