@@ -366,7 +366,7 @@ enum { GNM_RMI_ROOT_LINEAR = 0, GNM_RMI_ROOT_MLP = 1 };
 
 typedef struct {
     int32_t root_kind;   /* GNM_RMI_ROOT_* */
-    uint32_t n_leaves;   /* 1..65536 (4096) */
+    uint32_t n_leaves;   /* 1..1048576 (4096) */
     uint32_t hidden;     /* MLP root width: 8, 16 or 32 (32) */
     uint32_t leaf_iters; /* gradient steps for the linear stages (4) */
     uint32_t mlp_steps;  /* Adam steps for the MLP root (600) */

@@ -15,7 +15,7 @@ constexpr uint32_t kRateBuckets = GNM_RATE_BUCKETS;  // 10 kb/s buckets, the las
 constexpr int kAccCols = 5;         // accumulator row: flows<<32|e_flows, ineligible oct, pkts, e_oct, e_dur
 constexpr size_t kSmemRowBytes = 20;  // per-CTA shared-memory row: packed counts + 4 low words
 constexpr int kUnmatched = 4;       // classes appended after the 2*n_sites site rows
-constexpr int kMaxLeaves = 65536;
+constexpr int kMaxLeaves = 1 << 20;
 constexpr int kMaxHidden = 32;
 constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 

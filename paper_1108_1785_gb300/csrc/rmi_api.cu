@@ -87,7 +87,7 @@ gnm_status gnm_rmi_train(gnm_ctx* c, const uint32_t* keys, uint64_t n, const gnm
     if (cfg_in) cfg = *cfg_in;
     else gnm_rmi_config_default(&cfg);
     if (n == 0) return fail(GNM_E_INVAL, "no training keys");
-    if (cfg.n_leaves == 0 || cfg.n_leaves > (uint32_t)kMaxLeaves) return fail(GNM_E_INVAL, "n_leaves must be 1..65536");
+    if (cfg.n_leaves == 0 || cfg.n_leaves > (uint32_t)kMaxLeaves) return fail(GNM_E_INVAL, "n_leaves must be 1..1048576");
     if (cfg.root_kind != GNM_RMI_ROOT_LINEAR && cfg.root_kind != GNM_RMI_ROOT_MLP)
         return fail(GNM_E_INVAL, "unknown root kind");
     if (cfg.root_kind == GNM_RMI_ROOT_MLP && cfg.hidden != 8 && cfg.hidden != 16 && cfg.hidden != 32)
@@ -250,7 +250,7 @@ gnm_status gnm_rmi_import(gnm_ctx* c, int32_t root_kind, uint32_t L, const float
                           const float* b, const uint32_t* x0, void* stream) {
     if (!c || !root || !a || !b || !x0) return fail(GNM_E_INVAL, "NULL argument");
     if (!c->have_registry) return fail(GNM_E_STATE, "no registry loaded");
-    if (L == 0 || L > (uint32_t)kMaxLeaves) return fail(GNM_E_INVAL, "n_leaves must be 1..65536");
+    if (L == 0 || L > (uint32_t)kMaxLeaves) return fail(GNM_E_INVAL, "n_leaves must be 1..1048576");
     if (root_kind != GNM_RMI_ROOT_LINEAR && root_kind != GNM_RMI_ROOT_MLP) return fail(GNM_E_INVAL, "unknown root kind");
     if (c->h_starts.size() >= (1u << 24)) return fail(GNM_E_INVAL, "learned index needs fewer than 2^24 ranges");
     GNM_CU(cudaSetDevice(c->device));
