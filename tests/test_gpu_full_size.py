@@ -1,0 +1,77 @@
+"""Parity at the benchmark's full sizes, in the launch configurations bench.py times:
+- 256 uneven windows, 84.5 M records, one autotuned CUDA-graph launch: sampled windows
+  against the oracle one by one, and for every window the invariant that its sums over
+  keys add up to its record count and octets;
+- one 50 M-record window on the learned-index registry with the 65,536-leaf model whose
+  leaves are read from global memory: the whole window against the oracle.
+Integers bit-exact, rates within 1e-12 (and bit-identical where compared directly)."""
+import numpy as np
+import pytest
+
+import flowgen as fg
+import oracle
+from helpers import assert_window_matches, oracle_full
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gnm():
+    from paper_1108_1785_gb300 import build, gnm as g
+    build.build()
+    return g
+
+
+def test_batched_256_windows_full_size(gnm):
+    reg = fg.registry_c1()
+    counts = fg.uneven_windows_c4()
+    rec, off = fg.batched_records_c4(reg, counts)
+    n_win = len(off) - 1
+    assert n_win == 256 and int(off[-1]) > 80_000_000
+    ctx = gnm.Context(window_slots=n_win + 8)
+    ctx.load(reg)
+    d = gnm.Records.to_device(rec)
+    ids = np.arange(n_win, dtype=np.uint64)
+    ctx.autotune(d, off, ids)
+    plan = ctx.plan(d, off, ids)
+    plan.launch()
+    torch.cuda.synchronize()
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    rng = np.random.default_rng(4)
+    sample = sorted({int(np.argmax(counts)), int(np.argmin(counts)), 0, n_win - 1,
+                     *rng.choice(n_win, size=6, replace=False).tolist()})
+    for w in sample:
+        part = {k: v[off[w]:off[w + 1]] for k, v in rec.items()}
+        assert_window_matches(ctx.dense(int(ids[w])), oracle_full(reg, part, lpm=lpm))
+    for w in range(n_win):  # every record lands in one key; octets add up
+        st, un, _, _ = ctx.dense(int(ids[w]))
+        assert int(st[:, 0].sum()) + int(un[:, 0].sum()) == int(counts[w])
+        o = rec["dOctets"][off[w]:off[w + 1]].astype(np.uint64).sum()
+        assert int(st[:, 1].sum()) + int(un[:, 1].sum()) == int(o)
+    plan.close()
+    ctx.close()
+
+
+def test_learned_index_window_full_size(gnm):
+    reg = fg.registry_c3()
+    n = 50_000_000
+    rec = fg.make_records(reg, n, seed=2, p_reg=0.9, zipf_s=0.9)
+    tr = fg.make_records(reg, 5_000_000, seed=12, p_reg=0.9, zipf_s=0.9)
+    keys = torch.from_numpy(np.concatenate([tr["srcaddr"], tr["dstaddr"]]).view(np.int32)).cuda()
+    ctx = gnm.Context(window_slots=4, lookup_mode=gnm.LOOKUP_RMI)
+    ctx.load(reg)
+    ctx.rmi_train(keys, root_kind=gnm.ROOT_LINEAR, n_leaves=65536, leaf_iters=4)
+    ctx.rmi_violations(reset=True)
+    plan = ctx.plan(gnm.Records.to_device(rec), [0, n], [1])
+    plan.launch()
+    torch.cuda.synchronize()
+    got = ctx.dense(1)
+    want = oracle_full(reg, rec, n_threads=16)
+    assert_window_matches(got, want)
+    gr, wr = np.asarray(got[2]), np.asarray(want[2])
+    ok = ~np.isnan(wr)
+    np.testing.assert_array_equal(gr[ok].view(np.uint64), wr[ok].view(np.uint64))
+    assert ctx.rmi_violations() == 0
+    plan.close()
+    ctx.close()
