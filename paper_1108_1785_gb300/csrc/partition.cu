@@ -123,16 +123,33 @@ __global__ void __launch_bounds__(kPartThreads)
         const WinDesc wd = p.wins[w];
         if (wd.begin >= hi) break;
         const uint64_t e0 = min(wd.end, hi);
+        // a tile's five fields are in registers before it is sorted; the next tile of the
+        // segment is loaded while this one goes out, so its memory latency overlaps the stores
+        uint32_t v[5][kTileRecs];
+        auto load = [&](uint64_t t0) {
+            const uint32_t n = (uint32_t)min((uint64_t)kTile, e0 - t0);
+#pragma unroll
+            for (int u = 0; u < kTileRecs; ++u) {
+                const uint32_t j = tid + u * kPartThreads;
+                const bool ok = j < n;
+                const uint64_t i = t0 + (ok ? j : 0u);
+                v[0][u] = ok ? __ldcs(p.src + i) : 0u;
+                v[1][u] = ok ? __ldcs(p.pkts + i) : 0u;
+                v[2][u] = ok ? __ldcs(p.oct + i) : 0u;
+                v[3][u] = ok ? __ldcs(p.first + i) : 0u;
+                v[4][u] = ok ? __ldcs(p.last + i) : 0u;
+            }
+        };
+        if (max(wd.begin, lo) < e0) load(max(wd.begin, lo));
         for (uint64_t t0 = max(wd.begin, lo); t0 < e0; t0 += kTile) {
             const uint32_t n = (uint32_t)min((uint64_t)kTile, e0 - t0);
             for (uint32_t g = tid; g < groups; g += kPartThreads) hist[g] = 0u;
             __syncthreads();
-            uint32_t key[kTileRecs], grp[kTileRecs], rk[kTileRecs];
+            uint32_t grp[kTileRecs], rk[kTileRecs];
 #pragma unroll
             for (int u = 0; u < kTileRecs; ++u) {
                 const uint32_t j = tid + u * kPartThreads;
-                key[u] = j < n ? __ldg(p.src + t0 + j) : 0u;
-                grp[u] = key[u] / rows;
+                grp[u] = v[0][u] / rows;
                 rk[u] = j < n ? atomicAdd(&hist[grp[u]], 1u) : 0u;
             }
             __syncthreads();
@@ -144,16 +161,14 @@ __global__ void __launch_bounds__(kPartThreads)
                 const uint32_t j = tid + u * kPartThreads;
                 if (j < n) {
                     const uint32_t pos = toff[grp[u]] + rk[u];
-                    const uint64_t i = t0 + j;
-                    s_rec[pos] = key[u] - grp[u] * rows;
-                    s_rec[kTile + pos] = __ldcs(p.pkts + i);
-                    s_rec[2 * kTile + pos] = __ldcs(p.oct + i);
-                    s_rec[3 * kTile + pos] = __ldcs(p.first + i);
-                    s_rec[4 * kTile + pos] = __ldcs(p.last + i);
+                    s_rec[pos] = v[0][u] - grp[u] * rows;
+#pragma unroll
+                    for (int f = 1; f < 5; ++f) s_rec[f * kTile + pos] = v[f][u];
                     s_grp[pos] = grp[u];
                 }
             }
             __syncthreads();
+            if (t0 + kTile < e0) load(t0 + kTile);
             for (uint32_t j = tid; j < n; j += kPartThreads) {
                 const uint32_t g = s_grp[j];
                 const uint32_t r = gpos[g] + (j - toff[g]);
