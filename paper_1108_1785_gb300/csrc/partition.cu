@@ -51,8 +51,18 @@ __global__ void __launch_bounds__(kPartThreads)
         const WinDesc wd = p.wins[w];
         if (wd.begin >= hi) break;
         const uint64_t e0 = min(wd.end, hi);
-        for (uint64_t i = max(wd.begin, lo) + threadIdx.x; i < e0; i += blockDim.x)
-            atomicAdd(&hist[w * groups + __ldg(p.src + i) / rows], 1u);
+        // four keys per thread and step, their loads in flight together
+        for (uint64_t i = max(wd.begin, lo) + threadIdx.x; i < e0; i += 4u * blockDim.x) {
+            uint32_t k[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t j = i + (uint64_t)u * blockDim.x;
+                k[u] = j < e0 ? __ldcs(p.src + j) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i + (uint64_t)u * blockDim.x < e0) atomicAdd(&hist[w * groups + k[u] / rows], 1u);
+        }
     }
     __syncthreads();
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x)
