@@ -162,8 +162,14 @@ __device__ __forceinline__ void radix_block(const uint32_t* dir, uint32_t bits, 
 #pragma unroll
     for (int j = 0; j < R; ++j) {
         const uint4* q = reinterpret_cast<const uint4*>(pairs) + (BR / 2) * (size_t)g[j];
-        lo[j] = __ldg(q);                          // start0 site0 start1 site1
-        if (BR == 4) hi[j] = __ldg(q + 1);         // start2 site2 start3 site3
+        if (BR == 2) {
+            lo[j] = __ldg(q);  // start0 site0 start1 site1
+        } else {  // one 32-byte load (a 32-byte aligned block): start0 site0 .. start3 site3
+            asm("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                : "=r"(lo[j].x), "=r"(lo[j].y), "=r"(lo[j].z), "=r"(lo[j].w), "=r"(hi[j].x), "=r"(hi[j].y),
+                  "=r"(hi[j].z), "=r"(hi[j].w)
+                : "l"(q));
+        }
     }
 #pragma unroll
     for (int j = 0; j < R; ++j) {
