@@ -132,18 +132,27 @@ __device__ __forceinline__ void pair_search(const uint2* __restrict__ pairs, con
 // the blocks' first starts `smp` (shared memory) picks it, and one load of its BR (start,
 // site) pairs (16 bytes for BR = 2, 32 for BR = 4) gives the site. Pairs past the last
 // range are start 0xFFFFFFFF with the last range's site, so the count is right for every x.
+// With fewer than 2^16 blocks (`packed`) the directory holds one word per bucket: the first
+// block in its low 16 bits and the number of blocks after it in the high 16, one load instead
+// of two.
 template <int BR, int R>
 __device__ __forceinline__ void radix_block(const uint32_t* dir, uint32_t bits, const uint32_t* smp,
                                             const uint2* __restrict__ pairs, const uint32_t (&x)[R],
-                                            uint32_t (&site)[R]) {
+                                            uint32_t (&site)[R], bool packed) {
     static_assert(BR == 2 || BR == 4, "blocks of 2 or 4 ranges");
     uint32_t g[R], len[R];
     bool more = false;
 #pragma unroll
     for (int j = 0; j < R; ++j) {
         const uint32_t t = x[j] >> (32u - bits);
-        g[j] = dir[t];
-        len[j] = dir[t + 1] - g[j] + 1u;
+        if (packed) {
+            const uint32_t e = dir[t];
+            g[j] = e & 0xFFFFu;
+            len[j] = (e >> 16) + 1u;
+        } else {
+            g[j] = dir[t];
+            len[j] = dir[t + 1] - g[j] + 1u;
+        }
         more |= len[j] > 1u;
     }
     while (more) {
@@ -912,9 +921,9 @@ __device__ __forceinline__ void lookup_sites(const AggParams& p, const Smem& sm,
 #pragma unroll
         for (int j = 0; j < R; ++j) site[j] = __ldg(p.rsite + idx[j]);
     } else if (LOOKUP == kLookupRadixBlk) {
-        radix_block<4, R>(sm.s_starts, p.radix_bits, sm.s_site, p.pairs, x, site);
+        radix_block<4, R>(sm.s_starts, p.radix_bits, sm.s_site, p.pairs, x, site, p.n_blk4 < 65536u);
     } else if (LOOKUP == kLookupRadixBlk2) {
-        radix_block<2, R>(sm.s_starts, p.radix_bits, sm.s_site, p.pairs, x, site);
+        radix_block<2, R>(sm.s_starts, p.radix_bits, sm.s_site, p.pairs, x, site, p.n_blk2 < 65536u);
     } else if (LOOKUP == kLookupRadixBlk2H) {
         radix_block16<R>(sm.dh, sm.s16, p.pairs, x, site);
     } else if (LOOKUP == kLookupRmi) {
@@ -1093,7 +1102,15 @@ __device__ __forceinline__ void stage_lookup(const AggParams& p, unsigned char* 
         const uint32_t nb = LOOKUP == kLookupRadixBlk ? p.n_blk4 : p.n_blk2;
         uint32_t* d = reinterpret_cast<uint32_t*>(base);
         const uint32_t nd = 1u << p.radix_bits, sh = 16u - p.radix_bits;
-        for (uint32_t i = tid; i <= nd; i += B) d[i] = __ldg(p.dir16 + ((size_t)i << sh)) >> lg;
+        if (nb < 65536u) {  // one word per bucket: first block (low 16 bits), blocks after it
+            for (uint32_t i = tid; i < nd; i += B) {
+                const uint32_t b0 = __ldg(p.dir16 + ((size_t)i << sh)) >> lg;
+                const uint32_t b1 = __ldg(p.dir16 + ((size_t)(i + 1u) << sh)) >> lg;
+                d[i] = b0 | ((b1 - b0) << 16);
+            }
+        } else {
+            for (uint32_t i = tid; i <= nd; i += B) d[i] = __ldg(p.dir16 + ((size_t)i << sh)) >> lg;
+        }
         uint32_t* smp = d + (((nd + 1u) + 3u) & ~3u);
         for (uint32_t i = tid; i < nb; i += B) smp[i] = __ldg(sample + i);
         sm.s_starts = d;
