@@ -868,10 +868,17 @@ __device__ __forceinline__ void lookup_sites(const AggParams& p, const Smem& sm,
             // loop has no per-lane exit; a step on a one-range interval keeps it
             uint32_t len[R];
 #pragma unroll
+            const bool packed = p.n_ranges < 65536u;
             for (int j = 0; j < R; ++j) {
                 const uint32_t t = x[j] >> (32u - p.radix_bits);
-                idx[j] = sm.s_dir[t];
-                len[j] = sm.s_dir[t + 1] - idx[j] + 1u;
+                if (packed) {
+                    const uint32_t e = sm.s_dir[t];
+                    idx[j] = e & 0xFFFFu;
+                    len[j] = (e >> 16) + 1u;
+                } else {
+                    idx[j] = sm.s_dir[t];
+                    len[j] = sm.s_dir[t + 1] - idx[j] + 1u;
+                }
             }
 #pragma unroll 1
             for (uint32_t it = 0; it < p.dir_iters; ++it) {
@@ -1080,7 +1087,15 @@ __device__ __forceinline__ void stage_lookup(const AggParams& p, unsigned char* 
         if (p.radix_bits && p.dir16) {  // every 2^(16-bits)-th entry of the 16-bit directory
             uint32_t* d = si + p.n_ranges;
             const uint32_t nd = 1u << p.radix_bits, sh = 16u - p.radix_bits;
-            for (uint32_t i = tid; i <= nd; i += B) d[i] = __ldg(p.dir16 + ((size_t)i << sh));
+            if (p.n_ranges < 65536u) {  // one word per bucket: first range, ranges after it
+                for (uint32_t i = tid; i < nd; i += B) {
+                    const uint32_t r0 = __ldg(p.dir16 + ((size_t)i << sh));
+                    const uint32_t r1 = __ldg(p.dir16 + ((size_t)(i + 1u) << sh));
+                    d[i] = r0 | ((r1 - r0) << 16);
+                }
+            } else {
+                for (uint32_t i = tid; i <= nd; i += B) d[i] = __ldg(p.dir16 + ((size_t)i << sh));
+            }
             sm.s_dir = d;
         }
     }
