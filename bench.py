@@ -41,10 +41,14 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "hour_c2_dram_traffic.json")
 
 
 def kernel_source_hash() -> str:
+    """Hash of the kernel sources' code: comments and whitespace do not count."""
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            code = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        code = re.sub(r"//[^\n]*", "", code)
+        h.update(re.sub(r"\s+", "", code).encode())
     return h.hexdigest()[:16]
 
 

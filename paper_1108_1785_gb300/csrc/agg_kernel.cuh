@@ -4,10 +4,12 @@
 //
 // One persistent launch processes any number of windows laid out back to back in one
 // struct-of-arrays batch. CTA b owns the contiguous record range
-// [b*chunk, (b+1)*chunk); it walks the windows that overlap it, accumulates each
-// window's per-(site, direction) sums in shared memory, adds them to the window's
-// global accumulator row with one atomic per column and key, and takes a ticket; the
-// CTA that takes a window's last ticket finalises it (rates and flags) in place.
+// [b*chunk, (b+1)*chunk); it walks the windows that overlap it and accumulates each
+// window's per-(site, direction) sums in shared memory. At the end of its segment of a
+// window it hands them over: with a direct table, as plain stores of its rows to a partial
+// block of its own; otherwise with one global atomic per column and key. It then takes the
+// window's ticket; the CTA that takes the last one finalises the window (rates and flags)
+// when its key space is small, else a grid-wide finalisation kernel follows.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
