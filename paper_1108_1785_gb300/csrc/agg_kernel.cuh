@@ -748,24 +748,11 @@ __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot,
     for (uint32_t kb = k0 - lane; kb < keys; kb += step) {
         const uint32_t k = kb + lane;
         const bool act = k < keys;
-        // accumulator rows of an unmarked group are zero: neither read nor cleared
-        const bool dirty = !dg || (kL1 ? dg[kb >> 5] : __ldcg(dg + (kb >> 5))) != 0;
-        __syncwarp();
-        if (dg && dirty && lane == 0) dg[kb >> 5] = 0;
-        uint64_t sv[kNStat] = {0, 0, 0, 0, 0, 0};
+        // the group's dirty mark and the partial blocks (four at a time) are loaded before any
+        // of them is used, so their latencies overlap
+        const uint32_t mark = dg ? (kL1 ? dg[kb >> 5] : __ldcg(dg + (kb >> 5))) : 1u;
+        uint64_t packed = 0, oc = 0, pk = 0, eo = 0, ed = 0;
         if (act) {
-            uint64_t* a = acc + (size_t)k * kAccCols;
-            uint64_t packed = 0, oc = 0, pk = 0, eo = 0, ed = 0;
-            if (dirty) {
-                packed = ld64(a);
-                oc = ld64(a + 1);
-                pk = ld64(a + 2);
-                eo = ld64(a + 3);
-                ed = ld64(a + 4);
-                // accumulators return to zero for the slot's next window
-#pragma unroll
-                for (int c = 0; c < kAccCols; ++c) a[c] = 0;
-            }
             const uint32_t* kp = parts + k;
             uint32_t np = n_parts;
             if (p.part_groups) {
@@ -774,7 +761,6 @@ __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot,
                 kp = p.partials + (size_t)pd.x * pstride + (k - g * rows);
                 np = p.partials ? pd.y : 0u;
             }
-            // partial blocks of the window's CTAs, four at a time (their loads in flight together)
             for (uint32_t q0 = 0; q0 < np; q0 += 4) {
                 uint32_t v[4][kRowWords];
 #pragma unroll
@@ -791,6 +777,24 @@ __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot,
                     eo += v[j][3];
                     ed += v[j][4];
                 }
+            }
+        }
+        // accumulator rows of an unmarked group are zero: neither read nor cleared
+        const bool dirty = mark != 0u;
+        __syncwarp();
+        if (dg && dirty && lane == 0) dg[kb >> 5] = 0;
+        uint64_t sv[kNStat] = {0, 0, 0, 0, 0, 0};
+        if (act) {
+            if (dirty) {
+                uint64_t* a = acc + (size_t)k * kAccCols;
+                packed += ld64(a);
+                oc += ld64(a + 1);
+                pk += ld64(a + 2);
+                eo += ld64(a + 3);
+                ed += ld64(a + 4);
+                // accumulators return to zero for the slot's next window
+#pragma unroll
+                for (int c = 0; c < kAccCols; ++c) a[c] = 0;
             }
             const uint64_t ef = packed & 0xFFFFFFFFull;
             sv[0] = packed >> 32;
