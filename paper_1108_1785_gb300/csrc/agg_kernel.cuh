@@ -537,6 +537,37 @@ __device__ __forceinline__ void srow_add_sums(const Smem& sm, int r, uint32_t ke
     if (g) touch(sm, key);
 }
 
+// srow_add for R items of a direct table (row = key) at once: every item's shared atomics
+// are issued before any wrap check reads their results, so their latencies overlap; the rare
+// wraps are handled after. The same per-atomic wrap test as srow_add, so the same sums.
+template <int R>
+__device__ __forceinline__ void srow_add_all(const Smem& sm, const Item (&it)[R], uint64_t* gacc) {
+    uint32_t o1[R], o2[R], o4[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        o1[j] = 0u;
+        o2[j] = 0u;
+        o4[j] = 0u;
+        if (it[j].valid) {
+            uint32_t* w = sm.t + it[j].key * kRowWords;
+            red32(w, it[j].elig ? 0x10001u : 1u);
+            o1[j] = atomicAdd(w + (it[j].elig ? 3 : 1), it[j].oc);
+            o2[j] = atomicAdd(w + 2, it[j].pk);
+            if (it[j].elig) o4[j] = atomicAdd(w + 4, it[j].dur);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        if (!it[j].valid) continue;
+        uint64_t* gk = gacc + (size_t)it[j].key * kAccCols;
+        const bool w1 = o1[j] > ~it[j].oc, w2 = o2[j] > ~it[j].pk, w4 = it[j].elig && o4[j] > ~it[j].dur;
+        if (w1) red_add(gk + (it[j].elig ? 3 : 1), 1ull << 32);
+        if (w2) red_add(gk + 2, 1ull << 32);
+        if (w4) red_add(gk + 4, 1ull << 32);
+        if (w1 || w2 || w4) touch(sm, it[j].key);
+    }
+}
+
 // Sum of a 32-bit value over the lanes of `peers`, exact in 64 bits (16-bit halves).
 __device__ __forceinline__ uint64_t peer_sum(unsigned peers, uint32_t v) {
     const uint32_t lo = __reduce_add_sync(peers, v & 0xFFFFu);
@@ -996,11 +1027,24 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
                                         const uint32_t (&oc)[R], const uint32_t (&fi)[R],
                                         const uint32_t (&la)[R]) {
     if constexpr (LOOKUP == kLookupKeys) {
+        if constexpr (TABLE == kTableDirect && AGG == GNM_AGG_DIRECT) {
+            Item its[R];
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-            const Item it = classify_key(p, valid[j], src[j], sm.key_base, pk[j], oc[j], fi[j], la[j]);
-            accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
-            if (sm.hist && it.valid && it.elig) rate_stat_add(sm, it.key, it.oc, it.dur);
+            for (int j = 0; j < R; ++j)
+                its[j] = classify_key(p, valid[j], src[j], sm.key_base, pk[j], oc[j], fi[j], la[j]);
+            srow_add_all<R>(sm, its, gacc);
+            if (sm.hist) {
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    if (its[j].valid && its[j].elig) rate_stat_add(sm, its[j].key, its[j].oc, its[j].dur);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const Item it = classify_key(p, valid[j], src[j], sm.key_base, pk[j], oc[j], fi[j], la[j]);
+                accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
+                if (sm.hist && it.valid && it.elig) rate_stat_add(sm, it.key, it.oc, it.dur);
+            }
         }
     } else {
         uint32_t x[R], site[R];
@@ -1011,11 +1055,24 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
             x[j] = sl[j] ? dst[j] : src[j];  // the remote endpoint
         }
         lookup_sites<LOOKUP, R>(p, sm, valid, x, site);
+        if constexpr (TABLE == kTableDirect && AGG == GNM_AGG_DIRECT) {
+            Item its[R];
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-            const Item it = classify(p, valid[j], sl[j], dl[j], pk[j], oc[j], fi[j], la[j], site[j]);
-            accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
-            if (sm.hist && it.valid && it.elig) rate_stat_add(sm, it.key, it.oc, it.dur);
+            for (int j = 0; j < R; ++j)
+                its[j] = classify(p, valid[j], sl[j], dl[j], pk[j], oc[j], fi[j], la[j], site[j]);
+            srow_add_all<R>(sm, its, gacc);
+            if (sm.hist) {
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    if (its[j].valid && its[j].elig) rate_stat_add(sm, its[j].key, its[j].oc, its[j].dur);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const Item it = classify(p, valid[j], sl[j], dl[j], pk[j], oc[j], fi[j], la[j], site[j]);
+                accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
+                if (sm.hist && it.valid && it.elig) rate_stat_add(sm, it.key, it.oc, it.dur);
+            }
         }
     }
 }
