@@ -779,50 +779,62 @@ __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot,
     for (uint32_t kb = k0 - lane; kb < keys; kb += step) {
         const uint32_t k = kb + lane;
         const bool act = k < keys;
-        // the group's dirty mark and the partial blocks (four at a time) are loaded before any
-        // of them is used, so their latencies overlap
+        // the group's dirty mark, the first four partial blocks and (for a marked group) the
+        // accumulator row are all loaded before any of them is used, so their latencies overlap
         const uint32_t mark = dg ? (kL1 ? dg[kb >> 5] : __ldcg(dg + (kb >> 5))) : 1u;
         uint64_t packed = 0, oc = 0, pk = 0, eo = 0, ed = 0;
-        if (act) {
-            const uint32_t* kp = parts + k;
-            uint32_t np = n_parts;
-            if (p.part_groups) {
-                const uint32_t g = k / rows;
-                const uint2 pd = p.part_desc[(size_t)win * p.part_groups + g];
-                kp = p.partials + (size_t)pd.x * pstride + (k - g * rows);
-                np = p.partials ? pd.y : 0u;
-            }
-            for (uint32_t q0 = 0; q0 < np; q0 += 4) {
-                uint32_t v[4][kRowWords];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint32_t* w = kp + (size_t)(q0 + j) * pstride;
-#pragma unroll
-                    for (int c = 0; c < kRowWords; ++c) v[j][c] = q0 + j < np ? ld32(w + (size_t)c * rows) : 0u;
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    packed += ((uint64_t)(v[j][0] & 0xFFFFu) << 32) | (v[j][0] >> 16);
-                    oc += v[j][1];
-                    pk += v[j][2];
-                    eo += v[j][3];
-                    ed += v[j][4];
-                }
-            }
+        const uint32_t* kp = parts + k;
+        uint32_t np = n_parts;
+        if (act && p.part_groups) {
+            const uint32_t g = k / rows;
+            const uint2 pd = p.part_desc[(size_t)win * p.part_groups + g];
+            kp = p.partials + (size_t)pd.x * pstride + (k - g * rows);
+            np = p.partials ? pd.y : 0u;
         }
+        if (!act) np = 0;
+        uint32_t v[4][kRowWords];
+        auto load4 = [&](uint32_t q0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t* w = kp + (size_t)(q0 + j) * pstride;
+#pragma unroll
+                for (int c = 0; c < kRowWords; ++c) v[j][c] = q0 + j < np ? ld32(w + (size_t)c * rows) : 0u;
+            }
+        };
+        auto add4 = [&]() {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                packed += ((uint64_t)(v[j][0] & 0xFFFFu) << 32) | (v[j][0] >> 16);
+                oc += v[j][1];
+                pk += v[j][2];
+                eo += v[j][3];
+                ed += v[j][4];
+            }
+        };
+        load4(0);
         // accumulator rows of an unmarked group are zero: neither read nor cleared
         const bool dirty = mark != 0u;
+        uint64_t av[kAccCols] = {0, 0, 0, 0, 0};
+        uint64_t* a = acc + (size_t)k * kAccCols;
+        if (act && dirty) {
+#pragma unroll
+            for (int c = 0; c < kAccCols; ++c) av[c] = ld64(a + c);
+        }
+        add4();
+        for (uint32_t q0 = 4; q0 < np; q0 += 4) {  // further partial blocks, four at a time
+            load4(q0);
+            add4();
+        }
         __syncwarp();
         if (dg && dirty && lane == 0) dg[kb >> 5] = 0;
         uint64_t sv[kNStat] = {0, 0, 0, 0, 0, 0};
         if (act) {
             if (dirty) {
-                uint64_t* a = acc + (size_t)k * kAccCols;
-                packed += ld64(a);
-                oc += ld64(a + 1);
-                pk += ld64(a + 2);
-                eo += ld64(a + 3);
-                ed += ld64(a + 4);
+                packed += av[0];
+                oc += av[1];
+                pk += av[2];
+                eo += av[3];
+                ed += av[4];
                 // accumulators return to zero for the slot's next window
 #pragma unroll
                 for (int c = 0; c < kAccCols; ++c) a[c] = 0;

@@ -63,7 +63,7 @@ __global__ void k_finalize(const __grid_constant__ AggParams p, uint32_t slot) {
 // blockIdx.y: window of the launch; its keys are spread over blockIdx.x.
 constexpr uint32_t kFinKeys = 256;
 
-__global__ void __launch_bounds__(kFinKeys) k_finalize_windows(const __grid_constant__ AggParams p) {
+__global__ void __launch_bounds__(kFinKeys, 4) k_finalize_windows(const __grid_constant__ AggParams p) {
     __shared__ __align__(16) uint64_t stage[kFinKeys * kNStat];  // per warp: 32 keys' stats rows
     const WinDesc wd = p.wins[blockIdx.y];
     const uint32_t* parts =
