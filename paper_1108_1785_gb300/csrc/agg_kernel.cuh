@@ -916,8 +916,8 @@ __device__ __forceinline__ void lookup_sites(const AggParams& p, const Smem& sm,
             // the same number of steps for every lane (enough for the largest bucket), so the
             // loop has no per-lane exit; a step on a one-range interval keeps it
             uint32_t len[R];
-#pragma unroll
             const bool packed = p.n_ranges < 65536u;
+#pragma unroll
             for (int j = 0; j < R; ++j) {
                 const uint32_t t = x[j] >> (32u - p.radix_bits);
                 if (packed) {
