@@ -40,15 +40,20 @@ KERNEL_SOURCES = ["paper_1108_1785_gb300/csrc/agg_kernel.cuh", "paper_1108_1785_
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "hour_c2_dram_traffic.json")
 
 
+def code_only(text: str) -> str:
+    """C/CUDA source without comments and whitespace."""
+    import re
+    code = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    code = re.sub(r"//[^\n]*", "", code)
+    return re.sub(r"\s+", "", code)
+
+
 def kernel_source_hash() -> str:
     """Hash of the kernel sources' code: comments and whitespace do not count."""
-    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
-            code = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
-        code = re.sub(r"//[^\n]*", "", code)
-        h.update(re.sub(r"\s+", "", code).encode())
+            h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
