@@ -17,6 +17,12 @@ Training (mean squared error):
   root target  = true position * L / n;   leaf target = true position
   linear stage on standardised input z = (d - mu) / sigma:  yhat = w z + c
   gradients    dL/dw = 2/m sum (yhat - y) z,  dL/dc = 2/m sum (yhat - y)
+
+Pins (tests/test_oracle_pins.py): the FP32 evaluation (xnorm, root_linear, root_mlp,
+_clamp_floor, leaf_first_addresses, leaf_predict) and the endpoint error bound against
+values worked out by hand in tests/golden/rmi_hand.json, including the FP32 rounding of x
+and of d, keys that rounding sends to the next leaf, and the clamps at 0 and n-1; least
+squares against numpy.polyfit; gradients against central finite differences.
 """
 from __future__ import annotations
 

@@ -499,3 +499,95 @@ def test_eps_endpoints_bound_holds_and_is_tight():
     np.maximum.at(got_hi, leaf, np.maximum(t - p, 0))
     np.testing.assert_array_equal(got_lo, elo)
     np.testing.assert_array_equal(got_hi, ehi)
+
+
+# ------------------------------------------------ learned index: hand-worked FP32 pins
+
+def _f(s):
+    return float.fromhex(s) if isinstance(s, str) and s not in ("nan", "inf", "-inf") else float(s)
+
+
+def _rmi_hand():
+    with open(os.path.join(GOLD, "rmi_hand.json")) as f:
+        return json.load(f)
+
+
+def test_rmi_hand_xnorm():
+    """fl(fl(x) * 2^-32), with the FP32 rounding of x worked out by hand."""
+    g = _rmi_hand()
+    x = np.array([c["x"] for c in g["xnorm"]], np.uint32)
+    want = np.array([_f(c["xn"]) for c in g["xnorm"]], np.float32)
+    got = rmi_ref.xnorm(x)
+    assert got.dtype == np.float32
+    np.testing.assert_array_equal(got, want)
+
+
+def test_rmi_hand_clamp_floor():
+    g = _rmi_hand()["clamp_floor"]
+    v = np.array([_f(s) for s in g["v"]], np.float32)
+    np.testing.assert_array_equal(rmi_ref._clamp_floor(v, g["n"]), np.array(g["want"]))
+
+
+def test_rmi_hand_root_linear():
+    """Linear root by hand, including keys that FP32 rounding sends to the next leaf."""
+    for blk in _rmi_hand()["root_linear"]:
+        x = np.array([c["x"] for c in blk["cases"]], np.uint32)
+        want = np.array([c["leaf"] for c in blk["cases"]])
+        got = rmi_ref.root_linear(_f(blk["ra"]), _f(blk["rb"]), x, blk["L"])
+        np.testing.assert_array_equal(got, want)
+
+
+def test_rmi_hand_root_mlp():
+    """1 -> 2 -> 1 ReLU root by hand (negative output clamped to 0, large output to L-1)."""
+    for blk in _rmi_hand()["root_mlp"]:
+        p = {"w1": np.array([_f(s) for s in blk["w1"]]), "b1": np.array([_f(s) for s in blk["b1"]]),
+             "w2": np.array([_f(s) for s in blk["w2"]]), "b2": _f(blk["b2"])}
+        x = np.array([c["x"] for c in blk["cases"]], np.uint32)
+        want = np.array([c["leaf"] for c in blk["cases"]])
+        np.testing.assert_array_equal(rmi_ref.root_mlp(p, x, blk["L"]), want)
+
+
+def test_rmi_hand_leaf_first_addresses():
+    """First address of every leaf of a monotone linear root: powers of two where FP32 is
+    exact, and the rounding ties at 2^29, 1.5*2^30 and 2.5*2^30 worked out by hand."""
+    for blk in _rmi_hand()["leaf_first_addresses"]:
+        got = rmi_ref.leaf_first_addresses(_f(blk["ra"]), _f(blk["rb"]), blk["L"])
+        np.testing.assert_array_equal(got, np.array(blk["first"], np.int64))
+
+
+def test_rmi_hand_leaf_predict():
+    """Leaf of each key through the root, then the leaf's FP32 prediction: negative
+    predictions clamp to 0, predictions past n-1 clamp to n-1, misrouted keys use the
+    leaf the rounding picked (negative d)."""
+    g = _rmi_hand()["leaf_predict"]
+    r = g["root"]
+    x = np.array([c["x"] for c in g["cases"]], np.uint32)
+    leaf = rmi_ref.root_linear(_f(r["ra"]), _f(r["rb"]), x, r["L"])
+    np.testing.assert_array_equal(leaf, np.array([c["leaf"] for c in g["cases"]]))
+    a = np.array([_f(s) for s in g["a"]])
+    b = np.array([_f(s) for s in g["b"]])
+    x0 = np.array(g["x0"], np.int64)
+    got = rmi_ref.leaf_predict(a, b, x0, leaf, x.astype(np.int64), g["n"])
+    np.testing.assert_array_equal(got, np.array([c["pos"] for c in g["cases"]]))
+
+
+def test_rmi_hand_eps_endpoints():
+    """A one-leaf model that is exact in real arithmetic over-predicts by one just below
+    each boundary because fl(x) rounds up to it: the bound is (1, 0) by hand."""
+    g = _rmi_hand()["eps_endpoints_linear"]
+    elo, ehi = rmi_ref.eps_endpoints_linear(np.array(g["starts"], np.uint32), _f(g["ra"]), _f(g["rb"]),
+                                            np.array([_f(s) for s in g["a"]]), np.array([_f(s) for s in g["b"]]),
+                                            np.array(g["x0"], np.int64), g["L"])
+    np.testing.assert_array_equal(elo, g["eps_lo"])
+    np.testing.assert_array_equal(ehi, g["eps_hi"])
+
+
+def test_rmi_hand_leaf_predict_rounds_d():
+    """The leaf-relative offset d is rounded to FP32 before the product: a hand case where
+    that rounding decides the floor."""
+    g = _rmi_hand()["leaf_predict_d_rounding"]
+    x = np.array([c["x"] for c in g["cases"]], np.int64)
+    leaf = np.zeros(x.size, np.int64)
+    got = rmi_ref.leaf_predict(np.array([_f(s) for s in g["a"]]), np.array([_f(s) for s in g["b"]]),
+                               np.array(g["x0"], np.int64), leaf, x, g["n"])
+    np.testing.assert_array_equal(got, np.array([c["pos"] for c in g["cases"]]))
