@@ -178,3 +178,150 @@ def eps_endpoints_linear(starts: np.ndarray, ra: float, rb: float, a, b, x0, n_l
     np.maximum.at(eps_lo, leaf, np.maximum(p_hi - t, 0))
     np.maximum.at(eps_hi, leaf, np.maximum(t - p_lo, 0))
     return eps_lo, eps_hi
+
+
+# ------------------------------------------------- minimax leaves and split leaves
+#
+# A leaf's worst-case error over every address it owns is what the proven bound
+# measures, so a leaf is fitted by minimising that error (a Chebyshev, or minimax, fit)
+# rather than the mean squared error over sampled lookups. Inside a leaf the true
+# position is a step function: constant t_k on each piece [dlo_k, dhi_k] of a range
+# (offsets from the leaf's first address). For a line f(d) = a d + c with a >= 0, the
+# largest under-prediction on a piece is at dlo_k and the largest over-prediction at
+# dhi_k, so the fit minimises
+#     E(a, c) = max( max_k (t_k - f(dlo_k)),  max_k (f(dhi_k) - t_k) ).
+# For a fixed slope the best c centres the band: with G(a) = max_k (t_k - a dlo_k) and
+# H(a) = min_k (t_k - a dhi_k), c = (G + H) / 2 and E = (G - H) / 2. G is convex and H
+# concave in a, so E(a) is convex and a ternary search finds its minimum. Since
+# E(a) >= a * w_max / 2 for the widest piece and E(0) = (t_max - t_min) / 2, the optimal
+# slope lies in [0, (t_max - t_min) / w_max].
+#
+# A leaf whose fitted window (about 2E + 3 positions after rounding and the floor) exceeds
+# a target is split into `count` equal sub-leaves of 2^shift addresses (the last one
+# takes the remainder): the hybrid form of Kraska et al.'s index, which replaces a leaf
+# whose error is too large, here with one more level of linear models. split[l] = ((count - 1) << 8) | shift
+# for a split leaf, 0 otherwise; sub-leaves follow the L leaves in leaf order.
+
+def minimax_line(dlo, dhi, t, iters: int = 200):
+    """FP64 minimax line over pieces: returns (a, c, E) with a >= 0 minimising E."""
+    dlo = np.asarray(dlo, np.float64)
+    dhi = np.asarray(dhi, np.float64)
+    t = np.asarray(t, np.float64)
+    if t.size == 0:
+        return 0.0, 0.0, 0.0
+
+    def band(a):
+        g = np.max(t - a * dlo)
+        h = np.min(t - a * dhi)
+        return g, h
+
+    wmax = max(float(np.max(dhi - dlo)), 1.0)
+    lo, hi = 0.0, float(t.max() - t.min()) / wmax
+    for _ in range(iters):
+        m1 = lo + (hi - lo) / 3.0
+        m2 = hi - (hi - lo) / 3.0
+        g1, h1 = band(m1)
+        g2, h2 = band(m2)
+        if g1 - h1 < g2 - h2:
+            hi = m2
+        else:
+            lo = m1
+    a = (lo + hi) / 2.0
+    g, h = band(a)
+    return a, (g + h) / 2.0, (g - h) / 2.0
+
+
+def interval_pieces(starts: np.ndarray, F: int, G: int):
+    """Pieces of the ranges inside addresses [F, G): offsets from F and positions."""
+    starts = np.asarray(starts, np.int64)
+    n = starts.size
+    if F >= G:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0, np.int64)
+    i0 = int(np.searchsorted(starts, F, side="right") - 1)
+    i1 = int(np.searchsorted(starts, G - 1, side="right") - 1)
+    idx = np.arange(i0, i1 + 1)
+    s = starts[idx]
+    e = np.where(idx + 1 < n, starts[np.minimum(idx + 1, n - 1)], 1 << 32)
+    return np.maximum(s, F) - F, np.minimum(e, G) - 1 - F, idx
+
+
+def fit_interval_minimax(starts: np.ndarray, F: int, G: int):
+    """Minimax leaf line for addresses [F, G) in the library's convention: x0 = F,
+    pos = floor(a d + b) with b = c + 0.5 (the floor then rounds to the nearest position).
+    Returns (a, b, E)."""
+    dlo, dhi, t = interval_pieces(starts, F, G)
+    if t.size == 0:
+        return 0.0, 0.0, 0.0
+    a, c, E = minimax_line(dlo, dhi, t)
+    return a, c + 0.5, E
+
+
+def split_tables(ra: float, rb: float, n_leaves: int, split: np.ndarray):
+    """Leaf first addresses and, per model (L leaves then the sub-leaves in leaf order),
+    its first address and the address one past its last; split leaves own no interval
+    themselves (lo = hi)."""
+    split = np.asarray(split, np.int64)
+    first = leaf_first_addresses(ra, rb, n_leaves)
+    count = np.where(split != 0, (split >> 8) + 1, 0)
+    M = n_leaves + int(count.sum())
+    lo = np.zeros(M, np.int64)
+    hi = np.zeros(M, np.int64)
+    lo[:n_leaves] = first[:n_leaves]
+    hi[:n_leaves] = first[1:]
+    nxt = n_leaves
+    for l in np.nonzero(split)[0]:
+        sh = int(split[l] & 0xFF)
+        c = int(count[l])
+        F, G = int(first[l]), int(first[l + 1])
+        j = np.arange(c)
+        lo[nxt:nxt + c] = F + (j << sh)
+        hi[nxt:nxt + c] = np.minimum(F + ((j + 1) << sh), G)
+        hi[nxt + c - 1] = G
+        hi[l] = lo[l]
+        nxt += c
+    return first, lo, hi
+
+
+def route_models(ra: float, rb: float, n_leaves: int, split: np.ndarray, first: np.ndarray,
+                 x: np.ndarray) -> np.ndarray:
+    """Model of each address: the root's leaf, or for a split leaf its sub-leaf
+    j = min(((x - x0) mod 2^32) >> shift, count - 1) with x0 the leaf's first address."""
+    split = np.asarray(split, np.int64)
+    x = np.asarray(x, np.int64)
+    leaf = root_linear(ra, rb, x.astype(np.uint32), n_leaves)
+    model = leaf.copy()
+    count = np.where(split != 0, (split >> 8) + 1, 0)
+    base = n_leaves + np.concatenate([[0], np.cumsum(count)[:-1]])
+    sp = split[leaf] != 0
+    if np.any(sp):
+        l = leaf[sp]
+        x0 = np.minimum(first[l], (1 << 32) - 1)
+        j = ((x[sp] - x0) & 0xFFFFFFFF) >> (split[l] & 0xFF)
+        model[sp] = base[l] + np.minimum(j, count[l] - 1)
+    return model
+
+
+def eps_endpoints_models(starts: np.ndarray, ra: float, rb: float, n_leaves: int, split: np.ndarray,
+                         a, b, x0):
+    """eps_endpoints_linear for a model with split leaves: every model (leaf or sub-leaf)
+    owns one interval of addresses under the monotone linear root, so the same endpoint
+    argument gives each model's bounds. Returns (eps_lo, eps_hi) over all models (0 for
+    split leaves)."""
+    starts = np.asarray(starts, np.int64)
+    n = starts.size
+    assert ra >= 0 and np.all(np.asarray(a) >= 0)
+    first, mlo, _ = split_tables(ra, rb, n_leaves, split)
+    M = mlo.size
+    bounds = np.unique(np.concatenate([starts, mlo, first[1:n_leaves]]))
+    bounds = bounds[bounds < (1 << 32)]
+    seg_lo = bounds
+    seg_hi = np.concatenate([bounds[1:], [1 << 32]]) - 1
+    t = np.searchsorted(starts, seg_lo, side="right") - 1
+    model = route_models(ra, rb, n_leaves, split, first, seg_lo)
+    p_lo = leaf_predict(a, b, x0, model, seg_lo, n)
+    p_hi = leaf_predict(a, b, x0, model, seg_hi, n)
+    eps_lo = np.zeros(M, np.int64)
+    eps_hi = np.zeros(M, np.int64)
+    np.maximum.at(eps_lo, model, np.maximum(p_hi - t, 0))
+    np.maximum.at(eps_hi, model, np.maximum(t - p_lo, 0))
+    return eps_lo, eps_hi

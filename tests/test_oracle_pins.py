@@ -591,3 +591,115 @@ def test_rmi_hand_leaf_predict_rounds_d():
     got = rmi_ref.leaf_predict(np.array([_f(s) for s in g["a"]]), np.array([_f(s) for s in g["b"]]),
                                np.array(g["x0"], np.int64), leaf, x, g["n"])
     np.testing.assert_array_equal(got, np.array([c["pos"] for c in g["cases"]]))
+
+
+# --------------------------------------- learned index: minimax leaves, split leaves
+
+def _lp_minimax(dlo, dhi, t):
+    """The same minimax line as a linear programme (scipy's HiGHS): variables (a, c, E),
+    minimise E subject to t - a dlo - c <= E, a dhi + c - t <= E, a >= 0."""
+    linprog = pytest.importorskip("scipy.optimize").linprog
+    dlo = np.asarray(dlo, np.float64)
+    dhi = np.asarray(dhi, np.float64)
+    t = np.asarray(t, np.float64)
+    A = np.concatenate([np.stack([-dlo, -np.ones_like(dlo), -np.ones_like(dlo)], 1),
+                        np.stack([dhi, np.ones_like(dhi), -np.ones_like(dhi)], 1)])
+    ub = np.concatenate([-t, t])
+    r = linprog([0, 0, 1], A_ub=A, b_ub=ub, bounds=[(0, None), (None, None), (None, None)], method="highs")
+    assert r.status == 0
+    return r.x[2]
+
+
+def test_minimax_line_matches_linear_programme():
+    """The ternary-search minimax fit reaches the optimum of the linear programme, on
+    pieces that tile an interval (as a leaf's ranges do) and on scattered points."""
+    rng = np.random.default_rng(7)
+    for trial in range(60):
+        k = int(rng.integers(1, 80))
+        if trial % 2:
+            cuts = np.sort(rng.choice(np.arange(1, 5000), size=k - 1, replace=False)) if k > 1 else np.zeros(0, int)
+            lo = np.concatenate([[0], cuts])
+            hi = np.concatenate([cuts, [5000]]) - 1
+        else:
+            lo = np.sort(rng.choice(np.arange(0, 10 ** 6), size=k, replace=False))
+            hi = lo.copy()
+        t = np.arange(k) + (rng.integers(0, 3, size=k).cumsum() if trial % 3 == 0 else 0)
+        a, c, E = rmi_ref.minimax_line(lo, hi, t)
+        assert a >= 0
+        # the returned line achieves E, and E is the LP optimum
+        got = max(np.max(t - (a * lo + c)), np.max(a * hi + c - t))
+        assert got == pytest.approx(E, abs=1e-6)
+        assert E == pytest.approx(_lp_minimax(lo, hi, t), abs=1e-6 * max(1.0, t.max()))
+
+
+def test_minimax_line_closed_form():
+    """k pieces of equal width w at positions 0..k-1: the best line is d / w with error
+    (1 - 1/w) / 2 (the band is set by each piece's first and last address)."""
+    for w in (1, 2, 7, 64, 1000):
+        k = 37
+        lo = np.arange(k) * w
+        a, c, E = rmi_ref.minimax_line(lo, lo + w - 1, np.arange(k))
+        assert E == pytest.approx((1 - 1 / w) / 2, abs=1e-9)
+        assert a == pytest.approx(1 / w, rel=1e-9)
+
+
+def test_route_models_by_hand():
+    """Root leaves [0, 2^20), [2^20, 2^21), [2^21, 3*2^20), [3*2^20, 2^32) (ra = 4096); leaf 1
+    split into 4 sub-leaves of 2^18 addresses (models 4..7), leaf 3 into 2 of 2^31 (models 8, 9)."""
+    split = np.array([0, (3 << 8) | 18, 0, (1 << 8) | 31])
+    first, lo, hi = rmi_ref.split_tables(4096.0, 0.0, 4, split)
+    np.testing.assert_array_equal(first, [0, 1 << 20, 1 << 21, 3 << 20, 1 << 32])
+    np.testing.assert_array_equal(lo[4:], [(1 << 20) + j * (1 << 18) for j in range(4)] + [3 << 20, (3 << 20) + (1 << 31)])
+    np.testing.assert_array_equal(hi[4:], [(1 << 20) + (j + 1) * (1 << 18) for j in range(4)] + [(3 << 20) + (1 << 31), 1 << 32])
+    x = np.array([0, (1 << 20) - 1, 1 << 20, (1 << 20) + (1 << 18) - 1, (1 << 20) + 3 * (1 << 18) + 5,
+                  (1 << 21) - 1, 1 << 21, 3 << 20, (3 << 20) + (1 << 31) - 1, (3 << 20) + (1 << 31), 0xFFFFFFFF])
+    want = [0, 0, 4, 4, 7, 7, 2, 8, 8, 9, 9]
+    np.testing.assert_array_equal(rmi_ref.route_models(4096.0, 0.0, 4, split, first, x), want)
+
+
+def test_eps_endpoints_models_by_brute_force():
+    """Error bounds of a model with split leaves: without splits they equal the leaf-only
+    analysis; with splits they equal the largest errors found by evaluating every address
+    of [0, 2^20) and of the last 2^20 addresses, plus every model and range boundary +-1."""
+    rng = np.random.default_rng(11)
+    starts = np.unique(np.concatenate([[0], rng.integers(1, 1 << 20, 3000), [(1 << 32) - 5000]])).astype(np.int64)
+    n = starts.size
+    L = 8
+    ra, rb = 8.0 * (1 << 12), 0.0          # leaves of 2^17 addresses up to 7 * 2^17, the rest in leaf 7
+    split = np.zeros(L, np.int64)
+    split[2] = (7 << 8) | 14               # 8 sub-leaves of 2^14
+    split[7] = (3 << 8) | 30               # 4 sub-leaves over [7 * 2^17, 2^32)
+    first, mlo, mhi = rmi_ref.split_tables(ra, rb, L, split)
+    M = mlo.size
+    a = np.zeros(M)
+    b = np.zeros(M)
+    x0 = np.minimum(mlo, (1 << 32) - 1)
+    for m in range(M):
+        if m < L and split[m]:
+            continue
+        am, bm, _ = rmi_ref.fit_interval_minimax(starts, int(mlo[m]), int(mhi[m]))
+        a[m], b[m] = am, bm
+    nosplit_lo, nosplit_hi = rmi_ref.eps_endpoints_models(starts, ra, rb, L, np.zeros(L, np.int64), a[:L], b[:L], x0[:L])
+    ref_lo, ref_hi = rmi_ref.eps_endpoints_linear(starts, ra, rb, a[:L], b[:L], x0[:L], L)
+    np.testing.assert_array_equal(nosplit_lo, ref_lo)
+    np.testing.assert_array_equal(nosplit_hi, ref_hi)
+    elo, ehi = rmi_ref.eps_endpoints_models(starts, ra, rb, L, split, a, b, x0)
+    assert elo[2] == ehi[2] == elo[7] == ehi[7] == 0
+    xs = np.concatenate([np.arange(0, 1 << 20), np.arange((1 << 32) - (1 << 20), 1 << 32), starts - 1, starts + 1,
+                         mlo - 1, mlo, mhi - 1])
+    xs = np.unique(xs[(xs >= 0) & (xs < (1 << 32))])
+    model = rmi_ref.route_models(ra, rb, L, split, first, xs)
+    t = np.searchsorted(starts, xs, side="right") - 1
+    p = rmi_ref.leaf_predict(a, b, x0, model, xs, n)
+    got_lo = np.zeros(M, np.int64)
+    got_hi = np.zeros(M, np.int64)
+    np.maximum.at(got_lo, model, np.maximum(p - t, 0))
+    np.maximum.at(got_hi, model, np.maximum(t - p, 0))
+    np.testing.assert_array_equal(got_lo, elo)
+    np.testing.assert_array_equal(got_hi, ehi)
+    # the minimax leaves keep every model's error near its optimum
+    for m in range(M):
+        if m < L and split[m]:
+            continue
+        E = rmi_ref.fit_interval_minimax(starts, int(mlo[m]), int(mhi[m]))[2]
+        assert max(elo[m], ehi[m]) <= np.ceil(E + 0.5) + 1
