@@ -76,8 +76,19 @@ def workload_desc(n_records, n_windows, reg, n_ranges):
 LOOKUP_NAMES = {1: "binary search", 2: "learned index (RMI)", 3: "radix directory + binary search"}
 
 
+def rmi_mode(name):
+    """'rmi' = the learned-index workload's model (linear root, 4,096 minimax leaves, leaves
+    whose window would exceed 64 split); 'rmi_mse' = the same root with mean-squared-error
+    leaves; 'rmiL' = L minimax leaves. Returns (leaves, leaf_fit name) or (0, None)."""
+    if not name.startswith("rmi"):
+        return 0, None
+    if name == "rmi_mse":
+        return 4096, "mse"
+    return (int(name[3:]) if len(name) > 3 else 4096), "minimax"
+
+
 def learned_vs_plain(gnm, torch, local, steps, warmup, n_records=50_000_000,
-                     modes=("bsearch", "radix", "rmi", "rmi8192", "rmi65536")):
+                     modes=("bsearch", "radix", "rmi", "rmi_mse", "rmi65536")):
     """Same GPU, same records, 100,000-site / 1,000,000-prefix registry: one window of
     n_records processed with the plain binary search, the radix-directed search and the
     learned index. Results must be bit-exact across the three; throughput per lookup."""
@@ -85,24 +96,25 @@ def learned_vs_plain(gnm, torch, local, steps, warmup, n_records=50_000_000,
     reg = fg.registry_c3()
     rec = fg.make_records(reg, n_records, seed=2, p_reg=0.9, zipf_s=0.9)
     dev = gnm.Records.to_device(rec)
-    # training keys: both addresses of 5,000,000 other records of the same distribution
-    tr = fg.make_records(reg, 5_000_000, seed=12, p_reg=0.9, zipf_s=0.9)
-    keys = torch.from_numpy(np.concatenate([tr["srcaddr"], tr["dstaddr"]]).view(np.int32)).cuda()
+    # training keys: 10,000,000 lookups of the plain method (the remote endpoints of other
+    # records of the same distribution)
+    keys = torch.from_numpy(fg.lookup_keys_c3(reg, 10_000_000).view(np.int32)).cuda()
     peak, peak_kind = hbm_peak()
     stream = torch.cuda.current_stream()
     res, dense, info_out = {}, {}, {}
-    # "rmi" is the 4,096-leaf model; "rmiL" a model of L leaves (same training otherwise; leaf
-    # parameters staged in shared memory when they fit, else read from global memory)
     for name in modes:
-        leaves = (int(name[3:]) if len(name) > 3 else 4096) if name.startswith("rmi") else 0
+        leaves, fit = rmi_mode(name)
         mode = {"bsearch": gnm.LOOKUP_BSEARCH, "radix": gnm.LOOKUP_RADIX}.get(name, gnm.LOOKUP_RMI)
         ctx = gnm.Context(device=local, window_slots=4, lookup_mode=mode)
         ctx.load(reg)
         if leaves:
-            rep = ctx.rmi_train(keys, root_kind=gnm.ROOT_LINEAR, n_leaves=leaves, leaf_iters=4)
-            info_out[name] = {"leaves": leaves, "root": "linear", "eps_max": int(rep.eps_max),
-                              "eps_mean": round(float(rep.eps_mean), 2), "train_ms": round(float(rep.train_ms), 1),
-                              "sweep_ms": round(float(rep.sweep_ms), 1), "train_keys": int(keys.numel())}
+            rep = ctx.rmi_train(keys, root_kind=gnm.ROOT_LINEAR, n_leaves=leaves, leaf_iters=4,
+                                leaf_fit=gnm.FIT_MSE if fit == "mse" else gnm.FIT_MINIMAX)
+            info_out[name] = {"leaves": leaves, "root": "linear", "leaf_fit": fit, "models": int(rep.n_models),
+                              "split_leaves": int(rep.split_leaves), "eps_max": int(rep.eps_max),
+                              "err_max": int(rep.err_max), "eps_mean": round(float(rep.eps_mean), 2),
+                              "train_ms": round(float(rep.train_ms), 1), "sweep_ms": round(float(rep.sweep_ms), 1),
+                              "train_keys": int(keys.numel())}
             ctx.rmi_violations(reset=True)
         plan = ctx.plan(dev, [0, n_records], [1], kernel_times=True)
         for _ in range(warmup):
@@ -314,8 +326,7 @@ def serve_c5(gnm, torch, local, minutes=120, speedup=600.0, pool_n=20_000_000, b
     win_of = (times // 60.0).astype(np.int64)
     ctx = gnm.Context(device=local, window_slots=16)
     ctx.load(reg)
-    tr = fg.make_records(reg, 5_000_000, seed=12, p_reg=0.9, zipf_s=0.9)
-    keys = torch.from_numpy(np.concatenate([tr["srcaddr"], tr["dstaddr"]]).view(np.int32)).cuda()
+    keys = torch.from_numpy(fg.lookup_keys_c3(reg, 10_000_000).view(np.int32)).cuda()
     ctx.rmi_train(keys, root_kind=gnm.ROOT_LINEAR, n_leaves=4096, leaf_iters=4)
     checked = sorted({0, int(rng.integers(1, minutes))})[:check]
     got = {}
@@ -572,7 +583,7 @@ def main():
                          "or the batched windows")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-window batched launch")
     ap.add_argument("--learned-records", type=int, default=50_000_000)
-    ap.add_argument("--learned-modes", default="bsearch,radix,rmi,rmi8192,rmi65536")
+    ap.add_argument("--learned-modes", default="bsearch,radix,rmi,rmi_mse,rmi65536")
     ap.add_argument("--serve-minutes", type=int, default=120)
     ap.add_argument("--serve-speedup", type=float, default=600.0)
     args = ap.parse_args()

@@ -210,8 +210,11 @@ def zipf_probs(n: int, s: float) -> np.ndarray:
 
 def make_records(reg: Registry, n: int, seed: int, p_reg: float = 0.85, zipf_s: float = 1.1,
                  p_in: float = 0.3, t0_ms: int = 0, mu: float = 12.0, sigma: float = 3.0,
-                 window_ms: int = 60000, t0_per_record: Optional[np.ndarray] = None) -> Dict[str, np.ndarray]:
-    """One struct-of-arrays batch of ``n`` records (see the module docstring)."""
+                 window_ms: int = 60000, t0_per_record: Optional[np.ndarray] = None,
+                 with_remote: bool = False) -> Dict[str, np.ndarray]:
+    """One struct-of-arrays batch of ``n`` records (see the module docstring). With
+    ``with_remote`` the batch also carries "remote": the endpoint drawn as the remote one
+    (registered or unregistered), i.e. the address each record's site lookup receives."""
     rng = np.random.default_rng(seed)
     # remote endpoint
     is_reg = rng.random(n) < p_reg
@@ -254,13 +257,16 @@ def make_records(reg: Registry, n: int, seed: int, p_reg: float = 0.85, zipf_s: 
     base = np.int64(t0_ms) if t0_per_record is None else t0_per_record.astype(np.int64)
     first = (base + rng.integers(0, window_ms, size=n, dtype=np.int64)) & MAX_U32
     last = (first + dur) & MAX_U32
-    return {
+    out = {
         "srcaddr": src, "dstaddr": dst, "dPkts": pkts, "dOctets": octets,
         "first": first.astype(np.uint32), "last": last.astype(np.uint32),
         "srcport": rng.integers(0, 1 << 16, size=n, dtype=np.int64).astype(np.uint16),
         "dstport": rng.integers(0, 1 << 16, size=n, dtype=np.int64).astype(np.uint16),
         "prot": np.where(rng.random(n) < 0.9, 6, 17).astype(np.uint8),
     }
+    if with_remote:
+        out["remote"] = remote.astype(np.uint32)
+    return out
 
 
 FIELDS = ("srcaddr", "dstaddr", "dPkts", "dOctets", "first", "last")
@@ -297,6 +303,12 @@ def registry_c2_24(seed: int = 1) -> Registry:
 def registry_c3(seed: int = 2, n_prefixes: int = 1_000_000, n_sites: int = 100_000) -> Registry:
     """100,000 sites, 1,000,000 prefixes /16-/30, 30% nested."""
     return make_registry(n_sites, n_prefixes, C3_LEN, 0.3, seed)
+
+
+def lookup_keys_c3(reg: Registry, n: int = 10_000_000, seed: int = 12) -> np.ndarray:
+    """Training lookups of the learned index: the remote endpoints of ``n`` records of the
+    learned-index workload's distribution (90% registered, Zipf 0.9)."""
+    return make_records(reg, n, seed=seed, p_reg=0.9, zipf_s=0.9, with_remote=True)["remote"]
 
 
 def window_records_c1(reg: Registry, n: int = 100_000, seed: int = 0):

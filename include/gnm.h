@@ -361,14 +361,27 @@ gnm_status gnm_lookup(gnm_ctx *ctx, const uint32_t *addr, uint64_t n, uint32_t *
  * Kraska et al. 2018). It predicts the position of an address; an exact search within
  * [pred - eps_lo, pred + eps_hi] of the leaf finishes the lookup and a full binary search
  * is the fallback whenever that window does not hold the answer, so results never depend
- * on the model. */
+ * on the model.
+ *
+ * Leaves are fitted by default by minimising their worst-case error over every address
+ * they own (GNM_RMI_FIT_MINIMAX: a Chebyshev line over the range pieces of the leaf's
+ * address interval, whose positions are the plain binary search's answers), since that
+ * error is the proven bound; GNM_RMI_FIT_MSE fits them by gradient descent on the mean
+ * squared error of the training lookups instead. With minimax leaves, a leaf whose window
+ * would exceed eps_target is split into 2^k equal sub-leaves (one more linear model level
+ * for that leaf's addresses only; the hybrid form of Kraska et al.'s index). Models are
+ * numbered leaves first (0..n_leaves-1), then the sub-leaves of split leaves in leaf order.
+ * Minimax training (root, leaves, splits) is deterministic: the same keys, configuration
+ * and GPU give the same model bit for bit. MSE leaves sum with FP64 atomics and may differ
+ * in the last bits between runs. */
 enum { GNM_RMI_ROOT_LINEAR = 0, GNM_RMI_ROOT_MLP = 1 };
+enum { GNM_RMI_FIT_MINIMAX = 0, GNM_RMI_FIT_MSE = 1 };
 
 typedef struct {
     int32_t root_kind;   /* GNM_RMI_ROOT_* */
     uint32_t n_leaves;   /* 1..1048576 (4096) */
     uint32_t hidden;     /* MLP root width: 8, 16 or 32 (32) */
-    uint32_t leaf_iters; /* gradient steps for the linear stages (4) */
+    uint32_t leaf_iters; /* gradient steps for the linear root and for MSE leaves (4) */
     uint32_t mlp_steps;  /* Adam steps for the MLP root (600) */
     uint32_t mlp_batch;  /* samples per Adam step (65536) */
     float mlp_lr;        /* Adam learning rate (0.01) */
@@ -376,15 +389,25 @@ typedef struct {
     int32_t exhaustive_eps; /* 1: error bounds from all 2^32 addresses (default);
                                0: from the training samples only (the verify-and-
                                fall-back path keeps results exact either way) */
+    int32_t leaf_fit;       /* GNM_RMI_FIT_MINIMAX (default) or GNM_RMI_FIT_MSE */
+    uint32_t eps_target;    /* minimax leaves: a leaf whose window eps_lo + eps_hi is
+                               estimated above this is split (64); 0: never split */
+    uint32_t max_split_log2; /* at most 2^max_split_log2 sub-leaves per leaf (14, <= 16) */
 } gnm_rmi_config;
 
 typedef struct {
     uint64_t n_train;
-    double root_loss, leaf_loss;  /* final mean squared errors */
-    uint32_t eps_max;             /* max over leaves of eps_lo + eps_hi */
-    double eps_mean;              /* mean window width (eps_lo + eps_hi + 1) per leaf,
-                                     weighted by training samples */
-    uint32_t empty_leaves;
+    double root_loss;             /* mean squared error of the root (leaf units) */
+    double leaf_loss;             /* mean squared error of the predicted position over
+                                     the training lookups */
+    uint32_t eps_max;             /* max over models of eps_lo + eps_hi (window - 1) */
+    uint32_t err_max;             /* max over models of max(eps_lo, eps_hi): the largest
+                                     |predicted - true position| over all addresses */
+    double eps_mean;              /* mean window width eps_lo + eps_hi + 1 over the
+                                     training lookups */
+    uint32_t empty_leaves;        /* leaves that own no address (minimax) or no training key */
+    uint32_t n_models;            /* leaves + sub-leaves */
+    uint32_t split_leaves;        /* leaves split into sub-leaves */
     double train_ms, sweep_ms;
 } gnm_rmi_report;
 
@@ -414,15 +437,24 @@ gnm_status gnm_rmi_linear_grad(gnm_ctx *ctx, const float *z, const float *y, uin
 gnm_status gnm_rmi_mlp_grad(gnm_ctx *ctx, const float *xn, const float *y, uint64_t n,
                             uint32_t hidden, const float *params, double *grad, void *stream);
 
-/* Copies the trained model to host arrays (any may be NULL): root[2 + 3*32 + 1]
- * (ra, rb, w1[32], b1[32], w2[32], b2), a/b/x0/eps_lo/eps_hi[n_leaves]. */
-gnm_status gnm_rmi_export(gnm_ctx *ctx, int32_t *root_kind, uint32_t *n_leaves, float *root,
-                          float *a, float *b, uint32_t *x0, uint32_t *eps_lo, uint32_t *eps_hi);
+/* Copies the trained model to host arrays (any may be NULL; call once with NULL arrays to
+ * read the sizes): root[2 + 3*32 + 1] (ra, rb, w1[32], b1[32], w2[32], b2);
+ * split[n_leaves]: 0 for a leaf that is not split, else ((count - 1) << 8) | shift: the
+ * leaf's addresses [F, F') go to `count` sub-leaves of 2^shift addresses each from F (the
+ * last one takes the remainder), address x to sub-leaf min((x - F) >> shift, count - 1);
+ * a/b/x0/eps_lo/eps_hi[n_models] per model (zeros for split leaves). Position of x in
+ * model m: clamp(floor(fl(fl(a[m] * fl(x - x0[m])) + b[m])), 0, n_ranges - 1). */
+gnm_status gnm_rmi_export(gnm_ctx *ctx, int32_t *root_kind, uint32_t *n_leaves, uint32_t *n_models,
+                          float *root, uint32_t *split, float *a, float *b, uint32_t *x0,
+                          uint32_t *eps_lo, uint32_t *eps_hi);
 
-/* Installs a model (same layout as gnm_rmi_export) and computes its error bounds by the
- * exhaustive sweep over all 2^32 addresses. */
-gnm_status gnm_rmi_import(gnm_ctx *ctx, int32_t root_kind, uint32_t n_leaves, const float *root,
-                          const float *a, const float *b, const uint32_t *x0, void *stream);
+/* Installs a model (same layout as gnm_rmi_export; split may be NULL when no leaf is
+ * split, and n_models must then equal n_leaves) and computes its error bounds by the
+ * exhaustive sweep over all 2^32 addresses. GNM_E_INVAL when the split table does not add
+ * up to n_models, a count exceeds 65,536 or a shift exceeds 31. */
+gnm_status gnm_rmi_import(gnm_ctx *ctx, int32_t root_kind, uint32_t n_leaves, uint32_t n_models,
+                          const float *root, const uint32_t *split, const float *a, const float *b,
+                          const uint32_t *x0, void *stream);
 
 /* ------------------------------------------------------- batched plans and tuning */
 

@@ -323,10 +323,32 @@ __device__ __forceinline__ RmiLeaf rmi_leaf(const RmiDev& m, const float* a, con
     return f;
 }
 
+// fl(int64(x) - int64(x0)) on the 32-bit converter: round-to-nearest-even is symmetric in
+// sign, so rounding |x - x0| and negating gives the same float as rounding the signed
+// 64-bit difference.
+__device__ __forceinline__ float rel_offset(uint32_t x, uint32_t x0) {
+    return x >= x0 ? __uint2float_rn(x - x0) : -__uint2float_rn(x0 - x);
+}
+
 // Predicted position of x inside its leaf.
 __device__ __forceinline__ uint32_t rmi_leaf_pos(const RmiLeaf& f, uint32_t x, uint32_t n) {
-    const float d = __ll2float_rn((long long)x - (long long)f.x0);
-    return clamp_floor(__fadd_rn(__fmul_rn(f.a, d), f.b), n);
+    return clamp_floor(__fadd_rn(__fmul_rn(f.a, rel_offset(x, f.x0)), f.b), n);
+}
+
+// Sub-leaf of x in a split leaf's record: min(((x - x0) mod 2^32) >> shift, count - 1),
+// counted from the record's first sub-leaf.
+__device__ __forceinline__ uint32_t rmi_sub_model(const RmiLeaf& f, uint32_t x) {
+    const uint32_t w = __float_as_uint(f.a);
+    return __float_as_uint(f.b) + min((x - f.x0) >> (w & 31u), w >> 8);
+}
+
+// Parameters of the model that answers x: the root's leaf, or its sub-leaf when the leaf
+// is split (one more dependent load, for the addresses of split leaves only).
+__device__ __forceinline__ RmiLeaf rmi_model(const RmiDev& m, const float* a, const float* b, const uint32_t* x0,
+                                             const uint32_t* eps, uint32_t x) {
+    RmiLeaf f = rmi_leaf(m, a, b, x0, eps, rmi_root(m, x));
+    if (f.eps == kEpsSplit) f = rmi_leaf(m, a, b, x0, eps, rmi_sub_model(f, x));
+    return f;
 }
 
 // Learned-index lookup: model window, exact search inside it, verification, fallback.
@@ -334,7 +356,7 @@ __device__ __forceinline__ uint32_t rmi_lookup(const RmiDev& m, const float* a, 
                                                const uint32_t* x0, const uint32_t* eps,
                                                const uint32_t* __restrict__ starts, uint32_t n,
                                                uint32_t x, unsigned long long* violations) {
-    const RmiLeaf f = rmi_leaf(m, a, b, x0, eps, rmi_root(m, x));
+    const RmiLeaf f = rmi_model(m, a, b, x0, eps, x);
     const uint32_t e = f.eps;
     if (e == 0xFFFFFFFFu) return pred_search1(starts, 0, n, x);
     const uint32_t pi = rmi_leaf_pos(f, x, n);
@@ -361,7 +383,7 @@ __device__ __forceinline__ void rmi_sites(const RmiDev& m, const float* a, const
     uint32_t first[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-        const RmiLeaf lf = rmi_leaf(m, a, b, x0, eps, rmi_root(m, x[j]));
+        const RmiLeaf lf = rmi_model(m, a, b, x0, eps, x[j]);
         const uint32_t e = lf.eps;
         if (!valid[j]) {
             lo[j] = 0u;
@@ -890,7 +912,7 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a -
 
 // Shared-memory layout: [table values][hash keys][registry or leaf arrays].
 __host__ __device__ inline size_t smem_layout(int lookup, int table, uint32_t n_ranges,
-                                              uint32_t keys, uint32_t cap, uint32_t n_leaves,
+                                              uint32_t keys, uint32_t cap, uint32_t n_models,
                                               uint32_t radix_bits, size_t* off_keys, size_t* off_lookup) {
     const uint32_t rows = table == kTableDirect ? keys : (table == kTableHash ? cap : 0u);
     size_t o = (size_t)rows * kSmemRowBytes;
@@ -900,7 +922,7 @@ __host__ __device__ inline size_t smem_layout(int lookup, int table, uint32_t n_
     *off_lookup = o;
     if (lookup == kLookupSmem) o += (size_t)n_ranges * 8 + (radix_bits ? (((size_t)1 << radix_bits) + 1) * 4 : 0);
     if (lookup == kLookupStaged) o += (size_t)((n_ranges + kBlockRanges - 1) / kBlockRanges) * 4;
-    if (lookup == kLookupRmi) o += (size_t)n_leaves * 16;
+    if (lookup == kLookupRmi) o += (size_t)n_models * 16;
     if (lookup == kLookupRadix) o += ((size_t)1 << radix_bits) * 4 + 4;
     return align_up(o, 16);
 }
@@ -1222,7 +1244,7 @@ __device__ __forceinline__ void stage_lookup(const AggParams& p, unsigned char* 
         sm.rx0 = nullptr;
         sm.reps = nullptr;
     } else if (LOOKUP == kLookupRmi) {
-        const uint32_t L = p.rmi.n_leaves;
+        const uint32_t L = p.rmi.n_models;
         float* a = reinterpret_cast<float*>(base);
         float* b = a + L;
         uint32_t* x0 = reinterpret_cast<uint32_t*>(b + L);
@@ -1253,7 +1275,7 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
 
     size_t off_keys, off_lookup;
     smem_layout(LOOKUP, TABLE, p.n_ranges, p.table_rows, p.table_cap,
-                LOOKUP == kLookupRmi && !p.rmi.leaves_global ? p.rmi.n_leaves : 0u, p.radix_bits, &off_keys,
+                LOOKUP == kLookupRmi && !p.rmi.leaves_global ? p.rmi.n_models : 0u, p.radix_bits, &off_keys,
                 &off_lookup);
     Smem sm;
     sm.key_base = 0u;

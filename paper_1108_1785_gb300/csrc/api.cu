@@ -253,7 +253,7 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s, size_t n_win) {
         s->lookup = kLookupRmi;
         // leaf parameters staged in shared memory, or read (16 bytes per lookup) from global
         // memory: placement L2, or AUTO when they do not fit
-        const size_t leaf_bytes = (size_t)c->rmi.n_leaves * 16;
+        const size_t leaf_bytes = (size_t)c->rmi.n_models * 16;
         int place = cfg.placement != GNM_PLACE_AUTO ? cfg.placement : c->tuned.placement;
         if (place == GNM_PLACE_STAGED) place = GNM_PLACE_AUTO;
         const bool fits = leaf_bytes + 1024 <= (size_t)c->smem_optin;
@@ -447,7 +447,7 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s, size_t n_win) {
     s->block = block;
     s->unroll = unroll;
     s->smem = aggregate_smem_bytes(s->split ? kLookupKeys : s->lookup, s->table, nr, rows, cap,
-                                   s->lookup == kLookupRmi && !s->rmi_global ? c->rmi.n_leaves : 0, s->radix_bits);
+                                   s->lookup == kLookupRmi && !s->rmi_global ? c->rmi.n_models : 0, s->radix_bits);
     if (s->smem > (size_t)c->smem_optin) return fail(GNM_E_INVAL, "shared-memory layout exceeds the device limit");
     int cps = cfg.ctas_per_sm ? cfg.ctas_per_sm : c->tuned.ctas_per_sm;
     const int by_threads = std::max(1, 2048 / block);

@@ -146,6 +146,7 @@ struct gnm_ctx {
     uint32_t* d_rmi_elo = nullptr;
     uint32_t* d_rmi_ehi = nullptr;
     uint32_t rmi_cap = 0;
+    std::vector<uint32_t> rmi_split;  // per leaf: 0, or shift | (count - 1) << 8
     // tuning
     gnm::Tuned tuned;
     uint32_t last_launches = 0;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "gnm.h"
 #include "hash24.hpp"
 
@@ -16,6 +18,11 @@ constexpr int kAccCols = 5;         // accumulator row: flows<<32|e_flows, ineli
 constexpr size_t kSmemRowBytes = 20;  // per-CTA shared-memory row: packed counts + 4 low words
 constexpr int kUnmatched = 4;       // classes appended after the 2*n_sites site rows
 constexpr int kMaxLeaves = 1 << 20;
+constexpr uint32_t kMaxModels = 1u << 22;  // leaves plus sub-leaves of split leaves
+// eps word of a split leaf's record: its `a` bits hold shift | (count - 1) << 8 and its `b`
+// bits the index of its first sub-leaf; x0 is the leaf's first address. Packed bounds never
+// take this value (each half is at most 0xFFFE, else the word is 0xFFFFFFFF).
+constexpr uint32_t kEpsSplit = 0xFFFFFFFEu;
 constexpr int kMaxHidden = 32;
 constexpr uint32_t kEmptyKey = 0xFFFFFFFFu;
 
@@ -39,18 +46,21 @@ constexpr uint64_t kFlushRecords = 65532;  // < 2^16, multiple of 4
 constexpr uint64_t kCountPiece = 32764;    // 2^15 + kCountPiece < 2^16, multiple of 4
 constexpr uint32_t kWinFinalize = 1u;
 
-// Learned index: root parameters by value, per-leaf arrays in device memory.
+// Learned index: root parameters by value, per-model arrays in device memory (the root's
+// n_leaves leaves, then the sub-leaves of split leaves).
 struct RmiDev {
     int32_t root_kind;     // GNM_RMI_ROOT_*
     uint32_t n_leaves;
+    uint32_t n_models;     // n_leaves + sub-leaves; the length of a, b, x0, eps, leaf4
     uint32_t hidden;
     float ra, rb;          // linear root, on xn = float(x) * 2^-32
     float w1[kMaxHidden], b1[kMaxHidden], w2[kMaxHidden], b2;
     const float* a;
     const float* b;
     const uint32_t* x0;
-    const uint32_t* eps;   // packed eps_lo | eps_hi << 16; 0xFFFFFFFF: always full search
-    const uint4* leaf4;    // per leaf (a bits, b bits, x0, eps) interleaved: one 16-byte load
+    const uint32_t* eps;   // packed eps_lo | eps_hi << 16; 0xFFFFFFFF: always full search;
+                           // kEpsSplit: a split leaf
+    const uint4* leaf4;    // per model (a bits, b bits, x0, eps) interleaved: one 16-byte load
     uint32_t leaves_global;  // this launch reads leaf4 from global memory instead of staging
 };
 
@@ -231,15 +241,26 @@ cudaError_t launch_lookup(const AggParams& p, int lookup, const uint32_t* addr, 
                           uint32_t* site_out, uint32_t* pos_out, cudaStream_t st);
 
 // rmi.cu
+// A trained model on the host: the root (in RmiDev) and per model a, b, x0 and the initial
+// eps word (kEpsSplit for split leaves, else 0 until the bounds are computed).
 struct RmiTrainOut {
-    double root_loss, leaf_loss;
-    uint32_t empty_leaves;
+    double root_loss = 0.0;
+    uint32_t empty_leaves = 0, split_leaves = 0;
+    std::vector<float> a, b;
+    std::vector<uint32_t> x0, eps;
+    std::vector<uint32_t> split;  // per leaf: 0, or shift | (count - 1) << 8
 };
 size_t rmi_train_scratch_bytes(uint64_t n, uint32_t n_leaves);
-cudaError_t rmi_train_device(RmiDev* model, float* d_a, float* d_b, uint32_t* d_x0,
-                             const uint32_t* keys, const uint32_t* pos, uint64_t n,
-                             uint32_t n_ranges, const gnm_rmi_config& cfg, void* scratch,
-                             RmiTrainOut* out, cudaStream_t st);
+size_t rmi_partials_bytes();  // per-block partial sums of the ordered reductions
+// Root and leaves (model arrays in `out`, on the host). `pos` holds the plain search's
+// positions of the n device keys; `starts` the device range starts.
+cudaError_t rmi_train_device(RmiDev* model, const uint32_t* keys, const uint32_t* pos, uint64_t n,
+                             const uint32_t* starts, uint32_t n_ranges, const gnm_rmi_config& cfg,
+                             void* scratch, RmiTrainOut* out, cudaStream_t st);
+// Over n_s training lookups: out2[0] = sum of squared position errors, out2[1] = sum of the
+// window widths searched.
+cudaError_t rmi_model_stats(const RmiDev& model, const uint32_t* keys, const uint32_t* pos, uint64_t n_s,
+                            uint32_t n_ranges, double* part, double* out2, cudaStream_t st);
 cudaError_t rmi_eps_sweep(const RmiDev& model, const uint32_t* starts, uint32_t n_ranges,
                           uint32_t* d_eps_lo, uint32_t* d_eps_hi, int sm_count, cudaStream_t st);
 cudaError_t rmi_eps_from_samples(const RmiDev& model, const uint32_t* keys, const uint32_t* pos,
@@ -250,8 +271,8 @@ cudaError_t rmi_pack_eps(const uint32_t* lo, const uint32_t* hi, uint32_t* packe
 cudaError_t rmi_pack_leaf4(const float* a, const float* b, const uint32_t* x0, const uint32_t* eps, uint4* out,
                            uint32_t L, cudaStream_t st);
 cudaError_t rmi_linear_grad(const float* z, const float* y, uint64_t n, float w, float c,
-                            double* d_acc3, cudaStream_t st);
+                            double* d_part, double* d_acc3, cudaStream_t st);
 cudaError_t rmi_mlp_grad(const float* xn, const float* y, uint64_t n, uint32_t hidden,
-                         const float* d_params, double* d_grad, cudaStream_t st);
+                         const float* d_params, double* d_part, double* d_grad, cudaStream_t st);
 
 }  // namespace gnm

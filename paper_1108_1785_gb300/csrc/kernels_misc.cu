@@ -49,9 +49,9 @@ cudaError_t launch_aggregate(const AggParams& p, const LaunchShape& s, cudaStrea
 }
 
 size_t aggregate_smem_bytes(int lookup, int table, uint32_t n_ranges, uint32_t keys,
-                            uint32_t table_cap, uint32_t n_leaves, uint32_t radix_bits) {
+                            uint32_t table_cap, uint32_t n_models, uint32_t radix_bits) {
     size_t a, b;
-    return dev::smem_layout(lookup, table, n_ranges, keys, table_cap, n_leaves, radix_bits, &a, &b);
+    return dev::smem_layout(lookup, table, n_ranges, keys, table_cap, n_models, radix_bits, &a, &b);
 }
 
 namespace {
@@ -161,7 +161,7 @@ __global__ void k_lookup(const __grid_constant__ AggParams p, const uint32_t* __
         s_starts = d;
     }
     if (LOOKUP == kLookupRmi && !p.rmi.leaves_global) {
-        const uint32_t L = p.rmi.n_leaves;
+        const uint32_t L = p.rmi.n_models;
         float* a = reinterpret_cast<float*>(smem_raw);
         float* b = a + L;
         uint32_t* x0 = reinterpret_cast<uint32_t*>(b + L);
@@ -284,7 +284,7 @@ cudaError_t launch_lookup(const AggParams& p, int lookup, const uint32_t* addr, 
     if (lookup == kLookupSmem) smem = (size_t)p.n_ranges * 4;
     if (lookup == kLookupStaged) smem = (size_t)p.n_blocks * 4;
     if (lookup == kLookupRadix) smem = ((size_t)1 << p.radix_bits) * 4 + 4;
-    if (lookup == kLookupRmi) smem = p.rmi.leaves_global ? 0 : (size_t)p.rmi.n_leaves * 16;
+    if (lookup == kLookupRmi) smem = p.rmi.leaves_global ? 0 : (size_t)p.rmi.n_models * 16;
     cudaError_t e;
     switch (lookup) {
         case kLookupSmem:

@@ -1,6 +1,6 @@
 // rmi.cu -- the learned index over the flattened range starts: GPU training of a
 // two-stage recursive model index (Kraska et al., "The Case for Learned Index
-// Structures", 2018) and its per-leaf error bounds.
+// Structures", 2018) and its per-model error bounds.
 //
 // Not in the paper: it replaces the full search that assigns a record to a registered
 // subnet (the paper's hash table, Sec. III.B.2.1, Sec. IV.A.1). Results stay exact:
@@ -8,12 +8,26 @@
 //
 // Arithmetic (identical in training, the error sweep and inference):
 //   xn = fl(fl(x) * 2^-32); root -> leaf = clamp(floor(root(xn)), 0, L-1)
-//   d  = fl(int64(x) - int64(x0[leaf])); pos = clamp(floor(fl(fl(a*d) + b)), 0, n-1)
-// Training minimises the mean squared error of each stage by gradient descent: the
-// linear stages on a standardised input (so a handful of steps reach the least-squares
-// line), the MLP root (1 -> H -> 1, ReLU) with Adam on mini-batches.
+//   split leaf -> sub-leaf min(((x - x0) mod 2^32) >> shift, count - 1)
+//   d  = fl(int64(x) - int64(x0[m])); pos = clamp(floor(fl(fl(a*d) + b)), 0, n-1)
+// Training:
+//   root: mean squared error by gradient descent (linear, on a standardised input, so a
+//         handful of steps reach the least-squares line) or Adam on mini-batches (the
+//         1 -> H -> 1 ReLU MLP), on the training lookups and the plain search's positions;
+//   leaves (minimax, default): each leaf's address interval [F, F') comes from the root by
+//         bisection; its line minimises the worst-case error over the pieces of the ranges
+//         inside the interval (convex in the slope: ternary search, max/min reductions);
+//         a leaf whose window stays above the target is split into 2^k equal sub-leaves;
+//   leaves (MSE): gradient descent per leaf on the training lookups it receives.
+// Every reduction of the root and minimax paths is in a fixed order (per-block partials,
+// then one ordered sum; max/min otherwise), so those models are reproducible bit for bit.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "agg_kernel.cuh"
 
@@ -21,6 +35,10 @@ namespace gnm {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxRed = 3 * kMaxHidden + 2;  // widest reduction (MLP gradient + loss)
+constexpr int kFitThreads = 128;
+constexpr int kFitIters = 48;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -28,18 +46,32 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Sums of `cnt` per-thread doubles over the block, added atomically to out[0..cnt).
+// Per-block sums of CNT per-thread doubles, in a fixed order: a shuffle tree per warp,
+// then the warps in order; block b writes part[b * CNT + k]. k_sum_partials adds the
+// blocks in order.
 template <int CNT>
-__device__ __forceinline__ void block_add(const double (&v)[CNT], double* out, double* sred) {
-    for (int k = threadIdx.x; k < CNT; k += blockDim.x) sred[k] = 0.0;
-    __syncthreads();
+__device__ __forceinline__ void block_partials(const double (&v)[CNT], double* part) {
+    __shared__ double sred[kWarps * CNT];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < CNT; ++k) {
         const double s = warp_sum(v[k]);
-        if ((threadIdx.x & 31) == 0) atomicAdd(sred + k, s);
+        if (lane == 0) sred[warp * CNT + k] = s;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < CNT; k += blockDim.x) atomicAdd(out + k, sred[k]);
+    for (int k = threadIdx.x; k < CNT; k += blockDim.x) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sred[w * CNT + k];
+        part[(size_t)blockIdx.x * CNT + k] = t;
+    }
+}
+
+__global__ void k_sum_partials(const double* __restrict__ part, int nblk, int cnt, double* __restrict__ out) {
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        double t = 0.0;
+        for (int b = 0; b < nblk; ++b) t += part[(size_t)b * cnt + k];
+        out[k] = t;
+    }
 }
 
 __device__ __forceinline__ float xnorm(uint32_t x) {
@@ -49,23 +81,22 @@ __device__ __forceinline__ float xnorm(uint32_t x) {
 // ------------------------------------------------------------ linear stage (root)
 
 // sum of xn and xn^2 (for standardisation)
-__global__ void k_moments(const uint32_t* __restrict__ keys, uint64_t n, double* out2) {
-    __shared__ double sred[2];
+__global__ void __launch_bounds__(kThreads) k_moments(const uint32_t* __restrict__ keys, uint64_t n, double* part) {
     double v[2] = {0.0, 0.0};
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const double x = (double)xnorm(__ldg(keys + i));
         v[0] += x;
         v[1] += x * x;
     }
-    block_add<2>(v, out2, sred);
+    block_partials<2>(v, part);
 }
 
 // Forward + backward of yhat = w*z + c with z = (xn - mu) * inv_sigma and target
-// y = pos * scale: accumulates sum(r*z), sum(r), sum(r^2).
-__global__ void k_root_linear_grad(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ pos,
-                                   uint64_t n, float mu, float inv_sigma, float scale, float w, float c,
-                                   double* out3) {
-    __shared__ double sred[3];
+// y = pos * scale: sums of r*z, r and r^2.
+__global__ void __launch_bounds__(kThreads) k_root_linear_grad(const uint32_t* __restrict__ keys,
+                                                               const uint32_t* __restrict__ pos, uint64_t n,
+                                                               float mu, float inv_sigma, float scale, float w,
+                                                               float c, double* part) {
     double v[3] = {0.0, 0.0, 0.0};
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const float z = __fmul_rn(__fsub_rn(xnorm(__ldg(keys + i)), mu), inv_sigma);
@@ -75,13 +106,12 @@ __global__ void k_root_linear_grad(const uint32_t* __restrict__ keys, const uint
         v[1] += (double)r;
         v[2] += (double)r * (double)r;
     }
-    block_add<3>(v, out3, sred);
+    block_partials<3>(v, part);
 }
 
 // The same gradient over explicit (z, y) samples, exposed through the C ABI.
-__global__ void k_linear_grad(const float* __restrict__ z, const float* __restrict__ y, uint64_t n, float w,
-                              float c, double* out3) {
-    __shared__ double sred[3];
+__global__ void __launch_bounds__(kThreads) k_linear_grad(const float* __restrict__ z, const float* __restrict__ y,
+                                                          uint64_t n, float w, float c, double* part) {
     double v[3] = {0.0, 0.0, 0.0};
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const float zi = __ldg(z + i);
@@ -90,13 +120,12 @@ __global__ void k_linear_grad(const float* __restrict__ z, const float* __restri
         v[1] += (double)r;
         v[2] += (double)r * (double)r;
     }
-    block_add<3>(v, out3, sred);
+    block_partials<3>(v, part);
 }
 
 // ---------------------------------------------------------------- MLP root
 
-// params: w1[H], b1[H], w2[H], b2 (FP32); grad: same layout, then the loss (FP64 sums of
-// 2/m * dL terms are formed on the host side of the call by scaling).
+// params: w1[H], b1[H], w2[H], b2 (FP32); per sample the terms of r*dout/dtheta and r^2.
 template <int H>
 __device__ __forceinline__ void mlp_sample(const float* p, float xn, float y, float (&g)[3 * H + 2]) {
     float pre[H], h[H];
@@ -128,10 +157,9 @@ __global__ void __launch_bounds__(kThreads) k_mlp_grad(const float* __restrict__
                                                        const uint32_t* __restrict__ keys,
                                                        const uint32_t* __restrict__ pos, float yscale,
                                                        uint64_t n, uint64_t n_all, uint64_t seed,
-                                                       const float* __restrict__ params, double* out) {
+                                                       const float* __restrict__ params, double* part) {
     constexpr int CNT = 3 * H + 2;
     __shared__ float sp[3 * H + 1];
-    __shared__ double sred[CNT];
     for (int k = threadIdx.x; k < 3 * H + 1; k += blockDim.x) sp[k] = params[k];
     __syncthreads();
     float g[CNT];
@@ -157,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_grad(const float* __restrict__
     double v[CNT];
 #pragma unroll
     for (int k = 0; k < CNT; ++k) v[k] = (double)g[k];
-    block_add<CNT>(v, out, sred);
+    block_partials<CNT>(v, part);
 }
 
 // Adam update of the 3H+1 MLP parameters from summed gradients (scaled by 2/m here).
@@ -173,7 +201,7 @@ __global__ void k_adam(float* params, float* m, float* v, const double* gsum, in
     params[k] -= lr * mh / (sqrtf(vh) + eps);
 }
 
-// ----------------------------------------------------------------- leaves
+// ------------------------------------------------------- leaves: mean squared error
 
 __global__ void k_route(const RmiDev m, const uint32_t* __restrict__ keys, uint64_t n, uint32_t* __restrict__ leaf,
                         uint32_t* __restrict__ x0) {
@@ -185,12 +213,12 @@ __global__ void k_route(const RmiDev m, const uint32_t* __restrict__ keys, uint6
     }
 }
 
-// per leaf: count, sum d, sum d^2 (d relative to the leaf's smallest key)
+// per leaf: count, sum d, sum d^2 (d relative to the leaf's smallest key, so d >= 0)
 __global__ void k_leaf_moments(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ leaf, uint64_t n,
                                const uint32_t* __restrict__ x0, double* mom) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t l = __ldg(leaf + i);
-        const double d = (double)__ll2float_rn((long long)__ldg(keys + i) - (long long)__ldg(x0 + l));
+        const double d = (double)dev::rel_offset(__ldg(keys + i), __ldg(x0 + l));
         atomicAdd(mom + 3 * (size_t)l, 1.0);
         atomicAdd(mom + 3 * (size_t)l + 1, d);
         atomicAdd(mom + 3 * (size_t)l + 2, d * d);
@@ -221,7 +249,7 @@ __global__ void k_leaf_grad(const uint32_t* __restrict__ keys, const uint32_t* _
                             const float* __restrict__ w, const float* __restrict__ c, double* acc) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t l = __ldg(leaf + i);
-        const float d = __ll2float_rn((long long)__ldg(keys + i) - (long long)__ldg(x0 + l));
+        const float d = dev::rel_offset(__ldg(keys + i), __ldg(x0 + l));
         const float z = __fmul_rn(__fsub_rn(d, __ldg(mu + l)), __ldg(isd + l));
         const float r = __fsub_rn(__fadd_rn(__fmul_rn(__ldg(w + l), z), __ldg(c + l)), __uint2float_rn(__ldg(pos + i)));
         atomicAdd(acc + 3 * (size_t)l, (double)r * (double)z);
@@ -257,6 +285,124 @@ __global__ void k_leaf_fold(const double* mom, uint32_t L, uint32_t n_ranges, co
     b[l] = (float)((double)c[l] - sl * (double)mu[l]);
 }
 
+// ----------------------------------------------------------- leaves: minimax
+
+// first[l] = smallest address whose leaf is >= l (bisection over [0, 2^32] on the
+// root, which is monotone for the linear root); first[0] = 0, first[L] = 2^32.
+__global__ void k_leaf_first(const RmiDev m, uint32_t L, unsigned long long* first) {
+    const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l > L) return;
+    uint64_t lo = 0, hi = 1ull << 32;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (dev::rmi_root(m, (uint32_t)mid) >= l) hi = mid;
+        else lo = mid + 1;
+    }
+    first[l] = l == 0 ? 0ull : lo;
+}
+
+__device__ __forceinline__ float block_max(float v, float* s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float r = s[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, s[w]);
+    return r;
+}
+
+__device__ __forceinline__ float block_min(float v, float* s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float r = s[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fminf(r, s[w]);
+    return r;
+}
+
+// Piece k of the ranges inside [F, G): offsets (from F) of its first and last address.
+__device__ __forceinline__ void piece(const uint32_t* __restrict__ starts, uint32_t n, uint32_t i, uint64_t F,
+                                      uint64_t G, float& dlo, float& dhi) {
+    const uint64_t s = __ldg(starts + i);
+    const uint64_t e = i + 1 < n ? (uint64_t)__ldg(starts + i + 1) : (1ull << 32);
+    dlo = (float)((s > F ? s : F) - F);
+    dhi = (float)((e < G ? e : G) - 1 - F);
+}
+
+// Minimax line of every interval [lo[i], hi[i]) (one CTA per interval): the slope a >= 0
+// minimising E(a) = (G(a) - H(a)) / 2 with G(a) = max_k (t_k - a*dlo_k) and
+// H(a) = min_k (t_k - a*dhi_k) over the pieces k of the ranges inside the interval
+// (t_k = k), by ternary search over [0, (count - 1) / widest piece]; then c = (G + H) / 2.
+// Output in the library's convention: pos = floor(a*d + b) with b = i0 + c + 0.5 (i0 the
+// interval's first range), and E.
+__global__ void __launch_bounds__(kFitThreads) k_fit_minimax(const uint32_t* __restrict__ starts, uint32_t n,
+                                                             const unsigned long long* __restrict__ ivl_lo,
+                                                             const unsigned long long* __restrict__ ivl_hi,
+                                                             uint32_t count, float* out_a, float* out_b,
+                                                             float* out_e) {
+    __shared__ float s[kFitThreads / 32];
+    for (uint32_t iv = blockIdx.x; iv < count; iv += gridDim.x) {
+        const uint64_t F = ivl_lo[iv], G = ivl_hi[iv];
+        if (F >= G) {
+            if (threadIdx.x == 0) {
+                out_a[iv] = 0.f;
+                out_b[iv] = 0.f;
+                out_e[iv] = 0.f;
+            }
+            continue;
+        }
+        const uint32_t i0 = dev::pred_search1(starts, 0, n, (uint32_t)F);
+        const uint32_t i1 = dev::pred_search1(starts, 0, n, (uint32_t)(G - 1));
+        const uint32_t cnt = i1 - i0 + 1;
+        float wmax = 0.f;
+        for (uint32_t k = threadIdx.x; k < cnt; k += blockDim.x) {
+            float dlo, dhi;
+            piece(starts, n, i0 + k, F, G, dlo, dhi);
+            wmax = fmaxf(wmax, dhi - dlo);
+        }
+        wmax = block_max(wmax, s);
+        float alo = 0.f, ahi = (float)(cnt - 1) / fmaxf(wmax, 1.f);
+        for (int it = 0; it < kFitIters; ++it) {
+            const float m1 = alo + (ahi - alo) / 3.f, m2 = ahi - (ahi - alo) / 3.f;
+            float g1 = -INFINITY, h1 = INFINITY, g2 = -INFINITY, h2 = INFINITY;
+            for (uint32_t k = threadIdx.x; k < cnt; k += blockDim.x) {
+                float dlo, dhi;
+                piece(starts, n, i0 + k, F, G, dlo, dhi);
+                const float t = (float)k;
+                g1 = fmaxf(g1, t - m1 * dlo);
+                h1 = fminf(h1, t - m1 * dhi);
+                g2 = fmaxf(g2, t - m2 * dlo);
+                h2 = fminf(h2, t - m2 * dhi);
+            }
+            g1 = block_max(g1, s);
+            h1 = block_min(h1, s);
+            g2 = block_max(g2, s);
+            h2 = block_min(h2, s);
+            if (g1 - h1 < g2 - h2) ahi = m2;
+            else alo = m1;
+        }
+        const float a = 0.5f * (alo + ahi);
+        float g = -INFINITY, h = INFINITY;
+        for (uint32_t k = threadIdx.x; k < cnt; k += blockDim.x) {
+            float dlo, dhi;
+            piece(starts, n, i0 + k, F, G, dlo, dhi);
+            g = fmaxf(g, (float)k - a * dlo);
+            h = fminf(h, (float)k - a * dhi);
+        }
+        g = block_max(g, s);
+        h = block_min(h, s);
+        if (threadIdx.x == 0) {
+            out_a[iv] = a;
+            out_b[iv] = __fadd_rn((float)i0, 0.5f * (g + h) + 0.5f);
+            out_e[iv] = 0.5f * (g - h);
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- error bounds
 
 __device__ __forceinline__ void flush_eps(uint32_t l, uint32_t lo, uint32_t hi, uint32_t* elo, uint32_t* ehi) {
@@ -264,7 +410,7 @@ __device__ __forceinline__ void flush_eps(uint32_t l, uint32_t lo, uint32_t hi, 
     if (hi) atomicMax(ehi + l, hi);
 }
 
-// Exhaustive sweep over every 32-bit address: per leaf, the largest amount by which the
+// Exhaustive sweep over every 32-bit address: per model, the largest amount by which the
 // predicted position exceeds (eps_lo) or falls short of (eps_hi) the true position.
 __global__ void __launch_bounds__(kThreads) k_eps_sweep(const RmiDev m, const uint32_t* __restrict__ starts,
                                                         uint32_t n, uint32_t* elo, uint32_t* ehi) {
@@ -276,25 +422,26 @@ __global__ void __launch_bounds__(kThreads) k_eps_sweep(const RmiDev m, const ui
     if (xa >= xb) return;
     uint32_t t = dev::pred_search1(starts, 0, n, (uint32_t)xa);
     uint64_t next = t + 1 < n ? (uint64_t)__ldg(starts + t + 1) : (1ull << 32);
-    uint32_t cur = 0xFFFFFFFFu, mlo = 0, mhi = 0;
-    float ca = 0.f, cb = 0.f;
-    uint32_t cx0 = 0;
+    uint32_t cl = 0xFFFFFFFFu, cur = 0xFFFFFFFFu, mlo = 0, mhi = 0;
+    dev::RmiLeaf lf{0.f, 0.f, 0u, 0u}, f{0.f, 0.f, 0u, 0u};
     for (uint64_t x = xa; x < xb; ++x) {
         while (x >= next) {
             ++t;
             next = t + 1 < n ? (uint64_t)__ldg(starts + t + 1) : (1ull << 32);
         }
         const uint32_t l = dev::rmi_root(m, (uint32_t)x);
-        if (l != cur) {
-            if (cur != 0xFFFFFFFFu) flush_eps(cur, mlo, mhi, elo, ehi);
-            cur = l;
-            mlo = mhi = 0;
-            ca = __ldg(m.a + l);
-            cb = __ldg(m.b + l);
-            cx0 = __ldg(m.x0 + l);
+        if (l != cl) {
+            cl = l;
+            lf = dev::rmi_leaf(m, m.a, m.b, m.x0, m.eps, l);
         }
-        const float d = __ll2float_rn((long long)x - (long long)cx0);
-        const uint32_t p = dev::clamp_floor(__fadd_rn(__fmul_rn(ca, d), cb), n);
+        const uint32_t md = lf.eps == kEpsSplit ? dev::rmi_sub_model(lf, (uint32_t)x) : l;
+        if (md != cur) {
+            if (cur != 0xFFFFFFFFu) flush_eps(cur, mlo, mhi, elo, ehi);
+            cur = md;
+            mlo = mhi = 0;
+            f = md == l ? lf : dev::rmi_leaf(m, m.a, m.b, m.x0, m.eps, md);
+        }
+        const uint32_t p = dev::rmi_leaf_pos(f, (uint32_t)x, n);
         if (p > t) mlo = max(mlo, p - t);
         else mhi = max(mhi, t - p);
     }
@@ -307,24 +454,43 @@ __global__ void k_eps_samples(const RmiDev m, const uint32_t* __restrict__ keys,
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_s; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t x = __ldg(keys + i), t = __ldg(pos + i);
         const uint32_t l = dev::rmi_root(m, x);
-        const dev::RmiLeaf f{__ldg(m.a + l), __ldg(m.b + l), __ldg(m.x0 + l), 0u};
+        const dev::RmiLeaf lf = dev::rmi_leaf(m, m.a, m.b, m.x0, m.eps, l);
+        const uint32_t md = lf.eps == kEpsSplit ? dev::rmi_sub_model(lf, x) : l;
+        const dev::RmiLeaf f = md == l ? lf : dev::rmi_leaf(m, m.a, m.b, m.x0, m.eps, md);
         const uint32_t p = dev::rmi_leaf_pos(f, x, n);
-        flush_eps(l, p > t ? p - t : 0u, t > p ? t - p : 0u, elo, ehi);
+        flush_eps(md, p > t ? p - t : 0u, t > p ? t - p : 0u, elo, ehi);
     }
 }
 
-__global__ void k_pack_eps(const uint32_t* lo, const uint32_t* hi, uint32_t* packed, uint32_t L) {
+// Packed bounds of every model (split leaves keep their marker).
+__global__ void k_pack_eps(const uint32_t* lo, const uint32_t* hi, uint32_t* packed, uint32_t M) {
     const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= L) return;
-    packed[l] = (lo[l] > 0xFFFFu || hi[l] > 0xFFFFu) ? 0xFFFFFFFFu : (lo[l] | (hi[l] << 16));
+    if (l >= M || packed[l] == kEpsSplit) return;
+    packed[l] = (lo[l] > 0xFFFEu || hi[l] > 0xFFFEu) ? 0xFFFFFFFFu : (lo[l] | (hi[l] << 16));
 }
 
-// Leaf parameters interleaved for lookups that read them from global memory.
+// Model parameters interleaved for lookups that read them from global memory.
 __global__ void k_pack_leaf4(const float* a, const float* b, const uint32_t* x0, const uint32_t* eps, uint4* out,
-                             uint32_t L) {
+                             uint32_t M) {
     const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= L) return;
+    if (l >= M) return;
     out[l] = make_uint4(__float_as_uint(a[l]), __float_as_uint(b[l]), x0[l], eps[l]);
+}
+
+// Over the training lookups: squared error of the predicted position and the width of
+// the model window searched (the whole registry where no bound holds).
+__global__ void __launch_bounds__(kThreads) k_model_stats(const RmiDev m, const uint32_t* __restrict__ keys,
+                                                          const uint32_t* __restrict__ pos, uint64_t n_s,
+                                                          uint32_t n, double* part) {
+    double v[2] = {0.0, 0.0};
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_s; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = __ldg(keys + i);
+        const dev::RmiLeaf f = dev::rmi_model(m, m.a, m.b, m.x0, m.eps, x);
+        const double r = (double)dev::rmi_leaf_pos(f, x, n) - (double)__ldg(pos + i);
+        v[0] += r * r;
+        v[1] += f.eps == 0xFFFFFFFFu ? (double)n : (double)((f.eps & 0xFFFFu) + (f.eps >> 16) + 1u);
+    }
+    block_partials<2>(v, part);
 }
 
 int grid_for(uint64_t n) {
@@ -339,18 +505,20 @@ int grid_for(uint64_t n) {
 template <int H>
 cudaError_t launch_mlp_grad(const float* xs, const float* ys, const uint32_t* keys, const uint32_t* pos,
                             float yscale, uint64_t n, uint64_t n_all, uint64_t seed, const float* params,
-                            double* out, cudaStream_t st) {
-    k_mlp_grad<H><<<grid_for(n), kThreads, 0, st>>>(xs, ys, keys, pos, yscale, n, n_all, seed, params, out);
+                            double* part, double* out, cudaStream_t st) {
+    const int g = grid_for(n);
+    k_mlp_grad<H><<<g, kThreads, 0, st>>>(xs, ys, keys, pos, yscale, n, n_all, seed, params, part);
+    k_sum_partials<<<1, 128, 0, st>>>(part, g, 3 * H + 2, out);
     return cudaGetLastError();
 }
 
 cudaError_t mlp_grad_dispatch(uint32_t hidden, const float* xs, const float* ys, const uint32_t* keys,
                               const uint32_t* pos, float yscale, uint64_t n, uint64_t n_all, uint64_t seed,
-                              const float* params, double* out, cudaStream_t st) {
+                              const float* params, double* part, double* out, cudaStream_t st) {
     switch (hidden) {
-        case 8: return launch_mlp_grad<8>(xs, ys, keys, pos, yscale, n, n_all, seed, params, out, st);
-        case 16: return launch_mlp_grad<16>(xs, ys, keys, pos, yscale, n, n_all, seed, params, out, st);
-        case 32: return launch_mlp_grad<32>(xs, ys, keys, pos, yscale, n, n_all, seed, params, out, st);
+        case 8: return launch_mlp_grad<8>(xs, ys, keys, pos, yscale, n, n_all, seed, params, part, out, st);
+        case 16: return launch_mlp_grad<16>(xs, ys, keys, pos, yscale, n, n_all, seed, params, part, out, st);
+        case 32: return launch_mlp_grad<32>(xs, ys, keys, pos, yscale, n, n_all, seed, params, part, out, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -359,42 +527,56 @@ cudaError_t mlp_grad_dispatch(uint32_t hidden, const float* xs, const float* ys,
 
 // --------------------------------------------------------------- host side
 
+size_t rmi_partials_bytes() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return ((size_t)sms * 8 * kMaxRed + kMaxRed) * sizeof(double);
+}
+
 struct TrainScratch {
-    uint32_t* pos;      // [n] (owned by caller)
     uint32_t* leaf;     // [n]
-    double* red;        // small reductions [128]
+    double* red;        // ordered sums [kMaxRed]
+    double* part;       // per-block partials [grid][kMaxRed]
     double* mom;        // [3L]
     double* acc;        // [3L]
     float *mu, *isd, *w, *c;  // [L]
+    float *la, *lb;           // [L] MSE leaf lines
+    uint32_t* lx0;            // [L]
+    unsigned long long* first;  // [L + 1]
     float *mp, *mm, *mv;      // MLP params / Adam state [3*32+1]
 };
 
-size_t rmi_train_scratch_bytes(uint64_t n, uint32_t L) {
-    return n * 4 + 128 * 8 + (size_t)L * 3 * 8 * 2 + (size_t)L * 4 * 4 + 3 * 128 * 4 + 1024;
-}
-
-static TrainScratch carve(void* base, uint64_t n, uint32_t L) {
+static size_t carve_bytes(uint64_t n, uint32_t L, TrainScratch* s, void* base) {
     char* p = (char*)base;
+    size_t used = 0;
     auto take = [&](size_t bytes) {
-        char* r = p;
-        p += (bytes + 255) / 256 * 256;
+        char* r = p ? p + used : nullptr;
+        used += (bytes + 255) / 256 * 256;
         return (void*)r;
     };
-    TrainScratch s;
-    s.pos = nullptr;
-    s.leaf = (uint32_t*)take(n * 4);
-    s.red = (double*)take(128 * 8);
-    s.mom = (double*)take((size_t)L * 3 * 8);
-    s.acc = (double*)take((size_t)L * 3 * 8);
-    s.mu = (float*)take((size_t)L * 4);
-    s.isd = (float*)take((size_t)L * 4);
-    s.w = (float*)take((size_t)L * 4);
-    s.c = (float*)take((size_t)L * 4);
-    s.mp = (float*)take(128 * 4);
-    s.mm = (float*)take(128 * 4);
-    s.mv = (float*)take(128 * 4);
-    return s;
+    TrainScratch t;
+    t.leaf = (uint32_t*)take(n * 4);
+    t.red = (double*)take(kMaxRed * 8);
+    t.part = (double*)take(rmi_partials_bytes());
+    t.mom = (double*)take((size_t)L * 3 * 8);
+    t.acc = (double*)take((size_t)L * 3 * 8);
+    t.mu = (float*)take((size_t)L * 4);
+    t.isd = (float*)take((size_t)L * 4);
+    t.w = (float*)take((size_t)L * 4);
+    t.c = (float*)take((size_t)L * 4);
+    t.la = (float*)take((size_t)L * 4);
+    t.lb = (float*)take((size_t)L * 4);
+    t.lx0 = (uint32_t*)take((size_t)L * 4);
+    t.first = (unsigned long long*)take((size_t)(L + 1) * 8);
+    t.mp = (float*)take(128 * 4);
+    t.mm = (float*)take(128 * 4);
+    t.mv = (float*)take(128 * 4);
+    if (s) *s = t;
+    return used;
 }
+
+size_t rmi_train_scratch_bytes(uint64_t n, uint32_t L) { return carve_bytes(n, L, nullptr, nullptr) + 1024; }
 
 #define RMI_CU(x)                              \
     do {                                       \
@@ -402,21 +584,163 @@ static TrainScratch carve(void* base, uint64_t n, uint32_t L) {
         if (e_ != cudaSuccess) return e_;      \
     } while (0)
 
-cudaError_t rmi_train_device(RmiDev* m, float* d_a, float* d_b, uint32_t* d_x0, const uint32_t* keys,
-                             const uint32_t* pos, uint64_t n, uint32_t n_ranges, const gnm_rmi_config& cfg,
-                             void* scratch, RmiTrainOut* out, cudaStream_t st) {
+namespace {
+
+// Minimax lines of `lo.size()` intervals on the device (synchronous; host vectors out).
+cudaError_t fit_intervals(const uint32_t* starts, uint32_t n, const std::vector<unsigned long long>& lo,
+                          const std::vector<unsigned long long>& hi, std::vector<float>& a, std::vector<float>& b,
+                          std::vector<float>& e, cudaStream_t st) {
+    const size_t k = lo.size();
+    a.assign(k, 0.f);
+    b.assign(k, 0.f);
+    e.assign(k, 0.f);
+    if (k == 0) return cudaSuccess;
+    void* buf = nullptr;
+    RMI_CU(cudaMalloc(&buf, k * (8 + 8 + 4 + 4 + 4)));
+    unsigned long long* dlo = (unsigned long long*)buf;
+    unsigned long long* dhi = dlo + k;
+    float* da = (float*)(dhi + k);
+    float* db = da + k;
+    float* de = db + k;
+    cudaError_t r = cudaMemcpyAsync(dlo, lo.data(), k * 8, cudaMemcpyHostToDevice, st);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(dhi, hi.data(), k * 8, cudaMemcpyHostToDevice, st);
+    if (r == cudaSuccess) {
+        const uint32_t grid = (uint32_t)std::min<size_t>(k, 65535);
+        k_fit_minimax<<<grid, kFitThreads, 0, st>>>(starts, n, dlo, dhi, (uint32_t)k, da, db, de);
+        r = cudaGetLastError();
+    }
+    if (r == cudaSuccess) r = cudaMemcpyAsync(a.data(), da, k * 4, cudaMemcpyDeviceToHost, st);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(b.data(), db, k * 4, cudaMemcpyDeviceToHost, st);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(e.data(), de, k * 4, cudaMemcpyDeviceToHost, st);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    return r;
+}
+
+// Window width expected from a minimax error E: each side rounds to about E + 0.5 after
+// the floor, plus the FP32 rounding of the prediction.
+inline bool window_ok(float E, uint32_t target) { return target == 0 || 2.f * E + 3.f <= (float)target; }
+
+// Minimax leaves with split leaves (host orchestration of k_leaf_first and
+// k_fit_minimax): fills the model arrays of `out`.
+cudaError_t minimax_leaves(const RmiDev& m, const uint32_t* starts, uint32_t n_ranges, const gnm_rmi_config& cfg,
+                           unsigned long long* d_first, RmiTrainOut* out, cudaStream_t st) {
+    const uint32_t L = m.n_leaves;
+    k_leaf_first<<<(L + 1 + 255) / 256, 256, 0, st>>>(m, L, d_first);
+    RMI_CU(cudaGetLastError());
+    std::vector<unsigned long long> first(L + 1);
+    RMI_CU(cudaMemcpyAsync(first.data(), d_first, (size_t)(L + 1) * 8, cudaMemcpyDeviceToHost, st));
+    RMI_CU(cudaStreamSynchronize(st));
+    for (uint32_t l = 0; l < L; ++l)
+        if (first[l] > first[l + 1]) return cudaErrorNotSupported;
+    std::vector<unsigned long long> lo(first.begin(), first.end() - 1), hi(first.begin() + 1, first.end());
+    std::vector<float> la, lb, le;
+    RMI_CU(fit_intervals(starts, n_ranges, lo, hi, la, lb, le, st));
+    // split leaves: try 2, 4, 8, ... sub-leaves per failing leaf until every sub-leaf fits
+    struct Split {
+        uint32_t shift = 0, count = 0;
+        std::vector<float> a, b;
+        std::vector<uint32_t> x0;
+    };
+    std::vector<Split> split(L);
+    std::vector<uint32_t> failing;
+    for (uint32_t l = 0; l < L; ++l)
+        if (!window_ok(le[l], cfg.eps_target) && hi[l] - lo[l] > 1) failing.push_back(l);
+    const uint32_t max_r = std::min<uint32_t>(cfg.max_split_log2, 16);
+    uint64_t n_sub = 0;
+    for (uint32_t r = 1; r <= max_r && !failing.empty(); ++r) {
+        std::vector<unsigned long long> slo, shi;
+        std::vector<uint32_t> sh(failing.size()), cnt(failing.size());
+        for (size_t i = 0; i < failing.size(); ++i) {
+            const uint32_t l = failing[i];
+            const uint64_t W = hi[l] - lo[l];
+            uint32_t lg = 0;
+            while ((1ull << lg) < W) ++lg;
+            sh[i] = lg > r ? lg - r : 0u;
+            cnt[i] = (uint32_t)((W + (1ull << sh[i]) - 1) >> sh[i]);
+            for (uint32_t j = 0; j < cnt[i]; ++j) {
+                slo.push_back(lo[l] + ((uint64_t)j << sh[i]));
+                shi.push_back(std::min<unsigned long long>(lo[l] + ((uint64_t)(j + 1) << sh[i]), hi[l]));
+            }
+        }
+        if (n_sub + slo.size() + L > kMaxModels) break;  // keep the last accepted splits
+        std::vector<float> sa, sb, se;
+        RMI_CU(fit_intervals(starts, n_ranges, slo, shi, sa, sb, se, st));
+        std::vector<uint32_t> still;
+        size_t o = 0;
+        for (size_t i = 0; i < failing.size(); ++i) {
+            const uint32_t l = failing[i];
+            bool ok = true;
+            for (uint32_t j = 0; j < cnt[i]; ++j) ok = ok && window_ok(se[o + j], cfg.eps_target);
+            if (ok || sh[i] == 0 || r == max_r) {
+                if (split[l].count) n_sub -= split[l].count;
+                Split& s = split[l];
+                s.shift = sh[i];
+                s.count = cnt[i];
+                s.a.assign(sa.begin() + o, sa.begin() + o + cnt[i]);
+                s.b.assign(sb.begin() + o, sb.begin() + o + cnt[i]);
+                s.x0.resize(cnt[i]);
+                for (uint32_t j = 0; j < cnt[i]; ++j) s.x0[j] = (uint32_t)slo[o + j];
+                n_sub += cnt[i];
+            }
+            if (!ok && sh[i] > 0 && r < max_r) still.push_back(l);
+            o += cnt[i];
+        }
+        failing.swap(still);
+    }
+    // models: leaves, then the sub-leaves of split leaves in leaf order
+    const uint32_t M = L + (uint32_t)n_sub;
+    out->a.assign(M, 0.f);
+    out->b.assign(M, 0.f);
+    out->x0.assign(M, 0u);
+    out->eps.assign(M, 0u);
+    out->split.assign(L, 0u);
+    out->empty_leaves = 0;
+    out->split_leaves = 0;
+    uint32_t nxt = L;
+    for (uint32_t l = 0; l < L; ++l) {
+        const uint32_t fx = (uint32_t)std::min<unsigned long long>(lo[l], 0xFFFFFFFFull);
+        out->x0[l] = fx;
+        out->empty_leaves += lo[l] >= hi[l];
+        if (split[l].count) {
+            const Split& s = split[l];
+            const uint32_t w = s.shift | ((s.count - 1) << 8);
+            std::memcpy(&out->a[l], &w, 4);
+            std::memcpy(&out->b[l], &nxt, 4);
+            out->eps[l] = kEpsSplit;
+            out->split[l] = w;
+            ++out->split_leaves;
+            for (uint32_t j = 0; j < s.count; ++j, ++nxt) {
+                out->a[nxt] = s.a[j];
+                out->b[nxt] = s.b[j];
+                out->x0[nxt] = s.x0[j];
+            }
+        } else {
+            out->a[l] = la[l];
+            out->b[l] = lb[l];
+        }
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t rmi_train_device(RmiDev* m, const uint32_t* keys, const uint32_t* pos, uint64_t n,
+                             const uint32_t* starts, uint32_t n_ranges, const gnm_rmi_config& cfg, void* scratch,
+                             RmiTrainOut* out, cudaStream_t st) {
     const uint32_t L = cfg.n_leaves;
-    TrainScratch s = carve(scratch, n, L);
+    TrainScratch s;
+    carve_bytes(n, L, &s, scratch);
     const int g = grid_for(n);
-    double h[4];
+    double h[kMaxRed];
     // ---- root
     m->n_leaves = L;
     m->root_kind = cfg.root_kind;
     m->hidden = cfg.hidden;
     const float yscale_root = (float)((double)L / n_ranges);
     if (cfg.root_kind == GNM_RMI_ROOT_LINEAR) {
-        RMI_CU(cudaMemsetAsync(s.red, 0, 2 * 8, st));
-        k_moments<<<g, kThreads, 0, st>>>(keys, n, s.red);
+        k_moments<<<g, kThreads, 0, st>>>(keys, n, s.part);
+        k_sum_partials<<<1, 128, 0, st>>>(s.part, g, 2, s.red);
         RMI_CU(cudaMemcpyAsync(h, s.red, 16, cudaMemcpyDeviceToHost, st));
         RMI_CU(cudaStreamSynchronize(st));
         const double mu = h[0] / n, var = h[1] / n - mu * mu;
@@ -424,8 +748,9 @@ cudaError_t rmi_train_device(RmiDev* m, float* d_a, float* d_b, uint32_t* d_x0, 
         float w = 0.f, c = 0.f;
         double loss = 0.0;
         for (uint32_t it = 0; it <= cfg.leaf_iters; ++it) {
-            RMI_CU(cudaMemsetAsync(s.red, 0, 3 * 8, st));
-            k_root_linear_grad<<<g, kThreads, 0, st>>>(keys, pos, n, (float)mu, (float)(1.0 / sd), yscale_root, w, c, s.red);
+            k_root_linear_grad<<<g, kThreads, 0, st>>>(keys, pos, n, (float)mu, (float)(1.0 / sd), yscale_root, w, c,
+                                                      s.part);
+            k_sum_partials<<<1, 128, 0, st>>>(s.part, g, 3, s.red);
             RMI_CU(cudaMemcpyAsync(h, s.red, 24, cudaMemcpyDeviceToHost, st));
             RMI_CU(cudaStreamSynchronize(st));
             loss = h[2] / n;
@@ -458,20 +783,17 @@ cudaError_t rmi_train_device(RmiDev* m, float* d_a, float* d_b, uint32_t* d_x0, 
         const uint64_t batch = cfg.mlp_batch < n ? cfg.mlp_batch : n;
         const float ys = (float)(1.0 / n_ranges);  // targets in [0, 1): position / n
         for (uint32_t step = 1; step <= cfg.mlp_steps; ++step) {
-            RMI_CU(cudaMemsetAsync(s.red, 0, (3 * H + 2) * 8, st));
             RMI_CU(mlp_grad_dispatch(cfg.hidden, nullptr, nullptr, keys, pos, ys, batch, n,
-                                     cfg.seed * 1000003ull + step, s.mp, s.red, st));
+                                     cfg.seed * 1000003ull + step, s.mp, s.part, s.red, st));
             k_adam<<<1, 128, 0, st>>>(s.mp, s.mm, s.mv, s.red, cnt, 1.0 / batch, cfg.mlp_lr, 0.9f, 0.999f, 1e-8f,
                                       (int)step);
         }
         // final loss over all samples (in leaf units)
-        RMI_CU(cudaMemsetAsync(s.red, 0, (3 * H + 2) * 8, st));
-        RMI_CU(mlp_grad_dispatch(cfg.hidden, nullptr, nullptr, keys, pos, ys, n, n, 0, s.mp, s.red, st));
-        double gl[3 * 32 + 2];
+        RMI_CU(mlp_grad_dispatch(cfg.hidden, nullptr, nullptr, keys, pos, ys, n, n, 0, s.mp, s.part, s.red, st));
         RMI_CU(cudaMemcpyAsync(p, s.mp, cnt * 4, cudaMemcpyDeviceToHost, st));
-        RMI_CU(cudaMemcpyAsync(gl, s.red, (3 * H + 2) * 8, cudaMemcpyDeviceToHost, st));
+        RMI_CU(cudaMemcpyAsync(h, s.red, (3 * H + 2) * 8, cudaMemcpyDeviceToHost, st));
         RMI_CU(cudaStreamSynchronize(st));
-        out->root_loss = gl[3 * H + 1] / n * (double)L * L;
+        out->root_loss = h[3 * H + 1] / n * (double)L * L;
         for (int j = 0; j < H; ++j) {
             m->w1[j] = p[j];
             m->b1[j] = p[H + j];
@@ -480,87 +802,91 @@ cudaError_t rmi_train_device(RmiDev* m, float* d_a, float* d_b, uint32_t* d_x0, 
         for (int j = H; j < 32; ++j) m->w1[j] = m->b1[j] = m->w2[j] = 0.f;
         m->b2 = p[3 * H] * (float)L;
     }
-    // ---- leaves
-    RMI_CU(cudaMemsetAsync(d_x0, 0xFF, (size_t)L * 4, st));
+    // ---- leaves (minimax needs contiguous leaf intervals: a root whose leaf boundaries
+    // come out unordered takes the MSE leaves)
+    if (cfg.leaf_fit == GNM_RMI_FIT_MINIMAX) {
+        const cudaError_t e = minimax_leaves(*m, starts, n_ranges, cfg, s.first, out, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
+    RMI_CU(cudaMemsetAsync(s.lx0, 0xFF, (size_t)L * 4, st));
     RmiDev route = *m;
-    k_route<<<g, kThreads, 0, st>>>(route, keys, n, s.leaf, d_x0);
+    k_route<<<g, kThreads, 0, st>>>(route, keys, n, s.leaf, s.lx0);
     RMI_CU(cudaMemsetAsync(s.mom, 0, (size_t)L * 3 * 8, st));
-    k_leaf_moments<<<g, kThreads, 0, st>>>(keys, s.leaf, n, d_x0, s.mom);
+    k_leaf_moments<<<g, kThreads, 0, st>>>(keys, s.leaf, n, s.lx0, s.mom);
     const int gl = (int)((L + 255) / 256);
     k_leaf_standardise<<<gl, 256, 0, st>>>(s.mom, L, s.mu, s.isd);
     RMI_CU(cudaMemsetAsync(s.w, 0, (size_t)L * 4, st));
     RMI_CU(cudaMemsetAsync(s.c, 0, (size_t)L * 4, st));
     for (uint32_t it = 0; it < cfg.leaf_iters; ++it) {
         RMI_CU(cudaMemsetAsync(s.acc, 0, (size_t)L * 3 * 8, st));
-        k_leaf_grad<<<g, kThreads, 0, st>>>(keys, pos, s.leaf, n, d_x0, s.mu, s.isd, s.w, s.c, s.acc);
+        k_leaf_grad<<<g, kThreads, 0, st>>>(keys, pos, s.leaf, n, s.lx0, s.mu, s.isd, s.w, s.c, s.acc);
         k_leaf_step<<<gl, 256, 0, st>>>(s.acc, s.mom, L, 0.5f, s.w, s.c);
     }
-    RMI_CU(cudaMemsetAsync(s.acc, 0, (size_t)L * 3 * 8, st));
-    k_leaf_grad<<<g, kThreads, 0, st>>>(keys, pos, s.leaf, n, d_x0, s.mu, s.isd, s.w, s.c, s.acc);
-    k_leaf_fold<<<gl, 256, 0, st>>>(s.mom, L, n_ranges, s.mu, s.isd, s.w, s.c, d_a, d_b, d_x0);
+    k_leaf_fold<<<gl, 256, 0, st>>>(s.mom, L, n_ranges, s.mu, s.isd, s.w, s.c, s.la, s.lb, s.lx0);
     RMI_CU(cudaGetLastError());
-    // leaf loss and empty leaves
-    double* hacc = new double[(size_t)L * 3];
-    double* hmom = new double[(size_t)L * 3];
-    cudaError_t e = cudaMemcpyAsync(hacc, s.acc, (size_t)L * 3 * 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hmom, s.mom, (size_t)L * 3 * 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess) {
-        double sse = 0;
-        uint32_t empty = 0;
-        for (uint32_t l = 0; l < L; ++l) {
-            sse += hacc[3 * l + 2];
-            empty += hmom[3 * l] == 0.0;
-        }
-        out->leaf_loss = sse / n;
-        out->empty_leaves = empty;
-    }
-    delete[] hacc;
-    delete[] hmom;
-    m->a = d_a;
-    m->b = d_b;
-    m->x0 = d_x0;
-    return e;
+    out->a.assign(L, 0.f);
+    out->b.assign(L, 0.f);
+    out->x0.assign(L, 0u);
+    out->eps.assign(L, 0u);
+    out->split.assign(L, 0u);
+    std::vector<double> hmom((size_t)L * 3);
+    RMI_CU(cudaMemcpyAsync(out->a.data(), s.la, (size_t)L * 4, cudaMemcpyDeviceToHost, st));
+    RMI_CU(cudaMemcpyAsync(out->b.data(), s.lb, (size_t)L * 4, cudaMemcpyDeviceToHost, st));
+    RMI_CU(cudaMemcpyAsync(out->x0.data(), s.lx0, (size_t)L * 4, cudaMemcpyDeviceToHost, st));
+    RMI_CU(cudaMemcpyAsync(hmom.data(), s.mom, (size_t)L * 3 * 8, cudaMemcpyDeviceToHost, st));
+    RMI_CU(cudaStreamSynchronize(st));
+    out->empty_leaves = 0;
+    out->split_leaves = 0;
+    for (uint32_t l = 0; l < L; ++l) out->empty_leaves += hmom[3 * l] == 0.0;
+    return cudaSuccess;
 }
 
 cudaError_t rmi_eps_sweep(const RmiDev& m, const uint32_t* starts, uint32_t n, uint32_t* elo, uint32_t* ehi,
                           int sm_count, cudaStream_t st) {
-    RMI_CU(cudaMemsetAsync(elo, 0, (size_t)m.n_leaves * 4, st));
-    RMI_CU(cudaMemsetAsync(ehi, 0, (size_t)m.n_leaves * 4, st));
+    RMI_CU(cudaMemsetAsync(elo, 0, (size_t)m.n_models * 4, st));
+    RMI_CU(cudaMemsetAsync(ehi, 0, (size_t)m.n_models * 4, st));
     k_eps_sweep<<<sm_count * 8, kThreads, 0, st>>>(m, starts, n, elo, ehi);
     return cudaGetLastError();
 }
 
 cudaError_t rmi_eps_from_samples(const RmiDev& m, const uint32_t* keys, const uint32_t* pos, uint64_t n_s,
                                  uint32_t n, uint32_t* elo, uint32_t* ehi, cudaStream_t st) {
-    RMI_CU(cudaMemsetAsync(elo, 0, (size_t)m.n_leaves * 4, st));
-    RMI_CU(cudaMemsetAsync(ehi, 0, (size_t)m.n_leaves * 4, st));
+    RMI_CU(cudaMemsetAsync(elo, 0, (size_t)m.n_models * 4, st));
+    RMI_CU(cudaMemsetAsync(ehi, 0, (size_t)m.n_models * 4, st));
     k_eps_samples<<<grid_for(n_s), kThreads, 0, st>>>(m, keys, pos, n_s, n, elo, ehi);
     return cudaGetLastError();
 }
 
 cudaError_t rmi_pack_leaf4(const float* a, const float* b, const uint32_t* x0, const uint32_t* eps, uint4* out,
-                           uint32_t L, cudaStream_t st) {
-    k_pack_leaf4<<<(L + 255) / 256, 256, 0, st>>>(a, b, x0, eps, out, L);
+                           uint32_t M, cudaStream_t st) {
+    k_pack_leaf4<<<(M + 255) / 256, 256, 0, st>>>(a, b, x0, eps, out, M);
     return cudaGetLastError();
 }
 
-cudaError_t rmi_pack_eps(const uint32_t* lo, const uint32_t* hi, uint32_t* packed, uint32_t L, cudaStream_t st) {
-    k_pack_eps<<<(L + 255) / 256, 256, 0, st>>>(lo, hi, packed, L);
+cudaError_t rmi_pack_eps(const uint32_t* lo, const uint32_t* hi, uint32_t* packed, uint32_t M, cudaStream_t st) {
+    k_pack_eps<<<(M + 255) / 256, 256, 0, st>>>(lo, hi, packed, M);
     return cudaGetLastError();
 }
 
-cudaError_t rmi_linear_grad(const float* z, const float* y, uint64_t n, float w, float c, double* acc3,
+cudaError_t rmi_model_stats(const RmiDev& m, const uint32_t* keys, const uint32_t* pos, uint64_t n_s, uint32_t n,
+                            double* part, double* out2, cudaStream_t st) {
+    const int g = grid_for(n_s);
+    k_model_stats<<<g, kThreads, 0, st>>>(m, keys, pos, n_s, n, part);
+    k_sum_partials<<<1, 128, 0, st>>>(part, g, 2, out2);
+    return cudaGetLastError();
+}
+
+cudaError_t rmi_linear_grad(const float* z, const float* y, uint64_t n, float w, float c, double* part, double* acc3,
                             cudaStream_t st) {
-    RMI_CU(cudaMemsetAsync(acc3, 0, 3 * 8, st));
-    k_linear_grad<<<grid_for(n), kThreads, 0, st>>>(z, y, n, w, c, acc3);
+    const int g = grid_for(n);
+    k_linear_grad<<<g, kThreads, 0, st>>>(z, y, n, w, c, part);
+    k_sum_partials<<<1, 128, 0, st>>>(part, g, 3, acc3);
     return cudaGetLastError();
 }
 
 cudaError_t rmi_mlp_grad(const float* xn, const float* y, uint64_t n, uint32_t hidden, const float* params,
-                         double* grad, cudaStream_t st) {
-    RMI_CU(cudaMemsetAsync(grad, 0, (3 * hidden + 2) * 8, st));
-    return mlp_grad_dispatch(hidden, xn, y, nullptr, nullptr, 1.f, n, n, 0, params, grad, st);
+                         double* part, double* grad, cudaStream_t st) {
+    return mlp_grad_dispatch(hidden, xn, y, nullptr, nullptr, 1.f, n, n, 0, params, part, grad, st);
 }
 
 }  // namespace gnm

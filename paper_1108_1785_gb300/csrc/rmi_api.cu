@@ -10,7 +10,7 @@ using namespace gnm;
 
 namespace {
 
-gnm_status ensure_leaves(gnm_ctx* c, uint32_t L) {
+gnm_status ensure_models(gnm_ctx* c, uint32_t L) {
     if (c->rmi_cap >= L) return GNM_OK;
     cudaFree(c->d_rmi_a);
     cudaFree(c->d_rmi_b);
@@ -34,7 +34,26 @@ gnm_status ensure_leaves(gnm_ctx* c, uint32_t L) {
     return GNM_OK;
 }
 
-// Error bounds of the model in c->rmi (exhaustive or from samples), packed for lookups.
+// Uploads a host model (root in m, arrays in t) into the context's model arrays.
+gnm_status upload_model(gnm_ctx* c, RmiDev& m, const RmiTrainOut& t, cudaStream_t st) {
+    const uint32_t M = (uint32_t)t.a.size();
+    GNM_TRY(ensure_models(c, M));
+    GNM_CU(cudaMemcpyAsync(c->d_rmi_a, t.a.data(), (size_t)M * 4, cudaMemcpyHostToDevice, st));
+    GNM_CU(cudaMemcpyAsync(c->d_rmi_b, t.b.data(), (size_t)M * 4, cudaMemcpyHostToDevice, st));
+    GNM_CU(cudaMemcpyAsync(c->d_rmi_x0, t.x0.data(), (size_t)M * 4, cudaMemcpyHostToDevice, st));
+    GNM_CU(cudaMemcpyAsync(c->d_rmi_eps, t.eps.data(), (size_t)M * 4, cudaMemcpyHostToDevice, st));
+    GNM_CU(cudaStreamSynchronize(st));  // the host vectors may go away
+    m.n_models = M;
+    m.a = c->d_rmi_a;
+    m.b = c->d_rmi_b;
+    m.x0 = c->d_rmi_x0;
+    m.eps = c->d_rmi_eps;
+    c->rmi_split = t.split;
+    return GNM_OK;
+}
+
+// Error bounds of the model in m (exhaustive or from samples), packed for lookups; the
+// eps array already marks split leaves.
 gnm_status finish_model(gnm_ctx* c, RmiDev& m, bool exhaustive, const uint32_t* keys, const uint32_t* pos,
                         uint64_t n, cudaStream_t st, double* sweep_ms) {
     const uint32_t nr = (uint32_t)c->h_starts.size();
@@ -44,8 +63,8 @@ gnm_status finish_model(gnm_ctx* c, RmiDev& m, bool exhaustive, const uint32_t* 
     GNM_CU(cudaEventRecord(e0, st));
     if (exhaustive) GNM_CU(rmi_eps_sweep(m, c->d_starts, nr, c->d_rmi_elo, c->d_rmi_ehi, c->sm_count, st));
     else GNM_CU(rmi_eps_from_samples(m, keys, pos, n, nr, c->d_rmi_elo, c->d_rmi_ehi, st));
-    GNM_CU(rmi_pack_eps(c->d_rmi_elo, c->d_rmi_ehi, c->d_rmi_eps, m.n_leaves, st));
-    GNM_CU(rmi_pack_leaf4(m.a, m.b, m.x0, c->d_rmi_eps, c->d_rmi_leaf4, m.n_leaves, st));
+    GNM_CU(rmi_pack_eps(c->d_rmi_elo, c->d_rmi_ehi, c->d_rmi_eps, m.n_models, st));
+    GNM_CU(rmi_pack_leaf4(m.a, m.b, m.x0, c->d_rmi_eps, c->d_rmi_leaf4, m.n_models, st));
     GNM_CU(cudaEventRecord(e1, st));
     GNM_CU(cudaEventSynchronize(e1));
     float ms = 0;
@@ -77,6 +96,9 @@ void gnm_rmi_config_default(gnm_rmi_config* cfg) {
     cfg->mlp_lr = 0.01f;
     cfg->seed = 1;
     cfg->exhaustive_eps = 1;
+    cfg->leaf_fit = GNM_RMI_FIT_MINIMAX;
+    cfg->eps_target = 64;
+    cfg->max_split_log2 = 14;
 }
 
 gnm_status gnm_rmi_train(gnm_ctx* c, const uint32_t* keys, uint64_t n, const gnm_rmi_config* cfg_in,
@@ -92,10 +114,12 @@ gnm_status gnm_rmi_train(gnm_ctx* c, const uint32_t* keys, uint64_t n, const gnm
         return fail(GNM_E_INVAL, "unknown root kind");
     if (cfg.root_kind == GNM_RMI_ROOT_MLP && cfg.hidden != 8 && cfg.hidden != 16 && cfg.hidden != 32)
         return fail(GNM_E_INVAL, "MLP root width must be 8, 16 or 32");
+    if (cfg.leaf_fit != GNM_RMI_FIT_MINIMAX && cfg.leaf_fit != GNM_RMI_FIT_MSE)
+        return fail(GNM_E_INVAL, "unknown leaf fit");
+    if (cfg.max_split_log2 > 16) return fail(GNM_E_INVAL, "max_split_log2 must be at most 16");
     if (c->h_starts.size() >= (1u << 24)) return fail(GNM_E_INVAL, "learned index needs fewer than 2^24 ranges");
     GNM_CU(cudaSetDevice(c->device));
     cudaStream_t st = (cudaStream_t)stream;
-    GNM_TRY(ensure_leaves(c, cfg.n_leaves));
     std::memset(rep, 0, sizeof(*rep));
     rep->n_train = n;
     uint32_t* pos = nullptr;
@@ -121,8 +145,7 @@ gnm_status gnm_rmi_train(gnm_ctx* c, const uint32_t* keys, uint64_t n, const gnm
         RmiDev m{};
         RmiTrainOut to{};
         if (e == cudaSuccess)
-            e = rmi_train_device(&m, c->d_rmi_a, c->d_rmi_b, c->d_rmi_x0, keys, pos, n,
-                                 (uint32_t)c->h_starts.size(), cfg, scratch, &to, st);
+            e = rmi_train_device(&m, keys, pos, n, c->d_starts, (uint32_t)c->h_starts.size(), cfg, scratch, &to, st);
         cudaEventRecord(e1, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) {
@@ -133,26 +156,40 @@ gnm_status gnm_rmi_train(gnm_ctx* c, const uint32_t* keys, uint64_t n, const gnm
         cudaEventElapsedTime(&ms, e0, e1);
         rep->train_ms = ms;
         rep->root_loss = to.root_loss;
-        rep->leaf_loss = to.leaf_loss;
         rep->empty_leaves = to.empty_leaves;
+        rep->split_leaves = to.split_leaves;
+        rep->n_models = (uint32_t)to.a.size();
         c->rmi_ready = false;
-        status = finish_model(c, m, cfg.exhaustive_eps != 0, keys, pos, n, st, &rep->sweep_ms);
+        status = upload_model(c, m, to, st);
+        if (status == GNM_OK) status = finish_model(c, m, cfg.exhaustive_eps != 0, keys, pos, n, st, &rep->sweep_ms);
         if (status != GNM_OK) break;
-        // report: widest window and the sample-weighted mean window
-        std::vector<uint32_t> lo(cfg.n_leaves), hi(cfg.n_leaves), leaf_of(0);
-        if (cudaMemcpy(lo.data(), c->d_rmi_elo, cfg.n_leaves * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(hi.data(), c->d_rmi_ehi, cfg.n_leaves * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        // report: widest window and error over the models, and over the training lookups the
+        // mean squared position error and the mean window searched
+        const uint32_t M = m.n_models;
+        std::vector<uint32_t> lo(M), hi(M);
+        if (cudaMemcpy(lo.data(), c->d_rmi_elo, (size_t)M * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(hi.data(), c->d_rmi_ehi, (size_t)M * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
             status = fail(GNM_E_CUDA, "error-bound readback failed");
             break;
         }
-        uint32_t mx = 0;
-        double sum = 0;
-        for (uint32_t l = 0; l < cfg.n_leaves; ++l) {
+        uint32_t mx = 0, mxe = 0;
+        for (uint32_t l = 0; l < M; ++l) {
             mx = std::max(mx, lo[l] + hi[l]);
-            sum += (double)lo[l] + hi[l] + 1;
+            mxe = std::max(mxe, std::max(lo[l], hi[l]));
         }
         rep->eps_max = mx;
-        rep->eps_mean = sum / cfg.n_leaves;
+        rep->err_max = mxe;
+        double* part = (double*)scratch;  // the training scratch is free again
+        double h2[2] = {0.0, 0.0};
+        e = rmi_model_stats(c->rmi, keys, pos, n, (uint32_t)c->h_starts.size(), part + 2, part, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h2, part, 16, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            status = fail(GNM_E_CUDA, std::string("learned-index report: ") + cudaGetErrorString(e));
+            break;
+        }
+        rep->leaf_loss = h2[0] / n;
+        rep->eps_mean = h2[1] / n;
     } while (false);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -177,10 +214,10 @@ gnm_status gnm_rmi_linear_grad(gnm_ctx* c, const float* z, const float* y, uint6
     if (!c || !z || !y || !grad || n == 0) return fail(GNM_E_INVAL, "bad argument");
     GNM_CU(cudaSetDevice(c->device));
     double* d = nullptr;
-    GNM_CU(cudaMalloc(&d, 3 * 8));
+    GNM_CU(cudaMalloc(&d, 3 * 8 + rmi_partials_bytes()));
     cudaStream_t st = (cudaStream_t)stream;
     double h[3];
-    cudaError_t e = rmi_linear_grad(z, y, n, w, cc, d, st);
+    cudaError_t e = rmi_linear_grad(z, y, n, w, cc, d + 3, d, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, 24, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(d);
@@ -200,14 +237,14 @@ gnm_status gnm_rmi_mlp_grad(gnm_ctx* c, const float* xn, const float* y, uint64_
     float* dp = nullptr;
     double* dg = nullptr;
     GNM_CU(cudaMalloc(&dp, cnt * 4));
-    if (cudaMalloc(&dg, (cnt + 1) * 8) != cudaSuccess) {
+    if (cudaMalloc(&dg, (cnt + 1) * 8 + rmi_partials_bytes()) != cudaSuccess) {
         cudaFree(dp);
         return fail(GNM_E_NOMEM, "allocation failed");
     }
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<double> h(cnt + 1);
     cudaError_t e = cudaMemcpyAsync(dp, params, cnt * 4, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = rmi_mlp_grad(xn, y, n, hidden, dp, dg, st);
+    if (e == cudaSuccess) e = rmi_mlp_grad(xn, y, n, hidden, dp, dg + (cnt + 1), dg, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), dg, (cnt + 1) * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(dp);
@@ -218,16 +255,17 @@ gnm_status gnm_rmi_mlp_grad(gnm_ctx* c, const float* xn, const float* y, uint64_
     return GNM_OK;
 }
 
-gnm_status gnm_rmi_export(gnm_ctx* c, int32_t* root_kind, uint32_t* n_leaves, float* root, float* a, float* b,
-                          uint32_t* x0, uint32_t* eps_lo, uint32_t* eps_hi) {
+gnm_status gnm_rmi_export(gnm_ctx* c, int32_t* root_kind, uint32_t* n_leaves, uint32_t* n_models, float* root,
+                          uint32_t* split, float* a, float* b, uint32_t* x0, uint32_t* eps_lo, uint32_t* eps_hi) {
     if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
     if (!c->rmi_ready) return fail(GNM_E_STATE, "no learned index");
     GNM_CU(cudaSetDevice(c->device));
     GNM_CU(cudaDeviceSynchronize());
     const RmiDev& m = c->rmi;
-    const uint32_t L = m.n_leaves;
+    const uint32_t L = m.n_leaves, M = m.n_models;
     if (root_kind) *root_kind = m.root_kind;
     if (n_leaves) *n_leaves = L;
+    if (n_models) *n_models = M;
     if (root) {
         root[0] = m.ra;
         root[1] = m.rb;
@@ -238,27 +276,54 @@ gnm_status gnm_rmi_export(gnm_ctx* c, int32_t* root_kind, uint32_t* n_leaves, fl
         }
         root[2 + 3 * kMaxHidden] = m.b2;
     }
-    if (a) GNM_CU(cudaMemcpy(a, c->d_rmi_a, (size_t)L * 4, cudaMemcpyDeviceToHost));
-    if (b) GNM_CU(cudaMemcpy(b, c->d_rmi_b, (size_t)L * 4, cudaMemcpyDeviceToHost));
-    if (x0) GNM_CU(cudaMemcpy(x0, c->d_rmi_x0, (size_t)L * 4, cudaMemcpyDeviceToHost));
-    if (eps_lo) GNM_CU(cudaMemcpy(eps_lo, c->d_rmi_elo, (size_t)L * 4, cudaMemcpyDeviceToHost));
-    if (eps_hi) GNM_CU(cudaMemcpy(eps_hi, c->d_rmi_ehi, (size_t)L * 4, cudaMemcpyDeviceToHost));
+    if (split)
+        for (uint32_t l = 0; l < L; ++l) split[l] = l < c->rmi_split.size() ? c->rmi_split[l] : 0u;
+    if (a) GNM_CU(cudaMemcpy(a, c->d_rmi_a, (size_t)M * 4, cudaMemcpyDeviceToHost));
+    if (b) GNM_CU(cudaMemcpy(b, c->d_rmi_b, (size_t)M * 4, cudaMemcpyDeviceToHost));
+    if (x0) GNM_CU(cudaMemcpy(x0, c->d_rmi_x0, (size_t)M * 4, cudaMemcpyDeviceToHost));
+    if (eps_lo) GNM_CU(cudaMemcpy(eps_lo, c->d_rmi_elo, (size_t)M * 4, cudaMemcpyDeviceToHost));
+    if (eps_hi) GNM_CU(cudaMemcpy(eps_hi, c->d_rmi_ehi, (size_t)M * 4, cudaMemcpyDeviceToHost));
+    // split leaves' entries hold their routing words on the device; the export shows zeros
+    for (uint32_t l = 0; l < L && l < c->rmi_split.size(); ++l)
+        if (c->rmi_split[l]) {
+            if (a) a[l] = 0.f;
+            if (b) b[l] = 0.f;
+            if (eps_lo) eps_lo[l] = 0u;
+            if (eps_hi) eps_hi[l] = 0u;
+        }
     return GNM_OK;
 }
 
-gnm_status gnm_rmi_import(gnm_ctx* c, int32_t root_kind, uint32_t L, const float* root, const float* a,
-                          const float* b, const uint32_t* x0, void* stream) {
+gnm_status gnm_rmi_import(gnm_ctx* c, int32_t root_kind, uint32_t L, uint32_t M, const float* root,
+                          const uint32_t* split, const float* a, const float* b, const uint32_t* x0, void* stream) {
     if (!c || !root || !a || !b || !x0) return fail(GNM_E_INVAL, "NULL argument");
     if (!c->have_registry) return fail(GNM_E_STATE, "no registry loaded");
     if (L == 0 || L > (uint32_t)kMaxLeaves) return fail(GNM_E_INVAL, "n_leaves must be 1..1048576");
+    if (M < L || M > kMaxModels) return fail(GNM_E_INVAL, "n_models must be n_leaves..4194304");
     if (root_kind != GNM_RMI_ROOT_LINEAR && root_kind != GNM_RMI_ROOT_MLP) return fail(GNM_E_INVAL, "unknown root kind");
     if (c->h_starts.size() >= (1u << 24)) return fail(GNM_E_INVAL, "learned index needs fewer than 2^24 ranges");
+    RmiTrainOut t;
+    t.a.assign(a, a + M);
+    t.b.assign(b, b + M);
+    t.x0.assign(x0, x0 + M);
+    t.eps.assign(M, 0u);
+    t.split.assign(L, 0u);
+    uint64_t nxt = L;
+    for (uint32_t l = 0; split && l < L; ++l) {
+        const uint32_t w = split[l];
+        if (!w) continue;
+        if ((w & 0xFFu) > 31u || (w >> 8) > 0xFFFFu) return fail(GNM_E_INVAL, "split word: shift > 31 or count > 65536");
+        const uint32_t base = (uint32_t)nxt;
+        nxt += (w >> 8) + 1u;
+        if (nxt > M) break;
+        std::memcpy(&t.a[l], &w, 4);
+        std::memcpy(&t.b[l], &base, 4);
+        t.eps[l] = kEpsSplit;
+        t.split[l] = w;
+    }
+    if (nxt != M) return fail(GNM_E_INVAL, "the split table does not add up to n_models");
     GNM_CU(cudaSetDevice(c->device));
-    GNM_TRY(ensure_leaves(c, L));
     cudaStream_t st = (cudaStream_t)stream;
-    GNM_CU(cudaMemcpyAsync(c->d_rmi_a, a, (size_t)L * 4, cudaMemcpyHostToDevice, st));
-    GNM_CU(cudaMemcpyAsync(c->d_rmi_b, b, (size_t)L * 4, cudaMemcpyHostToDevice, st));
-    GNM_CU(cudaMemcpyAsync(c->d_rmi_x0, x0, (size_t)L * 4, cudaMemcpyHostToDevice, st));
     RmiDev m{};
     m.root_kind = root_kind;
     m.n_leaves = L;
@@ -271,10 +336,8 @@ gnm_status gnm_rmi_import(gnm_ctx* c, int32_t root_kind, uint32_t L, const float
         m.w2[j] = root[2 + 2 * kMaxHidden + j];
     }
     m.b2 = root[2 + 3 * kMaxHidden];
-    m.a = c->d_rmi_a;
-    m.b = c->d_rmi_b;
-    m.x0 = c->d_rmi_x0;
     c->rmi_ready = false;
+    GNM_TRY(upload_model(c, m, t, st));
     return finish_model(c, m, true, nullptr, nullptr, 0, st, nullptr);
 }
 

@@ -25,6 +25,7 @@ ADMIN_OR, ADMIN_AND = 0, 1
 TABLE_AUTO, TABLE_DIRECT, TABLE_HASH, TABLE_GLOBAL, TABLE_PARTITION = 0, 1, 2, 3, 4
 SPLIT_AUTO, SPLIT_FUSED, SPLIT_TWO_KERNELS = 0, 1, 2
 ROOT_LINEAR, ROOT_MLP = 0, 1
+FIT_MINIMAX, FIT_MSE = 0, 1
 HOST_AUTO, HOST_STAGE, HOST_IN_PLACE = 0, 1, 2
 RATE_BUCKETS = 10001
 NO_MEDIAN = 0xFFFFFFFF
@@ -75,12 +76,14 @@ class RegistryInfo(C.Structure):
 class RmiConfig(C.Structure):
     _fields_ = [("root_kind", C.c_int32), ("n_leaves", C.c_uint32), ("hidden", C.c_uint32),
                 ("leaf_iters", C.c_uint32), ("mlp_steps", C.c_uint32), ("mlp_batch", C.c_uint32),
-                ("mlp_lr", C.c_float), ("seed", C.c_uint32), ("exhaustive_eps", C.c_int32)]
+                ("mlp_lr", C.c_float), ("seed", C.c_uint32), ("exhaustive_eps", C.c_int32),
+                ("leaf_fit", C.c_int32), ("eps_target", C.c_uint32), ("max_split_log2", C.c_uint32)]
 
 
 class RmiReport(C.Structure):
     _fields_ = [("n_train", C.c_uint64), ("root_loss", C.c_double), ("leaf_loss", C.c_double),
-                ("eps_max", C.c_uint32), ("eps_mean", C.c_double), ("empty_leaves", C.c_uint32),
+                ("eps_max", C.c_uint32), ("err_max", C.c_uint32), ("eps_mean", C.c_double),
+                ("empty_leaves", C.c_uint32), ("n_models", C.c_uint32), ("split_leaves", C.c_uint32),
                 ("train_ms", C.c_double), ("sweep_ms", C.c_double)]
 
 
@@ -155,8 +158,8 @@ def lib():
             "gnm_rmi_violations": (st, [P, C.POINTER(U64), C.c_int]),
             "gnm_rmi_linear_grad": (st, [P, P, P, U64, C.c_float, C.c_float, P, P]),
             "gnm_rmi_mlp_grad": (st, [P, P, P, U64, U32, P, P, P]),
-            "gnm_rmi_export": (st, [P, P, P, P, P, P, P, P, P]),
-            "gnm_rmi_import": (st, [P, C.c_int32, U32, P, P, P, P, P]),
+            "gnm_rmi_export": (st, [P, P, P, P, P, P, P, P, P, P, P]),
+            "gnm_rmi_import": (st, [P, C.c_int32, U32, U32, P, P, P, P, P, P]),
             "gnm_plan_create": (st, [P, C.POINTER(RecordsC), P, P, S, C.POINTER(P)]),
             "gnm_plan_launch": (st, [P, P]),
             "gnm_plan_create_ex": (st, [P, C.POINTER(RecordsC), P, P, S, U32, C.POINTER(P)]),
@@ -513,27 +516,35 @@ class Context:
         return g
 
     def rmi_export(self):
+        """The learned index: root parameters, per-leaf split words and per-model lines and
+        error bounds (models: the leaves, then the sub-leaves of split leaves)."""
         kind = C.c_int32()
         L = C.c_uint32()
-        lib().gnm_rmi_export(self.h, C.byref(kind), C.byref(L), None, None, None, None, None, None)
-        n = L.value
+        M = C.c_uint32()
+        self._c(lib().gnm_rmi_export(self.h, C.byref(kind), C.byref(L), C.byref(M), None, None, None, None, None,
+                                     None, None))
+        n, m = L.value, M.value
         root = np.zeros(2 + 3 * 32 + 1, np.float32)
-        a = np.zeros(n, np.float32)
-        b = np.zeros(n, np.float32)
-        x0 = np.zeros(n, np.uint32)
-        elo = np.zeros(n, np.uint32)
-        ehi = np.zeros(n, np.uint32)
-        self._c(lib().gnm_rmi_export(self.h, C.byref(kind), C.byref(L), _ptr(root), _ptr(a), _ptr(b), _ptr(x0),
-                                     _ptr(elo), _ptr(ehi)))
-        return dict(root_kind=kind.value, n_leaves=n, root=root, a=a, b=b, x0=x0, eps_lo=elo, eps_hi=ehi)
+        split = np.zeros(n, np.uint32)
+        a = np.zeros(m, np.float32)
+        b = np.zeros(m, np.float32)
+        x0 = np.zeros(m, np.uint32)
+        elo = np.zeros(m, np.uint32)
+        ehi = np.zeros(m, np.uint32)
+        self._c(lib().gnm_rmi_export(self.h, C.byref(kind), C.byref(L), C.byref(M), _ptr(root), _ptr(split), _ptr(a),
+                                     _ptr(b), _ptr(x0), _ptr(elo), _ptr(ehi)))
+        return dict(root_kind=kind.value, n_leaves=n, n_models=m, root=root, split=split, a=a, b=b, x0=x0,
+                    eps_lo=elo, eps_hi=ehi)
 
-    def rmi_import(self, root_kind: int, root, a, b, x0, stream=None):
+    def rmi_import(self, root_kind: int, root, a, b, x0, split=None, n_leaves=None, stream=None):
         r = np.ascontiguousarray(root, np.float32)
         a = np.ascontiguousarray(a, np.float32)
         b = np.ascontiguousarray(b, np.float32)
         x0 = np.ascontiguousarray(x0, np.uint32)
-        self._c(lib().gnm_rmi_import(self.h, root_kind, a.size, _ptr(r), _ptr(a), _ptr(b), _ptr(x0),
-                                     _stream_ptr(stream)))
+        sp = None if split is None else np.ascontiguousarray(split, np.uint32)
+        L = int(n_leaves) if n_leaves is not None else (sp.size if sp is not None else a.size)
+        self._c(lib().gnm_rmi_import(self.h, root_kind, L, a.size, _ptr(r), _ptr(sp),
+                                     _ptr(a), _ptr(b), _ptr(x0), _stream_ptr(stream)))
 
     # ---------------------------------------------------------- plans / tuning
     def plan(self, rec: Records, offsets, window_ids, kernel_times: bool = False) -> "Plan":

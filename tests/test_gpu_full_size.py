@@ -57,11 +57,11 @@ def test_learned_index_window_full_size(gnm):
     reg = fg.registry_c3()
     n = 50_000_000
     rec = fg.make_records(reg, n, seed=2, p_reg=0.9, zipf_s=0.9)
-    tr = fg.make_records(reg, 5_000_000, seed=12, p_reg=0.9, zipf_s=0.9)
-    keys = torch.from_numpy(np.concatenate([tr["srcaddr"], tr["dstaddr"]]).view(np.int32)).cuda()
+    keys = torch.from_numpy(fg.lookup_keys_c3(reg, 10_000_000).view(np.int32)).cuda()
     ctx = gnm.Context(window_slots=4, lookup_mode=gnm.LOOKUP_RMI)
     ctx.load(reg)
-    ctx.rmi_train(keys, root_kind=gnm.ROOT_LINEAR, n_leaves=65536, leaf_iters=4)
+    rep = ctx.rmi_train(keys, root_kind=gnm.ROOT_LINEAR, n_leaves=4096, leaf_iters=4)
+    assert rep.eps_max <= 64
     ctx.rmi_violations(reset=True)
     plan = ctx.plan(gnm.Records.to_device(rec), [0, n], [1])
     plan.launch()

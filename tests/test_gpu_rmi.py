@@ -84,6 +84,8 @@ def test_mlp_gradient_matches_fp64(gnm, H):
 
 @pytest.fixture(scope="module")
 def trained_linear(gnm, c3):
+    """The learned-index workload's model: linear root, 4,096 minimax leaves, leaves whose
+    window would exceed 64 split (the defaults)."""
     reg, lpm, starts, sites, rec, keys = c3
     ctx = gnm.Context(window_slots=4)
     ctx.load(reg)
@@ -91,23 +93,89 @@ def trained_linear(gnm, c3):
     return ctx, rep
 
 
+@pytest.fixture(scope="module")
+def trained_mse(gnm, c3):
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx = gnm.Context(window_slots=2)
+    ctx.load(reg)
+    rep = ctx.rmi_train(to_dev(keys), root_kind=gnm.ROOT_LINEAR, n_leaves=4096, leaf_iters=4,
+                        leaf_fit=gnm.FIT_MSE)
+    return ctx, rep
+
+
 def test_linear_rmi_bounds_equal_endpoint_analysis(gnm, c3, trained_linear):
+    """The exhaustive GPU sweep's per-model bounds equal the oracle's endpoint analysis of
+    the exported model (split leaves included), and meet the 4,096-leaf model's target:
+    window eps_lo + eps_hi <= 64, so every |predicted - true position| <= 64."""
     reg, lpm, starts, sites, rec, keys = c3
     ctx, rep = trained_linear
     m = ctx.rmi_export()
     assert m["root_kind"] == gnm.ROOT_LINEAR and m["n_leaves"] == 4096
-    elo, ehi = rmi_ref.eps_endpoints_linear(starts, float(m["root"][0]), float(m["root"][1]), m["a"], m["b"],
-                                            m["x0"], 4096)
+    assert m["n_models"] == rep.n_models == 4096 + int(sum((w >> 8) + 1 for w in m["split"] if w))
+    assert rep.split_leaves == int(np.count_nonzero(m["split"]))
+    elo, ehi = rmi_ref.eps_endpoints_models(starts, float(m["root"][0]), float(m["root"][1]), 4096, m["split"],
+                                            m["a"], m["b"], m["x0"])
     np.testing.assert_array_equal(m["eps_lo"], elo)
     np.testing.assert_array_equal(m["eps_hi"], ehi)
     assert rep.eps_max == int(np.max(elo + ehi))
-    print(f"\nlinear RMI: ranges {starts.size}, eps_max {rep.eps_max}, mean window {rep.eps_mean:.1f}, "
+    assert rep.err_max == int(np.max(np.maximum(elo, ehi)))
+    assert rep.eps_max <= 64 and rep.err_max <= 64
+    print(f"\nlinear RMI: ranges {starts.size}, models {rep.n_models} ({rep.split_leaves} split leaves), "
+          f"eps_max {rep.eps_max}, err_max {rep.err_max}, mean window {rep.eps_mean:.1f}, "
           f"train {rep.train_ms:.1f} ms, sweep {rep.sweep_ms:.1f} ms, empty leaves {rep.empty_leaves}")
 
 
-def test_linear_rmi_leaves_are_least_squares(gnm, c3, trained_linear):
+def test_minimax_leaves_near_optimal(gnm, c3, trained_linear):
+    """Every sampled model's proven error is within rounding of the FP64 optimum of the
+    oracle's minimax fit over the same address interval."""
     reg, lpm, starts, sites, rec, keys = c3
     ctx, _ = trained_linear
+    m = ctx.rmi_export()
+    first, mlo, mhi = rmi_ref.split_tables(float(m["root"][0]), float(m["root"][1]), 4096, m["split"])
+    models = [i for i in range(m["n_models"]) if not (i < 4096 and m["split"][i])]
+    rng = np.random.default_rng(3)
+    pick = sorted(set(rng.choice(models, size=150, replace=False).tolist()) |
+                  set(np.argsort(np.maximum(m["eps_lo"], m["eps_hi"]))[-20:].tolist()))
+    for i in pick:
+        if i < 4096 and m["split"][i]:
+            continue
+        np.testing.assert_equal(int(m["x0"][i]), int(min(mlo[i], (1 << 32) - 1)))
+        E = rmi_ref.fit_interval_minimax(starts, int(mlo[i]), int(mhi[i]))[2]
+        got = max(int(m["eps_lo"][i]), int(m["eps_hi"][i]))
+        assert got <= np.ceil(E + 0.5) + 2, f"model {i}: bound {got}, optimum {E:.2f}"
+
+
+def test_minimax_training_is_deterministic(gnm, c3):
+    """Two trainings on the same keys give the same model bit for bit (ordered reductions)."""
+    reg, lpm, starts, sites, rec, keys = c3
+    out = []
+    for _ in range(2):
+        ctx = gnm.Context(window_slots=1)
+        ctx.load(reg)
+        rep = ctx.rmi_train(to_dev(keys[:500_000]), n_leaves=2048)
+        out.append((ctx.rmi_export(), rep.eps_max, rep.leaf_loss))
+        ctx.close()
+    (m1, e1, l1), (m2, e2, l2) = out
+    assert e1 == e2 and l1 == l2
+    for k in ("root", "split", "a", "b", "x0", "eps_lo", "eps_hi"):
+        np.testing.assert_array_equal(m1[k].view(np.uint32), m2[k].view(np.uint32), err_msg=k)
+
+
+def test_minimax_beats_mse_on_the_bound(gnm, trained_linear, trained_mse):
+    """What the minimax fit gains over the mean-squared-error leaves on the same root: a far
+    smaller proven bound, and a smaller mean window over the training lookups."""
+    _, rep = trained_linear
+    _, mse = trained_mse
+    assert mse.n_models == 4096 and mse.split_leaves == 0
+    assert rep.eps_max < mse.eps_max / 2
+    assert rep.eps_mean < mse.eps_mean
+    print(f"\nminimax leaves: eps_max {rep.eps_max}, mean window {rep.eps_mean:.1f}; "
+          f"MSE leaves: eps_max {mse.eps_max}, mean window {mse.eps_mean:.1f}")
+
+
+def test_linear_rmi_leaves_are_least_squares(gnm, c3, trained_mse):
+    reg, lpm, starts, sites, rec, keys = c3
+    ctx, _ = trained_mse
     m = ctx.rmi_export()
     pos = np.searchsorted(starts, keys, side="right") - 1
     leaf = rmi_ref.root_linear(float(m["root"][0]), float(m["root"][1]), keys, 4096)
@@ -208,7 +276,7 @@ def test_rmi_sample_bounds_fall_back_exactly(gnm, c3):
     reg, lpm, starts, sites, rec, keys = c3
     ctx = gnm.Context(window_slots=2)
     ctx.load(reg)
-    ctx.rmi_train(to_dev(keys[:20000]), n_leaves=4096, exhaustive_eps=0)
+    ctx.rmi_train(to_dev(keys[:20000]), n_leaves=4096, exhaustive_eps=0, leaf_fit=gnm.FIT_MSE)
     ctx.rmi_violations(reset=True)
     x = probe_set(starts, seed=1)
     dx = to_dev(x)
@@ -229,7 +297,7 @@ def test_rmi_window_fallback_exact(gnm, c3, split, unroll):
     reg, lpm, starts, sites, rec, keys = c3
     ctx = gnm.Context(window_slots=2, split=getattr(gnm, split), unroll=unroll)
     ctx.load(reg)
-    ctx.rmi_train(to_dev(keys[:20000]), n_leaves=4096, exhaustive_eps=0)
+    ctx.rmi_train(to_dev(keys[:20000]), n_leaves=4096, exhaustive_eps=0, leaf_fit=gnm.FIT_MSE)
     assert ctx.registry_info().lookup_mode == gnm.LOOKUP_RMI
     ctx.rmi_violations(reset=True)
     rng = np.random.default_rng(4)
@@ -314,10 +382,16 @@ def test_rmi_export_import_roundtrip(gnm, c3, trained_linear):
     m = ctx.rmi_export()
     other = gnm.Context()
     other.load(reg)
-    other.rmi_import(m["root_kind"], m["root"], m["a"], m["b"], m["x0"])
+    assert np.count_nonzero(m["split"]) > 0
+    other.rmi_import(m["root_kind"], m["root"], m["a"], m["b"], m["x0"], split=m["split"])
     m2 = other.rmi_export()
-    for k in ("a", "b", "x0", "eps_lo", "eps_hi"):
+    for k in ("split", "a", "b", "x0", "eps_lo", "eps_hi"):
         np.testing.assert_array_equal(m[k], m2[k])
+    # a split table that does not add up to the model count is refused
+    bad = m["split"].copy()
+    bad[np.nonzero(bad)[0][0]] += 1 << 8
+    with pytest.raises(gnm.GnmError, match="add up"):
+        other.rmi_import(m["root_kind"], m["root"], m["a"], m["b"], m["x0"], split=bad)
     other.close()
 
 
