@@ -624,12 +624,14 @@ void gnm_stream_close(gnm_stream *s);
  * fixed 1 MiB array in the library's device image, which every GPU that loads the library
  * keeps until the process exits -- hence n_sites <= GNM_NOALLOC_MAX_SITES (GNM_E_INVAL with
  * a message beyond it). The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress); make the first call on each device before any stream capture.
+ * (cudaGetSymbolAddress), and so does the first call after the device's context changed
+ * (cudaDeviceReset, a new primary context); make those calls before any stream capture.
  * All calls on a device share the one array and clear it before use: calls that overlap
  * on the GPU (other streams, other host threads) race on it and must not be issued.
  * Arguments: cfg (host; NULL = defaults; filters and threshold_bps apply), starts/site
  * (device, n_ranges entries: the flattened registry, e.g. gnm_registry_flatten's output
- * copied to the device), n_sites, the local prefixes (host), rec (device records,
+ * copied to the device; a range whose site id is GNM_NO_SITE or at least n_sites counts as
+ * unregistered), n_sites, the local prefixes (host), rec (device records,
  * n < 2^32), and the device results stats[(2*n_sites+4) x GNM_NSTAT] (layout of
  * gnm_window_device), rate[2*n_sites], flag[2*n_sites]. Work is queued on `stream`; the
  * call does not synchronise the host. */

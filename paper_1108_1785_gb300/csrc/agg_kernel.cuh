@@ -444,7 +444,9 @@ __device__ __forceinline__ Item classify(const AggParams& p, bool valid, bool sl
     const uint32_t dir = sl ? 1u : 0u;  // outbound when the source is local
     const uint32_t dur = la - fi;       // modulo 2^32
     const bool mixed = sl != dl;        // exactly one endpoint local
-    const bool reg = site != kNoSite;
+    // registered: a site id below n_sites (kNoSite, and any id a caller's own registry
+    // arrays hold beyond n_sites, count as unregistered, so keys stay below 2*n_sites + 4)
+    const bool reg = site < p.n_sites;
     // unmatched classes: 0 neither local, 1 both local, 2 inbound unregistered, 3 outbound
     it.key = mixed ? (reg ? site * 2u + dir : nk + 2u + dir) : nk + dir;
     const bool ack_ok = (uint64_t)oc >= (uint64_t)p.min_avg * (uint64_t)pk;
@@ -1018,7 +1020,7 @@ __device__ __forceinline__ uint32_t record_key(const AggParams& p, bool sl, bool
     const uint32_t nk = 2u * p.n_sites;
     const uint32_t dir = sl ? 1u : 0u;  // outbound when the source is local
     const bool mixed = sl != dl;
-    return mixed ? (site != kNoSite ? site * 2u + dir : nk + 2u + dir) : nk + dir;
+    return mixed ? (site < p.n_sites ? site * 2u + dir : nk + 2u + dir) : nk + dir;
 }
 
 // A record whose key is already known (split launches: a lookup kernel wrote it).
@@ -1455,16 +1457,9 @@ __global__ void __launch_bounds__(keys_block_max(LOOKUP, U)) k_keys(const __grid
 template <int LOOKUP>
 cudaError_t launch_keys_impl(const AggParams& p, const LaunchShape& s, uint32_t* keys, cudaStream_t st) {
     auto k = s.keys_unroll == 2 ? k_keys<LOOKUP, 2> : k_keys<LOOKUP, 1>;
-    static int set_bytes[64][2];
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    static OptInCache granted[2];  // per unroll variant
+    cudaError_t e = ensure_smem_optin((const void*)k, (int)s.keys_smem, granted[s.keys_unroll == 2 ? 1 : 0]);
     if (e != cudaSuccess) return e;
-    const int ui = s.keys_unroll == 2 ? 1 : 0;
-    if (s.keys_smem >= 46 * 1024 && (dev >= 64 || set_bytes[dev][ui] < (int)s.keys_smem)) {
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.keys_smem);
-        if (e != cudaSuccess) return e;
-        if (dev < 64) set_bytes[dev][ui] = (int)s.keys_smem;
-    }
     (void)cudaGetLastError();
     k<<<s.keys_grid, s.keys_block, s.keys_smem, st>>>(p, keys);
     return cudaGetLastError();
@@ -1473,15 +1468,9 @@ cudaError_t launch_keys_impl(const AggParams& p, const LaunchShape& s, uint32_t*
 template <int LOOKUP, int TABLE, int AGG, int U>
 cudaError_t launch_variant(const AggParams& p, const LaunchShape& s, cudaStream_t st) {
     auto k = k_aggregate<LOOKUP, TABLE, AGG, U>;
-    static int set_bytes[64];  // opt-in already granted, per device (0 = none yet)
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    static OptInCache granted;
+    cudaError_t e = ensure_smem_optin((const void*)k, (int)s.smem, granted);
     if (e != cudaSuccess) return e;
-    if (s.smem >= 46 * 1024 && (dev >= 64 || set_bytes[dev] < (int)s.smem)) {
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
-        if (e != cudaSuccess) return e;
-        if (dev < 64) set_bytes[dev] = (int)s.smem;
-    }
     (void)cudaGetLastError();  // report this launch's error only
     k<<<s.grid, s.block, s.smem, st>>>(p);
     return cudaGetLastError();

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <vector>
 
 #include "gnm.h"
@@ -239,6 +240,22 @@ cudaError_t launch_flag_compact(const double* rate, const uint64_t* stats, uint3
                                 uint32_t* out_count, cudaStream_t st);
 cudaError_t launch_lookup(const AggParams& p, int lookup, const uint32_t* addr, uint64_t n,
                           uint32_t* site_out, uint32_t* pos_out, cudaStream_t st);
+
+// Unique id of the calling thread's current CUDA context (the driver's cuCtxGetId,
+// reached through the runtime's driver entry point, so the library does not link the
+// driver library itself); 0 when there is no current context or it cannot be read.
+unsigned long long current_context_id();
+
+// Per-device record of the dynamic shared memory a kernel has been granted, valid for one
+// context: a device reset or a new primary context starts again from nothing.
+struct OptInCache {
+    std::mutex mu;
+    unsigned long long ctx[64] = {};
+    int bytes[64] = {};
+};
+// Grants kernel `fn` `bytes` of dynamic shared memory (cudaFuncSetAttribute) unless the
+// current context already granted as much; thread-safe.
+cudaError_t ensure_smem_optin(const void* fn, int bytes, OptInCache& cache);
 
 // rmi.cu
 // A trained model on the host: the root (in RmiDev) and per model a, b, x0 and the initial

@@ -316,4 +316,50 @@ cudaError_t launch_lookup(const AggParams& p, int lookup, const uint32_t* addr, 
     return cudaGetLastError();
 }
 
+namespace {
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+std::once_flag g_ctx_once;
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+}  // namespace
+
+unsigned long long current_context_id() {
+    std::call_once(g_ctx_once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_id = reinterpret_cast<CtxGetIdFn>(f);
+        (void)cudaGetLastError();
+    });
+    if (!g_ctx_current || !g_ctx_id) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&ctx) != 0 || !ctx || g_ctx_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+cudaError_t ensure_smem_optin(const void* fn, int bytes, OptInCache& cache) {
+    if (bytes < 46 * 1024) return cudaSuccess;  // within the default 48 KB
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long ctx = current_context_id();
+    std::lock_guard<std::mutex> lock(cache.mu);
+    if (dev < 64 && ctx != 0 && cache.ctx[dev] == ctx && cache.bytes[dev] >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) {
+        if (cache.ctx[dev] != ctx) cache.bytes[dev] = 0;
+        cache.ctx[dev] = ctx;
+        cache.bytes[dev] = bytes > cache.bytes[dev] ? bytes : cache.bytes[dev];
+    }
+    return cudaSuccess;
+}
+
 }  // namespace gnm

@@ -32,19 +32,25 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {nullptr};
+unsigned long long g_ctx[kMaxDevices] = {0};
 
-// Device address of the scratch on the current device (looked up once per device).
+// Device address of the scratch on the current device: looked up once per device and
+// context (set-up), again only after the device's context changed (a cudaDeviceReset or a
+// new primary context reloads the library's device image).
 gnm_status scratch_address(int dev, unsigned char** out) {
     if (dev < 0 || dev >= kMaxDevices) return fail(GNM_E_INVAL, "device ordinal beyond the supported range");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_addr[dev] || ctx == 0 || ctx != g_ctx[dev]) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || p == nullptr) {
             (void)cudaGetLastError();
+            g_addr[dev] = nullptr;
             return fail(GNM_E_CUDA, std::string("cudaGetSymbolAddress of the scratch array: ") + cudaGetErrorString(e));
         }
         g_addr[dev] = p;
+        g_ctx[dev] = current_context_id();  // the lookup made the device's context current
     }
     *out = static_cast<unsigned char*>(g_addr[dev]);
     return GNM_OK;

@@ -303,16 +303,10 @@ cudaError_t launch_part_scan(const AggParams& p, const LaunchShape& s, uint64_t 
 cudaError_t launch_part_scatter(const AggParams& p, const LaunchShape& s, uint32_t* cnt, uint32_t* out,
                                 cudaStream_t st) {
     const uint64_t chunk = (p.n_total + s.part_grid - 1) / s.part_grid;
-    static int set_bytes[64];
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
+    static OptInCache granted;
     const int bytes = (int)((6 * kTile + 3 * s.part_groups) * 4);
-    if (bytes >= 46 * 1024 && (dev >= 64 || set_bytes[dev] < bytes)) {
-        e = cudaFuncSetAttribute(k_part_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e != cudaSuccess) return e;
-        if (dev < 64) set_bytes[dev] = bytes;
-    }
+    cudaError_t e = ensure_smem_optin((const void*)k_part_scatter, bytes, granted);
+    if (e != cudaSuccess) return e;
     (void)cudaGetLastError();
     k_part_scatter<<<s.part_grid, kPartThreads, (size_t)bytes, st>>>(p, chunk, s.part_rows, s.part_groups, cnt, out,
                                                                       part_array_stride(p.n_total));

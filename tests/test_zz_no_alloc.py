@@ -68,3 +68,27 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(gnm):
     with pytest.raises(gnm.GnmError, match="allocation-free limit"):
         gnm.window_process_noalloc(_dev_u32(starts), _dev_u32(sites), n_sites, reg.local_prefix, reg.local_len, rec,
                                    stats, rate, flag)
+
+
+def test_noalloc_site_ids_beyond_n_sites_count_as_unregistered(gnm):
+    """The caller's registry arrays may hold site ids at or above the n_sites it passes:
+    those ranges count as unregistered (unmatched classes 2 and 3), so no key reaches past
+    the 2*n_sites + 4 rows of the scratch or of `stats`. The 2,000 prefixes of this registry
+    do not overlap, so this equals the allocating entry point over the prefixes of the
+    first 250 sites only."""
+    import dataclasses
+    reg = fg.registry_c1()
+    starts, sites = gnm.registry_flatten(reg.prefix, reg.plen, reg.site, reg.n_sites)
+    keep = reg.site < 250
+    small = dataclasses.replace(reg, prefix=reg.prefix[keep], plen=reg.plen[keep], site=reg.site[keep], n_sites=250,
+                                nested=reg.nested[keep])
+    ctx = gnm.Context(window_slots=2)
+    ctx.load(small)
+    rec = fg.make_records(reg, 120_000, seed=43, zipf_s=1.1)
+    d = gnm.Records.to_device(rec)
+    got = _noalloc(gnm, small, _dev_u32(starts), _dev_u32(sites), d)
+    ctx.process(d, 1)
+    want = ctx.dense(1)
+    assert_window_matches(got, want)
+    assert int(want[1][2, 0] + want[1][3, 0]) > int(0.3 * rec["srcaddr"].size)  # many records left unmatched
+    ctx.close()
