@@ -190,6 +190,55 @@ def rate_stats(lpm: LPM, local_prefix, local_len, n_sites: int, rec: Dict[str, n
     return hist, rmin, rmax, med
 
 
+def rate_stats_keys(lpm: LPM, local_prefix, local_len, n_sites: int, rec: Dict[str, np.ndarray], keys,
+                    min_avg_pkt_bytes: int = 100, min_pkts: int = 10, min_dur_ms: int = 1000, admin_rule: int = 0):
+    """rate_stats for the given (site, dir) keys only, without a histogram for every key
+    (a registry of 100,000 sites would need 8 GB of them): the same definitions (Sec.
+    III.B.2.1), written out per record with numpy over this module's LPM. Per key, the
+    buckets and rates of its eligible flows; the lower median is the ceil(n/2)-th smallest
+    bucket. Returns (rmin, rmax, median_bucket, n_eligible) for `keys`, in their order."""
+    keys = np.asarray(keys, np.int64)
+    src = np.asarray(rec["srcaddr"], np.uint32)
+    dst = np.asarray(rec["dstaddr"], np.uint32)
+    pk = np.asarray(rec["dPkts"], np.uint64)
+    oc = np.asarray(rec["dOctets"], np.uint64)
+    dur = ((np.asarray(rec["last"], np.int64) - np.asarray(rec["first"], np.int64)) & 0xFFFFFFFF).astype(np.uint64)
+
+    def is_local(a):
+        r = np.zeros(a.shape, bool)
+        for p_, l_ in zip(np.asarray(local_prefix, np.int64), np.asarray(local_len, np.int64)):
+            r |= (a.astype(np.int64) >> (32 - l_)) == (p_ >> (32 - l_)) if l_ else True
+        return r
+
+    sl, dl = is_local(src), is_local(dst)
+    mixed = sl != dl                        # exactly one endpoint local
+    site = lpm.lookup(np.where(sl, dst, src)).astype(np.int64)
+    reg = mixed & (site != NO_SITE)
+    ack_ok = oc >= np.uint64(min_avg_pkt_bytes) * pk
+    many, longd = pk >= min_pkts, dur >= np.uint64(min_dur_ms)
+    admin_ok = (many & longd) if admin_rule == 0 else (many | longd)
+    elig = reg & (dur != 0) & ack_ok & admin_ok
+    key = np.where(elig, site * 2 + sl.astype(np.int64), -1)
+    want = np.isin(key, keys)
+    k_e, oc_e, dur_e = key[want], oc[want], dur[want]
+    bucket = np.minimum((oc_e * np.uint64(4)) // (dur_e * np.uint64(5)), np.uint64(10000)).astype(np.int64)
+    rate = (oc_e.astype(np.float64) * 8000.0) / dur_e.astype(np.float64)
+    order = np.argsort(k_e, kind="stable")
+    k_e, bucket, rate = k_e[order], bucket[order], rate[order]
+    rmin = np.full(keys.size, np.nan)
+    rmax = np.full(keys.size, np.nan)
+    med = np.full(keys.size, NO_MEDIAN, np.uint32)
+    cnt = np.zeros(keys.size, np.int64)
+    for i, k in enumerate(keys):
+        a, b = np.searchsorted(k_e, k, "left"), np.searchsorted(k_e, k, "right")
+        n = b - a
+        cnt[i] = n
+        if n:
+            rmin[i], rmax[i] = rate[a:b].min(), rate[a:b].max()
+            med[i] = np.sort(bucket[a:b])[(n + 1) // 2 - 1]
+    return rmin, rmax, med, cnt
+
+
 def host_stats(lpm: LPM, local_prefix, local_len, n_sites: int, rec: Dict[str, np.ndarray],
                min_avg_pkt_bytes: int = 100, min_pkts: int = 10, min_dur_ms: int = 1000, admin_rule: int = 0):
     """Per-host sums of a window (Sec. III.B.2.1: statistics "for each host in a registered

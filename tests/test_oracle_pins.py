@@ -703,3 +703,20 @@ def test_eps_endpoints_models_by_brute_force():
             continue
         E = rmi_ref.fit_interval_minimax(starts, int(mlo[m]), int(mhi[m]))[2]
         assert max(elo[m], ehi[m]) <= np.ceil(E + 0.5) + 1
+
+
+def test_rate_stats_keys_equals_dense_rate_stats():
+    """The per-key form of the rate statistics (for registries too large for a histogram
+    per key) equals the histogram form on windows of the three registries, for every key
+    with eligible flows and some without."""
+    for reg, n, seed in ((fg.registry_c1(), 60_000, 5), (fg.registry_c2(), 60_000, 6)):
+        rec = fg.make_records(reg, n, seed=seed)
+        lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+        h, lo, hi, med = oracle.rate_stats(lpm, reg.local_prefix, reg.local_len, reg.n_sites, rec)
+        keys = np.arange(2 * reg.n_sites)
+        rmin, rmax, m, cnt = oracle.rate_stats_keys(lpm, reg.local_prefix, reg.local_len, reg.n_sites, rec, keys)
+        np.testing.assert_array_equal(cnt, h.sum(axis=1))
+        np.testing.assert_array_equal(m, med)
+        np.testing.assert_array_equal(rmin, lo)
+        np.testing.assert_array_equal(rmax, hi)
+        assert (cnt > 0).sum() > 100 and (cnt == 0).sum() > 0
