@@ -674,7 +674,9 @@ def main():
 
     # algorithmic bytes: 24 B per record read, each window's per-key sums (48 B), rate
     # (8 B) and flag (1 B) written once, the registry read once -- split over the kernels
-    # as each one's compulsory reads and writes
+    # as the method's own compulsory reads and writes each one performs. The 4-byte key a
+    # split launch passes from its key kernel to its aggregation kernel is the design's own
+    # traffic, not the method's: it is not counted (it shows in traffic_ratio).
     nk = 2 * reg.n_sites
     out_bytes = n_win * (nk * (48 + 8 + 1) + 4 * 48)
     reg_bytes = int(info.n_ranges) * 8
@@ -682,8 +684,8 @@ def main():
     if names == ["k_aggregate"]:  # fused: the one kernel does it all
         kern_bytes = {"k_aggregate": alg_bytes}
     else:
-        kern_bytes = {"k_keys": 8 * n + 4 * n + reg_bytes,              # both addresses in, a key out
-                      "k_aggregate": 4 * n + 16 * n + (0 if "k_finalize_windows" in names else out_bytes),
+        kern_bytes = {"k_keys": 8 * n + reg_bytes,                       # the two addresses, the registry
+                      "k_aggregate": 16 * n + (0 if "k_finalize_windows" in names else out_bytes),
                       "k_finalize_windows": out_bytes}
     top = max(kern_avg, key=kern_avg.get)
     peak, peak_kind = hbm_peak()
@@ -718,6 +720,7 @@ def main():
                              "candidates": tune.n_tried}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                     "traffic_ratio": (traffic / kern_bytes[top]) if traffic else None,
                      "kernel": top, "kernel_ms": kern_avg[top], "algorithmic_bytes": kern_bytes[top],
                      "kernels_ms": kern_avg,
                      "kernel_timing": "CUDA events between the graph's kernels, K further launches",
@@ -729,28 +732,31 @@ def main():
 
     if not args.no_e2e:
         # end to end through the C ABI: page-locked host records (the kernels read them in
-        # place over the host link) -> D2H of every window's rates and flags
+        # place over the host link) -> D2H of every window's full result: the six u64 sums
+        # per (site, dir) key, the unmatched classes, the rates and the flags
         pinned = {k: torch.from_numpy(np.ascontiguousarray(rec[k]).view(np.int32)).pin_memory()
                   for k in gnm.FIELDS}
         hostrec = gnm.Records({k: v.numpy() for k, v in pinned.items()})
-        rate = np.empty(n_win * nk, np.float64)
-        flag = np.empty(n_win * nk, np.uint8)
+        stats = torch.empty(n_win * nk * 6, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+        unm = torch.empty(n_win * 12, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+        rate = torch.empty(n_win * nk, dtype=torch.float64).pin_memory().numpy()
+        flag = torch.empty(n_win * nk, dtype=torch.uint8).pin_memory().numpy()
         e2e_ids = ids + n_win
         for _ in range(max(1, args.warmup)):
             ctx.process_windows(hostrec, off, e2e_ids, stream)
-            ctx.windows_results(e2e_ids, rate=rate, flag=flag)
+            ctx.windows_results(e2e_ids, stats=stats, unmatched=unm, rate=rate, flag=flag)
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             ctx.process_windows(hostrec, off, e2e_ids, stream)
-            ctx.windows_results(e2e_ids, rate=rate, flag=flag)
+            ctx.windows_results(e2e_ids, stats=stats, unmatched=unm, rate=rate, flag=flag)
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0, world)
         out["e2e"] = {"value": n * world * args.steps / e2e_s, "unit": "records/s",
-                      "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": n_win * nk * 9,
+                      "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": n_win * (nk * (48 + 8 + 1) + 12 * 8),
                       "api": "gnm_windows_process over page-locked host records (read in place by the kernels "
-                             "over the host link) + gnm_windows_results"}
+                             "over the host link) + gnm_windows_results (sums, unmatched classes, rates, flags)"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1

@@ -128,9 +128,15 @@ typedef struct {
                                    otherwise); 2 = the range directory and a search over
                                    L2; 0 = 3, else 1, whichever fits first */
     int32_t host_records;       /* GNM_HOST_*: how kernels get host (on_device = 0) records */
-    int32_t rate_stats;         /* 1: per-flow rate statistics per window (gnm_window_rate_stats):
-                                   each result slot also holds a 10001-bucket histogram per key
-                                   (40 KB per key); 0: off */
+    int32_t rate_stats;         /* per-flow rate statistics per window (gnm_window_rate_stats):
+                                   1: each result slot also holds a 10001-bucket histogram per
+                                   key (40 KB per key); 2: each result slot logs one 32-bit
+                                   (key, bucket) word per eligible flow instead (4 bytes per
+                                   record of the window, grown as records arrive), sorted on
+                                   the GPU when first read (needs n_sites <= 131,072; a log
+                                   that grows synchronises the stream, so do not capture such
+                                   calls); both keep 16 bytes per key for the least and
+                                   greatest rate. 0: off */
     uint32_t host_capacity;     /* > 0: per-host sums per window (gnm_window_hosts) for up to
                                    this many (remote host, dir) pairs per window; each result
                                    slot holds a table of 2^ceil(log2(2 * capacity)) entries of
@@ -276,7 +282,7 @@ gnm_status gnm_flag_suboptimal(gnm_ctx *ctx, uint64_t window_id, double threshol
                                uint32_t *site_out, uint8_t *dir_out, size_t cap, size_t *n_out);
 
 /* Per-flow transfer-rate statistics of a finalised window (contexts created with
- * rate_stats = 1; GNM_E_STATE otherwise). Sec. III.B.2.1: the maximum, minimum and median
+ * rate_stats = 1 or 2; GNM_E_STATE otherwise). Sec. III.B.2.1: the maximum, minimum and median
  * of the rates of each (site, dir)'s flows, the median from a histogram of 10 kb/s buckets
  * whose last bucket holds every rate from 100 Mb/s up. Over the eligible flows of key
  * site*2+dir, with rate = (double)octets * 8000.0 / (double)duration_ms (one rounding per
@@ -285,12 +291,21 @@ gnm_status gnm_flag_suboptimal(gnm_ctx *ctx, uint64_t window_id, double threshol
  *   median_bucket[k]     bucket of the ceil(n/2)-th smallest of the key's n rates (the
  *                        lower median): its rate lies in [10 kb/s * b, 10 kb/s * (b+1));
  *                        GNM_NO_MEDIAN without eligible flows
- *   hist[k * 10001 + b]  flows of key k in bucket b
- * Arrays have 2*n_sites entries (hist 2*n_sites*10001); each may be NULL. */
+ *   hist[k * 10001 + b]  flows of key k in bucket b (rate_stats = 1 only; must be NULL
+ *                        with rate_stats = 2, GNM_E_INVAL otherwise)
+ * Arrays have 2*n_sites entries (hist 2*n_sites*10001); each may be NULL. The medians are
+ * the same in both modes. */
 #define GNM_RATE_BUCKETS 10001u
 #define GNM_NO_MEDIAN 0xFFFFFFFFu
 gnm_status gnm_window_rate_stats(gnm_ctx *ctx, uint64_t window_id, double *rmin, double *rmax,
                                  uint32_t *median_bucket, uint32_t *hist);
+
+/* The non-empty cells of a finalised window's rate histograms (rate_stats = 1 or 2), in
+ * (key, bucket) order: key[i] = site*2+dir, bucket[i] (as in gnm_window_rate_stats),
+ * count[i] > 0 flows. *n_out = number of cells; GNM_E_CAPACITY (with *n_out set) when cap
+ * is smaller. Host arrays, each may be NULL. */
+gnm_status gnm_window_rate_cells(gnm_ctx *ctx, uint64_t window_id, uint32_t *key, uint32_t *bucket,
+                                 uint32_t *count, size_t cap, size_t *n_out);
 
 /* Median-rate warnings across windows (Sec. III.B.1, Sec. IV.B: a warning for a site
  * whose median transfer rate stays below a standard, 1 Mb/s, for two consecutive periods).

@@ -11,6 +11,7 @@
 // window's ticket; the CTA that takes the last one finalises the window (rates and flags)
 // when its key space is small, else a grid-wide finalisation kernel follows.
 #pragma once
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -517,6 +518,9 @@ struct Smem {
     uint32_t* hist;     // rate statistics of the current window, offset by key_base (or null)
     unsigned long long* rmin;
     unsigned long long* rmax;
+    uint32_t* rlog;     // sparse rate statistics of the current window (or null): its log,
+    uint32_t* rlog_cnt; // the words appended so far
+    uint32_t rlog_cap;  // and the log's capacity in words
     uint32_t* t;        // table rows (kRowWords words each)
     uint32_t* tk;       // hash keys
     uint32_t rows;      // table rows
@@ -1046,7 +1050,18 @@ __device__ __forceinline__ Item classify_key(const AggParams& p, bool valid, uin
 // patterns order like the values; a read first skips the atomics that cannot change them.
 __device__ __forceinline__ void rate_stat_add(const Smem& sm, uint32_t key, uint32_t oc, uint32_t dur) {
     const uint64_t b = ((uint64_t)oc * 4u) / ((uint64_t)dur * 5u);
-    atomicAdd(sm.hist + (size_t)key * kRateBuckets + (b < 10000u ? b : 10000u), 1u);
+    const uint32_t bucket = b < 10000u ? (uint32_t)b : 10000u;
+    if (sm.rlog) {
+        // sparse: append (key << 14 | bucket) to the window's log, one counter atomic per
+        // group of lanes that arrive together (the host reserved a word per record)
+        const cooperative_groups::coalesced_group g = cooperative_groups::coalesced_threads();
+        uint32_t base = 0;
+        if (g.thread_rank() == 0) base = atomicAdd(sm.rlog_cnt, g.size());
+        base = g.shfl(base, 0) + g.thread_rank();
+        if (base < sm.rlog_cap) sm.rlog[base] = ((sm.key_base + key) << 14) | bucket;
+    } else {
+        atomicAdd(sm.hist + (size_t)key * kRateBuckets + bucket, 1u);
+    }
     const double r = __ddiv_rn(__dmul_rn(__uint2double_rn(oc), 8000.0), __uint2double_rn(dur));
     const unsigned long long bits = (unsigned long long)__double_as_longlong(r);
     if (bits > __ldcg(sm.rmax + key)) atomicMax(sm.rmax + key, bits);
@@ -1069,7 +1084,7 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
             for (int j = 0; j < R; ++j)
                 its[j] = classify_key(p, valid[j], src[j], sm.key_base, pk[j], oc[j], fi[j], la[j]);
             srow_add_all<R>(sm, its, gacc);
-            if (sm.hist) {
+            if (sm.hist || sm.rlog) {
 #pragma unroll
                 for (int j = 0; j < R; ++j)
                     if (its[j].valid && its[j].elig) rate_stat_add(sm, its[j].key, its[j].oc, its[j].dur);
@@ -1079,7 +1094,7 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
             for (int j = 0; j < R; ++j) {
                 const Item it = classify_key(p, valid[j], src[j], sm.key_base, pk[j], oc[j], fi[j], la[j]);
                 accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
-                if (sm.hist && it.valid && it.elig) rate_stat_add(sm, it.key, it.oc, it.dur);
+                if ((sm.hist || sm.rlog) && it.valid && it.elig) rate_stat_add(sm, it.key, it.oc, it.dur);
             }
         }
     } else {
@@ -1097,7 +1112,7 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
             for (int j = 0; j < R; ++j)
                 its[j] = classify(p, valid[j], sl[j], dl[j], pk[j], oc[j], fi[j], la[j], site[j]);
             srow_add_all<R>(sm, its, gacc);
-            if (sm.hist) {
+            if (sm.hist || sm.rlog) {
 #pragma unroll
                 for (int j = 0; j < R; ++j)
                     if (its[j].valid && its[j].elig) rate_stat_add(sm, its[j].key, its[j].oc, its[j].dur);
@@ -1107,7 +1122,7 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
             for (int j = 0; j < R; ++j) {
                 const Item it = classify(p, valid[j], sl[j], dl[j], pk[j], oc[j], fi[j], la[j], site[j]);
                 accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
-                if (sm.hist && it.valid && it.elig) rate_stat_add(sm, it.key, it.oc, it.dur);
+                if ((sm.hist || sm.rlog) && it.valid && it.elig) rate_stat_add(sm, it.key, it.oc, it.dur);
             }
         }
     }
@@ -1285,6 +1300,9 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
     sm.hist = nullptr;
     sm.rmin = nullptr;
     sm.rmax = nullptr;
+    sm.rlog = nullptr;
+    sm.rlog_cnt = nullptr;
+    sm.rlog_cap = 0u;
     sm.rows = TABLE == kTableDirect ? p.table_rows : (TABLE == kTableHash ? p.table_cap : 0u);
     sm.t = reinterpret_cast<uint32_t*>(smem_raw);
     sm.tk = reinterpret_cast<uint32_t*>(smem_raw + off_keys);
@@ -1306,6 +1324,13 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
         if (p.hist) {
             const size_t k0 = (size_t)wd.slot * 2u * p.n_sites + wd.key_base;
             sm.hist = p.hist + k0 * kRateBuckets;
+            sm.rmin = p.rmin + k0;
+            sm.rmax = p.rmax + k0;
+        } else if (p.rlog) {
+            const size_t k0 = (size_t)wd.slot * 2u * p.n_sites + wd.key_base;
+            sm.rlog = p.rlog[wd.slot];
+            sm.rlog_cnt = p.rlog_cnt + wd.slot;
+            sm.rlog_cap = p.rlog_cap[wd.slot];
             sm.rmin = p.rmin + k0;
             sm.rmax = p.rmax + k0;
         }
@@ -1374,6 +1399,9 @@ __global__ void __launch_bounds__(keys_block_max(LOOKUP, U)) k_keys(const __grid
     sm.hist = nullptr;
     sm.rmin = nullptr;
     sm.rmax = nullptr;
+    sm.rlog = nullptr;
+    sm.rlog_cnt = nullptr;
+    sm.rlog_cap = 0u;
     sm.t = nullptr;
     sm.tk = nullptr;
     sm.rows = 0;

@@ -131,6 +131,26 @@ void release_slots(gnm_ctx* c) {
     free_dev(c->d_mcnt);
     free_dev(c->d_warn_run);
     c->d_warn_run = nullptr;
+    for (auto* q : c->rlog) free_dev(q);
+    c->rlog.clear();
+    c->rlog_cap.clear();
+    c->rlog_sorted.clear();
+    if (c->h_rlog_ptr) cudaFreeHost(c->h_rlog_ptr);
+    if (c->h_rlog_cap) cudaFreeHost(c->h_rlog_cap);
+    c->h_rlog_ptr = nullptr;
+    c->h_rlog_cap = nullptr;
+    free_dev(c->d_rlog_ptr);
+    free_dev(c->d_rlog_cap);
+    free_dev(c->d_rlog_cnt);
+    free_dev(c->d_rlog_tmp);
+    free_dev(c->d_rs_hist);
+    c->d_rlog_ptr = nullptr;
+    c->d_rlog_cap = nullptr;
+    c->d_rlog_cnt = nullptr;
+    c->d_rlog_tmp = nullptr;
+    c->d_rs_hist = nullptr;
+    c->rlog_tmp_cap = 0;
+    c->rs_hist_cap = 0;
     free_dev(c->d_hkeys);
     free_dev(c->d_hrows);
     free_dev(c->d_hover);
@@ -526,6 +546,9 @@ gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p) {
     p->hist = c->d_hist;
     p->rmin = c->d_rmin;
     p->rmax = c->d_rmax;
+    p->rlog = c->d_hist ? nullptr : c->d_rlog_ptr;
+    p->rlog_cap = c->d_rlog_cap;
+    p->rlog_cnt = c->d_rlog_cnt;
     p->hkeys = c->d_hkeys;
     p->hrows = c->d_hrows;
     p->hover = c->d_hover;
@@ -633,14 +656,18 @@ PartLayout part_layout(uint64_t n, uint32_t nb) {
 }
 
 gnm_status clear_rate_stats(gnm_ctx* c, const uint32_t* slots, size_t n, cudaStream_t st) {
-    if (!c->d_hist && !c->d_hkeys) return GNM_OK;
+    if (!c->d_hist && !c->d_rlog_cnt && !c->d_hkeys) return GNM_OK;
     const size_t nk = (size_t)2 * c->n_sites, hc = c->hcap;
     for (size_t k = 0; k < n;) {  // runs of consecutive slots: one memset per array
         size_t m = 1;
         while (k + m < n && slots[k + m] == slots[k] + m) ++m;
         const size_t s0 = slots[k];
-        if (c->d_hist) {
-            GNM_CU(cudaMemsetAsync(c->d_hist + s0 * nk * kRateBuckets, 0, m * nk * kRateBuckets * 4, st));
+        if (c->d_hist) GNM_CU(cudaMemsetAsync(c->d_hist + s0 * nk * kRateBuckets, 0, m * nk * kRateBuckets * 4, st));
+        if (c->d_rlog_cnt) {
+            GNM_CU(cudaMemsetAsync(c->d_rlog_cnt + s0, 0, m * 4, st));
+            for (size_t j = s0; j < s0 + m; ++j) c->rlog_sorted[j] = 0;
+        }
+        if (c->d_hist || c->d_rlog_cnt) {
             GNM_CU(cudaMemsetAsync(c->d_rmax + s0 * nk, 0, m * nk * 8, st));
             GNM_CU(cudaMemsetAsync(c->d_rmin + s0 * nk, 0xFF, m * nk * 8, st));  // above every rate
         }
@@ -650,6 +677,43 @@ gnm_status clear_rate_stats(gnm_ctx* c, const uint32_t* slots, size_t n, cudaStr
             GNM_CU(cudaMemsetAsync(c->d_hover + s0, 0, m * 4, st));
         }
         k += m;
+    }
+    return GNM_OK;
+}
+
+gnm_status reserve_rate_log(gnm_ctx* c, const uint32_t* slots, const uint64_t* need, size_t n, cudaStream_t st) {
+    if (!c->d_rlog_cnt) return GNM_OK;
+    bool synced = false;
+    for (size_t k = 0; k < n; ++k) {
+        const uint32_t s = slots[k];
+        if (need[k] <= c->rlog_cap[s]) continue;
+        if (need[k] > 0xFFFFFFFFull) return fail(GNM_E_INVAL, "a window holds 2^32 records or more");
+        if (!synced) {  // nothing queued may still use a log that is replaced
+            GNM_CU(cudaStreamSynchronize(st));
+            synced = true;
+        }
+        const uint64_t cap = std::min<uint64_t>(0xFFFFFFFFull,
+                                                std::max<uint64_t>({need[k], 2 * c->rlog_cap[s], 1ull << 16}));
+        uint32_t* nb = nullptr;
+        if (cudaMalloc(&nb, cap * 4) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(GNM_E_NOMEM, "rate-statistics log allocation failed (" + std::to_string(cap * 4) + " bytes)");
+        }
+        if (c->rlog[s] && c->rlog_cap[s]) {  // an open window keeps the words logged so far
+            const cudaError_t e = cudaMemcpyAsync(nb, c->rlog[s], c->rlog_cap[s] * 4, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) {
+                cudaFree(nb);
+                GNM_CU(e);
+            }
+        }
+        c->h_rlog_ptr[s] = nb;
+        c->h_rlog_cap[s] = (uint32_t)cap;
+        GNM_CU(cudaMemcpyAsync(c->d_rlog_ptr + s, c->h_rlog_ptr + s, sizeof(uint32_t*), cudaMemcpyHostToDevice, st));
+        GNM_CU(cudaMemcpyAsync(c->d_rlog_cap + s, c->h_rlog_cap + s, 4, cudaMemcpyHostToDevice, st));
+        GNM_CU(cudaStreamSynchronize(st));
+        free_dev(c->rlog[s]);
+        c->rlog[s] = nb;
+        c->rlog_cap[s] = cap;
     }
     return GNM_OK;
 }
@@ -839,6 +903,12 @@ gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offse
     if (!pr.wins.empty()) {
         std::memcpy(lb->h_wins, pr.wins.data(), sizeof(WinDesc) * pr.wins.size());
         GNM_CU(cudaMemcpyAsync(lb->d_wins, lb->h_wins, sizeof(WinDesc) * pr.wins.size(), cudaMemcpyHostToDevice, st));
+    }
+    if (c->d_rlog_cnt) {  // sparse rate statistics: a log word per record of each window
+        std::vector<uint64_t> need(n_win);
+        for (size_t k = 0; k < n_win; ++k)
+            need[k] = (open_add ? c->slots[slot[k]].records : 0) + (offsets[k + 1] - offsets[k]);
+        GNM_TRY(reserve_rate_log(c, slot.data(), need.data(), n_win, st));
     }
     GNM_TRY(enqueue_prepared(c, pr, offsets, n_win, slot.data(), finalize, lb->d_wins, lb->d_done,
                              lb->d_partials, lb->d_keys, lb->d_part, st, &c->last_launches, nullptr, nullptr,
@@ -1168,9 +1238,26 @@ gnm_status gnm_registry_load(gnm_ctx* c, const uint32_t* prefix, const uint8_t* 
     GNM_CU(cudaMemset(c->d_acc, 0, slots * keys * kAccCols * 8));
     GNM_CU(cudaMalloc(&c->d_dirty, slots * ((keys + 31) / 32)));
     GNM_CU(cudaMemset(c->d_dirty, 0, slots * ((keys + 31) / 32)));
-    if (c->cfg.rate_stats) {  // per-flow rate statistics: a histogram per site key and slot
+    if (c->cfg.rate_stats < 0 || c->cfg.rate_stats > 2) return fail(GNM_E_INVAL, "rate_stats must be 0, 1 or 2");
+    if (c->cfg.rate_stats == 2 && (size_t)2 * n_sites > (1u << 18))
+        return fail(GNM_E_INVAL, "rate_stats = 2 needs at most 131,072 sites (keys of 18 bits)");
+    if (c->cfg.rate_stats) {  // per-flow rate statistics: per site key and slot
         const size_t nk = (size_t)2 * n_sites;
-        GNM_CU(cudaMalloc(&c->d_hist, slots * nk * kRateBuckets * 4));
+        if (c->cfg.rate_stats == 1) {  // a histogram of 10001 buckets
+            GNM_CU(cudaMalloc(&c->d_hist, slots * nk * kRateBuckets * 4));
+        } else {  // a log word per eligible flow, grown per slot as records arrive
+            c->rlog.assign(slots, nullptr);
+            c->rlog_cap.assign(slots, 0);
+            c->rlog_sorted.assign(slots, 0);
+            GNM_CU(cudaMallocHost(&c->h_rlog_ptr, slots * sizeof(uint32_t*)));
+            GNM_CU(cudaMallocHost(&c->h_rlog_cap, slots * 4));
+            GNM_CU(cudaMalloc(&c->d_rlog_ptr, slots * sizeof(uint32_t*)));
+            GNM_CU(cudaMalloc(&c->d_rlog_cap, slots * 4));
+            GNM_CU(cudaMalloc(&c->d_rlog_cnt, slots * 4));
+            GNM_CU(cudaMemset(c->d_rlog_ptr, 0, slots * sizeof(uint32_t*)));
+            GNM_CU(cudaMemset(c->d_rlog_cap, 0, slots * 4));
+            GNM_CU(cudaMemset(c->d_rlog_cnt, 0, slots * 4));
+        }
         GNM_CU(cudaMalloc(&c->d_rmin, slots * nk * 8));
         GNM_CU(cudaMalloc(&c->d_rmax, slots * nk * 8));
         GNM_CU(cudaMalloc(&c->d_med, nk * 4));
@@ -1267,18 +1354,120 @@ static gnm_status sync_slot(gnm_ctx* c, uint32_t s) {
     return GNM_OK;
 }
 
-gnm_status gnm_window_rate_stats(gnm_ctx* c, uint64_t wid, double* rmin, double* rmax, uint32_t* median_bucket,
-                                 uint32_t* hist) {
-    if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
-    if (!c->d_hist) return fail(GNM_E_STATE, "the context keeps no rate statistics (rate_stats = 0)");
+namespace {
+
+// Sparse rate statistics: sorts slot s's log once (in place) and returns its word count.
+gnm_status sorted_rate_log(gnm_ctx* c, uint32_t s, cudaStream_t st, uint32_t* n_out) {
+    uint32_t n = 0;
+    GNM_CU(cudaMemcpyAsync(&n, c->d_rlog_cnt + s, 4, cudaMemcpyDeviceToHost, st));
+    GNM_CU(cudaStreamSynchronize(st));
+    if (n > c->rlog_cap[s]) return fail(GNM_E_INTERNAL, "rate-statistics log overflow");
+    *n_out = n;
+    if (c->rlog_sorted[s] || n <= 1) {
+        c->rlog_sorted[s] = 1;
+        return GNM_OK;
+    }
+    const uint64_t hw = radix_sort_hist_words(n, c->sm_count);
+    if (n > c->rlog_tmp_cap) {
+        free_dev(c->d_rlog_tmp);
+        c->d_rlog_tmp = nullptr;
+        c->rlog_tmp_cap = 0;
+        GNM_CU(cudaMalloc(&c->d_rlog_tmp, (size_t)n * 4));
+        c->rlog_tmp_cap = n;
+    }
+    if (hw > c->rs_hist_cap) {
+        free_dev(c->d_rs_hist);
+        c->d_rs_hist = nullptr;
+        c->rs_hist_cap = 0;
+        GNM_CU(cudaMalloc(&c->d_rs_hist, hw * 4));
+        c->rs_hist_cap = hw;
+    }
+    // significant bits of the largest word, ((2S - 1) << 14) | 10000
+    const uint32_t top = ((2u * c->n_sites - 1u) << 14) | 10000u;
+    int bits = 0;
+    while (bits < 32 && (top >> bits)) ++bits;
+    uint32_t* res = nullptr;
+    GNM_CU(radix_sort_u32(c->rlog[s], c->d_rlog_tmp, n, bits, c->d_rs_hist, c->sm_count, st, &res));
+    if (res != c->rlog[s]) GNM_CU(cudaMemcpyAsync(c->rlog[s], res, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+    c->rlog_sorted[s] = 1;
+    return GNM_OK;
+}
+
+// Lower-median bucket and eligible flows of every site key of slot s into d_med / d_mcnt.
+gnm_status rate_medians(gnm_ctx* c, uint32_t s, cudaStream_t st) {
+    const uint32_t nk = 2u * c->n_sites;
+    if (c->d_hist) {
+        GNM_CU(launch_rate_median(c->d_hist + (size_t)s * nk * kRateBuckets, nk, c->d_med, c->d_mcnt, st));
+        return GNM_OK;
+    }
+    uint32_t n = 0;
+    GNM_TRY(sorted_rate_log(c, s, st, &n));
+    GNM_CU(launch_sparse_median(c->rlog[s], n, nk, c->d_med, c->d_mcnt, st));
+    return GNM_OK;
+}
+
+}  // namespace
+
+gnm_status gnm_window_rate_cells(gnm_ctx* c, uint64_t wid, uint32_t* key, uint32_t* bucket, uint32_t* count,
+                                 size_t cap, size_t* n_out) {
+    if (!c || !n_out) return fail(GNM_E_INVAL, "NULL argument");
+    if (!c->d_hist && !c->d_rlog_cnt) return fail(GNM_E_STATE, "the context keeps no rate statistics (rate_stats = 0)");
     GNM_CU(cudaSetDevice(c->device));
     uint32_t s;
     GNM_TRY(find_window(c, wid, &s));
     if (!c->slots[s].finalized) return fail(GNM_E_STATE, "window is open (not finalised)");
     GNM_TRY(wait_slot_on_stream(c, s, c->aux));
     const size_t nk = (size_t)2 * c->n_sites;
-    const uint32_t* h = c->d_hist + (size_t)s * nk * kRateBuckets;
-    GNM_CU(launch_rate_median(h, (uint32_t)nk, c->d_med, c->d_mcnt, c->aux));
+    std::vector<uint32_t> ck, cb, cc;
+    if (c->d_hist) {  // non-zero cells of the dense histograms
+        std::vector<uint32_t> h(nk * kRateBuckets);
+        GNM_CU(cudaMemcpyAsync(h.data(), c->d_hist + (size_t)s * nk * kRateBuckets, h.size() * 4,
+                               cudaMemcpyDeviceToHost, c->aux));
+        GNM_CU(cudaStreamSynchronize(c->aux));
+        for (size_t k = 0; k < nk; ++k)
+            for (uint32_t b = 0; b < kRateBuckets; ++b)
+                if (h[k * kRateBuckets + b]) {
+                    ck.push_back((uint32_t)k);
+                    cb.push_back(b);
+                    cc.push_back(h[k * kRateBuckets + b]);
+                }
+    } else {  // runs of the sorted log
+        uint32_t n = 0;
+        GNM_TRY(sorted_rate_log(c, s, c->aux, &n));
+        std::vector<uint32_t> w(n);
+        if (n) GNM_CU(cudaMemcpyAsync(w.data(), c->rlog[s], (size_t)n * 4, cudaMemcpyDeviceToHost, c->aux));
+        GNM_CU(cudaStreamSynchronize(c->aux));
+        for (uint32_t i = 0; i < n;) {
+            uint32_t j = i + 1;
+            while (j < n && w[j] == w[i]) ++j;
+            ck.push_back(w[i] >> 14);
+            cb.push_back(w[i] & 0x3FFFu);
+            cc.push_back(j - i);
+            i = j;
+        }
+    }
+    *n_out = ck.size();
+    if (cap < ck.size()) return fail(GNM_E_CAPACITY, "cap smaller than the number of non-empty cells");
+    if (key && !ck.empty()) std::memcpy(key, ck.data(), ck.size() * 4);
+    if (bucket && !cb.empty()) std::memcpy(bucket, cb.data(), cb.size() * 4);
+    if (count && !cc.empty()) std::memcpy(count, cc.data(), cc.size() * 4);
+    return GNM_OK;
+}
+
+gnm_status gnm_window_rate_stats(gnm_ctx* c, uint64_t wid, double* rmin, double* rmax, uint32_t* median_bucket,
+                                 uint32_t* hist) {
+    if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
+    if (!c->d_hist && !c->d_rlog_cnt) return fail(GNM_E_STATE, "the context keeps no rate statistics (rate_stats = 0)");
+    if (hist && !c->d_hist)
+        return fail(GNM_E_INVAL, "rate_stats = 2 keeps no dense histograms (gnm_window_rate_cells lists the cells)");
+    GNM_CU(cudaSetDevice(c->device));
+    uint32_t s;
+    GNM_TRY(find_window(c, wid, &s));
+    if (!c->slots[s].finalized) return fail(GNM_E_STATE, "window is open (not finalised)");
+    GNM_TRY(wait_slot_on_stream(c, s, c->aux));
+    const size_t nk = (size_t)2 * c->n_sites;
+    const uint32_t* h = c->d_hist ? c->d_hist + (size_t)s * nk * kRateBuckets : nullptr;
+    GNM_TRY(rate_medians(c, s, c->aux));
     std::vector<uint32_t> cnt(nk);
     std::vector<unsigned long long> lo(rmin ? nk : 0), hi(rmax ? nk : 0);
     GNM_CU(cudaMemcpyAsync(cnt.data(), c->d_mcnt, nk * 4, cudaMemcpyDeviceToHost, c->aux));
@@ -1356,7 +1545,7 @@ gnm_status gnm_window_hosts(gnm_ctx* c, uint64_t wid, gnm_host_stat* out, size_t
 gnm_status gnm_warnings_update(gnm_ctx* c, uint64_t wid, uint32_t below_bucket, uint32_t consecutive,
                                uint32_t* keys_out, size_t cap, size_t* n_out) {
     if (!c || !n_out) return fail(GNM_E_INVAL, "NULL argument");
-    if (!c->d_hist) return fail(GNM_E_STATE, "the context keeps no rate statistics (rate_stats = 0)");
+    if (!c->d_warn_run) return fail(GNM_E_STATE, "the context keeps no rate statistics (rate_stats = 0)");
     if (consecutive == 0) return fail(GNM_E_INVAL, "consecutive must be at least 1");
     GNM_CU(cudaSetDevice(c->device));
     uint32_t s;
@@ -1364,7 +1553,7 @@ gnm_status gnm_warnings_update(gnm_ctx* c, uint64_t wid, uint32_t below_bucket, 
     if (!c->slots[s].finalized) return fail(GNM_E_STATE, "window is open (not finalised)");
     GNM_TRY(wait_slot_on_stream(c, s, c->aux));
     const uint32_t nk = 2u * c->n_sites;
-    GNM_CU(launch_rate_median(c->d_hist + (size_t)s * nk * kRateBuckets, nk, c->d_med, c->d_mcnt, c->aux));
+    GNM_TRY(rate_medians(c, s, c->aux));
     GNM_CU(launch_warn_runs(c->d_med, nk, below_bucket, consecutive, c->d_warn_run, c->d_flag_keys, c->d_flag_count,
                             c->aux));
     uint32_t cnt = 0;
@@ -1448,13 +1637,16 @@ gnm_status gnm_windows_results(gnm_ctx* c, const uint64_t* wids, size_t n, uint6
         const uint32_t s = slot[k];
         if (rate) GNM_CU(cudaMemcpyAsync(rate + k * nk, c->d_rate + (size_t)s * nk, m * nk * 8, cudaMemcpyDeviceToHost, c->aux));
         if (flag) GNM_CU(cudaMemcpyAsync(flag + k * nk, c->d_flag + (size_t)s * nk, m * nk, cudaMemcpyDeviceToHost, c->aux));
-        for (size_t j = k; j < k + m; ++j) {
-            const uint64_t* st = c->d_stats + (size_t)slot[j] * c->keys * kNStat;
-            if (stats) GNM_CU(cudaMemcpyAsync(stats + j * nk * kNStat, st, nk * kNStat * 8, cudaMemcpyDeviceToHost, c->aux));
-            if (unmatched)
-                GNM_CU(cudaMemcpyAsync(un6.data() + j * kUnmatched * kNStat, st + nk * kNStat, kUnmatched * kNStat * 8,
-                                       cudaMemcpyDeviceToHost, c->aux));
-        }
+        // stats: the run's windows are rows of keys * GNM_NSTAT words, the site rows first
+        // and the unmatched rows after them: one pitched copy for each part
+        const uint64_t* st = c->d_stats + (size_t)s * c->keys * kNStat;
+        const size_t pitch = (size_t)c->keys * kNStat * 8;
+        if (stats)
+            GNM_CU(cudaMemcpy2DAsync(stats + k * nk * kNStat, nk * kNStat * 8, st, pitch, nk * kNStat * 8, m,
+                                     cudaMemcpyDeviceToHost, c->aux));
+        if (unmatched)
+            GNM_CU(cudaMemcpy2DAsync(un6.data() + k * kUnmatched * kNStat, kUnmatched * kNStat * 8, st + nk * kNStat,
+                                     pitch, kUnmatched * kNStat * 8, m, cudaMemcpyDeviceToHost, c->aux));
         k += m;
     }
     GNM_CU(cudaStreamSynchronize(c->aux));

@@ -120,6 +120,20 @@ struct gnm_ctx {
     uint32_t* d_med = nullptr;            // [2S] readout scratch: median buckets
     uint32_t* d_mcnt = nullptr;           // [2S] readout scratch: eligible flows
     uint32_t* d_warn_run = nullptr;       // [2S] windows in a row with a below-standard median
+    // sparse rate statistics (cfg.rate_stats == 2): per slot a log of (key << 14 | bucket)
+    // words of the eligible flows, sorted when the statistics are first read
+    std::vector<uint32_t*> rlog;          // [slots] device logs
+    std::vector<uint64_t> rlog_cap;       // [slots] capacity in words
+    std::vector<char> rlog_sorted;        // [slots] sorted since the window was cleared
+    uint32_t** h_rlog_ptr = nullptr;      // [slots] page-locked mirrors of the tables below
+    uint32_t* h_rlog_cap = nullptr;
+    uint32_t** d_rlog_ptr = nullptr;      // [slots] device copy of rlog
+    uint32_t* d_rlog_cap = nullptr;       // [slots] device copy of rlog_cap
+    uint32_t* d_rlog_cnt = nullptr;       // [slots] words appended
+    uint32_t* d_rlog_tmp = nullptr;       // sort scratch (words) and histograms
+    uint64_t rlog_tmp_cap = 0;
+    uint32_t* d_rs_hist = nullptr;
+    uint64_t rs_hist_cap = 0;
     unsigned long long* d_hkeys = nullptr; // per-host sums (cfg.host_capacity): [slots][hcap] keys
     unsigned long long* d_hrows = nullptr; // [slots][hcap][6] sums
     uint32_t* d_hover = nullptr;           // [slots] hosts lost to a full table
@@ -200,6 +214,9 @@ void unpin_slot(gnm_ctx* c, uint32_t s);
 gnm_status reserve_launch_scratch(gnm_ctx* c, uint64_t n);
 // Clears the rate statistics of slots[0..n) on st (windows that start there).
 gnm_status clear_rate_stats(gnm_ctx* c, const uint32_t* slots, size_t n, cudaStream_t st);
+// Sparse rate statistics: room for need[k] log words in slot slots[k] (keeping the words
+// already logged); synchronises `st` when a log grows, so call it outside stream capture.
+gnm_status reserve_rate_log(gnm_ctx* c, const uint32_t* slots, const uint64_t* need, size_t n, cudaStream_t st);
 // Windows k = [offsets[k], offsets[k+1]) of rec on stream st. finalize: rates and flags at
 // the end; open_add: add to windows already open instead of starting them.
 gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets, const uint64_t* wids,

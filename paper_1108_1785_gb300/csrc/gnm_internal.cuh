@@ -120,6 +120,11 @@ struct AggParams {
     uint32_t* hist;              // [slots][2*n_sites][kRateBuckets] rate histograms, or null
     unsigned long long* rmin;    // [slots][2*n_sites] least rate (bits of a double >= 0)
     unsigned long long* rmax;    // [slots][2*n_sites] greatest rate
+    // sparse rate statistics (hist == null): per slot a log of (key << 14 | bucket) words of
+    // the eligible flows, its capacity in words and the words appended so far (or null)
+    uint32_t* const* rlog;
+    const uint32_t* rlog_cap;
+    uint32_t* rlog_cnt;
     unsigned long long* hkeys;   // [slots][hcap] host table keys ((addr << 1 | dir) + 1; 0 empty), or null
     unsigned long long* hrows;   // [slots][hcap][kNStat] host sums
     uint32_t* hover;             // [slots] hosts that found no free entry
@@ -232,6 +237,14 @@ cudaError_t launch_warn_runs(const uint32_t* med, uint32_t n_keys, uint32_t belo
 cudaError_t launch_host_stats(const AggParams& p, const uint32_t* keys, int grid, cudaStream_t st);
 // FP64 rate of each of n host entries (rows of kNStat sums).
 cudaError_t launch_host_rates(const unsigned long long* rows, uint32_t n, double* rate, cudaStream_t st);
+// rsort.cu: LSD radix sort of n words (bits significant bits, 8 per pass) between keys and
+// tmp; *result is whichever holds the sorted words. hist needs radix_sort_hist_words(n).
+size_t radix_sort_hist_words(uint32_t n, int sms);
+cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* tmp, uint32_t n, int bits, uint32_t* hist, int sms,
+                           cudaStream_t st, uint32_t** result);
+// Lower-median bucket and eligible-flow count of every key from a sorted sparse log.
+cudaError_t launch_sparse_median(const uint32_t* sorted, uint32_t n, uint32_t n_keys, uint32_t* med, uint32_t* count,
+                                 cudaStream_t st);
 // Lower-median bucket and eligible-flow count of every site key of one slot's histograms.
 cudaError_t launch_rate_median(const uint32_t* hist, uint32_t n_keys, uint32_t* med, uint32_t* count,
                                cudaStream_t st);

@@ -96,6 +96,12 @@ gnm_status gnm_plan_create_ex(gnm_ctx* c, const gnm_records* rec, const uint64_t
         p->slots.push_back(s);
     }
     if (cudaStreamSynchronize(c->aux) != cudaSuccess) return bail(fail(GNM_E_CUDA, "slot preparation failed"));
+    {  // sparse rate statistics: each window's log holds a word per record of the window
+        std::vector<uint64_t> need(n_win);
+        for (size_t k = 0; k < n_win; ++k) need[k] = offsets[k + 1] - offsets[k];
+        const gnm_status st = reserve_rate_log(c, p->slots.data(), need.data(), n_win, c->aux);
+        if (st != GNM_OK) return bail(st);
+    }
     gnm_records dr = *rec;
     const uint64_t base = offsets[0];
     if (offsets[n_win] > base) {

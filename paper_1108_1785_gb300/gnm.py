@@ -168,6 +168,7 @@ def lib():
             "gnm_autotune": (st, [P, C.POINTER(RecordsC), P, P, S, C.POINTER(TuneReport)]),
             "gnm_last_launch_count": (U32, [P]),
             "gnm_window_rate_stats": (st, [P, U64, P, P, P, P]),
+            "gnm_window_rate_cells": (st, [P, U64, P, P, P, C.c_size_t, C.POINTER(C.c_size_t)]),
             "gnm_warnings_update": (st, [P, U64, U32, U32, P, S, C.POINTER(S)]),
             "gnm_warnings_reset": (st, [P]),
             "gnm_warnings_export": (st, [P, P]),
@@ -404,9 +405,23 @@ class Context:
         self._c(lib().gnm_windows_results(self.h, _ptr(ids), ids.size, _ptr(stats), _ptr(unmatched), _ptr(rate),
                                           _ptr(flag)))
 
+    def rate_cells(self, window_id: int):
+        """Non-empty cells of a finalised window's rate histograms: (key, bucket, count)
+        arrays in (key, bucket) order (rate_stats = 1 or 2)."""
+        n = C.c_size_t()
+        st = lib().gnm_window_rate_cells(self.h, window_id, None, None, None, 0, C.byref(n))
+        if st not in (0, 5):
+            self._c(st)
+        k = np.empty(n.value, np.uint32)
+        b = np.empty(n.value, np.uint32)
+        c = np.empty(n.value, np.uint32)
+        self._c(lib().gnm_window_rate_cells(self.h, window_id, _ptr(k), _ptr(b), _ptr(c), n.value, C.byref(n)))
+        return k, b, c
+
     def rate_stats(self, window_id: int, hist: bool = False):
         """(rmin[2S], rmax[2S], median_bucket[2S], hist[2S, 10001] or None) of a finalised
-        window of a context made with rate_stats=1."""
+        window of a context made with rate_stats=1 (dense histograms) or 2 (sparse: no
+        dense histogram, see rate_cells)."""
         nk = 2 * self.n_sites
         rmin = np.empty(nk, np.float64)
         rmax = np.empty(nk, np.float64)

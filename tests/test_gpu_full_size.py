@@ -2,8 +2,10 @@
 - 256 uneven windows, 84.5 M records, one autotuned CUDA-graph launch: sampled windows
   against the oracle one by one, and for every window the invariant that its sums over
   keys add up to its record count and octets;
-- one 50 M-record window on the learned-index registry with the 65,536-leaf model whose
-  leaves are read from global memory: the whole window against the oracle.
+- one 50 M-record window on the learned-index registry with the 4,096-leaf minimax model
+  (window <= 64 proven): the whole window against the oracle;
+- the same window with the sparse per-flow rate statistics: sampled keys' medians, least
+  and greatest rates against the oracle.
 Integers bit-exact, rates within 1e-12 (and bit-identical where compared directly)."""
 import numpy as np
 import pytest
@@ -73,5 +75,42 @@ def test_learned_index_window_full_size(gnm):
     ok = ~np.isnan(wr)
     np.testing.assert_array_equal(gr[ok].view(np.uint64), wr[ok].view(np.uint64))
     assert ctx.rmi_violations() == 0
+    plan.close()
+    ctx.close()
+
+
+def test_learned_index_window_sparse_rate_stats_full_size(gnm):
+    """Per-flow rate statistics on the 100,000-site registry (200,004 keys: dense histograms
+    would take 8 GB per window), one window of 50,000,000 records through the learned index
+    with the sparse log: medians, least and greatest rates equal the oracle's on 300 sampled
+    keys (the busiest, random ones and any without eligible flows), and the log's cells add
+    up to every key's eligible flows."""
+    reg = fg.registry_c3()
+    n = 50_000_000
+    rec = fg.make_records(reg, n, seed=2, p_reg=0.9, zipf_s=0.9)
+    keys = torch.from_numpy(fg.lookup_keys_c3(reg, 10_000_000).view(np.int32)).cuda()
+    ctx = gnm.Context(window_slots=2, lookup_mode=gnm.LOOKUP_RMI, rate_stats=2)
+    ctx.load(reg)
+    ctx.rmi_train(keys, root_kind=gnm.ROOT_LINEAR, n_leaves=4096, leaf_iters=4)
+    plan = ctx.plan(gnm.Records.to_device(rec), [0, n], [1])
+    plan.launch()
+    torch.cuda.synchronize()
+    rmin, rmax, med, _ = ctx.rate_stats(1)
+    st, _, _, _ = ctx.dense(1)
+    ck, cb, cc = ctx.rate_cells(1)
+    efl = np.bincount(ck, weights=cc, minlength=2 * reg.n_sites).astype(np.uint64)
+    np.testing.assert_array_equal(efl, st[:, 3])  # e_flows per key
+    rng = np.random.default_rng(9)
+    busy = np.argsort(st[:, 3])[-50:]
+    some = rng.choice(np.nonzero(st[:, 3])[0], 230, replace=False)
+    zero = np.nonzero(st[:, 3] == 0)[0]  # (at this size every key may have eligible flows)
+    empty = rng.choice(zero, min(20, zero.size), replace=False)
+    sample = np.unique(np.concatenate([busy, some, empty]))
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    lo, hi, m, cnt = oracle.rate_stats_keys(lpm, reg.local_prefix, reg.local_len, reg.n_sites, rec, sample)
+    np.testing.assert_array_equal(cnt, st[sample, 3])
+    np.testing.assert_array_equal(med[sample], m)
+    np.testing.assert_array_equal(rmin[sample], lo)
+    np.testing.assert_array_equal(rmax[sample], hi)
     plan.close()
     ctx.close()
