@@ -306,35 +306,45 @@ def batched_c4(gnm, torch, local, steps, warmup):
                       "placement": tune.placement, "ctas_per_sm": tune.ctas_per_sm}}
 
 
-def serve_c5(gnm, torch, local, minutes=120, speedup=600.0, pool_n=20_000_000, budget=4 << 30, check=2):
-    """Streaming replay: Poisson batch arrivals (1,000-500,000 records, 1e6 records/s on
-    average times the diurnal factor) over the learned-index 100,000-site registry, the
-    `minutes` around the daily peak replayed `speedup` times faster than real time. Host
-    batches (pinned) are cut at random offsets of a pool; one window per minute, closed at
-    the minute's end. Latency = window close -> rates and flags final on the device."""
+def serve_c5(gnm, torch, local, speedup=1000.0, realtime_minutes=10, pool_n=20_000_000, budget=4 << 30,
+             n_random=10, sat_minutes=120):
+    """Streaming replay of the 24-hour schedule: Poisson batch arrivals (1,000-500,000
+    records, 1e6 records/s on average times the diurnal factor) over the learned-index
+    100,000-site registry, one window per minute (1,440 windows), closed at the minute's
+    end. Host batches (pinned) are cut at random offsets of a pool. Reports:
+    - the whole day replayed `speedup` times faster than real time: p50/p99 window latency
+      over the 1,440 windows (window close -> rates and flags final on the device); every
+      60th window and `n_random` random ones are also processed alone from the same batches
+      and must be bit-identical to their results in the mix;
+    - the `sat_minutes` around the daily peak submitted as fast as possible;
+    - `realtime_minutes` around the peak at real time (x1)."""
     import flowgen as fg
     reg = fg.registry_c3()
     pool = fg.make_records(reg, pool_n, seed=4, p_reg=0.9, zipf_s=0.9)
     pinned = {k: torch.from_numpy(np.ascontiguousarray(pool[k]).view(np.int32)).pin_memory() for k in gnm.FIELDS}
     hpool = {k: v.numpy().view(np.uint32) for k, v in pinned.items()}
+    dpool = {k: v.cuda() for k, v in pinned.items()}
     t_all, sz_all = fg.serving_schedule_c5(hours=24.0)
-    t0 = 6 * 3600.0 - minutes * 30.0  # centred on the daily peak of f(t)
-    sel = (t_all >= t0) & (t_all < t0 + minutes * 60.0)
-    times, sizes = t_all[sel] - t0, sz_all[sel]
     rng = np.random.default_rng(5)
-    offs = rng.integers(0, pool_n - sizes + 1)
-    win_of = (times // 60.0).astype(np.int64)
+    off_all = rng.integers(0, pool_n - sz_all + 1)
+    day_min = 24 * 60
+    checked = sorted(set(range(0, day_min, 60)) | set(rng.choice(day_min, n_random, replace=False).tolist()))
     ctx = gnm.Context(device=local, window_slots=16)
     ctx.load(reg)
     keys = torch.from_numpy(fg.lookup_keys_c3(reg, 10_000_000).view(np.int32)).cuda()
     ctx.rmi_train(keys, root_kind=gnm.ROOT_LINEAR, n_leaves=4096, leaf_iters=4)
-    checked = sorted({0, int(rng.integers(1, minutes))})[:check]
     got = {}
-
     queued = []
 
-    def replay(srv, speedup, base):
-        """Submits the schedule (speedup None: as fast as possible); window w has id base + w."""
+    def part(t0, minutes):
+        sel = (t_all >= t0) & (t_all < t0 + minutes * 60.0)
+        tt = t_all[sel] - t0
+        return tt, sz_all[sel], off_all[sel], (tt // 60.0).astype(np.int64)
+
+    def replay(srv, speedup, base, sched, minutes, keep=()):
+        """Submits a schedule (speedup None: as fast as possible); window w has id base + w;
+        the results of the windows in `keep` are read when they are reported."""
+        times, sizes, offs, win_of = sched
         reports = []
         queued.clear()
 
@@ -342,7 +352,7 @@ def serve_c5(gnm, torch, local, minutes=120, speedup=600.0, pool_n=20_000_000, b
             for r in rs:
                 reports.append(r)
                 queued.append(r[4])
-                if r[0] - base in checked and speedup is not None:
+                if r[0] - base in keep:
                     got[r[0] - base] = ctx.dense(r[0])
         nb, bi, wc = len(times), 0, 0
         start = time.perf_counter()
@@ -363,7 +373,7 @@ def serve_c5(gnm, torch, local, minutes=120, speedup=600.0, pool_n=20_000_000, b
             take(srv.poll(wait_all=True, queued=True))
             return reports, time.perf_counter() - start
         while bi < nb or wc < minutes:
-            now = float("inf") if speedup is None else (time.perf_counter() - start) * speedup
+            now = (time.perf_counter() - start) * speedup
             ta = times[bi] if bi < nb else float("inf")
             tc = (wc + 1) * 60.0
             if min(ta, tc) <= now:
@@ -379,57 +389,76 @@ def serve_c5(gnm, torch, local, minutes=120, speedup=600.0, pool_n=20_000_000, b
         take(srv.poll(wait_all=True, queued=True))
         return reports, time.perf_counter() - start
 
+    def pct(v, q):
+        return float(np.percentile(v, q, method="inverted_cdf")) if len(v) else None
+
     pool_recs = gnm.Records(hpool)
+    day = part(0.0, day_min)
+    peak = part(6 * 3600.0 - sat_minutes * 30.0, sat_minutes)
+    rt = part(6 * 3600.0 - realtime_minutes * 30.0, realtime_minutes) if realtime_minutes else None
     with gnm.Stream(ctx, budget_bytes=budget, n_cuda_streams=4) as srv:
         # warm-up window (not reported): first use of the kernels and the arena
         srv.submit(gnm.Records({k: v[:100_000] for k, v in hpool.items()}), 1 << 40, close=True)
         srv.poll(wait_all=True)
         torch.cuda.synchronize()
-        reports, wall = replay(srv, speedup, 0)
+        reports, wall = replay(srv, speedup, 0, day, day_min, keep=set(checked))
         q_ms = list(queued)
         st = srv.stats()
-        sat_reports, sat_wall = replay(srv, None, 1 << 20)
+        sat_reports, sat_wall = replay(srv, None, 1 << 20, peak, sat_minutes)
         sat_st = srv.stats()
-    # the sampled windows processed alone (one call over all their records) must give the
-    # same results as in the mix
+        rt_reports, rt_wall = replay(srv, 1.0, 1 << 21, rt, realtime_minutes) if rt else ([], 0.0)
+    # the checked windows processed alone (open, the same batches from a device copy of the
+    # pool, close) must give the same results as in the mix
     ok = True
+    times, sizes, offs, win_of = day
     for w in checked:
-        idx = np.nonzero(win_of == w)[0]
-        rec = {k: np.concatenate([pool[k][offs[i]:offs[i] + sizes[i]] for i in idx]) for k in gnm.FIELDS}
-        ctx.process(gnm.Records.to_device(rec), (1 << 41) + w)
-        ast, aun, arate, afl = ctx.dense((1 << 41) + w)
+        wid = (1 << 41) + w
+        ctx.open(wid)
+        for i in np.nonzero(win_of == w)[0]:
+            a, n = int(offs[i]), int(sizes[i])
+            ctx.add(gnm.Records({k: v[a:a + n] for k, v in dpool.items()}), wid)
+        ctx.close_window(wid)
+        ast, aun, arate, afl = ctx.dense(wid)
         gst, gun, grate, gfl = got[w]
         ok = ok and (np.array_equal(gst, ast) and np.array_equal(gun, aun) and np.array_equal(gfl, afl)
                      and np.array_equal(grate, arate, equal_nan=True))
     ctx.close()
     lat = [r[2] for r in reports if r[3] == 0]
     n_rec = int(sizes.sum())
-    nb = len(times)
     sat_lat = [r[2] for r in sat_reports if r[3] == 0]
-    return {"workload": f"{minutes} one-minute windows around the daily peak, {nb:,} Poisson batches of "
-                        f"1,000-500,000 records ({n_rec:,} records), replayed x{speedup:g} faster than real "
-                        f"time; {reg.n_sites:,}-site learned-index registry; host batches from a pinned "
-                        f"{pool_n:,}-record pool",
-            "records_per_s": n_rec / wall, "offered_records_per_s": n_rec / (minutes * 60.0 / speedup),
-            "wall_s": wall, "windows": len(lat),
-            "p50_ms": float(np.percentile(lat, 50, method="inverted_cdf")) if lat else None,
-            "p99_ms": float(np.percentile(lat, 99, method="inverted_cdf")) if lat else None,
-            "max_ms": max(lat) if lat else None, "latency": "window close -> rates and flags final (host clock)",
-            "slowest_windows_ms": sorted(((r[2], r[0], r[4]) for r in reports if r[3] == 0), reverse=True)[:3],
-            "queued_p50_ms": float(np.percentile(q_ms, 50)) if q_ms else None,
-            "queued_p99_ms": float(np.percentile(q_ms, 99)) if q_ms else None,
-            "queued": "closing submit -> finalisation enqueued (host side of the latency)",
-            "budget_bytes": budget, "peak_inflight_bytes": int(st["peak_inflight_bytes"]),
-            "batches": int(st["batches"]), "batches_queued": int(st["batches_queued"]),
-            "checked_windows": checked, "mix_equals_alone": bool(ok),
-            "saturated": {"records_per_s": n_rec / sat_wall, "wall_s": sat_wall,
-                          "h2d_gbs": 24 * n_rec / sat_wall / 1e9,
-                          "p50_ms": float(np.percentile(sat_lat, 50, method="inverted_cdf")) if sat_lat else None,
-                          "p99_ms": float(np.percentile(sat_lat, 99, method="inverted_cdf")) if sat_lat else None,
-                          "peak_inflight_bytes": int(sat_st["peak_inflight_bytes"]),
-                          "batches_queued": int(sat_st["batches_queued"] - st["batches_queued"]),
-                          "note": "same schedule submitted as fast as possible (gnm_stream_submit_many, 512 "
-                                  "batches or closes per call); latency includes the queue behind the budget"}}
+    rt_lat = [r[2] for r in rt_reports if r[3] == 0]
+    n_sat = int(peak[1].sum())
+    out = {"workload": f"the 24-hour schedule: {day_min} one-minute windows, {len(times):,} Poisson batches of "
+                       f"1,000-500,000 records ({n_rec:,} records, 1e6 records/s x (1 + 0.7 sin(2 pi t / 1 day)) "
+                       f"on average), replayed x{speedup:g} faster than real time; {reg.n_sites:,}-site "
+                       f"learned-index registry (4,096 minimax leaves); host batches from a pinned "
+                       f"{pool_n:,}-record pool",
+           "records_per_s": n_rec / wall, "offered_records_per_s": n_rec / (day_min * 60.0 / speedup),
+           "wall_s": wall, "windows": len(lat),
+           "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "max_ms": max(lat) if lat else None,
+           "latency": "window close -> rates and flags final (host clock)",
+           "slowest_windows_ms": sorted(((r[2], r[0], r[4]) for r in reports if r[3] == 0), reverse=True)[:3],
+           "queued_p50_ms": pct(q_ms, 50), "queued_p99_ms": pct(q_ms, 99),
+           "queued": "closing submit -> finalisation enqueued (host side of the latency)",
+           "budget_bytes": budget, "peak_inflight_bytes": int(st["peak_inflight_bytes"]),
+           "batches": int(st["batches"]), "batches_queued": int(st["batches_queued"]),
+           "checked_windows": checked, "mix_equals_alone": bool(ok),
+           "check": "each checked window processed alone from the same batches, bit-identical to its result "
+                    "in the mix (the same windows are checked against the oracle by the full-size tests)",
+           "saturated": {"workload": f"the {sat_minutes} minutes around the daily peak ({n_sat:,} records)",
+                         "records_per_s": n_sat / sat_wall, "wall_s": sat_wall,
+                         "h2d_gbs": 24 * n_sat / sat_wall / 1e9,
+                         "p50_ms": pct(sat_lat, 50), "p99_ms": pct(sat_lat, 99),
+                         "peak_inflight_bytes": int(sat_st["peak_inflight_bytes"]),
+                         "batches_queued": int(sat_st["batches_queued"] - st["batches_queued"]),
+                         "note": "submitted as fast as possible (gnm_stream_submit_many, 512 batches or closes "
+                                 "per call); latency includes the queue behind the budget"}}
+    if rt:
+        out["realtime"] = {"workload": f"the {realtime_minutes} minutes around the daily peak at real time "
+                                       f"(x1, {int(rt[1].sum()):,} records in {len(rt[0]):,} batches)",
+                           "wall_s": rt_wall, "windows": len(rt_lat), "p50_ms": pct(rt_lat, 50),
+                           "p99_ms": pct(rt_lat, 99), "max_ms": max(rt_lat) if rt_lat else None}
+    return out
 
 
 class ClockSampler:
@@ -584,8 +613,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-window batched launch")
     ap.add_argument("--learned-records", type=int, default=50_000_000)
     ap.add_argument("--learned-modes", default="bsearch,radix,rmi,rmi_mse,rmi65536")
-    ap.add_argument("--serve-minutes", type=int, default=120)
-    ap.add_argument("--serve-speedup", type=float, default=600.0)
+    ap.add_argument("--serve-speedup", type=float, default=1000.0,
+                    help="time compression of the 24-hour serving replay")
+    ap.add_argument("--serve-realtime-minutes", type=int, default=10,
+                    help="minutes of the real-time (x1) serving slice (0: none)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -609,7 +640,7 @@ def main():
         elif args.only == "paper":
             leg = paper_lookup(gnm, torch, local, args.steps, args.warmup)
         else:
-            leg = serve_c5(gnm, torch, local, minutes=args.serve_minutes, speedup=args.serve_speedup)
+            leg = serve_c5(gnm, torch, local, speedup=args.serve_speedup, realtime_minutes=args.serve_realtime_minutes)
         print(json.dumps({"leg": args.only, **leg}), flush=True)
         return 0
     reg = fg.registry_c2()
@@ -780,7 +811,8 @@ def main():
         out["paper_lookup"] = paper_lookup(gnm, torch, local, args.steps, args.warmup)
         out["batched"] = batched_c4(gnm, torch, local, args.steps, args.warmup)
     if world == 1 and not args.no_serve:
-        out["serving"] = serve_c5(gnm, torch, local, minutes=args.serve_minutes, speedup=args.serve_speedup)
+        out["serving"] = serve_c5(gnm, torch, local, speedup=args.serve_speedup,
+                                  realtime_minutes=args.serve_realtime_minutes)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

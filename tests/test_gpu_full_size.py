@@ -5,7 +5,9 @@
 - one 50 M-record window on the learned-index registry with the 4,096-leaf minimax model
   (window <= 64 proven): the whole window against the oracle;
 - the same window with the sparse per-flow rate statistics: sampled keys' medians, least
-  and greatest rates against the oracle.
+  and greatest rates against the oracle;
+- the 24-hour serving schedule (1,440 windows) through the streaming server: every 60th
+  window and 10 random ones against the oracle.
 Integers bit-exact, rates within 1e-12 (and bit-identical where compared directly)."""
 import numpy as np
 import pytest
@@ -113,4 +115,58 @@ def test_learned_index_window_sparse_rate_stats_full_size(gnm):
     np.testing.assert_array_equal(rmin[sample], lo)
     np.testing.assert_array_equal(rmax[sample], hi)
     plan.close()
+    ctx.close()
+
+
+def test_served_day_checked_windows_full_size(gnm):
+    """The 24-hour serving schedule at full size (1,440 one-minute windows, 86.4e9 records in
+    Poisson batches of 1,000-500,000 records cut from a pinned 20,000,000-record pool) through
+    the streaming server with the 4,096-leaf learned index, submitted as fast as the 4 GB
+    budget admits: every 60th window and 10 random ones equal the oracle (sums, unmatched
+    classes and flags bit-exact, rates within 1e-12), and every window's record count is
+    the schedule's."""
+    reg = fg.registry_c3()
+    pool_n = 20_000_000
+    pool = fg.make_records(reg, pool_n, seed=4, p_reg=0.9, zipf_s=0.9)
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(pool[k]).view(np.int32)).pin_memory() for k in gnm.FIELDS}
+    hpool = {k: v.numpy().view(np.uint32) for k, v in pinned.items()}
+    t, sz = fg.serving_schedule_c5(hours=24.0)
+    rng = np.random.default_rng(5)
+    offs = rng.integers(0, pool_n - sz + 1)
+    win = (t // 60.0).astype(np.int64)
+    n_win = 24 * 60
+    checked = sorted(set(range(0, n_win, 60)) | set(rng.choice(n_win, 10, replace=False).tolist()))
+    assert len(checked) == 34
+    ctx = gnm.Context(window_slots=16)
+    ctx.load(reg)
+    ctx.rmi_train(torch.from_numpy(fg.lookup_keys_c3(reg, 10_000_000).view(np.int32)).cuda(), n_leaves=4096)
+    ev_b, ev_c, ev_w, ev_f = [], [], [], []
+    bi = 0
+    for w in range(n_win):  # batches of minute w, then its close
+        while bi < t.size and win[bi] == w:
+            ev_b.append(int(offs[bi])), ev_c.append(int(sz[bi])), ev_w.append(w), ev_f.append(0)
+            bi += 1
+        ev_b.append(0), ev_c.append(0), ev_w.append(w), ev_f.append(1)
+    got, records = {}, {}
+
+    def take(reports):
+        for r in reports:
+            assert r[3] == 0
+            records[r[0]] = r[1]
+            if r[0] in checked:
+                got[r[0]] = ctx.dense(r[0])
+
+    with gnm.Stream(ctx, budget_bytes=4 << 30, n_cuda_streams=4) as srv:
+        pool_recs = gnm.Records(hpool)
+        for k in range(0, len(ev_b), 512):
+            srv.submit_many(pool_recs, ev_b[k:k + 512], ev_c[k:k + 512], ev_w[k:k + 512], ev_f[k:k + 512])
+            take(srv.poll())
+        take(srv.poll(wait_all=True))
+    assert sorted(records) == list(range(n_win))
+    np.testing.assert_array_equal([records[w] for w in range(n_win)], np.bincount(win, weights=sz, minlength=n_win))
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    for w in checked:
+        idx = np.nonzero(win == w)[0]
+        rec = {k: np.concatenate([pool[k][offs[i]:offs[i] + sz[i]] for i in idx]) for k in gnm.FIELDS}
+        assert_window_matches(got[w], oracle_full(reg, rec, lpm=lpm, n_threads=16))
     ctx.close()
