@@ -627,6 +627,32 @@ void gnm_stream_close(gnm_stream *s);
 
 /* ------------------------------------------------------------ without allocation */
 
+/* ------------------------------------------------------------- checked build */
+
+/* The library is also built with device-side bounds checks (libgnm_checked.so, same ABI;
+ * not in the paper). Its kernels test every index where they trust data -- a record's key
+ * before the table, accumulator and histogram accesses it drives; a registry search's
+ * starting window before its loads; a learned-index model number; a regrouping bucket
+ * and position; a partial-sum block -- and on a failure skip the access and record the
+ * first failure in the context's error word. Readouts (gnm_window_dense,
+ * gnm_windows_results, gnm_site_stats, gnm_flag_suboptimal) then return GNM_E_INTERNAL
+ * naming the check. The default build has no checks and never reports through this word. */
+
+/* 1 in the checked build, 0 in the default one. */
+int gnm_checked_build(void);
+
+/* Synchronises the device, returns the context's error word in *word (may be NULL; top
+ * byte = check, low 56 bits = the offending value; 0 = no failure), clears it, and returns
+ * GNM_E_INTERNAL when it was set (always GNM_OK in the default build). */
+gnm_status gnm_device_checks(gnm_ctx *ctx, uint64_t *word);
+
+/* Checked build only (GNM_E_STATE in the default build): overwrites one value of the
+ * context's device state from the host, so tests can show that a corrupt index is caught
+ * without any access out of bounds. GNM_DEBUG_RMI_SPLIT_BASE: the first-sub-leaf number of
+ * split leaf `index` of the learned index becomes `value`. */
+enum { GNM_DEBUG_RMI_SPLIT_BASE = 1 };
+gnm_status gnm_debug_corrupt(gnm_ctx *ctx, int32_t what, uint32_t index, uint32_t value);
+
 /* Largest n_sites gnm_window_process_noalloc accepts (its fixed scratch is 1 MiB). */
 #define GNM_NOALLOC_MAX_SITES 13102u
 

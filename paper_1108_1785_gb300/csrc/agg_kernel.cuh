@@ -78,7 +78,7 @@ __device__ __forceinline__ uint32_t pred_search1(const uint32_t* __restrict__ s,
 template <int R, bool kShared = false>
 __device__ __forceinline__ void radix_search(const uint32_t* __restrict__ dir, uint32_t bits,
                                              const uint32_t* __restrict__ starts, const uint32_t (&x)[R],
-                                             uint32_t (&base)[R]) {
+                                             uint32_t (&base)[R], uint32_t n, unsigned long long* err) {
     uint32_t len[R];
     bool more = false;
 #pragma unroll
@@ -86,6 +86,10 @@ __device__ __forceinline__ void radix_search(const uint32_t* __restrict__ dir, u
         const uint32_t t = bits ? x[j] >> (32u - bits) : 0u;
         base[j] = dir[t];
         len[j] = dir[t + 1] - base[j] + 1u;
+        if (!chk(err, (uint64_t)base[j] + len[j] <= n, kChkWindow, base[j])) {
+            base[j] = 0u;
+            len[j] = 1u;
+        }
         more |= len[j] > 1u;
     }
     while (more) {
@@ -141,7 +145,8 @@ __device__ __forceinline__ void pair_search(const uint2* __restrict__ pairs, con
 template <int BR, int R>
 __device__ __forceinline__ void radix_block(const uint32_t* dir, uint32_t bits, const uint32_t* smp,
                                             const uint2* __restrict__ pairs, const uint32_t (&x)[R],
-                                            uint32_t (&site)[R], bool packed) {
+                                            uint32_t (&site)[R], bool packed, uint32_t n_blk,
+                                            unsigned long long* err) {
     static_assert(BR == 2 || BR == 4, "blocks of 2 or 4 ranges");
     uint32_t g[R], len[R];
     bool more = false;
@@ -155,6 +160,10 @@ __device__ __forceinline__ void radix_block(const uint32_t* dir, uint32_t bits, 
         } else {
             g[j] = dir[t];
             len[j] = dir[t + 1] - g[j] + 1u;
+        }
+        if (!chk(err, (uint64_t)g[j] + len[j] <= n_blk, kChkBlocks, g[j])) {
+            g[j] = 0u;
+            len[j] = 1u;
         }
         more |= len[j] > 1u;
     }
@@ -203,7 +212,7 @@ __device__ __forceinline__ void radix_block(const uint32_t* dir, uint32_t bits, 
 template <int R>
 __device__ __forceinline__ void radix_block16(const uint16_t* dh, const uint16_t* s16,
                                               const uint2* __restrict__ pairs, const uint32_t (&x)[R],
-                                              uint32_t (&site)[R]) {
+                                              uint32_t (&site)[R], uint32_t n_blk, unsigned long long* err) {
     uint32_t l[R], n[R];
     bool more = false;
 #pragma unroll
@@ -211,6 +220,10 @@ __device__ __forceinline__ void radix_block16(const uint16_t* dh, const uint16_t
         const uint32_t t = x[j] >> 16;
         l[j] = dh[t];
         n[j] = (uint32_t)dh[t + 1] - l[j];
+        if (!chk(err, (uint64_t)l[j] + n[j] <= n_blk && dh[t + 1] >= l[j], kChkBlocks, l[j])) {
+            l[j] = 1u;
+            n[j] = 0u;
+        }
         more |= n[j] > 0u;
     }
     while (more) {  // l: first candidate whose low bits exceed x's, within [l, l + n)
@@ -231,8 +244,10 @@ __device__ __forceinline__ void radix_block16(const uint16_t* dh, const uint16_t
     }
     uint4 v[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j)  // l >= 1: block 0 starts at address 0, inside bucket 0
+    for (int j = 0; j < R; ++j) {  // l >= 1: block 0 starts at address 0, inside bucket 0
+        if (!chk(err, l[j] >= 1u, kChkBlocks, l[j])) l[j] = 1u;
         v[j] = __ldg(reinterpret_cast<const uint4*>(pairs) + (l[j] - 1u));
+    }
 #pragma unroll
     for (int j = 0; j < R; ++j) site[j] = v[j].z <= x[j] ? v[j].w : v[j].y;
 }
@@ -348,7 +363,11 @@ __device__ __forceinline__ uint32_t rmi_sub_model(const RmiLeaf& f, uint32_t x) 
 __device__ __forceinline__ RmiLeaf rmi_model(const RmiDev& m, const float* a, const float* b, const uint32_t* x0,
                                              const uint32_t* eps, uint32_t x) {
     RmiLeaf f = rmi_leaf(m, a, b, x0, eps, rmi_root(m, x));
-    if (f.eps == kEpsSplit) f = rmi_leaf(m, a, b, x0, eps, rmi_sub_model(f, x));
+    if (f.eps == kEpsSplit) {
+        const uint32_t sub = rmi_sub_model(f, x);
+        if (chk(m.check_err, sub < m.n_models, kChkModel, sub)) f = rmi_leaf(m, a, b, x0, eps, sub);
+        else f.eps = 0xFFFFFFFFu;  // (checked build) no model: the full search
+    }
     return f;
 }
 
@@ -818,6 +837,7 @@ __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot,
             const uint2 pd = p.part_desc[(size_t)win * p.part_groups + g];
             kp = p.partials + (size_t)pd.x * pstride + (k - g * rows);
             np = p.partials ? pd.y : 0u;
+            if (np && !chk(p.check_err, ((uint64_t)pd.x + np) * pstride <= p.partial_cap, kChkPartial, pd.x)) np = 0u;
         }
         if (!act) np = 0;
         uint32_t v[4][kRowWords];
@@ -956,6 +976,10 @@ __device__ __forceinline__ void lookup_sites(const AggParams& p, const Smem& sm,
                     idx[j] = sm.s_dir[t];
                     len[j] = sm.s_dir[t + 1] - idx[j] + 1u;
                 }
+                if (!chk(p.check_err, (uint64_t)idx[j] + len[j] <= p.n_ranges, kChkWindow, idx[j])) {
+                    idx[j] = 0u;
+                    len[j] = 1u;
+                }
             }
 #pragma unroll 1
             for (uint32_t it = 0; it < p.dir_iters; ++it) {
@@ -995,6 +1019,10 @@ __device__ __forceinline__ void lookup_sites(const AggParams& p, const Smem& sm,
             const uint32_t t = p.radix_bits ? x[j] >> (32u - p.radix_bits) : 0u;
             idx[j] = sm.s_starts[t];
             len[j] = sm.s_starts[t + 1] - idx[j] + 1u;
+            if (!chk(p.check_err, (uint64_t)idx[j] + len[j] <= p.n_ranges, kChkWindow, idx[j])) {
+                idx[j] = 0u;
+                len[j] = 1u;
+            }
             site[j] = __ldg(p.pairs + idx[j]).y;
         }
         pair_search<R>(p.pairs, x, idx, len, site);
@@ -1005,11 +1033,13 @@ __device__ __forceinline__ void lookup_sites(const AggParams& p, const Smem& sm,
 #pragma unroll
         for (int j = 0; j < R; ++j) site[j] = __ldg(p.rsite + idx[j]);
     } else if (LOOKUP == kLookupRadixBlk) {
-        radix_block<4, R>(sm.s_starts, p.radix_bits, sm.s_site, p.pairs, x, site, p.n_blk4 < 65536u);
+        radix_block<4, R>(sm.s_starts, p.radix_bits, sm.s_site, p.pairs, x, site, p.n_blk4 < 65536u, p.n_blk4,
+                          p.check_err);
     } else if (LOOKUP == kLookupRadixBlk2) {
-        radix_block<2, R>(sm.s_starts, p.radix_bits, sm.s_site, p.pairs, x, site, p.n_blk2 < 65536u);
+        radix_block<2, R>(sm.s_starts, p.radix_bits, sm.s_site, p.pairs, x, site, p.n_blk2 < 65536u, p.n_blk2,
+                          p.check_err);
     } else if (LOOKUP == kLookupRadixBlk2H) {
-        radix_block16<R>(sm.dh, sm.s16, p.pairs, x, site);
+        radix_block16<R>(sm.dh, sm.s16, p.pairs, x, site, p.n_blk2, p.check_err);
     } else if (LOOKUP == kLookupRmi) {
         rmi_sites<R>(p.rmi, sm.ra, sm.rb, sm.rx0, sm.reps, p.pairs, p.n_ranges, valid, x, site, p.violations);
     } else if (LOOKUP == kLookupHash24) {
@@ -1077,12 +1107,16 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
                                         const uint32_t (&dst)[R], const uint32_t (&pk)[R],
                                         const uint32_t (&oc)[R], const uint32_t (&fi)[R],
                                         const uint32_t (&la)[R]) {
+    // checked build: a key must name a row of the table and of the window's accumulators
+    const uint32_t key_lim = TABLE == kTableDirect ? sm.rows : p.keys - sm.key_base;
     if constexpr (LOOKUP == kLookupKeys) {
         if constexpr (TABLE == kTableDirect && AGG == GNM_AGG_DIRECT) {
             Item its[R];
 #pragma unroll
-            for (int j = 0; j < R; ++j)
+            for (int j = 0; j < R; ++j) {
                 its[j] = classify_key(p, valid[j], src[j], sm.key_base, pk[j], oc[j], fi[j], la[j]);
+                its[j].valid = its[j].valid && chk(p.check_err, its[j].key < key_lim, kChkKey, its[j].key);
+            }
             srow_add_all<R>(sm, its, gacc);
             if (sm.hist || sm.rlog) {
 #pragma unroll
@@ -1092,7 +1126,8 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
         } else {
 #pragma unroll
             for (int j = 0; j < R; ++j) {
-                const Item it = classify_key(p, valid[j], src[j], sm.key_base, pk[j], oc[j], fi[j], la[j]);
+                Item it = classify_key(p, valid[j], src[j], sm.key_base, pk[j], oc[j], fi[j], la[j]);
+                it.valid = it.valid && chk(p.check_err, it.key < key_lim, kChkKey, it.key);
                 accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
                 if ((sm.hist || sm.rlog) && it.valid && it.elig) rate_stat_add(sm, it.key, it.oc, it.dur);
             }
@@ -1109,8 +1144,10 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
         if constexpr (TABLE == kTableDirect && AGG == GNM_AGG_DIRECT) {
             Item its[R];
 #pragma unroll
-            for (int j = 0; j < R; ++j)
+            for (int j = 0; j < R; ++j) {
                 its[j] = classify(p, valid[j], sl[j], dl[j], pk[j], oc[j], fi[j], la[j], site[j]);
+                its[j].valid = its[j].valid && chk(p.check_err, its[j].key < key_lim, kChkKey, its[j].key);
+            }
             srow_add_all<R>(sm, its, gacc);
             if (sm.hist || sm.rlog) {
 #pragma unroll
@@ -1120,7 +1157,8 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
         } else {
 #pragma unroll
             for (int j = 0; j < R; ++j) {
-                const Item it = classify(p, valid[j], sl[j], dl[j], pk[j], oc[j], fi[j], la[j], site[j]);
+                Item it = classify(p, valid[j], sl[j], dl[j], pk[j], oc[j], fi[j], la[j], site[j]);
+                it.valid = it.valid && chk(p.check_err, it.key < key_lim, kChkKey, it.key);
                 accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
                 if ((sm.hist || sm.rlog) && it.valid && it.elig) rate_stat_add(sm, it.key, it.oc, it.dur);
             }
@@ -1354,8 +1392,12 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
             if (TABLE != kTableGlobal) {
                 __syncthreads();
                 if (TABLE == kTableDirect && p.partials) {
-                    if (e >= e0)
-                        dump_rows(sm, p.partials + ((size_t)wd.part_base + q) * part_stride_words(sm.rows));
+                    if (e >= e0) {
+                        if (chk(p.check_err,
+                                ((uint64_t)wd.part_base + q + 1) * part_stride_words(sm.rows) <= p.partial_cap,
+                                kChkPartial, (uint64_t)wd.part_base + q))
+                            dump_rows(sm, p.partials + ((size_t)wd.part_base + q) * part_stride_words(sm.rows));
+                    }
                     else
                         flush_counts(sm, gacc);
                 } else {
@@ -1378,7 +1420,12 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
         if (s_last && (wd.flags & kWinFinalize)) {
             if (TABLE == kTableDirect && p.partials)
                 finalize_rows(p, wd.slot, tid, B, p.partials + (size_t)wd.part_base * part_stride_words(p.table_rows),
-                              wd.n_parts);
+                              chk(p.check_err,
+                                  ((uint64_t)wd.part_base + wd.n_parts) * part_stride_words(p.table_rows) <=
+                                      p.partial_cap,
+                                  kChkPartial, wd.part_base)
+                                  ? wd.n_parts
+                                  : 0u);
             else
                 finalize_rows(p, wd.slot, tid, B);
         }

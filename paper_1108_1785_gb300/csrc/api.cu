@@ -526,6 +526,8 @@ gnm_status build_params(gnm_ctx* c, const gnm_records* rec, AggParams* p) {
     p->n_ranges = (uint32_t)c->h_starts.size();
     p->n_sites = c->n_sites;
     p->rmi = c->rmi;
+    p->rmi.check_err = c->d_check;
+    p->check_err = c->d_check;
     for (uint32_t i = 0; i < GNM_MAX_LOCAL; ++i) {
         p->local_pfx[i] = c->local_pfx[i];
         p->local_mask[i] = c->local_mask[i];
@@ -736,6 +738,7 @@ gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, s
         pr.p.n_wins = (uint32_t)pr.wins.size();
         pr.p.done = d_done;
         pr.p.partials = pr.partial_words ? d_partials : nullptr;
+        pr.p.partial_cap = pr.partial_words;
         GNM_TRY(mark(-1));
         if (pr.sh.part) {
             // keys; regrouping by (window, key group); sums per group; grid finalisation
@@ -972,6 +975,20 @@ gnm_status close_window(gnm_ctx* c, uint64_t wid, cudaStream_t st) {
     return GNM_OK;
 }
 
+gnm_status device_checks(gnm_ctx* c) {
+#if GNM_CHECKED
+    unsigned long long v = 0;
+    GNM_CU(cudaMemcpyAsync(&v, c->d_check, 8, cudaMemcpyDeviceToHost, c->aux));
+    GNM_CU(cudaStreamSynchronize(c->aux));
+    if (v)
+        return fail(GNM_E_INTERNAL, std::string("device bounds check failed: ") + check_site_name((uint32_t)(v >> 56)) +
+                                        " (value " + std::to_string(v & 0x00FFFFFFFFFFFFFFull) + ")");
+#else
+    (void)c;
+#endif
+    return GNM_OK;
+}
+
 }  // namespace gnm
 
 using namespace gnm;
@@ -1038,8 +1055,10 @@ gnm_status gnm_create(const gnm_config* cfg, gnm_ctx** out) {
     if (cudaEventCreateWithFlags(&c->staging.ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc(&c->d_violations, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_check, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->d_flag_count, sizeof(uint32_t)) != cudaSuccess ||
-        cudaMemset(c->d_violations, 0, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMemset(c->d_violations, 0, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(c->d_check, 0, sizeof(unsigned long long)) != cudaSuccess) {
         gnm_destroy(c);
         return fail(GNM_E_CUDA, "context allocation failed");
     }
@@ -1076,6 +1095,7 @@ void gnm_destroy(gnm_ctx* c) {
     free_dev(c->d_smp16);
     free_dev(c->d_h24);
     free_dev(c->d_violations);
+    free_dev(c->d_check);
     free_dev(c->d_flag_count);
     free_dev(c->d_rmi_a);
     free_dev(c->d_rmi_b);
@@ -1614,7 +1634,7 @@ gnm_status gnm_window_dense(gnm_ctx* c, uint64_t wid, uint64_t* stats, uint64_t*
     if (unmatched)
         for (int k = 0; k < kUnmatched; ++k)
             for (int j = 0; j < 3; ++j) unmatched[k * 3 + j] = un6[k * kNStat + j];
-    return GNM_OK;
+    return device_checks(c);
 }
 
 gnm_status gnm_windows_results(gnm_ctx* c, const uint64_t* wids, size_t n, uint64_t* stats,
@@ -1654,7 +1674,7 @@ gnm_status gnm_windows_results(gnm_ctx* c, const uint64_t* wids, size_t n, uint6
         for (size_t k = 0; k < n; ++k)
             for (int q = 0; q < kUnmatched; ++q)
                 for (int j = 0; j < 3; ++j) unmatched[(k * kUnmatched + q) * 3 + j] = un6[(k * kUnmatched + q) * kNStat + j];
-    return GNM_OK;
+    return device_checks(c);
 }
 
 gnm_status gnm_window_device(gnm_ctx* c, uint64_t wid, const uint64_t** stats, const double** rate,
@@ -1726,7 +1746,7 @@ gnm_status gnm_flag_suboptimal(gnm_ctx* c, uint64_t wid, double thr, uint32_t* s
         if (site_out) site_out[i] = keys[i] >> 1;
         if (dir_out) dir_out[i] = (uint8_t)(keys[i] & 1);
     }
-    return GNM_OK;
+    return device_checks(c);
 }
 
 gnm_status gnm_window_release(gnm_ctx* c, uint64_t wid) {
@@ -1784,6 +1804,41 @@ gnm_status gnm_registry_flatten(const uint32_t* prefix, const uint8_t* len, cons
     if (starts) std::memcpy(starts, st.data(), st.size() * 4);
     if (site) std::memcpy(site, si.data(), si.size() * 4);
     return GNM_OK;
+}
+
+int gnm_checked_build(void) { return GNM_CHECKED; }
+
+gnm_status gnm_device_checks(gnm_ctx* c, uint64_t* word) {
+    if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
+    GNM_CU(cudaSetDevice(c->device));
+    GNM_CU(cudaDeviceSynchronize());
+    unsigned long long v = 0;
+    GNM_CU(cudaMemcpy(&v, c->d_check, 8, cudaMemcpyDeviceToHost));
+    if (word) *word = v;
+    const gnm_status st = device_checks(c);
+    GNM_CU(cudaMemset(c->d_check, 0, 8));
+    return st;
+}
+
+gnm_status gnm_debug_corrupt(gnm_ctx* c, int32_t what, uint32_t index, uint32_t value) {
+    if (!c) return fail(GNM_E_INVAL, "ctx is NULL");
+#if GNM_CHECKED
+    if (what != GNM_DEBUG_RMI_SPLIT_BASE) return fail(GNM_E_INVAL, "unknown corruption");
+    if (!c->rmi_ready) return fail(GNM_E_STATE, "no learned index");
+    if (index >= c->rmi.n_leaves || index >= c->rmi_split.size() || !c->rmi_split[index])
+        return fail(GNM_E_INVAL, "index is not a split leaf");
+    GNM_CU(cudaSetDevice(c->device));
+    GNM_CU(cudaDeviceSynchronize());
+    // the split leaf's first sub-leaf, in the model arrays and in their interleaved copy
+    GNM_CU(cudaMemcpy(const_cast<float*>(c->rmi.b) + index, &value, 4, cudaMemcpyHostToDevice));
+    GNM_CU(cudaMemcpy(reinterpret_cast<uint32_t*>(c->d_rmi_leaf4 + index) + 1, &value, 4, cudaMemcpyHostToDevice));
+    return GNM_OK;
+#else
+    (void)what;
+    (void)index;
+    (void)value;
+    return fail(GNM_E_STATE, "state can be corrupted only in the checked build (libgnm_checked.so)");
+#endif
 }
 
 }  // extern "C"

@@ -147,6 +147,7 @@ struct gnm_ctx {
     uint32_t ring_next = 0;
     gnm::Staging staging;
     unsigned long long* d_violations = nullptr;
+    unsigned long long* d_check = nullptr;  // the checked build's error word (site << 56 | value)
     uint32_t* d_flag_keys = nullptr;
     uint32_t* d_flag_count = nullptr;
     // learned index
@@ -214,6 +215,9 @@ void unpin_slot(gnm_ctx* c, uint32_t s);
 gnm_status reserve_launch_scratch(gnm_ctx* c, uint64_t n);
 // Clears the rate statistics of slots[0..n) on st (windows that start there).
 gnm_status clear_rate_stats(gnm_ctx* c, const uint32_t* slots, size_t n, cudaStream_t st);
+// Checked build: GNM_E_INTERNAL (naming the check) when a device bounds check has failed
+// since the context's error word was last cleared; the default build returns GNM_OK.
+gnm_status device_checks(gnm_ctx* c);
 // Sparse rate statistics: room for need[k] log words in slot slots[k] (keeping the words
 // already logged); synchronises `st` when a log grows, so call it outside stream capture.
 gnm_status reserve_rate_log(gnm_ctx* c, const uint32_t* slots, const uint64_t* need, size_t n, cudaStream_t st);

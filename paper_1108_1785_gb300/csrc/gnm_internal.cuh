@@ -10,7 +10,43 @@
 #include "gnm.h"
 #include "hash24.hpp"
 
+// The checked build (-DGNM_CHECKED=1, libgnm_checked.so) tests every index at the points
+// where kernels trust data -- a record's key before the table, accumulator and histogram
+// accesses it drives, a registry search's starting window before its loads, a learned-index
+// model number, a regrouping bucket and position, a partial block -- and on a failure skips
+// the access and records the first failure in a device word that the host reports as
+// GNM_E_INTERNAL. In the default build the checks compile away.
+#ifndef GNM_CHECKED
+#define GNM_CHECKED 0
+#endif
+
 namespace gnm {
+
+// Check sites of the checked build (the top byte of the device error word).
+enum : uint32_t {
+    kChkKey = 1,          // a record's key beyond its table / accumulator rows
+    kChkWindow = 2,       // a registry search window beyond the ranges
+    kChkBlocks = 3,       // a block-sample search window beyond the blocks
+    kChkModel = 4,        // a learned-index model number beyond the models
+    kChkBucket = 5,       // a regrouping bucket beyond the launch's buckets
+    kChkPosition = 6,     // a regrouped record position beyond the records
+    kChkPartial = 7,      // a partial-sum block beyond the partial area
+    kChkHostKey = 8,      // a per-host key beyond the site keys
+};
+
+__host__ __device__ inline const char* check_site_name(uint32_t s) {
+    switch (s) {
+        case kChkKey: return "record key beyond its table or accumulator rows";
+        case kChkWindow: return "registry search window beyond the ranges";
+        case kChkBlocks: return "block-sample search window beyond the blocks";
+        case kChkModel: return "learned-index model number beyond the models";
+        case kChkBucket: return "regrouping bucket beyond the launch's buckets";
+        case kChkPosition: return "regrouped record position beyond the records";
+        case kChkPartial: return "partial-sum block beyond the partial area";
+        case kChkHostKey: return "per-host key beyond the site keys";
+        default: return "unknown check";
+    }
+}
 
 constexpr uint32_t kNoSite = GNM_NO_SITE;
 constexpr int kNStat = GNM_NSTAT;   // columns of a user-facing stats row
@@ -63,6 +99,7 @@ struct RmiDev {
                            // kEpsSplit: a split leaf
     const uint4* leaf4;    // per model (a bits, b bits, x0, eps) interleaved: one 16-byte load
     uint32_t leaves_global;  // this launch reads leaf4 from global memory instead of staging
+    unsigned long long* check_err;  // the checked build's error word
 };
 
 struct AggParams {
@@ -144,7 +181,24 @@ struct AggParams {
     uint32_t* partials;          // per (window, CTA) dumps of the shared rows, or null
     uint32_t* done;              // [n_wins] finalise tickets, zero between launches
     unsigned long long* violations;  // learned-index fallbacks
+    unsigned long long* check_err;   // the checked build's error word (site << 56 | value)
+    uint64_t partial_cap;            // words of `partials` (checked build)
+    uint64_t part_cap;               // records of a partitioned launch's regrouped arrays (checked build)
 };
+
+// The checked build's test: false when !ok, recording the first failure as site << 56 |
+// value; in the default build always true, and the compiler drops the test.
+__device__ __forceinline__ bool chk(unsigned long long* err, bool ok, uint32_t site, uint64_t value) {
+#if GNM_CHECKED
+    if (!ok && err) atomicCAS(err, 0ull, ((unsigned long long)site << 56) | (value & 0x00FFFFFFFFFFFFFFull));
+    return ok;
+#else
+    (void)err;
+    (void)site;
+    (void)value;
+    return true;
+#endif
+}
 
 // kLookupKeys: the aggregation reads per-record keys that a lookup kernel wrote (split
 // launches), instead of addresses.

@@ -68,8 +68,13 @@ __global__ void __launch_bounds__(kFinKeys, 4) k_finalize_windows(const __grid_c
     const WinDesc wd = p.wins[blockIdx.y];
     const uint32_t* parts =
         p.partials ? p.partials + (size_t)wd.part_base * part_stride_words(p.table_rows) : nullptr;
+    const bool in_area = !p.partials || p.part_groups ||
+                         chk(p.check_err,
+                             ((uint64_t)wd.part_base + wd.n_parts) * part_stride_words(p.table_rows) <= p.partial_cap,
+                             kChkPartial, wd.part_base);
     dev::finalize_rows<true>(p, wd.slot, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, parts,
-                             p.partials ? wd.n_parts : 0u, blockIdx.y, stage + (threadIdx.x & ~31u) * kNStat);
+                             p.partials && in_area ? wd.n_parts : 0u, blockIdx.y,
+                             stage + (threadIdx.x & ~31u) * kNStat);
 }
 
 // One warp per key: the key's eligible flows (the histogram's total) and the bucket where
@@ -189,7 +194,7 @@ __global__ void k_lookup(const __grid_constant__ AggParams p, const uint32_t* __
             idx = dev::rmi_lookup(p.rmi, ra, rb, rx0, reps, p.starts, p.n_ranges, x, p.violations);
         } else if (LOOKUP == kLookupRadix) {
             uint32_t xs[1] = {x}, b[1];
-            dev::radix_search<1>(s_starts, p.radix_bits, p.starts, xs, b);
+            dev::radix_search<1>(s_starts, p.radix_bits, p.starts, xs, b, p.n_ranges, p.check_err);
             idx = b[0];
         } else if (LOOKUP == kLookupStaged) {
             uint32_t xs[1] = {x}, b[1];

@@ -138,6 +138,7 @@ extern "C" gnm_status gnm_window_process_noalloc(const gnm_config* cfg_in, const
     p.wins = reinterpret_cast<const WinDesc*>(scr);
     p.done = reinterpret_cast<uint32_t*>(scr + 64);
     p.violations = reinterpret_cast<unsigned long long*>(scr + 128);
+    p.check_err = reinterpret_cast<unsigned long long*>(scr + 192);  // (checked build)
     p.n_wins = 1;
     p.n_total = rec->n;
 

@@ -61,7 +61,8 @@ __global__ void __launch_bounds__(kPartThreads)
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (i + (uint64_t)u * blockDim.x < e0) atomicAdd(&hist[w * groups + k[u] / rows], 1u);
+                if (i + (uint64_t)u * blockDim.x < e0 && chk(p.check_err, k[u] / rows < groups, kChkBucket, k[u]))
+                    atomicAdd(&hist[w * groups + k[u] / rows], 1u);
         }
     }
     __syncthreads();
@@ -156,20 +157,27 @@ __global__ void __launch_bounds__(kPartThreads)
             for (uint32_t g = tid; g < groups; g += kPartThreads) hist[g] = 0u;
             __syncthreads();
             uint32_t grp[kTileRecs], rk[kTileRecs];
+            bool in[kTileRecs];
 #pragma unroll
             for (int u = 0; u < kTileRecs; ++u) {
                 const uint32_t j = tid + u * kPartThreads;
                 grp[u] = v[0][u] / rows;
-                rk[u] = j < n ? atomicAdd(&hist[grp[u]], 1u) : 0u;
+                // (checked build: a key beyond the groups is left out here as in the count)
+                in[u] = j < n && (GNM_CHECKED == 0 || grp[u] < groups);
+                rk[u] = in[u] ? atomicAdd(&hist[grp[u]], 1u) : 0u;
             }
             __syncthreads();
             cta_exclusive_scan(hist, toff, groups, tmp);
             for (uint32_t g = tid; g < groups; g += kPartThreads)
                 gpos[g] = hist[g] ? atomicAdd(cnt + w * groups + g, hist[g]) : 0u;
+            uint32_t placed = n;  // records of the tile that are placed
+#if GNM_CHECKED
+            placed = 0;
+            for (uint32_t g = 0; g < groups; ++g) placed += hist[g];
+#endif
 #pragma unroll
             for (int u = 0; u < kTileRecs; ++u) {
-                const uint32_t j = tid + u * kPartThreads;
-                if (j < n) {
+                if (in[u]) {
                     const uint32_t pos = toff[grp[u]] + rk[u];
                     s_rec[pos] = v[0][u] - grp[u] * rows;
 #pragma unroll
@@ -179,9 +187,10 @@ __global__ void __launch_bounds__(kPartThreads)
             }
             __syncthreads();
             if (t0 + kTile < e0) load(t0 + kTile);
-            for (uint32_t j = tid; j < n; j += kPartThreads) {
+            for (uint32_t j = tid; j < placed; j += kPartThreads) {
                 const uint32_t g = s_grp[j];
                 const uint32_t r = gpos[g] + (j - toff[g]);
+                if (!chk(p.check_err, r < stride, kChkPosition, r)) continue;
 #pragma unroll
                 for (int f = 0; f < 5; ++f) o[f][r] = s_rec[f * kTile + j];
             }

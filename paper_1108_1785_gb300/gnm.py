@@ -14,7 +14,8 @@ from typing import Dict, Optional, Sequence, Tuple
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgnm.so")
+# GNM_CHECKED=1 in the environment selects the build with device-side bounds checks
+LIB_PATH = os.path.join(_HERE, "libgnm_checked.so" if os.environ.get("GNM_CHECKED") == "1" else "libgnm.so")
 
 NO_SITE = 0xFFFFFFFF
 NSTAT = 6
@@ -26,6 +27,7 @@ TABLE_AUTO, TABLE_DIRECT, TABLE_HASH, TABLE_GLOBAL, TABLE_PARTITION = 0, 1, 2, 3
 SPLIT_AUTO, SPLIT_FUSED, SPLIT_TWO_KERNELS = 0, 1, 2
 ROOT_LINEAR, ROOT_MLP = 0, 1
 FIT_MINIMAX, FIT_MSE = 0, 1
+DEBUG_RMI_SPLIT_BASE = 1
 HOST_AUTO, HOST_STAGE, HOST_IN_PLACE = 0, 1, 2
 RATE_BUCKETS = 10001
 NO_MEDIAN = 0xFFFFFFFF
@@ -120,6 +122,11 @@ class TuneReport(C.Structure):
 _lib = None
 
 
+def checked_build() -> bool:
+    """True when the loaded library is the build with device-side bounds checks."""
+    return bool(lib().gnm_checked_build())
+
+
 def lib():
     """The loaded C library (raises if it has not been built)."""
     global _lib
@@ -169,6 +176,9 @@ def lib():
             "gnm_last_launch_count": (U32, [P]),
             "gnm_window_rate_stats": (st, [P, U64, P, P, P, P]),
             "gnm_window_rate_cells": (st, [P, U64, P, P, P, C.c_size_t, C.POINTER(C.c_size_t)]),
+            "gnm_checked_build": (C.c_int, []),
+            "gnm_device_checks": (st, [P, C.POINTER(U64)]),
+            "gnm_debug_corrupt": (st, [P, C.c_int32, U32, U32]),
             "gnm_warnings_update": (st, [P, U64, U32, U32, P, S, C.POINTER(S)]),
             "gnm_warnings_reset": (st, [P]),
             "gnm_warnings_export": (st, [P, P]),
@@ -404,6 +414,17 @@ class Context:
         ids = np.ascontiguousarray(window_ids, np.uint64)
         self._c(lib().gnm_windows_results(self.h, _ptr(ids), ids.size, _ptr(stats), _ptr(unmatched), _ptr(rate),
                                           _ptr(flag)))
+
+    def device_checks(self) -> int:
+        """The checked build's error word since the last call (0: no failed bounds check);
+        raises GnmError (GNM_E_INTERNAL) when a check failed."""
+        w = C.c_uint64()
+        self._c(lib().gnm_device_checks(self.h, C.byref(w)))
+        return w.value
+
+    def debug_corrupt(self, what: int, index: int, value: int):
+        """Checked build only: overwrite one value of the device state (see gnm.h)."""
+        self._c(lib().gnm_debug_corrupt(self.h, what, index, value))
 
     def rate_cells(self, window_id: int):
         """Non-empty cells of a finalised window's rate histograms: (key, bucket, count)

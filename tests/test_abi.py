@@ -28,12 +28,16 @@ def declared_functions():
     return sorted(set(re.findall(r"\b(gnm_[a-z0-9_]+)\s*\(", txt)))
 
 
-def test_library_exports_every_declared_entry_point(gnm):
-    lib = C.CDLL(gnm.LIB_PATH)
+@pytest.mark.parametrize("name", ["libgnm.so", "libgnm_checked.so"])
+def test_library_exports_every_declared_entry_point(gnm, name):
+    """Both builds (the library and the one with device-side bounds checks) export every
+    function gnm.h declares."""
+    lib = C.CDLL(os.path.join(os.path.dirname(gnm.LIB_PATH), name))
     names = declared_functions()
     assert len(names) >= 30
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, f"declared in gnm.h but not exported: {missing}"
+    assert lib.gnm_checked_build() == (1 if "checked" in name else 0)
 
 
 def test_config_defaults(gnm):
