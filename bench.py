@@ -79,12 +79,15 @@ LOOKUP_NAMES = {1: "binary search", 2: "learned index (RMI)", 3: "radix director
 def rmi_mode(name):
     """'rmi' = the learned-index workload's model (linear root, 4,096 minimax leaves, leaves
     whose window would exceed 64 split); 'rmi_mse' = the same root with mean-squared-error
-    leaves; 'rmiL' = L minimax leaves. Returns (leaves, leaf_fit name) or (0, None)."""
+    leaves; 'rmi_tE' = 4,096 minimax leaves split above a window of E; 'rmiL' = L minimax
+    leaves. Returns (leaves, leaf_fit name, eps_target) or (0, None, 0)."""
     if not name.startswith("rmi"):
-        return 0, None
+        return 0, None, 0
     if name == "rmi_mse":
-        return 4096, "mse"
-    return (int(name[3:]) if len(name) > 3 else 4096), "minimax"
+        return 4096, "mse", 64
+    if name.startswith("rmi_t"):
+        return 4096, "minimax", int(name[5:])
+    return (int(name[3:]) if len(name) > 3 else 4096), "minimax", 64
 
 
 def learned_vs_plain(gnm, torch, local, steps, warmup, n_records=50_000_000,
@@ -103,14 +106,15 @@ def learned_vs_plain(gnm, torch, local, steps, warmup, n_records=50_000_000,
     stream = torch.cuda.current_stream()
     res, dense, info_out = {}, {}, {}
     for name in modes:
-        leaves, fit = rmi_mode(name)
+        leaves, fit, target = rmi_mode(name)
         mode = {"bsearch": gnm.LOOKUP_BSEARCH, "radix": gnm.LOOKUP_RADIX}.get(name, gnm.LOOKUP_RMI)
         ctx = gnm.Context(device=local, window_slots=4, lookup_mode=mode)
         ctx.load(reg)
         if leaves:
             rep = ctx.rmi_train(keys, root_kind=gnm.ROOT_LINEAR, n_leaves=leaves, leaf_iters=4,
-                                leaf_fit=gnm.FIT_MSE if fit == "mse" else gnm.FIT_MINIMAX)
-            info_out[name] = {"leaves": leaves, "root": "linear", "leaf_fit": fit, "models": int(rep.n_models),
+                                leaf_fit=gnm.FIT_MSE if fit == "mse" else gnm.FIT_MINIMAX, eps_target=target)
+            info_out[name] = {"leaves": leaves, "root": "linear", "leaf_fit": fit, "eps_target": target,
+                              "models": int(rep.n_models),
                               "split_leaves": int(rep.split_leaves), "eps_max": int(rep.eps_max),
                               "err_max": int(rep.err_max), "eps_mean": round(float(rep.eps_mean), 2),
                               "train_ms": round(float(rep.train_ms), 1), "sweep_ms": round(float(rep.sweep_ms), 1),

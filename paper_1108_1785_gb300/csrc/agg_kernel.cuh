@@ -390,48 +390,74 @@ __device__ __forceinline__ uint32_t rmi_lookup(const RmiDev& m, const float* a, 
     return pred_search1(starts, 0, n, x);
 }
 
-// Learned-index lookups of R addresses in lock step over the (start, site) pairs: the
-// model's window for each, one bounded search for all, then the same verification as
-// rmi_lookup (the window's lower end not above x, the answer below its upper end unless
-// that is the last range), with a full search for the lookups that fail it.
+// The four (start, site) pairs of 32-byte sector k of `pairs` (one 256-bit load, sm_100).
+__device__ __forceinline__ void ld_sector(const uint2* __restrict__ pairs, uint32_t k, uint4& lo, uint4& hi) {
+    const uint4* q = reinterpret_cast<const uint4*>(pairs) + 2u * (size_t)k;
+    asm("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
+        : "l"(q));
+}
+
+// Learned-index lookups of R addresses in lock step over the (start, site) pairs. The model
+// gives each a window [lo, hi] (hi one past the proven bound, to verify it); the window is
+// searched by 32-byte sectors of four pairs: a binary search over the sectors' first starts
+// (one 4-byte probe each) finds the last sector from lo's sector to hi's whose first start
+// is <= x, and one 256-bit load of it gives the count c of its starts <= x and the site.
+// The answer is exact when c >= 1 (lo's sector does start at or below x) and the range
+// after it was seen (c < 4, or a later sector was probed, or the array ends there);
+// otherwise the lookup counts a fallback and takes the full search. Pairs past the last
+// range have start 0xFFFFFFFF and the last range's site, and the array is padded so that
+// the sector of any hi <= n - 1 is whole.
 template <int R>
 __device__ __forceinline__ void rmi_sites(const RmiDev& m, const float* a, const float* b, const uint32_t* x0,
                                           const uint32_t* eps, const uint2* __restrict__ pairs, uint32_t n,
                                           const bool (&valid)[R], const uint32_t (&x)[R], uint32_t (&site)[R],
                                           unsigned long long* violations) {
-    uint32_t base[R], len[R], lo[R], hi[R];
-    uint32_t first[R];
+    uint32_t sb[R], len[R], s1[R];
+    bool more = false;
 #pragma unroll
     for (int j = 0; j < R; ++j) {
         const RmiLeaf lf = rmi_model(m, a, b, x0, eps, x[j]);
         const uint32_t e = lf.eps;
-        if (!valid[j]) {
-            lo[j] = 0u;
-            hi[j] = 0u;
-        } else if (e == 0xFFFFFFFFu) {  // no proven bound for this leaf: full search
-            lo[j] = 0u;
-            hi[j] = n - 1u;
-        } else {
+        uint32_t lo = 0u, hi = 0u;
+        if (valid[j] && e == 0xFFFFFFFFu) {  // no proven bound for this leaf: full search
+            hi = n - 1u;
+        } else if (valid[j]) {
             const uint32_t pi = rmi_leaf_pos(lf, x[j], n);
             const uint32_t elo = e & 0xFFFFu, ehi = e >> 16;
-            lo[j] = pi > elo ? pi - elo : 0u;
-            hi[j] = min(pi + ehi + 1u, n - 1u);  // one past the bound, to verify it
+            lo = pi > elo ? pi - elo : 0u;
+            hi = min(pi + ehi + 1u, n - 1u);  // one past the bound, to verify it
         }
-        const uint2 f = __ldg(pairs + lo[j]);
-        first[j] = f.x;
-        site[j] = f.y;
-        base[j] = lo[j];
-        len[j] = hi[j] - lo[j] + 1u;
+        sb[j] = lo >> 2;
+        s1[j] = hi >> 2;
+        len[j] = s1[j] - sb[j] + 1u;
+        more |= len[j] > 1u;
     }
-    pair_search<R>(pairs, x, base, len, site);
+    const uint32_t* st = reinterpret_cast<const uint32_t*>(pairs);  // start of pair i at word 2i
+    while (more) {
+        more = false;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (len[j] > 1u) {
+                const uint32_t half = len[j] >> 1;
+                if (__ldg(st + 8u * (size_t)(sb[j] + half)) <= x[j]) sb[j] += half;
+                len[j] -= half;
+                more |= len[j] > 1u;
+            }
+        }
+    }
 #pragma unroll
     for (int j = 0; j < R; ++j) {
-        const bool ok = (lo[j] == 0u || first[j] <= x[j]) && (base[j] < hi[j] || hi[j] == n - 1u);
+        uint4 v0, v1;
+        ld_sector(pairs, sb[j], v0, v1);
+        const uint32_t c = (v0.x <= x[j]) + (v0.z <= x[j]) + (v1.x <= x[j]) + (v1.z <= x[j]);
+        site[j] = c <= 1u ? v0.y : (c == 2u ? v0.w : (c == 3u ? v1.y : v1.w));
+        const bool ok = c >= 1u && (c < 4u || sb[j] < s1[j] || 4u * sb[j] + 3u >= n - 1u);
         if (valid[j] && !ok) {
             atomicAdd(violations, 1ull);
-            uint32_t xb[1] = {x[j]}, bb[1] = {0u}, lb[1] = {n}, sb[1] = {__ldg(pairs).y};
-            pair_search<1>(pairs, xb, bb, lb, sb);
-            site[j] = sb[0];
+            uint32_t xb[1] = {x[j]}, bb[1] = {0u}, lb[1] = {n}, sbb[1] = {__ldg(pairs).y};
+            pair_search<1>(pairs, xb, bb, lb, sbb);
+            site[j] = sbb[0];
         }
     }
 }
