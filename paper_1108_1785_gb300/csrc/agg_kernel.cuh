@@ -1209,7 +1209,7 @@ __device__ __forceinline__ void scalar_range(const AggParams& p, const Smem& sm,
             d[j] = LOOKUP == kLookupKeys ? 0u : ld_stream1(p.dst + ii);
             pk[j] = ld_stream1(p.pkts + ii);
             oc[j] = ld_stream1(p.oct + ii);
-            fi[j] = ld_stream1(p.first + ii);
+            fi[j] = p.first ? ld_stream1(p.first + ii) : 0u;
             la[j] = ld_stream1(p.last + ii);
         }
         process<LOOKUP, TABLE, AGG, 4>(p, sm, gacc, v, s, d, pk, oc, fi, la);
@@ -1233,7 +1233,9 @@ __device__ __forceinline__ void vector_range(const AggParams& p, const Smem& sm,
             const uint4 vs = ld_stream4(p.src + i);
             const uint4 vd = LOOKUP == kLookupKeys ? make_uint4(0, 0, 0, 0) : ld_stream4(p.dst + i);
             const uint4 vp = ld_stream4(p.pkts + i), vo = ld_stream4(p.oct + i);
-            const uint4 vf = ld_stream4(p.first + i), vl = ld_stream4(p.last + i);
+            // (regrouped records hold the duration in `last` and no `first`)
+            const uint4 vf = p.first ? ld_stream4(p.first + i) : make_uint4(0, 0, 0, 0);
+            const uint4 vl = ld_stream4(p.last + i);
             s[4 * u + 0] = vs.x; s[4 * u + 1] = vs.y; s[4 * u + 2] = vs.z; s[4 * u + 3] = vs.w;
             d[4 * u + 0] = vd.x; d[4 * u + 1] = vd.y; d[4 * u + 2] = vd.z; d[4 * u + 3] = vd.w;
             pk[4 * u + 0] = vp.x; pk[4 * u + 1] = vp.y; pk[4 * u + 2] = vp.z; pk[4 * u + 3] = vp.w;
@@ -1479,10 +1481,27 @@ __global__ void __launch_bounds__(keys_block_max(LOOKUP, U)) k_keys(const __grid
     sm.tk = nullptr;
     sm.rows = 0;
     stage_lookup<LOOKUP>(p, smem_raw, sm);
+    // partitioned launches: this CTA's record counts per (window, key group) bucket
+    uint32_t* hist = p.key_hist ? reinterpret_cast<uint32_t*>(smem_raw + p.key_hist_off) : nullptr;
+    const uint32_t nbk = p.key_hist ? p.n_wins * p.part_groups : 0u;
+    for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x) hist[b] = 0u;
     __syncthreads();
     const uint64_t N = p.n_total;
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // bucket count of record i with key k (the lanes of a warp that share a bucket add once)
+    uint32_t wcur = 0;
+    auto count = [&](bool ok, uint64_t i, uint32_t k) {
+        if (!hist) return;
+        if (ok)
+            while (wcur + 1 < p.n_wins && p.wins[wcur].end <= i) ++wcur;
+        const uint32_t g = ok ? k / p.key_group_rows : 0u;
+        const uint32_t b = ok ? wcur * p.part_groups + g : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, b);
+        if (ok && chk(p.check_err, g < p.part_groups, kChkBucket, k) &&
+            (threadIdx.x & 31u) == (uint32_t)(__ffs(peers) - 1))
+            atomicAdd(hist + b, (uint32_t)__popc(peers));
+    };
     uint64_t a0 = N, a1 = N;
     if (p.vec_ok) {
         const uint32_t mis = p.phase & 3u;
@@ -1492,19 +1511,30 @@ __global__ void __launch_bounds__(keys_block_max(LOOKUP, U)) k_keys(const __grid
     // unaligned head and tail (at most 3 + 3 records), or every record when the arrays'
     // 16-byte phases differ
     const uint64_t ns = a0 + (N - a1);
-    for (uint64_t t = tid; t < ns; t += T) {
-        const uint64_t i = t < a0 ? t : a1 + (t - a0);
-        const uint32_t src = __ldcs(p.src + i), dst = __ldcs(p.dst + i);
-        bool sl, dl;
-        local_pair(p, src, dst, sl, dl);
-        const bool v[1] = {true};
-        const uint32_t x[1] = {sl ? dst : src};
-        uint32_t site[1];
-        lookup_sites<LOOKUP, 1>(p, sm, v, x, site);
-        keys[i] = record_key(p, sl, dl, site[0]);
+    for (uint64_t tb = 0; tb < ns; tb += T) {  // uniform loop (the counts are warp-collective)
+        const uint64_t t = tb + tid;
+        const bool ok = t < ns;
+        const uint64_t i = !ok ? 0u : (t < a0 ? t : a1 + (t - a0));
+        uint32_t k = 0u;
+        if (ok) {
+            const uint32_t src = __ldcs(p.src + i), dst = __ldcs(p.dst + i);
+            bool sl, dl;
+            local_pair(p, src, dst, sl, dl);
+            const bool v[1] = {true};
+            const uint32_t x[1] = {sl ? dst : src};
+            uint32_t site[1];
+            lookup_sites<LOOKUP, 1>(p, sm, v, x, site);
+            k = record_key(p, sl, dl, site[0]);
+            keys[i] = k;
+        }
+        if (hist) {
+            wcur = ok ? min(first_window(p.wins, p.n_wins, i), p.n_wins - 1u) : 0u;
+            count(ok, i, k);
+        }
     }
     constexpr int R = 4 * U;
     const uint64_t G = (a1 - a0) >> 2;
+    if (hist && tid < G) wcur = min(first_window(p.wins, p.n_wins, a0 + 4u * tid), p.n_wins - 1u);
     // one group per thread: the next step's addresses are loaded before this step's
     // lookups, so that their memory latency overlaps them (two groups per thread have no
     // registers left for it)
@@ -1543,15 +1573,25 @@ __global__ void __launch_bounds__(keys_block_max(LOOKUP, U)) k_keys(const __grid
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint64_t g = gb + (uint64_t)u * T + tid;
-            if (g < G) {
-                uint4 k;
-                k.x = record_key(p, sl[4 * u + 0], dl[4 * u + 0], site[4 * u + 0]);
-                k.y = record_key(p, sl[4 * u + 1], dl[4 * u + 1], site[4 * u + 1]);
-                k.z = record_key(p, sl[4 * u + 2], dl[4 * u + 2], site[4 * u + 2]);
-                k.w = record_key(p, sl[4 * u + 3], dl[4 * u + 3], site[4 * u + 3]);
-                __stcg(reinterpret_cast<uint4*>(keys + a0 + 4u * g), k);
+            uint4 k;
+            k.x = record_key(p, sl[4 * u + 0], dl[4 * u + 0], site[4 * u + 0]);
+            k.y = record_key(p, sl[4 * u + 1], dl[4 * u + 1], site[4 * u + 1]);
+            k.z = record_key(p, sl[4 * u + 2], dl[4 * u + 2], site[4 * u + 2]);
+            k.w = record_key(p, sl[4 * u + 3], dl[4 * u + 3], site[4 * u + 3]);
+            if (g < G) __stcg(reinterpret_cast<uint4*>(keys + a0 + 4u * g), k);
+            if (hist) {  // (every lane takes part: the counts are warp-collective)
+                const uint64_t i0 = a0 + 4u * g;  // (a thread's groups only grow: wcur only advances)
+                count(g < G, i0, k.x);
+                count(g < G, i0 + 1, k.y);
+                count(g < G, i0 + 2, k.z);
+                count(g < G, i0 + 3, k.w);
             }
         }
+    }
+    if (hist) {  // this CTA's counts to the launch's
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < nbk; b += blockDim.x)
+            if (hist[b]) atomicAdd(p.key_hist + b, hist[b]);
     }
 }
 

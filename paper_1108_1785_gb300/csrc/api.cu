@@ -650,7 +650,7 @@ gnm_status prepare_launch(gnm_ctx* c, const gnm_records* dr, const uint64_t* off
 
 PartLayout part_layout(uint64_t n, uint32_t nb) {
     PartLayout l;
-    l.cnt = 5 * part_array_stride(n) * 4;
+    l.cnt = 4 * part_array_stride(n) * 4;
     l.descs = (l.cnt + (uint64_t)nb * 4 + 15) & ~15ull;
     l.pdesc = l.descs + (uint64_t)nb * sizeof(WinDesc);
     l.bytes = l.pdesc + (uint64_t)nb * sizeof(uint2);
@@ -743,9 +743,28 @@ gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, s
         if (pr.sh.part) {
             // keys; regrouping by (window, key group); sums per group; grid finalisation
             uint32_t* keys = d_keys + pr.p.phase;
+            const PartLayout L = part_layout(pr.n, pr.n_buckets);
+            uint32_t* out = reinterpret_cast<uint32_t*>(d_part);
+            uint32_t* cnt = reinterpret_cast<uint32_t*>(d_part + L.cnt);
+            WinDesc* descs = reinterpret_cast<WinDesc*>(d_part + L.descs);
+            uint2* pdesc = reinterpret_cast<uint2*>(d_part + L.pdesc);
+            // the key kernel also counts the records of every (window, key group) bucket when
+            // its shared memory has room for the counts; else the count kernel does
+            const uint32_t nb = pr.p.n_wins * pr.sh.part_groups;
             AggParams pk = pr.p;
+            LaunchShape sk = pr.sh;
             if (pr.sh.keys_blk) pk.radix_bits = pr.sh.keys_bits;
-            GNM_CU(launch_keys(pk, pr.sh, keys, st));
+            const size_t hist_off = (pr.sh.keys_smem + 15) / 16 * 16;
+            const bool fold = hist_off + (size_t)nb * 4 + 1024 <= (size_t)c->smem_optin;
+            if (fold) {
+                GNM_CU(cudaMemsetAsync(cnt, 0, (size_t)nb * 4, st));
+                pk.key_hist = cnt;
+                pk.part_groups = pr.sh.part_groups;
+                pk.key_group_rows = pr.sh.part_rows;
+                pk.key_hist_off = (uint32_t)hist_off;
+                sk.keys_smem = hist_off + (size_t)nb * 4;
+            }
+            GNM_CU(launch_keys(pk, sk, keys, st));
             ++*launches;
             GNM_TRY(mark(GNM_KERNEL_KEYS));
             if (pr.p.hkeys) {
@@ -753,17 +772,14 @@ gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, s
                 ++*launches;
                 GNM_TRY(mark(GNM_KERNEL_HOSTS));
             }
-            const PartLayout L = part_layout(pr.n, pr.n_buckets);
-            uint32_t* out = reinterpret_cast<uint32_t*>(d_part);
-            uint32_t* cnt = reinterpret_cast<uint32_t*>(d_part + L.cnt);
-            WinDesc* descs = reinterpret_cast<WinDesc*>(d_part + L.descs);
-            uint2* pdesc = reinterpret_cast<uint2*>(d_part + L.pdesc);
             AggParams pp = pr.p;
             pp.src = keys;
             pp.dst = keys;
-            GNM_CU(launch_part_count(pp, pr.sh, cnt, st));
-            ++*launches;
-            GNM_TRY(mark(GNM_KERNEL_PART_COUNT));
+            if (!fold) {
+                GNM_CU(launch_part_count(pp, pr.sh, cnt, st));
+                ++*launches;
+                GNM_TRY(mark(GNM_KERNEL_PART_COUNT));
+            }
             GNM_CU(launch_part_scan(pp, pr.sh, pr.p.chunk, cnt, descs, pdesc, st));
             ++*launches;
             GNM_TRY(mark(GNM_KERNEL_PART_SCAN));
@@ -776,8 +792,8 @@ gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, s
             pa.dst = out;
             pa.pkts = out + stride;
             pa.oct = out + 2 * stride;
-            pa.first = out + 3 * stride;
-            pa.last = out + 4 * stride;
+            pa.first = nullptr;  // regrouped records carry the duration as `last`
+            pa.last = out + 3 * stride;
             pa.vec_ok = 1;
             pa.phase = 0;
             pa.wins = descs;

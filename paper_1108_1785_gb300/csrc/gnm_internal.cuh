@@ -182,6 +182,12 @@ struct AggParams {
     uint32_t* done;              // [n_wins] finalise tickets, zero between launches
     unsigned long long* violations;  // learned-index fallbacks
     unsigned long long* check_err;   // the checked build's error word (site << 56 | value)
+    // key kernel of a partitioned launch: per (window, key group) record counts (global,
+    // zeroed before the launch), the keys per group, and the shared-memory offset of the
+    // kernel's own counts (or key_hist == null)
+    uint32_t* key_hist;
+    uint32_t key_group_rows;
+    uint32_t key_hist_off;
     uint64_t partial_cap;            // words of `partials` (checked build)
     uint64_t part_cap;               // records of a partitioned launch's regrouped arrays (checked build)
 };

@@ -111,8 +111,9 @@ __device__ __forceinline__ void cta_exclusive_scan(const uint32_t* v, uint32_t* 
 // The regrouping itself, tile by tile (kTile records of one window): the tile is sorted by
 // key group in shared memory, each group's run of the tile takes its place in the bucket
 // with one atomic on cnt (the bucket's next free place), and the runs go out with
-// coalesced stores. out: 5 arrays of `stride` words (key within its group, pkts, octets,
-// first, last). Any split of the records into CTAs works: places are reserved per tile.
+// coalesced stores. out: 4 arrays of `stride` words (key within its group, pkts, octets,
+// duration = last - first mod 2^32, the only use of the two times). Any split of the
+// records into CTAs works: places are reserved per tile.
 constexpr uint32_t kTile = 4 * kPartThreads;
 constexpr int kTileRecs = (int)(kTile / kPartThreads);  // records per thread and tile
 
@@ -121,12 +122,12 @@ __global__ void __launch_bounds__(kPartThreads)
                    uint32_t* __restrict__ cnt, uint32_t* __restrict__ out, uint64_t stride) {
     extern __shared__ __align__(16) uint32_t sh[];
     __shared__ uint32_t tmp[kPartThreads];
-    uint32_t* s_rec = sh;                 // [5][kTile] the tile in group order
-    uint32_t* s_grp = sh + 5 * kTile;     // [kTile] group of each placed record
+    uint32_t* s_rec = sh;                 // [4][kTile] the tile in group order
+    uint32_t* s_grp = sh + 4 * kTile;     // [kTile] group of each placed record
     uint32_t* hist = s_grp + kTile;       // [groups] records of the tile per group
     uint32_t* toff = hist + groups;       // [groups] first place of each group in the tile
     uint32_t* gpos = toff + groups;       // [groups] first place of each group's run in its bucket
-    uint32_t* o[5] = {out, out + stride, out + 2 * stride, out + 3 * stride, out + 4 * stride};
+    uint32_t* o[4] = {out, out + stride, out + 2 * stride, out + 3 * stride};
     const uint32_t tid = threadIdx.x;
     const uint64_t lo = min((uint64_t)blockIdx.x * chunk, p.n_total);
     const uint64_t hi = min(lo + chunk, p.n_total);
@@ -134,9 +135,9 @@ __global__ void __launch_bounds__(kPartThreads)
         const WinDesc wd = p.wins[w];
         if (wd.begin >= hi) break;
         const uint64_t e0 = min(wd.end, hi);
-        // a tile's five fields are in registers before it is sorted; the next tile of the
-        // segment is loaded while this one goes out, so its memory latency overlaps the stores
-        uint32_t v[5][kTileRecs];
+        // a tile's fields are in registers before it is sorted; the next tile of the segment
+        // is loaded while this one goes out, so its memory latency overlaps the stores
+        uint32_t v[4][kTileRecs];
         auto load = [&](uint64_t t0) {
             const uint32_t n = (uint32_t)min((uint64_t)kTile, e0 - t0);
 #pragma unroll
@@ -147,8 +148,7 @@ __global__ void __launch_bounds__(kPartThreads)
                 v[0][u] = ok ? __ldcs(p.src + i) : 0u;
                 v[1][u] = ok ? __ldcs(p.pkts + i) : 0u;
                 v[2][u] = ok ? __ldcs(p.oct + i) : 0u;
-                v[3][u] = ok ? __ldcs(p.first + i) : 0u;
-                v[4][u] = ok ? __ldcs(p.last + i) : 0u;
+                v[3][u] = ok ? __ldcs(p.last + i) - __ldcs(p.first + i) : 0u;  // duration
             }
         };
         if (max(wd.begin, lo) < e0) load(max(wd.begin, lo));
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kPartThreads)
                     const uint32_t pos = toff[grp[u]] + rk[u];
                     s_rec[pos] = v[0][u] - grp[u] * rows;
 #pragma unroll
-                    for (int f = 1; f < 5; ++f) s_rec[f * kTile + pos] = v[f][u];
+                    for (int f = 1; f < 4; ++f) s_rec[f * kTile + pos] = v[f][u];
                     s_grp[pos] = grp[u];
                 }
             }
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kPartThreads)
                 const uint32_t r = gpos[g] + (j - toff[g]);
                 if (!chk(p.check_err, r < stride, kChkPosition, r)) continue;
 #pragma unroll
-                for (int f = 0; f < 5; ++f) o[f][r] = s_rec[f * kTile + j];
+                for (int f = 0; f < 4; ++f) o[f][r] = s_rec[f * kTile + j];
             }
             __syncthreads();
         }
@@ -313,7 +313,7 @@ cudaError_t launch_part_scatter(const AggParams& p, const LaunchShape& s, uint32
                                 cudaStream_t st) {
     const uint64_t chunk = (p.n_total + s.part_grid - 1) / s.part_grid;
     static OptInCache granted;
-    const int bytes = (int)((6 * kTile + 3 * s.part_groups) * 4);
+    const int bytes = (int)((5 * kTile + 3 * s.part_groups) * 4);
     cudaError_t e = ensure_smem_optin((const void*)k_part_scatter, bytes, granted);
     if (e != cudaSuccess) return e;
     (void)cudaGetLastError();

@@ -186,8 +186,9 @@ def test_c2_hour_batched_bitexact(gnm, c2hour, cfg):
     plan = ctx.plan(d, off, ids)  # the benchmark's path: a CUDA graph of one launch
     plan.launch()
     # fused: one kernel; split: keys + sums; 10,004 keys: a grid-wide finalisation after them;
-    # partitioned: keys, count, scan, scatter, sums, finalisation
-    n_kernels = 6 if cfg.get("table_mode") == "PARTITION" else (1 if cfg.get("split") == "FUSED" else 2) + 1
+    # partitioned: keys (which also count the records of each bucket), scan, scatter, sums,
+    # finalisation
+    n_kernels = 5 if cfg.get("table_mode") == "PARTITION" else (1 if cfg.get("split") == "FUSED" else 2) + 1
     assert ctx.last_launch_count() == n_kernels
     for w in range(60):
         assert_window_matches(ctx.dense(int(ids[w])), expect[w])
