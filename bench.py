@@ -264,7 +264,16 @@ def window_c1(gnm, torch, local, reps=1000):
                           "least and greatest rate"}
 
 
-def batched_c4(gnm, torch, local, steps, warmup):
+AGGREGATIONS = {"auto": 0, "direct": 1, "warp": 2}  # gnm_aggregation
+
+
+def agg_times(tune):
+    """The autotuner's fastest candidate per aggregation: per-lane shared-memory atomics
+    (direct) against one atomic per distinct key of a warp (warp)."""
+    return {"direct": round(tune.best_ms_by_agg[1], 4) or None, "warp": round(tune.best_ms_by_agg[2], 4) or None}
+
+
+def batched_c4(gnm, torch, local, steps, warmup, aggregation=0):
     """256 uneven windows (lognormal sizes around 200,000 records, clamped to 10,000-2,000,000)
     over the 500-site registry in one CUDA-graph launch, shape autotuned by the library."""
     import flowgen as fg
@@ -274,7 +283,7 @@ def batched_c4(gnm, torch, local, steps, warmup):
     n, n_win = int(off[-1]), len(off) - 1
     dev = gnm.Records.to_device(rec)
     del rec
-    ctx = gnm.Context(device=local, window_slots=n_win + 8)
+    ctx = gnm.Context(device=local, window_slots=n_win + 8, aggregation=aggregation)
     ctx.load(reg)
     ids = np.arange(n_win, dtype=np.uint64)
     tune = ctx.autotune(dev, off, ids)
@@ -307,7 +316,8 @@ def batched_c4(gnm, torch, local, steps, warmup):
             "peak_kind": peak_kind, "kernels_ms": kms,
             "tuned": {"block_threads": tune.block_threads, "unroll": tune.unroll, "aggregation": tune.aggregation,
                       "radix_bits": tune.radix_bits,
-                      "placement": tune.placement, "ctas_per_sm": tune.ctas_per_sm}}
+                      "placement": tune.placement, "ctas_per_sm": tune.ctas_per_sm,
+                      "best_ms_by_aggregation": agg_times(tune)}}
 
 
 def serve_c5(gnm, torch, local, speedup=1000.0, realtime_minutes=10, pool_n=20_000_000, budget=4 << 30,
@@ -615,6 +625,8 @@ def main():
                     help="run one leg alone (profiling): the learned-index comparison, the server replay "
                          "or the batched windows")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-window batched launch")
+    ap.add_argument("--aggregation", default="auto", choices=list(AGGREGATIONS),
+                    help="per-key reduction of the hour and batched workloads (auto: the autotuner's choice)")
     ap.add_argument("--learned-records", type=int, default=50_000_000)
     ap.add_argument("--learned-modes", default="bsearch,radix,rmi,rmi_mse,rmi65536")
     ap.add_argument("--serve-speedup", type=float, default=1000.0,
@@ -638,7 +650,7 @@ def main():
             leg = learned_vs_plain(gnm, torch, local, args.steps, args.warmup, args.learned_records,
                                    tuple(args.learned_modes.split(",")))
         elif args.only == "batched":
-            leg = batched_c4(gnm, torch, local, args.steps, args.warmup)
+            leg = batched_c4(gnm, torch, local, args.steps, args.warmup, AGGREGATIONS[args.aggregation])
         elif args.only == "window":
             leg = window_c1(gnm, torch, local)
         elif args.only == "paper":
@@ -651,7 +663,7 @@ def main():
     rec, off = fg.hour_records_c2(reg, seed=1 + rank)
     n = int(off[-1])
     n_win = len(off) - 1
-    ctx = gnm.Context(device=local, window_slots=2 * n_win + 8)
+    ctx = gnm.Context(device=local, window_slots=2 * n_win + 8, aggregation=AGGREGATIONS[args.aggregation])
     ctx.load(reg)
     dev = gnm.Records.to_device(rec)
     ids = np.arange(n_win, dtype=np.uint64)
@@ -752,7 +764,7 @@ def main():
                              "unroll": tune.unroll, "aggregation": tune.aggregation, "placement": tune.placement,
                              "radix_bits": tune.radix_bits, "split": tune.split, "key_directory": tune.key_directory, "keys_unroll": tune.keys_unroll,
                              "default_ms": round(tune.default_ms, 4), "tuned_ms": round(tune.best_ms, 4),
-                             "candidates": tune.n_tried}},
+                             "best_ms_by_aggregation": agg_times(tune), "candidates": tune.n_tried}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                      "traffic_ratio": (traffic / kern_bytes[top]) if traffic else None,
@@ -813,7 +825,7 @@ def main():
     if world == 1 and not args.no_batched:
         out["window"] = window_c1(gnm, torch, local)
         out["paper_lookup"] = paper_lookup(gnm, torch, local, args.steps, args.warmup)
-        out["batched"] = batched_c4(gnm, torch, local, args.steps, args.warmup)
+        out["batched"] = batched_c4(gnm, torch, local, args.steps, args.warmup, AGGREGATIONS[args.aggregation])
     if world == 1 and not args.no_serve:
         out["serving"] = serve_c5(gnm, torch, local, speedup=args.serve_speedup,
                                   realtime_minutes=args.serve_realtime_minutes)

@@ -509,6 +509,10 @@ typedef struct {
     int32_t split;
     int32_t key_directory;
     int32_t keys_unroll;      /* key kernel: groups of 4 records per thread and step */
+    /* the fastest candidate of each aggregation (index GNM_AGG_DIRECT, GNM_AGG_WARP; 0 where
+     * none of that aggregation ran): per-lane shared-memory atomics against one atomic per
+     * distinct key of a warp after __match_any_sync */
+    double best_ms_by_agg[3];
 } gnm_tune_report;
 
 /* Times candidate launch shapes (block size, CTAs per SM, records per thread,

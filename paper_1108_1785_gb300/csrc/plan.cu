@@ -265,6 +265,10 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
                             double ms;
                             status = time_cfg(&ms);
                             rep->n_tried++;
+                            {
+                                double& ba = rep->best_ms_by_agg[c->cfg.aggregation == GNM_AGG_WARP ? 2 : 1];
+                                if (status == GNM_OK && (ba == 0.0 || ms < ba)) ba = ms;
+                            }
                             if (status == GNM_OK && ms < rep->best_ms) {
                                 rep->best_ms = ms;
                                 rep->block_threads = c->cfg.block_threads;

@@ -116,7 +116,8 @@ class TuneReport(C.Structure):
     _fields_ = [("block_threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("unroll", C.c_int32),
                 ("aggregation", C.c_int32), ("placement", C.c_int32), ("best_ms", C.c_double),
                 ("default_ms", C.c_double), ("n_tried", C.c_uint32), ("radix_bits", C.c_uint32),
-                ("split", C.c_int32), ("key_directory", C.c_int32), ("keys_unroll", C.c_int32)]
+                ("split", C.c_int32), ("key_directory", C.c_int32), ("keys_unroll", C.c_int32),
+                ("best_ms_by_agg", C.c_double * 3)]
 
 
 _lib = None
