@@ -125,11 +125,13 @@ def learned_vs_plain(gnm, torch, local, steps, warmup, n_records=50_000_000,
             plan.launch(stream)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")
         a.record(stream)
         for _ in range(steps):
             plan.launch(stream)
         b.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         ms = a.elapsed_time(b) / steps
         per = []
         for _ in range(3):  # per-kernel split of a launch
