@@ -269,6 +269,15 @@ def window_c1(gnm, torch, local, reps=1000):
 AGGREGATIONS = {"auto": 0, "direct": 1, "warp": 2}  # gnm_aggregation
 
 
+def parse_shape(text):
+    """'k=v,k=v' -> {k: int(v)} (context config fields of a fixed launch shape)."""
+    out = {}
+    for item in filter(None, (t.strip() for t in text.split(","))):
+        k, v = item.split("=")
+        out[k.strip()] = int(v)
+    return out
+
+
 def agg_times(tune):
     """The autotuner's fastest candidate per aggregation: per-lane shared-memory atomics
     (direct) against one atomic per distinct key of a warp (warp)."""
@@ -629,6 +638,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-window batched launch")
     ap.add_argument("--aggregation", default="auto", choices=list(AGGREGATIONS),
                     help="per-key reduction of the hour and batched workloads (auto: the autotuner's choice)")
+    ap.add_argument("--shape", default="",
+                    help="launch shape of the hour workload instead of autotuning it, as context config "
+                         "fields (e.g. block_threads=1024,unroll=1,radix_bits=13,split=2,key_directory=3): "
+                         "profiles then capture the kernels the plain run timed")
     ap.add_argument("--learned-records", type=int, default=50_000_000)
     ap.add_argument("--learned-modes", default="bsearch,radix,rmi,rmi_mse,rmi65536")
     ap.add_argument("--serve-speedup", type=float, default=1000.0,
@@ -665,13 +678,16 @@ def main():
     rec, off = fg.hour_records_c2(reg, seed=1 + rank)
     n = int(off[-1])
     n_win = len(off) - 1
-    ctx = gnm.Context(device=local, window_slots=2 * n_win + 8, aggregation=AGGREGATIONS[args.aggregation])
+    shape = parse_shape(args.shape)
+    ctx = gnm.Context(device=local, window_slots=2 * n_win + 8,
+                      **{"aggregation": AGGREGATIONS[args.aggregation], **shape})
     ctx.load(reg)
     dev = gnm.Records.to_device(rec)
     ids = np.arange(n_win, dtype=np.uint64)
     # the library's own autotuner picks block size, records per thread, aggregation and
-    # registry placement on this workload (outside the timed region)
-    tune = ctx.autotune(dev, off, ids)
+    # registry placement on this workload (outside the timed region), unless the launch
+    # shape is given
+    tune = None if shape else ctx.autotune(dev, off, ids)
     info = ctx.registry_info()
     plan = ctx.plan(dev, off, ids)
     stream = torch.cuda.current_stream()
@@ -682,7 +698,7 @@ def main():
     launches = 0
     # the clock samples (every 200 ms) cover the timed steps plus about 0.5 s of identical
     # untimed steps on each side of them, so that they see the GPU under this load
-    pad = int(min(20000, max(1, 500.0 / max(tune.best_ms, 1e-3))))
+    pad = int(min(20000, max(1, 500.0 / max(tune.best_ms if tune else 0.2, 1e-3))))
     with ClockSampler(local) as clk:
         for _ in range(pad):
             plan.launch(stream)
@@ -764,9 +780,11 @@ def main():
                              f"CUDA graph per step: {launches // max(1, args.steps)} kernel launch(es)",
                    "tuned": {"block_threads": tune.block_threads, "ctas_per_sm": tune.ctas_per_sm,
                              "unroll": tune.unroll, "aggregation": tune.aggregation, "placement": tune.placement,
-                             "radix_bits": tune.radix_bits, "split": tune.split, "key_directory": tune.key_directory, "keys_unroll": tune.keys_unroll,
+                             "radix_bits": tune.radix_bits, "split": tune.split, "key_directory": tune.key_directory,
+                             "keys_unroll": tune.keys_unroll,
                              "default_ms": round(tune.default_ms, 4), "tuned_ms": round(tune.best_ms, 4),
-                             "best_ms_by_aggregation": agg_times(tune), "candidates": tune.n_tried}},
+                             "best_ms_by_aggregation": agg_times(tune), "candidates": tune.n_tried}
+                   if tune else {"fixed": shape}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                      "traffic_ratio": (traffic / kern_bytes[top]) if traffic else None,

@@ -560,12 +560,8 @@ __device__ __forceinline__ bool add_wrap64(uint32_t* lo, uint64_t* g, uint64_t v
 struct Smem {
     uint32_t key_base;  // keys of the current segment are relative to it (partitioned launches)
     uint8_t* dirty;     // the window's dirty marks of 32-key accumulator groups, or null
-    uint32_t* hist;     // rate statistics of the current window, offset by key_base (or null)
-    unsigned long long* rmin;
-    unsigned long long* rmax;
-    uint32_t* rlog;     // sparse rate statistics of the current window (or null): its log,
-    uint32_t* rlog_cnt; // the words appended so far
-    uint32_t rlog_cap;  // and the log's capacity in words
+    uint32_t slot;      // the window's result slot (its rate statistics are found from it:
+                        // kept out of registers, they cost the hot loop nothing when off)
     uint32_t* t;        // table rows (kRowWords words each)
     uint32_t* tk;       // hash keys
     uint32_t rows;      // table rows
@@ -1104,24 +1100,26 @@ __device__ __forceinline__ Item classify_key(const AggParams& p, bool valid, uin
 // histogram) of one eligible record of key `key`: bucket = min(10000, floor(4 o / (5 d))),
 // rate = o * 8000 / d in FP64 (one rounding per operation). Rates are >= 0, so their bit
 // patterns order like the values; a read first skips the atomics that cannot change them.
-__device__ __forceinline__ void rate_stat_add(const Smem& sm, uint32_t key, uint32_t oc, uint32_t dur) {
+static __device__ __noinline__ void rate_stat_add(const AggParams& p, const Smem& sm, uint32_t key, uint32_t oc,
+                                                     uint32_t dur) {
     const uint64_t b = ((uint64_t)oc * 4u) / ((uint64_t)dur * 5u);
     const uint32_t bucket = b < 10000u ? (uint32_t)b : 10000u;
-    if (sm.rlog) {
+    const size_t k = (size_t)sm.slot * 2u * p.n_sites + sm.key_base + key;  // the key's statistics row
+    if (p.rlog) {
         // sparse: append (key << 14 | bucket) to the window's log, one counter atomic per
         // group of lanes that arrive together (the host reserved a word per record)
         const cooperative_groups::coalesced_group g = cooperative_groups::coalesced_threads();
         uint32_t base = 0;
-        if (g.thread_rank() == 0) base = atomicAdd(sm.rlog_cnt, g.size());
+        if (g.thread_rank() == 0) base = atomicAdd(p.rlog_cnt + sm.slot, g.size());
         base = g.shfl(base, 0) + g.thread_rank();
-        if (base < sm.rlog_cap) sm.rlog[base] = ((sm.key_base + key) << 14) | bucket;
+        if (base < p.rlog_cap[sm.slot]) p.rlog[sm.slot][base] = ((sm.key_base + key) << 14) | bucket;
     } else {
-        atomicAdd(sm.hist + (size_t)key * kRateBuckets + bucket, 1u);
+        atomicAdd(p.hist + k * kRateBuckets + bucket, 1u);
     }
     const double r = __ddiv_rn(__dmul_rn(__uint2double_rn(oc), 8000.0), __uint2double_rn(dur));
     const unsigned long long bits = (unsigned long long)__double_as_longlong(r);
-    if (bits > __ldcg(sm.rmax + key)) atomicMax(sm.rmax + key, bits);
-    if (bits < __ldcg(sm.rmin + key)) atomicMin(sm.rmin + key, bits);
+    if (bits > __ldcg(p.rmax + k)) atomicMax(p.rmax + k, bits);
+    if (bits < __ldcg(p.rmin + k)) atomicMin(p.rmin + k, bits);
 }
 
 // Processes R records per thread: lookups for all of them first (independent loads in
@@ -1144,10 +1142,10 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
                 its[j].valid = its[j].valid && chk(p.check_err, its[j].key < key_lim, kChkKey, its[j].key);
             }
             srow_add_all<R>(sm, its, gacc);
-            if (sm.hist || sm.rlog) {
+            if (p.hist || p.rlog) {
 #pragma unroll
                 for (int j = 0; j < R; ++j)
-                    if (its[j].valid && its[j].elig) rate_stat_add(sm, its[j].key, its[j].oc, its[j].dur);
+                    if (its[j].valid && its[j].elig) rate_stat_add(p, sm, its[j].key, its[j].oc, its[j].dur);
             }
         } else {
 #pragma unroll
@@ -1155,7 +1153,7 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
                 Item it = classify_key(p, valid[j], src[j], sm.key_base, pk[j], oc[j], fi[j], la[j]);
                 it.valid = it.valid && chk(p.check_err, it.key < key_lim, kChkKey, it.key);
                 accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
-                if ((sm.hist || sm.rlog) && it.valid && it.elig) rate_stat_add(sm, it.key, it.oc, it.dur);
+                if ((p.hist || p.rlog) && it.valid && it.elig) rate_stat_add(p, sm, it.key, it.oc, it.dur);
             }
         }
     } else {
@@ -1175,10 +1173,10 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
                 its[j].valid = its[j].valid && chk(p.check_err, its[j].key < key_lim, kChkKey, its[j].key);
             }
             srow_add_all<R>(sm, its, gacc);
-            if (sm.hist || sm.rlog) {
+            if (p.hist || p.rlog) {
 #pragma unroll
                 for (int j = 0; j < R; ++j)
-                    if (its[j].valid && its[j].elig) rate_stat_add(sm, its[j].key, its[j].oc, its[j].dur);
+                    if (its[j].valid && its[j].elig) rate_stat_add(p, sm, its[j].key, its[j].oc, its[j].dur);
             }
         } else {
 #pragma unroll
@@ -1186,14 +1184,15 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
                 Item it = classify(p, valid[j], sl[j], dl[j], pk[j], oc[j], fi[j], la[j], site[j]);
                 it.valid = it.valid && chk(p.check_err, it.key < key_lim, kChkKey, it.key);
                 accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
-                if ((sm.hist || sm.rlog) && it.valid && it.elig) rate_stat_add(sm, it.key, it.oc, it.dur);
+                if ((p.hist || p.rlog) && it.valid && it.elig) rate_stat_add(p, sm, it.key, it.oc, it.dur);
             }
         }
     }
 }
 
 // Records [lo, hi) one per thread and slot (head/tail of a window, or unaligned arrays).
-template <int LOOKUP, int TABLE, int AGG>
+// FIRST: the records carry First; without it (regrouped records) `last` holds the duration.
+template <int LOOKUP, int TABLE, int AGG, bool FIRST>
 __device__ __forceinline__ void scalar_range(const AggParams& p, const Smem& sm, uint64_t* gacc,
                                              uint64_t lo, uint64_t hi) {
     const uint32_t B = blockDim.x;
@@ -1209,7 +1208,7 @@ __device__ __forceinline__ void scalar_range(const AggParams& p, const Smem& sm,
             d[j] = LOOKUP == kLookupKeys ? 0u : ld_stream1(p.dst + ii);
             pk[j] = ld_stream1(p.pkts + ii);
             oc[j] = ld_stream1(p.oct + ii);
-            fi[j] = p.first ? ld_stream1(p.first + ii) : 0u;
+            fi[j] = !FIRST ? 0u : p.first ? ld_stream1(p.first + ii) : 0u;
             la[j] = ld_stream1(p.last + ii);
         }
         process<LOOKUP, TABLE, AGG, 4>(p, sm, gacc, v, s, d, pk, oc, fi, la);
@@ -1217,7 +1216,7 @@ __device__ __forceinline__ void scalar_range(const AggParams& p, const Smem& sm,
 }
 
 // Records [a0, a0 + 4*G): G aligned groups of four, 16-byte vector loads.
-template <int LOOKUP, int TABLE, int AGG, int U>
+template <int LOOKUP, int TABLE, int AGG, int U, bool FIRST>
 __device__ __forceinline__ void vector_range(const AggParams& p, const Smem& sm, uint64_t* gacc,
                                              uint64_t a0, uint64_t G) {
     constexpr int R = 4 * U;
@@ -1233,8 +1232,7 @@ __device__ __forceinline__ void vector_range(const AggParams& p, const Smem& sm,
             const uint4 vs = ld_stream4(p.src + i);
             const uint4 vd = LOOKUP == kLookupKeys ? make_uint4(0, 0, 0, 0) : ld_stream4(p.dst + i);
             const uint4 vp = ld_stream4(p.pkts + i), vo = ld_stream4(p.oct + i);
-            // (regrouped records hold the duration in `last` and no `first`)
-            const uint4 vf = p.first ? ld_stream4(p.first + i) : make_uint4(0, 0, 0, 0);
+            const uint4 vf = FIRST && p.first ? ld_stream4(p.first + i) : make_uint4(0, 0, 0, 0);
             const uint4 vl = ld_stream4(p.last + i);
             s[4 * u + 0] = vs.x; s[4 * u + 1] = vs.y; s[4 * u + 2] = vs.z; s[4 * u + 3] = vs.w;
             d[4 * u + 0] = vd.x; d[4 * u + 1] = vd.y; d[4 * u + 2] = vd.z; d[4 * u + 3] = vd.w;
@@ -1363,12 +1361,7 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
     Smem sm;
     sm.key_base = 0u;
     sm.dirty = nullptr;
-    sm.hist = nullptr;
-    sm.rmin = nullptr;
-    sm.rmax = nullptr;
-    sm.rlog = nullptr;
-    sm.rlog_cnt = nullptr;
-    sm.rlog_cap = 0u;
+    sm.slot = 0u;
     sm.rows = TABLE == kTableDirect ? p.table_rows : (TABLE == kTableHash ? p.table_cap : 0u);
     sm.t = reinterpret_cast<uint32_t*>(smem_raw);
     sm.tk = reinterpret_cast<uint32_t*>(smem_raw + off_keys);
@@ -1387,19 +1380,7 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
         uint64_t* gacc = p.acc + ((size_t)wd.slot * p.keys + wd.key_base) * kAccCols;
         sm.key_base = wd.key_base;
         sm.dirty = p.dirty ? p.dirty + (size_t)wd.slot * p.dirty_groups : nullptr;
-        if (p.hist) {
-            const size_t k0 = (size_t)wd.slot * 2u * p.n_sites + wd.key_base;
-            sm.hist = p.hist + k0 * kRateBuckets;
-            sm.rmin = p.rmin + k0;
-            sm.rmax = p.rmax + k0;
-        } else if (p.rlog) {
-            const size_t k0 = (size_t)wd.slot * 2u * p.n_sites + wd.key_base;
-            sm.rlog = p.rlog[wd.slot];
-            sm.rlog_cnt = p.rlog_cnt + wd.slot;
-            sm.rlog_cap = p.rlog_cap[wd.slot];
-            sm.rmin = p.rmin + k0;
-            sm.rmax = p.rmax + k0;
-        }
+        sm.slot = wd.slot;
         // pieces of at most kFlushRecords records, so the 16-bit counts cannot wrap. With a
         // partial-sum area the CTA's segment of the window ends in one block of its own
         // (block q = the CTA's position among the window's CTAs), and the pieces before
@@ -1414,9 +1395,11 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
                 a0 = mis ? min(s + (4u - mis), e) : s;
                 a1 = a0 + ((e - a0) & ~3ull);
             }
-            scalar_range<LOOKUP, TABLE, AGG>(p, sm, gacc, s, a0);
-            if (a1 > a0) vector_range<LOOKUP, TABLE, AGG, U>(p, sm, gacc, a0, (a1 - a0) >> 2);
-            scalar_range<LOOKUP, TABLE, AGG>(p, sm, gacc, a1, e);
+            // (regrouped records, read by key launches only, hold the duration in `last`
+            // and no `first`)
+            scalar_range<LOOKUP, TABLE, AGG, true>(p, sm, gacc, s, a0);
+            if (a1 > a0) vector_range<LOOKUP, TABLE, AGG, U, true>(p, sm, gacc, a0, (a1 - a0) >> 2);
+            scalar_range<LOOKUP, TABLE, AGG, true>(p, sm, gacc, a1, e);
             if (TABLE != kTableGlobal) {
                 __syncthreads();
                 if (TABLE == kTableDirect && p.partials) {
@@ -1471,12 +1454,7 @@ __global__ void __launch_bounds__(keys_block_max(LOOKUP, U)) k_keys(const __grid
     Smem sm;
     sm.key_base = 0u;
     sm.dirty = nullptr;
-    sm.hist = nullptr;
-    sm.rmin = nullptr;
-    sm.rmax = nullptr;
-    sm.rlog = nullptr;
-    sm.rlog_cnt = nullptr;
-    sm.rlog_cap = 0u;
+    sm.slot = 0u;
     sm.t = nullptr;
     sm.tk = nullptr;
     sm.rows = 0;

@@ -229,10 +229,10 @@ __host__ __device__ constexpr int keys_block_max(int lookup, int unroll) {
 constexpr uint32_t kBlockRanges = 16;  // ranges per staged block (16 starts, 64 bytes)
 enum { kTableDirect = 0, kTableHash = 1, kTableGlobal = 2 };
 
-// Largest block of the aggregation kernel: two groups of 4 records per thread fit 64
-// registers (1024 threads) only when it reads precomputed keys into a direct table.
+// Largest block of the aggregation kernel: two groups of 4 records per thread (40 words
+// of records in flight per thread) take more than the 64 registers of 1024-thread blocks.
 __host__ __device__ constexpr int agg_block_max(int lookup, int table, int agg, int unroll) {
-    return (unroll == 1 || (lookup == kLookupKeys && table == kTableDirect && agg == GNM_AGG_DIRECT)) ? 1024 : 512;
+    return (void)lookup, (void)table, (void)agg, unroll == 1 ? 1024 : 512;
 }
 
 // Launch shape chosen by the host.
