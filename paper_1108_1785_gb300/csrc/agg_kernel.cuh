@@ -1125,7 +1125,7 @@ static __device__ __noinline__ void rate_stat_add(const AggParams& p, const Smem
 // Processes R records per thread: lookups for all of them first (independent loads in
 // flight together), then classification and accumulation. With LOOKUP == kLookupKeys the
 // `src` field carries each record's precomputed key instead of an address.
-template <int LOOKUP, int TABLE, int AGG, int R>
+template <int LOOKUP, int TABLE, int AGG, int R, bool STATS>
 __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint64_t* gacc,
                                         const bool (&valid)[R], const uint32_t (&src)[R],
                                         const uint32_t (&dst)[R], const uint32_t (&pk)[R],
@@ -1142,7 +1142,7 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
                 its[j].valid = its[j].valid && chk(p.check_err, its[j].key < key_lim, kChkKey, its[j].key);
             }
             srow_add_all<R>(sm, its, gacc);
-            if (p.hist || p.rlog) {
+            if (STATS && (p.hist || p.rlog)) {
 #pragma unroll
                 for (int j = 0; j < R; ++j)
                     if (its[j].valid && its[j].elig) rate_stat_add(p, sm, its[j].key, its[j].oc, its[j].dur);
@@ -1153,7 +1153,7 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
                 Item it = classify_key(p, valid[j], src[j], sm.key_base, pk[j], oc[j], fi[j], la[j]);
                 it.valid = it.valid && chk(p.check_err, it.key < key_lim, kChkKey, it.key);
                 accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
-                if ((p.hist || p.rlog) && it.valid && it.elig) rate_stat_add(p, sm, it.key, it.oc, it.dur);
+                if (STATS && (p.hist || p.rlog) && it.valid && it.elig) rate_stat_add(p, sm, it.key, it.oc, it.dur);
             }
         }
     } else {
@@ -1173,7 +1173,7 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
                 its[j].valid = its[j].valid && chk(p.check_err, its[j].key < key_lim, kChkKey, its[j].key);
             }
             srow_add_all<R>(sm, its, gacc);
-            if (p.hist || p.rlog) {
+            if (STATS && (p.hist || p.rlog)) {
 #pragma unroll
                 for (int j = 0; j < R; ++j)
                     if (its[j].valid && its[j].elig) rate_stat_add(p, sm, its[j].key, its[j].oc, its[j].dur);
@@ -1184,15 +1184,17 @@ __device__ __forceinline__ void process(const AggParams& p, const Smem& sm, uint
                 Item it = classify(p, valid[j], sl[j], dl[j], pk[j], oc[j], fi[j], la[j], site[j]);
                 it.valid = it.valid && chk(p.check_err, it.key < key_lim, kChkKey, it.key);
                 accumulate<TABLE, AGG>(it, sm, p.table_cap, gacc);
-                if ((p.hist || p.rlog) && it.valid && it.elig) rate_stat_add(p, sm, it.key, it.oc, it.dur);
+                if (STATS && (p.hist || p.rlog) && it.valid && it.elig) rate_stat_add(p, sm, it.key, it.oc, it.dur);
             }
         }
     }
 }
 
 // Records [lo, hi) one per thread and slot (head/tail of a window, or unaligned arrays).
-// FIRST: the records carry First; without it (regrouped records) `last` holds the duration.
-template <int LOOKUP, int TABLE, int AGG, bool FIRST>
+// STATS: the launch may keep per-flow rate statistics (when false, their code is left out:
+// the hot loop then needs fewer registers). Regrouped records (no `first`) hold the
+// duration in `last`.
+template <int LOOKUP, int TABLE, int AGG, bool STATS>
 __device__ __forceinline__ void scalar_range(const AggParams& p, const Smem& sm, uint64_t* gacc,
                                              uint64_t lo, uint64_t hi) {
     const uint32_t B = blockDim.x;
@@ -1208,15 +1210,15 @@ __device__ __forceinline__ void scalar_range(const AggParams& p, const Smem& sm,
             d[j] = LOOKUP == kLookupKeys ? 0u : ld_stream1(p.dst + ii);
             pk[j] = ld_stream1(p.pkts + ii);
             oc[j] = ld_stream1(p.oct + ii);
-            fi[j] = !FIRST ? 0u : p.first ? ld_stream1(p.first + ii) : 0u;
+            fi[j] = p.first ? ld_stream1(p.first + ii) : 0u;
             la[j] = ld_stream1(p.last + ii);
         }
-        process<LOOKUP, TABLE, AGG, 4>(p, sm, gacc, v, s, d, pk, oc, fi, la);
+        process<LOOKUP, TABLE, AGG, 4, STATS>(p, sm, gacc, v, s, d, pk, oc, fi, la);
     }
 }
 
 // Records [a0, a0 + 4*G): G aligned groups of four, 16-byte vector loads.
-template <int LOOKUP, int TABLE, int AGG, int U, bool FIRST>
+template <int LOOKUP, int TABLE, int AGG, int U, bool STATS>
 __device__ __forceinline__ void vector_range(const AggParams& p, const Smem& sm, uint64_t* gacc,
                                              uint64_t a0, uint64_t G) {
     constexpr int R = 4 * U;
@@ -1232,7 +1234,7 @@ __device__ __forceinline__ void vector_range(const AggParams& p, const Smem& sm,
             const uint4 vs = ld_stream4(p.src + i);
             const uint4 vd = LOOKUP == kLookupKeys ? make_uint4(0, 0, 0, 0) : ld_stream4(p.dst + i);
             const uint4 vp = ld_stream4(p.pkts + i), vo = ld_stream4(p.oct + i);
-            const uint4 vf = FIRST && p.first ? ld_stream4(p.first + i) : make_uint4(0, 0, 0, 0);
+            const uint4 vf = p.first ? ld_stream4(p.first + i) : make_uint4(0, 0, 0, 0);
             const uint4 vl = ld_stream4(p.last + i);
             s[4 * u + 0] = vs.x; s[4 * u + 1] = vs.y; s[4 * u + 2] = vs.z; s[4 * u + 3] = vs.w;
             d[4 * u + 0] = vd.x; d[4 * u + 1] = vd.y; d[4 * u + 2] = vd.z; d[4 * u + 3] = vd.w;
@@ -1243,7 +1245,7 @@ __device__ __forceinline__ void vector_range(const AggParams& p, const Smem& sm,
 #pragma unroll
             for (int j = 0; j < 4; ++j) v[4 * u + j] = ok;
         }
-        process<LOOKUP, TABLE, AGG, R>(p, sm, gacc, v, s, d, pk, oc, fi, la);
+        process<LOOKUP, TABLE, AGG, R, STATS>(p, sm, gacc, v, s, d, pk, oc, fi, la);
     }
 }
 
@@ -1343,7 +1345,7 @@ __device__ __forceinline__ void stage_lookup(const AggParams& p, unsigned char* 
     }
 }
 
-template <int LOOKUP, int TABLE, int AGG, int U>
+template <int LOOKUP, int TABLE, int AGG, int U, bool STATS = true>
 __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
     k_aggregate(const __grid_constant__ AggParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1397,9 +1399,9 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
             }
             // (regrouped records, read by key launches only, hold the duration in `last`
             // and no `first`)
-            scalar_range<LOOKUP, TABLE, AGG, true>(p, sm, gacc, s, a0);
-            if (a1 > a0) vector_range<LOOKUP, TABLE, AGG, U, true>(p, sm, gacc, a0, (a1 - a0) >> 2);
-            scalar_range<LOOKUP, TABLE, AGG, true>(p, sm, gacc, a1, e);
+            scalar_range<LOOKUP, TABLE, AGG, STATS>(p, sm, gacc, s, a0);
+            if (a1 > a0) vector_range<LOOKUP, TABLE, AGG, U, STATS>(p, sm, gacc, a0, (a1 - a0) >> 2);
+            scalar_range<LOOKUP, TABLE, AGG, STATS>(p, sm, gacc, a1, e);
             if (TABLE != kTableGlobal) {
                 __syncthreads();
                 if (TABLE == kTableDirect && p.partials) {
@@ -1587,6 +1589,10 @@ cudaError_t launch_keys_impl(const AggParams& p, const LaunchShape& s, uint32_t*
 template <int LOOKUP, int TABLE, int AGG, int U>
 cudaError_t launch_variant(const AggParams& p, const LaunchShape& s, cudaStream_t st) {
     auto k = k_aggregate<LOOKUP, TABLE, AGG, U>;
+    // key launches without rate statistics (the hour workload, the regrouped window) take the
+    // variant without their code
+    if constexpr (LOOKUP == kLookupKeys)
+        if (!p.hist && !p.rlog) k = k_aggregate<LOOKUP, TABLE, AGG, U, false>;
     static OptInCache granted;
     cudaError_t e = ensure_smem_optin((const void*)k, (int)s.smem, granted);
     if (e != cudaSuccess) return e;
