@@ -1589,12 +1589,16 @@ cudaError_t launch_keys_impl(const AggParams& p, const LaunchShape& s, uint32_t*
 template <int LOOKUP, int TABLE, int AGG, int U>
 cudaError_t launch_variant(const AggParams& p, const LaunchShape& s, cudaStream_t st) {
     auto k = k_aggregate<LOOKUP, TABLE, AGG, U>;
+    static OptInCache granted, granted_plain;  // one per kernel
+    OptInCache* g = &granted;
     // key launches without rate statistics (the hour workload, the regrouped window) take the
     // variant without their code
     if constexpr (LOOKUP == kLookupKeys)
-        if (!p.hist && !p.rlog) k = k_aggregate<LOOKUP, TABLE, AGG, U, false>;
-    static OptInCache granted;
-    cudaError_t e = ensure_smem_optin((const void*)k, (int)s.smem, granted);
+        if (!p.hist && !p.rlog) {
+            k = k_aggregate<LOOKUP, TABLE, AGG, U, false>;
+            g = &granted_plain;
+        }
+    cudaError_t e = ensure_smem_optin((const void*)k, (int)s.smem, *g);
     if (e != cudaSuccess) return e;
     (void)cudaGetLastError();  // report this launch's error only
     k<<<s.grid, s.block, s.smem, st>>>(p);
