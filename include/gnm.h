@@ -107,7 +107,9 @@ typedef struct {
     int32_t block_threads;      /* 0: tuned default; else 128..1024, multiple of 32 */
     int32_t ctas_per_sm;        /* 0: tuned default; else 1..8 */
     int32_t unroll;             /* 0: tuned default; else 1 or 2 (4-record groups per
-                                   thread per iteration) */
+                                   thread per iteration), or 3: one group, the next
+                                   group's loads issued before this one is processed
+                                   (split launches with direct tables; else 1) */
     int32_t table_mode;         /* GNM_TABLE_*: where a CTA accumulates its sums */
     uint32_t hash_slots;        /* GNM_TABLE_HASH size: 0 = largest that fits, else an
                                    even number in 256..65536 */

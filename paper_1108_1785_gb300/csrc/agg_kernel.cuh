@@ -1218,9 +1218,42 @@ __device__ __forceinline__ void scalar_range(const AggParams& p, const Smem& sm,
 }
 
 // Records [a0, a0 + 4*G): G aligned groups of four, 16-byte vector loads.
+//   U = 1, 2: U groups per thread and step, loaded together, then processed.
+//   U = 3 (key launches): one group per thread and step; the next step's group is loaded
+//   before this one is processed, so its memory latency overlaps the table atomics.
 template <int LOOKUP, int TABLE, int AGG, int U, bool STATS>
 __device__ __forceinline__ void vector_range(const AggParams& p, const Smem& sm, uint64_t* gacc,
                                              uint64_t a0, uint64_t G) {
+    if constexpr (U == 3) {
+        static_assert(LOOKUP == kLookupKeys, "pipelined groups read precomputed keys");
+        const uint32_t B = blockDim.x;
+        // lanes past the end load group 0 again (in bounds) and process nothing
+        auto load = [&](uint64_t g, uint4& k, uint4& pk4, uint4& oc4, uint4& fi4, uint4& la4) {
+            const uint64_t i = a0 + 4u * (g < G ? g : 0u);
+            k = ld_stream4(p.src + i);
+            pk4 = ld_stream4(p.pkts + i);
+            oc4 = ld_stream4(p.oct + i);
+            fi4 = p.first ? ld_stream4(p.first + i) : make_uint4(0, 0, 0, 0);
+            la4 = ld_stream4(p.last + i);
+        };
+        uint4 ck, cp, co, cf, cl;
+        load(threadIdx.x, ck, cp, co, cf, cl);
+        for (uint64_t gb = 0; gb < G; gb += B) {  // uniform loop
+            uint4 nk, np, no, nf, nl;
+            load(gb + B + threadIdx.x, nk, np, no, nf, nl);
+            const bool ok = gb + threadIdx.x < G;
+            const bool v[4] = {ok, ok, ok, ok};
+            const uint32_t s[4] = {ck.x, ck.y, ck.z, ck.w}, d[4] = {0u, 0u, 0u, 0u};
+            const uint32_t pk[4] = {cp.x, cp.y, cp.z, cp.w}, oc[4] = {co.x, co.y, co.z, co.w};
+            const uint32_t fi[4] = {cf.x, cf.y, cf.z, cf.w}, la[4] = {cl.x, cl.y, cl.z, cl.w};
+            process<LOOKUP, TABLE, AGG, 4, STATS>(p, sm, gacc, v, s, d, pk, oc, fi, la);
+            ck = nk;
+            cp = np;
+            co = no;
+            cf = nf;
+            cl = nl;
+        }
+    } else {
     constexpr int R = 4 * U;
     const uint32_t B = blockDim.x;
     for (uint64_t gb = 0; gb < G; gb += (uint64_t)B * U) {  // uniform loop
@@ -1246,6 +1279,7 @@ __device__ __forceinline__ void vector_range(const AggParams& p, const Smem& sm,
             for (int j = 0; j < 4; ++j) v[4 * u + j] = ok;
         }
         process<LOOKUP, TABLE, AGG, R, STATS>(p, sm, gacc, v, s, d, pk, oc, fi, la);
+    }
     }
 }
 
@@ -1611,6 +1645,8 @@ cudaError_t launch_table(const AggParams& p, const LaunchShape& s, cudaStream_t 
         return s.unroll == 2 ? launch_variant<LOOKUP, TABLE, GNM_AGG_WARP, 2>(p, s, st)
                              : launch_variant<LOOKUP, TABLE, GNM_AGG_WARP, 1>(p, s, st);
     }
+    if constexpr (LOOKUP == kLookupKeys && TABLE == kTableDirect)
+        if (s.unroll == 3) return launch_variant<LOOKUP, TABLE, GNM_AGG_DIRECT, 3>(p, s, st);
     return s.unroll == 2 ? launch_variant<LOOKUP, TABLE, GNM_AGG_DIRECT, 2>(p, s, st)
                          : launch_variant<LOOKUP, TABLE, GNM_AGG_DIRECT, 1>(p, s, st);
 }

@@ -462,8 +462,9 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s, size_t n_win) {
     int block = cfg.block_threads ? cfg.block_threads : (c->tuned.block ? c->tuned.block : 1024);
     int unroll = cfg.unroll ? cfg.unroll : (c->tuned.unroll ? c->tuned.unroll : 1);
     if (block < 64 || block > 1024 || block % 32) return fail(GNM_E_INVAL, "block_threads must be 64..1024, multiple of 32");
-    if (unroll != 1 && unroll != 2) return fail(GNM_E_INVAL, "unroll must be 1 or 2");
-    if (unroll == 2 && block > agg_block_max(s->split ? kLookupKeys : s->lookup, s->table, s->agg, 2)) unroll = 1;
+    if (unroll < 1 || unroll > 3) return fail(GNM_E_INVAL, "unroll must be 1, 2 or 3");
+    if (unroll == 3 && !(s->split && s->table == kTableDirect && s->agg == GNM_AGG_DIRECT)) unroll = 1;
+    if (unroll > 1 && block > agg_block_max(s->split ? kLookupKeys : s->lookup, s->table, s->agg, unroll)) unroll = 1;
     s->block = block;
     s->unroll = unroll;
     s->smem = aggregate_smem_bytes(s->split ? kLookupKeys : s->lookup, s->table, nr, rows, cap,

@@ -230,9 +230,10 @@ constexpr uint32_t kBlockRanges = 16;  // ranges per staged block (16 starts, 64
 enum { kTableDirect = 0, kTableHash = 1, kTableGlobal = 2 };
 
 // Largest block of the aggregation kernel: two groups of 4 records per thread (40 words
-// of records in flight per thread) take more than the 64 registers of 1024-thread blocks.
+// of records in flight per thread) take more than the 64 registers of 1024-thread blocks;
+// a group in flight while the previous one is processed (unroll 3) fits 80 registers.
 __host__ __device__ constexpr int agg_block_max(int lookup, int table, int agg, int unroll) {
-    return (void)lookup, (void)table, (void)agg, unroll == 1 ? 1024 : 512;
+    return (void)lookup, (void)table, (void)agg, unroll == 1 ? 1024 : unroll == 3 ? 768 : 512;
 }
 
 // Launch shape chosen by the host.

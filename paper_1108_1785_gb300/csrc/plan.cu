@@ -202,8 +202,8 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
     std::memset(rep, 0, sizeof(*rep));
     gnm_status status = time_cfg(&rep->default_ms);
     rep->best_ms = 1e30;
-    const int blocks[] = {256, 512, 1024};
-    const int unrolls[] = {1, 2};
+    const int blocks[] = {256, 512, 768, 1024};
+    const int unrolls[] = {1, 2, 3};
     const int aggs[] = {GNM_AGG_DIRECT, GNM_AGG_WARP};
     const int places[] = {GNM_PLACE_SMEM, GNM_PLACE_STAGED, GNM_PLACE_L2};
     // the lookup method decides which knob matters: placement (binary search) or
@@ -243,7 +243,12 @@ gnm_status gnm_autotune(gnm_ctx* c, const gnm_records* rec, const uint64_t* offs
                     for (int rb : bits_v)
                         for (int cps : cpss) {
                             if (status != GNM_OK) break;
-                            if (u == 2 && b > 512 && !(sp == GNM_SPLIT_TWO_KERNELS && a == GNM_AGG_DIRECT)) continue;
+                            // two groups per thread: up to 512 threads; pipelined groups (3):
+                            // split launches with direct aggregation, up to 768 threads; 768
+                            // threads for pipelined groups only
+                            if (u == 2 && b > 512) continue;
+                            if (u == 3 && (b > 768 || sp != GNM_SPLIT_TWO_KERNELS || a != GNM_AGG_DIRECT)) continue;
+                            if (b == 768 && u != 3) continue;
                             c->cfg = saved;
                             if (c->cfg.block_threads == 0) c->cfg.block_threads = b;
                             if (c->cfg.unroll == 0) c->cfg.unroll = u;

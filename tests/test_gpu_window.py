@@ -78,7 +78,7 @@ SPLITS = ["AUTO", "TWO_KERNELS"]
 @pytest.mark.parametrize("table", ["DIRECT", "HASH", "GLOBAL"])
 @pytest.mark.parametrize("agg", ["DIRECT", "WARP"])
 @pytest.mark.parametrize("lookup", LOOKUPS, ids=lambda l: f"{l[0]}-{l[1]}-{l[2]}")
-@pytest.mark.parametrize("unroll,block", [(1, 256), (2, 512), (1, 1024)])
+@pytest.mark.parametrize("unroll,block", [(1, 256), (2, 512), (1, 1024), (3, 768)])
 @pytest.mark.parametrize("split", SPLITS)
 def test_c1_window_all_variants(gnm, c1, table, agg, lookup, unroll, block, split):
     reg, rec, expect = c1
@@ -165,7 +165,8 @@ def c2hour():
                                  {"aggregation": "WARP"}, {"hash_slots": 1024}, {"table_mode": "GLOBAL"},
                                  {"radix_bits": 12, "split": "FUSED"}, {"table_mode": "HASH", "unroll": 2,
                                                                           "block_threads": 512},
-                                 {"table_mode": "PARTITION"}])
+                                 {"table_mode": "PARTITION"}, {"unroll": 3, "block_threads": 768},
+                                 {"unroll": 3, "block_threads": 256}, {"table_mode": "PARTITION", "unroll": 3}])
 def test_c2_hour_batched_bitexact(gnm, c2hour, cfg):
     """Sixty one-minute windows (10M records, nested registry) in one launch -- the
     benchmark's workload and, with cfg {}, its launch configuration; every window equals
