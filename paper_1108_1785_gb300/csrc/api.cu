@@ -459,8 +459,11 @@ gnm_status choose_shape(gnm_ctx* c, uint64_t n, LaunchShape* s, size_t n_win) {
     }
     int agg = cfg.aggregation != GNM_AGG_AUTO ? cfg.aggregation : c->tuned.agg;
     s->agg = agg == GNM_AGG_WARP ? GNM_AGG_WARP : GNM_AGG_DIRECT;
-    int block = cfg.block_threads ? cfg.block_threads : (c->tuned.block ? c->tuned.block : 1024);
-    int unroll = cfg.unroll ? cfg.unroll : (c->tuned.unroll ? c->tuned.unroll : 1);
+    // untuned defaults: 1024 threads, one group of four records per thread and step; split
+    // launches into direct tables: 512 threads with the next group in flight (unroll 3)
+    const bool piped = s->split && s->table == kTableDirect && s->agg == GNM_AGG_DIRECT && !cfg.unroll;
+    int block = cfg.block_threads ? cfg.block_threads : (c->tuned.block ? c->tuned.block : (piped ? 512 : 1024));
+    int unroll = cfg.unroll ? cfg.unroll : (c->tuned.unroll ? c->tuned.unroll : (piped && block <= 768 ? 3 : 1));
     if (block < 64 || block > 1024 || block % 32) return fail(GNM_E_INVAL, "block_threads must be 64..1024, multiple of 32");
     if (unroll < 1 || unroll > 3) return fail(GNM_E_INVAL, "unroll must be 1, 2 or 3");
     if (unroll == 3 && !(s->split && s->table == kTableDirect && s->agg == GNM_AGG_DIRECT)) unroll = 1;
