@@ -356,6 +356,19 @@ gnm_status gnm_windows_results(gnm_ctx *ctx, const uint64_t *window_ids, size_t 
                                uint64_t *stats, uint64_t *unmatched, double *rate,
                                uint8_t *flag);
 
+/* gnm_windows_results enqueued on cuda_stream (a cudaStream_t; NULL: the legacy default
+ * stream), without waiting. The copies start after each window's last processing. The next
+ * processing of these windows (or of the slots they hold) waits for the copies, so results of
+ * one batch of windows can be read while another batch is processed. The host arrays are
+ * read once the stream is synchronised; they should be page-locked, or the copies are not
+ * asynchronous. stats, rate and flag are laid out as in gnm_windows_results. unmatched6
+ * holds the unmatched rows as stored: window k's class c in unmatched6[(k*4 + c)*GNM_NSTAT
+ * ...], words 0..2 its flows, octets and packets (those gnm_windows_results reports). Errors
+ * found by the checked build's device checks surface at the next synchronising call. */
+gnm_status gnm_windows_results_async(gnm_ctx *ctx, const uint64_t *window_ids, size_t n,
+                                     uint64_t *stats, uint64_t *unmatched6, double *rate,
+                                     uint8_t *flag, void *cuda_stream);
+
 /* Device addresses of a window's dense results (same layouts as gnm_window_dense; the
  * stats block has 2*n_sites+4 rows, the last four being the unmatched classes with
  * e_* columns zero). Valid until the slot is reused or the registry is replaced. No

@@ -1657,44 +1657,68 @@ gnm_status gnm_window_dense(gnm_ctx* c, uint64_t wid, uint64_t* stats, uint64_t*
     return device_checks(c);
 }
 
-gnm_status gnm_windows_results(gnm_ctx* c, const uint64_t* wids, size_t n, uint64_t* stats,
-                               uint64_t* unmatched, double* rate, uint8_t* flag) {
-    if (!c || (n && !wids)) return fail(GNM_E_INVAL, "NULL argument");
-    GNM_CU(cudaSetDevice(c->device));
+// Enqueues on st the copies of windows' results (after each window's last processing):
+// stats, the unmatched rows as stored (un6: kUnmatched x kNStat words per window), rates
+// and flags; any of them may be null.
+static gnm_status enqueue_results(gnm_ctx* c, const uint64_t* wids, size_t n, uint64_t* stats, uint64_t* un6,
+                                  double* rate, uint8_t* flag, cudaStream_t st, std::vector<uint32_t>& slot) {
     const size_t nk = 2 * (size_t)c->n_sites;
-    std::vector<uint32_t> slot(n);
+    slot.resize(n);
     for (size_t k = 0; k < n; ++k) {
         GNM_TRY(find_window(c, wids[k], &slot[k]));
         if (!c->slots[slot[k]].finalized) return fail(GNM_E_STATE, "window is open (not finalised)");
-        GNM_TRY(wait_slot_on_stream(c, slot[k], c->aux));
+        GNM_TRY(wait_slot_on_stream(c, slot[k], st));
     }
-    std::vector<uint64_t> un6(unmatched ? n * kUnmatched * kNStat : 0);
     for (size_t k = 0; k < n;) {
         // windows k..k+m-1 in consecutive slots: one copy per array for the run (rates and
         // flags are contiguous across slots; stats rows carry the unmatched rows between)
         size_t m = 1;
         while (k + m < n && slot[k + m] == slot[k] + m) ++m;
         const uint32_t s = slot[k];
-        if (rate) GNM_CU(cudaMemcpyAsync(rate + k * nk, c->d_rate + (size_t)s * nk, m * nk * 8, cudaMemcpyDeviceToHost, c->aux));
-        if (flag) GNM_CU(cudaMemcpyAsync(flag + k * nk, c->d_flag + (size_t)s * nk, m * nk, cudaMemcpyDeviceToHost, c->aux));
+        if (rate) GNM_CU(cudaMemcpyAsync(rate + k * nk, c->d_rate + (size_t)s * nk, m * nk * 8, cudaMemcpyDeviceToHost, st));
+        if (flag) GNM_CU(cudaMemcpyAsync(flag + k * nk, c->d_flag + (size_t)s * nk, m * nk, cudaMemcpyDeviceToHost, st));
         // stats: the run's windows are rows of keys * GNM_NSTAT words, the site rows first
         // and the unmatched rows after them: one pitched copy for each part
-        const uint64_t* st = c->d_stats + (size_t)s * c->keys * kNStat;
+        const uint64_t* sp = c->d_stats + (size_t)s * c->keys * kNStat;
         const size_t pitch = (size_t)c->keys * kNStat * 8;
         if (stats)
-            GNM_CU(cudaMemcpy2DAsync(stats + k * nk * kNStat, nk * kNStat * 8, st, pitch, nk * kNStat * 8, m,
-                                     cudaMemcpyDeviceToHost, c->aux));
-        if (unmatched)
-            GNM_CU(cudaMemcpy2DAsync(un6.data() + k * kUnmatched * kNStat, kUnmatched * kNStat * 8, st + nk * kNStat,
-                                     pitch, kUnmatched * kNStat * 8, m, cudaMemcpyDeviceToHost, c->aux));
+            GNM_CU(cudaMemcpy2DAsync(stats + k * nk * kNStat, nk * kNStat * 8, sp, pitch, nk * kNStat * 8, m,
+                                     cudaMemcpyDeviceToHost, st));
+        if (un6)
+            GNM_CU(cudaMemcpy2DAsync(un6 + k * kUnmatched * kNStat, kUnmatched * kNStat * 8, sp + nk * kNStat,
+                                     pitch, kUnmatched * kNStat * 8, m, cudaMemcpyDeviceToHost, st));
         k += m;
     }
+    return GNM_OK;
+}
+
+gnm_status gnm_windows_results(gnm_ctx* c, const uint64_t* wids, size_t n, uint64_t* stats,
+                               uint64_t* unmatched, double* rate, uint8_t* flag) {
+    if (!c || (n && !wids)) return fail(GNM_E_INVAL, "NULL argument");
+    GNM_CU(cudaSetDevice(c->device));
+    std::vector<uint64_t> un6(unmatched ? n * kUnmatched * kNStat : 0);
+    std::vector<uint32_t> slot;
+    GNM_TRY(enqueue_results(c, wids, n, stats, unmatched ? un6.data() : nullptr, rate, flag, c->aux, slot));
     GNM_CU(cudaStreamSynchronize(c->aux));
     if (unmatched)
         for (size_t k = 0; k < n; ++k)
             for (int q = 0; q < kUnmatched; ++q)
                 for (int j = 0; j < 3; ++j) unmatched[(k * kUnmatched + q) * 3 + j] = un6[(k * kUnmatched + q) * kNStat + j];
     return device_checks(c);
+}
+
+gnm_status gnm_windows_results_async(gnm_ctx* c, const uint64_t* wids, size_t n, uint64_t* stats,
+                                     uint64_t* unmatched6, double* rate, uint8_t* flag, void* cuda_stream) {
+    if (!c || (n && !wids)) return fail(GNM_E_INVAL, "NULL argument");
+    GNM_CU(cudaSetDevice(c->device));
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    std::vector<uint32_t> slot;
+    GNM_TRY(enqueue_results(c, wids, n, stats, unmatched6, rate, flag, st, slot));
+    // the next work on these slots waits for the copies too
+    cudaEvent_t ev;
+    GNM_TRY(record_event(c, st, &ev));
+    for (uint32_t s : slot) c->slots[s].ev = ev;
+    return GNM_OK;
 }
 
 gnm_status gnm_window_device(gnm_ctx* c, uint64_t wid, const uint64_t** stats, const double** rate,

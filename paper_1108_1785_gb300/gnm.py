@@ -159,6 +159,7 @@ def lib():
             "gnm_window_dense": (st, [P, U64, P, P, P, P]),
             "gnm_window_device": (st, [P, U64, C.POINTER(P), C.POINTER(P), C.POINTER(P)]),
             "gnm_windows_results": (st, [P, P, S, P, P, P, P]),
+            "gnm_windows_results_async": (st, [P, P, S, P, P, P, P, P]),
             "gnm_window_release": (st, [P, U64]),
             "gnm_lookup": (st, [P, P, U64, P, P, P]),
             "gnm_rmi_config_default": (None, [C.POINTER(RmiConfig)]),
@@ -415,6 +416,14 @@ class Context:
         ids = np.ascontiguousarray(window_ids, np.uint64)
         self._c(lib().gnm_windows_results(self.h, _ptr(ids), ids.size, _ptr(stats), _ptr(unmatched), _ptr(rate),
                                           _ptr(flag)))
+
+    def windows_results_async(self, window_ids, stats=None, unmatched6=None, rate=None, flag=None, stream=None):
+        """gnm_windows_results_async: the copies enqueued on `stream` (default: torch's
+        current stream); the host arrays (page-locked) are valid after it synchronises.
+        unmatched6: [n][4][NSTAT] u64, the unmatched rows as stored."""
+        ids = np.ascontiguousarray(window_ids, np.uint64)
+        self._c(lib().gnm_windows_results_async(self.h, _ptr(ids), ids.size, _ptr(stats), _ptr(unmatched6),
+                                                _ptr(rate), _ptr(flag), _stream_ptr(stream)))
 
     def device_checks(self) -> int:
         """The checked build's error word since the last call (0: no failed bounds check);

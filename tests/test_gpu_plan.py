@@ -113,6 +113,46 @@ def test_windows_results_batch_readout(gnm, batch):
     ctx.close()
 
 
+def test_windows_results_async_overlaps_processing(gnm, batch):
+    """Asynchronous readouts on a second stream while the other set of windows is processed:
+    two sets of window ids, each reprocessed with a different batch (the windows in reverse
+    order) while the copy of its previous results may still run. Every copy holds the
+    results of the batch processed just before it (the reprocessing waits for the copy)."""
+    reg, rec, off, expect = batch
+    W = len(off) - 1
+    # the same windows in reverse order
+    order = np.arange(W)[::-1]
+    rec_r = {k: np.concatenate([v[off[w]:off[w + 1]] for w in order]) for k, v in rec.items()}
+    off_r = np.concatenate([[0], np.cumsum([off[w + 1] - off[w] for w in order])]).astype(np.int64)
+    batches = [(rec, off, expect), (rec_r, off_r, [expect[w] for w in order])]
+    dev = [gnm.Records.to_device(b[0]) for b in batches]
+    ctx = gnm.Context(window_slots=2 * W + 4)
+    ctx.load(reg)
+    nk = 2 * reg.n_sites
+    sets = [np.arange(W) + 5000, np.arange(W) + 6000]
+    proc, copy = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def pinned(shape, dt):
+        t = torch.empty(int(np.prod(shape)) * np.dtype(dt).itemsize, dtype=torch.uint8).pin_memory()
+        return t.numpy().view(dt).reshape(shape)
+
+    steps = 6
+    outs = [(pinned((W, nk, 6), np.uint64), pinned((W, 4, 6), np.uint64), pinned((W, nk), np.float64),
+             pinned((W, nk), np.uint8)) for _ in range(steps)]
+    for k in range(steps):
+        b = (k // 2) % 2  # set k % 2 gets batch 0, 0, 1, 1, 0, 0 ...: each set alternates
+        ctx.process_windows(dev[b], batches[b][1], sets[k % 2], proc)
+        ctx.windows_results_async(sets[k % 2], *outs[k], stream=copy)
+    copy.synchronize()
+    proc.synchronize()
+    for k in range(steps):
+        b = (k // 2) % 2
+        st, un6, r, f = outs[k]
+        for w in range(W):
+            assert_window_matches((st[w], un6[w][:, :3], r[w], f[w]), batches[b][2][w])
+    ctx.close()
+
+
 @pytest.mark.parametrize("which", ["c1", "c2"])
 def test_plan_kernel_times(gnm, which):
     """A plan made with kernel timing names its kernels in launch order, each with a positive
