@@ -600,7 +600,7 @@ typedef struct {
     uint64_t records;             /* submitted */
     uint64_t windows_closed;
     uint64_t windows_done;
-    uint64_t inflight_bytes;      /* now */
+    uint64_t inflight_bytes;      /* now: admitted batches not yet finished on the GPU */
     uint64_t peak_inflight_bytes; /* never above budget_bytes */
     double p50_ms, p99_ms, max_ms, mean_ms;  /* window latency over the windows done */
 } gnm_stream_stats;

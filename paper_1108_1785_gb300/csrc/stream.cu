@@ -569,6 +569,11 @@ gnm_status gnm_stream_poll(gnm_stream* s, gnm_window_done* out, size_t cap, size
 
 gnm_status gnm_stream_stats_get(gnm_stream* s, gnm_stream_stats* out) {
     if (!s || !out) return fail(GNM_E_INVAL, "NULL argument");
+    // batches that finished since the last call are retired first, so that the figures
+    // are those of now (a window can be reported done by its callback before the poll that
+    // reported it had seen its last batch finish)
+    GNM_CU(cudaSetDevice(s->c->device));
+    GNM_TRY(retire(s));
     *out = s->st;
     out->inflight_bytes = s->inflight_bytes;
     const auto& v = s->latencies_ms;
