@@ -266,6 +266,11 @@ def window_c1(gnm, torch, local, reps=1000):
                           "least and greatest rate"}
 
 
+E2E_HOST = {"auto": "read in place by the kernels over the host link",
+            "in_place": "read in place by the kernels over the host link",
+            "stage": "copied to a device staging buffer, then processed",
+            "pipeline": "chunks of windows copied on a second stream, each processed as soon as it "
+                        "has landed"}
 AGGREGATIONS = {"auto": 0, "direct": 1, "warp": 2}  # gnm_aggregation
 
 
@@ -642,6 +647,9 @@ def main():
                     help="launch shape of the hour workload instead of autotuning it, as context config "
                          "fields (e.g. block_threads=1024,unroll=1,radix_bits=13,split=2,key_directory=3): "
                          "profiles then capture the kernels the plain run timed")
+    ap.add_argument("--e2e-host", default="pipeline", choices=["auto", "stage", "in_place", "pipeline"],
+                    help="how the end-to-end leg's page-locked host records reach the kernels "
+                         "(gnm_config.host_records)")
     ap.add_argument("--learned-records", type=int, default=50_000_000)
     ap.add_argument("--learned-modes", default="bsearch,radix,rmi,rmi_mse,rmi65536")
     ap.add_argument("--serve-speedup", type=float, default=1000.0,
@@ -680,7 +688,8 @@ def main():
     n_win = len(off) - 1
     shape = parse_shape(args.shape)
     ctx = gnm.Context(device=local, window_slots=2 * n_win + 8,
-                      **{"aggregation": AGGREGATIONS[args.aggregation], **shape})
+                      **{"aggregation": AGGREGATIONS[args.aggregation],
+                         "host_records": getattr(gnm, "HOST_" + args.e2e_host.upper()), **shape})
     ctx.load(reg)
     dev = gnm.Records.to_device(rec)
     ids = np.arange(n_win, dtype=np.uint64)
@@ -833,10 +842,10 @@ def main():
         e2e_s = max_over_ranks(time.perf_counter() - t0, world)
         out["e2e"] = {"value": n * world * args.steps / e2e_s, "unit": "records/s",
                       "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": n_win * (nk * (48 + 8 + 1) + 4 * 48),
-                      "api": "gnm_windows_process over page-locked host records (read in place by the kernels "
-                             "over the host link) + gnm_windows_results_async (sums, unmatched classes, rates, "
-                             "flags) on a second stream, overlapping the next step's processing; two sets of "
-                             "window ids alternate"}
+                      "api": "gnm_windows_process over page-locked host records (host_records "
+                             f"{args.e2e_host.upper()}: " + E2E_HOST[args.e2e_host] + ") + "
+                             "gnm_windows_results_async (sums, unmatched classes, rates, flags) on a second "
+                             "stream, overlapping the next step's processing; two sets of window ids alternate"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1

@@ -148,8 +148,14 @@ typedef struct {
 /* Host records: AUTO reads them in place when every array is page-locked host memory that
  * the device can address (cudaHostAlloc / cudaHostRegister; the kernels then read it over
  * the host link, with no staging copy), else STAGE; STAGE copies them to a device staging
- * buffer first; IN_PLACE requires addressable page-locked arrays (GNM_E_INVAL otherwise). */
-enum { GNM_HOST_AUTO = 0, GNM_HOST_STAGE = 1, GNM_HOST_IN_PLACE = 2 };
+ * buffer first; IN_PLACE requires addressable page-locked arrays (GNM_E_INVAL otherwise).
+ * PIPELINE (gnm_windows_process of two or more windows): the windows are split into chunks
+ * of consecutive windows (about an eighth of the records each, at least 1M records), each
+ * chunk is copied to one of two device buffer sets on a stream of the context's own, and
+ * processed on the caller's stream as soon as its copy has landed, so that copying a chunk
+ * overlaps processing the one before it (for page-locked arrays, the fastest way over a
+ * host link that copies faster than kernels read through it); other calls stage as STAGE. */
+enum { GNM_HOST_AUTO = 0, GNM_HOST_STAGE = 1, GNM_HOST_IN_PLACE = 2, GNM_HOST_PIPELINE = 3 };
 
 /* One struct-of-arrays batch of NetFlow v5 fields (Sec. IV.A.3: 48-byte v5 records; only
  * the six fields below are read). Element i of every array is record i. Device arrays

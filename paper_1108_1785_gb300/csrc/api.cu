@@ -212,7 +212,7 @@ gnm_status acquire_ring(gnm_ctx* c, uint32_t n_win, LaunchBuf** out) {
 // device (the runtime reports a device address for it). out[k]: the device address of
 // field k's element `base`.
 static bool host_addressable(gnm_ctx* c, const gnm_records* rec, uint64_t base, const uint32_t* out[6]) {
-    if (c->cfg.host_records == GNM_HOST_STAGE) return false;
+    if (c->cfg.host_records == GNM_HOST_STAGE || c->cfg.host_records == GNM_HOST_PIPELINE) return false;
     const uint32_t* f[6] = {rec->srcaddr, rec->dstaddr, rec->dPkts, rec->dOctets, rec->first, rec->last};
     for (int k = 0; k < 6; ++k) {
         cudaPointerAttributes a;
@@ -857,12 +857,79 @@ gnm_status enqueue_prepared(gnm_ctx* c, Prepared& pr, const uint64_t* offsets, s
 
 // Core of every processing call: windows k = [offsets[k], offsets[k+1]) of rec.
 // finalize: rates and flags at the end; open_add: add to already open windows.
+// GNM_HOST_PIPELINE: chunks of consecutive windows copied to two alternating device buffer
+// sets on the context's copy stream, each processed on st once its copy has landed; a
+// buffer set is refilled only after the processing that read it.
+static gnm_status run_windows_pipelined(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets,
+                                        const uint64_t* wids, size_t n_win, cudaStream_t st, bool finalize) {
+    const uint64_t N = offsets[n_win] - offsets[0];
+    const uint64_t target = std::max<uint64_t>(N / 8, (uint64_t)1 << 20);
+    std::vector<size_t> cut{0};  // chunk k holds windows cut[k] .. cut[k+1]-1
+    for (size_t w = 1; w <= n_win; ++w)
+        if (w == n_win || offsets[w] - offsets[cut.back()] >= target) cut.push_back(w);
+    {
+        std::vector<uint64_t> ids(wids, wids + n_win);
+        std::sort(ids.begin(), ids.end());
+        if (std::adjacent_find(ids.begin(), ids.end()) != ids.end())
+            return fail(GNM_E_INVAL, "duplicate window id in one call");
+    }
+    uint64_t most = 0;
+    for (size_t k = 0; k + 1 < cut.size(); ++k) most = std::max(most, offsets[cut[k + 1]] - offsets[cut[k]]);
+    PipeStaging& ps = c->pipe;
+    if (!ps.copy) {
+        GNM_CU(cudaStreamCreateWithFlags(&ps.copy, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            GNM_CU(cudaEventCreateWithFlags(&ps.copied[b], cudaEventDisableTiming));
+            GNM_CU(cudaEventCreateWithFlags(&ps.freed[b], cudaEventDisableTiming));
+        }
+    }
+    if (ps.cap < most) {  // grow both sets once the work that reads them is done
+        GNM_CU(cudaStreamSynchronize(ps.copy));
+        for (int b = 0; b < 2; ++b)
+            if (ps.freed_recorded[b]) GNM_CU(cudaEventSynchronize(ps.freed[b]));
+        for (auto& set : ps.d)
+            for (auto& p : set) {
+                free_dev(p);
+                p = nullptr;
+            }
+        ps.cap = 0;
+        for (auto& set : ps.d)
+            for (auto& p : set) GNM_CU(cudaMalloc(&p, most * 4));
+        ps.cap = most;
+    }
+    const uint32_t* src[6] = {rec->srcaddr, rec->dstaddr, rec->dPkts, rec->dOctets, rec->first, rec->last};
+    std::vector<uint64_t> off;
+    for (size_t k = 0; k + 1 < cut.size(); ++k) {
+        const int b = (int)(k & 1);
+        const uint64_t lo = offsets[cut[k]], n = offsets[cut[k + 1]] - lo;
+        if (ps.freed_recorded[b]) GNM_CU(cudaStreamWaitEvent(ps.copy, ps.freed[b], 0));
+        for (int f = 0; f < 6; ++f)
+            if (n) GNM_CU(cudaMemcpyAsync(ps.d[b][f], src[f] + lo, n * 4, cudaMemcpyHostToDevice, ps.copy));
+        GNM_CU(cudaEventRecord(ps.copied[b], ps.copy));
+        GNM_CU(cudaStreamWaitEvent(st, ps.copied[b], 0));
+        gnm_records dk = *rec;
+        dk.n = n;
+        dk.srcaddr = ps.d[b][0]; dk.dstaddr = ps.d[b][1]; dk.dPkts = ps.d[b][2];
+        dk.dOctets = ps.d[b][3]; dk.first = ps.d[b][4]; dk.last = ps.d[b][5];
+        dk.on_device = 1;
+        off.assign(offsets + cut[k], offsets + cut[k + 1] + 1);
+        for (auto& o : off) o -= lo;
+        GNM_TRY(run_windows(c, &dk, off.data(), wids + cut[k], cut[k + 1] - cut[k], st, finalize, false));
+        GNM_CU(cudaEventRecord(ps.freed[b], st));
+        ps.freed_recorded[b] = true;
+    }
+    return GNM_OK;
+}
+
 gnm_status run_windows(gnm_ctx* c, const gnm_records* rec, const uint64_t* offsets,
                        const uint64_t* wids, size_t n_win, cudaStream_t st, bool finalize,
                        bool open_add) {
     if (n_win == 0) return GNM_OK;
     if (!wids) return fail(GNM_E_INVAL, "window ids are NULL");
     GNM_TRY(check_windows(c, rec, offsets, n_win));
+    if (!rec->on_device && c->cfg.host_records == GNM_HOST_PIPELINE && !open_add && n_win > 1 &&
+        offsets[n_win] > offsets[0])
+        return run_windows_pipelined(c, rec, offsets, wids, n_win, st, finalize);
     const uint64_t base = offsets[0], N = offsets[n_win] - offsets[0];
     gnm_records dr = *rec;
     const uint32_t* inplace[6];
@@ -1043,9 +1110,9 @@ gnm_status gnm_create(const gnm_config* cfg, gnm_ctx** out) {
         return fail(GNM_E_INVAL, "admin_rule must be GNM_ADMIN_OR or GNM_ADMIN_AND");
     }
     if (c->cfg.window_slots == 0) c->cfg.window_slots = 64;
-    if (c->cfg.host_records < GNM_HOST_AUTO || c->cfg.host_records > GNM_HOST_IN_PLACE) {
+    if (c->cfg.host_records < GNM_HOST_AUTO || c->cfg.host_records > GNM_HOST_PIPELINE) {
         delete c;
-        return fail(GNM_E_INVAL, "host_records must be GNM_HOST_AUTO, _STAGE or _IN_PLACE");
+        return fail(GNM_E_INVAL, "host_records must be GNM_HOST_AUTO, _STAGE, _IN_PLACE or _PIPELINE");
     }
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -1102,6 +1169,13 @@ void gnm_destroy(gnm_ctx* c) {
     }
     for (auto* p : c->staging.d) free_dev(p);
     if (c->staging.ev) cudaEventDestroy(c->staging.ev);
+    for (auto& set : c->pipe.d)
+        for (auto* p : set) free_dev(p);
+    for (int b = 0; b < 2; ++b) {
+        if (c->pipe.copied[b]) cudaEventDestroy(c->pipe.copied[b]);
+        if (c->pipe.freed[b]) cudaEventDestroy(c->pipe.freed[b]);
+    }
+    if (c->pipe.copy) cudaStreamDestroy(c->pipe.copy);
     if (c->aux) cudaStreamDestroy(c->aux);
     free_dev(c->d_starts);
     free_dev(c->d_site);

@@ -70,6 +70,17 @@ struct Staging {
     bool ev_recorded = false;
 };
 
+// Pipelined staging of host records (GNM_HOST_PIPELINE): two buffer sets, the copy of one
+// chunk of windows on `copy` overlapping the processing of the previous chunk.
+struct PipeStaging {
+    uint32_t* d[2][6] = {};
+    uint64_t cap = 0;                       // records per buffer set
+    cudaStream_t copy = nullptr;            // non-blocking copy stream
+    cudaEvent_t copied[2] = {nullptr, nullptr};
+    cudaEvent_t freed[2] = {nullptr, nullptr};  // recorded on the processing stream after a chunk
+    bool freed_recorded[2] = {false, false};
+};
+
 struct Tuned {
     int block = 0, ctas_per_sm = 0, unroll = 0, agg = 0, placement = 0, split = 0, key_dir = 0, keys_unroll = 0;
     uint32_t radix_bits = 0;
@@ -146,6 +157,7 @@ struct gnm_ctx {
     std::vector<gnm::LaunchBuf> ring;
     uint32_t ring_next = 0;
     gnm::Staging staging;
+    gnm::PipeStaging pipe;
     unsigned long long* d_violations = nullptr;
     unsigned long long* d_check = nullptr;  // the checked build's error word (site << 56 | value)
     uint32_t* d_flag_keys = nullptr;

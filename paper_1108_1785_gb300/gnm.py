@@ -28,7 +28,7 @@ SPLIT_AUTO, SPLIT_FUSED, SPLIT_TWO_KERNELS = 0, 1, 2
 ROOT_LINEAR, ROOT_MLP = 0, 1
 FIT_MINIMAX, FIT_MSE = 0, 1
 DEBUG_RMI_SPLIT_BASE = 1
-HOST_AUTO, HOST_STAGE, HOST_IN_PLACE = 0, 1, 2
+HOST_AUTO, HOST_STAGE, HOST_IN_PLACE, HOST_PIPELINE = 0, 1, 2, 3
 RATE_BUCKETS = 10001
 NO_MEDIAN = 0xFFFFFFFF
 KERNEL_TIMES = 1  # GNM_PLAN_KERNEL_TIMES

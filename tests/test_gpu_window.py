@@ -392,6 +392,29 @@ def test_host_records_in_place_and_staged(gnm, c1, which):
         ctx.close()
 
 
+def test_host_records_pipelined(gnm):
+    """PIPELINE: 12 windows (4.2 M records, with an empty one) copied in chunks of at least
+    2^20 records to two alternating buffer sets while earlier chunks are processed; twice
+    in a row (the buffers are reused) and from pageable arrays: every window equals the
+    oracle."""
+    reg = fg.registry_c2()
+    rec = fg.make_records(reg, 4_200_000, seed=8)
+    off = [0] + [350_000 * (w + 1) for w in range(12)]
+    off[6] = off[5]  # window 5 empty
+    expect = [oracle_full(reg, {k: v[a:b] for k, v in rec.items()}) for a, b in zip(off[:-1], off[1:])]
+    pinned = gnm.Records({k: torch.from_numpy(np.ascontiguousarray(rec[k]).view(np.int32)).pin_memory()
+                          for k in gnm.FIELDS})
+    ctx = _ctx(gnm, reg, window_slots=32, host_records=gnm.HOST_PIPELINE)
+    for rep, recs in enumerate((pinned, pinned, gnm.Records.host(rec))):
+        ids = np.arange(12) + 100 * rep
+        ctx.process_windows(recs, off, ids)
+        for w in range(12):
+            assert_window_matches(ctx.dense(int(ids[w])), expect[w])
+    with pytest.raises(gnm.GnmError, match="duplicate"):
+        ctx.process_windows(pinned, off, [1] * 12)
+    ctx.close()
+
+
 def test_partition_needs_split_launches(gnm):
     reg = fg.registry_c2()
     ctx = _ctx(gnm, reg, table_mode=gnm.TABLE_PARTITION, split=gnm.SPLIT_FUSED)
