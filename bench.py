@@ -647,7 +647,7 @@ def main():
                     help="launch shape of the hour workload instead of autotuning it, as context config "
                          "fields (e.g. block_threads=1024,unroll=1,radix_bits=13,split=2,key_directory=3): "
                          "profiles then capture the kernels the plain run timed")
-    ap.add_argument("--e2e-host", default="pipeline", choices=["auto", "stage", "in_place", "pipeline"],
+    ap.add_argument("--e2e-host", default="auto", choices=["auto", "stage", "in_place", "pipeline"],
                     help="how the end-to-end leg's page-locked host records reach the kernels "
                          "(gnm_config.host_records)")
     ap.add_argument("--learned-records", type=int, default=50_000_000)
@@ -799,6 +799,9 @@ def main():
                      "traffic_ratio": (traffic / kern_bytes[top]) if traffic else None,
                      "kernel": top, "kernel_ms": kern_avg[top], "algorithmic_bytes": kern_bytes[top],
                      "kernels_ms": kern_avg,
+                     # every kernel of the step on its own method bytes (the key and aggregation
+                     # kernels take similar times, so either can be the dominant one in a run)
+                     "kernels_frac": {k: kern_bytes[k] / (kern_avg[k] / 1e3) / 1e9 / peak for k in kern_avg},
                      "kernel_timing": "CUDA events between the graph's kernels, K further launches",
                      "step": {"ms": step_ms, "algorithmic_bytes": alg_bytes, "achieved": step_gbs,
                               "frac": step_gbs / peak}},

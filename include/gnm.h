@@ -220,6 +220,18 @@ gnm_status gnm_registry_load(gnm_ctx *ctx, const uint32_t *prefix, const uint8_t
 
 gnm_status gnm_registry_info_get(gnm_ctx *ctx, gnm_registry_info *out);
 
+/* The rate step alone (Sec. III.B.1 and Sec. III.B.2.1: a site's transfer rate from its
+ * eligible flows' bytes and durations): rate[i] = (e_octets[i] * 8000) / e_dur_ms[i] in bits
+ * per second, each operand converted to binary64 and each operation rounded to nearest
+ * (ties to even), NaN when e_dur_ms[i] = 0 -- the same bits as the rates the window calls
+ * report, for sums gathered elsewhere (e.g. the sums of one site over several windows or
+ * GPUs). e_octets, e_dur_ms and rate are device arrays of n entries (8-byte aligned) on the
+ * current device, owned by the caller; the kernel is queued on cuda_stream (NULL: the legacy
+ * stream) and the call does not wait for it. No context is needed. GNM_E_INVAL for NULL or
+ * misaligned arrays (n = 0 accepts anything), GNM_E_CUDA when the launch fails. */
+gnm_status gnm_rates(const uint64_t *e_octets, const uint64_t *e_dur_ms, uint64_t n, double *rate,
+                     void *cuda_stream);
+
 /* Host-only form of the registry step (no context, no GPU): validates the registry as
  * gnm_registry_load does and writes the flattened ranges (see gnm_registry_ranges).
  * *n_out receives the number of ranges (GNM_E_CAPACITY if cap is smaller). */

@@ -815,6 +815,80 @@ __device__ __forceinline__ uint64_t f64_bits_times8000(uint64_t o) {
     return f64_bits_rn(m * 125u) + ((uint64_t)(k + 6) << 52);
 }
 
+// Bits of RN(a / b) for binary64 operands given as bits, a = 0 or normal, b normal and
+// positive, with a quotient in the normal range (here: 2^-64 < a / b < 2^1000), formed on the
+// integer and FP32 units (GB300 runs FP64 at 1/64 of the FP32 rate; a division per eligible
+// flow in the per-flow rate statistics is on the aggregation's hot path).
+// With a = ma * 2^ka and b = mb * 2^kb (53-bit significands ma, mb), the quotient's
+// significand is Q = floor(ma * 2^s / mb) with s = 52 when ma >= mb and 53 otherwise, so that
+// 2^52 <= Q < 2^53, and the remainder R decides the rounding (to nearest, ties to even) as in
+// schoolbook division: Q + 1 when 2R > mb, or 2R = mb and Q is odd. Q is found digit by digit
+// (10 bits a step, so R * 2^10 stays below 2^63); each digit is estimated from FP32 values
+// within one of the true digit and corrected with the exact integer remainder. A remainder
+// left outside [0, mb) would mean a digit more than one off; that case is reported (`ok`
+// false) and the caller uses the FP64 division instead, so the result is exact either way.
+__device__ __forceinline__ uint64_t f64_div_bits(uint64_t abits, uint64_t bbits, bool& ok) {
+    ok = true;
+    if (abits == 0) return 0;
+    constexpr uint64_t kFrac = (1ull << 52) - 1ull;
+    const uint64_t ma = (abits & kFrac) | (1ull << 52), mb = (bbits & kFrac) | (1ull << 52);
+    const int ea = (int)(abits >> 52), eb = (int)(bbits >> 52);
+    const bool ge = ma >= mb;
+    const int s = ge ? 52 : 53;
+    int64_t r = (int64_t)(ge ? ma - mb : ma);  // remainder, 0 <= r < mb
+    uint64_t q = ge ? 1u : 0u;                  // quotient digits so far
+    const int64_t d = (int64_t)mb;
+    const float rd = __frcp_rn(__ull2float_rn(mb));
+    bool bad = false;
+    // five digits of 10 bits, then one of s - 50 (2 or 3) bits
+    auto digit = [&](int c) {
+        const float est = __ull2float_rn((uint64_t)r) * rd * (float)(1u << c);
+        int64_t dig = (int64_t)min(__float2uint_rz(est), (1u << c) - 1u);
+        int64_t nr = (r << c) - dig * d;  // |nr| < 2^63: r < 2^53, dig < 2^10
+        if (nr < 0) {
+            --dig;
+            nr += d;
+        } else if (nr >= d) {
+            ++dig;
+            nr -= d;
+        }
+        bad |= nr < 0 || nr >= d;
+        q = (q << c) + (uint64_t)dig;
+        r = nr;
+    };
+#pragma unroll
+    for (int i = 0; i < 5; ++i) digit(10);
+    digit(s - 50);
+    if (bad) {
+        ok = false;
+        return 0;
+    }
+    const uint64_t r2 = (uint64_t)r << 1;
+    if (r2 > mb || (r2 == mb && (q & 1ull))) ++q;
+    int e = ea - eb - s + 52 + 1023;  // biased exponent of Q * 2^(ka - kb - s)
+    if (q == (1ull << 53)) {
+        q >>= 1;
+        ++e;
+    }
+    return ((uint64_t)e << 52) | (q & kFrac);
+}
+
+// The FP64 division of two operands given as bits (out of line: rarely taken).
+static __device__ __noinline__ double f64_div_fallback(uint64_t a, uint64_t b) {
+    return __ddiv_rn(__longlong_as_double((long long)a), __longlong_as_double((long long)b));
+}
+
+// Rate from eligible octets and milliseconds, (RN(eo) * 8000) / RN(ed) with one rounding per
+// operation (NaN when ed = 0): the conversions, the product and the division exact on the
+// integer units, with the FP64 division as the fallback of f64_div_bits.
+__device__ __forceinline__ double rate_of_sums(uint64_t eo, uint64_t ed) {
+    if (!ed) return __longlong_as_double(0x7FF8000000000000ll);
+    const uint64_t a = f64_bits_times8000(eo), b = f64_bits_rn(ed);
+    bool ok;
+    const uint64_t q = f64_div_bits(a, b, ok);
+    return ok ? __longlong_as_double((long long)q) : f64_div_fallback(a, b);
+}
+
 // Rates and flags of one window from its accumulators (Sec. III.B.1: rates per site;
 // a site is sub-optimal when its rate is below the standard). kL1: the sums were written
 // by an earlier kernel, so loads may go through L1; inside the aggregation kernel they
@@ -918,8 +992,9 @@ __device__ __forceinline__ void finalize_rows(const AggParams& p, uint32_t slot,
             sv[5] = ed;
             if (k < nk) {
                 // rate = (octets * 8 bits) / (ms / 1000), one rounding per operation; the
-                // conversions and the product are formed exactly on the integer units, so the
-                // division is the only FP64 operation
+                // conversions and the product are formed exactly on the integer units, the
+                // division is the FP64 one (f64_div_bits made this kernel slower: 20 -> 22 us
+                // on the hour, its FP64 divisions are not what bounds it)
                 const double r = ed ? __ddiv_rn(__longlong_as_double((long long)f64_bits_times8000(eo)),
                                                 __longlong_as_double((long long)f64_bits_rn(ed)))
                                     : __longlong_as_double(0x7FF8000000000000ll);
@@ -1098,7 +1173,7 @@ __device__ __forceinline__ Item classify_key(const AggParams& p, bool valid, uin
 
 // Per-flow rate statistics (Sec. III.B.2.1: minimum, maximum and the median's 10 kb/s
 // histogram) of one eligible record of key `key`: bucket = min(10000, floor(4 o / (5 d))),
-// rate = o * 8000 / d in FP64 (one rounding per operation). Rates are >= 0, so their bit
+// rate = o * 8000 / d as in FP64 (one rounding per operation). Rates are >= 0, so their bit
 // patterns order like the values; a read first skips the atomics that cannot change them.
 static __device__ __noinline__ void rate_stat_add(const AggParams& p, const Smem& sm, uint32_t key, uint32_t oc,
                                                      uint32_t dur) {
@@ -1116,7 +1191,7 @@ static __device__ __noinline__ void rate_stat_add(const AggParams& p, const Smem
     } else {
         atomicAdd(p.hist + k * kRateBuckets + bucket, 1u);
     }
-    const double r = __ddiv_rn(__dmul_rn(__uint2double_rn(oc), 8000.0), __uint2double_rn(dur));
+    const double r = rate_of_sums(oc, dur);  // (oc * 8000 is exact in FP64: below 2^45)
     const unsigned long long bits = (unsigned long long)__double_as_longlong(r);
     if (bits > __ldcg(p.rmax + k)) atomicMax(p.rmax + k, bits);
     if (bits < __ldcg(p.rmin + k)) atomicMin(p.rmin + k, bits);

@@ -1908,6 +1908,16 @@ gnm_status gnm_lookup(gnm_ctx* c, const uint32_t* addr, uint64_t n, uint32_t* si
 
 uint32_t gnm_last_launch_count(const gnm_ctx* c) { return c ? c->last_launches : 0; }
 
+gnm_status gnm_rates(const uint64_t* e_octets, const uint64_t* e_dur_ms, uint64_t n, double* rate,
+                     void* stream) {
+    if (n == 0) return GNM_OK;
+    if (!e_octets || !e_dur_ms || !rate) return fail(GNM_E_INVAL, "NULL array");
+    const uintptr_t mis = (uintptr_t)e_octets | (uintptr_t)e_dur_ms | (uintptr_t)rate;
+    if (mis & 7u) return fail(GNM_E_INVAL, "arrays must be 8-byte aligned");
+    GNM_CU(launch_rates(e_octets, e_dur_ms, n, rate, (cudaStream_t)stream));
+    return GNM_OK;
+}
+
 gnm_status gnm_registry_flatten(const uint32_t* prefix, const uint8_t* len, const uint32_t* site_id,
                                 size_t n, uint32_t n_sites, uint32_t* starts, uint32_t* site,
                                 size_t cap, size_t* n_out) {

@@ -314,6 +314,9 @@ cudaError_t launch_flag_compact(const double* rate, const uint64_t* stats, uint3
                                 uint32_t* out_count, cudaStream_t st);
 cudaError_t launch_lookup(const AggParams& p, int lookup, const uint32_t* addr, uint64_t n,
                           uint32_t* site_out, uint32_t* pos_out, cudaStream_t st);
+// Rates of n given (eligible octets, eligible milliseconds) sums (the rate step alone).
+cudaError_t launch_rates(const uint64_t* e_octets, const uint64_t* e_dur_ms, uint64_t n, double* rate,
+                         cudaStream_t st);
 
 // Unique id of the calling thread's current CUDA context (the driver's cuCtxGetId,
 // reached through the runtime's driver entry point, so the library does not link the

@@ -276,6 +276,25 @@ cudaError_t launch_flag_compact(const double* rate, const uint64_t* stats, uint3
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void k_rates(const uint64_t* __restrict__ eo, const uint64_t* __restrict__ ed, uint64_t n,
+                        double* __restrict__ rate) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        rate[i] = dev::rate_of_sums(__ldg(eo + i), __ldg(ed + i));
+}
+}  // namespace
+
+cudaError_t launch_rates(const uint64_t* e_octets, const uint64_t* e_dur_ms, uint64_t n, double* rate,
+                         cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint64_t want = (n + 255) / 256, cap = (uint64_t)(sms > 0 ? sms : 1) * 8;
+    k_rates<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(e_octets, e_dur_ms, n, rate);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_lookup(const AggParams& p, int lookup, const uint32_t* addr, uint64_t n,
                           uint32_t* site_out, uint32_t* pos_out, cudaStream_t st) {
     if (n == 0) return cudaSuccess;

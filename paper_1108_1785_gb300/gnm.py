@@ -162,6 +162,7 @@ def lib():
             "gnm_windows_results_async": (st, [P, P, S, P, P, P, P, P]),
             "gnm_window_release": (st, [P, U64]),
             "gnm_lookup": (st, [P, P, U64, P, P, P]),
+            "gnm_rates": (st, [P, P, U64, P, P]),
             "gnm_rmi_config_default": (None, [C.POINTER(RmiConfig)]),
             "gnm_rmi_train": (st, [P, P, U64, C.POINTER(RmiConfig), C.POINTER(RmiReport), P]),
             "gnm_rmi_violations": (st, [P, C.POINTER(U64), C.c_int]),
@@ -278,6 +279,15 @@ def registry_flatten(prefix, plen, site, n_sites: int) -> Tuple[np.ndarray, np.n
     _check(None, lib().gnm_registry_flatten(_ptr(p), _ptr(l), _ptr(s), p.size, n_sites, _ptr(a), _ptr(b),
                                             n.value, C.byref(n)))
     return a, b
+
+
+def rates(e_octets, e_dur_ms, rate, stream=None):
+    """The rate step alone (gnm_rates): rate[i] = e_octets[i] * 8000 / e_dur_ms[i] as the window
+    calls compute it, for device uint64 tensors of sums and a float64 device tensor."""
+    n = int(e_octets.numel())
+    if int(e_dur_ms.numel()) != n or int(rate.numel()) < n:
+        raise ValueError("e_octets, e_dur_ms and rate need n entries")
+    _check(None, lib().gnm_rates(_ptr(e_octets), _ptr(e_dur_ms), n, _ptr(rate), _stream_ptr(stream)))
 
 
 def window_process_noalloc(starts, site, n_sites: int, local_prefix, local_len, rec: "Records", stats, rate, flag,
