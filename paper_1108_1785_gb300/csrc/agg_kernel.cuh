@@ -625,6 +625,11 @@ __device__ __forceinline__ void srow_add_all(const Smem& sm, const Item (&it)[R]
             if (it[j].elig) o4[j] = atomicAdd(w + 4, it[j].dur);
         }
     }
+    // an add wrapped when old > ~v; records without an add have old = 0, which never does
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < R; ++j) any |= (o1[j] > ~it[j].oc) | (o2[j] > ~it[j].pk) | (o4[j] > ~it[j].dur);
+    if (!any) return;
 #pragma unroll
     for (int j = 0; j < R; ++j) {
         if (!it[j].valid) continue;
@@ -730,13 +735,38 @@ __device__ __forceinline__ void accumulate(const Item& it, const Smem& sm, uint3
 // Direct tables with a partial-sum area: the CTA stores its rows (as they are, 16-bit
 // counts and low 32-bit sums) to its own block of the area, column by column (word c of
 // row r at c * rows + r, so that finalisation reads each column coalesced), and clears
-// them; the window's finalisation adds the blocks up. Row stride 5 is odd: lanes reading
-// consecutive rows of one column hit 32 different banks.
+// them; the window's finalisation adds the blocks up. With a multiple of four rows (and so
+// 16-byte aligned columns: blocks start 16-byte aligned), a thread takes four rows at a
+// time: their 20 words are five 16-byte shared loads (the 80-byte groups of a quarter
+// warp's lanes start in 8 different bank quads), transposed in registers into five 16-byte
+// column words. Otherwise word by word (row stride 5 is odd: lanes reading consecutive rows
+// of one column hit 32 different banks).
 __device__ __forceinline__ void dump_rows(const Smem& sm, uint32_t* dst) {
+    const uint32_t rows = sm.rows;
+    if ((rows & 3u) == 0u) {
+        const uint32_t g4 = rows >> 2, cs4 = rows >> 2;  // groups of four rows; column stride in uint4
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        for (uint32_t g = threadIdx.x; g < g4; g += blockDim.x) {
+            uint4* q = reinterpret_cast<uint4*>(sm.t + g * 4u * kRowWords);  // rows 4g .. 4g+3
+            const uint4 a = q[0], b = q[1], c = q[2], d = q[3], e = q[4];
+            q[0] = z;
+            q[1] = z;
+            q[2] = z;
+            q[3] = z;
+            q[4] = z;
+            uint4* o = reinterpret_cast<uint4*>(dst) + g;
+            __stcg(o, make_uint4(a.x, b.y, c.z, d.w));
+            __stcg(o + cs4, make_uint4(a.y, b.z, c.w, e.x));
+            __stcg(o + 2u * cs4, make_uint4(a.z, b.w, d.x, e.y));
+            __stcg(o + 3u * cs4, make_uint4(a.w, c.x, d.y, e.z));
+            __stcg(o + 4u * cs4, make_uint4(b.x, c.y, d.z, e.w));
+        }
+        return;
+    }
 #pragma unroll 1
     for (int c = 0; c < kRowWords; ++c)
-        for (uint32_t r = threadIdx.x; r < sm.rows; r += blockDim.x) {
-            __stcg(dst + (size_t)c * sm.rows + r, sm.t[r * kRowWords + c]);
+        for (uint32_t r = threadIdx.x; r < rows; r += blockDim.x) {
+            __stcg(dst + (size_t)c * rows + r, sm.t[r * kRowWords + c]);
             sm.t[r * kRowWords + c] = 0;
         }
 }
@@ -1476,8 +1506,13 @@ __global__ void __launch_bounds__(agg_block_max(LOOKUP, TABLE, AGG, U))
     sm.rows = TABLE == kTableDirect ? p.table_rows : (TABLE == kTableHash ? p.table_cap : 0u);
     sm.t = reinterpret_cast<uint32_t*>(smem_raw);
     sm.tk = reinterpret_cast<uint32_t*>(smem_raw + off_keys);
-    // stage the table (zero), the registry or the leaf parameters
-    for (uint32_t i = tid; i < sm.rows * kRowWords; i += B) sm.t[i] = 0;
+    // stage the table (zero; 16-byte stores, the table starts 16-byte aligned), the registry
+    // or the leaf parameters
+    {
+        const uint32_t words = sm.rows * kRowWords, w4 = words >> 2;
+        for (uint32_t i = tid; i < w4; i += B) reinterpret_cast<uint4*>(sm.t)[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (uint32_t i = 4u * w4 + tid; i < words; i += B) sm.t[i] = 0;
+    }
     if (TABLE == kTableHash)
         for (uint32_t i = tid; i < p.table_cap; i += B) sm.tk[i] = kEmptyKey;
     stage_lookup<LOOKUP>(p, smem_raw + off_lookup, sm);
