@@ -650,6 +650,8 @@ def main():
     ap.add_argument("--e2e-host", default="auto", choices=["auto", "stage", "in_place", "pipeline"],
                     help="how the end-to-end leg's page-locked host records reach the kernels "
                          "(gnm_config.host_records)")
+    ap.add_argument("--e2e-streams", type=int, default=2,
+                    help="compute streams that consecutive end-to-end steps alternate between")
     ap.add_argument("--learned-records", type=int, default=50_000_000)
     ap.add_argument("--learned-modes", default="bsearch,radix,rmi,rmi_mse,rmi65536")
     ap.add_argument("--serve-speedup", type=float, default=1000.0,
@@ -827,9 +829,13 @@ def main():
                  host(n_win * nk, np.uint8)) for _ in range(2)]
         sets = [ids + n_win, ids + 2 * n_win]
         copy_stream = torch.cuda.Stream()
+        # consecutive steps alternate between compute streams (each step's windows and the
+        # library's launch buffers are its own), so that one step's device-only work (its
+        # finalisation, kernel ramps) overlaps the next step's reads over the host link
+        comp = [stream] + [torch.cuda.Stream() for _ in range(max(1, args.e2e_streams) - 1)]
 
         def e2e_step(k):
-            ctx.process_windows(hostrec, off, sets[k % 2], stream)
+            ctx.process_windows(hostrec, off, sets[k % 2], comp[k % len(comp)])
             ctx.windows_results_async(sets[k % 2], *outs[k % 2], stream=copy_stream)
 
         for k in range(max(2, args.warmup)):
@@ -843,12 +849,30 @@ def main():
         copy_stream.synchronize()
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+        # the host link: a plain copy of the same page-locked records (best of three)
+        dst = {k: torch.empty_like(v, device=f"cuda:{local}") for k, v in pinned.items() if k in gnm.FIELDS}
+        best = None
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for k in dst:
+                dst[k].copy_(pinned[k], non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            best = a.elapsed_time(b) if best is None else min(best, a.elapsed_time(b))
+        h2d_gbs = sum(v.numel() * v.element_size() for v in dst.values()) / (best / 1e3) / 1e9
+        del dst
         out["e2e"] = {"value": n * world * args.steps / e2e_s, "unit": "records/s",
                       "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": n_win * (nk * (48 + 8 + 1) + 4 * 48),
                       "api": "gnm_windows_process over page-locked host records (host_records "
                              f"{args.e2e_host.upper()}: " + E2E_HOST[args.e2e_host] + ") + "
                              "gnm_windows_results_async (sums, unmatched classes, rates, flags) on a second "
-                             "stream, overlapping the next step's processing; two sets of window ids alternate"}
+                             "stream, overlapping the next step's processing; two sets of window ids alternate"
+                             + (f", consecutive steps on {len(comp)} compute streams" if len(comp) > 1 else ""),
+                      "h2d_copy_gbs": h2d_gbs,
+                      "records_bound": h2d_gbs * 1e9 / 24,
+                      "bound_note": "a plain copy of the step's page-locked records to the device, timed "
+                                    "in the same run; at 24 bytes a record it bounds e2e"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
