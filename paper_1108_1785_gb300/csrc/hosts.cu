@@ -5,6 +5,7 @@
 // 64-bit atomic adds (integer sums: exact in any order).
 #include <cuda_runtime.h>
 
+#include "agg_kernel.cuh"  // (rate_of_sums)
 #include "gnm_internal.cuh"
 
 namespace gnm {
@@ -86,14 +87,11 @@ __global__ void __launch_bounds__(kHostThreads)
 }
 
 // Rate of every host entry (as the per-site rate: octets * 8 bits / (ms / 1000), one
-// rounding per operation; NaN without eligible duration).
+// rounding per operation, formed on the integer units; NaN without eligible duration).
 __global__ void k_host_rates(const unsigned long long* __restrict__ rows, uint32_t n, double* __restrict__ rate) {
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += stride) {
-        const unsigned long long eo = rows[(size_t)h * kNStat + 4], ed = rows[(size_t)h * kNStat + 5];
-        rate[h] = ed ? __ddiv_rn(__dmul_rn(__ull2double_rn(eo), 8000.0), __ull2double_rn(ed))
-                     : __longlong_as_double(0x7FF8000000000000ll);
-    }
+    for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += stride)
+        rate[h] = dev::rate_of_sums(rows[(size_t)h * kNStat + 4], rows[(size_t)h * kNStat + 5]);
 }
 
 }  // namespace
