@@ -525,3 +525,21 @@ def test_hash24_batch_lookup_and_limits(gnm, reg24):
     with pytest.raises(gnm.GnmError, match="longer than /24"):
         longer.process(gnm.Records.to_device(fg.make_records(fg.registry_c2(), 1000, seed=2)), 1)
     longer.close()
+
+
+@pytest.mark.parametrize("n_sites", [4999, 2001])
+def test_odd_site_count_windows_equal_oracle(gnm, n_sites):
+    """Registries with an odd number of sites (2 * n_sites + 4 keys, not a multiple of four):
+    the aggregation stores its partial blocks word by word instead of in 16-byte column
+    words. Three windows of 700,000 records each (many CTAs per window, several count
+    hand-overs per CTA), split launches and one fused launch, every window equal to the
+    oracle."""
+    reg = fg.make_registry(n_sites, 8 * n_sites, fg.C2_LEN, 0.2, seed=n_sites)
+    recs = [fg.make_records(reg, 700_000, seed=n_sites + k, p_reg=0.85, zipf_s=1.0) for k in range(3)]
+    lpm = oracle.LPM(reg.prefix, reg.plen, reg.site)
+    for cfg in ({}, {"split": gnm.SPLIT_FUSED, "lookup_mode": gnm.LOOKUP_BSEARCH, "placement": gnm.PLACE_L2}):
+        ctx = _ctx(gnm, reg, window_slots=8, **cfg)
+        for w, rec in enumerate(recs):
+            ctx.process(gnm.Records.to_device(rec), 40 + w)
+            assert_window_matches(ctx.dense(40 + w), oracle_full(reg, rec, lpm=lpm))
+        ctx.close()
